@@ -1,0 +1,351 @@
+"""Throughput benchmark of the GB300 central-moment LBM (one JSON line on rank 0).
+
+Default workload: the 256^3 smoke plume (inflow disk of radius 16 at u = 0.1 with a seeded
++/-1 % perturbation, voxelised sphere of radius 24, open faces, nu = 1e-5, passive scalar),
+FP32 storage.  A step is one reference step of the whole hot path: one fused
+collide-stream + scalar launch over every node.  The state (1.9 GB) is far larger than L2,
+so no flush is needed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload plume256|plume256_fp16]
+                  [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this build: there is
+no runnable reference code) on a bounded sample of the same workload.
+Under torchrun each rank advances its own replica (the single-domain workload is not
+partitioned: "replicas only"); value = all ranks' lattice updates / max wall time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1807_02284_gb300", "csrc")
+    for fn in ("lbm_device.cuh", "lbm_cell.cuh", "kernels_step.cu"):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload):
+    """DRAM bytes per launch of the collide-stream kernel from the committed ncu summary,
+    or None when the summary is missing or was taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"k_step_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    hm = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    if not m or not hm or hm.group(1) != _kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, val):
+    if ws == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _workload(name):
+    import synth
+    storage = "fp16" if name.endswith("fp16") else "fp32"
+    sc = synth.plume(256)
+    return sc, storage
+
+
+def _algorithmic_bytes(flags, storage):
+    """Bytes the collide-stream launch must move per step, by node kind: fluid nodes read
+    and write 27 populations, the lagged velocity and the scalar; obstacle voxels only write
+    their rest state; inflow nodes read their velocity and write their equilibrium."""
+    pop = 2 if storage == "fp16" else 4
+    solid = int(((flags & 1) != 0).sum())
+    inflow = int(((flags & 2) != 0).sum()) - int(((flags & 3) == 3).sum())
+    fluid = flags.size - solid - inflow
+    per_fluid = 27 * pop * 2 + 12 * 2 + 4 * 2 + 1
+    per_solid = 27 * pop + 12 + 4 + 1
+    per_inflow = 27 * pop + 12 * 2 + 4 * 2 + 1
+    return fluid * per_fluid + solid * per_solid + inflow * per_inflow, per_fluid
+
+
+def cpu_baseline_measure(budget_s=15.0):
+    """The FP64 oracle as it stands, on a bounded sample of the plume workload: the same
+    scene geometry scaled to a 32^3 box (inflow disk, sphere, open faces), stepped until
+    about ``budget_s`` seconds of CPU time have been spent."""
+    import torch
+
+    import synth
+    from oracle import grid
+    sc = synth.plume(32)
+    b = sc.blocks[0]
+    st = grid.init_state(b.rho0, b.u0, b.c0, b.flags)
+    p = grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=sc.adaptive, c_src=sc.c_src)
+    st = grid.step(st, p)  # warm-up
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        st = grid.step(st, p)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    mlups = b.flags.size * n / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": int(torch.get_num_threads()),
+            "kind": "oracle",
+            "sample": f"oracle (FP64, dense per-node M and LU solve) on the plume geometry "
+                      f"scaled to 32^3, {n} full steps in {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
+    import torch
+
+    import synth
+    from oracle import grid
+    sc = synth.plume(32)
+    b = sc.blocks[0]
+    st = grid.init_state(b.rho0, b.u0, b.c0, b.flags)
+    p = grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=sc.adaptive, c_src=sc.c_src)
+    for _ in range(warm):
+        st = grid.step(st, p)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = grid.step(st, p)
+    el = time.perf_counter() - t0
+    mlups = b.flags.size * steps / el / 1e6
+    cores = int(torch.get_num_threads())
+    sample = (f"oracle (FP64 CPU, dense per-node M and LU solve) on the plume geometry scaled "
+              f"to 32^3 (the 256^3 step takes minutes on the CPU), {steps} timed steps")
+    line = {"impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+            "ms_per_step": el / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "plume256_fp32", "nodes": int(b.flags.size),
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import synth
+    from paper_1807_02284_gb300 import lbm
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    sc, storage = _workload(args.workload)
+    b = sc.blocks[0]
+    stream = torch.cuda.Stream(device=dev)
+    dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, storage=storage,
+                     adaptive=sc.adaptive, c_src=sc.c_src, stream=stream)
+    dom.set_flags(b.flags)
+    dom.init_macro(b.u0.astype(np.float32), rho=b.rho0.astype(np.float32),
+                   c=b.c0.astype(np.float32))
+    N = b.flags.size
+    K, W = args.steps, args.warmup
+
+    # ---- device-resident throughput (value) and the collide-stream roofline
+    dom.step(W)
+    dom.sync()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    dom.step(K)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clk = clocks.stop()
+    dom.sync()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    t_max = _max_over_ranks(ws, t_dev)
+    value = N * K * ws / t_max / 1e6
+
+    alg_bytes, per_fluid = _algorithmic_bytes(b.flags, storage)
+    peak, peak_src = _peaks()
+    achieved = alg_bytes / (t_dev / K) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _profiled_traffic(args.workload),
+                "peak_source": peak_src, "kernel": "k_step (fused pull/collide/scalar)",
+                "bytes_per_fluid_node": per_fluid}
+
+    # ---- end to end through the public API with host buffers
+    E = max(3, min(K, 50))
+    recs = synth.inflow_records(b)
+    rng = np.random.default_rng(123)
+    pinned = torch.empty(recs.nbytes, dtype=torch.uint8, pin_memory=True)
+    host_recs = pinned.numpy().view(lbm.INFLOW_RECORD)
+    base = np.stack([recs["ux"], recs["uy"], recs["uz"]]).astype(np.float32)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(E):
+        host_recs[:] = recs
+        jitter = (1.0 + 0.01 * (2 * rng.random(base.shape) - 1)).astype(np.float32)
+        host_recs["ux"] = base[0] * jitter[0]
+        dom.set_inflow(host_recs)
+        dom.step(1)
+        red = dom.reduce()
+    t_e2e = time.perf_counter() - t0
+    t_e2e = _max_over_ranks(ws, t_e2e)
+    e2e = {"value": N * E * ws / t_e2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": int(recs.nbytes), "d2h_bytes_per_step": 5 * 8,
+           "steps": E, "api": "lbm_set_boundary(INFLOW, pinned host) + lbm_step(1) + "
+                             "lbm_reduce(host)"}
+
+    if rank == 0:
+        line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": K,
+                "warmup": W, "ms_per_step": t_max / K * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f16-storage/f32-math" if storage == "fp16" else "f32",
+                "data": "synthetic",
+                "config": {"workload": f"plume256_{storage}", "nodes": int(N),
+                           "dims": list(b.dims), "storage": storage,
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "inputs larger than L2 (state %.2f GB)" %
+                                 (N * (27 * (2 if storage == 'fp16' else 4) * 2 + 32) / 1e9)},
+                "gb_per_s_algorithmic": achieved,
+                "roofline": roofline,
+                "e2e": e2e,
+                "gpu_launches": K,
+                "clocks": clk,
+                "mass_check": float(red[0])}
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_measure(args.cpu_budget)
+        print(json.dumps(line), flush=True)
+    dom.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--workload", default="plume256",
+                    choices=["plume256", "plume256_fp16"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/* C-ABI of the GB300 continuous-scale central-moment lattice Boltzmann library.
+ *
+ * Method: arXiv 1807.02284 (Li, Bai, Liu, "Continuous-Scale Kinetic Fluid Simulation").
+ *   - D3Q27 lattice Boltzmann equation, stream + collide            Sec. 1 (LBE), Appendix
+ *   - non-orthogonal central-moment collision Omega = -T S (m-m^eq)  Sec. 3.1, Appendix
+ *   - adaptive high-order relaxation                                 Sec. 4.1
+ *   - continuous-scale blocks: K-hat rescale, prior-/post-mapping,
+ *     trilinear + temporal interpolation, Algorithm 1 schedule       Sec. 3.2, 4.2, Alg. 1
+ *   - initial equilibrium, inflow, open (Neumann) boundaries         Sec. 6.1
+ *
+ * Conventions for every entry point
+ *   - Returns lbm_status; never throws, aborts or traps.  On failure the domain's
+ *     lbm_last_error() string says why.
+ *   - Pointers flagged by `on_device` != 0 are device pointers on the domain's device;
+ *     otherwise host pointers (pinned or pageable).  Caller memory is never retained: the
+ *     library copies what it needs before returning and never frees caller memory.
+ *   - Library buffers come from desc.alloc (e.g. PyTorch's caching allocator) or, when
+ *     desc.alloc.alloc is NULL, from cudaMalloc.  They are released by lbm_destroy_domain.
+ *   - All GPU work is ordered on desc.cuda_stream (NULL: the library creates its own).
+ *     Calls that return data to the host synchronise that stream; lbm_step only enqueues.
+ *   - Device-side failures (non-finite density, bad inflow record) are recorded in a device
+ *     error word and reported by the next synchronising call as LBM_ERR_DIVERGED.
+ *   - Calls on one domain are not thread-safe; different domains are independent.
+ *   - Array layout: node (x, y, z) of a block with dims (nx, ny, nz) has linear index
+ *     (z*ny + y)*nx + x.  Vector fields are 3 planes (x, y, z components) of N = nx*ny*nz;
+ *     populations are 27 planes in the order of the paper's Appendix velocity list (with
+ *     index 13 read as (1,0,-1), the printed list duplicates (1,0,1)).
+ *   - Units: lattice units of the block (dx = dt = 1 on the block's own grid).  Velocity
+ *     is the same number on every scale because dt = dx on each scale (Sec. 4.2.4).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_domain lbm_domain; /* opaque; owned by the library */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_INVALID_ARG = 1, /* bad pointer, size, block id, enum value or geometry */
+  LBM_ERR_OOM = 2,         /* allocation failed */
+  LBM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in lbm_last_error) */
+  LBM_ERR_DIVERGED = 4,    /* a node reached a non-finite or non-positive density */
+  LBM_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  LBM_ERR_UNSUPPORTED = 6, /* valid request outside what this build implements */
+  LBM_ERR_STATE = 7        /* call not valid in the current state (e.g. no tape) */
+} lbm_status;
+
+/* storage of the populations */
+enum { LBM_FP32 = 0, LBM_FP16_SHIFTED = 1 };
+
+/* lbm_set_boundary kinds */
+enum {
+  LBM_BC_FLAGS = 0,  /* uint8 per node (N bytes): bit0 obstacle voxel (halfway bounce-back),
+                        bit1 Dirichlet inflow node, bit2 scalar source node.  Replaces the
+                        three bits on every node; other bits are library-owned. */
+  LBM_BC_INFLOW = 1  /* array of lbm_inflow_record: marks the nodes as inflow (clearing the
+                        obstacle bit) and sets their inflow velocity.  Records outside the
+                        block are skipped and reported as LBM_ERR_DIVERGED-class device
+                        errors by the next synchronising call. */
+};
+
+typedef struct {
+  int32_t x, y, z;
+  float ux, uy, uz;
+} lbm_inflow_record;
+
+/* lbm_read_field / lbm_write_field selectors */
+enum {
+  LBM_FIELD_F = 0,      /* populations f_i, 27*N values (read/write) */
+  LBM_FIELD_U = 1,      /* velocity stored by the last step, 3*N (read/write) */
+  LBM_FIELD_SCALAR = 2, /* passive scalar, N (read/write) */
+  LBM_FIELD_RHO = 3,    /* density sum_i f_i, N (read only) */
+  LBM_FIELD_FLAGS = 4   /* uint8 node flags, N (read only; bit3 = scale-boundary ghost) */
+};
+/* element types */
+enum { LBM_F32 = 0, LBM_F64 = 1, LBM_U8 = 2 };
+
+/* lbm_read_macro selectors (float32 output) */
+enum { LBM_MACRO_RHO = 0, LBM_MACRO_U = 1, LBM_MACRO_SCALAR = 2 };
+
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx);       /* returns device memory or NULL */
+  void (*free)(void* p, size_t bytes, void* ctx);
+  void* ctx;
+} lbm_allocator;
+
+typedef struct {
+  int32_t dims[3];     /* nx, ny, nz of the reference block s0 (>= 1 each) */
+  int32_t periodic[3]; /* per axis: 1 periodic, 0 open (zero-gradient copy, Sec. 6.1) */
+  double nu;           /* kinematic viscosity in reference-scale lattice units; S_4..8 =
+                          1/(3 nu + 1/2) (Sec. 3.1, Eq. 3); must be > 0 */
+  int32_t storage;     /* LBM_FP32 or LBM_FP16_SHIFTED (f_i - w_i stored as binary16) */
+  int32_t adaptive;    /* 1: adaptive high-order relaxation of Sec. 4.1; 0: fixed nu' */
+  double a, b, g_max;  /* Sec. 4.1 parameters (paper: -4, 5, g_max in [0.1, 0.13]) */
+  double nu_hi[4];     /* Appendix artificial viscosities of moment groups 9..16, 17..22,
+                          23..25, 26 (paper: 0.005, 0.007, 0.009, 0.01) */
+  double c_src;        /* scalar value imposed on scalar-source nodes */
+  void* cuda_stream;   /* cudaStream_t or NULL */
+  lbm_allocator alloc; /* alloc.alloc == NULL: cudaMalloc / cudaFree */
+  int32_t device;      /* CUDA device ordinal */
+} lbm_domain_desc;
+
+typedef struct {
+  int32_t dims[3];
+  double origin[3];  /* position of node (0,0,0) in reference-scale units */
+  double h;          /* node spacing relative to the reference scale (dx_s / dx_0) */
+  double nu;         /* viscosity in this block's lattice units (nu_0 / h, Sec. 3.2 Eq. 4) */
+  int32_t substeps;  /* sub-steps per reference step (1 for s0) */
+  int64_t steps;     /* reference steps taken by the domain */
+} lbm_block_info;
+
+/* Version of this header's ABI. */
+int32_t lbm_abi_version(void);
+
+/* Fills *desc with the paper's defaults (a=-4, b=5, g_max=0.1, nu' table, adaptive on,
+   FP32, non-periodic, c_src=1, device 0, cudaMalloc).  dims and nu are set to 0 and must be
+   filled by the caller. */
+lbm_status lbm_default_desc(lbm_domain_desc* desc);
+
+/* Creates a domain whose block 0 is the reference scale s0 with h = 1 (Sec. 4.2.4,
+   "reference scale").  Populations start at the rest equilibrium, u = 0, scalar 0, no
+   flags.  *out receives the handle.  INVALID_ARG for bad dims/nu/storage, OOM, CUDA. */
+lbm_status lbm_create_domain(const lbm_domain_desc* desc, lbm_domain** out);
+
+/* Releases every library buffer of the domain.  NULL is accepted. */
+lbm_status lbm_destroy_domain(lbm_domain* dom);
+
+/* Adds a finer scale block (Sec. 4.2: blocks at arbitrary, non-integer spacing ratios
+   overlaid on coarser ones).  origin: position of its node (0,0,0) in reference units;
+   h = dx_s/dx_0 in (0, 1); dims >= 4 per axis.  The whole block must lie inside block 0
+   and inside every block it is nested in; its outermost node layer is the scale boundary
+   (ghost layer) written by prior-mapping.  Blocks must be added coarse to fine (h not
+   increasing).  UNSUPPORTED for h >= 1 (far-field scales) and for FP16 storage. */
+lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3], double h,
+                               const int32_t dims[3], int32_t* block_id);
+
+/* Sets boundary data of one block (see LBM_BC_*).  ptr/nbytes describe the caller array;
+   it is copied before return (host) or before the next enqueued work (device). */
+lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, const void* ptr,
+                            size_t nbytes, int32_t on_device);
+
+/* Initialises block populations to the equilibrium f = T m^eq(rho, u) (Algorithm 1 and
+   Sec. 6.1), the stored velocity to u and the scalar to c.  rho (N floats) and c (N floats)
+   may be NULL (rho = 1, c = 0); u (3*N floats) is required.  Obstacle voxels get the rest
+   state.  Clears the device error word and any recorded tape. */
+lbm_status lbm_init_macro(lbm_domain* dom, int32_t block_id, const float* rho, const float* u,
+                          const float* c, int32_t on_device);
+
+/* Advances the whole domain by n reference steps (Algorithm 1: s0 one step, then every
+   finer block coarse to fine with prior-mapping, l sub-steps, temporal alignment and
+   post-mapping to all coarser blocks).  Enqueues only; returns the status of host checks
+   and of previously recorded device errors. */
+lbm_status lbm_step(lbm_domain* dom, int32_t n_reference_steps);
+
+/* Waits for the domain's stream and reports device errors (DIVERGED) recorded so far. */
+lbm_status lbm_sync(lbm_domain* dom);
+
+/* Reads rho, u (3 planes) or the scalar of a block as float32 into dst (dst_bytes must be
+   at least the field size).  Synchronises. */
+lbm_status lbm_read_macro(lbm_domain* dom, int32_t block_id, int32_t what, void* dst,
+                          size_t dst_bytes, int32_t on_device);
+
+/* Reads a field (LBM_FIELD_*) of a block as LBM_F32 / LBM_F64 (LBM_U8 for flags).
+   Populations are returned unshifted (f_i, not f_i - w_i) in the paper's velocity order.
+   Synchronises. */
+lbm_status lbm_read_field(lbm_domain* dom, int32_t block_id, int32_t field, int32_t dtype,
+                          void* dst, size_t dst_bytes, int32_t on_device);
+
+/* Overwrites a field (F, U or SCALAR) of a block's current state from F32/F64 data.
+   Populations are unshifted and in the paper's order.  Clears the device error word. */
+lbm_status lbm_write_field(lbm_domain* dom, int32_t block_id, int32_t field, int32_t dtype,
+                           const void* src, size_t src_bytes, int32_t on_device);
+
+/* FP64 diagnostics of a block over non-obstacle, non-ghost nodes:
+   out[0] mass sum rho, out[1..3] momentum sum rho u, out[4] kinetic energy
+   (1/2) sum rho |u|^2.  out is a host array of 5 doubles.  Synchronises; returns DIVERGED
+   if the device error word is set. */
+lbm_status lbm_reduce(lbm_domain* dom, int32_t block_id, double out[5]);
+
+lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block_info* info);
+
+/* Advances n independent single-block domains by `steps` reference steps with one
+   persistent kernel per step over a joint tile work list, captured in one CUDA graph and
+   launched on doms[0]'s stream (tile shape chosen by the library's autotuner on first use).
+   Every domain must be single-block, with the same storage and device.  Results are
+   bit-identical to calling lbm_step on each domain. */
+lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t steps);
+
+/* Enables recording of a reverse-mode tape by lbm_step: the state is checkpointed every
+   `checkpoint_every` steps from the last lbm_init_macro (k >= 1; 0 disables). */
+lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every);
+
+/* Reverse-mode gradient of a loss L(c_T, u_T) of the final scalar and velocity of block 0
+   after the n_steps steps recorded since the last lbm_init_macro (n_steps must equal the
+   recorded count): dL_dscalar_final (N floats, device) and dL_du_final (3N floats, device,
+   may be NULL) in; dL_du0 (3N floats, device) receives dL/du_0 for the u passed to
+   lbm_init_macro.  dL_dinflow must be NULL (UNSUPPORTED otherwise).  Single-block domains
+   with FP32 storage and periodic faces only (UNSUPPORTED otherwise).  Not in the paper. */
+lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dscalar_final,
+                            const float* dL_du_final, float* dL_du0, float* dL_dinflow);
+
+/* Message of the last failure on this domain (empty if none); valid until the next call
+   on the domain.  NULL dom gives the message of the last failed lbm_create_domain. */
+const char* lbm_last_error(const lbm_domain* dom);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -20,7 +20,8 @@ Per step and per node x (LBE of Sec. 1 / Appendix, iterated in pull form):
      coarse-to-fine mapping).
   6. Passive scalar (stands in for the paper's smoke particles, Sec. 6.4): semi-Lagrangian
      c^{n+1}(x) = trilinear sample of c^n at x - u^{n+1}(x) (periodic wrap or clamp to the
-     block); source nodes are reset to c_src; obstacle voxels hold 0.
+     block; each displacement component limited to one node, which only matters for the
+     non-physical |u| >= 1); source nodes are reset to c_src; obstacle voxels hold 0.
 
 An optional ``body_force`` (test-only; not part of the paper's solver) adds the
 exact-difference forcing f += f^eq(rho, u + F/rho) - f^eq(rho, u) after the collision; it
@@ -184,8 +185,10 @@ def step_cells(st: State, p: Params, z: torch.Tensor, y: torch.Tensor, x: torch.
         f_post[is_ghost] = st.f[:, z, y, x].T[is_ghost]
         u[is_ghost] = u_own[is_ghost]
 
-    # 6. passive scalar
-    c_new = sample_trilinear(st.c, x.to(DT) - u[:, 0], y.to(DT) - u[:, 1], z.to(DT) - u[:, 2], per)
+    # 6. passive scalar (departure point at most one node away: |u| < 1 in any stable run)
+    dsp = torch.clamp(-u, -1.0, 1.0)
+    c_new = sample_trilinear(st.c, x.to(DT) + dsp[:, 0], y.to(DT) + dsp[:, 1],
+                             z.to(DT) + dsp[:, 2], per)
     c_new = torch.where((fl & SCALAR_SRC) != 0, torch.full_like(c_new, p.c_src), c_new)
     c_new = torch.where(is_solid, torch.zeros_like(c_new), c_new)
     c_new = torch.where(is_ghost, st.c[z, y, x], c_new)

@@ -1,0 +1,291 @@
+// Single-block kernels: collide-stream step, equilibrium initialisation, flag derivation,
+// field conversion and the deterministic FP64 diagnostics reduction.
+#include "lbm_cell.cuh"
+
+namespace lbm {
+
+// Paper velocity index q (Appendix list, index 13 read as (1,0,-1)) -> cube slot k.
+__constant__ int c_paper_to_cube[27] = {13, 14, 12, 16, 10, 22, 4,  17, 15, 11, 9,  23, 21, 5,
+                                        3,  25, 19, 7,  1,  26, 24, 20, 18, 8,  6,  2,  0};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_step(BlockView v) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= v.nx || y >= v.ny) return;
+  cell_update<T>(v, x, y, z);
+}
+
+cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s) {
+  dim3 block(bx, by, 1);
+  dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, v.nz);
+  if (storage == ST_FP16) k_step<__half><<<grid, block, 0, s>>>(v);
+  else k_step<float><<<grid, block, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
+// f_0 = f^eq(rho_0, u_0) (Algorithm 1 initialisation); obstacle voxels hold the rest state.
+template <typename T>
+__global__ void k_init(BlockView v, const float* rho, const float* u, const float* c) {
+  const size_t N = v.N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    T* dout = static_cast<T*>(v.d_out);
+    const bool solid = v.flags[idx] & F_SOLID;
+    const float r = (rho && !solid) ? rho[idx] : 1.0f;
+    const float ux = solid ? 0.f : u[idx], uy = solid ? 0.f : u[N + idx],
+                uz = solid ? 0.f : u[2 * N + idx];
+    float d[27];
+    equilibrium(d, r, ux, uy, uz);
+#pragma unroll
+    for (int k = 0; k < 27; ++k) store_pop(dout + (size_t)k * N + idx, d[k]);
+    v.u_out[idx] = ux; v.u_out[N + idx] = uy; v.u_out[2 * N + idx] = uz;
+    v.c_out[idx] = (solid || !c) ? 0.0f : c[idx];
+  }
+}
+
+cudaError_t launch_init(const BlockView& v, int storage, const float* rho, const float* u,
+                        const float* c, cudaStream_t s) {
+  const int threads = 256;
+  const size_t want = (v.N + threads - 1) / threads;
+  const int grid = (int)(want < 65535 ? want : 65535);
+  if (storage == ST_FP16) k_init<__half><<<grid, threads, 0, s>>>(v, rho, u, c);
+  else k_init<float><<<grid, threads, 0, s>>>(v, rho, u, c);
+  return cudaGetLastError();
+}
+
+// User bits (obstacle, inflow, scalar source) replace the node's; library bits are kept.
+__global__ void k_merge_user_flags(uint8_t* flags, const uint8_t* user, size_t N) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint8_t keep = flags[i] & (F_GHOST);
+    flags[i] = keep | (user[i] & (F_SOLID | F_INFLOW | F_SCALAR_SRC));
+  }
+}
+
+cudaError_t launch_merge_user_flags(uint8_t* flags, const uint8_t* user, size_t N,
+                                    cudaStream_t s) {
+  const size_t g = (N + 255) / 256;
+  k_merge_user_flags<<<(int)(g < 8192 ? g : 8192), 256, 0, s>>>(flags, user, N);
+  return cudaGetLastError();
+}
+
+// Derived flag: F_NEAR_SOLID when any pull source of a non-solid node is an obstacle voxel.
+__global__ void k_near_solid(uint8_t* flags, int nx, int ny, int nz, int px, int py, int pz) {
+  const size_t N = (size_t)nx * ny * nz;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((size_t)nx * ny));
+    bool near = false;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (!dx && !dy && !dz) continue;
+          const int sx = nbr(x, dx, nx, px), sy = nbr(y, dy, ny, py), sz = nbr(z, dz, nz, pz);
+          near |= (flags[((size_t)sz * ny + sy) * nx + sx] & F_SOLID) != 0;
+        }
+    uint8_t f = flags[idx];
+    f = near ? (f | F_NEAR_SOLID) : (f & ~F_NEAR_SOLID);
+    flags[idx] = f;
+  }
+}
+
+cudaError_t launch_near_solid(uint8_t* flags, int nx, int ny, int nz, const int per[3],
+                              cudaStream_t s) {
+  const size_t N = (size_t)nx * ny * nz;
+  const int grid = (int)((N + 255) / 256 < 65535 ? (N + 255) / 256 : 65535);
+  k_near_solid<<<grid, 256, 0, s>>>(flags, nx, ny, nz, per[0], per[1], per[2]);
+  return cudaGetLastError();
+}
+
+struct InflowRec {
+  int x, y, z;
+  float ux, uy, uz;
+};
+
+__global__ void k_inflow_records(const InflowRec* rec, int n, uint8_t* flags, float* u0, float* u1,
+                                 float* u2, int nx, int ny, int nz, size_t N, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const InflowRec r = rec[i];
+  if (r.x < 0 || r.y < 0 || r.z < 0 || r.x >= nx || r.y >= ny || r.z >= nz) {
+    atomicOr(err, 4);  // bad record: ignored, reported
+    return;
+  }
+  const size_t idx = ((size_t)r.z * ny + r.y) * nx + r.x;
+  flags[idx] = (flags[idx] | F_INFLOW) & ~F_SOLID;
+  float* lv[3] = {u0, u1, u2};
+  for (int l = 0; l < 3; ++l)
+    if (lv[l]) { lv[l][idx] = r.ux; lv[l][N + idx] = r.uy; lv[l][2 * N + idx] = r.uz; }
+}
+
+cudaError_t launch_inflow_records(const void* rec, int n, uint8_t* flags, float* const* u_levels,
+                                  int n_levels, int nx, int ny, int nz, size_t N, int* err,
+                                  cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  float* u0 = n_levels > 0 ? u_levels[0] : nullptr;
+  float* u1 = n_levels > 1 ? u_levels[1] : nullptr;
+  float* u2 = n_levels > 2 ? u_levels[2] : nullptr;
+  k_inflow_records<<<(n + 255) / 256, 256, 0, s>>>(static_cast<const InflowRec*>(rec), n, flags,
+                                                  u0, u1, u2, nx, ny, nz, N, err);
+  return cudaGetLastError();
+}
+
+// ---- field conversion ------------------------------------------------------------------
+
+template <typename T, typename O>
+__global__ void k_read_f(const T* d, size_t N, O* out) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const int k = c_paper_to_cube[q];
+      const double val = wkd(k) + (double)load_pop(d + (size_t)k * N + idx);
+      out[(size_t)q * N + idx] = (O)val;
+    }
+  }
+}
+
+template <typename T, typename I>
+__global__ void k_write_f(T* d, size_t N, const I* in) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      const int k = c_paper_to_cube[q];
+      const double dev = (double)in[(size_t)q * N + idx] - wkd(k);
+      if constexpr (sizeof(T) == 2) d[(size_t)k * N + idx] = __double2half(dev);
+      else d[(size_t)k * N + idx] = (float)dev;
+    }
+  }
+}
+
+static int grid_for(size_t n) {
+  const size_t g = (n + 255) / 256;
+  return (int)(g < 8192 ? (g ? g : 1) : 8192);
+}
+
+cudaError_t launch_read_f(const void* d, int storage, size_t N, void* out, int out_f64,
+                          cudaStream_t s) {
+  const int g = grid_for(N);
+  if (storage == ST_FP16) {
+    if (out_f64) k_read_f<__half, double><<<g, 256, 0, s>>>((const __half*)d, N, (double*)out);
+    else k_read_f<__half, float><<<g, 256, 0, s>>>((const __half*)d, N, (float*)out);
+  } else {
+    if (out_f64) k_read_f<float, double><<<g, 256, 0, s>>>((const float*)d, N, (double*)out);
+    else k_read_f<float, float><<<g, 256, 0, s>>>((const float*)d, N, (float*)out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_f(void* d, int storage, size_t N, const void* in, int in_f64,
+                           cudaStream_t s) {
+  const int g = grid_for(N);
+  if (storage == ST_FP16) {
+    if (in_f64) k_write_f<__half, double><<<g, 256, 0, s>>>((__half*)d, N, (const double*)in);
+    else k_write_f<__half, float><<<g, 256, 0, s>>>((__half*)d, N, (const float*)in);
+  } else {
+    if (in_f64) k_write_f<float, double><<<g, 256, 0, s>>>((float*)d, N, (const double*)in);
+    else k_write_f<float, float><<<g, 256, 0, s>>>((float*)d, N, (const float*)in);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_read_rho(const T* d, size_t N, float* out) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) s += load_pop(d + (size_t)k * N + idx);
+    out[idx] = 1.0f + s;
+  }
+}
+
+cudaError_t launch_read_rho(const void* d, int storage, size_t N, float* out, cudaStream_t s) {
+  const int g = grid_for(N);
+  if (storage == ST_FP16) k_read_rho<__half><<<g, 256, 0, s>>>((const __half*)d, N, out);
+  else k_read_rho<float><<<g, 256, 0, s>>>((const float*)d, N, out);
+  return cudaGetLastError();
+}
+
+template <typename I, typename O>
+__global__ void k_convert(const I* in, O* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (O)in[i];
+}
+
+cudaError_t launch_convert(const void* in, int in_f64, void* out, int out_f64, size_t n,
+                           cudaStream_t s) {
+  const int g = grid_for(n);
+  if (in_f64 && out_f64) k_convert<double, double><<<g, 256, 0, s>>>((const double*)in, (double*)out, n);
+  else if (in_f64) k_convert<double, float><<<g, 256, 0, s>>>((const double*)in, (float*)out, n);
+  else if (out_f64) k_convert<float, double><<<g, 256, 0, s>>>((const float*)in, (double*)out, n);
+  else k_convert<float, float><<<g, 256, 0, s>>>((const float*)in, (float*)out, n);
+  return cudaGetLastError();
+}
+
+// ---- diagnostics reduction ---------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(const T* d, const uint8_t* flags,
+                                                           size_t N, double* partials) {
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    if (flags[idx] & (F_SOLID | F_GHOST)) continue;
+    float dd[27];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) dd[k] = load_pop(d + (size_t)k * N + idx);
+    float drho, jx, jy, jz;
+    macros(dd, drho, jx, jy, jz);
+    const float rho = 1.0f + drho;
+    acc[0] += 1.0;
+    acc[1] += (double)drho;
+    acc[2] += (double)jx;
+    acc[3] += (double)jy;
+    acc[4] += (double)jz;
+    acc[5] += 0.5 * ((double)jx * jx + (double)jy * jy + (double)jz * jz) / (double)rho;
+  }
+  __shared__ double sh[REDUCE_THREADS / 32][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double w = warp_sum(acc[i]);
+    if (lane == 0) sh[wid][i] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0;
+    for (int w = 0; w < REDUCE_THREADS / 32; ++w) s += sh[w][threadIdx.x];
+    partials[blockIdx.x * 6 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_final(const double* partials, int n, double* out) {
+  if (threadIdx.x < 6) {
+    double s = 0;
+    for (int b = 0; b < n; ++b) s += partials[b * 6 + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
+                          double* partials, double* out, cudaStream_t s) {
+  if (storage == ST_FP16)
+    k_reduce<__half><<<REDUCE_CTAS, REDUCE_THREADS, 0, s>>>((const __half*)d, flags, N, partials);
+  else
+    k_reduce<float><<<REDUCE_CTAS, REDUCE_THREADS, 0, s>>>((const float*)d, flags, N, partials);
+  k_reduce_final<<<1, 32, 0, s>>>(partials, REDUCE_CTAS, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,67 @@
+// Internal (non-ABI) declarations shared by the runtime and the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+enum Storage : int { ST_FP32 = 0, ST_FP16 = 1 };
+
+// Everything one collide-stream launch needs about one block of nodes.
+struct BlockView {
+  const void* d_in;    // shifted populations at time t, 27 planes of N (cube order)
+  void* d_out;         // same at t + dt
+  const float* u_in;   // velocity stored at t (lagged field for |grad u|), 3 planes
+  float* u_out;
+  const float* c_in;   // passive scalar
+  float* c_out;
+  const uint8_t* flags;
+  int nx, ny, nz;
+  int per[3];
+  size_t N;
+  RelaxParams rp;
+  float c_src;
+  int* err;            // device error word (bit 0: non-finite or non-positive density)
+};
+
+// One tile of the batched work list: a BX x BY patch of one z-plane of one simulation.
+struct WorkItem {
+  int view;            // index into the BlockView array
+  int x0, y0, z;
+};
+
+// ---- kernels_step.cu
+cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s);
+cudaError_t launch_init(const BlockView& v, int storage, const float* rho, const float* u,
+                        const float* c, cudaStream_t s);
+cudaError_t launch_merge_user_flags(uint8_t* flags, const uint8_t* user, size_t N,
+                                    cudaStream_t s);
+cudaError_t launch_near_solid(uint8_t* flags, int nx, int ny, int nz, const int per[3],
+                              cudaStream_t s);
+cudaError_t launch_inflow_records(const void* rec, int n, uint8_t* flags, float* const* u_levels,
+                                  int n_levels, int nx, int ny, int nz, size_t N, int* err,
+                                  cudaStream_t s);
+// fields: 0 = populations f (27 planes, paper order), 1 = u, 2 = scalar, 3 = rho
+cudaError_t launch_read_f(const void* d, int storage, size_t N, void* out, int out_f64,
+                          cudaStream_t s);
+cudaError_t launch_write_f(void* d, int storage, size_t N, const void* in, int in_f64,
+                           cudaStream_t s);
+cudaError_t launch_read_rho(const void* d, int storage, size_t N, float* out, cudaStream_t s);
+cudaError_t launch_convert(const void* in, int in_f64, void* out, int out_f64, size_t n,
+                           cudaStream_t s);
+// deterministic FP64 reduction of mass, momentum and kinetic energy over non-solid,
+// non-ghost nodes: writes per-CTA partials into `partials` (REDUCE_CTAS * 6 doubles) and the
+// final six doubles {count, sum drho, sum jx, sum jy, sum jz, sum |j|^2/(2 rho)} into `out`.
+constexpr int REDUCE_CTAS = 304;
+constexpr int REDUCE_THREADS = 256;
+cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
+                          double* partials, double* out, cudaStream_t s);
+
+// ---- kernels_batch.cu
+cudaError_t launch_step_batch(const BlockView* views_dev, const WorkItem* items, int n_items,
+                              int storage, int bx, int by, int grid, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,88 @@
+// Host-side domain object behind the opaque lbm_domain handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+struct Level {             // one time level of a block
+  void* f = nullptr;       // 27 planes of shifted populations (cube order), FP32 or FP16
+  float* u = nullptr;      // 3 planes, velocity stored by the step that produced this level
+  float* c = nullptr;      // passive scalar
+};
+
+struct Block {
+  int nx = 0, ny = 0, nz = 0;
+  size_t N = 0;
+  double origin[3] = {0, 0, 0};
+  double h = 1.0;          // dx_s / dx_0
+  double nu = 0.0;         // viscosity in this block's lattice units
+  int substeps = 1;        // l = sub-steps per reference step
+  bool integer_ratio = true;
+  std::vector<Level> lv;   // 2 levels for s0, 3 for refined blocks
+  uint8_t* flags = nullptr;
+  int cur = 0;             // level holding the current state
+  int saved = 0;           // level holding the state at t_n (refined blocks)
+  int parent = 0;          // nearest coarser block containing this one (prior-mapping source)
+  RelaxParams rp;
+  int bx = 128, by = 2;    // tile of the collide-stream launch
+};
+
+struct TapeState;          // adjoint tape (adjoint.cu)
+struct GraphCache;         // captured step graphs (scheduler.cu)
+
+}  // namespace lbm
+
+struct lbm_domain {
+  lbm_domain_desc desc{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t elt = 4;
+  std::vector<lbm::Block> blocks;
+  std::vector<std::pair<void*, size_t>> allocs;
+  int* d_err = nullptr;
+  int* h_err = nullptr;                 // pinned
+  double* d_partials = nullptr;         // reduction scratch: REDUCE_CTAS * 6 doubles
+  double* d_red = nullptr;
+  double* h_red = nullptr;              // pinned
+  void* staging_buf = nullptr;
+  size_t staging_bytes = 0;
+  void* small_host = nullptr;           // pinned bounce buffer for small uploads
+  void* small_dev = nullptr;
+  size_t small_bytes = 0;
+  cudaEvent_t small_done = nullptr;
+  std::string last_error;
+  long long steps = 0;
+  lbm::TapeState* tape = nullptr;
+  lbm::GraphCache* graphs = nullptr;
+
+  lbm_status fail(lbm_status st, const std::string& msg);
+  lbm_status cuda_fail(cudaError_t e, const char* what);
+  void* dev_alloc(size_t bytes);
+  void dev_free(void* p);
+  void* staging(size_t bytes);
+  const void* device_source(const void* src, size_t bytes, int on_device, lbm_status* st);
+  const void* upload_small(const void* src, size_t bytes, lbm_status* st);
+  lbm::BlockView view(int b, int from, int to) const;
+  lbm_status alloc_block_levels(lbm::Block& B, int levels);
+  lbm::RelaxParams relax_params(double nu_block) const;
+  lbm_status clear_block(int b);
+  lbm_status check_block(int32_t b);
+  void post_error_probe();
+  lbm_status sync_and_check();
+  lbm_status reset_error_word();
+  void pick_tiles(int b);
+  void invalidate_graphs();
+  void release_extras();
+  void on_state_reset(int b);
+  lbm_status advance(int n);            // Algorithm 1, n reference steps
+  lbm_status advance_direct(int n);     // same, launched without graph capture
+};
+
+using Domain = lbm_domain;

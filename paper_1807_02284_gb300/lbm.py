@@ -1,0 +1,288 @@
+"""Python binding of the C-ABI in ``include/lbm.h`` (ctypes; argument marshalling only).
+
+Every function of the header is exposed under the same name on the loaded library object
+(``lib.lbm_step(...)``); :class:`Domain` is a thin convenience wrapper that converts numpy
+arrays / torch tensors into pointers, raises :class:`LBMError` on a non-zero status and, by
+default, routes the library's device allocations through PyTorch's caching allocator on the
+current torch stream.  No solver arithmetic happens here: every step runs in the CUDA
+library, and loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "liblbm.so")
+
+# status codes
+LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA = 0, 1, 2, 3
+LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_UNSUPPORTED, LBM_ERR_STATE = 4, 5, 6, 7
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_OOM", 3: "LBM_ERR_CUDA",
+                4: "LBM_ERR_DIVERGED", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_UNSUPPORTED",
+                7: "LBM_ERR_STATE"}
+LBM_FP32, LBM_FP16_SHIFTED = 0, 1
+LBM_BC_FLAGS, LBM_BC_INFLOW = 0, 1
+LBM_FIELD_F, LBM_FIELD_U, LBM_FIELD_SCALAR, LBM_FIELD_RHO, LBM_FIELD_FLAGS = 0, 1, 2, 3, 4
+LBM_F32, LBM_F64, LBM_U8 = 0, 1, 2
+LBM_MACRO_RHO, LBM_MACRO_U, LBM_MACRO_SCALAR = 0, 1, 2
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class lbm_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class lbm_domain_desc(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("periodic", C.c_int32 * 3), ("nu", C.c_double),
+                ("storage", C.c_int32), ("adaptive", C.c_int32), ("a", C.c_double),
+                ("b", C.c_double), ("g_max", C.c_double), ("nu_hi", C.c_double * 4),
+                ("c_src", C.c_double), ("cuda_stream", C.c_void_p), ("alloc", lbm_allocator),
+                ("device", C.c_int32)]
+
+
+class lbm_block_info(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("origin", C.c_double * 3), ("h", C.c_double),
+                ("nu", C.c_double), ("substeps", C.c_int32), ("steps", C.c_int64)]
+
+
+INFLOW_RECORD = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"),
+                          ("ux", "<f4"), ("uy", "<f4"), ("uz", "<f4")])
+
+_P = C.c_void_p
+_I = C.c_int32
+_SIGNATURES = {
+    "lbm_abi_version": (_I, []),
+    "lbm_default_desc": (_I, [C.POINTER(lbm_domain_desc)]),
+    "lbm_create_domain": (_I, [C.POINTER(lbm_domain_desc), C.POINTER(_P)]),
+    "lbm_destroy_domain": (_I, [_P]),
+    "lbm_add_scale_block": (_I, [_P, C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int32)]),
+    "lbm_set_boundary": (_I, [_P, _I, _I, _P, C.c_size_t, _I]),
+    "lbm_init_macro": (_I, [_P, _I, _P, _P, _P, _I]),
+    "lbm_step": (_I, [_P, _I]),
+    "lbm_sync": (_I, [_P]),
+    "lbm_read_macro": (_I, [_P, _I, _I, _P, C.c_size_t, _I]),
+    "lbm_read_field": (_I, [_P, _I, _I, _I, _P, C.c_size_t, _I]),
+    "lbm_write_field": (_I, [_P, _I, _I, _I, _P, C.c_size_t, _I]),
+    "lbm_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
+    "lbm_get_block_info": (_I, [_P, _I, C.POINTER(lbm_block_info)]),
+    "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
+    "lbm_set_tape": (_I, [_P, _I]),
+    "lbm_adjoint_step": (_I, [_P, _I, _P, _P, _P, _P]),
+    "lbm_last_error": (C.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the built CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build() or python -m paper_1807_02284_gb300.build)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """Pointer and on-device flag of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _nbytes(a):
+    if isinstance(a, np.ndarray):
+        return a.nbytes
+    return a.numel() * a.element_size()
+
+
+class Domain:
+    """Owning wrapper of one ``lbm_domain`` handle."""
+
+    def __init__(self, dims: Sequence[int], nu: float, periodic=(False, False, False),
+                 storage: str = "fp32", adaptive: bool = True, a: float = -4.0, b: float = 5.0,
+                 g_max: float = 0.1, nu_hi=(0.005, 0.007, 0.009, 0.01), c_src: float = 1.0,
+                 stream=None, torch_allocator: bool = True, device: int = 0):
+        self.lib = load()
+        self.handle = C.c_void_p()
+        d = lbm_domain_desc()
+        self.lib.lbm_default_desc(C.byref(d))
+        d.dims[:] = [int(v) for v in dims]
+        d.periodic[:] = [1 if p else 0 for p in periodic]
+        d.nu = float(nu)
+        d.storage = LBM_FP16_SHIFTED if storage in ("fp16", "fp16s", LBM_FP16_SHIFTED) else LBM_FP32
+        d.adaptive = 1 if adaptive else 0
+        d.a, d.b, d.g_max = float(a), float(b), float(g_max)
+        d.nu_hi[:] = [float(v) for v in nu_hi]
+        d.c_src = float(c_src)
+        d.device = int(device)
+        self._keep = []
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device)
+        self.torch_stream = stream
+        d.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+        if torch_allocator:
+            import torch
+
+            dev = int(device)
+            tstream = stream
+
+            def _alloc(nbytes, ctx):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, tstream)
+                except Exception:  # OOM or other failure -> NULL (library reports LBM_ERR_OOM)
+                    return None
+
+            def _free(p, nbytes, ctx):
+                torch.cuda.caching_allocator_delete(p)
+
+            fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._keep += [fa, ff]
+            d.alloc = lbm_allocator(fa, ff, None)
+        self.desc = d
+        self.storage = d.storage
+        self.check(self.lib.lbm_create_domain(C.byref(d), C.byref(self.handle)), create=True)
+
+    # -------------------------------------------------------------------------- plumbing
+    def check(self, st, create=False):
+        if st != LBM_OK:
+            h = None if create else self.handle
+            msg = self.lib.lbm_last_error(h)
+            raise LBMError(st, msg.decode() if msg else "")
+        return st
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.lib.lbm_destroy_domain(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------------------- API
+    def add_scale_block(self, origin, h, dims) -> int:
+        o = (C.c_double * 3)(*[float(v) for v in origin])
+        dd = (C.c_int32 * 3)(*[int(v) for v in dims])
+        bid = C.c_int32()
+        self.check(self.lib.lbm_add_scale_block(self.handle, o, float(h), dd, C.byref(bid)))
+        return bid.value
+
+    def info(self, block=0) -> lbm_block_info:
+        i = lbm_block_info()
+        self.check(self.lib.lbm_get_block_info(self.handle, block, C.byref(i)))
+        return i
+
+    def n_nodes(self, block=0) -> int:
+        i = self.info(block)
+        return int(i.dims[0]) * int(i.dims[1]) * int(i.dims[2])
+
+    def set_flags(self, flags, block=0):
+        if isinstance(flags, np.ndarray):
+            flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        p, dev = _ptr(flags)
+        self.check(self.lib.lbm_set_boundary(self.handle, block, LBM_BC_FLAGS, p, _nbytes(flags), dev))
+
+    def set_inflow(self, records, block=0):
+        if isinstance(records, np.ndarray):
+            records = np.ascontiguousarray(records, dtype=INFLOW_RECORD)
+        p, dev = _ptr(records)
+        self.check(self.lib.lbm_set_boundary(self.handle, block, LBM_BC_INFLOW, p, _nbytes(records), dev))
+
+    def init_macro(self, u, rho=None, c=None, block=0):
+        arrs = []
+        for a in (rho, u, c):
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=np.float32)
+            arrs.append(a)
+        rho, u, c = arrs
+        devs = {_ptr(a)[1] for a in (rho, u, c) if a is not None}
+        if len(devs) != 1:
+            raise ValueError("rho, u and c must all live on the host or all on the device")
+        self.check(self.lib.lbm_init_macro(self.handle, block, _ptr(rho)[0], _ptr(u)[0],
+                                           _ptr(c)[0], devs.pop()))
+
+    def step(self, n=1):
+        self.check(self.lib.lbm_step(self.handle, int(n)))
+
+    def sync(self):
+        self.check(self.lib.lbm_sync(self.handle))
+
+    def read_field(self, field, dtype=LBM_F64, block=0, out=None):
+        N = self.n_nodes(block)
+        count = {LBM_FIELD_F: 27 * N, LBM_FIELD_U: 3 * N, LBM_FIELD_SCALAR: N,
+                 LBM_FIELD_RHO: N, LBM_FIELD_FLAGS: N}[field]
+        npdt = {LBM_F32: np.float32, LBM_F64: np.float64, LBM_U8: np.uint8}[dtype]
+        if out is None:
+            out = np.empty(count, dtype=npdt)
+        p, dev = _ptr(out)
+        self.check(self.lib.lbm_read_field(self.handle, block, field, dtype, p, _nbytes(out), dev))
+        return out
+
+    def write_field(self, field, data, block=0):
+        if isinstance(data, np.ndarray):
+            if data.dtype not in (np.float32, np.float64):
+                data = data.astype(np.float64)
+            data = np.ascontiguousarray(data)
+            dtype = LBM_F64 if data.dtype == np.float64 else LBM_F32
+        else:
+            import torch
+            dtype = LBM_F64 if data.dtype == torch.float64 else LBM_F32
+        p, dev = _ptr(data)
+        self.check(self.lib.lbm_write_field(self.handle, block, field, dtype, p, _nbytes(data), dev))
+
+    def reduce(self, block=0) -> np.ndarray:
+        out = (C.c_double * 5)()
+        self.check(self.lib.lbm_reduce(self.handle, block, out))
+        return np.array(list(out))
+
+    def set_tape(self, every):
+        self.check(self.lib.lbm_set_tape(self.handle, int(every)))
+
+    def adjoint_step(self, n_steps, dL_dc, dL_du0, dL_du=None):
+        pc, _ = _ptr(dL_dc)
+        pu, _ = _ptr(dL_du)
+        p0, _ = _ptr(dL_du0)
+        self.check(self.lib.lbm_adjoint_step(self.handle, int(n_steps), pc, pu, p0, None))
+
+
+def step_batch(domains: Sequence[Domain], steps: int):
+    """``lbm_step_batch`` over the handles of several domains."""
+    lib = load()
+    arr = (C.c_void_p * len(domains))(*[d.handle.value for d in domains])
+    st = lib.lbm_step_batch(arr, len(domains), int(steps))
+    if st != LBM_OK:
+        domains[0].check(st)
