@@ -143,7 +143,7 @@ def _max_over_ranks(ws, val):
 def _workload(name):
     import synth
     storage = "fp16" if name.endswith("fp16") else "fp32"
-    sc = synth.plume(256)
+    sc = synth.plume(128 if name.startswith("plume128") else 256)
     return sc, storage
 
 
@@ -310,7 +310,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f16-storage/f32-math" if storage == "fp16" else "f32",
                 "data": "synthetic",
-                "config": {"workload": f"plume256_{storage}", "nodes": int(N),
+                "config": {"workload": args.workload if "_" in args.workload
+                           else f"{args.workload}_{storage}", "nodes": int(N),
                            "dims": list(b.dims), "storage": storage,
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (state %.2f GB)" %
@@ -336,7 +337,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="plume256",
-                    choices=["plume256", "plume256_fp16"])
+                    choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -59,10 +59,10 @@ enum {
   LBM_BC_FLAGS = 0,  /* uint8 per node (N bytes): bit0 obstacle voxel (halfway bounce-back),
                         bit1 Dirichlet inflow node, bit2 scalar source node.  Replaces the
                         three bits on every node; other bits are library-owned. */
-  LBM_BC_INFLOW = 1  /* array of lbm_inflow_record: marks the nodes as inflow (clearing the
-                        obstacle bit) and sets their inflow velocity.  Records outside the
-                        block are skipped and reported as LBM_ERR_DIVERGED-class device
-                        errors by the next synchronising call. */
+  LBM_BC_INFLOW = 1  /* array of lbm_inflow_record: marks the nodes as inflow and sets
+                        their inflow velocity (applied to every time level).  Records outside
+                        the block or on obstacle voxels / ghost nodes are skipped and
+                        reported as LBM_ERR_DIVERGED by the next synchronising call. */
 };
 
 typedef struct {
@@ -113,6 +113,7 @@ typedef struct {
   double nu;         /* viscosity in this block's lattice units (nu_0 / h, Sec. 3.2 Eq. 4) */
   int32_t substeps;  /* sub-steps per reference step (1 for s0) */
   int64_t steps;     /* reference steps taken by the domain */
+  int32_t tile[2];   /* x, y extent of the collide-stream thread tile (chosen by autotuning) */
 } lbm_block_info;
 
 /* Version of this header's ABI. */

@@ -8,20 +8,28 @@ namespace lbm {
 __constant__ int c_paper_to_cube[27] = {13, 14, 12, 16, 10, 22, 4,  17, 15, 11, 9,  23, 21, 5,
                                         3,  25, 19, 7,  1,  26, 24, 20, 18, 8,  6,  2,  0};
 
-template <typename T>
+template <typename T, typename IT>
 __global__ void __launch_bounds__(256) k_step(BlockView v) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= v.nx || y >= v.ny) return;
-  cell_update<T>(v, x, y, z);
+  cell_update<T, IT>(v, x, y, z);
 }
+
+bool fits_32bit_index(size_t N) { return 27ull * (unsigned long long)N < 0xFFFFFFFFull; }
 
 cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s) {
   dim3 block(bx, by, 1);
   dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, v.nz);
-  if (storage == ST_FP16) k_step<__half><<<grid, block, 0, s>>>(v);
-  else k_step<float><<<grid, block, 0, s>>>(v);
+  const bool i32 = fits_32bit_index(v.N);
+  if (storage == ST_FP16) {
+    if (i32) k_step<__half, uint32_t><<<grid, block, 0, s>>>(v);
+    else k_step<__half, uint64_t><<<grid, block, 0, s>>>(v);
+  } else {
+    if (i32) k_step<float, uint32_t><<<grid, block, 0, s>>>(v);
+    else k_step<float, uint64_t><<<grid, block, 0, s>>>(v);
+  }
   return cudaGetLastError();
 }
 
@@ -114,7 +122,11 @@ __global__ void k_inflow_records(const InflowRec* rec, int n, uint8_t* flags, fl
     return;
   }
   const size_t idx = ((size_t)r.z * ny + r.y) * nx + r.x;
-  flags[idx] = (flags[idx] | F_INFLOW) & ~F_SOLID;
+  if (flags[idx] & (F_SOLID | F_GHOST)) {
+    atomicOr(err, 4);  // obstacle voxels and ghost nodes cannot become inflow nodes
+    return;
+  }
+  flags[idx] |= F_INFLOW;
   float* lv[3] = {u0, u1, u2};
   for (int l = 0; l < 3; ++l)
     if (lv[l]) { lv[l][idx] = r.ux; lv[l][N + idx] = r.uy; lv[l][2 * N + idx] = r.uz; }

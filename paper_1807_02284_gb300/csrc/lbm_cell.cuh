@@ -1,93 +1,117 @@
 // Per-node collide-and-stream update shared by the single-block, batched and adjoint-recompute
 // kernels, so that every launch shape computes bit-identical results.
+//
+// IT is the index type: 32-bit when every array of the block has fewer than 2^32 elements
+// (27 N < 2^32), which halves the address arithmetic, 64-bit otherwise.
 #pragma once
 #include "lbm_internal.h"
 
 namespace lbm {
 
+template <typename IT>
 struct Nbr {
-  int xm, xp;               // x - 1, x + 1 (wrapped or clamped)
-  size_t rm, r0, rp;        // row offsets (y - 1, y, y + 1) * nx
-  size_t pm, p0, pp;        // plane offsets (z - 1, z, z + 1) * nx * ny
+  IT xm, x0, xp;            // x - 1, x, x + 1 (wrapped or clamped)
+  IT rm, r0, rp;            // row offsets (y - 1, y, y + 1) * nx
+  IT pm, p0, pp;            // plane offsets (z - 1, z, z + 1) * nx * ny
 };
 
-__device__ __forceinline__ Nbr neighbours(const BlockView& v, int x, int y, int z) {
-  Nbr n;
-  const size_t nx = (size_t)v.nx, nxy = (size_t)v.nx * v.ny;
-  n.xm = nbr(x, -1, v.nx, v.per[0]);
-  n.xp = nbr(x, 1, v.nx, v.per[0]);
-  n.rm = nx * nbr(y, -1, v.ny, v.per[1]);
-  n.r0 = nx * y;
-  n.rp = nx * nbr(y, 1, v.ny, v.per[1]);
-  n.pm = nxy * nbr(z, -1, v.nz, v.per[2]);
-  n.p0 = nxy * z;
-  n.pp = nxy * nbr(z, 1, v.nz, v.per[2]);
+template <typename IT>
+__device__ __forceinline__ Nbr<IT> neighbours(const BlockView& v, int x, int y, int z) {
+  Nbr<IT> n;
+  const IT nx = (IT)v.nx, nxy = (IT)v.nx * (IT)v.ny;
+  n.xm = (IT)nbr(x, -1, v.nx, v.per[0]);
+  n.x0 = (IT)x;
+  n.xp = (IT)nbr(x, 1, v.nx, v.per[0]);
+  n.rm = nx * (IT)nbr(y, -1, v.ny, v.per[1]);
+  n.r0 = nx * (IT)y;
+  n.rp = nx * (IT)nbr(y, 1, v.ny, v.per[1]);
+  n.pm = nxy * (IT)nbr(z, -1, v.nz, v.per[2]);
+  n.p0 = nxy * (IT)z;
+  n.pp = nxy * (IT)nbr(z, 1, v.nz, v.per[2]);
   return n;
 }
 
 // Source node of the pull for velocity slot k: x - c_k.
-template <int K>
-__device__ __forceinline__ size_t pull_src(const Nbr& n, int x) {
+template <int K, typename IT>
+__device__ __forceinline__ IT pull_src(const Nbr<IT>& n) {
   constexpr int cx = cxk(K), cy = cyk(K), cz = czk(K);
-  const size_t sx = cx > 0 ? (size_t)n.xm : cx < 0 ? (size_t)n.xp : (size_t)x;
-  const size_t sy = cy > 0 ? n.rm : cy < 0 ? n.rp : n.r0;
-  const size_t sz = cz > 0 ? n.pm : cz < 0 ? n.pp : n.p0;
+  const IT sx = cx > 0 ? n.xm : cx < 0 ? n.xp : n.x0;
+  const IT sy = cy > 0 ? n.rm : cy < 0 ? n.rp : n.r0;
+  const IT sz = cz > 0 ? n.pm : cz < 0 ? n.pp : n.p0;
   return sz + sy + sx;
 }
 
-template <typename T, int K = 0>
-__device__ __forceinline__ void pull_all(float (&d)[27], const T* din, size_t N, const Nbr& n,
-                                         int x) {
+template <typename T, typename IT, int K = 0>
+__device__ __forceinline__ void pull_all(float (&d)[27], const T* __restrict__ din, IT N,
+                                         const Nbr<IT>& n) {
   if constexpr (K < 27) {
-    d[K] = load_pop(din + (size_t)K * N + pull_src<K>(n, x));
-    pull_all<T, K + 1>(d, din, N, n, x);
+    d[K] = load_pop(din + ((IT)K * N + pull_src<K>(n)));
+    pull_all<T, IT, K + 1>(d, din, N, n);
   }
 }
 
 // Halfway bounce-back: a population whose source node is an obstacle voxel is replaced by
 // the opposite population of this node (wall at rest).
-template <typename T, int K = 0>
-__device__ __forceinline__ void bounce_back(float (&d)[27], const T* din, size_t N,
-                                            const uint8_t* flags, const Nbr& n, int x,
-                                            size_t idx) {
+template <typename T, typename IT, int K = 0>
+__device__ __forceinline__ void bounce_back(float (&d)[27], const T* __restrict__ din, IT N,
+                                            const uint8_t* __restrict__ flags,
+                                            const Nbr<IT>& n, IT idx) {
   if constexpr (K < 27) {
     if constexpr (K != 13) {
-      if (flags[pull_src<K>(n, x)] & F_SOLID) d[K] = load_pop(din + (size_t)(26 - K) * N + idx);
+      if (__ldg(flags + pull_src<K>(n)) & F_SOLID)
+        d[K] = load_pop(din + ((IT)(26 - K) * N + idx));
     }
-    bounce_back<T, K + 1>(d, din, N, flags, n, x, idx);
+    bounce_back<T, IT, K + 1>(d, din, N, flags, n, idx);
   }
 }
 
-__device__ __forceinline__ float grad_norm(const float* U, size_t N, const Nbr& n, int x) {
+template <typename IT>
+__device__ __forceinline__ float grad_norm(const float* __restrict__ U, IT N, const Nbr<IT>& n) {
   float s = 0.0f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const float* Ua = U + (size_t)a * N;
-    const float dx = __ldg(Ua + n.p0 + n.r0 + n.xp) - __ldg(Ua + n.p0 + n.r0 + n.xm);
-    const float dy = __ldg(Ua + n.p0 + n.rp + x) - __ldg(Ua + n.p0 + n.rm + x);
-    const float dz = __ldg(Ua + n.pp + n.r0 + x) - __ldg(Ua + n.pm + n.r0 + x);
-    s += dx * dx + dy * dy + dz * dz;
+    const float* Ua = U + (IT)a * N;
+    const float dx = __ldg(Ua + (n.p0 + n.r0 + n.xp)) - __ldg(Ua + (n.p0 + n.r0 + n.xm));
+    const float dy = __ldg(Ua + (n.p0 + n.rp + n.x0)) - __ldg(Ua + (n.p0 + n.rm + n.x0));
+    const float dz = __ldg(Ua + (n.pp + n.r0 + n.x0)) - __ldg(Ua + (n.pm + n.r0 + n.x0));
+    s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, s)));
   }
   return 0.5f * sqrtf(s);
 }
 
-__device__ __forceinline__ float sample_scalar(const BlockView& v, int x, int y, int z, float ux,
-                                               float uy, float uz) {
+// The eight corner values of the departure cell and the interpolation weights.
+struct ScalarCell {
+  float c[8];
+  float tx, ty, tz;
+};
+
+template <typename IT>
+__device__ __forceinline__ ScalarCell scalar_corners(const BlockView& v, int x, int y, int z,
+                                                     float ux, float uy, float uz) {
   const Axis1 ax = sl_axis(x, ux, v.nx, v.per[0]);
   const Axis1 ay = sl_axis(y, uy, v.ny, v.per[1]);
   const Axis1 az = sl_axis(z, uz, v.nz, v.per[2]);
-  const size_t nx = (size_t)v.nx, nxy = (size_t)v.nx * v.ny;
-  const float* c = v.c_in;
-  const size_t z0 = nxy * az.i0, z1 = nxy * az.i1, y0 = nx * ay.i0, y1 = nx * ay.i1;
-  const float c000 = __ldg(c + z0 + y0 + ax.i0), c001 = __ldg(c + z0 + y0 + ax.i1);
-  const float c010 = __ldg(c + z0 + y1 + ax.i0), c011 = __ldg(c + z0 + y1 + ax.i1);
-  const float c100 = __ldg(c + z1 + y0 + ax.i0), c101 = __ldg(c + z1 + y0 + ax.i1);
-  const float c110 = __ldg(c + z1 + y1 + ax.i0), c111 = __ldg(c + z1 + y1 + ax.i1);
-  const float tx = ax.t, ty = ay.t, tz = az.t;
-  const float a00 = c000 + tx * (c001 - c000), a01 = c010 + tx * (c011 - c010);
-  const float a10 = c100 + tx * (c101 - c100), a11 = c110 + tx * (c111 - c110);
-  const float b0 = a00 + ty * (a01 - a00), b1 = a10 + ty * (a11 - a10);
-  return b0 + tz * (b1 - b0);
+  const IT nx = (IT)v.nx, nxy = (IT)v.nx * (IT)v.ny;
+  const float* __restrict__ c = v.c_in;
+  const IT z0 = nxy * (IT)az.i0, z1 = nxy * (IT)az.i1, y0 = nx * (IT)ay.i0, y1 = nx * (IT)ay.i1;
+  const IT x0 = (IT)ax.i0, x1 = (IT)ax.i1;
+  ScalarCell s;
+  s.c[0] = __ldg(c + (z0 + y0 + x0)); s.c[1] = __ldg(c + (z0 + y0 + x1));
+  s.c[2] = __ldg(c + (z0 + y1 + x0)); s.c[3] = __ldg(c + (z0 + y1 + x1));
+  s.c[4] = __ldg(c + (z1 + y0 + x0)); s.c[5] = __ldg(c + (z1 + y0 + x1));
+  s.c[6] = __ldg(c + (z1 + y1 + x0)); s.c[7] = __ldg(c + (z1 + y1 + x1));
+  s.tx = ax.t; s.ty = ay.t; s.tz = az.t;
+  return s;
+}
+
+__device__ __forceinline__ float scalar_value(const ScalarCell& s) {
+  const float a00 = fmaf(s.tx, s.c[1] - s.c[0], s.c[0]);
+  const float a01 = fmaf(s.tx, s.c[3] - s.c[2], s.c[2]);
+  const float a10 = fmaf(s.tx, s.c[5] - s.c[4], s.c[4]);
+  const float a11 = fmaf(s.tx, s.c[7] - s.c[6], s.c[6]);
+  const float b0 = fmaf(s.ty, a01 - a00, a00);
+  const float b1 = fmaf(s.ty, a11 - a10, a10);
+  return fmaf(s.tz, b1 - b0, b0);
 }
 
 __device__ __forceinline__ void flag_error(int* err, bool bad) {
@@ -97,14 +121,14 @@ __device__ __forceinline__ void flag_error(int* err, bool bad) {
 
 // One node of one block: pull (with bounce-back and face handling), macroscopic moments,
 // adaptive rates from the lagged velocity, CMR collision, store of f~, u and the scalar.
-template <typename T>
+template <typename T, typename IT>
 __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, int z) {
-  const size_t N = v.N;
-  const size_t idx = ((size_t)z * v.ny + y) * v.nx + x;
-  const T* din = static_cast<const T*>(v.d_in);
-  T* dout = static_cast<T*>(v.d_out);
-  const uint8_t fl = v.flags[idx];
-  const Nbr n = neighbours(v, x, y, z);
+  const IT N = (IT)v.N;
+  const T* __restrict__ din = static_cast<const T*>(v.d_in);
+  T* __restrict__ dout = static_cast<T*>(v.d_out);
+  const Nbr<IT> n = neighbours<IT>(v, x, y, z);
+  const IT idx = n.p0 + n.r0 + n.x0;
+  const uint8_t fl = __ldg(v.flags + idx);
   float d[27];
 
   if (fl & (F_SOLID | F_INFLOW | F_GHOST)) {
@@ -113,40 +137,49 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
 #pragma unroll
       for (int k = 0; k < 27; ++k) d[k] = 0.0f;
     } else if (fl & F_GHOST) {
+      // scale-boundary node: carried over unchanged (its next value comes from mapping)
 #pragma unroll
-      for (int k = 0; k < 27; ++k) d[k] = load_pop(din + (size_t)k * N + idx);
+      for (int k = 0; k < 27; ++k) d[k] = load_pop(din + ((IT)k * N + idx));
       ux = v.u_in[idx]; uy = v.u_in[N + idx]; uz = v.u_in[2 * N + idx];
       cval = v.c_in[idx];
     } else {  // Dirichlet inflow: equilibrium at rho = 1 and the stored inflow velocity
       ux = v.u_in[idx]; uy = v.u_in[N + idx]; uz = v.u_in[2 * N + idx];
       equilibrium(d, 1.0f, ux, uy, uz);
-      cval = (fl & F_SCALAR_SRC) ? v.c_src : sample_scalar(v, x, y, z, ux, uy, uz);
+      cval = (fl & F_SCALAR_SRC) ? v.c_src
+                                 : scalar_value(scalar_corners<IT>(v, x, y, z, ux, uy, uz));
     }
 #pragma unroll
-    for (int k = 0; k < 27; ++k) store_pop(dout + (size_t)k * N + idx, d[k]);
+    for (int k = 0; k < 27; ++k) store_pop(dout + ((IT)k * N + idx), d[k]);
     v.u_out[idx] = ux; v.u_out[N + idx] = uy; v.u_out[2 * N + idx] = uz;
     v.c_out[idx] = cval;
     return;
   }
 
-  pull_all<T>(d, din, N, n, x);
-  if (fl & F_NEAR_SOLID) bounce_back<T>(d, din, N, v.flags, n, x, idx);
+  // all independent loads first: the pull and the lagged velocity neighbourhood
+  pull_all<T, IT>(d, din, N, n);
+  if (fl & F_NEAR_SOLID) bounce_back<T, IT>(d, din, N, v.flags, n, idx);
+  const float g = v.rp.adaptive ? grad_norm<IT>(v.u_in, N, n) : 0.0f;
 
-  float drho, jx, jy, jz;
-  macros(d, drho, jx, jy, jz);
-  const float rho = 1.0f + drho;
-  const float inv = 1.0f / rho;
-  const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-  flag_error(v.err, !(rho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 3.0f));
+  raw_moments(d);
+  const float drho = d[kap(0, 0, 0)];
+  const float inv = __frcp_rn(1.0f + drho);
+  const float ux = d[kap(1, 0, 0)] * inv, uy = d[kap(0, 1, 0)] * inv, uz = d[kap(0, 0, 1)] * inv;
+  flag_error(v.err, !(1.0f + drho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 3.0f));
 
-  const float g = v.rp.adaptive ? grad_norm(v.u_in, N, n, x) : 0.0f;
+  // departure-cell scalar loads go out before the collision arithmetic
+  ScalarCell sc;
+  const bool src = (fl & F_SCALAR_SRC) != 0;
+  if (!src) sc = scalar_corners<IT>(v, x, y, z, ux, uy, uz);
+
   const Keep kf = keep_factors(v.rp, g);
-  collide(d, drho, ux, uy, uz, kf);
+  collide_from_raw(d, drho, ux, uy, uz, kf);
 
 #pragma unroll
-  for (int k = 0; k < 27; ++k) store_pop(dout + (size_t)k * N + idx, d[k]);
-  v.u_out[idx] = ux; v.u_out[N + idx] = uy; v.u_out[2 * N + idx] = uz;
-  v.c_out[idx] = (fl & F_SCALAR_SRC) ? v.c_src : sample_scalar(v, x, y, z, ux, uy, uz);
+  for (int k = 0; k < 27; ++k) store_pop(dout + ((IT)k * N + idx), d[k]);
+  __stcs(v.u_out + idx, ux);
+  __stcs(v.u_out + (N + idx), uy);
+  __stcs(v.u_out + (2 * N + idx), uz);
+  __stcs(v.c_out + idx, src ? v.c_src : scalar_value(sc));
 }
 
 }  // namespace lbm

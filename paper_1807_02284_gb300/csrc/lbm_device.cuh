@@ -6,15 +6,23 @@
 // rest-state weight), which keeps the stored magnitudes small; the FP16 mode stores the same
 // quantity in half precision.
 //
-// The collision (Sec. 3.1, Eq. 2: Omega = -T S (m - m^eq)) is evaluated in the factorised
-// form  f~ = f^eq + P(u)^{-1} (I - S) P(u) (f - f^eq),  where P(u) maps populations to the
-// raw central moments kappa_abc = sum_i f_i (c_ix-u_x)^a (c_iy-u_y)^b (c_iz-u_z)^c by three
-// per-axis sweeps over 3-point lines.  The paper's moments m_j are fixed linear combinations
-// of the kappa_abc (the Appendix basis), and S is constant inside each combination group, so
-// relaxing kappa with the per-group rates is the paper's m-space relaxation; the only mixing
-// group is the second-order diagonal (m_7 = k200-k020, m_8 = k200-k002 relax with the shear
-// rate, the trace m_9 with the high-order rate of group 9..16).  f^eq is the second-order
-// polynomial equilibrium, which equals T m^eq(rho,u) for the Appendix m^eq.
+// Collision (Sec. 3.1, Eq. 2: Omega = -T S (m - m^eq)).  The paper's moments m_j are fixed
+// linear combinations of the raw central moments
+//     kappa_abc = sum_i f_i (c_ix - u_x)^a (c_iy - u_y)^b (c_iz - u_z)^c ,
+// and S is constant inside each combination group, so relaxing every kappa_abc towards its
+// equilibrium with its group's rate is the paper's m-space relaxation.  The only group that
+// mixes is the second-order diagonal: the deviators m_7 = k200 - k020, m_8 = k200 - k002
+// relax with the shear rate and the trace m_9 with the rate of group 9..16.
+//
+// Evaluation per node:
+//   1. raw moments r_abc = sum_i d_i c_ix^a c_iy^b c_iz^c by three 3-point sweeps; they give
+//      rho - 1 = r_000 and the momentum j = (r_100, r_010, r_001) for free;
+//   2. a binomial shift turns raw moments of d into central moments about u;
+//   3. relaxation towards Delta_abc = kappa^eq_abc - kappa_abc(w): the equilibrium central
+//      moments of the Appendix (m^eq recombined per kappa) minus the central moments of the
+//      rest weights (a product of the 1-D moments 1, -u, 1/3 + u^2).  All Delta are small
+//      numbers, so FP32 keeps the non-equilibrium part accurate;
+//   4. inverse sweeps (exact inverse of 1 + 2) give the post-collision shifted populations.
 #pragma once
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -52,7 +60,9 @@ __device__ __forceinline__ float load_pop(const __half* p) {
   return __half2float(__ldg(reinterpret_cast<const __half*>(p)));
 }
 __device__ __forceinline__ void store_pop(float* p, float v) { __stcs(p, v); }
-__device__ __forceinline__ void store_pop(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void store_pop(__half* p, float v) {
+  __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
+}
 
 // Relaxation "keep" factors 1 - S for the moment groups of the Appendix.
 struct Keep {
@@ -75,25 +85,17 @@ __device__ __forceinline__ Keep keep_factors(const RelaxParams& rp, float grad_n
   float phi = 1.0f;
   if (rp.adaptive) phi = rp.a * fminf(grad_norm * rp.inv_gmax, 1.0f) + rp.b;
 #pragma unroll
-  for (int g = 0; g < 4; ++g) kf.g[g] = 1.0f - 1.0f / (phi * rp.nuh3[g] + 0.5f);
+  for (int g = 0; g < 4; ++g) kf.g[g] = 1.0f - __frcp_rn(fmaf(phi, rp.nuh3[g], 0.5f));
   return kf;
 }
 
-// Shifted equilibrium d^eq_k = f^eq_k - w_k = w_k (drho + rho (3 cu + 9/2 cu^2 - 3/2 u.u)).
+// Shifted equilibrium d^eq_k = f^eq_k - w_k = w_k (drho + rho (3 cu + 9/2 cu^2 - 3/2 u.u))
+// (used for initialisation and Dirichlet inflow nodes).
 template <int K>
 __device__ __forceinline__ float deq_k(float drho, float rho, float ux, float uy, float uz,
                                        float usq15) {
   const float cu = float(cxk(K)) * ux + float(cyk(K)) * uy + float(czk(K)) * uz;
   return wk(K) * (drho + rho * (cu * (3.0f + 4.5f * cu) - usq15));
-}
-
-template <int K0 = 0>
-__device__ __forceinline__ void sub_deq(float (&d)[27], float drho, float rho, float ux, float uy,
-                                        float uz, float usq15) {
-  if constexpr (K0 < 27) {
-    d[K0] -= deq_k<K0>(drho, rho, ux, uy, uz, usq15);
-    sub_deq<K0 + 1>(d, drho, rho, ux, uy, uz, usq15);
-  }
 }
 template <int K0 = 0>
 __device__ __forceinline__ void add_deq(float (&d)[27], float drho, float rho, float ux, float uy,
@@ -104,89 +106,149 @@ __device__ __forceinline__ void add_deq(float (&d)[27], float drho, float rho, f
   }
 }
 
-// Forward 3-point central-moment transform of one line (slots s0,s1,s2 = velocity -1,0,+1)
-// into orders 0,1,2 about velocity u.
-__device__ __forceinline__ void fwd_line(float& s0, float& s1, float& s2, float u) {
-  const float k0 = s0 + s1 + s2;
-  const float s = s2 - s0;
-  const float t = s2 + s0;
-  const float k1 = s - u * k0;
-  const float k2 = t - u * (s + k1);
-  s0 = k0; s1 = k1; s2 = k2;
-}
-// Exact inverse of fwd_line.
-__device__ __forceinline__ void inv_line(float& s0, float& s1, float& s2, float u) {
-  const float k0 = s0, k1 = s1, k2 = s2;
-  const float r1 = k1 + u * k0;
-  const float r2 = k2 + u * (k1 + r1);
-  s0 = 0.5f * (r2 - r1);
-  s1 = k0 - r2;
-  s2 = 0.5f * (r2 + r1);
+// line base of line l (0..8) for sweeps along stride 1 (x), 3 (y) or 9 (z)
+template <int STRIDE>
+__host__ __device__ constexpr int line_base(int l) {
+  return (STRIDE == 1) ? 3 * l : (STRIDE == 3) ? (l % 3) + 9 * (l / 3) : l;
 }
 
-// stride 1: x lines, stride 3: y lines, stride 9: z lines
+// Raw 3-point moments of one line (slots = velocity -1, 0, +1) -> orders 0, 1, 2.
 template <int STRIDE>
-__device__ __forceinline__ void fwd_axis(float (&v)[27], float u) {
+__device__ __forceinline__ void raw_axis(float (&v)[27]) {
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
-    const int base = (STRIDE == 1) ? 3 * l : (STRIDE == 3) ? (l % 3) + 9 * (l / 3) : l;
-    fwd_line(v[base], v[base + STRIDE], v[base + 2 * STRIDE], u);
+    const int b = line_base<STRIDE>(l);
+    const float a = v[b], m = v[b + STRIDE], c = v[b + 2 * STRIDE];
+    v[b] = a + m + c;
+    v[b + STRIDE] = c - a;
+    v[b + 2 * STRIDE] = c + a;
   }
 }
+// Binomial shift of raw moments (orders 0,1,2) to central moments about u.
+template <int STRIDE>
+__device__ __forceinline__ void shift_axis(float (&v)[27], float u) {
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    const int b = line_base<STRIDE>(l);
+    const float r0 = v[b], r1 = v[b + STRIDE], r2 = v[b + 2 * STRIDE];
+    const float k1 = fmaf(-u, r0, r1);
+    v[b + STRIDE] = k1;
+    v[b + 2 * STRIDE] = fmaf(-u, r1 + k1, r2);
+  }
+}
+// Central moments about u (orders 0,1,2) back to the three populations of the line.
 template <int STRIDE>
 __device__ __forceinline__ void inv_axis(float (&v)[27], float u) {
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
-    const int base = (STRIDE == 1) ? 3 * l : (STRIDE == 3) ? (l % 3) + 9 * (l / 3) : l;
-    inv_line(v[base], v[base + STRIDE], v[base + 2 * STRIDE], u);
+    const int b = line_base<STRIDE>(l);
+    const float k0 = v[b], k1 = v[b + STRIDE], k2 = v[b + 2 * STRIDE];
+    const float r1 = fmaf(u, k0, k1);
+    const float r2 = fmaf(u, k1 + r1, k2);
+    v[b] = 0.5f * (r2 - r1);
+    v[b + STRIDE] = k0 - r2;
+    v[b + 2 * STRIDE] = 0.5f * (r2 + r1);
   }
 }
 
 // kappa index of orders (a, b, c)
 __host__ __device__ constexpr int kap(int a, int b, int c) { return a + 3 * b + 9 * c; }
 
-// Relaxation of non-equilibrium central moments in place (orders are slot indices).
-__device__ __forceinline__ void relax(float (&v)[27], const Keep& kf) {
-  // second order, off-diagonal (m_4, m_5, m_6)
-  v[kap(1, 1, 0)] *= kf.nu;
-  v[kap(1, 0, 1)] *= kf.nu;
-  v[kap(0, 1, 1)] *= kf.nu;
-  // second order, diagonal: deviators m_7, m_8 at the shear rate, trace m_9 at group 9..16
+// Relaxation of the central moments of d towards Delta (see header), in place.
+// v holds central moments of the shifted populations about u; keep factors kf; K = 1 - S.
+__device__ __forceinline__ void relax_to_equilibrium(float (&v)[27], float drho, float X,
+                                                     float Y, float Z, const Keep& kf) {
+  const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
+  const float X2 = X * X, Y2 = Y * Y, Z2 = Z * Z;
+#define LBM_RELAX(IDX, DELTA, K)              \
+  {                                           \
+    const float dl = (DELTA);                 \
+    v[IDX] = fmaf((K), v[IDX] - dl, dl);      \
+  }
+  // second order, off-diagonal (m_4, m_5, m_6): kappa^eq = 0, kappa(w) = u_a u_b
+  LBM_RELAX(kap(1, 1, 0), -X * Y, kf.nu)
+  LBM_RELAX(kap(1, 0, 1), -X * Z, kf.nu)
+  LBM_RELAX(kap(0, 1, 1), -Y * Z, kf.nu)
+  // second order, diagonal: kappa^eq = rho/3, kappa(w) = 1/3 + u_a^2
   {
-    const float A = v[kap(2, 0, 0)], B = v[kap(0, 2, 0)], Cc = v[kap(0, 0, 2)];
+    const float dr3 = drho * third;
+    const float ex = dr3 - X2, ey = dr3 - Y2, ez = dr3 - Z2;
+    const float A = v[kap(2, 0, 0)] - ex, B = v[kap(0, 2, 0)] - ey, Cc = v[kap(0, 0, 2)] - ez;
     const float d1 = kf.nu * (A - B);
     const float d2 = kf.nu * (A - Cc);
     const float tr = kf.g[0] * (A + B + Cc);
-    const float third = 1.0f / 3.0f;
-    v[kap(2, 0, 0)] = third * (tr + d1 + d2);
-    v[kap(0, 2, 0)] = third * (tr - 2.0f * d1 + d2);
-    v[kap(0, 0, 2)] = third * (tr + d1 - 2.0f * d2);
+    v[kap(2, 0, 0)] = ex + third * (tr + d1 + d2);
+    v[kap(0, 2, 0)] = ey + third * (tr - 2.0f * d1 + d2);
+    v[kap(0, 0, 2)] = ez + third * (tr + d1 - 2.0f * d2);
   }
   // third order (m_10 .. m_16)
-  v[kap(1, 2, 0)] *= kf.g[0];
-  v[kap(1, 0, 2)] *= kf.g[0];
-  v[kap(2, 1, 0)] *= kf.g[0];
-  v[kap(0, 1, 2)] *= kf.g[0];
-  v[kap(2, 0, 1)] *= kf.g[0];
-  v[kap(0, 2, 1)] *= kf.g[0];
-  v[kap(1, 1, 1)] *= kf.g[0];
+  LBM_RELAX(kap(1, 2, 0), X * fmaf(-drho, Y2, third), kf.g[0])
+  LBM_RELAX(kap(1, 0, 2), X * fmaf(-drho, Z2, third), kf.g[0])
+  LBM_RELAX(kap(2, 1, 0), Y * fmaf(-drho, X2, third), kf.g[0])
+  LBM_RELAX(kap(0, 1, 2), Y * fmaf(-drho, Z2, third), kf.g[0])
+  LBM_RELAX(kap(2, 0, 1), Z * fmaf(-drho, X2, third), kf.g[0])
+  LBM_RELAX(kap(0, 2, 1), Z * fmaf(-drho, Y2, third), kf.g[0])
+  LBM_RELAX(kap(1, 1, 1), -drho * X * Y * Z, kf.g[0])
   // fourth order (m_17 .. m_22)
-  v[kap(2, 2, 0)] *= kf.g[1];
-  v[kap(2, 0, 2)] *= kf.g[1];
-  v[kap(0, 2, 2)] *= kf.g[1];
-  v[kap(2, 1, 1)] *= kf.g[1];
-  v[kap(1, 2, 1)] *= kf.g[1];
-  v[kap(1, 1, 2)] *= kf.g[1];
+  {
+    const float r3m1 = fmaf(3.0f, drho, 2.0f);  // 3 rho - 1
+    const float dr9 = drho * ninth;
+    LBM_RELAX(kap(2, 2, 0), fmaf(r3m1, X2 * Y2, dr9 - (X2 + Y2) * third), kf.g[1])
+    LBM_RELAX(kap(2, 0, 2), fmaf(r3m1, X2 * Z2, dr9 - (X2 + Z2) * third), kf.g[1])
+    LBM_RELAX(kap(0, 2, 2), fmaf(r3m1, Y2 * Z2, dr9 - (Y2 + Z2) * third), kf.g[1])
+    LBM_RELAX(kap(2, 1, 1), Y * Z * fmaf(r3m1, X2, -third), kf.g[1])
+    LBM_RELAX(kap(1, 2, 1), X * Z * fmaf(r3m1, Y2, -third), kf.g[1])
+    LBM_RELAX(kap(1, 1, 2), X * Y * fmaf(r3m1, Z2, -third), kf.g[1])
+  }
   // fifth order (m_23 .. m_25)
-  v[kap(1, 2, 2)] *= kf.g[2];
-  v[kap(2, 1, 2)] *= kf.g[2];
-  v[kap(2, 2, 1)] *= kf.g[2];
+  {
+    const float o6 = fmaf(-6.0f, drho, -5.0f);  // 1 - 6 rho
+    const float dr3 = drho * third;
+    LBM_RELAX(kap(1, 2, 2), X * fmaf(o6, Y2 * Z2, fmaf(-dr3, Y2 + Z2, ninth)), kf.g[2])
+    LBM_RELAX(kap(2, 1, 2), Y * fmaf(o6, X2 * Z2, fmaf(-dr3, X2 + Z2, ninth)), kf.g[2])
+    LBM_RELAX(kap(2, 2, 1), Z * fmaf(o6, X2 * Y2, fmaf(-dr3, X2 + Y2, ninth)), kf.g[2])
+  }
   // sixth order (m_26)
-  v[kap(2, 2, 2)] *= kf.g[3];
+  {
+    const float rho = 1.0f + drho;
+    const float p2 = X2 * Y2 + X2 * Z2 + Y2 * Z2;
+    const float d222 = fmaf(fmaf(10.0f, rho, -1.0f), X2 * Y2 * Z2,
+                            fmaf(rho - third, p2, fmaf(drho, 1.0f / 27.0f, -(X2 + Y2 + Z2) * ninth)));
+    LBM_RELAX(kap(2, 2, 2), d222, kf.g[3])
+  }
+#undef LBM_RELAX
   // orders 0 and 1 (S_0..3 = 0) are left as they are
 }
 
-// Macroscopic moments of shifted populations: drho = rho - 1, j = sum c d.
+// Raw moment sweeps: afterwards v[kap(0,0,0)] = rho - 1 and v[kap(1,0,0)] = j_x etc.
+__device__ __forceinline__ void raw_moments(float (&v)[27]) {
+  raw_axis<1>(v);
+  raw_axis<3>(v);
+  raw_axis<9>(v);
+}
+
+// Collision of shifted populations given their raw moments (from raw_moments) and u:
+// raw -> central, relax towards equilibrium, back to populations (in place).
+__device__ __forceinline__ void collide_from_raw(float (&v)[27], float drho, float ux, float uy,
+                                                 float uz, const Keep& kf) {
+  shift_axis<1>(v, ux);
+  shift_axis<3>(v, uy);
+  shift_axis<9>(v, uz);
+  relax_to_equilibrium(v, drho, ux, uy, uz, kf);
+  inv_axis<9>(v, uz);
+  inv_axis<3>(v, uy);
+  inv_axis<1>(v, ux);
+}
+
+// Equilibrium (shifted) for given rho, u.
+__device__ __forceinline__ void equilibrium(float (&d)[27], float rho, float ux, float uy,
+                                            float uz) {
+#pragma unroll
+  for (int k = 0; k < 27; ++k) d[k] = 0.0f;
+  add_deq(d, rho - 1.0f, rho, ux, uy, uz, 1.5f * (ux * ux + uy * uy + uz * uz));
+}
+
+// Sums of shifted populations: drho = rho - 1, j = sum c d (for kernels that do not sweep).
 __device__ __forceinline__ void macros(const float (&d)[27], float& drho, float& jx, float& jy,
                                        float& jz) {
   float s = 0.f, x = 0.f, y = 0.f, z = 0.f;
@@ -198,30 +260,6 @@ __device__ __forceinline__ void macros(const float (&d)[27], float& drho, float&
     if (czk(k) > 0) z += d[k]; else if (czk(k) < 0) z -= d[k];
   }
   drho = s; jx = x; jy = y; jz = z;
-}
-
-// Full CMR collision of shifted populations, in place: d -> d~.
-__device__ __forceinline__ void collide(float (&d)[27], float drho, float ux, float uy, float uz,
-                                        const Keep& kf) {
-  const float rho = 1.0f + drho;
-  const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
-  sub_deq(d, drho, rho, ux, uy, uz, usq15);      // f - f^eq
-  fwd_axis<1>(d, ux);
-  fwd_axis<3>(d, uy);
-  fwd_axis<9>(d, uz);                            // kappa^neq
-  relax(d, kf);                                  // (I - S) kappa^neq
-  inv_axis<9>(d, uz);
-  inv_axis<3>(d, uy);
-  inv_axis<1>(d, ux);                            // back to populations
-  add_deq(d, drho, rho, ux, uy, uz, usq15);      // + f^eq
-}
-
-// Equilibrium (shifted) for given rho, u.
-__device__ __forceinline__ void equilibrium(float (&d)[27], float rho, float ux, float uy,
-                                            float uz) {
-#pragma unroll
-  for (int k = 0; k < 27; ++k) d[k] = 0.0f;
-  add_deq(d, rho - 1.0f, rho, ux, uy, uz, 1.5f * (ux * ux + uy * uy + uz * uz));
 }
 
 // Index of node k+o along an axis of n nodes: periodic wrap or clamp (open face).

@@ -149,7 +149,7 @@ lbm_status Domain::sync_and_check() {
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   if (*h_err & 1) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density detected");
-  if (*h_err & 4) return fail(LBM_ERR_DIVERGED, "inflow record outside the block was skipped");
+  if (*h_err & 4) return fail(LBM_ERR_DIVERGED, "an inflow record outside the block or on an obstacle/ghost node was skipped");
   if (*h_err & 8) return fail(LBM_ERR_TIMEOUT, "a bounded device wait gave up");
   return LBM_OK;
 }
@@ -307,13 +307,9 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
     if (st != LBM_OK) return st;
     std::vector<float*> lv;
     for (auto& L : B.lv) lv.push_back(L.u);
+    // records never touch obstacle voxels, so the derived near-obstacle bits stay valid
     cudaError_t e = launch_inflow_records(src, n, B.flags, lv.data(), (int)lv.size(), B.nx,
                                           B.ny, B.nz, B.N, dom->d_err, dom->stream);
-    if (e == cudaSuccess) {
-      int per[3] = {0, 0, 0};
-      if (block_id == 0) for (int a = 0; a < 3; ++a) per[a] = dom->desc.periodic[a];
-      e = launch_near_solid(B.flags, B.nx, B.ny, B.nz, per, dom->stream);
-    }
     if (e != cudaSuccess) return dom->cuda_fail(e, "inflow records");
     return LBM_OK;
   }
@@ -498,6 +494,8 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
   info->nu = B.nu;
   info->substeps = B.substeps;
   info->steps = dom->steps;
+  info->tile[0] = B.bx;
+  info->tile[1] = B.by;
   return LBM_OK;
 }
 

@@ -32,6 +32,7 @@ struct Block {
   int parent = 0;          // nearest coarser block containing this one (prior-mapping source)
   RelaxParams rp;
   int bx = 128, by = 2;    // tile of the collide-stream launch
+  bool tuned = false;      // tile shape chosen by autotune_tiles
 };
 
 struct TapeState;          // adjoint tape (adjoint.cu)
@@ -78,6 +79,7 @@ struct lbm_domain {
   lbm_status sync_and_check();
   lbm_status reset_error_word();
   void pick_tiles(int b);
+  lbm_status autotune_tiles(int b);
   void invalidate_graphs();
   void release_extras();
   void on_state_reset(int b);

@@ -2,6 +2,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "runtime.h"
@@ -21,6 +23,54 @@ void lbm_domain::pick_tiles(int b) {
   // x-contiguous tiles of 256 threads; narrow blocks use a 32-wide tile with more rows
   B.bx = B.nx >= 128 ? 128 : B.nx >= 64 ? 64 : 32;
   B.by = 256 / B.bx;
+  B.tuned = false;
+  if (const char* env = std::getenv("LBM_TILE")) {  // "bx,by" forces a tile shape
+    int bx = 0, by = 0;
+    if (std::sscanf(env, "%d,%d", &bx, &by) == 2 && bx > 0 && by > 0 && bx * by <= 256 &&
+        bx % 32 == 0) {
+      B.bx = bx;
+      B.by = by;
+      B.tuned = true;
+    }
+  }
+}
+
+// Times candidate tile shapes of the collide-stream launch on the block's current state and
+// keeps the fastest.  Candidates read the current level and write the next one without
+// advancing the clock, so tuning changes no result (every shape computes the same values).
+lbm_status lbm_domain::autotune_tiles(int b) {
+  Block& B = blocks[b];
+  if (B.tuned) return LBM_OK;
+  B.tuned = true;
+  if (B.N < (size_t)1 << 18 || B.lv.size() < 2) return LBM_OK;
+  const int cand[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {128, 1}};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(cudaGetLastError(), "event"); }
+  const int to = (B.cur + 1) % (int)B.lv.size();
+  float best = 1e30f;
+  int bx = B.bx, by = B.by;
+  for (const auto& c : cand) {
+    if (c[0] > 32 && c[0] > B.nx + 31) continue;
+    const BlockView v = view(b, B.cur, to);
+    cudaError_t e = launch_step(v, desc.storage, c[0], c[1], stream);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_step(v, desc.storage, c[0], c[1], stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0); cudaEventDestroy(e1);
+      return cuda_fail(e, "tile autotuning");
+    }
+    if (ms < best) { best = ms; bx = c[0]; by = c[1]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B.bx = bx;
+  B.by = by;
+  return LBM_OK;
 }
 
 void lbm_domain::invalidate_graphs() {
@@ -111,6 +161,14 @@ lbm_status lbm_domain::advance_direct(int n) {
 // (and multi-block domains) launch directly.
 lbm_status lbm_domain::advance(int n) {
   const int chunk = 16;
+  if (n > 0) {
+    for (size_t b = 0; b < blocks.size(); ++b) {
+      const bool was = blocks[b].tuned;
+      lbm_status st = autotune_tiles((int)b);
+      if (st != LBM_OK) return st;
+      if (!was) invalidate_graphs();
+    }
+  }
   if (blocks.size() != 1 || tape != nullptr || n < 2 * chunk) return advance_direct(n);
   Block& B = blocks[0];
   if (!graphs) {
