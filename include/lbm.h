@@ -206,8 +206,35 @@ lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every);
 lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dscalar_final,
                             const float* dL_du_final, float* dL_du0, float* dL_dinflow);
 
+/* Largest n_nodes accepted by lbm_reduce_noalloc. */
+#define LBM_REDUCE_NOALLOC_MAX_NODES 67108864
+
+/* The same diagnostics as lbm_reduce, for callers that cannot allocate device memory (the
+   paper has no counterpart; this is a library service).  Such callers include processes
+   whose device memory is entirely reserved by another framework's pool and latency-critical
+   loops that must never reach the driver's allocator.  This entry point allocates nothing:
+   its partial sums live in a fixed 192 KiB device array inside the library, which every GPU
+   that loads the library keeps until the process exits.
+     f       device array of unshifted populations, 27 planes of n_nodes values in the
+             paper's velocity order (the layout lbm_read_field returns), LBM_F32 or LBM_F64
+             as given by dtype;
+     flags   device array of n_nodes node flags (as lbm_read_field returns them) or NULL;
+             obstacle voxels and ghost nodes are skipped;
+     n_nodes 1 .. LBM_REDUCE_NOALLOC_MAX_NODES, larger values give LBM_ERR_INVALID_ARG;
+     out     device array of 5 doubles: mass, momentum x, y, z, kinetic energy;
+     cuda_stream  stream the work is enqueued on (NULL = legacy default stream); the call
+             does not synchronise.
+   The first call on a device (with that device current) looks up the array's device
+   address; make that first call before any stream capture.  All calls share the one array,
+   so calls whose work overlaps on the GPU (different streams, or different host threads on
+   one device) race with each other; serialise them.  Errors are reported through
+   lbm_last_error(NULL). */
+lbm_status lbm_reduce_noalloc(const void* f, int32_t dtype, const uint8_t* flags,
+                              int64_t n_nodes, double* out, void* cuda_stream);
+
 /* Message of the last failure on this domain (empty if none); valid until the next call
-   on the domain.  NULL dom gives the message of the last failed lbm_create_domain. */
+   on the domain.  NULL dom gives the message of the last failed call that has no domain
+   (lbm_create_domain, lbm_reduce_noalloc). */
 const char* lbm_last_error(const lbm_domain* dom);
 
 #ifdef __cplusplus

@@ -54,6 +54,13 @@ __host__ __device__ constexpr double wkd(int k) {
                        : 1.0 / 216.0;
 }
 
+// Paper velocity index q (Appendix list, index 13 read as (1,0,-1)) -> cube slot k.
+__host__ __device__ constexpr int paper_to_cube(int q) {
+  constexpr int t[27] = {13, 14, 12, 16, 10, 22, 4, 17, 15, 11, 9, 23, 21, 5,
+                         3,  25, 19, 7,  1,  26, 24, 20, 18, 8, 6, 2,  0};
+  return t[q];
+}
+
 // Storage element conversions.
 __device__ __forceinline__ float load_pop(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float load_pop(const __half* p) {

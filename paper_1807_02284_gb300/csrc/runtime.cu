@@ -25,6 +25,8 @@ lbm_status map_cuda(cudaError_t e) {
 }
 }  // namespace
 
+void lbm_set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 // ------------------------------------------------------------------------------ helpers
 
 lbm_status Domain::fail(lbm_status st, const std::string& msg) {

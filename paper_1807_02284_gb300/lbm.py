@@ -76,8 +76,10 @@ _SIGNATURES = {
     "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
     "lbm_set_tape": (_I, [_P, _I]),
     "lbm_adjoint_step": (_I, [_P, _I, _P, _P, _P, _P]),
+    "lbm_reduce_noalloc": (_I, [_P, _I, _P, C.c_int64, _P, _P]),
     "lbm_last_error": (C.c_char_p, [_P]),
 }
+LBM_REDUCE_NOALLOC_MAX_NODES = 67108864
 
 _lib = None
 
