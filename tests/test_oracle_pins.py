@@ -17,9 +17,9 @@ from oracle import cmr, grid
 DT = torch.float64
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
-# Textbook D3Q27 lattice weights by |c|^2 (rest, face, edge, corner); the paper refers to
-# them as "the lattice weight originally present in BGK model" (Sec. 4.2.1) without printing
-# them, so the test writes them down independently of the oracle.
+# Textbook D3Q27 lattice weights by |c|^2 (rest, face, edge, corner); Sec. 4.2.1 refers to
+# the BGK lattice weights without printing them, so the test writes them down independently
+# of the oracle.
 W_BY_NORM = {0: 8.0 / 27.0, 1: 2.0 / 27.0, 2: 1.0 / 54.0, 3: 1.0 / 216.0}
 
 
