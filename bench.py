@@ -143,6 +143,8 @@ def _max_over_ranks(ws, val):
 def _workload(name):
     import synth
     storage = "fp16" if name.endswith("fp16") else "fp32"
+    if name == "multiscale3":
+        return synth.multiscale(scale=1.0), "fp32"
     sc = synth.plume(128 if name.startswith("plume128") else 256)
     return sc, storage
 
@@ -245,10 +247,20 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, storage=storage,
                      adaptive=sc.adaptive, c_src=sc.c_src, stream=stream)
-    dom.set_flags(b.flags)
-    dom.init_macro(b.u0.astype(np.float32), rho=b.rho0.astype(np.float32),
-                   c=b.c0.astype(np.float32))
-    N = b.flags.size
+    for blk in sc.blocks[1:]:
+        dom.add_scale_block(blk.origin, blk.h, blk.dims)
+    for i, blk in enumerate(sc.blocks):
+        dom.set_flags(blk.flags, block=i)
+        dom.init_macro(blk.u0.astype(np.float32), rho=blk.rho0.astype(np.float32),
+                       c=blk.c0.astype(np.float32), block=i)
+    # lattice updates and launches per reference step (refined blocks sub-cycle)
+    subs = [dom.info(i).substeps for i in range(len(sc.blocks))]
+    N = sum(s * blk.flags.size for s, blk in zip(subs, sc.blocks))
+    launches_per_step = 1
+    for i in range(1, len(sc.blocks)):
+        h = sc.blocks[i].h
+        integer = abs(1.0 / h - round(1.0 / h)) < 1e-9 and abs(subs[i] * h - 1.0) < 1e-9
+        launches_per_step += 2 * subs[i] + (0 if integer else 1) + 1 + i  # post: i coarser
     K, W = args.steps, args.warmup
 
     # ---- device-resident throughput (value) and the collide-stream roofline
@@ -272,7 +284,10 @@ def run_ours(args):
     t_max = _max_over_ranks(ws, t_dev)
     value = N * K * ws / t_max / 1e6
 
-    alg_bytes, per_fluid = _algorithmic_bytes(b.flags, storage)
+    alg_bytes, per_fluid = 0, 0
+    for s, blk in zip(subs, sc.blocks):
+        ab, per_fluid = _algorithmic_bytes(blk.flags, storage)
+        alg_bytes += s * ab
     peak, peak_src = _peaks()
     achieved = alg_bytes / (t_dev / K) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -311,15 +326,18 @@ def run_ours(args):
                 "dtype": "f16-storage/f32-math" if storage == "fp16" else "f32",
                 "data": "synthetic",
                 "config": {"workload": args.workload if "_" in args.workload
-                           else f"{args.workload}_{storage}", "nodes": int(N),
-                           "dims": list(b.dims), "storage": storage,
+                           else f"{args.workload}_{storage}",
+                           "lattice_updates_per_step": int(N),
+                           "blocks": [{"dims": list(blk.dims), "h": blk.h, "substeps": s}
+                                      for blk, s in zip(sc.blocks, subs)],
+                           "storage": storage,
                            "parallelism": "replicas" if ws > 1 else "single",
                            "l2": "inputs larger than L2 (state %.2f GB)" %
                                  (N * (27 * (2 if storage == 'fp16' else 4) * 2 + 32) / 1e9)},
                 "gb_per_s_algorithmic": achieved,
                 "roofline": roofline,
                 "e2e": e2e,
-                "gpu_launches": K,
+                "gpu_launches": K * launches_per_step,
                 "clocks": clk,
                 "mass_check": float(red[0])}
         if ws == 1 and not args.no_cpu_baseline:
@@ -337,7 +355,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="plume256",
-                    choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16"])
+                    choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
+                             "multiscale3"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -193,6 +193,13 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
    bit-identical to calling lbm_step on each domain. */
 lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t steps);
 
+/* Self-test of the bounded device-wide barrier used by lbm_step_batch (no counterpart in the
+   paper): launches a small cooperative kernel whose barrier waits for `extra` CTAs that do
+   not exist, so every wait expires after about limit_ms (0 < limit_ms <= 5000).  Returns
+   LBM_ERR_TIMEOUT when the bounded wait gave up and reported it (extra > 0), LBM_OK when
+   the barrier completed (extra = 0); the CUDA context stays usable either way. */
+lbm_status lbm_barrier_selftest(int32_t extra, double limit_ms, void* cuda_stream);
+
 /* Enables recording of a reverse-mode tape by lbm_step: the state is checkpointed every
    `checkpoint_every` steps from the last lbm_init_macro (k >= 1; 0 disables). */
 lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every);

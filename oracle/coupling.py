@@ -32,6 +32,9 @@ Readings (the paper is silent or ambiguous):
   * Before sub-step j (j = 1..l) the ghost layer holds the mapping of the source scale at
     time t_n + (j-1) h, linearly interpolated between the source's states at t_n and
     t_n + dt_0 (Sec. 4.2.4); a pull step reads the ghost layer at the start of the sub-step.
+    The j = 1 mapping refreshes the ghost layer of the block's t_n state (its source may
+    have been post-mapped since), and that refreshed state is the t_n source of finer
+    blocks.
   * Temporal alignment (Sec. 4.2.4): the block's interior at t_n + dt_0 is the quadratic
     Lagrange interpolant through its states at t_n, t_n + (l-1) h and t_n + l h; the
     stored velocity is recomputed from the interpolated populations and the scalar is
@@ -268,6 +271,10 @@ class MultiScale:
             states = [b.state]
             for j in range(1, b.substeps + 1):
                 self.prior_map(i, (j - 1) * b.h, saved)
+                if j == 1:
+                    # the block's t_n state, with its ghost layer refreshed from the source
+                    # at t_n, is what finer blocks interpolate from
+                    saved[i] = b.state.clone()
                 b.state = grid.step(b.state, b.params)
                 states.append(b.state)
             if b.integer_ratio and abs(b.substeps * b.h - 1.0) < 1e-9:

@@ -1,10 +1,364 @@
-// Batched persistent stepping of many independent single-block domains.
+// Batched persistent stepping of many independent single-block domains of uneven sizes.
+//
+// All domains' nodes are cut into chunks of consecutive node indices; one cooperative,
+// persistent kernel walks the joint chunk list for every step and separates the steps with a
+// device-wide barrier.  The barrier's waits are bounded by a clock limit: a CTA that waits too
+// long sets the TIMEOUT bit of the error word and every CTA leaves the kernel, so a lost CTA
+// can never hang the GPU.  The launch (plus the reset of the barrier counters) is captured in
+// a CUDA graph and replayed.  Every node runs the same cell_update as the single-block kernel,
+// so results are bit-identical to stepping each domain on its own.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "lbm_cell.cuh"
 #include "runtime.h"
+
+namespace lbm {
+
+struct BatchItem {
+  int dom;        // domain index in the batch
+  uint32_t start; // first node of the chunk
+};
+
+struct BarrierState {
+  unsigned int count;
+  unsigned int gen;
+};
+
+constexpr long long kBarrierLimitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// Device-wide barrier with a bounded wait.  Returns false when the wait gave up.
+__device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned int nblocks, int* err,
+                                             long long limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = &bs->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bs->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&bs->count, 0u);
+      __threadfence();
+      atomicAdd(&bs->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > limit) {
+          atomicOr(err, 8);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename T, typename IT>
+__global__ void __launch_bounds__(256) k_batch(const BlockView* __restrict__ views,
+                                               const BatchItem* __restrict__ items, int n_items,
+                                               int chunk, int steps, BarrierState* bs,
+                                               unsigned int expected_blocks, int* err,
+                                               long long limit) {
+  for (int s = 0; s < steps; ++s) {
+    const int p = s & 1;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+      const BatchItem it = items[w];
+      const BlockView& v = views[2 * it.dom + p];
+      const uint32_t nx = (uint32_t)v.nx, nxy = (uint32_t)v.nx * (uint32_t)v.ny;
+      const uint32_t end = min((uint32_t)v.N, it.start + (uint32_t)chunk);
+      for (uint32_t idx = it.start + threadIdx.x; idx < end; idx += blockDim.x) {
+        const uint32_t z = idx / nxy;
+        const uint32_t r = idx - z * nxy;
+        const uint32_t y = r / nx;
+        cell_update<T, IT>(v, (int)(r - y * nx), (int)y, (int)z);
+      }
+    }
+    if (s + 1 < steps) {
+      if (!grid_barrier(bs, expected_blocks, err, limit)) return;
+      if (*((volatile int*)err) & 8) return;
+    }
+  }
+}
+
+template <typename T, typename IT>
+static cudaError_t launch_batch_t(const BlockView* views, const BatchItem* items, int n_items,
+                                  int chunk, int steps, BarrierState* bs, int threads, int grid,
+                                  unsigned int expected, int* err, long long limit,
+                                  bool cooperative, cudaStream_t s) {
+  if (!cooperative) {
+    k_batch<T, IT><<<grid, threads, 0, s>>>(views, items, n_items, chunk, steps, bs, expected,
+                                            err, limit);
+    return cudaGetLastError();
+  }
+  void* args[] = {(void*)&views, (void*)&items, (void*)&n_items, (void*)&chunk, (void*)&steps,
+                  (void*)&bs, (void*)&expected, (void*)&err, (void*)&limit};
+  return cudaLaunchCooperativeKernel((const void*)k_batch<T, IT>, dim3(grid), dim3(threads),
+                                     args, 0, s);
+}
+
+static cudaError_t launch_batch(int storage, bool i32, const BlockView* views,
+                                const BatchItem* items, int n_items, int chunk, int steps,
+                                BarrierState* bs, int threads, int grid, unsigned int expected,
+                                int* err, long long limit, bool cooperative, cudaStream_t s) {
+  if (storage == ST_FP16) {
+    if (i32) return launch_batch_t<__half, uint32_t>(views, items, n_items, chunk, steps, bs, threads, grid, expected, err, limit, cooperative, s);
+    return launch_batch_t<__half, uint64_t>(views, items, n_items, chunk, steps, bs, threads, grid, expected, err, limit, cooperative, s);
+  }
+  if (i32) return launch_batch_t<float, uint32_t>(views, items, n_items, chunk, steps, bs, threads, grid, expected, err, limit, cooperative, s);
+  return launch_batch_t<float, uint64_t>(views, items, n_items, chunk, steps, bs, threads, grid, expected, err, limit, cooperative, s);
+}
+
+static int resident_blocks(int storage, bool i32, int threads) {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* fn = storage == ST_FP16
+                       ? (i32 ? (const void*)k_batch<__half, uint32_t> : (const void*)k_batch<__half, uint64_t>)
+                       : (i32 ? (const void*)k_batch<float, uint32_t> : (const void*)k_batch<float, uint64_t>);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+  return std::max(1, per_sm) * std::max(1, sms);
+}
+
+// Persistent state of the batched stepper, owned by the first domain of the batch.
+struct BatchPlan {
+  std::vector<lbm_domain*> doms;
+  std::vector<int> curs;
+  int steps = 0;
+  int chunk = 0, threads = 0;
+  BlockView* views = nullptr;
+  BatchItem* items = nullptr;
+  BarrierState* bar = nullptr;
+  int n_items = 0;
+  bool i32 = true;
+  int grid = 0;
+  cudaGraphExec_t exec = nullptr;
+  bool captured = false;
+};
+
+}  // namespace lbm
 
 using namespace lbm;
 
+void release_batch_plan(lbm_domain* dom) {
+  BatchPlan* p = static_cast<BatchPlan*>(dom->batch_plan);
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  dom->dev_free(p->views);
+  dom->dev_free(p->items);
+  dom->dev_free(p->bar);
+  delete p;
+  dom->batch_plan = nullptr;
+}
+
+// Views for both step parities and the chunk list of the current batch.
+static lbm_status build_plan(lbm_domain* const* doms, int n, int chunk, BatchPlan* p) {
+  lbm_domain* d0 = doms[0];
+  std::vector<BlockView> hv(2 * (size_t)n);
+  std::vector<BatchItem> hi;
+  p->i32 = true;
+  for (int i = 0; i < n; ++i) {
+    const Block& B = doms[i]->blocks[0];
+    hv[2 * i + 0] = doms[i]->view(0, B.cur, B.cur ^ 1);
+    hv[2 * i + 1] = doms[i]->view(0, B.cur ^ 1, B.cur);
+    if (27ull * B.N >= 0xFFFFFFFFull) p->i32 = false;
+    for (size_t s = 0; s < B.N; s += (size_t)chunk) hi.push_back(BatchItem{i, (uint32_t)s});
+  }
+  if (!p->i32) return d0->fail(LBM_ERR_UNSUPPORTED, "batched domains must have 27 N < 2^32");
+  p->views = static_cast<BlockView*>(d0->dev_alloc(hv.size() * sizeof(BlockView)));
+  p->items = static_cast<BatchItem*>(d0->dev_alloc(hi.size() * sizeof(BatchItem)));
+  p->bar = static_cast<BarrierState*>(d0->dev_alloc(sizeof(BarrierState)));
+  if (!p->views || !p->items || !p->bar) return d0->fail(LBM_ERR_OOM, "batch plan allocation failed");
+  cudaError_t e = cudaMemcpyAsync(p->views, hv.data(), hv.size() * sizeof(BlockView),
+                                  cudaMemcpyHostToDevice, d0->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->items, hi.data(), hi.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                        d0->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d0->stream);
+  if (e != cudaSuccess) return d0->cuda_fail(e, "batch plan upload");
+  p->n_items = (int)hi.size();
+  p->chunk = chunk;
+  p->doms.assign(doms, doms + n);
+  p->curs.resize(n);
+  for (int i = 0; i < n; ++i) p->curs[i] = doms[i]->blocks[0].cur;
+  return LBM_OK;
+}
+
+// Picks the chunk size of the work list by timing single-step launches that write the next
+// level without advancing any domain (no result changes).
+static lbm_status tune_chunk(lbm_domain* const* doms, int n, int* chunk_out, int* threads_out) {
+  lbm_domain* d0 = doms[0];
+  const int cand[][2] = {{256, 256}, {256, 512}, {256, 1024}, {128, 128}, {128, 256}};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  *chunk_out = 256;
+  *threads_out = 256;
+  for (const auto& c : cand) {
+    BatchPlan p;
+    lbm_status st = build_plan(doms, n, c[1], &p);
+    if (st != LBM_OK) { d0->dev_free(p.views); d0->dev_free(p.items); d0->dev_free(p.bar); cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+    const int grid = resident_blocks(d0->desc.storage, p.i32, c[0]);
+    cudaError_t e = launch_batch(d0->desc.storage, p.i32, p.views, p.items, p.n_items, p.chunk, 1,
+                                 p.bar, c[0], grid, (unsigned)grid, d0->d_err,
+                                 kBarrierLimitCycles, false, d0->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, d0->stream);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+      e = launch_batch(d0->desc.storage, p.i32, p.views, p.items, p.n_items, p.chunk, 1, p.bar,
+                       c[0], grid, (unsigned)grid, d0->d_err, kBarrierLimitCycles, false,
+                       d0->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, d0->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    d0->dev_free(p.views);
+    d0->dev_free(p.items);
+    d0->dev_free(p.bar);
+    if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return d0->cuda_fail(e, "batch tuning"); }
+    if (ms < best) { best = ms; *chunk_out = c[1]; *threads_out = c[0]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t steps) {
   if (!doms || n <= 0 || !doms[0]) return LBM_ERR_INVALID_ARG;
-  (void)steps;
-  return doms[0]->fail(LBM_ERR_UNSUPPORTED, "batched stepping not built yet");
+  lbm_domain* d0 = doms[0];
+  cudaSetDevice(d0->desc.device);
+  if (steps < 0) return d0->fail(LBM_ERR_INVALID_ARG, "negative step count");
+  for (int i = 0; i < n; ++i) {
+    if (!doms[i]) return d0->fail(LBM_ERR_INVALID_ARG, "null domain in batch");
+    for (int j = 0; j < i; ++j)
+      if (doms[j] == doms[i]) return d0->fail(LBM_ERR_INVALID_ARG, "a domain appears twice");
+    if (doms[i]->blocks.size() != 1) return d0->fail(LBM_ERR_UNSUPPORTED, "batched domains must be single-block");
+    if (doms[i]->desc.storage != d0->desc.storage) return d0->fail(LBM_ERR_INVALID_ARG, "mixed storage in batch");
+    if (doms[i]->desc.device != d0->desc.device) return d0->fail(LBM_ERR_INVALID_ARG, "mixed devices in batch");
+    if (doms[i]->tape) return d0->fail(LBM_ERR_UNSUPPORTED, "batched stepping does not record tapes");
+    if (*doms[i]->h_err & 1) return d0->fail(LBM_ERR_DIVERGED, "a domain of the batch has diverged");
+  }
+  if (steps == 0) return LBM_OK;
+  cudaStream_t s = d0->stream;
+  // order the batch after pending work of every domain, and every domain after the batch
+  std::vector<cudaEvent_t> evs;
+  for (int i = 1; i < n; ++i) {
+    if (doms[i]->stream == s) continue;
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) break;
+    cudaEventRecord(ev, doms[i]->stream);
+    cudaStreamWaitEvent(s, ev, 0);
+    evs.push_back(ev);
+  }
+  for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+
+  BatchPlan* p = static_cast<BatchPlan*>(d0->batch_plan);
+  bool reuse = p && p->steps == steps && (int)p->doms.size() == n;
+  if (reuse)
+    for (int i = 0; i < n && reuse; ++i)
+      reuse = p->doms[i] == doms[i] && p->curs[i] == doms[i]->blocks[0].cur;
+  if (!reuse) {
+    int chunk = 256, threads = 256;
+    if (p) { chunk = p->chunk; threads = p->threads; }
+    else {
+      lbm_status st = tune_chunk(doms, n, &chunk, &threads);
+      if (st != LBM_OK) return st;
+    }
+    release_batch_plan(d0);
+    p = new BatchPlan();
+    d0->batch_plan = p;
+    lbm_status st = build_plan(doms, n, chunk, p);
+    if (st != LBM_OK) { release_batch_plan(d0); return st; }
+    p->threads = threads;
+    p->steps = steps;
+    p->grid = std::min(resident_blocks(d0->desc.storage, p->i32, threads), std::max(1, p->n_items));
+    // capture: reset the barrier, then the cooperative persistent launch
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaMemsetAsync(p->bar, 0, sizeof(BarrierState), s);
+      if (e1 == cudaSuccess)
+        e1 = launch_batch(d0->desc.storage, p->i32, p->views, p->items, p->n_items, p->chunk,
+                          steps, p->bar, threads, p->grid, (unsigned)p->grid, d0->d_err,
+                          kBarrierLimitCycles, true, s);
+      cudaError_t e2 = cudaStreamEndCapture(s, &g);
+      if (e1 == cudaSuccess && e2 == cudaSuccess && g) {
+        e = cudaGraphInstantiate(&p->exec, g, 0);
+        p->captured = e == cudaSuccess;
+        if (!p->captured) p->exec = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();  // a capture the driver refused leaves the direct launch below
+  }
+  cudaError_t e;
+  if (p->captured) {
+    e = cudaGraphLaunch(p->exec, s);
+  } else {
+    e = cudaMemsetAsync(p->bar, 0, sizeof(BarrierState), s);
+    if (e == cudaSuccess)
+      e = launch_batch(d0->desc.storage, p->i32, p->views, p->items, p->n_items, p->chunk, steps,
+                       p->bar, p->threads, p->grid, (unsigned)p->grid, d0->d_err,
+                       kBarrierLimitCycles, true, s);
+  }
+  if (e != cudaSuccess) return d0->cuda_fail(e, "batched launch");
+  for (int i = 0; i < n; ++i) {
+    Block& B = doms[i]->blocks[0];
+    if (steps & 1) B.cur ^= 1;
+    doms[i]->steps += steps;
+  }
+  // every domain's stream waits for the batch (each node reports divergence into its own
+  // domain's error word; a barrier timeout is reported by the first domain)
+  cudaEvent_t done;
+  if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+    cudaEventRecord(done, s);
+    for (int i = 1; i < n; ++i)
+      if (doms[i]->stream != s) cudaStreamWaitEvent(doms[i]->stream, done, 0);
+    cudaEventDestroy(done);
+  }
+  d0->post_error_probe();
+  return LBM_OK;
+}
+
+// Self-test of the bounded device barrier: a cooperative kernel waits for `extra` more CTAs
+// than it launched, so every wait runs out after about `limit_ms`; the expected result is
+// LBM_ERR_TIMEOUT with the context still usable.
+__global__ void k_barrier_selftest(BarrierState* bs, unsigned int expected, int* err,
+                                   long long limit) {
+  grid_barrier(bs, expected, err, limit);
+}
+
+extern "C" lbm_status lbm_barrier_selftest(int32_t extra, double limit_ms, void* cuda_stream) {
+  if (extra < 0 || !(limit_ms > 0.0) || limit_ms > 5000.0) return LBM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  BarrierState* bs = nullptr;
+  int* err = nullptr;
+  if (cudaMalloc(&bs, sizeof(BarrierState)) != cudaSuccess) return LBM_ERR_OOM;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) { cudaFree(bs); return LBM_ERR_OOM; }
+  int dev = 0, clock_khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
+  const long long limit = (long long)(limit_ms * (clock_khz > 0 ? clock_khz : 2000000));
+  cudaMemsetAsync(bs, 0, sizeof(BarrierState), s);
+  cudaMemsetAsync(err, 0, sizeof(int), s);
+  const int grid = 4;
+  const unsigned int expected = (unsigned)(grid + extra);
+  void* args[] = {(void*)&bs, (void*)&expected, (void*)&err, (void*)&limit};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3(grid),
+                                              dim3(32), args, 0, s);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(bs);
+  cudaFree(err);
+  if (e != cudaSuccess) return LBM_ERR_CUDA;
+  return (h & 8) ? LBM_ERR_TIMEOUT : LBM_OK;
 }

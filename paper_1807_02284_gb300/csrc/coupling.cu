@@ -1,16 +1,432 @@
-// Continuous-scale coupling (Sec. 4.2, Algorithm 1): refined blocks, prior-/post-mapping,
-// temporal alignment.
+// Continuous-scale coupling (Sec. 3.2, Sec. 4.2, Algorithm 1): refined blocks at arbitrary
+// spacing ratios, prior-mapping of their scale boundary from the nearest coarser block,
+// temporal alignment of their sub-cycled states, and post-mapping of their interior into
+// every coarser block.
+//
+// Mapping of post-collision populations from scale s_i to s_j (Sec. 3.2):
+//   f^{s_j} = T (m^eq + K_hat (m - m^eq)),  K_hat = (I - S^{s_j}) K (I - S^{s_i})^{-1},
+//   diag K = S^{s_i} / (alpha S^{s_j}) on moments 4..8 and 1 elsewhere, alpha = dx_i / dx_j.
+// With the same high-order rates on both scales K_hat is 1 outside moments 4..8, so the
+// mapping scales only the non-equilibrium shear and deviatoric stress moments: it is the
+// relaxation routine with keep factor K_hat on those moments and 1 on every other one.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lbm_cell.cuh"
 #include "runtime.h"
+
+namespace lbm {
+
+// ------------------------------------------------------------------------------ kernels
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_map(MapArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n) return;
+  const MapEntry m = a.table[e];
+  if (a.dst_flags[m.dst] & a.skip_mask) return;
+  const T* lo = static_cast<const T*>(a.f_lo);
+  const T* hi = static_cast<const T*>(a.f_hi);
+  const size_t sN = a.sN;
+  const size_t sx = 1, sy = (size_t)a.snx, sz = (size_t)a.snx * a.sny;
+  float acc[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) acc[k] = 0.0f;
+  float cacc = 0.0f, wsum = 0.0f;
+  const float th = a.theta;
+  const bool use_lo = th < 1.0f, use_hi = th > 0.0f;
+#pragma unroll 1
+  for (int corner = 0; corner < 8; ++corner) {
+    const int bx = corner & 1, by = (corner >> 1) & 1, bz = corner >> 2;
+    const size_t s = (size_t)m.src + bx * sx + by * sy + bz * sz;
+    float w = (bx ? m.tx : 1.0f - m.tx) * (by ? m.ty : 1.0f - m.ty) * (bz ? m.tz : 1.0f - m.tz);
+    if (a.src_flags[s] & F_SOLID) w = 0.0f;     // obstacle corners are dropped
+    if (w == 0.0f) continue;
+    wsum += w;
+    const float wl = w * (1.0f - th), wh = w * th;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+      float v = 0.0f;
+      if (use_lo) v = wl * load_pop(lo + (size_t)k * sN + s);
+      if (use_hi) v = fmaf(wh, load_pop(hi + (size_t)k * sN + s), v);
+      acc[k] += v;
+    }
+    float cv = 0.0f;
+    if (use_lo) cv = wl * a.c_lo[s];
+    if (use_hi) cv = fmaf(wh, a.c_hi[s], cv);
+    cacc += cv;
+  }
+  if (!(wsum > 0.0f)) return;                   // every corner is an obstacle: unchanged
+  const float inv_w = 1.0f / wsum;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) acc[k] *= inv_w;
+  raw_moments(acc);
+  const float drho = acc[kap(0, 0, 0)];
+  const float inv = 1.0f / (1.0f + drho);
+  const float ux = acc[kap(1, 0, 0)] * inv, uy = acc[kap(0, 1, 0)] * inv,
+              uz = acc[kap(0, 0, 1)] * inv;
+  Keep kf;
+  kf.nu = a.khat;
+  kf.g[0] = kf.g[1] = kf.g[2] = kf.g[3] = 1.0f;
+  collide_from_raw(acc, drho, ux, uy, uz, kf);
+  T* out = static_cast<T*>(a.f_dst);
+  const size_t dN = a.dN;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) store_pop(out + (size_t)k * dN + m.dst, acc[k]);
+  a.u_dst[m.dst] = ux;
+  a.u_dst[dN + m.dst] = uy;
+  a.u_dst[2 * dN + m.dst] = uz;
+  a.c_dst[m.dst] = cacc * inv_w;
+}
+
+cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const int threads = 128;
+  const int grid = (a.n + threads - 1) / threads;
+  if (storage == ST_FP16) k_map<__half><<<grid, threads, 0, s>>>(a);
+  else k_map<float><<<grid, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Quadratic Lagrange interpolation in time of a refined block's interior (Sec. 4.2.4).
+template <typename T>
+__global__ void k_align(AlignArgs a) {
+  const size_t N = a.N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    if (a.flags[idx] & (F_GHOST | F_SOLID)) continue;
+    const T* f0 = static_cast<const T*>(a.f0);
+    const T* f1 = static_cast<const T*>(a.f1);
+    const T* f2 = static_cast<const T*>(a.f2);
+    T* out = static_cast<T*>(a.f_out);
+    float d[27];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+      const size_t i = (size_t)k * N + idx;
+      d[k] = fmaf(a.L0, load_pop(f0 + i), fmaf(a.L1, load_pop(f1 + i), a.L2 * load_pop(f2 + i)));
+    }
+    const float c = fmaf(a.L0, a.c0[idx], fmaf(a.L1, a.c1[idx], a.L2 * a.c2[idx]));
+    float drho, jx, jy, jz;
+    macros(d, drho, jx, jy, jz);
+    const float inv = 1.0f / (1.0f + drho);
+#pragma unroll
+    for (int k = 0; k < 27; ++k) store_pop(out + (size_t)k * N + idx, d[k]);
+    a.u_out[idx] = jx * inv;
+    a.u_out[N + idx] = jy * inv;
+    a.u_out[2 * N + idx] = jz * inv;
+    a.c_out[idx] = c;
+  }
+}
+
+cudaError_t launch_align(const AlignArgs& a, int storage, cudaStream_t s) {
+  const size_t g = (a.N + 255) / 256;
+  const int grid = (int)(g < 16384 ? g : 16384);
+  if (storage == ST_FP16) k_align<__half><<<grid, 256, 0, s>>>(a);
+  else k_align<float><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_ghost_layer(uint8_t* flags, int nx, int ny, int nz) {
+  const size_t N = (size_t)nx * ny * nz;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((size_t)nx * ny));
+    const bool edge = x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1;
+    if (edge) flags[idx] |= F_GHOST;
+  }
+}
+
+cudaError_t launch_set_ghost_layer(uint8_t* flags, int nx, int ny, int nz, cudaStream_t s) {
+  const size_t N = (size_t)nx * ny * nz;
+  const size_t g = (N + 255) / 256;
+  k_set_ghost_layer<<<(int)(g < 8192 ? g : 8192), 256, 0, s>>>(flags, nx, ny, nz);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm
 
 using namespace lbm;
 
-lbm_status multiscale_step(lbm_domain* dom) {
-  return dom->fail(LBM_ERR_UNSUPPORTED, "multi-scale stepping not built yet");
+// --------------------------------------------------------------------------- host side
+
+namespace {
+
+double shear_rate(double nu) { return 1.0 / (3.0 * nu + 0.5); }
+
+// K_hat on moments 4..8 for src -> dst (Sec. 3.2); alpha = dx_src / dx_dst.
+double khat(const Block& src, const Block& dst) {
+  const double Ss = shear_rate(src.nu), Sd = shear_rate(dst.nu);
+  const double alpha = src.h / dst.h;
+  return (1.0 - Sd) * (Ss / (alpha * Sd)) / (1.0 - Ss);
+}
+
+// Trilinear cell of a reference-unit point p in block B: lower corner index and fractions.
+void cell_of(const Block& B, const double p[3], uint32_t* base, float t[3]) {
+  const int n[3] = {B.nx, B.ny, B.nz};
+  int i0[3];
+  for (int a = 0; a < 3; ++a) {
+    const double q = (p[a] - B.origin[a]) / B.h;
+    int i = (int)std::floor(q);
+    i = std::max(0, std::min(i, std::max(n[a] - 2, 0)));
+    i0[a] = i;
+    t[a] = (float)(q - i);
+  }
+  *base = (uint32_t)(((size_t)i0[2] * B.ny + i0[1]) * B.nx + i0[0]);
+}
+
+bool contains(const Block& outer, const Block& inner) {
+  for (int a = 0; a < 3; ++a) {
+    const int no = a == 0 ? outer.nx : a == 1 ? outer.ny : outer.nz;
+    const int ni = a == 0 ? inner.nx : a == 1 ? inner.ny : inner.nz;
+    const double lo = inner.origin[a], hi = inner.origin[a] + (ni - 1) * inner.h;
+    const double olo = outer.origin[a], ohi = outer.origin[a] + (no - 1) * outer.h;
+    if (lo < olo - 1e-9 || hi > ohi + 1e-9) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+static lbm_status upload_table(lbm_domain* dom, const std::vector<MapEntry>& h, MapTable* t) {
+  t->n = (int)h.size();
+  if (h.empty()) return LBM_OK;
+  t->d = static_cast<MapEntry*>(dom->dev_alloc(h.size() * sizeof(MapEntry)));
+  if (!t->d) return dom->fail(LBM_ERR_OOM, "mapping table allocation failed");
+  cudaError_t e = cudaMemcpyAsync(t->d, h.data(), h.size() * sizeof(MapEntry),
+                                  cudaMemcpyHostToDevice, dom->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "mapping table upload");
+  return LBM_OK;
 }
 
 extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3], double h,
                                           const int32_t dims[3], int32_t* block_id) {
   if (!dom) return LBM_ERR_INVALID_ARG;
-  (void)origin; (void)h; (void)dims; (void)block_id;
-  return dom->fail(LBM_ERR_UNSUPPORTED, "scale blocks not built yet");
+  cudaSetDevice(dom->desc.device);
+  if (!origin || !dims || !block_id) return dom->fail(LBM_ERR_INVALID_ARG, "null argument");
+  if (!(h > 0.0) || !std::isfinite(h)) return dom->fail(LBM_ERR_INVALID_ARG, "h must be positive");
+  if (h >= 1.0)
+    return dom->fail(LBM_ERR_UNSUPPORTED, "scales coarser than the reference scale (far field) are not built");
+  if (dom->desc.storage != LBM_FP32)
+    return dom->fail(LBM_ERR_UNSUPPORTED, "refined blocks need FP32 storage");
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 4) return dom->fail(LBM_ERR_INVALID_ARG, "refined blocks need >= 4 nodes per axis");
+  if ((double)dims[0] * dims[1] * dims[2] * 27.0 >= 4294967295.0)
+    return dom->fail(LBM_ERR_INVALID_ARG, "refined block too large");
+  if (dims[2] > 65535) return dom->fail(LBM_ERR_INVALID_ARG, "nz must be <= 65535");
+  if (dom->blocks.size() > 1 && h > dom->blocks.back().h + 1e-12)
+    return dom->fail(LBM_ERR_INVALID_ARG, "blocks must be added coarse to fine");
+  if ((double)dom->blocks[0].N * 27.0 >= 4294967295.0)
+    return dom->fail(LBM_ERR_UNSUPPORTED, "the reference block is too large for coupling tables");
+
+  Block B;
+  B.nx = dims[0]; B.ny = dims[1]; B.nz = dims[2];
+  B.N = (size_t)B.nx * B.ny * B.nz;
+  for (int a = 0; a < 3; ++a) B.origin[a] = origin[a];
+  B.h = h;
+  B.nu = dom->desc.nu / h;               // Re invariance: 1/S_f - 1/2 = alpha (1/S_c - 1/2)
+  const double ratio = 1.0 / h;
+  B.substeps = std::max(1, (int)std::ceil(ratio - 1e-9));
+  B.integer_ratio = std::fabs(ratio - std::round(ratio)) < 1e-9;
+  B.rp = dom->relax_params(B.nu);
+  if (!contains(dom->blocks[0], B))
+    return dom->fail(LBM_ERR_INVALID_ARG, "the block must lie inside the reference block");
+  if (std::fabs(1.0 - shear_rate(B.nu)) < 1e-12)
+    return dom->fail(LBM_ERR_INVALID_ARG, "K_hat is undefined for S = 1 (nu = 1/6 on this block)");
+  for (const Block& C : dom->blocks)
+    if (std::fabs(1.0 - shear_rate(C.nu)) < 1e-12)
+      return dom->fail(LBM_ERR_INVALID_ARG, "K_hat is undefined for S = 1 on a coarser block");
+
+  // prior-mapping source: the finest coarser block that contains the whole block
+  int parent = 0;
+  for (size_t j = 1; j < dom->blocks.size(); ++j) {
+    const Block& C = dom->blocks[j];
+    if (C.h > B.h && contains(C, B) && C.h < dom->blocks[parent].h) parent = (int)j;
+  }
+  B.parent = parent;
+  const int id = (int)dom->blocks.size();
+
+  lbm_status st = dom->alloc_block_levels(B, 3);
+  if (st != LBM_OK) return st;
+  dom->blocks.push_back(B);
+  Block& NB = dom->blocks.back();
+  st = dom->clear_block(id);
+  if (st != LBM_OK) return st;
+  cudaError_t e = launch_set_ghost_layer(NB.flags, NB.nx, NB.ny, NB.nz, dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "ghost flags");
+
+  // prior table: ghost nodes of the new block -> cells of the parent
+  {
+    std::vector<MapEntry> tab;
+    const Block& P = dom->blocks[parent];
+    for (int z = 0; z < NB.nz; ++z)
+      for (int y = 0; y < NB.ny; ++y)
+        for (int x = 0; x < NB.nx; ++x) {
+          const bool edge = x == 0 || y == 0 || z == 0 || x == NB.nx - 1 || y == NB.ny - 1 ||
+                            z == NB.nz - 1;
+          if (!edge) continue;
+          const double p[3] = {NB.origin[0] + x * NB.h, NB.origin[1] + y * NB.h,
+                               NB.origin[2] + z * NB.h};
+          MapEntry m;
+          m.dst = (uint32_t)(((size_t)z * NB.ny + y) * NB.nx + x);
+          float t[3];
+          cell_of(P, p, &m.src, t);
+          m.tx = t[0]; m.ty = t[1]; m.tz = t[2];
+          tab.push_back(m);
+        }
+    NB.prior.src = parent;
+    NB.prior.dst = id;
+    NB.prior.khat = (float)khat(P, NB);
+    st = upload_table(dom, tab, &NB.prior);
+    if (st != LBM_OK) return st;
+  }
+  // post tables: nodes of every coarser block inside the new block's interior span
+  for (int k = 0; k < id; ++k) {
+    const Block& T = dom->blocks[k];
+    if (!(T.h > NB.h)) continue;
+    const int nT[3] = {T.nx, T.ny, T.nz};
+    const int nB[3] = {NB.nx, NB.ny, NB.nz};
+    int lo[3], hi[3];
+    bool empty = false;
+    for (int a = 0; a < 3; ++a) {
+      const double plo = NB.origin[a] + NB.h, phi = NB.origin[a] + (nB[a] - 2) * NB.h;
+      lo[a] = std::max(0, (int)std::ceil((plo - 1e-9 - T.origin[a]) / T.h));
+      hi[a] = std::min(nT[a] - 1, (int)std::floor((phi + 1e-9 - T.origin[a]) / T.h));
+      while (lo[a] <= hi[a] && T.origin[a] + lo[a] * T.h < plo - 1e-9) ++lo[a];
+      while (hi[a] >= lo[a] && T.origin[a] + hi[a] * T.h > phi + 1e-9) --hi[a];
+      if (lo[a] > hi[a]) empty = true;
+    }
+    MapTable mt;
+    mt.src = id;
+    mt.dst = k;
+    mt.khat = (float)khat(NB, T);
+    if (!empty) {
+      std::vector<MapEntry> tab;
+      tab.reserve((size_t)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1));
+      for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+          for (int x = lo[0]; x <= hi[0]; ++x) {
+            const double p[3] = {T.origin[0] + x * T.h, T.origin[1] + y * T.h,
+                                 T.origin[2] + z * T.h};
+            MapEntry m;
+            m.dst = (uint32_t)(((size_t)z * T.ny + y) * T.nx + x);
+            float t[3];
+            cell_of(NB, p, &m.src, t);
+            m.tx = t[0]; m.ty = t[1]; m.tz = t[2];
+            tab.push_back(m);
+          }
+      st = upload_table(dom, tab, &mt);
+      if (st != LBM_OK) return st;
+    }
+    NB.post.push_back(mt);
+  }
+  dom->pick_tiles(id);
+  dom->invalidate_graphs();
+  dom->on_state_reset(id);
+  *block_id = id;
+  return LBM_OK;
+}
+
+// Prior-mapping of block b's ghost layer at time t_n + theta dt_0 into level `dst_level`.
+static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& saved, float theta,
+                             int dst_level) {
+  Block& B = dom->blocks[b];
+  const Block& P = dom->blocks[B.prior.src];
+  MapArgs a;
+  a.table = B.prior.d;
+  a.n = B.prior.n;
+  a.f_lo = P.lv[saved[B.prior.src]].f;
+  a.c_lo = P.lv[saved[B.prior.src]].c;
+  a.f_hi = P.lv[P.cur].f;
+  a.c_hi = P.lv[P.cur].c;
+  a.theta = theta;
+  a.src_flags = P.flags;
+  a.snx = P.nx; a.sny = P.ny; a.sN = P.N;
+  a.f_dst = B.lv[dst_level].f;
+  a.u_dst = B.lv[dst_level].u;
+  a.c_dst = B.lv[dst_level].c;
+  a.dst_flags = B.flags;
+  a.skip_mask = F_SOLID;
+  a.dN = B.N;
+  a.khat = B.prior.khat;
+  return launch_map(a, dom->desc.storage, dom->stream);
+}
+
+static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t) {
+  const Block& B = dom->blocks[b];
+  Block& T = dom->blocks[t.dst];
+  MapArgs a;
+  a.table = t.d;
+  a.n = t.n;
+  a.f_lo = a.f_hi = B.lv[B.cur].f;
+  a.c_lo = a.c_hi = B.lv[B.cur].c;
+  a.theta = 0.0f;
+  a.src_flags = B.flags;
+  a.snx = B.nx; a.sny = B.ny; a.sN = B.N;
+  a.f_dst = T.lv[T.cur].f;
+  a.u_dst = T.lv[T.cur].u;
+  a.c_dst = T.lv[T.cur].c;
+  a.dst_flags = T.flags;
+  a.skip_mask = F_SOLID | F_GHOST;
+  a.dN = T.N;
+  a.khat = t.khat;
+  return launch_map(a, dom->desc.storage, dom->stream);
+}
+
+// One reference step of Algorithm 1 over all blocks.
+lbm_status multiscale_step(lbm_domain* dom) {
+  std::vector<int> saved(dom->blocks.size());
+  for (size_t b = 0; b < dom->blocks.size(); ++b) saved[b] = dom->blocks[b].cur;
+  cudaStream_t s = dom->stream;
+  cudaError_t e;
+  {  // reference scale: one step
+    Block& B0 = dom->blocks[0];
+    const int nxt = B0.cur ^ 1;
+    e = launch_step(dom->view(0, B0.cur, nxt), dom->desc.storage, B0.bx, B0.by, s);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");
+    B0.cur = nxt;
+  }
+  for (size_t bi = 1; bi < dom->blocks.size(); ++bi) {
+    const int b = (int)bi;
+    Block& B = dom->blocks[b];
+    const int L = saved[b];
+    const int A = (L + 1) % 3, Bv = (L + 2) % 3;
+    int cur = L, prev = L;
+    for (int j = 1; j <= B.substeps; ++j) {
+      e = prior_map(dom, b, saved, (float)((j - 1) * B.h), cur);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
+      const int out = (j == 1) ? A : (cur == A ? Bv : A);
+      e = launch_step(dom->view(b, cur, out), dom->desc.storage, B.bx, B.by, s);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");
+      prev = cur;
+      cur = out;
+    }
+    int aligned = cur;
+    if (!(B.integer_ratio && std::fabs(B.substeps * B.h - 1.0) < 1e-9)) {
+      const double t0 = 0.0, t1 = (B.substeps - 1) * B.h, t2 = B.substeps * B.h, T = 1.0;
+      AlignArgs a;
+      a.f0 = B.lv[L].f; a.f1 = B.lv[prev].f; a.f2 = B.lv[cur].f;
+      a.c0 = B.lv[L].c; a.c1 = B.lv[prev].c; a.c2 = B.lv[cur].c;
+      a.f_out = B.lv[prev].f; a.u_out = B.lv[prev].u; a.c_out = B.lv[prev].c;
+      a.flags = B.flags;
+      a.N = B.N;
+      a.L0 = (float)((T - t1) * (T - t2) / ((t0 - t1) * (t0 - t2)));
+      a.L1 = (float)((T - t0) * (T - t2) / ((t1 - t0) * (t1 - t2)));
+      a.L2 = (float)((T - t0) * (T - t1) / ((t2 - t0) * (t2 - t1)));
+      e = launch_align(a, dom->desc.storage, s);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "temporal alignment");
+      aligned = prev;
+    }
+    e = prior_map(dom, b, saved, 1.0f, aligned);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
+    B.cur = aligned;
+    for (const MapTable& t : B.post) {
+      e = post_map(dom, b, t);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping");
+    }
+  }
+  return LBM_OK;
 }

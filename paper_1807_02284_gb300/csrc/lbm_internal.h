@@ -27,6 +27,48 @@ struct BlockView {
   int* err;            // device error word (bit 0: non-finite or non-positive density)
 };
 
+// One node mapped between scales: destination node index, index of the source cell's
+// lower corner (i0, j0, k0) and the trilinear fractions along x, y, z.
+struct MapEntry {
+  uint32_t dst;
+  uint32_t src;
+  float tx, ty, tz;
+};
+
+// Arguments of one prior- or post-mapping launch (Sec. 3.2 / 4.2).
+struct MapArgs {
+  const MapEntry* table;
+  int n;
+  // source block: populations at the two time levels mixed with weight theta (prior-mapping
+  // interpolates the source in time; post-mapping uses lo only, theta = 0)
+  const void* f_lo;
+  const void* f_hi;
+  const float* c_lo;
+  const float* c_hi;
+  float theta;
+  const uint8_t* src_flags;
+  int snx, sny;
+  size_t sN;
+  // destination block level
+  void* f_dst;
+  float* u_dst;
+  float* c_dst;
+  const uint8_t* dst_flags;
+  uint8_t skip_mask;   // destination nodes with any of these flags are left alone
+  size_t dN;
+  float khat;          // K_hat factor of moments 4..8 (1 for all others)
+};
+
+// Arguments of the temporal alignment of one refined block (Sec. 4.2.4).
+struct AlignArgs {
+  const void* f0; const void* f1; const void* f2;   // t_n, t_n + (l-1)h, t_n + l h
+  const float* c0; const float* c1; const float* c2;
+  void* f_out; float* u_out; float* c_out;         // may alias f1 / c1 (pointwise update)
+  const uint8_t* flags;
+  size_t N;
+  float L0, L1, L2;
+};
+
 // One tile of the batched work list: a BX x BY patch of one z-plane of one simulation.
 struct WorkItem {
   int view;            // index into the BlockView array
@@ -59,6 +101,11 @@ constexpr int REDUCE_CTAS = 304;
 constexpr int REDUCE_THREADS = 256;
 cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
                           double* partials, double* out, cudaStream_t s);
+
+// ---- coupling.cu
+cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s);
+cudaError_t launch_align(const AlignArgs& a, int storage, cudaStream_t s);
+cudaError_t launch_set_ghost_layer(uint8_t* flags, int nx, int ny, int nz, cudaStream_t s);
 
 // ---- kernels_batch.cu
 cudaError_t launch_step_batch(const BlockView* views_dev, const WorkItem* items, int n_items,

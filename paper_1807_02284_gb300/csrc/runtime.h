@@ -17,7 +17,16 @@ struct Level {             // one time level of a block
   float* c = nullptr;      // passive scalar
 };
 
+struct MapTable {
+  MapEntry* d = nullptr;   // device array
+  int n = 0;
+  int src = 0, dst = 0;    // block ids
+  float khat = 1.0f;       // K_hat factor of moments 4..8 for src -> dst
+};
+
 struct Block {
+  MapTable prior;                 // ghost layer <- parent (refined blocks)
+  std::vector<MapTable> post;     // every coarser block <- this block's interior
   int nx = 0, ny = 0, nz = 0;
   size_t N = 0;
   double origin[3] = {0, 0, 0};
@@ -62,6 +71,7 @@ struct lbm_domain {
   long long steps = 0;
   lbm::TapeState* tape = nullptr;
   lbm::GraphCache* graphs = nullptr;
+  void* batch_plan = nullptr;           // cached plan of lbm_step_batch (batch.cu)
 
   lbm_status fail(lbm_status st, const std::string& msg);
   lbm_status cuda_fail(cudaError_t e, const char* what);

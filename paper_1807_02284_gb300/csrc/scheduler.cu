@@ -81,10 +81,12 @@ void lbm_domain::invalidate_graphs() {
   graphs = nullptr;
 }
 
-void release_tape(lbm_domain* dom);  // adjoint.cu
+void release_tape(lbm_domain* dom);        // adjoint.cu
+void release_batch_plan(lbm_domain* dom);  // batch.cu
 
 void lbm_domain::release_extras() {
   invalidate_graphs();
+  release_batch_plan(this);
   release_tape(this);
   if (small_host) cudaFreeHost(small_host);
   small_host = nullptr;

@@ -77,6 +77,7 @@ _SIGNATURES = {
     "lbm_set_tape": (_I, [_P, _I]),
     "lbm_adjoint_step": (_I, [_P, _I, _P, _P, _P, _P]),
     "lbm_reduce_noalloc": (_I, [_P, _I, _P, C.c_int64, _P, _P]),
+    "lbm_barrier_selftest": (_I, [_I, C.c_double, _P]),
     "lbm_last_error": (C.c_char_p, [_P]),
 }
 LBM_REDUCE_NOALLOC_MAX_NODES = 67108864

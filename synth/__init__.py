@@ -233,7 +233,28 @@ def plume(n=256, seed=1, nu=1e-5, u_in=0.1, r_in=16, sphere_r=24) -> Scene:
                  name=f"plume_{n}", steps=1000)
 
 
-def multiscale(seed=2, sphere_seed=3, nu=1e-5, u_in=0.08, scale=1.0) -> Scene:
+def smooth_field(block: Block, seed, amp=0.05, wavelength=32.0):
+    """Seeded sum of low Fourier modes evaluated at the block's node positions (reference
+    units), so overlapping blocks of any spacing sample the same continuous field.
+    Returns (u (3,z,y,x), rho (z,y,x), c (z,y,x))."""
+    rng = np.random.default_rng(seed)
+    xs, ys, zs = block.node_coords()
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    k = 2 * math.pi / wavelength
+    u = np.zeros((3,) + Z.shape)
+    for a in range(3):
+        for _ in range(3):
+            kv = rng.integers(-2, 3, size=3)
+            ph = rng.random() * 2 * math.pi
+            u[a] += rng.standard_normal() * np.cos(k * (kv[0] * X + kv[1] * Y + kv[2] * Z) + ph)
+    m = max(np.abs(u).max(), 1e-12)
+    u *= amp / m
+    rho = 1.0 + 0.2 * amp * np.cos(k * (X + 2 * Y - Z) + rng.random())
+    c = 0.5 + 0.5 * np.sin(k * (2 * X - Y) + rng.random()) * np.cos(k * Z)
+    return u, rho, c
+
+
+def multiscale(seed=2, sphere_seed=3, nu=1e-5, u_in=0.08, scale=1.0, flow_amp=0.0) -> Scene:
     """Continuous-scale 3-block domain: s0 128^3 at h=1, s1 96^3 at h=1/1.5 with origin
     (24,32,32), s2 64^3 at h=1/2.25 with origin (36,50,50); 8 seeded spheres (r in [4,12])
     inside s1's span; inflow at x=0 of s0 with +/-1% noise.  ``scale`` < 1 shrinks every
@@ -253,9 +274,14 @@ def multiscale(seed=2, sphere_seed=3, nu=1e-5, u_in=0.08, scale=1.0) -> Scene:
         r = (4 + 8 * srng.random()) * scale
         c = lo + span * (0.15 + 0.7 * srng.random(3))
         spheres.append((float(c[0]), float(c[1]), float(c[2]), float(r)))
+    if flow_amp > 0.0:
+        for b in (s0, s1, s2):
+            b.u0[:], b.rho0[:], b.c0[:] = smooth_field(b, seed + 100, amp=flow_amp,
+                                                      wavelength=max(8.0, 32.0 * scale))
     inflow_disk(s0, (n0 / 2, n0 / 2), 0.25 * n0, u_in, rng=rng, noise=0.01)
     for b in (s0, s1, s2):
         voxelise_spheres(b, spheres)
+        b.rho0[(b.flags & SOLID) != 0] = 1.0
     return Scene(blocks=[s0, s1, s2], periodic=(False, False, False), nu=nu, adaptive=True,
                  name=f"multiscale_{n0}_{n1}_{n2}", steps=500)
 

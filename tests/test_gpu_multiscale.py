@@ -1,0 +1,181 @@
+"""GPU parity of the continuous-scale coupling (prior-mapping, sub-cycling, temporal
+alignment, post-mapping, Algorithm 1) against the FP64 oracle through the C-ABI."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import coupling, grid
+from tests.helpers import f32, max_err
+
+pytestmark = pytest.mark.gpu
+
+U_REL = 1e-5
+
+
+def gpu_multiscale(scene):
+    from paper_1807_02284_gb300 import lbm
+    b0 = scene.blocks[0]
+    dom = lbm.Domain(b0.dims, scene.nu, periodic=scene.periodic, adaptive=scene.adaptive,
+                     c_src=scene.c_src)
+    for b in scene.blocks[1:]:
+        dom.add_scale_block(b.origin, b.h, b.dims)
+    for i, b in enumerate(scene.blocks):
+        dom.set_flags(b.flags, block=i)
+        dom.init_macro(f32(b.u0), rho=f32(b.rho0), c=f32(b.c0), block=i)
+    return dom
+
+
+def read_block(dom, i, shape):
+    from paper_1807_02284_gb300 import lbm
+    f = dom.read_field(lbm.LBM_FIELD_F, lbm.LBM_F64, i).reshape((27,) + shape)
+    u = dom.read_field(lbm.LBM_FIELD_U, lbm.LBM_F64, i).reshape((3,) + shape)
+    c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64, i).reshape(shape)
+    return f, u, c
+
+
+def compare(dom, ms, label, f_tol=4e-7, c_tol=2e-6):
+    worst = []
+    for i, blk in enumerate(ms.blocks):
+        shape = tuple(reversed(blk.dims))
+        f, u, c = read_block(dom, i, shape)
+        uo = blk.state.u.numpy()
+        umax = float(np.abs(uo).max())
+        eu, ef, ec = max_err(u, uo), max_err(f, blk.state.f.numpy()), max_err(c, blk.state.c.numpy())
+        worst.append((i, eu, ef, ec, umax))
+        print(f"{label} block {i}: |du|={eu:.2e} (max|u| {umax:.3f}) |df|={ef:.2e} |dc|={ec:.2e}")
+    for i, eu, ef, ec, umax in worst:
+        assert eu <= U_REL * max(umax, 1e-3), f"{label} block {i} velocity"
+        assert ef <= f_tol, f"{label} block {i} populations"
+        assert ec <= c_tol, f"{label} block {i} scalar"
+
+
+def test_block_info_reports_scales(lib):
+    sc = synth.multiscale(scale=0.25)
+    dom = gpu_multiscale(sc)
+    i1, i2 = dom.info(1), dom.info(2)
+    assert (i1.substeps, i2.substeps) == (2, 3)
+    assert i1.nu == pytest.approx(sc.nu * 1.5) and i2.nu == pytest.approx(sc.nu * 2.25)
+    flags = dom.read_field(4, 2, block=2).reshape(tuple(reversed(sc.blocks[2].dims)))
+    assert (flags[0] & synth.GHOST).all() and not (flags[1:-1, 1:-1, 1:-1] & synth.GHOST).any()
+    dom.close()
+
+
+@pytest.mark.parametrize("steps", [1, 4])
+def test_three_block_parity_non_integer_ratios(lib, steps):
+    """Reduced copy (1/4 of every length) of the 3-block scene: s0 32^3, s1 24^3 at h=1/1.5,
+    s2 16^3 at h=1/2.25, 8 spheres, inflow with noise, and a seeded smooth flow, density
+    and scalar field sampled by every block so that every mapping moves non-trivial data."""
+    sc = synth.multiscale(scale=0.25, nu=2e-3, flow_amp=0.06)
+    dom = gpu_multiscale(sc)
+    ms = coupling.MultiScale.build(sc)
+    for _ in range(steps):
+        dom.step(1)
+        ms.step()
+    dom.sync()
+    compare(dom, ms, f"3-block x{steps}")
+    dom.close()
+
+
+def test_integer_ratio_two_block_parity(lib):
+    """alpha = 2 two-block case on a periodic Taylor-Green field (no temporal interpolation:
+    two sub-steps land exactly on t_n + dt_0)."""
+    sc = synth.taylor_green(24, nz=12, re=60)
+    b1 = synth._empty_block((16, 14, 10), origin=(5.0, 4.5, 3.0), h=0.5)
+    k = 2 * math.pi / 24
+    xs, ys, zs = b1.node_coords()
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    b1.u0[0] = 0.05 * np.sin(k * X) * np.cos(k * Y)
+    b1.u0[1] = -0.05 * np.cos(k * X) * np.sin(k * Y)
+    b1.c0[:] = np.exp(-((X - 9) ** 2 + (Y - 8) ** 2) / 8.0)
+    sc.blocks.append(b1)
+    dom = gpu_multiscale(sc)
+    ms = coupling.MultiScale.build(sc)
+    for _ in range(3):
+        dom.step(1)
+        ms.step()
+    compare(dom, ms, "alpha=2")
+    dom.close()
+
+
+def test_uniform_flow_stays_uniform_full_size(lib):
+    """Full-size 3-block geometry (128^3, 96^3 at h=1/1.5, 64^3 at h=1/2.25), periodic s0, no
+    obstacles, uniform flow: every step, mapping and interpolation keeps it uniform."""
+    from paper_1807_02284_gb300 import lbm
+    full = synth.multiscale(scale=1.0)
+    blocks = []
+    for b in full.blocks:
+        nb = synth._empty_block(b.dims, origin=b.origin, h=b.h)
+        nb.u0[0], nb.u0[1], nb.u0[2] = 0.05, -0.02, 0.01
+        blocks.append(nb)
+    sc = synth.Scene(blocks=blocks, periodic=(True, True, True), nu=1e-5)
+    dom = gpu_multiscale(sc)
+    dom.step(3)
+    dom.sync()
+    for i, b in enumerate(blocks):
+        u = dom.read_field(lbm.LBM_FIELD_U, lbm.LBM_F32, i).reshape(3, -1)
+        err = np.abs(u - np.array([[0.05], [-0.02], [0.01]], np.float32)).max()
+        print(f"uniform full-size block {i}: max |u - u0| = {err:.2e}")
+        assert err < 2e-6
+    dom.close()
+
+
+def test_full_size_reference_block_far_field_sampled(lib):
+    """Full-size 3-block scene: one reference step at s0 nodes away from the refined blocks
+    is the single-block update of the GPU's own t_n state, checked node by node."""
+    from paper_1807_02284_gb300 import lbm
+    sc = synth.multiscale(scale=1.0)
+    dom = gpu_multiscale(sc)
+    dom.step(3)
+    b0 = sc.blocks[0]
+    shape = b0.shape_zyx
+    f = dom.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32, 0).reshape((27,) + shape)
+    u = dom.read_field(lbm.LBM_FIELD_U, lbm.LBM_F32, 0).reshape((3,) + shape)
+    c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F32, 0).reshape(shape)
+    dom.step(1)
+    f1 = dom.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32, 0).reshape((27,) + shape)
+    st = grid.State(torch.from_numpy(f.astype(np.float64)), torch.from_numpy(u.astype(np.float64)),
+                    torch.from_numpy(c.astype(np.float64)), torch.from_numpy(b0.flags.copy()))
+    rng = np.random.default_rng(1)
+    s1 = sc.blocks[1]
+    lo = np.array(s1.origin) - 2
+    hi = np.array(s1.origin) + (np.array(s1.dims) - 1) * s1.h + 2
+    pts = []
+    while len(pts) < 3000:
+        p = rng.integers(0, 128, 3)   # (x, y, z)
+        if np.all(p >= lo) and np.all(p <= hi):
+            continue
+        pts.append(p)
+    pts = np.array(pts)
+    x, y, z = (torch.from_numpy(pts[:, i].astype(np.int64)) for i in range(3))
+    fo, uo, co = grid.step_cells(st, grid.Params(nu=sc.nu, periodic=sc.periodic, c_src=sc.c_src),
+                                 z, y, x)
+    got = f1[:, pts[:, 2], pts[:, 1], pts[:, 0]].T
+    err = np.abs(got - fo.numpy()).max()
+    print(f"far-field sampled s0: |df| = {err:.2e}")
+    assert err < 2e-7
+    dom.close()
+
+
+def test_scale_block_argument_checks(lib):
+    from paper_1807_02284_gb300 import lbm
+    dom = lbm.Domain((16, 16, 16), 1e-3)
+    with pytest.raises(lbm.LBMError) as ei:
+        dom.add_scale_block((2, 2, 2), 1.5, (8, 8, 8))
+    assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
+    with pytest.raises(lbm.LBMError) as ei:
+        dom.add_scale_block((10, 10, 10), 0.5, (20, 8, 8))          # sticks out of s0
+    assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
+    with pytest.raises(lbm.LBMError):
+        dom.add_scale_block((2, 2, 2), 0.5, (3, 8, 8))              # too thin
+    dom.add_scale_block((2, 2, 2), 0.5, (8, 8, 8))
+    with pytest.raises(lbm.LBMError):
+        dom.add_scale_block((2, 2, 2), 0.75, (8, 8, 8))             # not coarse to fine
+    dom.close()
+    d16 = lbm.Domain((16, 16, 16), 1e-3, storage="fp16")
+    with pytest.raises(lbm.LBMError) as ei:
+        d16.add_scale_block((2, 2, 2), 0.5, (8, 8, 8))
+    assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
+    d16.close()
