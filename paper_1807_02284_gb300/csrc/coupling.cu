@@ -22,47 +22,62 @@ namespace lbm {
 
 // ------------------------------------------------------------------------------ kernels
 
-template <typename T>
+// MODE 0: source level lo only; 1: level hi only; 2: (1 - theta) lo + theta hi.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(128) k_map(MapArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= a.n) return;
   const MapEntry m = a.table[e];
   if (a.dst_flags[m.dst] & a.skip_mask) return;
-  const T* lo = static_cast<const T*>(a.f_lo);
-  const T* hi = static_cast<const T*>(a.f_hi);
-  const size_t sN = a.sN;
-  const size_t sx = 1, sy = (size_t)a.snx, sz = (size_t)a.snx * a.sny;
-  float acc[27];
+  const T* __restrict__ lo = static_cast<const T*>(MODE == 1 ? a.f_hi : a.f_lo);
+  const T* __restrict__ hi = static_cast<const T*>(a.f_hi);
+  const float* __restrict__ clo = MODE == 1 ? a.c_hi : a.c_lo;
+  const uint32_t sN = (uint32_t)a.sN;
+  const uint32_t sy = (uint32_t)a.snx, sz = (uint32_t)a.snx * (uint32_t)a.sny;
+  // the 8 corners, their obstacle flags (loaded together) and trilinear weights
+  uint32_t s[8];
+  float w[8];
+  float wsum = 0.0f;
 #pragma unroll
-  for (int k = 0; k < 27; ++k) acc[k] = 0.0f;
-  float cacc = 0.0f, wsum = 0.0f;
-  const float th = a.theta;
-  const bool use_lo = th < 1.0f, use_hi = th > 0.0f;
-#pragma unroll 1
-  for (int corner = 0; corner < 8; ++corner) {
-    const int bx = corner & 1, by = (corner >> 1) & 1, bz = corner >> 2;
-    const size_t s = (size_t)m.src + bx * sx + by * sy + bz * sz;
-    float w = (bx ? m.tx : 1.0f - m.tx) * (by ? m.ty : 1.0f - m.ty) * (bz ? m.tz : 1.0f - m.tz);
-    if (a.src_flags[s] & F_SOLID) w = 0.0f;     // obstacle corners are dropped
-    if (w == 0.0f) continue;
-    wsum += w;
-    const float wl = w * (1.0f - th), wh = w * th;
+  for (int c = 0; c < 8; ++c) s[c] = m.src + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz;
 #pragma unroll
-    for (int k = 0; k < 27; ++k) {
-      float v = 0.0f;
-      if (use_lo) v = wl * load_pop(lo + (size_t)k * sN + s);
-      if (use_hi) v = fmaf(wh, load_pop(hi + (size_t)k * sN + s), v);
-      acc[k] += v;
-    }
-    float cv = 0.0f;
-    if (use_lo) cv = wl * a.c_lo[s];
-    if (use_hi) cv = fmaf(wh, a.c_hi[s], cv);
-    cacc += cv;
+  for (int c = 0; c < 8; ++c) {
+    const float wc = ((c & 1) ? m.tx : 1.0f - m.tx) * (((c >> 1) & 1) ? m.ty : 1.0f - m.ty) *
+                     ((c >> 2) ? m.tz : 1.0f - m.tz);
+    w[c] = (__ldg(a.src_flags + s[c]) & F_SOLID) ? 0.0f : wc;   // obstacle corners dropped
+    wsum += w[c];
   }
   if (!(wsum > 0.0f)) return;                   // every corner is an obstacle: unchanged
   const float inv_w = 1.0f / wsum;
+  const float th = a.theta;
+  float acc[27];
+  float cacc = 0.0f;
+  if (MODE == 2) {
 #pragma unroll
-  for (int k = 0; k < 27; ++k) acc[k] *= inv_w;
+    for (int c = 0; c < 8; ++c) {
+      cacc = fmaf(w[c] * (1.0f - th), __ldg(clo + s[c]), cacc);
+      cacc = fmaf(w[c] * th, __ldg(a.c_hi + s[c]), cacc);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cacc = fmaf(w[c], __ldg(clo + s[c]), cacc);
+  }
+  // population-outer, corner-inner: the 8 (or 16) loads of each population are independent
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const T* pl = lo + (uint32_t)k * sN;
+    float v = 0.0f;
+    if (MODE == 2) {
+      const T* ph = hi + (uint32_t)k * sN;
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        v = fmaf(w[c], fmaf(th, load_pop(ph + s[c]) - load_pop(pl + s[c]), load_pop(pl + s[c])), v);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v = fmaf(w[c], load_pop(pl + s[c]), v);
+    }
+    acc[k] = v * inv_w;
+  }
   raw_moments(acc);
   const float drho = acc[kap(0, 0, 0)];
   const float inv = 1.0f / (1.0f + drho);
@@ -82,12 +97,19 @@ __global__ void __launch_bounds__(128) k_map(MapArgs a) {
   a.c_dst[m.dst] = cacc * inv_w;
 }
 
+template <typename T>
+static void launch_map_t(const MapArgs& a, int grid, int threads, cudaStream_t s) {
+  if (a.theta <= 0.0f) k_map<T, 0><<<grid, threads, 0, s>>>(a);
+  else if (a.theta >= 1.0f) k_map<T, 1><<<grid, threads, 0, s>>>(a);
+  else k_map<T, 2><<<grid, threads, 0, s>>>(a);
+}
+
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
   const int threads = 128;
   const int grid = (a.n + threads - 1) / threads;
-  if (storage == ST_FP16) k_map<__half><<<grid, threads, 0, s>>>(a);
-  else k_map<float><<<grid, threads, 0, s>>>(a);
+  if (storage == ST_FP16) launch_map_t<__half>(a, grid, threads, s);
+  else launch_map_t<float>(a, grid, threads, s);
   return cudaGetLastError();
 }
 
