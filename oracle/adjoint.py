@@ -1,0 +1,64 @@
+"""FP64 gradients of a smoke-control loss with respect to the initial velocity field.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The paper has no adjoint; this module differentiates the oracle's own forward model
+(``oracle.grid``: equilibrium initialisation, pull, bounce-back, CMR collision with the
+adaptive rates, semi-Lagrangian scalar) in reverse mode with torch's autograd, in float64,
+recomputing each step during the backward sweep (per-step checkpoints) to bound memory.
+It is itself checked against central finite differences of the same forward model.
+
+Loss: L = 1/2 sum_x (c_T(x) - c_target(x))^2 (+ optional 1/2 sum |u_T - u_target|^2).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+from torch.utils.checkpoint import checkpoint
+
+from . import grid
+from .cmr import DT
+
+
+def _step_tensors(f, u, c, flags, p):
+    st = grid.step(grid.State(f, u, c, flags), p)
+    return st.f, st.u, st.c
+
+
+def forward(u0: torch.Tensor, rho0, c0, flags, p: grid.Params, steps: int,
+            use_checkpoint: bool = True):
+    """Runs `steps` steps from the equilibrium of (rho0, u0); returns the final State."""
+    flags_t = torch.as_tensor(np.asarray(flags).astype(np.uint8)) \
+        if not isinstance(flags, torch.Tensor) else flags
+    st = grid.init_state(torch.as_tensor(np.asarray(rho0), dtype=DT), u0,
+                         torch.as_tensor(np.asarray(c0), dtype=DT), flags_t)
+    f, u, c = st.f, st.u, st.c
+    for _ in range(steps):
+        if use_checkpoint and torch.is_grad_enabled():
+            f, u, c = checkpoint(_step_tensors, f, u, c, flags_t, p, use_reentrant=False)
+        else:
+            f, u, c = _step_tensors(f, u, c, flags_t, p)
+    return grid.State(f, u, c, flags_t)
+
+
+def loss_fn(st: grid.State, c_target, u_target=None):
+    L = 0.5 * ((st.c - torch.as_tensor(np.asarray(c_target), dtype=DT)) ** 2).sum()
+    if u_target is not None:
+        L = L + 0.5 * ((st.u - torch.as_tensor(np.asarray(u_target), dtype=DT)) ** 2).sum()
+    return L
+
+
+def loss_and_grad(u0, rho0, c0, flags, p: grid.Params, steps: int, c_target, u_target=None):
+    """(L, dL/du0, c_T) in float64."""
+    u = torch.as_tensor(np.asarray(u0), dtype=DT).clone().requires_grad_(True)
+    st = forward(u, rho0, c0, flags, p, steps)
+    L = loss_fn(st, c_target, u_target)
+    (g,) = torch.autograd.grad(L, u)
+    return float(L.detach()), g.detach(), st.c.detach()
+
+
+def loss_only(u0, rho0, c0, flags, p: grid.Params, steps: int, c_target, u_target=None):
+    with torch.no_grad():
+        u = torch.as_tensor(np.asarray(u0), dtype=DT)
+        st = forward(u, rho0, c0, flags, p, steps, use_checkpoint=False)
+        return float(loss_fn(st, c_target, u_target))

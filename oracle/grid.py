@@ -74,14 +74,16 @@ def neighbour_index(n: int, periodic: bool, offset: int) -> torch.Tensor:
 def init_state(rho0, u0, c0, flags) -> State:
     """f_0 = T m^eq(rho_0, u_0) on every node (Algorithm 1, Sec. 6.1); obstacle voxels get
     the rest state with u = 0."""
-    rho0 = torch.as_tensor(np.asarray(rho0), dtype=DT)
-    u0 = torch.as_tensor(np.asarray(u0), dtype=DT).clone()
-    c0 = torch.as_tensor(np.asarray(c0), dtype=DT).clone()
-    flags = torch.as_tensor(np.asarray(flags).astype(np.uint8))
+    def as_t(a):
+        return a.to(DT) if isinstance(a, torch.Tensor) else torch.as_tensor(np.asarray(a), dtype=DT)
+
+    rho0, u0, c0 = as_t(rho0), as_t(u0), as_t(c0)
+    flags = torch.as_tensor(np.asarray(flags).astype(np.uint8)) \
+        if not isinstance(flags, torch.Tensor) else flags
     solid = (flags & SOLID) != 0
     rho = torch.where(solid, torch.ones_like(rho0), rho0)
-    u0[:, solid] = 0.0
-    c0[solid] = 0.0
+    u0 = torch.where(solid[None], torch.zeros_like(u0), u0)
+    c0 = torch.where(solid, torch.zeros_like(c0), c0)
     f = cmr.equilibrium(rho.reshape(-1), u0.reshape(3, -1).T).T.reshape((27,) + rho.shape)
     return State(f.contiguous(), u0, c0, flags)
 
@@ -128,7 +130,9 @@ def lagged_gradient_norm(u: torch.Tensor, periodic, z, y, x) -> torch.Tensor:
         g2 = g2 + (0.5 * (u[a, z, y, nx[1][x]] - u[a, z, y, nx[-1][x]])) ** 2
         g2 = g2 + (0.5 * (u[a, z, ny[1][y], x] - u[a, z, ny[-1][y], x])) ** 2
         g2 = g2 + (0.5 * (u[a, nz[1][z], y, x] - u[a, nz[-1][z], y, x])) ** 2
-    return torch.sqrt(g2)
+    # the floor only keeps reverse-mode differentiation finite where the gradient is exactly
+    # zero (the value changes by less than 1e-149)
+    return torch.sqrt(torch.clamp(g2, min=1e-300))
 
 
 def _forced_shift(rho, u, F):
@@ -168,22 +172,22 @@ def step_cells(st: State, p: Params, z: torch.Tensor, y: torch.Tensor, x: torch.
     if p.body_force is not None:
         f_post = f_post + _forced_shift(rho, u, p.body_force)
 
-    # 5. node kinds
+    # 5. node kinds (selected with where, so the step stays differentiable)
     is_solid = (fl & SOLID) != 0
     is_in = ((fl & INFLOW) != 0) & ~is_solid
     is_ghost = (fl & GHOST) != 0
     u_own = st.u[:, z, y, x].T
     if bool(is_in.any()):
-        f_in_eq = cmr.equilibrium(torch.ones(int(is_in.sum()), dtype=DT), u_own[is_in])
-        f_post[is_in] = f_in_eq
-        u = u.clone()
-        u[is_in] = u_own[is_in]
+        f_in_eq = cmr.equilibrium(torch.ones(z.shape, dtype=DT), u_own)
+        f_post = torch.where(is_in[:, None], f_in_eq, f_post)
+        u = torch.where(is_in[:, None], u_own, u)
     if bool(is_solid.any()):
-        f_post[is_solid] = cmr.equilibrium(torch.ones(1, dtype=DT), torch.zeros(1, 3, dtype=DT))
-        u[is_solid] = 0.0
+        f_rest = cmr.equilibrium(torch.ones(1, dtype=DT), torch.zeros(1, 3, dtype=DT))
+        f_post = torch.where(is_solid[:, None], f_rest, f_post)
+        u = torch.where(is_solid[:, None], torch.zeros_like(u), u)
     if bool(is_ghost.any()):
-        f_post[is_ghost] = st.f[:, z, y, x].T[is_ghost]
-        u[is_ghost] = u_own[is_ghost]
+        f_post = torch.where(is_ghost[:, None], st.f[:, z, y, x].T, f_post)
+        u = torch.where(is_ghost[:, None], u_own, u)
 
     # 6. passive scalar (departure point at most one node away: |u| < 1 in any stable run)
     dsp = torch.clamp(-u, -1.0, 1.0)
@@ -200,12 +204,14 @@ def step(st: State, p: Params, chunk: int = 1 << 15) -> State:
     Z, Y, X = st.c.shape
     zz, yy, xx = torch.meshgrid(torch.arange(Z), torch.arange(Y), torch.arange(X), indexing="ij")
     zz, yy, xx = zz.reshape(-1), yy.reshape(-1), xx.reshape(-1)
-    f_out = torch.empty((zz.numel(), 27), dtype=DT)
-    u_out = torch.empty((zz.numel(), 3), dtype=DT)
-    c_out = torch.empty((zz.numel(),), dtype=DT)
+    fs, us, cs = [], [], []
     for s in range(0, zz.numel(), chunk):
         e = min(s + chunk, zz.numel())
-        f_out[s:e], u_out[s:e], c_out[s:e] = step_cells(st, p, zz[s:e], yy[s:e], xx[s:e])
+        fo, uo, co = step_cells(st, p, zz[s:e], yy[s:e], xx[s:e])
+        fs.append(fo)
+        us.append(uo)
+        cs.append(co)
+    f_out, u_out, c_out = torch.cat(fs), torch.cat(us), torch.cat(cs)
     return State(f_out.T.reshape(27, Z, Y, X).contiguous(), u_out.T.reshape(3, Z, Y, X).contiguous(),
                  c_out.reshape(Z, Y, X), st.flags)
 
