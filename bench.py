@@ -342,6 +342,8 @@ def run_ours(args):
                 "mass_check": float(red[0])}
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_measure(args.cpu_budget)
+        if ws == 1 and args.workload == "plume256" and not args.no_variants:
+            line["variants"] = _variants(args)
         print(json.dumps(line), flush=True)
     dom.close()
     if ws > 1:
@@ -446,6 +448,100 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args, emit=True):
+    """Smoke control at 128^3 (periodic, nu = 1e-3): forward K steps recording a checkpoint
+    every 20 steps, then the hand-written reverse sweep (recompute + adjoint) back to dL/du0.
+    value = lattice updates of the reverse sweep per second."""
+    import torch
+
+    import synth
+    from paper_1807_02284_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    sc, target = synth.adjoint_scene(n=128, seed=5, nu=1e-3, amp=0.05, steps=args.steps)
+    b = sc.blocks[0]
+    stream = torch.cuda.Stream()
+    dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, stream=stream)
+    dom.set_flags(b.flags)
+    N = b.flags.size
+    K = args.steps
+    u0 = torch.tensor(b.u0.astype(np.float32), device="cuda")
+    rho0 = torch.tensor(b.rho0.astype(np.float32), device="cuda")
+    c0 = torch.tensor(b.c0.astype(np.float32), device="cuda")
+    tgt = torch.tensor(target.astype(np.float32).reshape(-1), device="cuda")
+    g = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+    c = torch.empty(N, dtype=torch.float32, device="cuda")
+
+    def run_once():
+        dom.init_macro(u0, rho=rho0, c=c0)
+        dom.set_tape(20)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dom.step(K)
+        e1.record(stream)
+        dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F32, out=c)
+        with torch.cuda.stream(stream):
+            dldc = (c - tgt).contiguous()
+        e3 = torch.cuda.Event(enable_timing=True)
+        e3.record(stream)
+        dom.adjoint_step(K, dldc, g)
+        e2.record(stream)
+        e2.synchronize()
+        return e0.elapsed_time(e1) / 1e3, e3.elapsed_time(e2) / 1e3
+
+    run_once()                                   # warm-up (allocates tape and buffers)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t_fwd, t_rev = run_once()
+    clk = clocks.stop()
+    dom.sync()
+    peak, peak_src = _peaks()
+    # reverse step per fluid node: pass A 393 B (pulled f, Lam in/out, lagged u, adjoints of
+    # u and c, scalar, mu out), pass B 69 B, recompute 249 B
+    per_node = 393 + 69 + 249
+    achieved = N * K * per_node / t_rev / 1e9
+    out = {"metric": "MLUPS", "value": N * K / t_rev / 1e6, "unit": "MLUPS",
+           "what": "reverse sweep (segment recompute + adjoint) lattice updates per second",
+           "forward_with_tape_mlups": N * K / t_fwd / 1e6, "steps": K,
+           "config": {"workload": "adjoint128_fp32", "nodes": int(N), "checkpoint_every": 20},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                        "bytes_per_reverse_update": per_node},
+           "gradient_norm": float(torch.linalg.norm(g)), "clocks": clk}
+    dom.close()
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
+
+
+def _variants(args):
+    """Measured summaries of the other hot-path variants for the default bench line."""
+    import copy
+    import io
+    from contextlib import redirect_stdout
+
+    res = {}
+    for name, fn, steps, warm in (("plume256_fp16", run_ours, 100, 10),
+                                  ("multiscale3", run_ours, 50, 5),
+                                  ("batch64", run_batch, 100, 10),
+                                  ("adjoint128", run_adjoint, 200, 0)):
+        a = copy.copy(args)
+        a.workload, a.steps, a.warmup, a.no_cpu_baseline = name, steps, warm, True
+        buf = io.StringIO()
+        try:
+            with redirect_stdout(buf):
+                fn(a)
+            d = json.loads(buf.getvalue().strip().splitlines()[-1])
+            res[name] = {k: d[k] for k in ("value", "unit", "ms_per_step", "roofline", "e2e",
+                                           "forward_with_tape_mlups", "config")
+                         if k in d}
+        except Exception as ex:  # report, do not hide
+            res[name] = {"error": f"{type(ex).__name__}: {ex}"}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -453,13 +549,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="plume256",
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
-                             "multiscale3", "batch64"])
+                             "multiscale3", "batch64", "adjoint128"])
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "adjoint128":
+        run_adjoint(args)
     elif args.workload == "batch64":
         run_batch(args)
     else:

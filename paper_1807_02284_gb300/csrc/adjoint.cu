@@ -1,33 +1,450 @@
-// Reverse-mode (adjoint) stepping with checkpointing.
+// Reverse-mode (adjoint) stepping with checkpointing: gradients of a loss of the final scalar
+// (and velocity) field with respect to the initial velocity field.  Not in the paper.
+//
+// Forward step n -> n+1 at a fluid node x:
+//   d_in = pull(D^n);  (rho, u) = moments(d_in);  phi = phi(|grad U^n|(x));
+//   D^{n+1}(x) = collide(d_in, u, phi);  U^{n+1}(x) = u;  C^{n+1}(x) = trilinear(C^n, x - u).
+// Reverse step, given the adjoints (Lam, Ups, Gam) of (D^{n+1}, U^{n+1}, C^{n+1}):
+//   pass A (per fluid node x): recompute the forward at x, then the exact transpose of every
+//     stage; the population adjoints go to the pull sources (the pull, with bounce-back, reads
+//     every fluid slot exactly once, so these stores never collide), and the adjoint of the
+//     adaptive factor becomes 9 per-node terms mu_ab = dL/d(U_a(x+e_b) - U_a(x-e_b));
+//   pass B (per node y): Ups^n_a(y) = sum_b mu_ab(y - e_b) - mu_ab(y + e_b) and
+//     Gam^n(y) = sum over the nodes x whose departure cell touches y of w_{x->y} Gam^{n+1}(x)
+//     (a gather over the 27 neighbours: deterministic, no atomics).
+// Initial state: D^0 = f^eq(rho_0, u_0) - w and U^0 = u_0, so
+//   dL/du_0 = Ups^0 + (dD^0/du_0)^T Lam^0.
+// Scope: one periodic block with >= 3 nodes per axis, FP32 storage, no inflow nodes.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "lbm_adjoint.cuh"
+#include "lbm_cell.cuh"
 #include "runtime.h"
+
+namespace lbm {
+
+struct AdjArgs {
+  BlockView fwd;        // D^n, U^n, C^n in (d_out, u_out, c_out unused)
+  const float* lam_in;  // Lam^{n+1}: 27 planes (cube order)
+  const float* ups_in;  // Ups^{n+1}: 3 planes
+  const float* gam_in;  // Gam^{n+1}
+  const float* u_next;  // U^{n+1}: 3 planes (scalar gather)
+  float* lam_out;       // Lam^n
+  float* ups_out;       // Ups^n
+  float* gam_out;       // Gam^n
+  float* mu;            // 9 planes: adjoint of the velocity differences of the gradient norm
+};
+
+template <int K = 0>
+__device__ __forceinline__ void push_all(const float (&A)[27], float* __restrict__ lam,
+                                         uint32_t N, const Nbr<uint32_t>& n, uint32_t idx,
+                                         const uint8_t* __restrict__ flags, bool near) {
+  if constexpr (K < 27) {
+    const uint32_t src = pull_src<K>(n);
+    uint32_t slot = (uint32_t)K * N + src;
+    if (K != 13 && near && (__ldg(flags + src) & F_SOLID)) slot = (uint32_t)(26 - K) * N + idx;
+    lam[slot] = A[K];
+    push_all<K + 1>(A, lam, N, n, idx, flags, near);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_adj_a(AdjArgs a) {
+  const BlockView& v = a.fwd;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int z = blockIdx.z;
+  if (x >= v.nx) return;
+  const uint32_t N = (uint32_t)v.N;
+  const Nbr<uint32_t> n = neighbours<uint32_t>(v, x, y, z);
+  const uint32_t idx = n.p0 + n.r0 + n.x0;
+  const uint8_t fl = v.flags[idx];
+  if (fl & F_SOLID) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = 0.0f;
+    return;
+  }
+  const float* __restrict__ din = static_cast<const float*>(v.d_in);
+
+  // ---- forward recompute up to the central moments
+  float K[27];
+  pull_all<float, uint32_t>(K, din, N, n);
+  const bool near = (fl & F_NEAR_SOLID) != 0;
+  if (near) bounce_back<float, uint32_t>(K, din, N, v.flags, n, idx);
+  raw_moments(K);
+  const float drho = K[kap(0, 0, 0)];
+  const float inv = __frcp_rn(1.0f + drho);
+  const float ux = K[kap(1, 0, 0)] * inv, uy = K[kap(0, 1, 0)] * inv, uz = K[kap(0, 0, 1)] * inv;
+  float diff[9];
+  float g = 0.0f;
+  if (v.rp.adaptive) {
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float* Uc = v.u_in + (uint32_t)c * N;
+      diff[3 * c + 0] = __ldg(Uc + (n.p0 + n.r0 + n.xp)) - __ldg(Uc + (n.p0 + n.r0 + n.xm));
+      diff[3 * c + 1] = __ldg(Uc + (n.p0 + n.rp + n.x0)) - __ldg(Uc + (n.p0 + n.rm + n.x0));
+      diff[3 * c + 2] = __ldg(Uc + (n.pp + n.r0 + n.x0)) - __ldg(Uc + (n.pm + n.r0 + n.x0));
+      s = fmaf(diff[3 * c + 0], diff[3 * c + 0],
+               fmaf(diff[3 * c + 1], diff[3 * c + 1], fmaf(diff[3 * c + 2], diff[3 * c + 2], s)));
+    }
+    g = 0.5f * sqrtf(s);
+  }
+  const Keep kf = keep_factors(v.rp, g);
+  shift_axis<1>(K, ux);
+  shift_axis<3>(K, uy);
+  shift_axis<9>(K, uz);                  // K = central moments before relaxation
+
+  // ---- adjoint of the stored velocity and of the scalar step
+  float ub[3];
+  ub[0] = a.ups_in[idx];
+  ub[1] = a.ups_in[N + idx];
+  ub[2] = a.ups_in[2 * N + idx];
+  if (!(fl & F_SCALAR_SRC)) {
+    const float gam = a.gam_in[idx];
+    if (gam != 0.0f) {
+      const ScalarCell sc = scalar_corners<uint32_t>(v, x, y, z, ux, uy, uz);
+      const float tx = sc.tx, ty = sc.ty, tz = sc.tz;
+      // derivative of the trilinear interpolant along each fraction; the fraction grows
+      // with the departure displacement -u (derivative 0 where the displacement is clamped)
+      const float dtx = (1 - ty) * (1 - tz) * (sc.c[1] - sc.c[0]) + ty * (1 - tz) * (sc.c[3] - sc.c[2]) +
+                        (1 - ty) * tz * (sc.c[5] - sc.c[4]) + ty * tz * (sc.c[7] - sc.c[6]);
+      const float dty = (1 - tx) * (1 - tz) * (sc.c[2] - sc.c[0]) + tx * (1 - tz) * (sc.c[3] - sc.c[1]) +
+                        (1 - tx) * tz * (sc.c[6] - sc.c[4]) + tx * tz * (sc.c[7] - sc.c[5]);
+      const float dtz = (1 - tx) * (1 - ty) * (sc.c[4] - sc.c[0]) + tx * (1 - ty) * (sc.c[5] - sc.c[1]) +
+                        (1 - tx) * ty * (sc.c[6] - sc.c[2]) + tx * ty * (sc.c[7] - sc.c[3]);
+      if (fabsf(ux) < 1.0f) ub[0] -= gam * dtx;
+      if (fabsf(uy) < 1.0f) ub[1] -= gam * dty;
+      if (fabsf(uz) < 1.0f) ub[2] -= gam * dtz;
+    }
+  }
+
+  // ---- adjoint of the collision
+  float A[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) A[k] = a.lam_in[(uint32_t)k * N + idx];
+  float T[27];
+  // the inverse sweeps ran z, y, x: undo x first; its input is inv_y(inv_z(relaxed))
+#pragma unroll
+  for (int k = 0; k < 27; ++k) T[k] = K[k];
+  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
+  inv_axis<9>(T, uz);
+  inv_axis<3>(T, uy);
+  inv_axis_vjp<1>(T, A, ux, ub[0]);
+#pragma unroll
+  for (int k = 0; k < 27; ++k) T[k] = K[k];
+  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
+  inv_axis<9>(T, uz);
+  inv_axis_vjp<3>(T, A, uy, ub[1]);
+#pragma unroll
+  for (int k = 0; k < 27; ++k) T[k] = K[k];
+  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
+  inv_axis_vjp<9>(T, A, uz, ub[2]);
+  float bar[4] = {0.f, 0.f, 0.f, 0.f};     // d/d(rho - 1), d/du
+  float kbar[4] = {0.f, 0.f, 0.f, 0.f};    // d/d(keep factor) of the high-order groups
+  relax_vjp(K, A, drho, ux, uy, uz, kf, bar, kbar);
+  ub[0] += bar[1];
+  ub[1] += bar[2];
+  ub[2] += bar[3];
+  float drhob = bar[0];
+  // the shifts ran x, y, z: undo z first; its input is unshift_z(K)
+  unshift_axis<9>(K, uz);
+  shift_axis_vjp<9>(K, A, uz, ub[2]);
+  unshift_axis<3>(K, uy);
+  shift_axis_vjp<3>(K, A, uy, ub[1]);
+  unshift_axis<1>(K, ux);
+  shift_axis_vjp<1>(K, A, ux, ub[0]);
+  // u = j / rho with rho = 1 + r_000, j = (r_100, r_010, r_001)
+  drhob -= (ub[0] * ux + ub[1] * uy + ub[2] * uz) * inv;
+  A[kap(0, 0, 0)] += drhob;
+  A[kap(1, 0, 0)] += ub[0] * inv;
+  A[kap(0, 1, 0)] += ub[1] * inv;
+  A[kap(0, 0, 1)] += ub[2] * inv;
+  raw_axis_vjp<9>(A);
+  raw_axis_vjp<3>(A);
+  raw_axis_vjp<1>(A);                    // A = adjoint of the pulled populations
+  push_all(A, a.lam_out, N, n, idx, v.flags, near);
+
+  // ---- adjoint of the adaptive factor: K_g = 1 - 1/(phi nu3_g + 1/2)
+  float mu_scale = 0.0f;
+  if (v.rp.adaptive && g > 0.0f && g * v.rp.inv_gmax < 1.0f) {
+    float phib = 0.0f;
+#pragma unroll
+    for (int gi = 0; gi < 4; ++gi) {
+      const float S = 1.0f - kf.g[gi];
+      phib = fmaf(kbar[gi], v.rp.nuh3[gi] * S * S, phib);
+    }
+    const float gb = phib * v.rp.a * v.rp.inv_gmax;   // phi = a g / g_max + b below the clamp
+    mu_scale = gb * 0.25f / g;                        // dg/d(diff) = diff / (4 g)
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = v.rp.adaptive ? mu_scale * diff[i] : 0.0f;
+}
+
+__global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
+  const BlockView& v = a.fwd;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  const int z = blockIdx.z;
+  if (x >= v.nx) return;
+  const uint32_t N = (uint32_t)v.N;
+  const Nbr<uint32_t> n = neighbours<uint32_t>(v, x, y, z);
+  const uint32_t idx = n.p0 + n.r0 + n.x0;
+  // lagged-velocity adjoint
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* m0 = a.mu + (uint32_t)(3 * c + 0) * N;
+    const float* m1 = a.mu + (uint32_t)(3 * c + 1) * N;
+    const float* m2 = a.mu + (uint32_t)(3 * c + 2) * N;
+    const float s = __ldg(m0 + (n.p0 + n.r0 + n.xm)) - __ldg(m0 + (n.p0 + n.r0 + n.xp)) +
+                    __ldg(m1 + (n.p0 + n.rm + n.x0)) - __ldg(m1 + (n.p0 + n.rp + n.x0)) +
+                    __ldg(m2 + (n.pm + n.r0 + n.x0)) - __ldg(m2 + (n.pp + n.r0 + n.x0));
+    a.ups_out[(uint32_t)c * N + idx] = s;
+  }
+  // scalar adjoint: gather from the neighbours whose departure cell contains this node
+  const uint32_t xs[3] = {n.xm, n.x0, n.xp};
+  const uint32_t rs[3] = {n.rm, n.r0, n.rp};
+  const uint32_t ps[3] = {n.pm, n.p0, n.pp};
+  const int cx[3] = {(int)n.xm, x, (int)n.xp};
+  const int cy[3] = {(int)(n.rm / (uint32_t)v.nx), y, (int)(n.rp / (uint32_t)v.nx)};
+  const int cz[3] = {(int)(n.pm / ((uint32_t)v.nx * v.ny)), z, (int)(n.pp / ((uint32_t)v.nx * v.ny))};
+  float gam = 0.0f;
+#pragma unroll 1
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll 1
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const uint32_t j = ps[dz] + rs[dy] + xs[dx];
+        if (__ldg(v.flags + j) & (F_SOLID | F_SCALAR_SRC)) continue;
+        const float G = __ldg(a.gam_in + j);
+        if (G == 0.0f) continue;
+        const Axis1 ax = sl_axis(cx[dx], __ldg(a.u_next + j), v.nx, v.per[0]);
+        const Axis1 ay = sl_axis(cy[dy], __ldg(a.u_next + N + j), v.ny, v.per[1]);
+        const Axis1 az = sl_axis(cz[dz], __ldg(a.u_next + 2 * N + j), v.nz, v.per[2]);
+        const float wx = (ax.i0 == x ? 1.0f - ax.t : 0.0f) + (ax.i1 == x ? ax.t : 0.0f);
+        const float wy = (ay.i0 == y ? 1.0f - ay.t : 0.0f) + (ay.i1 == y ? ay.t : 0.0f);
+        const float wz = (az.i0 == z ? 1.0f - az.t : 0.0f) + (az.i1 == z ? az.t : 0.0f);
+        gam = fmaf(wx * wy * wz, G, gam);
+      }
+  a.gam_out[idx] = gam;
+}
+
+// dL/du_0 = Ups^0 + (dD^0/du_0)^T Lam^0 with D^0_k = w_k (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)).
+__global__ void k_adj_init(const float* __restrict__ d0, const float* __restrict__ u0,
+                           const uint8_t* __restrict__ flags, const float* __restrict__ lam,
+                           const float* __restrict__ ups, float* __restrict__ out, uint32_t N) {
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+    if (flags[idx] & F_SOLID) {
+      out[idx] = out[N + idx] = out[2 * N + idx] = 0.0f;
+      continue;
+    }
+    float drho = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) drho += d0[(uint32_t)k * N + idx];
+    const float rho = 1.0f + drho;
+    const float u[3] = {u0[idx], u0[N + idx], u0[2 * N + idx]};
+    float gsum[3] = {ups[idx], ups[N + idx], ups[2 * N + idx]};
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+      const float c[3] = {(float)cxk(k), (float)cyk(k), (float)czk(k)};
+      const float cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+      const float l = lam[(uint32_t)k * N + idx] * wk(k) * rho;
+#pragma unroll
+      for (int a2 = 0; a2 < 3; ++a2) gsum[a2] = fmaf(l, 3.0f * c[a2] + 9.0f * cu * c[a2] - 3.0f * u[a2], gsum[a2]);
+    }
+    out[idx] = gsum[0];
+    out[N + idx] = gsum[1];
+    out[2 * N + idx] = gsum[2];
+  }
+}
+
+struct TapeState {
+  int every = 0;
+  std::vector<Level> ckpt;    // states at steps 0, every, 2 every, ...
+  std::vector<Level> seg;     // recompute levels 1..every of one segment
+  float* lam[2] = {nullptr, nullptr};
+  float* ups[2] = {nullptr, nullptr};
+  float* gam[2] = {nullptr, nullptr};
+  float* mu = nullptr;
+};
+
+}  // namespace lbm
 
 using namespace lbm;
 
-namespace lbm {
-struct TapeState {
-  int every = 0;
-};
-}  // namespace lbm
+static void free_level(lbm_domain* dom, Level& L) {
+  dom->dev_free(L.f);
+  dom->dev_free(L.u);
+  dom->dev_free(L.c);
+  L = Level();
+}
 
 void release_tape(lbm_domain* dom) {
-  delete dom->tape;
+  TapeState* t = dom->tape;
+  if (!t) return;
+  for (Level& L : t->ckpt) free_level(dom, L);
+  for (Level& L : t->seg) free_level(dom, L);
+  for (int i = 0; i < 2; ++i) {
+    dom->dev_free(t->lam[i]);
+    dom->dev_free(t->ups[i]);
+    dom->dev_free(t->gam[i]);
+  }
+  dom->dev_free(t->mu);
+  delete t;
   dom->tape = nullptr;
 }
 
+static bool alloc_level(lbm_domain* dom, size_t N, Level& L) {
+  L.f = dom->dev_alloc(N * 27 * sizeof(float));
+  L.u = static_cast<float*>(dom->dev_alloc(N * 3 * sizeof(float)));
+  L.c = static_cast<float*>(dom->dev_alloc(N * sizeof(float)));
+  return L.f && L.u && L.c;
+}
+
+static BlockView view_of(lbm_domain* dom, const Level& from, const Level& to) {
+  BlockView v = dom->view(0, 0, 0);
+  v.d_in = from.f;
+  v.u_in = from.u;
+  v.c_in = from.c;
+  v.d_out = to.f;
+  v.u_out = to.u;
+  v.c_out = to.c;
+  return v;
+}
+
+// Records a checkpoint of the current state every `every` steps since the last init.
 lbm_status tape_before_step(lbm_domain* dom) {
-  (void)dom;
+  TapeState* t = dom->tape;
+  if (!t) return LBM_OK;
+  if (dom->steps % t->every != 0) return LBM_OK;
+  const size_t i = (size_t)(dom->steps / t->every);
+  Block& B = dom->blocks[0];
+  while (t->ckpt.size() <= i) {
+    Level L;
+    if (!alloc_level(dom, B.N, L)) return dom->fail(LBM_ERR_OOM, "checkpoint allocation failed");
+    t->ckpt.push_back(L);
+  }
+  const Level& S = B.lv[B.cur];
+  Level& D = t->ckpt[i];
+  cudaError_t e = cudaMemcpyAsync(D.f, S.f, B.N * 27 * sizeof(float), cudaMemcpyDeviceToDevice, dom->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D.u, S.u, B.N * 3 * sizeof(float), cudaMemcpyDeviceToDevice, dom->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D.c, S.c, B.N * sizeof(float), cudaMemcpyDeviceToDevice, dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "checkpoint copy");
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every) {
+static lbm_status adjoint_supported(lbm_domain* dom) {
+  if (dom->blocks.size() != 1) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint covers single-block domains");
+  if (dom->desc.storage != LBM_FP32) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP32 storage");
+  const Block& B = dom->blocks[0];
+  for (int a = 0; a < 3; ++a)
+    if (!dom->desc.periodic[a]) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs periodic faces");
+  if (B.nx < 3 || B.ny < 3 || B.nz < 3) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs >= 3 nodes per axis");
+  if (27ull * B.N >= 0xFFFFFFFFull) return dom->fail(LBM_ERR_UNSUPPORTED, "block too large for the adjoint");
+  std::vector<uint8_t> fl(B.N);
+  cudaError_t e = cudaMemcpyAsync(fl.data(), B.flags, B.N, cudaMemcpyDeviceToHost, dom->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "flag read-back");
+  for (uint8_t f : fl)
+    if ((f & F_INFLOW) && !(f & F_SOLID)) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint does not cover inflow nodes");
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_tape(lbm_domain* dom, int32_t every) {
   if (!dom) return LBM_ERR_INVALID_ARG;
-  (void)checkpoint_every;
-  return dom->fail(LBM_ERR_UNSUPPORTED, "adjoint not built yet");
+  cudaSetDevice(dom->desc.device);
+  if (every < 0) return dom->fail(LBM_ERR_INVALID_ARG, "checkpoint_every must be >= 0");
+  release_tape(dom);
+  if (every == 0) return LBM_OK;
+  if (dom->steps != 0)
+    return dom->fail(LBM_ERR_STATE, "the tape must be enabled right after lbm_init_macro");
+  lbm_status st = adjoint_supported(dom);
+  if (st != LBM_OK) return st;
+  dom->tape = new TapeState();
+  dom->tape->every = every;
+  dom->invalidate_graphs();
+  return LBM_OK;
 }
 
 extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dc,
                                        const float* dL_du, float* dL_du0, float* dL_dinflow) {
   if (!dom) return LBM_ERR_INVALID_ARG;
-  (void)n_steps; (void)dL_dc; (void)dL_du; (void)dL_du0; (void)dL_dinflow;
-  return dom->fail(LBM_ERR_UNSUPPORTED, "adjoint not built yet");
+  cudaSetDevice(dom->desc.device);
+  if (dL_dinflow) return dom->fail(LBM_ERR_UNSUPPORTED, "gradients with respect to inflow are not built");
+  TapeState* t = dom->tape;
+  if (!t) return dom->fail(LBM_ERR_STATE, "no tape: call lbm_set_tape after lbm_init_macro");
+  if (n_steps < 0 || n_steps != dom->steps)
+    return dom->fail(LBM_ERR_INVALID_ARG, "n_steps must equal the steps recorded since lbm_init_macro");
+  if (!dL_dc || !dL_du0) return dom->fail(LBM_ERR_INVALID_ARG, "dL_dscalar_final and dL_du0 are required");
+  Block& B = dom->blocks[0];
+  const size_t N = B.N;
+  cudaStream_t s = dom->stream;
+  // buffers
+  for (int i = 0; i < 2; ++i) {
+    if (!t->lam[i]) t->lam[i] = static_cast<float*>(dom->dev_alloc(N * 27 * sizeof(float)));
+    if (!t->ups[i]) t->ups[i] = static_cast<float*>(dom->dev_alloc(N * 3 * sizeof(float)));
+    if (!t->gam[i]) t->gam[i] = static_cast<float*>(dom->dev_alloc(N * sizeof(float)));
+    if (!t->lam[i] || !t->ups[i] || !t->gam[i]) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+  }
+  if (!t->mu) t->mu = static_cast<float*>(dom->dev_alloc(N * 9 * sizeof(float)));
+  if (!t->mu) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+  const int seg_len = std::min(t->every, std::max(1, n_steps));
+  while ((int)t->seg.size() < seg_len) {
+    Level L;
+    if (!alloc_level(dom, N, L)) return dom->fail(LBM_ERR_OOM, "recompute levels");
+    t->seg.push_back(L);
+  }
+  if (t->ckpt.empty()) {  // no step was taken: the checkpoint of step 0 is the current state
+    lbm_status st = tape_before_step(dom);
+    if (st != LBM_OK) return st;
+  }
+  int c = 0;
+  cudaError_t e = cudaMemsetAsync(t->lam[0], 0, N * 27 * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->lam[1], 0, N * 27 * sizeof(float), s);
+  if (e == cudaSuccess) {
+    if (dL_du) e = cudaMemcpyAsync(t->ups[0], dL_du, N * 3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    else e = cudaMemsetAsync(t->ups[0], 0, N * 3 * sizeof(float), s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t->gam[0], dL_dc, N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint initialisation");
+
+  const int n_seg = (n_steps + t->every - 1) / t->every;
+  const dim3 blk(128, 1, 1);
+  const dim3 grd((B.nx + 127) / 128, B.ny, B.nz);
+  for (int sg = n_seg - 1; sg >= 0; --sg) {
+    const int s0 = sg * t->every;
+    const int len = std::min(t->every, n_steps - s0);
+    // recompute the segment's states 1..len from its checkpoint
+    auto level = [&](int i) -> const Level& { return i == 0 ? t->ckpt[sg] : t->seg[i - 1]; };
+    for (int i = 0; i < len; ++i) {
+      e = launch_step(view_of(dom, level(i), level(i + 1)), ST_FP32, B.bx, B.by, s);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint recompute");
+    }
+    for (int i = len - 1; i >= 0; --i) {
+      AdjArgs a;
+      a.fwd = view_of(dom, level(i), level(i));
+      a.lam_in = t->lam[c];
+      a.ups_in = t->ups[c];
+      a.gam_in = t->gam[c];
+      a.u_next = level(i + 1).u;
+      a.lam_out = t->lam[c ^ 1];
+      a.ups_out = t->ups[c ^ 1];
+      a.gam_out = t->gam[c ^ 1];
+      a.mu = t->mu;
+      k_adj_a<<<grd, blk, 0, s>>>(a);
+      k_adj_b<<<grd, blk, 0, s>>>(a);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint step");
+      c ^= 1;
+    }
+  }
+  const int g = (int)std::min<size_t>((N + 255) / 256, 16384);
+  k_adj_init<<<g, 256, 0, s>>>(static_cast<const float*>(t->ckpt[0].f), t->ckpt[0].u, B.flags,
+                               t->lam[c], t->ups[c], dL_du0, (uint32_t)N);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return dom->cuda_fail(e, "initial-state adjoint");
+  dom->post_error_probe();
+  return LBM_OK;
 }

@@ -1,0 +1,182 @@
+"""Hand-written GPU adjoint of collide-stream + scalar advection (with checkpointing) against
+the FP64 adjoint oracle and against finite differences.
+
+Tolerance: the FP32 adjoint's gradient must match the FP64 gradient to 1e-3 in relative L2
+norm (FP32 rounding of forward and reverse accumulates over the horizon; 1e-3 leaves an
+order of magnitude of margin on the short horizons here)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import adjoint as oadj
+from oracle import grid
+from tests.helpers import f32
+
+pytestmark = pytest.mark.gpu
+
+
+def _domain(sc):
+    from paper_1807_02284_gb300 import lbm
+    b = sc.blocks[0]
+    dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, adaptive=sc.adaptive)
+    dom.set_flags(b.flags)
+    return dom
+
+
+def gpu_grad(sc, target, steps, every):
+    """(L, dL/du0, c_T) from the GPU forward + hand-written adjoint."""
+    from paper_1807_02284_gb300 import lbm
+    b = sc.blocks[0]
+    dom = _domain(sc)
+    dom.init_macro(f32(b.u0), rho=f32(b.rho0), c=f32(b.c0))
+    dom.set_tape(every)
+    dom.step(steps)
+    c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64)
+    resid = c - target.reshape(-1)
+    L = 0.5 * float((resid ** 2).sum())
+    dLdc = torch.tensor(resid, dtype=torch.float32, device="cuda")
+    g = torch.empty(3 * b.flags.size, dtype=torch.float32, device="cuda")
+    dom.adjoint_step(steps, dLdc, g)
+    dom.sync()
+    dom.close()
+    return L, g.cpu().numpy().astype(np.float64).reshape(b.u0.shape), c
+
+
+def oracle_grad(sc, target, steps):
+    b = sc.blocks[0]
+    p = grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=sc.adaptive)
+    return oadj.loss_and_grad(f32(b.u0).astype(np.float64), f32(b.rho0).astype(np.float64),
+                              f32(b.c0).astype(np.float64), b.flags, p, steps, target)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,steps,every,sphere", [(12, 8, 3, False), (16, 20, 5, False),
+                                                  (14, 12, 4, True)])
+def test_adjoint_matches_fp64_oracle(lib, n, steps, every, sphere):
+    sc, target = synth.adjoint_scene(n=n, seed=5, nu=0.01, amp=0.05)
+    if sphere:
+        synth.voxelise_spheres(sc.blocks[0], [(n / 2 + 1.5, n / 2, n / 2 - 1, 2.5)])
+    Lg, gg, cg = gpu_grad(sc, target, steps, every)
+    Lo, go, co = oracle_grad(sc, target, steps)
+    e = rel(gg, go.numpy())
+    print(f"adjoint n={n} steps={steps} k={every} sphere={sphere}: L gpu {Lg:.6e} oracle {Lo:.6e}, "
+          f"rel L2 grad err {e:.2e}")
+    assert abs(Lg - Lo) <= 1e-4 * abs(Lo)
+    assert e <= 1e-3
+
+
+def test_adjoint_config5_copy_32_cubed_200_steps(lib):
+    """The smoke-control problem scaled to 32^3 (every length / 4), nu = 1e-3, 200 steps,
+    checkpoint every 20: FP32 GPU adjoint against the FP64 oracle gradient."""
+    sc, target = synth.adjoint_scene(n=32, seed=5, nu=1e-3, amp=0.05, steps=200)
+    Lg, gg, _ = gpu_grad(sc, target, 200, 20)
+    Lo, go, _ = oracle_grad(sc, target, 200)
+    e = rel(gg, go.numpy())
+    print(f"config-5 copy 32^3 x 200: L gpu {Lg:.6e} oracle {Lo:.6e}, rel L2 grad err {e:.2e}")
+    assert abs(Lg - Lo) <= 1e-4 * abs(Lo)
+    assert e <= 1e-3
+
+
+def test_adjoint_full_size_finite_difference_along_gradient(lib):
+    """128^3 smoke control, 200 steps, checkpoint every 20: the GPU forward's central
+    difference along the normalised gradient equals the gradient norm."""
+    from paper_1807_02284_gb300 import lbm
+    sc, target = synth.adjoint_scene(n=128, seed=5, nu=1e-3, amp=0.05, steps=200)
+    b = sc.blocks[0]
+    steps = 200
+    L0, g, _ = gpu_grad(sc, target, steps, 20)
+    gn = float(np.linalg.norm(g))
+    vhat = g / gn
+
+    def loss(u):
+        dom = _domain(sc)
+        dom.init_macro(f32(u), rho=f32(b.rho0), c=f32(b.c0))
+        dom.step(steps)
+        c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64)
+        dom.close()
+        return 0.5 * float(((c - target.reshape(-1)) ** 2).sum())
+
+    eps = 2e-3
+    fd = (loss(b.u0 + eps * vhat) - loss(b.u0 - eps * vhat)) / (2 * eps)
+    print(f"128^3 x 200: |dL/du0| = {gn:.6e}, central FD along it = {fd:.6e}")
+    assert abs(fd - gn) <= 1e-2 * gn
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(lib):
+    sc, target = synth.adjoint_scene(n=12, seed=6, nu=0.01, amp=0.05)
+    _, g1, _ = gpu_grad(sc, target, 9, 1)
+    _, g4, _ = gpu_grad(sc, target, 9, 4)
+    _, g9, _ = gpu_grad(sc, target, 9, 9)
+    assert np.array_equal(g1, g4) and np.array_equal(g1, g9)
+
+
+def test_adjoint_directional_derivative_matches_central_differences(lib):
+    """dL/du0 . v against (L(u0 + e v) - L(u0 - e v)) / 2e of the FP64 forward model."""
+    sc, target = synth.adjoint_scene(n=12, seed=9, nu=0.01, amp=0.05)
+    b = sc.blocks[0]
+    steps = 10
+    _, g, _ = gpu_grad(sc, target, steps, 5)
+    p = grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=sc.adaptive)
+    rng = np.random.default_rng(3)
+    u0 = f32(b.u0).astype(np.float64)
+    rho0 = f32(b.rho0).astype(np.float64)
+    c0 = f32(b.c0).astype(np.float64)
+    for _ in range(2):
+        v = rng.standard_normal(b.u0.shape)
+        eps = 1e-5
+        lp = oadj.loss_only(u0 + eps * v, rho0, c0, b.flags, p, steps, target)
+        lm = oadj.loss_only(u0 - eps * v, rho0, c0, b.flags, p, steps, target)
+        fd = (lp - lm) / (2 * eps)
+        ad = float((g * v).sum())
+        print(f"directional derivative: adjoint {ad:.6e}, central FD {fd:.6e}")
+        assert abs(ad - fd) <= 2e-3 * abs(fd)
+
+
+def test_autograd_function_returns_the_adjoint(lib):
+    from paper_1807_02284_gb300 import lbm
+    from paper_1807_02284_gb300.autograd import smoke_rollout
+    sc, target = synth.adjoint_scene(n=12, seed=10, nu=0.01, amp=0.05)
+    b = sc.blocks[0]
+    dom = _domain(sc)
+    u0 = torch.tensor(f32(b.u0), device="cuda", requires_grad=True)
+    rho0 = torch.tensor(f32(b.rho0), device="cuda")
+    c0 = torch.tensor(f32(b.c0), device="cuda")
+    tgt = torch.tensor(f32(target).reshape(-1), device="cuda")
+    c = smoke_rollout(u0, dom, 8, 4, rho0, c0)
+    loss = 0.5 * ((c - tgt) ** 2).sum()
+    loss.backward()
+    _, g_ref, _ = gpu_grad(sc, target, 8, 4)
+    # dL/dc is formed in float32 here and rounded from float64 in gpu_grad
+    assert rel(u0.grad.cpu().numpy().astype(np.float64), g_ref) <= 1e-5
+    dom.close()
+
+
+def test_adjoint_argument_checks(lib):
+    from paper_1807_02284_gb300 import lbm
+    sc = synth.random_scene(dims=(10, 10, 10), seed=3, periodic=(False, True, True))
+    d = _domain(sc)
+    b = sc.blocks[0]
+    d.init_macro(f32(b.u0))
+    with pytest.raises(lbm.LBMError) as ei:
+        d.set_tape(2)
+    assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
+    d.close()
+    sc, target = synth.adjoint_scene(n=8, seed=1)
+    d = _domain(sc)
+    b = sc.blocks[0]
+    d.init_macro(f32(b.u0))
+    g = torch.empty(3 * b.flags.size, device="cuda")
+    dc = torch.zeros(b.flags.size, device="cuda")
+    with pytest.raises(lbm.LBMError) as ei:
+        d.adjoint_step(0, dc, g)
+    assert ei.value.status == lbm.LBM_ERR_STATE
+    d.set_tape(2)
+    d.step(3)
+    with pytest.raises(lbm.LBMError) as ei:
+        d.adjoint_step(2, dc, g)
+    assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
+    d.close()
