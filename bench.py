@@ -458,7 +458,8 @@ def run_adjoint(args, emit=True):
     from paper_1807_02284_gb300 import lbm
 
     torch.cuda.set_device(0)
-    sc, target = synth.adjoint_scene(n=128, seed=5, nu=1e-3, amp=0.05, steps=args.steps)
+    n_edge = 64 if args.workload == "adjoint64" else 128
+    sc, target = synth.adjoint_scene(n=n_edge, seed=5, nu=1e-3, amp=0.05, steps=args.steps)
     b = sc.blocks[0]
     stream = torch.cuda.Stream()
     dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, stream=stream)
@@ -505,7 +506,7 @@ def run_adjoint(args, emit=True):
     out = {"metric": "MLUPS", "value": N * K / t_rev / 1e6, "unit": "MLUPS",
            "what": "reverse sweep (segment recompute + adjoint) lattice updates per second",
            "forward_with_tape_mlups": N * K / t_fwd / 1e6, "steps": K,
-           "config": {"workload": "adjoint128_fp32", "nodes": int(N), "checkpoint_every": 20},
+           "config": {"workload": f"adjoint{n_edge}_fp32", "nodes": int(N), "checkpoint_every": 20},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                         "bytes_per_reverse_update": per_node},
@@ -549,7 +550,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="plume256",
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
-                             "multiscale3", "batch64", "adjoint128"])
+                             "multiscale3", "batch64", "adjoint128", "adjoint64"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -558,7 +559,7 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "adjoint128":
+    elif args.workload in ("adjoint128", "adjoint64"):
         run_adjoint(args)
     elif args.workload == "batch64":
         run_batch(args)
