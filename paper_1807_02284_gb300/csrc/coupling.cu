@@ -113,44 +113,6 @@ cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Quadratic Lagrange interpolation in time of a refined block's interior (Sec. 4.2.4).
-template <typename T>
-__global__ void k_align(AlignArgs a) {
-  const size_t N = a.N;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    if (a.flags[idx] & (F_GHOST | F_SOLID)) continue;
-    const T* f0 = static_cast<const T*>(a.f0);
-    const T* f1 = static_cast<const T*>(a.f1);
-    const T* f2 = static_cast<const T*>(a.f2);
-    T* out = static_cast<T*>(a.f_out);
-    float d[27];
-#pragma unroll
-    for (int k = 0; k < 27; ++k) {
-      const size_t i = (size_t)k * N + idx;
-      d[k] = fmaf(a.L0, load_pop(f0 + i), fmaf(a.L1, load_pop(f1 + i), a.L2 * load_pop(f2 + i)));
-    }
-    const float c = fmaf(a.L0, a.c0[idx], fmaf(a.L1, a.c1[idx], a.L2 * a.c2[idx]));
-    float drho, jx, jy, jz;
-    macros(d, drho, jx, jy, jz);
-    const float inv = 1.0f / (1.0f + drho);
-#pragma unroll
-    for (int k = 0; k < 27; ++k) store_pop(out + (size_t)k * N + idx, d[k]);
-    a.u_out[idx] = jx * inv;
-    a.u_out[N + idx] = jy * inv;
-    a.u_out[2 * N + idx] = jz * inv;
-    a.c_out[idx] = c;
-  }
-}
-
-cudaError_t launch_align(const AlignArgs& a, int storage, cudaStream_t s) {
-  const size_t g = (a.N + 255) / 256;
-  const int grid = (int)(g < 16384 ? g : 16384);
-  if (storage == ST_FP16) k_align<__half><<<grid, 256, 0, s>>>(a);
-  else k_align<float><<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
 __global__ void k_set_ghost_layer(uint8_t* flags, int nx, int ny, int nz) {
   const size_t N = (size_t)nx * ny * nz;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
@@ -354,7 +316,7 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
 
 // Prior-mapping of block b's ghost layer at time t_n + theta dt_0 into level `dst_level`.
 static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& saved, float theta,
-                             int dst_level) {
+                             int dst_level, cudaStream_t stream) {
   Block& B = dom->blocks[b];
   const Block& P = dom->blocks[B.prior.src];
   MapArgs a;
@@ -374,10 +336,10 @@ static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& sav
   a.skip_mask = F_SOLID;
   a.dN = B.N;
   a.khat = B.prior.khat;
-  return launch_map(a, dom->desc.storage, dom->stream);
+  return launch_map(a, dom->desc.storage, stream);
 }
 
-static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t) {
+static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t, cudaStream_t stream) {
   const Block& B = dom->blocks[b];
   Block& T = dom->blocks[t.dst];
   MapArgs a;
@@ -395,14 +357,22 @@ static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t) {
   a.skip_mask = F_SOLID | F_GHOST;
   a.dN = T.N;
   a.khat = t.khat;
-  return launch_map(a, dom->desc.storage, dom->stream);
+  return launch_map(a, dom->desc.storage, stream);
 }
 
-// One reference step of Algorithm 1 over all blocks.
+// One reference step of Algorithm 1 over all blocks.  Per refined block: the ghost-layer
+// mapping for the next sub-step runs on the auxiliary stream while the current sub-step's
+// collide-stream runs on the main stream (the two write disjoint nodes); the last sub-step
+// stores the temporal alignment directly; post-mappings into different coarser blocks run
+// concurrently.  Every fork is joined before the next dependent launch.
 lbm_status multiscale_step(lbm_domain* dom) {
   std::vector<int> saved(dom->blocks.size());
   for (size_t b = 0; b < dom->blocks.size(); ++b) saved[b] = dom->blocks[b].cur;
+  std::vector<char> pending(dom->blocks.size(), 0);   // target has post-mappings in flight
   cudaStream_t s = dom->stream;
+  cudaStream_t aux = nullptr;
+  lbm_status st = dom->aux(&aux);
+  if (st != LBM_OK) return st;
   cudaError_t e;
   {  // reference scale: one step
     Block& B0 = dom->blocks[0];
@@ -416,39 +386,59 @@ lbm_status multiscale_step(lbm_domain* dom) {
     Block& B = dom->blocks[b];
     const int L = saved[b];
     const int A = (L + 1) % 3, Bv = (L + 2) % 3;
-    int cur = L, prev = L;
+    const bool exact = B.integer_ratio && std::fabs(B.substeps * B.h - 1.0) < 1e-9;
+    int cur = L;
+    if (pending[B.prior.src]) {      // the source block may still receive post-mappings
+      e = cudaStreamWaitEvent(s, dom->event(10 + B.prior.src), 0);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping join");
+    }
+    e = prior_map(dom, b, saved, 0.0f, cur, s);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
     for (int j = 1; j <= B.substeps; ++j) {
-      e = prior_map(dom, b, saved, (float)((j - 1) * B.h), cur);
-      if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
       const int out = (j == 1) ? A : (cur == A ? Bv : A);
-      e = launch_step(dom->view(b, cur, out), dom->desc.storage, B.bx, B.by, s);
+      // fork: ghost layer of `out` for the next sub-step (or at t_n + dt_0 after the last)
+      const float theta = j < B.substeps ? (float)(j * B.h) : 1.0f;
+      e = cudaEventRecord(dom->event(0), s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, dom->event(0), 0);
+      if (e == cudaSuccess) e = prior_map(dom, b, saved, theta, out, aux);
+      if (e == cudaSuccess) e = cudaEventRecord(dom->event(1), aux);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
+      BlockView v = dom->view(b, cur, out);
+      if (j == B.substeps && !exact) {
+        const double t1 = (B.substeps - 1) * B.h, t2 = B.substeps * B.h, T = 1.0;
+        v.f_al0 = B.lv[L].f;
+        v.c_al0 = B.lv[L].c;
+        v.al0 = (float)((T - t1) * (T - t2) / ((0.0 - t1) * (0.0 - t2)));
+        v.al1 = (float)((T - 0.0) * (T - t2) / ((t1 - 0.0) * (t1 - t2)));
+        v.al2 = (float)((T - 0.0) * (T - t1) / ((t2 - 0.0) * (t2 - t1)));
+        e = launch_step_align(v, B.bx, B.by, s);
+      } else {
+        e = launch_step(v, dom->desc.storage, B.bx, B.by, s);
+      }
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, dom->event(1), 0);   // join
       if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");
-      prev = cur;
       cur = out;
     }
-    int aligned = cur;
-    if (!(B.integer_ratio && std::fabs(B.substeps * B.h - 1.0) < 1e-9)) {
-      const double t0 = 0.0, t1 = (B.substeps - 1) * B.h, t2 = B.substeps * B.h, T = 1.0;
-      AlignArgs a;
-      a.f0 = B.lv[L].f; a.f1 = B.lv[prev].f; a.f2 = B.lv[cur].f;
-      a.c0 = B.lv[L].c; a.c1 = B.lv[prev].c; a.c2 = B.lv[cur].c;
-      a.f_out = B.lv[prev].f; a.u_out = B.lv[prev].u; a.c_out = B.lv[prev].c;
-      a.flags = B.flags;
-      a.N = B.N;
-      a.L0 = (float)((T - t1) * (T - t2) / ((t0 - t1) * (t0 - t2)));
-      a.L1 = (float)((T - t0) * (T - t2) / ((t1 - t0) * (t1 - t2)));
-      a.L2 = (float)((T - t0) * (T - t1) / ((t2 - t0) * (t2 - t1)));
-      e = launch_align(a, dom->desc.storage, s);
-      if (e != cudaSuccess) return dom->cuda_fail(e, "temporal alignment");
-      aligned = prev;
+    B.cur = cur;
+    // post-mapping: each coarser target block has its own stream, so mappings into different
+    // targets run concurrently with each other and with the finer blocks' sub-steps; a later
+    // reader of a target (a prior-mapping source, the next step) waits for its mappings
+    e = cudaEventRecord(dom->event(2), s);
+    for (size_t t = 0; t < B.post.size() && e == cudaSuccess; ++t) {
+      const int k = B.post[t].dst;
+      cudaStream_t ps = dom->post_stream(k);
+      if (!ps) return dom->fail(LBM_ERR_CUDA, "post-mapping stream");
+      e = cudaStreamWaitEvent(ps, dom->event(2), 0);
+      if (e == cudaSuccess) e = post_map(dom, b, B.post[t], ps);
+      if (e == cudaSuccess) e = cudaEventRecord(dom->event(10 + k), ps);
+      pending[k] = 1;
     }
-    e = prior_map(dom, b, saved, 1.0f, aligned);
-    if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
-    B.cur = aligned;
-    for (const MapTable& t : B.post) {
-      e = post_map(dom, b, t);
-      if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping");
-    }
+    if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping");
   }
+  for (size_t k = 0; k < pending.size(); ++k)      // join every target before the next step
+    if (pending[k]) {
+      e = cudaStreamWaitEvent(s, dom->event(10 + (int)k), 0);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping join");
+    }
   return LBM_OK;
 }

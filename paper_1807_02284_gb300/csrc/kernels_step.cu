@@ -8,13 +8,13 @@ namespace lbm {
 __constant__ int c_paper_to_cube[27] = {13, 14, 12, 16, 10, 22, 4,  17, 15, 11, 9,  23, 21, 5,
                                         3,  25, 19, 7,  1,  26, 24, 20, 18, 8,  6,  2,  0};
 
-template <typename T, typename IT>
+template <typename T, typename IT, bool ALIGN = false>
 __global__ void __launch_bounds__(256) k_step(BlockView v) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= v.nx || y >= v.ny) return;
-  cell_update<T, IT>(v, x, y, z);
+  cell_update<T, IT, ALIGN>(v, x, y, z);
 }
 
 bool fits_32bit_index(size_t N) { return 27ull * (unsigned long long)N < 0xFFFFFFFFull; }
@@ -30,6 +30,15 @@ cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStr
     if (i32) k_step<float, uint32_t><<<grid, block, 0, s>>>(v);
     else k_step<float, uint64_t><<<grid, block, 0, s>>>(v);
   }
+  return cudaGetLastError();
+}
+
+// Last sub-step of a refined block with the temporal alignment fused in (FP32 storage,
+// 32-bit indexing: refined blocks are limited to 27 N < 2^32).
+cudaError_t launch_step_align(const BlockView& v, int bx, int by, cudaStream_t s) {
+  dim3 block(bx, by, 1);
+  dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, v.nz);
+  k_step<float, uint32_t, true><<<grid, block, 0, s>>>(v);
   return cudaGetLastError();
 }
 

@@ -121,7 +121,10 @@ __device__ __forceinline__ void flag_error(int* err, bool bad) {
 
 // One node of one block: pull (with bounce-back and face handling), macroscopic moments,
 // adaptive rates from the lagged velocity, CMR collision, store of f~, u and the scalar.
-template <typename T, typename IT>
+// Scale-boundary (ghost) nodes of refined blocks are not written: their next values come
+// from the coarse-to-fine mapping, which can therefore run concurrently with this update.
+// ALIGN: last sub-step of a refined block, storing the temporal alignment (see BlockView).
+template <typename T, typename IT, bool ALIGN = false>
 __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, int z) {
   const IT N = (IT)v.N;
   const T* __restrict__ din = static_cast<const T*>(v.d_in);
@@ -137,11 +140,7 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
 #pragma unroll
       for (int k = 0; k < 27; ++k) d[k] = 0.0f;
     } else if (fl & F_GHOST) {
-      // scale-boundary node: carried over unchanged (its next value comes from mapping)
-#pragma unroll
-      for (int k = 0; k < 27; ++k) d[k] = load_pop(din + ((IT)k * N + idx));
-      ux = v.u_in[idx]; uy = v.u_in[N + idx]; uz = v.u_in[2 * N + idx];
-      cval = v.c_in[idx];
+      return;
     } else {  // Dirichlet inflow: equilibrium at rho = 1 and the stored inflow velocity
       ux = v.u_in[idx]; uy = v.u_in[N + idx]; uz = v.u_in[2 * N + idx];
       equilibrium(d, 1.0f, ux, uy, uz);
@@ -174,12 +173,38 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
   const Keep kf = keep_factors(v.rp, g);
   collide_from_raw(d, drho, ux, uy, uz, kf);
 
+  if constexpr (ALIGN) {
+    // three-point Lagrange interpolation to t_n + dt_0 of this node's states at t_n, at
+    // t_n + (l-1)h (the sub-step's input) and at t_n + l h (just computed)
+    const T* __restrict__ f0 = static_cast<const T*>(v.f_al0);
+    float s = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
-  for (int k = 0; k < 27; ++k) store_pop(dout + ((IT)k * N + idx), d[k]);
-  __stcs(v.u_out + idx, ux);
-  __stcs(v.u_out + (N + idx), uy);
-  __stcs(v.u_out + (2 * N + idx), uz);
-  __stcs(v.c_out + idx, src ? v.c_src : scalar_value(sc));
+    for (int k = 0; k < 27; ++k) {
+      const IT i = (IT)k * N + idx;
+      const float val = fmaf(v.al0, load_pop(f0 + i), fmaf(v.al1, load_pop(din + i), v.al2 * d[k]));
+      d[k] = val;
+      s += val;
+      if (cxk(k) > 0) jx += val; else if (cxk(k) < 0) jx -= val;
+      if (cyk(k) > 0) jy += val; else if (cyk(k) < 0) jy -= val;
+      if (czk(k) > 0) jz += val; else if (czk(k) < 0) jz -= val;
+    }
+    const float ia = 1.0f / (1.0f + s);
+    const float cnew = src ? v.c_src : scalar_value(sc);
+    const float cal = fmaf(v.al0, v.c_al0[idx], fmaf(v.al1, v.c_in[idx], v.al2 * cnew));
+#pragma unroll
+    for (int k = 0; k < 27; ++k) store_pop(dout + ((IT)k * N + idx), d[k]);
+    __stcs(v.u_out + idx, jx * ia);
+    __stcs(v.u_out + (N + idx), jy * ia);
+    __stcs(v.u_out + (2 * N + idx), jz * ia);
+    __stcs(v.c_out + idx, cal);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 27; ++k) store_pop(dout + ((IT)k * N + idx), d[k]);
+    __stcs(v.u_out + idx, ux);
+    __stcs(v.u_out + (N + idx), uy);
+    __stcs(v.u_out + (2 * N + idx), uz);
+    __stcs(v.c_out + idx, src ? v.c_src : scalar_value(sc));
+  }
 }
 
 }  // namespace lbm

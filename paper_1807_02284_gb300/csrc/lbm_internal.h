@@ -25,6 +25,11 @@ struct BlockView {
   RelaxParams rp;
   float c_src;
   int* err;            // device error word (bit 0: non-finite or non-positive density)
+  // temporal alignment fused into the last sub-step of a refined block (Sec. 4.2.4): the
+  // stored state is L0 f(t_n) + L1 f(t_n+(l-1)h) + L2 f(t_n+lh), with f(t_n+(l-1)h) = d_in
+  const void* f_al0 = nullptr;   // populations at t_n
+  const float* c_al0 = nullptr;  // scalar at t_n
+  float al0 = 0.f, al1 = 0.f, al2 = 0.f;
 };
 
 // One node mapped between scales: destination node index, index of the source cell's
@@ -59,16 +64,6 @@ struct MapArgs {
   float khat;          // K_hat factor of moments 4..8 (1 for all others)
 };
 
-// Arguments of the temporal alignment of one refined block (Sec. 4.2.4).
-struct AlignArgs {
-  const void* f0; const void* f1; const void* f2;   // t_n, t_n + (l-1)h, t_n + l h
-  const float* c0; const float* c1; const float* c2;
-  void* f_out; float* u_out; float* c_out;         // may alias f1 / c1 (pointwise update)
-  const uint8_t* flags;
-  size_t N;
-  float L0, L1, L2;
-};
-
 // One tile of the batched work list: a BX x BY patch of one z-plane of one simulation.
 struct WorkItem {
   int view;            // index into the BlockView array
@@ -77,6 +72,7 @@ struct WorkItem {
 
 // ---- kernels_step.cu
 cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s);
+cudaError_t launch_step_align(const BlockView& v, int bx, int by, cudaStream_t s);
 cudaError_t launch_init(const BlockView& v, int storage, const float* rho, const float* u,
                         const float* c, cudaStream_t s);
 cudaError_t launch_merge_user_flags(uint8_t* flags, const uint8_t* user, size_t N,
@@ -104,7 +100,6 @@ cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size
 
 // ---- coupling.cu
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s);
-cudaError_t launch_align(const AlignArgs& a, int storage, cudaStream_t s);
 cudaError_t launch_set_ghost_layer(uint8_t* flags, int nx, int ny, int nz, cudaStream_t s);
 
 // ---- kernels_batch.cu

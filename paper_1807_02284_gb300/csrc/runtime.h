@@ -72,6 +72,14 @@ struct lbm_domain {
   lbm::TapeState* tape = nullptr;
   lbm::GraphCache* graphs = nullptr;
   void* batch_plan = nullptr;           // cached plan of lbm_step_batch (batch.cu)
+  cudaStream_t aux_stream = nullptr;    // second stream for concurrent mapping launches
+  std::vector<cudaEvent_t> events;      // fork / join events (timing disabled)
+
+  std::vector<cudaStream_t> post_streams;  // one per post-mapping target block
+
+  lbm_status aux(cudaStream_t* out);    // the auxiliary stream, created on first use
+  cudaEvent_t event(int i);             // fork / join event i, created on first use
+  cudaStream_t post_stream(int k);      // stream of post-mappings into block k
 
   lbm_status fail(lbm_status st, const std::string& msg);
   lbm_status cuda_fail(cudaError_t e, const char* what);

@@ -11,11 +11,25 @@
 using namespace lbm;
 
 namespace lbm {
+// Captured step graphs, one per starting assignment of time levels (the `cur` level of every
+// block).  Each graph advances `chunk` reference steps, a multiple of the period after which
+// the level assignment repeats, so it ends in the assignment it started from.
 struct GraphCache {
-  // graphs[p] advances the single-block domain by `chunk` steps starting from level p
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> exec;
   int chunk = 0;
 };
+
+// Level assignment after one reference step (mirrors the schedule of multiscale_step).
+static std::vector<int> next_levels(const std::vector<lbm::Block>& blocks, std::vector<int> cur) {
+  cur[0] ^= 1;
+  for (size_t b = 1; b < blocks.size(); ++b) {
+    const int L = cur[b], A = (L + 1) % 3, B = (L + 2) % 3;
+    int c = L;
+    for (int j = 1; j <= blocks[b].substeps; ++j) c = (j == 1) ? A : (c == A ? B : A);
+    cur[b] = c;
+  }
+  return cur;
+}
 }  // namespace lbm
 
 void lbm_domain::pick_tiles(int b) {
@@ -75,8 +89,8 @@ lbm_status lbm_domain::autotune_tiles(int b) {
 
 void lbm_domain::invalidate_graphs() {
   if (!graphs) return;
-  for (int p = 0; p < 2; ++p)
-    if (graphs->exec[p]) cudaGraphExecDestroy(graphs->exec[p]);
+  for (auto& kv : graphs->exec)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
   delete graphs;
   graphs = nullptr;
 }
@@ -84,9 +98,42 @@ void lbm_domain::invalidate_graphs() {
 void release_tape(lbm_domain* dom);        // adjoint.cu
 void release_batch_plan(lbm_domain* dom);  // batch.cu
 
+lbm_status lbm_domain::aux(cudaStream_t* out) {
+  if (!aux_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&aux_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { aux_stream = nullptr; return cuda_fail(e, "cudaStreamCreate"); }
+  }
+  *out = aux_stream;
+  return LBM_OK;
+}
+
+cudaEvent_t lbm_domain::event(int i) {
+  while ((int)events.size() <= i) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    events.push_back(ev);
+  }
+  return events[i];
+}
+
+cudaStream_t lbm_domain::post_stream(int k) {
+  while ((int)post_streams.size() <= k) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    post_streams.push_back(st);
+  }
+  return post_streams[k];
+}
+
 void lbm_domain::release_extras() {
   invalidate_graphs();
   release_batch_plan(this);
+  for (cudaEvent_t ev : events) cudaEventDestroy(ev);
+  events.clear();
+  for (cudaStream_t st : post_streams) cudaStreamDestroy(st);
+  post_streams.clear();
+  if (aux_stream) cudaStreamDestroy(aux_stream);
+  aux_stream = nullptr;
   release_tape(this);
   if (small_host) cudaFreeHost(small_host);
   small_host = nullptr;
@@ -159,10 +206,9 @@ lbm_status lbm_domain::advance_direct(int n) {
   return LBM_OK;
 }
 
-// Single-block domains without a tape replay a captured graph of `chunk` steps; the rest
-// (and multi-block domains) launch directly.
+// Without a tape, steps are replayed from captured graphs of `chunk` reference steps (a
+// multiple of the level-rotation period, at least 16 steps); the remainder launches directly.
 lbm_status lbm_domain::advance(int n) {
-  const int chunk = 16;
   if (n > 0) {
     for (size_t b = 0; b < blocks.size(); ++b) {
       const bool was = blocks[b].tuned;
@@ -171,36 +217,64 @@ lbm_status lbm_domain::advance(int n) {
       if (!was) invalidate_graphs();
     }
   }
-  if (blocks.size() != 1 || tape != nullptr || n < 2 * chunk) return advance_direct(n);
-  Block& B = blocks[0];
-  if (!graphs) {
-    graphs = new GraphCache();
-    graphs->chunk = chunk;
+  if (blocks.size() > 1) {  // stream and events of the fork/join schedule exist before capture
+    cudaStream_t a = nullptr;
+    lbm_status st = aux(&a);
+    if (st != LBM_OK) return st;
+    if (!event(10 + (int)blocks.size())) return fail(LBM_ERR_CUDA, "cudaEventCreate");
+    if (!post_stream((int)blocks.size() - 1)) return fail(LBM_ERR_CUDA, "cudaStreamCreate");
   }
+  if (tape != nullptr) return advance_direct(n);
+  std::vector<int> start(blocks.size());
+  for (size_t b = 0; b < blocks.size(); ++b) start[b] = blocks[b].cur;
+  if (!graphs) {
+    int period = 1;
+    std::vector<int> s = next_levels(blocks, start);
+    while (s != start && period < 64) { s = next_levels(blocks, s); ++period; }
+    if (s != start) return advance_direct(n);
+    graphs = new GraphCache();
+    graphs->chunk = period * ((16 + period - 1) / period);
+  }
+  const int chunk = graphs->chunk;
+  if (n < 2 * chunk) return advance_direct(n);
   int done = 0;
   while (n - done >= chunk) {
-    const int p = B.cur;
-    if (!graphs->exec[p]) {
+    std::vector<int> key(blocks.size());
+    for (size_t b = 0; b < blocks.size(); ++b) key[b] = blocks[b].cur;
+    cudaGraphExec_t exec = nullptr;
+    for (auto& kv : graphs->exec)
+      if (kv.first == key) exec = kv.second;
+    if (!exec) {
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-      int cur = p;
-      for (int i = 0; i < chunk && e == cudaSuccess; ++i) {
-        e = launch_step(view(0, cur, cur ^ 1), desc.storage, B.bx, B.by, stream);
-        cur ^= 1;
+      lbm_status st = LBM_OK;
+      for (int i = 0; i < chunk && st == LBM_OK; ++i) {
+        if (blocks.size() == 1) {
+          Block& B = blocks[0];
+          const cudaError_t el = launch_step(view(0, B.cur, B.cur ^ 1), desc.storage, B.bx, B.by, stream);
+          if (el != cudaSuccess) st = cuda_fail(el, "collide-stream launch");
+          B.cur ^= 1;
+        } else {
+          st = multiscale_step(this);
+        }
       }
       cudaError_t e2 = cudaStreamEndCapture(stream, &g);
-      if (e != cudaSuccess || e2 != cudaSuccess) {
+      for (size_t b = 0; b < blocks.size(); ++b) blocks[b].cur = key[b];
+      if (st != LBM_OK || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        return cuda_fail(e != cudaSuccess ? e : e2, "step graph capture");
+        return st != LBM_OK ? st : cuda_fail(e2, "step graph capture");
       }
-      e = cudaGraphInstantiate(&graphs->exec[p], g, 0);
+      e = cudaGraphInstantiate(&exec, g, 0);
       cudaGraphDestroy(g);
-      if (e != cudaSuccess) { graphs->exec[p] = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      graphs->exec.push_back({key, exec});
     }
-    cudaError_t e = cudaGraphLaunch(graphs->exec[p], stream);
+    cudaError_t e = cudaGraphLaunch(exec, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-    if (chunk % 2) B.cur ^= 1;
+    std::vector<int> s = key;
+    for (int i = 0; i < chunk; ++i) s = next_levels(blocks, s);
+    for (size_t b = 0; b < blocks.size(); ++b) blocks[b].cur = s[b];
     steps += chunk;
     done += chunk;
   }

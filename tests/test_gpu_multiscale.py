@@ -79,6 +79,26 @@ def test_three_block_parity_non_integer_ratios(lib, steps):
     dom.close()
 
 
+def test_graph_replay_matches_direct_steps_multiblock(lib):
+    """lbm_step(n) replays captured graphs of the concurrent fork/join schedule; it must give
+    the same bits as n single steps launched directly."""
+    from paper_1807_02284_gb300 import lbm
+    sc = synth.multiscale(scale=0.25, nu=2e-3, flow_amp=0.06)
+    a = gpu_multiscale(sc)
+    b = gpu_multiscale(sc)
+    a.step(40)
+    for _ in range(40):
+        b.step(1)
+    for i in range(3):
+        fa = a.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32, i)
+        fb = b.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32, i)
+        assert np.array_equal(fa, fb), f"block {i}"
+        assert np.array_equal(a.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F32, i),
+                              b.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F32, i))
+    a.close()
+    b.close()
+
+
 def test_integer_ratio_two_block_parity(lib):
     """alpha = 2 two-block case on a periodic Taylor-Green field (no temporal interpolation:
     two sub-steps land exactly on t_n + dt_0)."""
