@@ -367,8 +367,11 @@ def run_batch(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
+    from paper_1807_02284_gb300 import sharding
     scenes = synth.batch(64, seed=4)
-    mine = scenes[rank::ws]          # independent simulations shard across ranks
+    # independent simulations: largest-first placement by node count, no collective
+    mine = [scenes[i] for i in
+            sharding.rank_share([s.blocks[0].flags.size for s in scenes], rank, ws)]
     stream = torch.cuda.Stream(device=dev)
     doms = []
     for sc in mine:
