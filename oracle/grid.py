@@ -52,6 +52,8 @@ class Params:
     nu_hi: Sequence[float] = cmr.NU_HI_DEFAULT
     c_src: float = 1.0
     body_force: Optional[Sequence[float]] = None
+    grad_mode: str = "lagged"    # "lagged" central differences of the stored velocity, or
+                                 # "local" strain rate from the node's non-equilibrium moments
 
 
 @dataclasses.dataclass
@@ -135,6 +137,25 @@ def lagged_gradient_norm(u: torch.Tensor, periodic, z, y, x) -> torch.Tensor:
     return torch.sqrt(torch.clamp(g2, min=1e-300))
 
 
+def local_strain_norm(f_in: torch.Tensor, nu: float) -> torch.Tensor:
+    """|grad u| estimated from a node's own pre-collision populations: the non-equilibrium
+    second central moments Pi = m - m^eq (moments 4..9 of the Appendix basis) give the strain
+    rate through Pi^(1) = -2 c_s^2 rho S_hat / S (Sec. 4.2.1, with S the shear rate of
+    Sec. 3.1 Eq. 3 and c_s^2 = 1/3); the norm is sqrt(2 S_hat : S_hat), which equals |grad u|
+    for a shear flow."""
+    rho, u = cmr.macros(f_in)
+    m = (cmr.moment_matrix(u).transpose(-1, -2) @ f_in[..., None])[..., 0]
+    mn = m - cmr.m_eq(rho, u)
+    pxy, pxz, pyz = mn[..., 4], mn[..., 5], mn[..., 6]
+    pxx = (mn[..., 9] + mn[..., 7] + mn[..., 8]) / 3.0
+    pyy = (mn[..., 9] - 2.0 * mn[..., 7] + mn[..., 8]) / 3.0
+    pzz = (mn[..., 9] + mn[..., 7] - 2.0 * mn[..., 8]) / 3.0
+    S = 1.0 / (3.0 * nu + 0.5)
+    scale = -3.0 * S / (2.0 * rho)
+    ss = (pxx ** 2 + pyy ** 2 + pzz ** 2) + 2.0 * (pxy ** 2 + pxz ** 2 + pyz ** 2)
+    return torch.sqrt(torch.clamp(2.0 * ss * scale * scale, min=1e-300))
+
+
 def _forced_shift(rho, u, F):
     """Exact-difference forcing increment (test-only hook, see module docstring)."""
     Fv = torch.as_tensor(F, dtype=DT)
@@ -161,7 +182,9 @@ def step_cells(st: State, p: Params, z: torch.Tensor, y: torch.Tensor, x: torch.
     f_in = torch.stack(cols, dim=-1)
 
     # 3. adaptive factor from the lagged velocity field
-    if p.adaptive:
+    if p.adaptive and p.grad_mode == "local":
+        phi = cmr.adaptive_factor(local_strain_norm(f_in, p.nu), p.a, p.b, p.g_max)
+    elif p.adaptive:
         phi = cmr.adaptive_factor(lagged_gradient_norm(st.u, per, z, y, x), p.a, p.b, p.g_max)
     else:
         phi = torch.ones(z.shape, dtype=DT)

@@ -200,6 +200,35 @@ def test_adaptive_factor_on_linear_and_quadratic_shear():
     assert g.item() == pytest.approx(2e-3 * 4, rel=1e-13)
 
 
+def test_local_strain_estimate_on_a_decaying_shear_wave():
+    """The local estimate of |grad u| from non-equilibrium moments (Sec. 4.2.1 relation)
+    reproduces |du_x/dy| = A k |cos(k y)| exp(-nu k^2 t) of a periodic shear wave once the
+    start-up transient has decayed; a missing factor of S or rho would miss by > 20 %."""
+    n = 32
+    b = synth._empty_block((2, n, 2))
+    A, k = 0.04, 2 * math.pi / n
+    y = np.arange(n)
+    b.u0[0] = (A * np.sin(k * y))[None, :, None]
+    st = grid.init_state(b.rho0, b.u0, b.c0, b.flags)
+    nu = 0.02
+    p = grid.Params(nu=nu, periodic=(True, True, True), adaptive=False)
+    t = 60
+    st = grid.run(st, p, t)
+    # the populations entering step t+1 at x = z = 0, all y
+    zz = torch.zeros(n, dtype=torch.long)
+    yy = torch.arange(n)
+    nxt = {o: grid.neighbour_index(n, True, o) for o in (-1, 0, 1)}
+    cols = []
+    for q in range(27):
+        cx, cy, cz = (int(v) for v in cmr.C[q])
+        cols.append(st.f[q, 0, nxt[-cy][yy], 0])
+    f_in = torch.stack(cols, dim=-1)
+    g = grid.local_strain_norm(f_in, nu).numpy()
+    exact = A * k * np.abs(np.cos(k * (y + 0.0))) * math.exp(-nu * k * k * (t + 0.5))
+    big = exact > 0.5 * exact.max()
+    assert np.allclose(g[big], exact[big], rtol=5e-3)
+
+
 # ------------------------------------------------------------------------- flows
 
 def _state(scene):
