@@ -149,15 +149,16 @@ def _workload(name):
     return sc, storage
 
 
-def _algorithmic_bytes(flags, storage):
+def _algorithmic_bytes(flags, storage, local=False):
     """Bytes the collide-stream launch must move per step, by node kind: fluid nodes read
-    and write 27 populations, the lagged velocity and the scalar; obstacle voxels only write
-    their rest state; inflow nodes read their velocity and write their equilibrium."""
+    and write 27 populations, the lagged velocity (not read when the strain rate is taken
+    from the node's own moments) and the scalar; obstacle voxels only write their rest state;
+    inflow nodes read their velocity and write their equilibrium."""
     pop = 2 if storage == "fp16" else 4
     solid = int(((flags & 1) != 0).sum())
     inflow = int(((flags & 2) != 0).sum()) - int(((flags & 3) == 3).sum())
     fluid = flags.size - solid - inflow
-    per_fluid = 27 * pop * 2 + 12 * 2 + 4 * 2 + 1
+    per_fluid = 27 * pop * 2 + 12 * (1 if local else 2) + 4 * 2 + 1
     per_solid = 27 * pop + 12 + 4 + 1
     per_inflow = 27 * pop + 12 * 2 + 4 * 2 + 1
     return fluid * per_fluid + solid * per_solid + inflow * per_inflow, per_fluid
@@ -246,7 +247,8 @@ def run_ours(args):
     b = sc.blocks[0]
     stream = torch.cuda.Stream(device=dev)
     dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, storage=storage,
-                     adaptive=sc.adaptive, c_src=sc.c_src, stream=stream)
+                     adaptive=sc.adaptive, c_src=sc.c_src, stream=stream,
+                     grad_mode="local" if args.workload.endswith("_local") else "lagged")
     for blk in sc.blocks[1:]:
         dom.add_scale_block(blk.origin, blk.h, blk.dims)
     for i, blk in enumerate(sc.blocks):
@@ -286,7 +288,8 @@ def run_ours(args):
 
     alg_bytes, per_fluid = 0, 0
     for s, blk in zip(subs, sc.blocks):
-        ab, per_fluid = _algorithmic_bytes(blk.flags, storage)
+        ab, per_fluid = _algorithmic_bytes(blk.flags, storage,
+                                           local=args.workload.endswith("_local"))
         alg_bytes += s * ab
     peak, peak_src = _peaks()
     achieved = alg_bytes / (t_dev / K) / 1e9
@@ -528,6 +531,7 @@ def _variants(args):
 
     res = {}
     for name, fn, steps, warm in (("plume256_fp16", run_ours, 100, 10),
+                                  ("plume256_local", run_ours, 100, 10),
                                   ("multiscale3", run_ours, 50, 5),
                                   ("batch64", run_batch, 100, 10),
                                   ("adjoint128", run_adjoint, 200, 0)):
@@ -553,7 +557,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="plume256",
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
-                             "multiscale3", "batch64", "adjoint128", "adjoint64"])
+                             "multiscale3", "batch64", "adjoint128", "adjoint64",
+                             "plume256_local"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -104,7 +104,14 @@ typedef struct {
   void* cuda_stream;   /* cudaStream_t or NULL */
   lbm_allocator alloc; /* alloc.alloc == NULL: cudaMalloc / cudaFree */
   int32_t device;      /* CUDA device ordinal */
+  int32_t grad_mode;   /* |grad u| of the adaptive relaxation (Sec. 4.1):
+                          LBM_GRAD_LAGGED central differences of the velocity stored by the
+                          previous step (default); LBM_GRAD_LOCAL the node's own strain rate
+                          from its non-equilibrium second moments, Pi^(1) = -2 c_s^2 rho
+                          S_hat / S (Sec. 4.2.1), as sqrt(2 S_hat : S_hat) */
 } lbm_domain_desc;
+
+enum { LBM_GRAD_LAGGED = 0, LBM_GRAD_LOCAL = 1 };
 
 typedef struct {
   int32_t dims[3];

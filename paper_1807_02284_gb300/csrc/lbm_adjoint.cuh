@@ -148,27 +148,33 @@ __device__ __forceinline__ void raw_axis_vjp(float (&A)[27]) {
 __device__ __forceinline__ void relax_vjp(const float (&v)[27], float (&A)[27], float drho,
                                           float X, float Y, float Z, const Keep& kf,
                                           float (&bar)[4], float (&kbar)[4]) {
-  D4 D[27];
-  delta_moments(D4{drho, 1.f, 0.f, 0.f, 0.f}, D4{X, 0.f, 1.f, 0.f, 0.f},
-                D4{Y, 0.f, 0.f, 1.f, 0.f}, D4{Z, 0.f, 0.f, 0.f, 1.f}, D);
-  float db[27];
-#pragma unroll
-  for (int i = 0; i < 27; ++i) db[i] = 0.0f;
-  // group of each relaxed moment: -1 shear (keep nu), 0..3 high-order groups
-  auto relax_one = [&](int i, float K, int grp) {
+  // Each moment's Delta (with its four partials) is formed and consumed at once, so only a
+  // few dual numbers are live at any time.
+  const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
+  const D4 dr{drho, 1.f, 0.f, 0.f, 0.f}, x{X, 0.f, 1.f, 0.f, 0.f}, y{Y, 0.f, 0.f, 1.f, 0.f},
+           z{Z, 0.f, 0.f, 0.f, 1.f};
+  auto grad = [&](float db, const D4& dl) {
+    bar[0] = fmaf(db, dl.d0, bar[0]);
+    bar[1] = fmaf(db, dl.d1, bar[1]);
+    bar[2] = fmaf(db, dl.d2, bar[2]);
+    bar[3] = fmaf(db, dl.d3, bar[3]);
+  };
+  // out_i = Delta_i + K (v_i - Delta_i): dv_i = K o, dDelta_i = (1 - K) o, dK = o (v_i - Delta_i)
+  auto one = [&](int i, const D4& dl, float K, int grp) {
     const float o = A[i];
     A[i] = K * o;
-    db[i] = (1.0f - K) * o;
-    if (grp >= 0) kbar[grp] = fmaf(o, v[i] - D[i].v, kbar[grp]);
+    if (grp >= 0) kbar[grp] = fmaf(o, v[i] - dl.v, kbar[grp]);
+    grad((1.0f - K) * o, dl);
   };
-  relax_one(kap(1, 1, 0), kf.nu, -1);
-  relax_one(kap(1, 0, 1), kf.nu, -1);
-  relax_one(kap(0, 1, 1), kf.nu, -1);
-  {
-    const float ex = D[kap(2, 0, 0)].v, ey = D[kap(0, 2, 0)].v, ez = D[kap(0, 0, 2)].v;
-    const float Aa = v[kap(2, 0, 0)] - ex, Bb = v[kap(0, 2, 0)] - ey, Cc = v[kap(0, 0, 2)] - ez;
+  one(kap(1, 1, 0), -(x * y), kf.nu, -1);
+  one(kap(1, 0, 1), -(x * z), kf.nu, -1);
+  one(kap(0, 1, 1), -(y * z), kf.nu, -1);
+  const D4 x2 = x * x, y2 = y * y, z2 = z * z;
+  {  // second-order diagonal: deviators at the shear rate, trace at group 9..16
+    const D4 dr3 = dr * third;
+    const D4 ex = dr3 - x2, ey = dr3 - y2, ez = dr3 - z2;
+    const float Aa = v[kap(2, 0, 0)] - ex.v, Bb = v[kap(0, 2, 0)] - ey.v, Cc = v[kap(0, 0, 2)] - ez.v;
     const float o2 = A[kap(2, 0, 0)], o3 = A[kap(0, 2, 0)], o4 = A[kap(0, 0, 2)];
-    const float third = 1.0f / 3.0f;
     const float trb = (o2 + o3 + o4) * third;
     const float d1b = (o2 - 2.0f * o3 + o4) * third;
     const float d2b = (o2 + o3 - 2.0f * o4) * third;
@@ -179,33 +185,40 @@ __device__ __forceinline__ void relax_vjp(const float (&v)[27], float (&A)[27], 
     A[kap(2, 0, 0)] = Ab;
     A[kap(0, 2, 0)] = Bb_;
     A[kap(0, 0, 2)] = Cb;
-    db[kap(2, 0, 0)] = o2 - Ab;
-    db[kap(0, 2, 0)] = o3 - Bb_;
-    db[kap(0, 0, 2)] = o4 - Cb;
+    grad(o2 - Ab, ex);
+    grad(o3 - Bb_, ey);
+    grad(o4 - Cb, ez);
   }
-  relax_one(kap(1, 2, 0), kf.g[0], 0);
-  relax_one(kap(1, 0, 2), kf.g[0], 0);
-  relax_one(kap(2, 1, 0), kf.g[0], 0);
-  relax_one(kap(0, 1, 2), kf.g[0], 0);
-  relax_one(kap(2, 0, 1), kf.g[0], 0);
-  relax_one(kap(0, 2, 1), kf.g[0], 0);
-  relax_one(kap(1, 1, 1), kf.g[0], 0);
-  relax_one(kap(2, 2, 0), kf.g[1], 1);
-  relax_one(kap(2, 0, 2), kf.g[1], 1);
-  relax_one(kap(0, 2, 2), kf.g[1], 1);
-  relax_one(kap(2, 1, 1), kf.g[1], 1);
-  relax_one(kap(1, 2, 1), kf.g[1], 1);
-  relax_one(kap(1, 1, 2), kf.g[1], 1);
-  relax_one(kap(1, 2, 2), kf.g[2], 2);
-  relax_one(kap(2, 1, 2), kf.g[2], 2);
-  relax_one(kap(2, 2, 1), kf.g[2], 2);
-  relax_one(kap(2, 2, 2), kf.g[3], 3);
-#pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    bar[0] = fmaf(db[i], D[i].d0, bar[0]);
-    bar[1] = fmaf(db[i], D[i].d1, bar[1]);
-    bar[2] = fmaf(db[i], D[i].d2, bar[2]);
-    bar[3] = fmaf(db[i], D[i].d3, bar[3]);
+  one(kap(1, 2, 0), x * (third - dr * y2), kf.g[0], 0);
+  one(kap(1, 0, 2), x * (third - dr * z2), kf.g[0], 0);
+  one(kap(2, 1, 0), y * (third - dr * x2), kf.g[0], 0);
+  one(kap(0, 1, 2), y * (third - dr * z2), kf.g[0], 0);
+  one(kap(2, 0, 1), z * (third - dr * x2), kf.g[0], 0);
+  one(kap(0, 2, 1), z * (third - dr * y2), kf.g[0], 0);
+  one(kap(1, 1, 1), -(dr * x * y * z), kf.g[0], 0);
+  {
+    const D4 r3m1 = dr * 3.0f + 2.0f;   // 3 rho - 1
+    const D4 dr9 = dr * ninth;
+    one(kap(2, 2, 0), r3m1 * x2 * y2 + dr9 - (x2 + y2) * third, kf.g[1], 1);
+    one(kap(2, 0, 2), r3m1 * x2 * z2 + dr9 - (x2 + z2) * third, kf.g[1], 1);
+    one(kap(0, 2, 2), r3m1 * y2 * z2 + dr9 - (y2 + z2) * third, kf.g[1], 1);
+    one(kap(2, 1, 1), y * z * (r3m1 * x2 - d4c(third)), kf.g[1], 1);
+    one(kap(1, 2, 1), x * z * (r3m1 * y2 - d4c(third)), kf.g[1], 1);
+    one(kap(1, 1, 2), x * y * (r3m1 * z2 - d4c(third)), kf.g[1], 1);
+  }
+  {
+    const D4 o6 = dr * (-6.0f) + (-5.0f);   // 1 - 6 rho
+    const D4 dr3 = dr * third;
+    one(kap(1, 2, 2), x * (o6 * y2 * z2 + (ninth - dr3 * (y2 + z2))), kf.g[2], 2);
+    one(kap(2, 1, 2), y * (o6 * x2 * z2 + (ninth - dr3 * (x2 + z2))), kf.g[2], 2);
+    one(kap(2, 2, 1), z * (o6 * x2 * y2 + (ninth - dr3 * (x2 + y2))), kf.g[2], 2);
+  }
+  {
+    const D4 rho = dr + 1.0f;
+    const D4 p2 = x2 * y2 + x2 * z2 + y2 * z2;
+    const D4 d222 = (rho * 10.0f + (-1.0f)) * x2 * y2 * z2 + (rho + (-third)) * p2 +
+                    dr * (1.0f / 27.0f) - (x2 + y2 + z2) * ninth;
+    one(kap(2, 2, 2), d222, kf.g[3], 3);
   }
 }
 

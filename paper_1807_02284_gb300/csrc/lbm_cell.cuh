@@ -157,7 +157,7 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
   // all independent loads first: the pull and the lagged velocity neighbourhood
   pull_all<T, IT>(d, din, N, n);
   if (fl & F_NEAR_SOLID) bounce_back<T, IT>(d, din, N, v.flags, n, idx);
-  const float g = v.rp.adaptive ? grad_norm<IT>(v.u_in, N, n) : 0.0f;
+  const float g_lag = (v.rp.adaptive && !v.rp.local) ? grad_norm<IT>(v.u_in, N, n) : 0.0f;
 
   raw_moments(d);
   const float drho = d[kap(0, 0, 0)];
@@ -170,8 +170,11 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
   const bool src = (fl & F_SCALAR_SRC) != 0;
   if (!src) sc = scalar_corners<IT>(v, x, y, z, ux, uy, uz);
 
+  central_from_raw(d, ux, uy, uz);
+  const float g = (v.rp.adaptive && v.rp.local) ? local_strain(d, drho, ux, uy, uz, v.rp.s_nu)
+                                                : g_lag;
   const Keep kf = keep_factors(v.rp, g);
-  collide_from_raw(d, drho, ux, uy, uz, kf);
+  collide_from_central(d, drho, ux, uy, uz, kf);
 
   if constexpr (ALIGN) {
     // three-point Lagrange interpolation to t_n + dt_0 of this node's states at t_n, at

@@ -83,6 +83,7 @@ struct RelaxParams {
   float a, b;        // adaptive model parameters (Sec. 4.1)
   float inv_gmax;    // 1 / g_max
   int adaptive;
+  int local;         // 1: |grad u| from the node's non-equilibrium moments, 0: lagged field
 };
 
 // Sec. 4.1: S_i = 1/(3 phi nu'_i + 1/2) for i >= 9 with phi = a min(|grad u|/g_max, 1) + b.
@@ -234,17 +235,46 @@ __device__ __forceinline__ void raw_moments(float (&v)[27]) {
   raw_axis<9>(v);
 }
 
-// Collision of shifted populations given their raw moments (from raw_moments) and u:
-// raw -> central, relax towards equilibrium, back to populations (in place).
-__device__ __forceinline__ void collide_from_raw(float (&v)[27], float drho, float ux, float uy,
-                                                 float uz, const Keep& kf) {
+// Raw moments -> central moments about u (in place).
+__device__ __forceinline__ void central_from_raw(float (&v)[27], float ux, float uy, float uz) {
   shift_axis<1>(v, ux);
   shift_axis<3>(v, uy);
   shift_axis<9>(v, uz);
+}
+
+// Relaxation of central moments and the inverse sweeps back to populations (in place).
+__device__ __forceinline__ void collide_from_central(float (&v)[27], float drho, float ux,
+                                                     float uy, float uz, const Keep& kf) {
   relax_to_equilibrium(v, drho, ux, uy, uz, kf);
   inv_axis<9>(v, uz);
   inv_axis<3>(v, uy);
   inv_axis<1>(v, ux);
+}
+
+// Collision of shifted populations given their raw moments (from raw_moments) and u:
+// raw -> central, relax towards equilibrium, back to populations (in place).
+__device__ __forceinline__ void collide_from_raw(float (&v)[27], float drho, float ux, float uy,
+                                                 float uz, const Keep& kf) {
+  central_from_raw(v, ux, uy, uz);
+  collide_from_central(v, drho, ux, uy, uz, kf);
+}
+
+// |grad u| from a node's central moments (of the shifted populations, before relaxation):
+// the non-equilibrium second moments Pi = kappa - Delta give the strain rate through
+// Pi^(1) = -2 c_s^2 rho S_hat / S (Sec. 4.2.1, c_s^2 = 1/3); returns sqrt(2 S_hat : S_hat).
+__device__ __forceinline__ float local_strain(const float (&v)[27], float drho, float X, float Y,
+                                              float Z, float s_nu) {
+  const float dr3 = drho * (1.0f / 3.0f);
+  const float pxx = v[kap(2, 0, 0)] - (dr3 - X * X);
+  const float pyy = v[kap(0, 2, 0)] - (dr3 - Y * Y);
+  const float pzz = v[kap(0, 0, 2)] - (dr3 - Z * Z);
+  const float pxy = v[kap(1, 1, 0)] + X * Y;
+  const float pxz = v[kap(1, 0, 1)] + X * Z;
+  const float pyz = v[kap(0, 1, 1)] + Y * Z;
+  const float ss = fmaf(pxx, pxx, fmaf(pyy, pyy, pzz * pzz)) +
+                   2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz));
+  const float scale = 1.5f * s_nu / (1.0f + drho);
+  return scale * sqrtf(2.0f * ss);
 }
 
 // Equilibrium (shifted) for given rho, u.

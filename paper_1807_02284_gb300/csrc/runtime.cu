@@ -121,6 +121,7 @@ RelaxParams Domain::relax_params(double nu_block) const {
   rp.b = (float)desc.b;
   rp.inv_gmax = (float)(1.0 / desc.g_max);
   rp.adaptive = desc.adaptive ? 1 : 0;
+  rp.local = desc.grad_mode == LBM_GRAD_LOCAL ? 1 : 0;
   return rp;
 }
 
@@ -182,7 +183,7 @@ const void* Domain::device_source(const void* src, size_t bytes, int on_device,
 
 extern "C" {
 
-int32_t lbm_abi_version(void) { return 1; }
+int32_t lbm_abi_version(void) { return 2; }
 
 lbm_status lbm_default_desc(lbm_domain_desc* d) {
   if (!d) return LBM_ERR_INVALID_ARG;
@@ -212,6 +213,9 @@ lbm_status lbm_create_domain(const lbm_domain_desc* desc, lbm_domain** out) {
     g_create_error = "unknown storage"; return LBM_ERR_INVALID_ARG;
   }
   if (!(desc->g_max > 0.0)) { g_create_error = "g_max must be positive"; return LBM_ERR_INVALID_ARG; }
+  if (desc->grad_mode != LBM_GRAD_LAGGED && desc->grad_mode != LBM_GRAD_LOCAL) {
+    g_create_error = "unknown grad_mode"; return LBM_ERR_INVALID_ARG;
+  }
   for (int g = 0; g < 4; ++g)
     if (!(desc->nu_hi[g] > 0.0)) { g_create_error = "nu_hi must be positive"; return LBM_ERR_INVALID_ARG; }
   if ((desc->alloc.alloc == nullptr) != (desc->alloc.free == nullptr)) {

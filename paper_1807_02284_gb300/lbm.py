@@ -43,7 +43,9 @@ class lbm_domain_desc(C.Structure):
                 ("storage", C.c_int32), ("adaptive", C.c_int32), ("a", C.c_double),
                 ("b", C.c_double), ("g_max", C.c_double), ("nu_hi", C.c_double * 4),
                 ("c_src", C.c_double), ("cuda_stream", C.c_void_p), ("alloc", lbm_allocator),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("grad_mode", C.c_int32)]
+
+LBM_GRAD_LAGGED, LBM_GRAD_LOCAL = 0, 1
 
 
 class lbm_block_info(C.Structure):
@@ -136,7 +138,8 @@ class Domain:
     def __init__(self, dims: Sequence[int], nu: float, periodic=(False, False, False),
                  storage: str = "fp32", adaptive: bool = True, a: float = -4.0, b: float = 5.0,
                  g_max: float = 0.1, nu_hi=(0.005, 0.007, 0.009, 0.01), c_src: float = 1.0,
-                 stream=None, torch_allocator: bool = True, device: int = 0):
+                 stream=None, torch_allocator: bool = True, device: int = 0,
+                 grad_mode: str = "lagged"):
         self.lib = load()
         self.handle = C.c_void_p()
         d = lbm_domain_desc()
@@ -150,6 +153,7 @@ class Domain:
         d.nu_hi[:] = [float(v) for v in nu_hi]
         d.c_src = float(c_src)
         d.device = int(device)
+        d.grad_mode = LBM_GRAD_LOCAL if grad_mode == "local" else LBM_GRAD_LAGGED
         self._keep = []
         if stream is None:
             import torch

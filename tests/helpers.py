@@ -12,11 +12,11 @@ def f32(a):
     return np.asarray(a, dtype=np.float32)
 
 
-def gpu_domain(scene, storage="fp32", block=0):
+def gpu_domain(scene, storage="fp32", block=0, grad_mode="lagged"):
     from paper_1807_02284_gb300 import lbm
     b = scene.blocks[block]
     dom = lbm.Domain(b.dims, scene.nu, periodic=scene.periodic, storage=storage,
-                     adaptive=scene.adaptive, c_src=scene.c_src)
+                     adaptive=scene.adaptive, c_src=scene.c_src, grad_mode=grad_mode)
     dom.set_flags(b.flags)
     dom.init_macro(f32(b.u0), rho=f32(b.rho0), c=f32(b.c0))
     return dom
@@ -38,9 +38,9 @@ def oracle_state(scene, block=0):
                            f32(b.c0).astype(np.float64), b.flags)
 
 
-def oracle_params(scene):
+def oracle_params(scene, grad_mode="lagged"):
     return grid.Params(nu=scene.nu, periodic=scene.periodic, adaptive=scene.adaptive,
-                       c_src=scene.c_src)
+                       c_src=scene.c_src, grad_mode=grad_mode)
 
 
 def state_from_arrays(f, u, c, flags):

@@ -62,6 +62,22 @@ def test_parity_random_scenes(lib, name):
     dom.close()
 
 
+@pytest.mark.parametrize("name", ["open_sphere_inflow", "periodic_ragged"])
+def test_parity_local_strain_relaxation(lib, name):
+    """Adaptive relaxation driven by the node's own non-equilibrium strain rate."""
+    sc = synth.random_scene(**SCENES[name])
+    b = sc.blocks[0]
+    dom = gpu_domain(sc, grad_mode="local")
+    st = oracle_state(sc)
+    p = oracle_params(sc, grad_mode="local")
+    for n in range(8):
+        dom.step(1)
+        st = grid.step(st, p)
+    dom.sync()
+    _compare(dom, st, b, f"local strain {name}")
+    dom.close()
+
+
 def test_parity_far_from_equilibrium_populations(lib):
     """Arbitrary positive populations (all 27 moments away from equilibrium), random lagged
     velocity and scalar: one step."""
