@@ -297,6 +297,9 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": _profiled_traffic(args.workload),
                 "peak_source": peak_src, "kernel": "k_step (fused pull/collide/scalar)",
                 "bytes_per_fluid_node": per_fluid}
+    i0 = dom.info(0)
+    roofline["launch"] = {"tile": [int(i0.tile[0]), int(i0.tile[1])],
+                          "ctas_per_sm": int(i0.ctas_per_sm)}
 
     # ---- end to end through the public API with host buffers
     E = max(3, min(K, 50))

@@ -121,6 +121,8 @@ typedef struct {
   int32_t substeps;  /* sub-steps per reference step (1 for s0) */
   int64_t steps;     /* reference steps taken by the domain */
   int32_t tile[2];   /* x, y extent of the collide-stream thread tile (chosen by autotuning) */
+  int32_t ctas_per_sm; /* CTAs per SM the collide-stream kernel's registers are bounded for
+                          (3 or 4, chosen by autotuning together with the tile) */
 } lbm_block_info;
 
 /* Version of this header's ABI. */

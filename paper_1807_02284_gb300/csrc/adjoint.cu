@@ -425,7 +425,7 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
     // recompute the segment's states 1..len from its checkpoint
     auto level = [&](int i) -> const Level& { return i == 0 ? t->ckpt[sg] : t->seg[i - 1]; };
     for (int i = 0; i < len; ++i) {
-      e = launch_step(view_of(dom, level(i), level(i + 1)), ST_FP32, B.bx, B.by, s);
+      e = launch_step(view_of(dom, level(i), level(i + 1)), ST_FP32, B.bx, B.by, s, B.minb);
       if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint recompute");
     }
     for (int i = len - 1; i >= 0; --i) {

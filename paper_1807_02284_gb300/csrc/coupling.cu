@@ -377,7 +377,7 @@ lbm_status multiscale_step(lbm_domain* dom) {
   {  // reference scale: one step
     Block& B0 = dom->blocks[0];
     const int nxt = B0.cur ^ 1;
-    e = launch_step(dom->view(0, B0.cur, nxt), dom->desc.storage, B0.bx, B0.by, s);
+    e = launch_step(dom->view(0, B0.cur, nxt), dom->desc.storage, B0.bx, B0.by, s, B0.minb);
     if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");
     B0.cur = nxt;
   }
@@ -411,9 +411,9 @@ lbm_status multiscale_step(lbm_domain* dom) {
         v.al0 = (float)((T - t1) * (T - t2) / ((0.0 - t1) * (0.0 - t2)));
         v.al1 = (float)((T - 0.0) * (T - t2) / ((t1 - 0.0) * (t1 - t2)));
         v.al2 = (float)((T - 0.0) * (T - t1) / ((t2 - 0.0) * (t2 - t1)));
-        e = launch_step_align(v, B.bx, B.by, s);
+        e = launch_step_align(v, B.bx, B.by, s, B.minb);
       } else {
-        e = launch_step(v, dom->desc.storage, B.bx, B.by, s);
+        e = launch_step(v, dom->desc.storage, B.bx, B.by, s, B.minb);
       }
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s, dom->event(1), 0);   // join
       if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");

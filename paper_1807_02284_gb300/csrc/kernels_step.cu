@@ -8,8 +8,10 @@ namespace lbm {
 __constant__ int c_paper_to_cube[27] = {13, 14, 12, 16, 10, 22, 4,  17, 15, 11, 9,  23, 21, 5,
                                         3,  25, 19, 7,  1,  26, 24, 20, 18, 8,  6,  2,  0};
 
-template <typename T, typename IT, bool ALIGN = false>
-__global__ void __launch_bounds__(256) k_step(BlockView v) {
+// MINB: CTAs of 256 threads per SM the registers are bounded for (3: 80 registers, no
+// spills; 4: 64 registers with a small spill, more loads in flight); chosen by autotuning.
+template <typename T, typename IT, bool ALIGN, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step(BlockView v) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -19,26 +21,33 @@ __global__ void __launch_bounds__(256) k_step(BlockView v) {
 
 bool fits_32bit_index(size_t N) { return 27ull * (unsigned long long)N < 0xFFFFFFFFull; }
 
-cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s) {
+template <typename T, typename IT, bool ALIGN>
+static void launch_step_t(const BlockView& v, dim3 grid, dim3 block, int minb, cudaStream_t s) {
+  if (minb >= 4) k_step<T, IT, ALIGN, 4><<<grid, block, 0, s>>>(v);
+  else k_step<T, IT, ALIGN, 3><<<grid, block, 0, s>>>(v);
+}
+
+cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
+                        int minb) {
   dim3 block(bx, by, 1);
   dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, v.nz);
   const bool i32 = fits_32bit_index(v.N);
   if (storage == ST_FP16) {
-    if (i32) k_step<__half, uint32_t><<<grid, block, 0, s>>>(v);
-    else k_step<__half, uint64_t><<<grid, block, 0, s>>>(v);
+    if (i32) launch_step_t<__half, uint32_t, false>(v, grid, block, minb, s);
+    else launch_step_t<__half, uint64_t, false>(v, grid, block, minb, s);
   } else {
-    if (i32) k_step<float, uint32_t><<<grid, block, 0, s>>>(v);
-    else k_step<float, uint64_t><<<grid, block, 0, s>>>(v);
+    if (i32) launch_step_t<float, uint32_t, false>(v, grid, block, minb, s);
+    else launch_step_t<float, uint64_t, false>(v, grid, block, minb, s);
   }
   return cudaGetLastError();
 }
 
 // Last sub-step of a refined block with the temporal alignment fused in (FP32 storage,
 // 32-bit indexing: refined blocks are limited to 27 N < 2^32).
-cudaError_t launch_step_align(const BlockView& v, int bx, int by, cudaStream_t s) {
+cudaError_t launch_step_align(const BlockView& v, int bx, int by, cudaStream_t s, int minb) {
   dim3 block(bx, by, 1);
   dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, v.nz);
-  k_step<float, uint32_t, true><<<grid, block, 0, s>>>(v);
+  launch_step_t<float, uint32_t, true>(v, grid, block, minb, s);
   return cudaGetLastError();
 }
 

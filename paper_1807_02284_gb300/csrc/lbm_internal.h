@@ -71,8 +71,9 @@ struct WorkItem {
 };
 
 // ---- kernels_step.cu
-cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s);
-cudaError_t launch_step_align(const BlockView& v, int bx, int by, cudaStream_t s);
+cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
+                        int minb = 3);
+cudaError_t launch_step_align(const BlockView& v, int bx, int by, cudaStream_t s, int minb = 3);
 cudaError_t launch_init(const BlockView& v, int storage, const float* rho, const float* u,
                         const float* c, cudaStream_t s);
 cudaError_t launch_merge_user_flags(uint8_t* flags, const uint8_t* user, size_t N,

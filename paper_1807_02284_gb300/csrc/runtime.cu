@@ -183,7 +183,7 @@ const void* Domain::device_source(const void* src, size_t bytes, int on_device,
 
 extern "C" {
 
-int32_t lbm_abi_version(void) { return 2; }
+int32_t lbm_abi_version(void) { return 3; }
 
 lbm_status lbm_default_desc(lbm_domain_desc* d) {
   if (!d) return LBM_ERR_INVALID_ARG;
@@ -502,6 +502,7 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
   info->steps = dom->steps;
   info->tile[0] = B.bx;
   info->tile[1] = B.by;
+  info->ctas_per_sm = B.minb;
   return LBM_OK;
 }
 

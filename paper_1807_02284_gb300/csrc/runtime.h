@@ -41,6 +41,7 @@ struct Block {
   int parent = 0;          // nearest coarser block containing this one (prior-mapping source)
   RelaxParams rp;
   int bx = 128, by = 2;    // tile of the collide-stream launch
+  int minb = 3;            // register bound of the collide-stream launch (CTAs per SM)
   bool tuned = false;      // tile shape chosen by autotune_tiles
 };
 

@@ -38,19 +38,21 @@ void lbm_domain::pick_tiles(int b) {
   B.bx = B.nx >= 128 ? 128 : B.nx >= 64 ? 64 : 32;
   B.by = 256 / B.bx;
   B.tuned = false;
-  if (const char* env = std::getenv("LBM_TILE")) {  // "bx,by" forces a tile shape
-    int bx = 0, by = 0;
-    if (std::sscanf(env, "%d,%d", &bx, &by) == 2 && bx > 0 && by > 0 && bx * by <= 256 &&
-        bx % 32 == 0) {
+  B.minb = 3;
+  if (const char* env = std::getenv("LBM_TILE")) {  // "bx,by[,minb]" forces a launch shape
+    int bx = 0, by = 0, mb = 3;
+    const int n = std::sscanf(env, "%d,%d,%d", &bx, &by, &mb);
+    if (n >= 2 && bx > 0 && by > 0 && bx * by <= 256 && bx % 32 == 0 && (mb == 3 || mb == 4)) {
       B.bx = bx;
       B.by = by;
+      B.minb = mb;
       B.tuned = true;
     }
   }
 }
 
-// Times candidate tile shapes of the collide-stream launch on the block's current state and
-// keeps the fastest.  Candidates read the current level and write the next one without
+// Times candidate launch shapes of the collide-stream kernel (tile shape x register bound) on
+// the block's current state and keeps the fastest.  Candidates read the current level and write the next one without
 // advancing the clock, so tuning changes no result (every shape computes the same values).
 lbm_status lbm_domain::autotune_tiles(int b) {
   Block& B = blocks[b];
@@ -63,13 +65,14 @@ lbm_status lbm_domain::autotune_tiles(int b) {
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(cudaGetLastError(), "event"); }
   const int to = (B.cur + 1) % (int)B.lv.size();
   float best = 1e30f;
-  int bx = B.bx, by = B.by;
+  int bx = B.bx, by = B.by, minb = B.minb;
+  for (int mb = 3; mb <= 4; ++mb)
   for (const auto& c : cand) {
     if (c[0] > 32 && c[0] > B.nx + 31) continue;
     const BlockView v = view(b, B.cur, to);
-    cudaError_t e = launch_step(v, desc.storage, c[0], c[1], stream);  // warm-up
+    cudaError_t e = launch_step(v, desc.storage, c[0], c[1], stream, mb);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
-    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_step(v, desc.storage, c[0], c[1], stream);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_step(v, desc.storage, c[0], c[1], stream, mb);
     if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -78,12 +81,13 @@ lbm_status lbm_domain::autotune_tiles(int b) {
       cudaEventDestroy(e0); cudaEventDestroy(e1);
       return cuda_fail(e, "tile autotuning");
     }
-    if (ms < best) { best = ms; bx = c[0]; by = c[1]; }
+    if (ms < best) { best = ms; bx = c[0]; by = c[1]; minb = mb; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   B.bx = bx;
   B.by = by;
+  B.minb = minb;
   return LBM_OK;
 }
 
@@ -194,7 +198,7 @@ lbm_status lbm_domain::advance_direct(int n) {
     if (blocks.size() == 1) {
       Block& B = blocks[0];
       const int nxt = B.cur ^ 1;
-      cudaError_t e = launch_step(view(0, B.cur, nxt), desc.storage, B.bx, B.by, stream);
+      cudaError_t e = launch_step(view(0, B.cur, nxt), desc.storage, B.bx, B.by, stream, B.minb);
       if (e != cudaSuccess) return cuda_fail(e, "collide-stream launch");
       B.cur = nxt;
     } else {
@@ -252,7 +256,7 @@ lbm_status lbm_domain::advance(int n) {
       for (int i = 0; i < chunk && st == LBM_OK; ++i) {
         if (blocks.size() == 1) {
           Block& B = blocks[0];
-          const cudaError_t el = launch_step(view(0, B.cur, B.cur ^ 1), desc.storage, B.bx, B.by, stream);
+          const cudaError_t el = launch_step(view(0, B.cur, B.cur ^ 1), desc.storage, B.bx, B.by, stream, B.minb);
           if (el != cudaSuccess) st = cuda_fail(el, "collide-stream launch");
           B.cur ^= 1;
         } else {
