@@ -189,8 +189,10 @@ lbm_status lbm_write_field(lbm_domain* dom, int32_t block_id, int32_t field, int
 
 /* FP64 diagnostics of a block over non-obstacle, non-ghost nodes:
    out[0] mass sum rho, out[1..3] momentum sum rho u, out[4] kinetic energy
-   (1/2) sum rho |u|^2.  out is a host array of 5 doubles.  Synchronises; returns DIVERGED
-   if the device error word is set. */
+   (1/2) sum rho |u|^2.  Per-node values are formed in FP32 and summed per thread with a
+   compensated FP32 sum, threads are combined in FP64 in a fixed order (deterministic).
+   out is a host array of 5 doubles.  Synchronises; returns DIVERGED if the device error
+   word is set. */
 lbm_status lbm_reduce(lbm_domain* dom, int32_t block_id, double out[5]);
 
 lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block_info* info);

@@ -265,10 +265,26 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Compensated FP32 sum (Kahan): the error of a thread's partial sum stays near one FP32
+// rounding of the sum whatever the number of terms, so the per-node work runs on the FP32
+// pipe and only the cross-thread combination needs FP64 (whose issue rate on this part is a
+// small fraction of FP32's).  No product is involved, so no FMA contraction can undo it.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <typename T>
-__global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(const T* d, const uint8_t* flags,
-                                                           size_t N, double* partials) {
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+__global__ void __launch_bounds__(REDUCE_THREADS, 4) k_reduce(const T* d, const uint8_t* flags,
+                                                              size_t N, double* partials) {
+  unsigned count = 0;
+  KahanF acc[5];
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
        idx += (size_t)gridDim.x * blockDim.x) {
     if (flags[idx] & (F_SOLID | F_GHOST)) continue;
@@ -277,19 +293,18 @@ __global__ void __launch_bounds__(REDUCE_THREADS) k_reduce(const T* d, const uin
     for (int k = 0; k < 27; ++k) dd[k] = load_pop(d + (size_t)k * N + idx);
     float drho, jx, jy, jz;
     macros(dd, drho, jx, jy, jz);
-    const float rho = 1.0f + drho;
-    acc[0] += 1.0;
-    acc[1] += (double)drho;
-    acc[2] += (double)jx;
-    acc[3] += (double)jy;
-    acc[4] += (double)jz;
-    acc[5] += 0.5 * ((double)jx * jx + (double)jy * jy + (double)jz * jz) / (double)rho;
+    ++count;
+    acc[0].add(drho);
+    acc[1].add(jx);
+    acc[2].add(jy);
+    acc[3].add(jz);
+    acc[4].add(0.5f * (jx * jx + jy * jy + jz * jz) / (1.0f + drho));
   }
   __shared__ double sh[REDUCE_THREADS / 32][6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    const double w = warp_sum(acc[i]);
+    const double w = warp_sum(i == 0 ? (double)count : acc[i - 1].value());
     if (lane == 0) sh[wid][i] = w;
   }
   __syncthreads();

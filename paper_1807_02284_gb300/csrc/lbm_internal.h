@@ -91,10 +91,12 @@ cudaError_t launch_write_f(void* d, int storage, size_t N, const void* in, int i
 cudaError_t launch_read_rho(const void* d, int storage, size_t N, float* out, cudaStream_t s);
 cudaError_t launch_convert(const void* in, int in_f64, void* out, int out_f64, size_t n,
                            cudaStream_t s);
-// deterministic FP64 reduction of mass, momentum and kinetic energy over non-solid,
-// non-ghost nodes: writes per-CTA partials into `partials` (REDUCE_CTAS * 6 doubles) and the
+// deterministic reduction of mass, momentum and kinetic energy over non-solid, non-ghost
+// nodes (per-thread compensated FP32 sums of per-node FP32 values, combined in FP64 in a
+// fixed order):
+// writes per-CTA partials into `partials` (REDUCE_CTAS * 6 doubles) and the
 // final six doubles {count, sum drho, sum jx, sum jy, sum jz, sum |j|^2/(2 rho)} into `out`.
-constexpr int REDUCE_CTAS = 304;
+constexpr int REDUCE_CTAS = 608;   // 4 CTAs on each of 152 SMs
 constexpr int REDUCE_THREADS = 256;
 cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
                           double* partials, double* out, cudaStream_t s);
