@@ -195,6 +195,14 @@ lbm_status lbm_write_field(lbm_domain* dom, int32_t block_id, int32_t field, int
    word is set. */
 lbm_status lbm_reduce(lbm_domain* dom, int32_t block_id, double out[5]);
 
+/* lbm_reduce of block `block_id` of each of n domains (no counterpart in the paper: the
+   read-back of a batch), with every reduction queued on its domain's stream before the
+   call waits for any.  out is a host array of 5 n doubles, domain i's five values at
+   out[5 i].  INVALID_ARG for a null list, out or member, n <= 0, or a block id that some
+   member lacks (nothing is launched then); otherwise every member is reduced and the first
+   failing member's status is returned (DIVERGED, TIMEOUT, CUDA). */
+lbm_status lbm_reduce_batch(lbm_domain* const* doms, int32_t n, int32_t block_id, double* out);
+
 lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block_info* info);
 
 /* Advances n independent single-block domains by `steps` reference steps with one

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "lbm_cell.cuh"
@@ -128,9 +129,10 @@ static int resident_blocks(int storage, bool i32, int threads) {
   return std::max(1, per_sm) * std::max(1, sms);
 }
 
-// Persistent state of the batched stepper, owned by the first domain of the batch.
+// One captured batched launch: the work list and views of a set of domains, starting from a
+// given assignment of time levels and advancing a given number of steps.
 struct BatchPlan {
-  std::vector<lbm_domain*> doms;
+  std::vector<unsigned long long> serials;   // members (domain serials, in call order)
   std::vector<int> curs;
   int steps = 0;
   int chunk = 0, threads = 0;
@@ -144,18 +146,33 @@ struct BatchPlan {
   bool captured = false;
 };
 
+// Plans cached by the first domain of a batch.  A call with an odd step count flips every
+// member's current level, so alternating calls need two plans; a few more cover a caller
+// that alternates between batches.  Members are matched by serial, never by address, so a
+// plan never refers to a destroyed domain's memory once it is chosen.
+struct BatchCache {
+  std::vector<BatchPlan*> plans;   // most recently used last
+  int chunk = 0, threads = 0;      // tuned once per cache
+};
+constexpr size_t kMaxBatchPlans = 4;
+
 }  // namespace lbm
 
 using namespace lbm;
 
-void release_batch_plan(lbm_domain* dom) {
-  BatchPlan* p = static_cast<BatchPlan*>(dom->batch_plan);
-  if (!p) return;
+static void free_plan(lbm_domain* dom, BatchPlan* p) {
   if (p->exec) cudaGraphExecDestroy(p->exec);
   dom->dev_free(p->views);
   dom->dev_free(p->items);
   dom->dev_free(p->bar);
   delete p;
+}
+
+void release_batch_plan(lbm_domain* dom) {
+  BatchCache* c = static_cast<BatchCache*>(dom->batch_plan);
+  if (!c) return;
+  for (BatchPlan* p : c->plans) free_plan(dom, p);
+  delete c;
   dom->batch_plan = nullptr;
 }
 
@@ -186,9 +203,12 @@ static lbm_status build_plan(lbm_domain* const* doms, int n, int chunk, BatchPla
   if (e != cudaSuccess) return d0->cuda_fail(e, "batch plan upload");
   p->n_items = (int)hi.size();
   p->chunk = chunk;
-  p->doms.assign(doms, doms + n);
+  p->serials.resize(n);
   p->curs.resize(n);
-  for (int i = 0; i < n; ++i) p->curs[i] = doms[i]->blocks[0].cur;
+  for (int i = 0; i < n; ++i) {
+    p->serials[i] = doms[i]->serial;
+    p->curs[i] = doms[i]->blocks[0].cur;
+  }
   return LBM_OK;
 }
 
@@ -260,26 +280,44 @@ extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t
   }
   for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
 
-  BatchPlan* p = static_cast<BatchPlan*>(d0->batch_plan);
-  bool reuse = p && p->steps == steps && (int)p->doms.size() == n;
-  if (reuse)
-    for (int i = 0; i < n && reuse; ++i)
-      reuse = p->doms[i] == doms[i] && p->curs[i] == doms[i]->blocks[0].cur;
-  if (!reuse) {
-    int chunk = 256, threads = 256;
-    if (p) { chunk = p->chunk; threads = p->threads; }
-    else {
+  BatchCache* cache = static_cast<BatchCache*>(d0->batch_plan);
+  if (!cache) {
+    cache = new (std::nothrow) BatchCache();
+    if (!cache) return d0->fail(LBM_ERR_OOM, "out of host memory");
+    d0->batch_plan = cache;
+  }
+  BatchPlan* p = nullptr;
+  for (size_t k = 0; k < cache->plans.size() && !p; ++k) {
+    BatchPlan* q = cache->plans[k];
+    bool same = q->steps == steps && (int)q->serials.size() == n;
+    for (int i = 0; i < n && same; ++i)
+      same = q->serials[i] == doms[i]->serial && q->curs[i] == doms[i]->blocks[0].cur;
+    if (same) {
+      p = q;
+      cache->plans.erase(cache->plans.begin() + k);
+      cache->plans.push_back(p);
+    }
+  }
+  if (!p) {
+    if (!cache->chunk) {
+      int chunk = 256, threads = 256;
       lbm_status st = tune_chunk(doms, n, &chunk, &threads);
       if (st != LBM_OK) return st;
+      cache->chunk = chunk;
+      cache->threads = threads;
     }
-    release_batch_plan(d0);
-    p = new BatchPlan();
-    d0->batch_plan = p;
-    lbm_status st = build_plan(doms, n, chunk, p);
-    if (st != LBM_OK) { release_batch_plan(d0); return st; }
-    p->threads = threads;
+    while (cache->plans.size() >= kMaxBatchPlans) {
+      free_plan(d0, cache->plans.front());
+      cache->plans.erase(cache->plans.begin());
+    }
+    p = new (std::nothrow) BatchPlan();
+    if (!p) return d0->fail(LBM_ERR_OOM, "out of host memory");
+    lbm_status st = build_plan(doms, n, cache->chunk, p);
+    if (st != LBM_OK) { free_plan(d0, p); return st; }
+    p->threads = cache->threads;
+    cache->plans.push_back(p);
     p->steps = steps;
-    p->grid = std::min(resident_blocks(d0->desc.storage, p->i32, threads), std::max(1, p->n_items));
+    p->grid = std::min(resident_blocks(d0->desc.storage, p->i32, p->threads), std::max(1, p->n_items));
     // capture: reset the barrier, then the cooperative persistent launch
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -287,7 +325,7 @@ extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t
       cudaError_t e1 = cudaMemsetAsync(p->bar, 0, sizeof(BarrierState), s);
       if (e1 == cudaSuccess)
         e1 = launch_batch(d0->desc.storage, p->i32, p->views, p->items, p->n_items, p->chunk,
-                          steps, p->bar, threads, p->grid, (unsigned)p->grid, d0->d_err,
+                          steps, p->bar, p->threads, p->grid, (unsigned)p->grid, d0->d_err,
                           kBarrierLimitCycles, true, s);
       cudaError_t e2 = cudaStreamEndCapture(s, &g);
       if (e1 == cudaSuccess && e2 == cudaSuccess && g) {

@@ -22,94 +22,151 @@ namespace lbm {
 
 // ------------------------------------------------------------------------------ kernels
 
+// One CTA maps MAP_D consecutive table entries in three phases, so that the gathers of a
+// small mapping (a ghost layer of a few ten thousand nodes) still keep every SM busy:
+//   0. one thread per entry: source corners, obstacle-dropped trilinear weights;
+//   1. one thread per (entry, population) pair, lanes over consecutive entries: the 8 (or
+//      16, when mixing two time levels) gathered loads of one population, into shared memory;
+//   2. one thread per entry: moments, K_hat rescale, back to populations (Sec. 3.2);
+//   3. one thread per (entry, population) pair: the stores.
 // MODE 0: source level lo only; 1: level hi only; 2: (1 - theta) lo + theta hi.
+constexpr int MAP_D = 32;          // entries per CTA
+constexpr int MAP_THREADS = 128;
+constexpr int MAP_LD = 29;         // shared-memory row stride (odd: no bank conflicts)
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(128) k_map(MapArgs a) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.n) return;
-  const MapEntry m = a.table[e];
-  if (a.dst_flags[m.dst] & a.skip_mask) return;
+__global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
+  __shared__ float sv[MAP_D * MAP_LD];   // 27 populations + scalar per entry
+  __shared__ uint32_t scorner[8][MAP_D];
+  __shared__ float sweight[8][MAP_D];
+  __shared__ float sinv[MAP_D];          // 1 / sum of weights, 0 for an inactive entry
+  __shared__ uint32_t sdst[MAP_D];
+  __shared__ float su[3][MAP_D];
+  const int t = threadIdx.x;
+  const int e0 = blockIdx.x * MAP_D;
+  const int nloc = min(MAP_D, a.n - e0);
+  const uint32_t sN = (uint32_t)a.sN;
+  if (t < MAP_D) {
+    // inactive entries keep weight 0 on corner 0, so the gather phase needs no branch
+    float inv = 0.0f;
+    uint32_t sc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (t < nloc) {
+      const MapEntry m = a.table[e0 + t];
+      sdst[t] = m.dst;
+      if (!(a.dst_flags[m.dst] & a.skip_mask)) {
+        const uint32_t sy = (uint32_t)a.snx, sz = (uint32_t)a.snx * (uint32_t)a.sny;
+        float wsum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          sc[c] = m.src + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz;
+          const float wc = ((c & 1) ? m.tx : 1.0f - m.tx) * (((c >> 1) & 1) ? m.ty : 1.0f - m.ty) *
+                           ((c >> 2) ? m.tz : 1.0f - m.tz);
+          w[c] = (__ldg(a.src_flags + sc[c]) & F_SOLID) ? 0.0f : wc;  // obstacle corners dropped
+          wsum += w[c];
+        }
+        if (wsum > 0.0f) inv = 1.0f / wsum;   // every corner an obstacle: node left unchanged
+      }
+    }
+    if (inv == 0.0f) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) { sc[c] = 0; w[c] = 0.0f; }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) { scorner[c][t] = sc[c]; sweight[c][t] = w[c]; }
+    sinv[t] = inv;
+  }
+  __syncthreads();
   const T* __restrict__ lo = static_cast<const T*>(MODE == 1 ? a.f_hi : a.f_lo);
   const T* __restrict__ hi = static_cast<const T*>(a.f_hi);
   const float* __restrict__ clo = MODE == 1 ? a.c_hi : a.c_lo;
-  const uint32_t sN = (uint32_t)a.sN;
-  const uint32_t sy = (uint32_t)a.snx, sz = (uint32_t)a.snx * (uint32_t)a.sny;
-  // the 8 corners, their obstacle flags (loaded together) and trilinear weights
-  uint32_t s[8];
-  float w[8];
-  float wsum = 0.0f;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) s[c] = m.src + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float wc = ((c & 1) ? m.tx : 1.0f - m.tx) * (((c >> 1) & 1) ? m.ty : 1.0f - m.ty) *
-                     ((c >> 2) ? m.tz : 1.0f - m.tz);
-    w[c] = (__ldg(a.src_flags + s[c]) & F_SOLID) ? 0.0f : wc;   // obstacle corners dropped
-    wsum += w[c];
-  }
-  if (!(wsum > 0.0f)) return;                   // every corner is an obstacle: unchanged
-  const float inv_w = 1.0f / wsum;
   const float th = a.theta;
-  float acc[27];
-  float cacc = 0.0f;
-  if (MODE == 2) {
+  // every (entry, population) pair of this thread has entry d = lane: corners read once, and
+  // the unrolled pairs issue all their loads before the first sum is needed
+  static_assert(MAP_D == 32 && (MAP_D * 28) % MAP_THREADS == 0, "gather layout");
+  constexpr int PAIRS = MAP_D * 28 / MAP_THREADS;
+  const int d = t & 31;
+  uint32_t sc[8];
+  float w[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      cacc = fmaf(w[c] * (1.0f - th), __ldg(clo + s[c]), cacc);
-      cacc = fmaf(w[c] * th, __ldg(a.c_hi + s[c]), cacc);
-    }
-  } else {
+  for (int c = 0; c < 8; ++c) { sc[c] = scorner[c][d]; w[c] = sweight[c][d]; }
+  float vals[PAIRS];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) cacc = fmaf(w[c], __ldg(clo + s[c]), cacc);
-  }
-  // population-outer, corner-inner: the 8 (or 16) loads of each population are independent
-#pragma unroll
-  for (int k = 0; k < 27; ++k) {
-    const T* pl = lo + (uint32_t)k * sN;
+  for (int i = 0; i < PAIRS; ++i) {
+    const int k = (t >> 5) + i * (MAP_THREADS / 32);
     float v = 0.0f;
-    if (MODE == 2) {
-      const T* ph = hi + (uint32_t)k * sN;
+    if (k < 27) {
+      const T* pl = lo + (uint32_t)k * sN;
+      if (MODE == 2) {
+        const T* ph = hi + (uint32_t)k * sN;
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        v = fmaf(w[c], fmaf(th, load_pop(ph + s[c]) - load_pop(pl + s[c]), load_pop(pl + s[c])), v);
+        for (int c = 0; c < 8; ++c)
+          v = fmaf(w[c], fmaf(th, load_pop(ph + sc[c]) - load_pop(pl + sc[c]), load_pop(pl + sc[c])), v);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v = fmaf(w[c], load_pop(pl + sc[c]), v);
+      }
+    } else if (MODE == 2) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        v = fmaf(w[c] * (1.0f - th), __ldg(clo + sc[c]), v);
+        v = fmaf(w[c] * th, __ldg(a.c_hi + sc[c]), v);
+      }
     } else {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) v = fmaf(w[c], load_pop(pl + s[c]), v);
+      for (int c = 0; c < 8; ++c) v = fmaf(w[c], __ldg(clo + sc[c]), v);
     }
-    acc[k] = v * inv_w;
+    vals[i] = v;
   }
-  raw_moments(acc);
-  const float drho = acc[kap(0, 0, 0)];
-  const float inv = 1.0f / (1.0f + drho);
-  const float ux = acc[kap(1, 0, 0)] * inv, uy = acc[kap(0, 1, 0)] * inv,
-              uz = acc[kap(0, 0, 1)] * inv;
-  Keep kf;
-  kf.nu = a.khat;
-  kf.g[0] = kf.g[1] = kf.g[2] = kf.g[3] = 1.0f;
-  collide_from_raw(acc, drho, ux, uy, uz, kf);
+  const float inv_d = sinv[d];
+#pragma unroll
+  for (int i = 0; i < PAIRS; ++i) sv[d * MAP_LD + (t >> 5) + i * (MAP_THREADS / 32)] = vals[i] * inv_d;
+  __syncthreads();
+  if (t < MAP_D && sinv[t] != 0.0f) {
+    float acc[27];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) acc[k] = sv[t * MAP_LD + k];
+    raw_moments(acc);
+    const float drho = acc[kap(0, 0, 0)];
+    const float inv = 1.0f / (1.0f + drho);
+    const float ux = acc[kap(1, 0, 0)] * inv, uy = acc[kap(0, 1, 0)] * inv,
+                uz = acc[kap(0, 0, 1)] * inv;
+    Keep kf;
+    kf.nu = a.khat;
+    kf.g[0] = kf.g[1] = kf.g[2] = kf.g[3] = 1.0f;
+    collide_from_raw(acc, drho, ux, uy, uz, kf);
+#pragma unroll
+    for (int k = 0; k < 27; ++k) sv[t * MAP_LD + k] = acc[k];
+    su[0][t] = ux;
+    su[1][t] = uy;
+    su[2][t] = uz;
+  }
+  __syncthreads();
   T* out = static_cast<T*>(a.f_dst);
   const size_t dN = a.dN;
+  if (sinv[d] == 0.0f) return;
+  const uint32_t dst = sdst[d];
 #pragma unroll
-  for (int k = 0; k < 27; ++k) store_pop(out + (size_t)k * dN + m.dst, acc[k]);
-  a.u_dst[m.dst] = ux;
-  a.u_dst[dN + m.dst] = uy;
-  a.u_dst[2 * dN + m.dst] = uz;
-  a.c_dst[m.dst] = cacc * inv_w;
+  for (int i = 0; i < (31 + MAP_THREADS / 32 - 1) / (MAP_THREADS / 32); ++i) {
+    const int k = (t >> 5) + i * (MAP_THREADS / 32);
+    if (k < 27) store_pop(out + (size_t)k * dN + dst, sv[d * MAP_LD + k]);
+    else if (k < 30) a.u_dst[(size_t)(k - 27) * dN + dst] = su[k - 27][d];
+    else if (k == 30) a.c_dst[dst] = sv[d * MAP_LD + 27];
+  }
 }
 
 template <typename T>
-static void launch_map_t(const MapArgs& a, int grid, int threads, cudaStream_t s) {
-  if (a.theta <= 0.0f) k_map<T, 0><<<grid, threads, 0, s>>>(a);
-  else if (a.theta >= 1.0f) k_map<T, 1><<<grid, threads, 0, s>>>(a);
-  else k_map<T, 2><<<grid, threads, 0, s>>>(a);
+static void launch_map_t(const MapArgs& a, int grid, cudaStream_t s) {
+  if (a.theta <= 0.0f) k_map<T, 0><<<grid, MAP_THREADS, 0, s>>>(a);
+  else if (a.theta >= 1.0f) k_map<T, 1><<<grid, MAP_THREADS, 0, s>>>(a);
+  else k_map<T, 2><<<grid, MAP_THREADS, 0, s>>>(a);
 }
 
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const int threads = 128;
-  const int grid = (a.n + threads - 1) / threads;
-  if (storage == ST_FP16) launch_map_t<__half>(a, grid, threads, s);
-  else launch_map_t<float>(a, grid, threads, s);
+  const int grid = (a.n + MAP_D - 1) / MAP_D;
+  if (storage == ST_FP16) launch_map_t<__half>(a, grid, s);
+  else launch_map_t<float>(a, grid, s);
   return cudaGetLastError();
 }
 

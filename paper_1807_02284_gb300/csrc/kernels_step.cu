@@ -1,5 +1,5 @@
-// Single-block kernels: collide-stream step, equilibrium initialisation, flag derivation,
-// field conversion and the deterministic FP64 diagnostics reduction.
+// Single-block kernels: collide-stream step, equilibrium initialisation, flag derivation and
+// field conversion.
 #include "lbm_cell.cuh"
 
 namespace lbm {
@@ -254,82 +254,6 @@ cudaError_t launch_convert(const void* in, int in_f64, void* out, int out_f64, s
   else if (in_f64) k_convert<double, float><<<g, 256, 0, s>>>((const double*)in, (float*)out, n);
   else if (out_f64) k_convert<float, double><<<g, 256, 0, s>>>((const float*)in, (double*)out, n);
   else k_convert<float, float><<<g, 256, 0, s>>>((const float*)in, (float*)out, n);
-  return cudaGetLastError();
-}
-
-// ---- diagnostics reduction ---------------------------------------------------------------
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Compensated FP32 sum (Kahan): the error of a thread's partial sum stays near one FP32
-// rounding of the sum whatever the number of terms, so the per-node work runs on the FP32
-// pipe and only the cross-thread combination needs FP64 (whose issue rate on this part is a
-// small fraction of FP32's).  No product is involved, so no FMA contraction can undo it.
-struct KahanF {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
-template <typename T>
-__global__ void __launch_bounds__(REDUCE_THREADS, 4) k_reduce(const T* d, const uint8_t* flags,
-                                                              size_t N, double* partials) {
-  unsigned count = 0;
-  KahanF acc[5];
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    if (flags[idx] & (F_SOLID | F_GHOST)) continue;
-    float dd[27];
-#pragma unroll
-    for (int k = 0; k < 27; ++k) dd[k] = load_pop(d + (size_t)k * N + idx);
-    float drho, jx, jy, jz;
-    macros(dd, drho, jx, jy, jz);
-    ++count;
-    acc[0].add(drho);
-    acc[1].add(jx);
-    acc[2].add(jy);
-    acc[3].add(jz);
-    acc[4].add(0.5f * (jx * jx + jy * jy + jz * jz) / (1.0f + drho));
-  }
-  __shared__ double sh[REDUCE_THREADS / 32][6];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const double w = warp_sum(i == 0 ? (double)count : acc[i - 1].value());
-    if (lane == 0) sh[wid][i] = w;
-  }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    double s = 0;
-    for (int w = 0; w < REDUCE_THREADS / 32; ++w) s += sh[w][threadIdx.x];
-    partials[blockIdx.x * 6 + threadIdx.x] = s;
-  }
-}
-
-__global__ void k_reduce_final(const double* partials, int n, double* out) {
-  if (threadIdx.x < 6) {
-    double s = 0;
-    for (int b = 0; b < n; ++b) s += partials[b * 6 + threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-}
-
-cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
-                          double* partials, double* out, cudaStream_t s) {
-  if (storage == ST_FP16)
-    k_reduce<__half><<<REDUCE_CTAS, REDUCE_THREADS, 0, s>>>((const __half*)d, flags, N, partials);
-  else
-    k_reduce<float><<<REDUCE_CTAS, REDUCE_THREADS, 0, s>>>((const float*)d, flags, N, partials);
-  k_reduce_final<<<1, 32, 0, s>>>(partials, REDUCE_CTAS, out);
   return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -151,6 +152,11 @@ lbm_status Domain::sync_and_check() {
   post_error_probe();
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  return error_status();
+}
+
+// Interprets the error word last copied to the host by post_error_probe.
+lbm_status Domain::error_status() {
   if (*h_err & 1) return fail(LBM_ERR_DIVERGED, "non-finite or non-positive density detected");
   if (*h_err & 4) return fail(LBM_ERR_DIVERGED, "an inflow record outside the block or on an obstacle/ghost node was skipped");
   if (*h_err & 8) return fail(LBM_ERR_TIMEOUT, "a bounded device wait gave up");
@@ -230,7 +236,9 @@ lbm_status lbm_create_domain(const lbm_domain_desc* desc, lbm_domain** out) {
 
   Domain* dom = new (std::nothrow) Domain();
   if (!dom) { g_create_error = "out of host memory"; return LBM_ERR_OOM; }
+  static std::atomic<unsigned long long> next_serial{1};
   dom->desc = *desc;
+  dom->serial = next_serial++;
   dom->elt = desc->storage == LBM_FP16_SHIFTED ? 2 : 4;
   if (desc->cuda_stream) {
     dom->stream = static_cast<cudaStream_t>(desc->cuda_stream);
@@ -488,6 +496,45 @@ lbm_status lbm_reduce(lbm_domain* dom, int32_t block_id, double out[5]) {
   out[3] = r[4];
   out[4] = r[5];
   return st;
+}
+
+lbm_status lbm_reduce_batch(lbm_domain* const* doms, int32_t n, int32_t block_id, double* out) {
+  if (!doms || n <= 0 || !out) return LBM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!doms[i]) return LBM_ERR_INVALID_ARG;
+    cudaSetDevice(doms[i]->desc.device);
+    const lbm_status st = doms[i]->check_block(block_id);
+    if (st != LBM_OK) return st;
+  }
+  // queue every reduction and its read-back before waiting on any stream
+  for (int i = 0; i < n; ++i) {
+    lbm_domain* d = doms[i];
+    cudaSetDevice(d->desc.device);
+    Block& B = d->blocks[block_id];
+    cudaError_t e = launch_reduce(B.lv[B.cur].f, d->desc.storage, B.flags, B.N, d->d_partials,
+                                  d->d_red, d->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d->h_red, d->d_red, 6 * sizeof(double), cudaMemcpyDeviceToHost, d->stream);
+    if (e != cudaSuccess) return d->cuda_fail(e, "reduce");
+    d->post_error_probe();
+  }
+  lbm_status first = LBM_OK;
+  for (int i = 0; i < n; ++i) {
+    lbm_domain* d = doms[i];
+    cudaSetDevice(d->desc.device);
+    const cudaError_t e = cudaStreamSynchronize(d->stream);
+    const lbm_status st = e != cudaSuccess ? d->cuda_fail(e, "cudaStreamSynchronize")
+                                           : d->error_status();
+    if (st != LBM_OK && first == LBM_OK) first = st;
+    const double* r = d->h_red;
+    double* o = out + 5 * (size_t)i;
+    o[0] = r[0] + r[1];
+    o[1] = r[2];
+    o[2] = r[3];
+    o[3] = r[4];
+    o[4] = r[5];
+  }
+  return first;
 }
 
 lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block_info* info) {

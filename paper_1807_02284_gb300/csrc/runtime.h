@@ -52,6 +52,7 @@ struct GraphCache;         // captured step graphs (scheduler.cu)
 
 struct lbm_domain {
   lbm_domain_desc desc{};
+  unsigned long long serial = 0;        // unique per created domain (keys cached batch plans)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t elt = 4;
@@ -72,7 +73,7 @@ struct lbm_domain {
   long long steps = 0;
   lbm::TapeState* tape = nullptr;
   lbm::GraphCache* graphs = nullptr;
-  void* batch_plan = nullptr;           // cached plan of lbm_step_batch (batch.cu)
+  void* batch_plan = nullptr;           // cached plans of lbm_step_batch (batch.cu)
   cudaStream_t aux_stream = nullptr;    // second stream for concurrent mapping launches
   std::vector<cudaEvent_t> events;      // fork / join events (timing disabled)
 
@@ -96,6 +97,7 @@ struct lbm_domain {
   lbm_status check_block(int32_t b);
   void post_error_probe();
   lbm_status sync_and_check();
+  lbm_status error_status();
   lbm_status reset_error_word();
   void pick_tiles(int b);
   lbm_status autotune_tiles(int b);

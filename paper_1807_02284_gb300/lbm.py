@@ -76,6 +76,7 @@ _SIGNATURES = {
     "lbm_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
     "lbm_get_block_info": (_I, [_P, _I, C.POINTER(lbm_block_info)]),
     "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
+    "lbm_reduce_batch": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
     "lbm_set_tape": (_I, [_P, _I]),
     "lbm_adjoint_step": (_I, [_P, _I, _P, _P, _P, _P]),
     "lbm_reduce_noalloc": (_I, [_P, _I, _P, C.c_int64, _P, _P]),
@@ -294,3 +295,14 @@ def step_batch(domains: Sequence[Domain], steps: int):
     st = lib.lbm_step_batch(arr, len(domains), int(steps))
     if st != LBM_OK:
         domains[0].check(st)
+
+
+def reduce_batch(domains: Sequence[Domain], block: int = 0) -> np.ndarray:
+    """``lbm_reduce_batch``: the five diagnostics of every domain, shape (n, 5)."""
+    lib = load()
+    arr = (C.c_void_p * len(domains))(*[d.handle.value for d in domains])
+    out = (C.c_double * (5 * len(domains)))()
+    st = lib.lbm_reduce_batch(arr, len(domains), int(block), out)
+    if st != LBM_OK:
+        domains[0].check(st)
+    return np.array(list(out)).reshape(len(domains), 5)

@@ -36,6 +36,49 @@ def test_batch_is_bit_identical_to_single_domain_steps(lib, storage):
         d.close()
 
 
+def test_batch_single_steps_reuse_plans_and_stay_identical(lib):
+    """Repeated one-step calls flip every member's level each time (two cached plans in
+    turn); a member destroyed and replaced between calls must not be stepped through a stale
+    plan.  Results stay bit-identical to single-domain stepping."""
+    from paper_1807_02284_gb300 import lbm
+    scenes = _scenes(5, seed=42)
+    batched = [gpu_domain(s) for s in scenes]
+    single = [gpu_domain(s) for s in scenes]
+    for _ in range(5):
+        lbm.step_batch(batched, 1)
+        for d in single:
+            d.step(1)
+    batched[2].close()
+    single[2].close()
+    batched[2] = gpu_domain(scenes[2])
+    single[2] = gpu_domain(scenes[2])
+    for _ in range(3):
+        lbm.step_batch(batched, 1)
+        for d in single:
+            d.step(1)
+    for a, b in zip(batched, single):
+        assert np.array_equal(a.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32),
+                              b.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32))
+    for d in batched + single:
+        d.close()
+
+
+def test_reduce_batch_equals_per_domain_reduce(lib):
+    from paper_1807_02284_gb300 import lbm
+    scenes = _scenes(6, seed=43)
+    doms = [gpu_domain(s) for s in scenes]
+    lbm.step_batch(doms, 7)
+    r = lbm.reduce_batch(doms)
+    assert r.shape == (6, 5)
+    for i, d in enumerate(doms):
+        assert np.array_equal(r[i], d.reduce())
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.reduce_batch(doms, block=1)
+    assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
+    for d in doms:
+        d.close()
+
+
 def test_batch_matches_oracle(lib):
     from paper_1807_02284_gb300 import lbm
     scenes = _scenes(4, seed=41, lo=10, hi=22)
