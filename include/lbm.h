@@ -146,7 +146,9 @@ lbm_status lbm_destroy_domain(lbm_domain* dom);
    h = dx_s/dx_0 in (0, 1); dims >= 4 per axis.  The whole block must lie inside block 0
    and inside every block it is nested in; its outermost node layer is the scale boundary
    (ghost layer) written by prior-mapping.  Blocks must be added coarse to fine (h not
-   increasing).  UNSUPPORTED for h >= 1 (far-field scales) and for FP16 storage. */
+   increasing).  UNSUPPORTED for h >= 1 (far-field scales) and for FP16 storage; STATE while
+   an adjoint tape is recording; OOM / CUDA when a buffer or table cannot be created, in
+   which case the domain is left exactly as before the call. */
 lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3], double h,
                                const int32_t dims[3], int32_t* block_id);
 

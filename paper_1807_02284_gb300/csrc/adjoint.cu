@@ -327,7 +327,10 @@ lbm_status tape_before_step(lbm_domain* dom) {
   Block& B = dom->blocks[0];
   while (t->ckpt.size() <= i) {
     Level L;
-    if (!alloc_level(dom, B.N, L)) return dom->fail(LBM_ERR_OOM, "checkpoint allocation failed");
+    if (!alloc_level(dom, B.N, L)) {
+      free_level(dom, L);
+      return dom->fail(LBM_ERR_OOM, "checkpoint allocation failed");
+    }
     t->ckpt.push_back(L);
   }
   const Level& S = B.lv[B.cur];
@@ -399,7 +402,10 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
   const int seg_len = std::min(t->every, std::max(1, n_steps));
   while ((int)t->seg.size() < seg_len) {
     Level L;
-    if (!alloc_level(dom, N, L)) return dom->fail(LBM_ERR_OOM, "recompute levels");
+    if (!alloc_level(dom, N, L)) {
+      free_level(dom, L);
+      return dom->fail(LBM_ERR_OOM, "recompute levels");
+    }
     t->seg.push_back(L);
   }
   if (t->ckpt.empty()) {  // no step was taken: the checkpoint of step 0 is the current state

@@ -231,16 +231,41 @@ bool contains(const Block& outer, const Block& inner) {
 
 }  // namespace
 
+// The table's entry count is set only once its device copy exists, so a failed upload can
+// never leave a launchable table without storage.
 static lbm_status upload_table(lbm_domain* dom, const std::vector<MapEntry>& h, MapTable* t) {
-  t->n = (int)h.size();
+  t->n = 0;
+  t->d = nullptr;
   if (h.empty()) return LBM_OK;
-  t->d = static_cast<MapEntry*>(dom->dev_alloc(h.size() * sizeof(MapEntry)));
-  if (!t->d) return dom->fail(LBM_ERR_OOM, "mapping table allocation failed");
-  cudaError_t e = cudaMemcpyAsync(t->d, h.data(), h.size() * sizeof(MapEntry),
+  MapEntry* d = static_cast<MapEntry*>(dom->dev_alloc(h.size() * sizeof(MapEntry)));
+  if (!d) return dom->fail(LBM_ERR_OOM, "mapping table allocation failed");
+  cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(MapEntry),
                                   cudaMemcpyHostToDevice, dom->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(dom->stream);
-  if (e != cudaSuccess) return dom->cuda_fail(e, "mapping table upload");
+  if (e != cudaSuccess) {
+    dom->dev_free(d);
+    return dom->cuda_fail(e, "mapping table upload");
+  }
+  t->d = d;
+  t->n = (int)h.size();
   return LBM_OK;
+}
+
+// Frees every device buffer of a block that is not (or no longer) part of the domain.
+static void release_block(lbm_domain* dom, Block& B) {
+  for (Level& L : B.lv) {
+    dom->dev_free(L.f);
+    dom->dev_free(L.u);
+    dom->dev_free(L.c);
+    L = Level();
+  }
+  dom->dev_free(B.flags);
+  B.flags = nullptr;
+  dom->dev_free(B.prior.d);
+  B.prior.d = nullptr;
+  B.prior.n = 0;
+  for (MapTable& t : B.post) dom->dev_free(t.d);
+  B.post.clear();
 }
 
 extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3], double h,
@@ -253,6 +278,8 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
     return dom->fail(LBM_ERR_UNSUPPORTED, "scales coarser than the reference scale (far field) are not built");
   if (dom->desc.storage != LBM_FP32)
     return dom->fail(LBM_ERR_UNSUPPORTED, "refined blocks need FP32 storage");
+  if (dom->tape)
+    return dom->fail(LBM_ERR_STATE, "blocks cannot be added while an adjoint tape is recording");
   for (int a = 0; a < 3; ++a)
     if (dims[a] < 4) return dom->fail(LBM_ERR_INVALID_ARG, "refined blocks need >= 4 nodes per axis");
   if ((double)dims[0] * dims[1] * dims[2] * 27.0 >= 4294967295.0)
@@ -291,13 +318,24 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
   const int id = (int)dom->blocks.size();
 
   lbm_status st = dom->alloc_block_levels(B, 3);
-  if (st != LBM_OK) return st;
+  if (st != LBM_OK) {
+    release_block(dom, B);
+    return st;
+  }
+  // From here on the block is in the domain; any failure takes it out again, with its
+  // buffers and tables, so that no later step can launch on a half-built block.
   dom->blocks.push_back(B);
+  auto abandon = [dom](lbm_status s) {
+    cudaStreamSynchronize(dom->stream);
+    release_block(dom, dom->blocks.back());
+    dom->blocks.pop_back();
+    return s;
+  };
   Block& NB = dom->blocks.back();
   st = dom->clear_block(id);
-  if (st != LBM_OK) return st;
+  if (st != LBM_OK) return abandon(st);
   cudaError_t e = launch_set_ghost_layer(NB.flags, NB.nx, NB.ny, NB.nz, dom->stream);
-  if (e != cudaSuccess) return dom->cuda_fail(e, "ghost flags");
+  if (e != cudaSuccess) return abandon(dom->cuda_fail(e, "ghost flags"));
 
   // prior table: ghost nodes of the new block -> cells of the parent
   {
@@ -322,7 +360,7 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
     NB.prior.dst = id;
     NB.prior.khat = (float)khat(P, NB);
     st = upload_table(dom, tab, &NB.prior);
-    if (st != LBM_OK) return st;
+    if (st != LBM_OK) return abandon(st);
   }
   // post tables: nodes of every coarser block inside the new block's interior span
   for (int k = 0; k < id; ++k) {
@@ -360,7 +398,7 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
             tab.push_back(m);
           }
       st = upload_table(dom, tab, &mt);
-      if (st != LBM_OK) return st;
+      if (st != LBM_OK) return abandon(st);
     }
     NB.post.push_back(mt);
   }

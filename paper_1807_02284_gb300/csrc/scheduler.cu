@@ -155,6 +155,7 @@ const void* lbm_domain::upload_small(const void* src, size_t bytes, lbm_status* 
     small_host = nullptr;
     dev_free(small_dev);
     small_dev = nullptr;
+    small_bytes = 0;       // no buffer until both allocations below succeed
     size_t cap = std::max<size_t>(bytes, 4096);
     if (cudaMallocHost(&small_host, cap) != cudaSuccess) {
       small_host = nullptr;

@@ -69,6 +69,19 @@ def test_adjoint_matches_fp64_oracle(lib, n, steps, every, sphere):
     assert e <= 1e-3
 
 
+def test_adjoint_fixed_rates_matches_fp64_oracle(lib):
+    """Fixed high-order rates (adaptive factor off, phi = 1): no gradient flows through the
+    lagged velocity field, only through populations and the scalar."""
+    sc, target = synth.adjoint_scene(n=12, seed=6, nu=0.01, amp=0.05)
+    sc.adaptive = False
+    Lg, gg, _ = gpu_grad(sc, target, 10, 4)
+    Lo, go, _ = oracle_grad(sc, target, 10)
+    e = rel(gg, go.numpy())
+    print(f"adjoint fixed rates: rel L2 grad err {e:.2e}")
+    assert abs(Lg - Lo) <= 1e-4 * abs(Lo)
+    assert e <= 1e-3
+
+
 def test_adjoint_config5_copy_32_cubed_200_steps(lib):
     """The smoke-control problem scaled to 32^3 (every length / 4), nu = 1e-3, 200 steps,
     checkpoint every 20: FP32 GPU adjoint against the FP64 oracle gradient."""
