@@ -164,17 +164,22 @@ def _algorithmic_bytes(flags, storage, local=False):
     return fluid * per_fluid + solid * per_solid + inflow * per_inflow, per_fluid
 
 
-def cpu_baseline_measure(budget_s=15.0):
+def cpu_baseline_measure(budget_s=15.0, storage="fp32"):
     """The FP64 oracle as it stands, on a bounded sample of the plume workload: the same
     scene geometry scaled to a 32^3 box (inflow disk, sphere, open faces), stepped until
-    about ``budget_s`` seconds of CPU time have been spent."""
+    about ``budget_s`` seconds of CPU time have been spent.  The GPU path then runs the same
+    sample from the same (float32-rounded) inputs for the same number of steps, and the
+    velocity error against the oracle is reported with the timing."""
     import torch
 
     import synth
     from oracle import grid
+    from paper_1807_02284_gb300 import lbm
     sc = synth.plume(32)
     b = sc.blocks[0]
-    st = grid.init_state(b.rho0, b.u0, b.c0, b.flags)
+    r32 = lambda a: np.asarray(a, dtype=np.float32)
+    st = grid.init_state(r32(b.rho0).astype(np.float64), r32(b.u0).astype(np.float64),
+                         r32(b.c0).astype(np.float64), b.flags)
     p = grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=sc.adaptive, c_src=sc.c_src)
     st = grid.step(st, p)  # warm-up
     n = 0
@@ -186,10 +191,24 @@ def cpu_baseline_measure(budget_s=15.0):
         if el >= budget_s:
             break
     mlups = b.flags.size * n / el / 1e6
+    dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, storage=storage,
+                     adaptive=sc.adaptive, c_src=sc.c_src)
+    dom.set_flags(b.flags)
+    dom.init_macro(r32(b.u0), rho=r32(b.rho0), c=r32(b.c0))
+    dom.step(n + 1)
+    u = dom.read_field(lbm.LBM_FIELD_U, lbm.LBM_F64).reshape(st.u.shape)
+    c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64).reshape(st.c.shape)
+    dom.close()
+    uo = st.u.numpy()
+    umax = float(np.abs(uo).max())
     return {"value": mlups, "unit": "MLUPS", "cores": int(torch.get_num_threads()),
             "kind": "oracle",
             "sample": f"oracle (FP64, dense per-node M and LU solve) on the plume geometry "
-                      f"scaled to 32^3, {n} full steps in {el:.1f} s"}
+                      f"scaled to 32^3, {n} full steps in {el:.1f} s",
+            "parity": {"steps": n + 1, "storage": storage,
+                       "u_max_abs_err_rel": float(np.abs(u - uo).max()) / umax,
+                       "scalar_max_abs_err": float(np.abs(c - st.c.numpy()).max()),
+                       "bound_u_rel": 1e-5 if storage == "fp32" else None}}
 
 
 def run_reference(args):
@@ -347,7 +366,7 @@ def run_ours(args):
                 "clocks": clk,
                 "mass_check": float(red[0])}
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline_measure(args.cpu_budget)
+            line["cpu_baseline"] = cpu_baseline_measure(args.cpu_budget, storage)
         if ws == 1 and args.workload == "plume256" and not args.no_variants:
             line["variants"] = _variants(args)
         print(json.dumps(line), flush=True)
