@@ -1,0 +1,139 @@
+"""Dynamic scale construction (Sec. 5) — test infrastructure, never part of the product path.
+
+Plain FP64 restatement of how a dynamic scale is found, placed and started:
+
+  1. detection (Sec. 5): on a block's stored velocity field, keep the samples whose gradient
+     magnitude is at least g_threshold, then of those the samples whose velocity magnitude is
+     at least u_threshold; what remains is one dynamic-scale region;
+  2. placement: the region becomes a box block of spacing h;
+  3. start: the new block's samples are mapped from the coarser scale it is overlaid on
+     (Sec. 3.2 mapping with K_hat, at the current time), after any previous dynamic scale
+     has been discarded.
+
+Readings (the paper describes the procedure in words only):
+  * The gradient magnitude is the Frobenius norm of the central-difference Jacobian of the
+    stored velocity, the quantity the adaptive factor uses (grid.lagged_gradient_norm), in
+    the detection block's lattice units; the velocity magnitude is |u|.  Obstacle voxels and
+    ghost nodes are never selected.  The two thresholds applied one after the other select
+    the same samples as their conjunction.
+  * The region is represented by its axis-aligned bounding box in the detection block's node
+    indices, widened by `margin` of those nodes on every side and clipped to the reference
+    block [0, n_0 - 1] (reference units).  The new block starts at the clipped lower corner;
+    it has floor(extent / h + 1e-9) + 1 nodes per axis, at least 4, shifted down (not below
+    0) when 4 nodes would pass the reference block's upper end.
+  * Obstacle and scalar-source bits of the new block come from the nearest node of the
+    detection block (index floor(q + 1/2) of the node's position q in that block's node
+    units, clamped to the block); its outermost layer is its ghost layer.
+  * Every non-obstacle node of the new block, ghost layer included, is set to the mapping of
+    its prior-mapping source (the finest coarser block containing it) at the current time;
+    its velocity is that of the mapped populations and its scalar is interpolated.  Obstacle
+    nodes hold the rest state.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import cmr, coupling, grid
+from .cmr import DT
+
+SOLID, INFLOW, SCALAR_SRC, GHOST = grid.SOLID, grid.INFLOW, grid.SCALAR_SRC, grid.GHOST
+
+
+def detect(state: grid.State, periodic, g_threshold: float, u_threshold: float):
+    """(count, box) of the selected samples; box = (x0, y0, z0, x1, y1, z1) inclusive node
+    indices, or None when nothing is selected.  Also returns the per-node gradient and
+    velocity magnitudes (for tie checks in tests)."""
+    _, Z, Y, X = state.u.shape
+    z, y, x = torch.meshgrid(torch.arange(Z), torch.arange(Y), torch.arange(X), indexing="ij")
+    g = grid.lagged_gradient_norm(state.u, periodic, z, y, x)
+    umag = torch.sqrt((state.u ** 2).sum(0))
+    excluded = (state.flags & (SOLID | GHOST)) != 0
+    keep = (g >= g_threshold) & ~excluded          # first threshold: gradient magnitude
+    keep = keep & (umag >= u_threshold)             # second threshold: velocity magnitude
+    n = int(keep.sum())
+    if n == 0:
+        return 0, None, g, umag
+    zz, yy, xx = torch.nonzero(keep, as_tuple=True)
+    box = (int(xx.min()), int(yy.min()), int(zz.min()), int(xx.max()), int(yy.max()), int(zz.max()))
+    return n, box, g, umag
+
+
+def place(box, src_origin, src_h: float, h: float, margin: int, ref_dims):
+    """Origin (reference units) and node counts of the dynamic block for a detection box of
+    a block with origin src_origin and spacing src_h."""
+    origin, dims = [], []
+    for a in range(3):
+        lo = src_origin[a] + (box[a] - margin) * src_h
+        hi = src_origin[a] + (box[3 + a] + margin) * src_h
+        top = float(ref_dims[a] - 1)
+        lo = max(lo, 0.0)
+        hi = min(hi, top)
+        n = max(int(math.floor((hi - lo) / h + 1e-9)) + 1, 4)
+        if lo + (n - 1) * h > top + 1e-9:
+            lo = max(0.0, top - (n - 1) * h)
+        origin.append(lo)
+        dims.append(n)
+    return tuple(origin), tuple(dims)
+
+
+def nearest_flags(src: coupling.Blk, origin, h: float, dims):
+    """Obstacle / scalar-source bits of a new block from the nearest source node, plus its
+    ghost layer.  Returns uint8 flags shaped (z, y, x)."""
+    nx, ny, nz = dims
+    idx = []
+    for a, n in enumerate((nx, ny, nz)):
+        q = (origin[a] + h * np.arange(n) - src.origin[a]) / src.h
+        i = np.clip(np.floor(q + 0.5).astype(np.int64), 0, src.dims[a] - 1)
+        idx.append(i)
+    sf = src.state.flags.numpy()
+    fl = sf[np.ix_(idx[2], idx[1], idx[0])] & (SOLID | SCALAR_SRC)
+    fl = fl.astype(np.uint8)
+    fl[0, :, :] |= GHOST
+    fl[-1, :, :] |= GHOST
+    fl[:, 0, :] |= GHOST
+    fl[:, -1, :] |= GHOST
+    fl[:, :, 0] |= GHOST
+    fl[:, :, -1] |= GHOST
+    return fl
+
+
+def add_block_from_parent(ms: coupling.MultiScale, origin, h: float, dims, flags_src: int = 0):
+    """Appends a dynamic block to a MultiScale domain and starts it from its parent.
+    ``flags_src`` is the block whose nearest nodes give the obstacle / source bits."""
+    nx, ny, nz = dims
+    flags = nearest_flags(ms.blocks[flags_src], origin, h, dims)
+    zeros = np.zeros((nz, ny, nx))
+    st = grid.init_state(np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)), zeros, flags)
+    ref = ms.blocks[0].params
+    nu_b = ref.nu / h
+    p = grid.Params(nu=nu_b, periodic=(False, False, False), adaptive=ref.adaptive,
+                    c_src=ref.c_src, grad_mode=ref.grad_mode)
+    ratio = 1.0 / h
+    b = coupling.Blk(origin=np.array(origin, dtype=np.float64), h=float(h), dims=tuple(dims),
+                     state=st, params=p, substeps=max(1, math.ceil(ratio - 1e-9)),
+                     integer_ratio=abs(ratio - round(ratio)) < 1e-9)
+    ms.blocks.append(b)
+    i = len(ms.blocks) - 1
+    b.parent = ms._containing_parent(i)
+    par = ms.blocks[b.parent]
+    z, y, x = torch.nonzero((st.flags & SOLID) == 0, as_tuple=True)
+    f, c, ok = coupling.interpolate(par, par.state.f, par.state.c,
+                                    coupling.node_positions(b, z, y, x))
+    z, y, x, f, c = z[ok], y[ok], x[ok], f[ok], c[ok]
+    fm = coupling.map_populations(f, coupling.k_hat(par, b))
+    _, u = cmr.macros(fm)
+    st.f[:, z, y, x] = fm.T
+    st.u[:, z, y, x] = u.T
+    st.c[z, y, x] = c
+    return i
+
+
+def remove_last_block(ms: coupling.MultiScale):
+    """Discards the most recently added block (its interior was post-mapped into every
+    coarser block at the end of each reference step)."""
+    if len(ms.blocks) < 2:
+        raise ValueError("only refined blocks can be removed")
+    ms.blocks.pop()
