@@ -548,6 +548,87 @@ def run_adjoint(args, emit=True):
     return out
 
 
+def run_dynamic(args, emit=True):
+    """256^3 plume with a dynamic scale (Sec. 5) at h = 1/2 over the developed jet, rebuilt
+    every 40 steps from the gradient and velocity thresholds.  value = lattice updates of all
+    blocks per second (sub-cycled updates counted), rebuilds (detection, removal, placement,
+    start from the coarse scale, graph re-capture) included in the timed region."""
+    import torch
+
+    from paper_1807_02284_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    sc, _ = _workload("plume256")
+    b = sc.blocks[0]
+    stream = torch.cuda.Stream()
+    dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, adaptive=sc.adaptive,
+                     c_src=sc.c_src, stream=stream)
+    dom.set_flags(b.flags)
+    dom.init_macro(b.u0.astype(np.float32), rho=b.rho0.astype(np.float32),
+                   c=b.c0.astype(np.float32))
+    N0 = b.flags.size
+    dom.step(400)                                  # develop the jet before tracking it
+    u_thr, g_thr = 0.05, 0.02                      # |u| above half the inflow speed
+    for _ in range(10):                            # gradient threshold: region >= 0.2 % of s0
+        n, _ = dom.detect_region(g_thr, u_thr)
+        if n >= 0.002 * N0:
+            break
+        g_thr *= 0.5
+    h, every, margin = 0.5, 40, 4
+    K, W = max(args.steps, every), args.warmup
+    bid = dom.build_dynamic_scale(h, g_thr, u_thr, margin=margin)
+    dom.step(W)
+    dom.sync()
+    # detection kernel alone: bytes = stored velocity (12 B) + flags (1 B) per node
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dom.detect_region(g_thr, u_thr)
+    e1.record(stream)
+    e1.synchronize()
+    t_det = e0.elapsed_time(e1) / 1e3
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    lu, alg, sizes = 0, 0, []
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    done = 0
+    while done < K:
+        bid = dom.build_dynamic_scale(h, g_thr, u_thr, margin=margin, replace_last=bid > 0)
+        n = min(every, K - done)
+        per_step = N0
+        if bid > 0:
+            i = dom.info(bid)
+            nf = int(i.dims[0]) * int(i.dims[1]) * int(i.dims[2])
+            per_step += int(i.substeps) * nf
+            sizes.append(tuple(int(v) for v in i.dims))
+        dom.step(n)
+        lu += n * per_step
+        done += n
+    ev1.record(stream)
+    ev1.synchronize()
+    clk = clocks.stop()
+    dom.sync()
+    t = ev0.elapsed_time(ev1) / 1e3
+    peak, peak_src = _peaks()
+    achieved = lu * 249 / t / 1e9
+    out = {"metric": "MLUPS", "value": lu / t / 1e6, "unit": "MLUPS", "steps": K,
+           "ms_per_step": t / K * 1e3, "higher_is_better": True, "dtype": "f32",
+           "config": {"workload": "dynamic256_fp32", "reference_nodes": int(N0), "h": h,
+                      "rebuild_every": every, "g_threshold": g_thr, "u_threshold": u_thr,
+                      "margin": margin, "dynamic_block_dims": sizes},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                        "kernel": "k_step over all blocks (249 B per update), rebuilds included"},
+           "detect": {"ms_per_call": t_det * 1e3, "gb_per_s": N0 * 13 / t_det / 1e9,
+                      "note": "k_detect_init + k_detect + read-back and synchronisation"},
+           "clocks": clk}
+    dom.close()
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
+
+
 def _variants(args):
     """Measured summaries of the other hot-path variants for the default bench line."""
     import copy
@@ -558,6 +639,7 @@ def _variants(args):
     for name, fn, steps, warm in (("plume256_fp16", run_ours, 100, 10),
                                   ("plume256_local", run_ours, 100, 10),
                                   ("multiscale3", run_ours, 50, 5),
+                                  ("dynamic256", run_dynamic, 200, 10),
                                   ("batch64", run_batch, 100, 10),
                                   ("adjoint128", run_adjoint, 200, 0)):
         a = copy.copy(args)
@@ -568,7 +650,7 @@ def _variants(args):
                 fn(a)
             d = json.loads(buf.getvalue().strip().splitlines()[-1])
             res[name] = {k: d[k] for k in ("value", "unit", "ms_per_step", "roofline", "e2e",
-                                           "forward_with_tape_mlups", "config")
+                                           "forward_with_tape_mlups", "config", "detect")
                          if k in d}
         except Exception as ex:  # report, do not hide
             res[name] = {"error": f"{type(ex).__name__}: {ex}"}
@@ -583,7 +665,7 @@ def main():
     ap.add_argument("--workload", default="plume256",
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
                              "multiscale3", "batch64", "adjoint128", "adjoint64",
-                             "plume256_local"])
+                             "plume256_local", "dynamic256"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -596,6 +678,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "dynamic256":
+        run_dynamic(args)
     else:
         run_ours(args)
 

@@ -152,6 +152,45 @@ lbm_status lbm_destroy_domain(lbm_domain* dom);
 lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3], double h,
                                const int32_t dims[3], int32_t* block_id);
 
+/* Removes the most recently added refined block (Sec. 5: dynamic scales are discarded and
+   rebuilt; the block's interior has already been post-mapped into every coarser block at
+   the end of each reference step).  Waits for the domain's stream, then releases the
+   block's buffers and tables.  INVALID_ARG unless block_id is the last block and >= 1;
+   STATE while an adjoint tape is recording. */
+lbm_status lbm_remove_scale_block(lbm_domain* dom, int32_t block_id);
+
+/* Dynamic scale construction, detection (Sec. 5): among the nodes of a block that are
+   neither obstacle voxels nor ghost nodes, keeps those whose velocity-gradient magnitude
+   (Frobenius norm of the central-difference Jacobian of the stored velocity, the quantity
+   of the adaptive factor, Sec. 4.1) is >= g_threshold and whose |u| is >= u_threshold.
+   Writes their number to *count and their bounding box, in the block's node indices, to
+   box = {x0, y0, z0, x1, y1, z1} (inclusive; {0,0,0,-1,-1,-1} when count is 0).  The
+   thresholds are compared in FP32.  Synchronises; deterministic. */
+lbm_status lbm_detect_region(lbm_domain* dom, int32_t block_id, double g_threshold,
+                             double u_threshold, int64_t* count, int32_t box[6]);
+
+/* Starts a refined block from its prior-mapping source at the current time (Sec. 5 start of
+   a dynamic scale): obstacle and scalar-source bits come from the source's nearest node
+   (index floor(q + 1/2), q the node's position in the source's node units), every other
+   node gets the Sec. 3.2 mapping (trilinear, obstacle corners dropped, K_hat rescale) of the
+   source's current populations, with the velocity of the mapped populations and the
+   interpolated scalar; obstacle nodes hold the rest state.  INVALID_ARG for block 0. */
+lbm_status lbm_init_block_from_parent(lbm_domain* dom, int32_t block_id);
+
+/* Dynamic scale construction (Sec. 5), in one call: lbm_detect_region on src_block, then
+   (replace_last != 0) lbm_remove_scale_block of the last block, then, if any node was kept,
+   a block of spacing h (0 < h < 1) placed on the detection box widened by `margin` source
+   nodes on every side and clipped to the reference block: origin = clipped lower corner
+   (reference units), floor(extent / h + 1e-9) + 1 nodes per axis, at least 4 (shifted down,
+   not below 0, when they would pass the reference block's upper end); it is added with
+   lbm_add_scale_block and started with lbm_init_block_from_parent.  *block_id receives the
+   new block's id, or -1 when nothing was kept.  The paper repeats this every 40 steps.
+   INVALID_ARG for bad arguments (replace_last needs a refined last block that is not the
+   source block); the errors of the calls it makes otherwise. */
+lbm_status lbm_build_dynamic_scale(lbm_domain* dom, int32_t src_block, double h,
+                                   double g_threshold, double u_threshold, int32_t margin,
+                                   int32_t replace_last, int32_t* block_id);
+
 /* Sets boundary data of one block (see LBM_BC_*).  ptr/nbytes describe the caller array;
    it is copied before return (host) or before the next enqueued work (device). */
 lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, const void* ptr,

@@ -21,9 +21,11 @@ Readings (the paper describes the procedure in words only):
     block [0, n_0 - 1] (reference units).  The new block starts at the clipped lower corner;
     it has floor(extent / h + 1e-9) + 1 nodes per axis, at least 4, shifted down (not below
     0) when 4 nodes would pass the reference block's upper end.
-  * Obstacle and scalar-source bits of the new block come from the nearest node of the
-    detection block (index floor(q + 1/2) of the node's position q in that block's node
-    units, clamped to the block); its outermost layer is its ghost layer.
+  * Obstacle and scalar-source bits of the new block come from the nearest node of its
+    prior-mapping source (index floor(q + 1/2) of the node's position q in that block's node
+    units, clamped to the block); its outermost layer is its ghost layer.  (With the
+    reference block as detection block and source, as in the paper's jet flows, the two
+    are the same block.)
   * Every non-obstacle node of the new block, ghost layer included, is set to the mapping of
     its prior-mapping source (the finest coarser block containing it) at the current time;
     its velocity is that of the mapped populations and its scalar is interpolated.  Obstacle
@@ -100,18 +102,18 @@ def nearest_flags(src: coupling.Blk, origin, h: float, dims):
     return fl
 
 
-def add_block_from_parent(ms: coupling.MultiScale, origin, h: float, dims, flags_src: int = 0):
-    """Appends a dynamic block to a MultiScale domain and starts it from its parent.
-    ``flags_src`` is the block whose nearest nodes give the obstacle / source bits."""
+def add_block_from_parent(ms: coupling.MultiScale, origin, h: float, dims):
+    """Appends a dynamic block to a MultiScale domain and starts it from its parent (the
+    finest coarser block containing it), which also gives its obstacle / source bits."""
     nx, ny, nz = dims
-    flags = nearest_flags(ms.blocks[flags_src], origin, h, dims)
-    zeros = np.zeros((nz, ny, nx))
-    st = grid.init_state(np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)), zeros, flags)
     ref = ms.blocks[0].params
     nu_b = ref.nu / h
     p = grid.Params(nu=nu_b, periodic=(False, False, False), adaptive=ref.adaptive,
                     c_src=ref.c_src, grad_mode=ref.grad_mode)
     ratio = 1.0 / h
+    zeros = np.zeros((nz, ny, nx))
+    st = grid.init_state(np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)), zeros,
+                         np.zeros((nz, ny, nx), np.uint8))
     b = coupling.Blk(origin=np.array(origin, dtype=np.float64), h=float(h), dims=tuple(dims),
                      state=st, params=p, substeps=max(1, math.ceil(ratio - 1e-9)),
                      integer_ratio=abs(ratio - round(ratio)) < 1e-9)
@@ -119,6 +121,9 @@ def add_block_from_parent(ms: coupling.MultiScale, origin, h: float, dims, flags
     i = len(ms.blocks) - 1
     b.parent = ms._containing_parent(i)
     par = ms.blocks[b.parent]
+    flags = torch.as_tensor(nearest_flags(par, origin, h, dims))
+    st = grid.init_state(np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)), zeros, flags)
+    b.state = st
     z, y, x = torch.nonzero((st.flags & SOLID) == 0, as_tuple=True)
     f, c, ok = coupling.interpolate(par, par.state.f, par.state.c,
                                     coupling.node_positions(b, z, y, x))

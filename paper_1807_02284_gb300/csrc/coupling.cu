@@ -30,6 +30,32 @@ namespace lbm {
 //   2. one thread per entry: moments, K_hat rescale, back to populations (Sec. 3.2);
 //   3. one thread per (entry, population) pair: the stores.
 // MODE 0: source level lo only; 1: level hi only; 2: (1 - theta) lo + theta hi.
+// Entry of destination node e of a whole block: the source cell containing the node's
+// position and the fractions inside it, in the same double-precision steps as the host
+// tables (cell_of), so both give identical entries.
+__device__ __forceinline__ MapEntry geometric_entry(const MapArgs& a, uint32_t e) {
+  const uint32_t x = e % (uint32_t)a.dnx, r = e / (uint32_t)a.dnx;
+  const uint32_t y = r % (uint32_t)a.dny, z = r / (uint32_t)a.dny;
+  const uint32_t node[3] = {x, y, z};
+  const int sn[3] = {a.snx, a.sny, a.snz};
+  int i0[3];
+  MapEntry m;
+  float t[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double p = __dadd_rn(a.o_dst[k], __dmul_rn((double)node[k], a.h_dst));  // no FMA
+    const double q = __ddiv_rn(__dsub_rn(p, a.o_src[k]), a.h_src);
+    int i = (int)floor(q);
+    i = max(0, min(i, max(sn[k] - 2, 0)));
+    i0[k] = i;
+    t[k] = (float)(q - (double)i);
+  }
+  m.dst = e;
+  m.src = (uint32_t)(((size_t)i0[2] * a.sny + i0[1]) * a.snx + i0[0]);
+  m.tx = t[0]; m.ty = t[1]; m.tz = t[2];
+  return m;
+}
+
 constexpr int MAP_D = 32;          // entries per CTA
 constexpr int MAP_THREADS = 128;
 constexpr int MAP_LD = 29;         // shared-memory row stride (odd: no bank conflicts)
@@ -52,7 +78,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
     uint32_t sc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     float w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (t < nloc) {
-      const MapEntry m = a.table[e0 + t];
+      const MapEntry m = a.table ? a.table[e0 + t] : geometric_entry(a, (uint32_t)(e0 + t));
       sdst[t] = m.dst;
       if (!(a.dst_flags[m.dst] & a.skip_mask)) {
         const uint32_t sy = (uint32_t)a.snx, sz = (uint32_t)a.snx * (uint32_t)a.sny;
@@ -404,8 +430,24 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
   }
   dom->pick_tiles(id);
   dom->invalidate_graphs();
-  dom->on_state_reset(id);
   *block_id = id;
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_remove_scale_block(lbm_domain* dom, int32_t block_id) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (block_id < 1 || block_id != (int32_t)dom->blocks.size() - 1)
+    return dom->fail(LBM_ERR_INVALID_ARG, "only the most recently added refined block can be removed");
+  if (dom->tape)
+    return dom->fail(LBM_ERR_STATE, "blocks cannot be removed while an adjoint tape is recording");
+  // every launch that may read the block (steps, mappings on the side streams) has been
+  // joined into the domain's stream, so waiting for it makes the buffers free to release
+  const cudaError_t e = cudaStreamSynchronize(dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "cudaStreamSynchronize");
+  release_block(dom, dom->blocks.back());
+  dom->blocks.pop_back();
+  dom->invalidate_graphs();
   return LBM_OK;
 }
 

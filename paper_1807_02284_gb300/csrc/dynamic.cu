@@ -1,0 +1,260 @@
+// Dynamic scale construction (Sec. 5): detection of the samples that need a finer scale,
+// placement of a box block around them, and the start of a new block from the coarser scale
+// it is overlaid on.
+//
+// Detection keeps the nodes whose gradient magnitude (the Frobenius norm of the
+// central-difference Jacobian of the stored velocity, the quantity of the adaptive factor)
+// reaches g_threshold and whose velocity magnitude reaches u_threshold; obstacle and ghost
+// nodes never count.  Count and bounding box are order-independent reductions (sum, min,
+// max), so the result is deterministic.  A new block is placed around the box widened by a
+// margin and clipped to the reference block; its obstacle and scalar-source bits come from
+// the nearest node of its prior-mapping source, and every other node is started from that
+// source by the Sec. 3.2 mapping at the current time.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "lbm_cell.cuh"
+#include "runtime.h"
+
+namespace lbm {
+
+struct RegionOut {
+  unsigned long long count;
+  int lo[3];
+  int hi[3];
+};
+
+__global__ void k_detect_init(RegionOut* out) {
+  out->count = 0ull;
+  for (int a = 0; a < 3; ++a) {
+    out->lo[a] = INT_MAX;
+    out->hi[a] = -1;
+  }
+}
+
+// Persistent over the (y, z) rows of the block, threads along x; per-CTA reduction, then
+// one atomic per quantity and CTA.
+__global__ void __launch_bounds__(256) k_detect(BlockView v, float g_thr, float u_thr,
+                                                RegionOut* out) {
+  const uint32_t N = (uint32_t)v.N;
+  unsigned cnt = 0;
+  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
+  const int rows = v.ny * v.nz;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int y = r % v.ny, z = r / v.ny;
+    for (int x = threadIdx.x; x < v.nx; x += blockDim.x) {
+      const uint32_t idx = ((uint32_t)z * (uint32_t)v.ny + (uint32_t)y) * (uint32_t)v.nx + (uint32_t)x;
+      if (v.flags[idx] & (F_SOLID | F_GHOST)) continue;
+      const Nbr<uint32_t> n = neighbours<uint32_t>(v, x, y, z);
+      const float g = grad_norm<uint32_t>(v.u_in, N, n);
+      const float ux = v.u_in[idx], uy = v.u_in[N + idx], uz = v.u_in[2 * N + idx];
+      const float um = sqrtf(ux * ux + uy * uy + uz * uz);
+      if (g >= g_thr && um >= u_thr) {
+        ++cnt;
+        lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
+        lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
+        lo[2] = min(lo[2], z); hi[2] = max(hi[2], z);
+      }
+    }
+  }
+  const unsigned full = 0xffffffffu;
+  cnt = __reduce_add_sync(full, cnt);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(full, lo[a]);
+    hi[a] = __reduce_max_sync(full, hi[a]);
+  }
+  __shared__ unsigned s_cnt[8];
+  __shared__ int s_lo[8][3], s_hi[8][3];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_cnt[w] = cnt;
+    for (int a = 0; a < 3; ++a) { s_lo[w][a] = lo[a]; s_hi[w][a] = hi[a]; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned c = 0;
+    int l[3] = {INT_MAX, INT_MAX, INT_MAX}, h[3] = {-1, -1, -1};
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      c += s_cnt[i];
+      for (int a = 0; a < 3; ++a) { l[a] = min(l[a], s_lo[i][a]); h[a] = max(h[a], s_hi[i][a]); }
+    }
+    if (c) {
+      atomicAdd(&out->count, (unsigned long long)c);
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&out->lo[a], l[a]);
+        atomicMax(&out->hi[a], h[a]);
+      }
+    }
+  }
+}
+
+// Obstacle and scalar-source bits of a block from the nearest node of another block (index
+// floor(q + 1/2) of the node's position q in the source's node units, clamped); the ghost
+// bit of the destination is kept, every other bit cleared.
+__global__ void k_nearest_flags(uint8_t* dflags, int dnx, int dny, int dnz, double o0, double o1,
+                                double o2, double dh, const uint8_t* sflags, int snx, int sny,
+                                int snz, double s0, double s1, double s2, double sh) {
+  const size_t N = (size_t)dnx * dny * dnz;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int node[3] = {(int)(idx % dnx), (int)((idx / dnx) % dny), (int)(idx / ((size_t)dnx * dny))};
+    const double od[3] = {o0, o1, o2}, os[3] = {s0, s1, s2};
+    const int sn[3] = {snx, sny, snz};
+    int j[3];
+    for (int a = 0; a < 3; ++a) {
+      const double p = __dadd_rn(od[a], __dmul_rn((double)node[a], dh));
+      const double q = __ddiv_rn(__dsub_rn(p, os[a]), sh);
+      j[a] = max(0, min((int)floor(q + 0.5), sn[a] - 1));
+    }
+    const uint8_t src = sflags[((size_t)j[2] * sny + j[1]) * snx + j[0]];
+    dflags[idx] = (uint8_t)((dflags[idx] & F_GHOST) | (src & (F_SOLID | F_SCALAR_SRC)));
+  }
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" lbm_status lbm_detect_region(lbm_domain* dom, int32_t block_id, double g_threshold,
+                                        double u_threshold, int64_t* count, int32_t box[6]) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  lbm_status st = dom->check_block(block_id);
+  if (st != LBM_OK) return st;
+  if (!count || !box) return dom->fail(LBM_ERR_INVALID_ARG, "null output");
+  if (!std::isfinite(g_threshold) || !std::isfinite(u_threshold))
+    return dom->fail(LBM_ERR_INVALID_ARG, "thresholds must be finite");
+  const Block& B = dom->blocks[block_id];
+  if (27ull * B.N >= 0xFFFFFFFFull) return dom->fail(LBM_ERR_UNSUPPORTED, "block too large for detection");
+  // the result area reuses the reduction's read-back buffers (both calls synchronise)
+  RegionOut* d_out = reinterpret_cast<RegionOut*>(dom->d_red);
+  BlockView v = dom->view(block_id, B.cur, B.cur);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dom->desc.device);
+  const int rows = B.ny * B.nz;
+  const int grid = std::max(1, std::min(rows, 8 * std::max(sms, 1)));
+  k_detect_init<<<1, 1, 0, dom->stream>>>(d_out);
+  k_detect<<<grid, 256, 0, dom->stream>>>(v, (float)g_threshold, (float)u_threshold, d_out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dom->h_red, d_out, sizeof(RegionOut), cudaMemcpyDeviceToHost, dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "region detection");
+  st = dom->sync_and_check();
+  if (st != LBM_OK) return st;
+  RegionOut r;
+  std::memcpy(&r, dom->h_red, sizeof(RegionOut));
+  *count = (int64_t)r.count;
+  for (int a = 0; a < 3; ++a) {
+    box[a] = r.count ? r.lo[a] : 0;
+    box[3 + a] = r.count ? r.hi[a] : -1;
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_init_block_from_parent(lbm_domain* dom, int32_t block_id) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  lbm_status st = dom->check_block(block_id);
+  if (st != LBM_OK) return st;
+  if (block_id == 0) return dom->fail(LBM_ERR_INVALID_ARG, "the reference block has no parent");
+  Block& B = dom->blocks[block_id];
+  const Block& P = dom->blocks[B.prior.src];
+  cudaError_t e;
+  {
+    const size_t g = std::min<size_t>((B.N + 255) / 256, 65535);
+    k_nearest_flags<<<(int)g, 256, 0, dom->stream>>>(
+        B.flags, B.nx, B.ny, B.nz, B.origin[0], B.origin[1], B.origin[2], B.h, P.flags, P.nx,
+        P.ny, P.nz, P.origin[0], P.origin[1], P.origin[2], P.h);
+    e = cudaGetLastError();
+  }
+  const int per[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = launch_near_solid(B.flags, B.nx, B.ny, B.nz, per, dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "block flags");
+  st = dom->clear_block(block_id);   // rest state everywhere (obstacle nodes keep it)
+  if (st != LBM_OK) return st;
+  MapArgs a{};
+  a.table = nullptr;
+  a.n = (int)B.N;
+  a.f_lo = a.f_hi = P.lv[P.cur].f;
+  a.c_lo = a.c_hi = P.lv[P.cur].c;
+  a.theta = 0.0f;
+  a.src_flags = P.flags;
+  a.snx = P.nx; a.sny = P.ny; a.snz = P.nz; a.sN = P.N;
+  a.f_dst = B.lv[B.cur].f;
+  a.u_dst = B.lv[B.cur].u;
+  a.c_dst = B.lv[B.cur].c;
+  a.dst_flags = B.flags;
+  a.skip_mask = F_SOLID;
+  a.dN = B.N;
+  a.khat = B.prior.khat;
+  for (int k = 0; k < 3; ++k) { a.o_dst[k] = B.origin[k]; a.o_src[k] = P.origin[k]; }
+  a.h_dst = B.h;
+  a.h_src = P.h;
+  a.dnx = B.nx; a.dny = B.ny;
+  e = launch_map(a, dom->desc.storage, dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "block start mapping");
+  dom->invalidate_graphs();
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_build_dynamic_scale(lbm_domain* dom, int32_t src_block, double h,
+                                              double g_threshold, double u_threshold,
+                                              int32_t margin, int32_t replace_last,
+                                              int32_t* block_id) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (!block_id) return dom->fail(LBM_ERR_INVALID_ARG, "null block_id");
+  *block_id = -1;
+  lbm_status st = dom->check_block(src_block);
+  if (st != LBM_OK) return st;
+  if (margin < 0) return dom->fail(LBM_ERR_INVALID_ARG, "margin must be >= 0");
+  if (!(h > 0.0 && h < 1.0)) return dom->fail(LBM_ERR_INVALID_ARG, "h must be in (0, 1)");
+  {
+    const Block& B0 = dom->blocks[0];
+    const int m = std::max(B0.nx, std::max(B0.ny, B0.nz));
+    if ((double)m / h > 65535.0) return dom->fail(LBM_ERR_INVALID_ARG, "h too small for this reference block");
+  }
+  const int last = (int)dom->blocks.size() - 1;
+  if (replace_last && (last < 1 || src_block == last))
+    return dom->fail(LBM_ERR_INVALID_ARG, "replace_last needs a refined last block other than the source");
+  int64_t count = 0;
+  int32_t box[6];
+  st = lbm_detect_region(dom, src_block, g_threshold, u_threshold, &count, box);
+  if (st != LBM_OK) return st;
+  // geometry of the source block, read before any removal
+  const Block& S = dom->blocks[src_block];
+  const double so[3] = {S.origin[0], S.origin[1], S.origin[2]};
+  const double sh = S.h;
+  const int ref[3] = {dom->blocks[0].nx, dom->blocks[0].ny, dom->blocks[0].nz};
+  if (replace_last) {
+    st = lbm_remove_scale_block(dom, last);
+    if (st != LBM_OK) return st;
+  }
+  if (count == 0) return LBM_OK;
+  double origin[3];
+  int32_t dims[3];
+  for (int a = 0; a < 3; ++a) {
+    const double top = (double)(ref[a] - 1);
+    double lo = std::max(so[a] + (box[a] - margin) * sh, 0.0);
+    const double hi = std::min(so[a] + (box[3 + a] + margin) * sh, top);
+    const int n = std::max((int)std::floor((hi - lo) / h + 1e-9) + 1, 4);
+    if (lo + (n - 1) * h > top + 1e-9) lo = std::max(0.0, top - (n - 1) * h);
+    origin[a] = lo;
+    dims[a] = n;
+  }
+  int32_t id = -1;
+  st = lbm_add_scale_block(dom, origin, h, dims, &id);
+  if (st != LBM_OK) return st;
+  st = lbm_init_block_from_parent(dom, id);
+  if (st != LBM_OK) {
+    lbm_remove_scale_block(dom, id);
+    return st;
+  }
+  *block_id = id;
+  return LBM_OK;
+}

@@ -62,6 +62,12 @@ struct MapArgs {
   uint8_t skip_mask;   // destination nodes with any of these flags are left alone
   size_t dN;
   float khat;          // K_hat factor of moments 4..8 (1 for all others)
+  // table == nullptr: entry e is destination node e of a whole block, its source cell
+  // computed from the two blocks' geometry (reference units) instead of read from a table
+  double o_dst[3], h_dst;
+  double o_src[3], h_src;
+  int dnx, dny;
+  int snz;
 };
 
 // One tile of the batched work list: a BX x BY patch of one z-plane of one simulation.

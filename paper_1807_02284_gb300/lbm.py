@@ -68,6 +68,12 @@ _SIGNATURES = {
                                  C.POINTER(C.c_int32)]),
     "lbm_set_boundary": (_I, [_P, _I, _I, _P, C.c_size_t, _I]),
     "lbm_init_macro": (_I, [_P, _I, _P, _P, _P, _I]),
+    "lbm_remove_scale_block": (_I, [_P, _I]),
+    "lbm_detect_region": (_I, [_P, _I, C.c_double, C.c_double, C.POINTER(C.c_int64),
+                               C.POINTER(C.c_int32)]),
+    "lbm_init_block_from_parent": (_I, [_P, _I]),
+    "lbm_build_dynamic_scale": (_I, [_P, _I, C.c_double, C.c_double, C.c_double, _I, _I,
+                                     C.POINTER(C.c_int32)]),
     "lbm_step": (_I, [_P, _I]),
     "lbm_sync": (_I, [_P]),
     "lbm_read_macro": (_I, [_P, _I, _I, _P, C.c_size_t, _I]),
@@ -208,6 +214,29 @@ class Domain:
         dd = (C.c_int32 * 3)(*[int(v) for v in dims])
         bid = C.c_int32()
         self.check(self.lib.lbm_add_scale_block(self.handle, o, float(h), dd, C.byref(bid)))
+        return bid.value
+
+    def remove_scale_block(self, block: int):
+        self.check(self.lib.lbm_remove_scale_block(self.handle, int(block)))
+
+    def detect_region(self, g_threshold: float, u_threshold: float, block: int = 0):
+        """(count, box) with box = (x0, y0, z0, x1, y1, z1), or (0, None)."""
+        n = C.c_int64()
+        box = (C.c_int32 * 6)()
+        self.check(self.lib.lbm_detect_region(self.handle, int(block), float(g_threshold),
+                                              float(u_threshold), C.byref(n), box))
+        return (int(n.value), tuple(box)) if n.value else (0, None)
+
+    def init_block_from_parent(self, block: int):
+        self.check(self.lib.lbm_init_block_from_parent(self.handle, int(block)))
+
+    def build_dynamic_scale(self, h: float, g_threshold: float, u_threshold: float,
+                            margin: int = 2, replace_last: bool = False, src_block: int = 0) -> int:
+        bid = C.c_int32()
+        self.check(self.lib.lbm_build_dynamic_scale(self.handle, int(src_block), float(h),
+                                                    float(g_threshold), float(u_threshold),
+                                                    int(margin), 1 if replace_last else 0,
+                                                    C.byref(bid)))
         return bid.value
 
     def info(self, block=0) -> lbm_block_info:
