@@ -268,8 +268,12 @@ lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every);
    after the n_steps steps recorded since the last lbm_init_macro (n_steps must equal the
    recorded count): dL_dscalar_final (N floats, device) and dL_du_final (3N floats, device,
    may be NULL) in; dL_du0 (3N floats, device) receives dL/du_0 for the u passed to
-   lbm_init_macro.  dL_dinflow must be NULL (UNSUPPORTED otherwise).  Single-block domains
-   with FP32 storage and periodic faces only (UNSUPPORTED otherwise).  Not in the paper. */
+   lbm_init_macro.  An inflow node's velocity is its stored velocity, set with u_0 and
+   carried unchanged by every step, so dL_du0 at inflow nodes is the gradient with respect to
+   that inflow velocity; dL_dinflow (3N floats, device, may be NULL) receives the same values
+   at inflow nodes and 0 elsewhere (inflow velocities must not be changed while the tape
+   records).  Single-block domains with FP32 storage, periodic faces and the lagged-gradient
+   (or fixed) relaxation only (UNSUPPORTED otherwise).  Not in the paper. */
 lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dscalar_final,
                             const float* dL_du_final, float* dL_du0, float* dL_dinflow);
 

@@ -14,7 +14,11 @@
 //     (a gather over the 27 neighbours: deterministic, no atomics).
 // Initial state: D^0 = f^eq(rho_0, u_0) - w and U^0 = u_0, so
 //   dL/du_0 = Ups^0 + (dD^0/du_0)^T Lam^0.
-// Scope: one periodic block with >= 3 nodes per axis, FP32 storage, no inflow nodes.
+// Inflow nodes: D^{n+1} = f^eq(1, U^n) - w and U^{n+1} = U^n, so their pulled populations get
+// a zero adjoint and the adjoint of U^n collects the equilibrium's Jacobian, the copy and the
+// scalar's departure-point term; dL/du_0 at an inflow node is then the gradient with respect
+// to its (constant) inflow velocity.
+// Scope: one periodic block with >= 3 nodes per axis, FP32 storage.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -36,6 +40,26 @@ struct AdjArgs {
   float* gam_out;       // Gam^n
   float* mu;            // 9 planes: adjoint of the velocity differences of the gradient norm
 };
+
+// Adjoint of the scalar step with respect to the departure velocity: C^{n+1}(x) is the
+// trilinear interpolant of C^n at x - u, so ub -= gam * d(interpolant)/d(fraction) per axis
+// (the fraction grows with the displacement -u; derivative 0 where the displacement is
+// clamped at one node).
+__device__ __forceinline__ void scalar_u_vjp(const BlockView& v, int x, int y, int z, float ux,
+                                             float uy, float uz, float gam, float (&ub)[3]) {
+  if (gam == 0.0f) return;
+  const ScalarCell sc = scalar_corners<uint32_t>(v, x, y, z, ux, uy, uz);
+  const float tx = sc.tx, ty = sc.ty, tz = sc.tz;
+  const float dtx = (1 - ty) * (1 - tz) * (sc.c[1] - sc.c[0]) + ty * (1 - tz) * (sc.c[3] - sc.c[2]) +
+                    (1 - ty) * tz * (sc.c[5] - sc.c[4]) + ty * tz * (sc.c[7] - sc.c[6]);
+  const float dty = (1 - tx) * (1 - tz) * (sc.c[2] - sc.c[0]) + tx * (1 - tz) * (sc.c[3] - sc.c[1]) +
+                    (1 - tx) * tz * (sc.c[6] - sc.c[4]) + tx * tz * (sc.c[7] - sc.c[5]);
+  const float dtz = (1 - tx) * (1 - ty) * (sc.c[4] - sc.c[0]) + tx * (1 - ty) * (sc.c[5] - sc.c[1]) +
+                    (1 - tx) * ty * (sc.c[6] - sc.c[2]) + tx * ty * (sc.c[7] - sc.c[3]);
+  if (fabsf(ux) < 1.0f) ub[0] -= gam * dtx;
+  if (fabsf(uy) < 1.0f) ub[1] -= gam * dty;
+  if (fabsf(uz) < 1.0f) ub[2] -= gam * dtz;
+}
 
 template <int K = 0>
 __device__ __forceinline__ void push_all(const float (&A)[27], float* __restrict__ lam,
@@ -64,6 +88,32 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   const uint32_t idx = n.p0 + n.r0 + n.x0;
   const uint8_t fl = v.flags[idx];
   if (fl & F_SOLID) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = 0.0f;
+    return;
+  }
+  if (fl & F_INFLOW) {
+    // D^{n+1} = f^eq(1, U^n) - w, U^{n+1} = U^n, C^{n+1} sampled at x - U^n: the pulled
+    // populations are unused (their slots get a zero adjoint) and every adjoint goes to U^n,
+    // which pass B completes with the lagged-gradient terms of the neighbours
+    const float u[3] = {v.u_in[idx], v.u_in[N + idx], v.u_in[2 * N + idx]};
+    float ub[3] = {a.ups_in[idx], a.ups_in[N + idx], a.ups_in[2 * N + idx]};
+    if (!(fl & F_SCALAR_SRC)) scalar_u_vjp(v, x, y, z, u[0], u[1], u[2], a.gam_in[idx], ub);
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+      const float c[3] = {(float)cxk(k), (float)cyk(k), (float)czk(k)};
+      const float cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+      const float l = a.lam_in[(uint32_t)k * N + idx] * wk(k);
+#pragma unroll
+      for (int a2 = 0; a2 < 3; ++a2) ub[a2] = fmaf(l, 3.0f * c[a2] + 9.0f * cu * c[a2] - 3.0f * u[a2], ub[a2]);
+    }
+    a.ups_out[idx] = ub[0];
+    a.ups_out[N + idx] = ub[1];
+    a.ups_out[2 * N + idx] = ub[2];
+    float Z[27];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) Z[k] = 0.0f;
+    push_all(Z, a.lam_out, N, n, idx, v.flags, (fl & F_NEAR_SOLID) != 0);
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = 0.0f;
     return;
@@ -104,24 +154,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   ub[0] = a.ups_in[idx];
   ub[1] = a.ups_in[N + idx];
   ub[2] = a.ups_in[2 * N + idx];
-  if (!(fl & F_SCALAR_SRC)) {
-    const float gam = a.gam_in[idx];
-    if (gam != 0.0f) {
-      const ScalarCell sc = scalar_corners<uint32_t>(v, x, y, z, ux, uy, uz);
-      const float tx = sc.tx, ty = sc.ty, tz = sc.tz;
-      // derivative of the trilinear interpolant along each fraction; the fraction grows
-      // with the departure displacement -u (derivative 0 where the displacement is clamped)
-      const float dtx = (1 - ty) * (1 - tz) * (sc.c[1] - sc.c[0]) + ty * (1 - tz) * (sc.c[3] - sc.c[2]) +
-                        (1 - ty) * tz * (sc.c[5] - sc.c[4]) + ty * tz * (sc.c[7] - sc.c[6]);
-      const float dty = (1 - tx) * (1 - tz) * (sc.c[2] - sc.c[0]) + tx * (1 - tz) * (sc.c[3] - sc.c[1]) +
-                        (1 - tx) * tz * (sc.c[6] - sc.c[4]) + tx * tz * (sc.c[7] - sc.c[5]);
-      const float dtz = (1 - tx) * (1 - ty) * (sc.c[4] - sc.c[0]) + tx * (1 - ty) * (sc.c[5] - sc.c[1]) +
-                        (1 - tx) * ty * (sc.c[6] - sc.c[2]) + tx * ty * (sc.c[7] - sc.c[3]);
-      if (fabsf(ux) < 1.0f) ub[0] -= gam * dtx;
-      if (fabsf(uy) < 1.0f) ub[1] -= gam * dty;
-      if (fabsf(uz) < 1.0f) ub[2] -= gam * dtz;
-    }
-  }
+  if (!(fl & F_SCALAR_SRC)) scalar_u_vjp(v, x, y, z, ux, uy, uz, a.gam_in[idx], ub);
 
   // ---- adjoint of the collision
   float A[27];
@@ -194,7 +227,8 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
   const uint32_t N = (uint32_t)v.N;
   const Nbr<uint32_t> n = neighbours<uint32_t>(v, x, y, z);
   const uint32_t idx = n.p0 + n.r0 + n.x0;
-  // lagged-velocity adjoint
+  // lagged-velocity adjoint (inflow nodes add it to what pass A left there)
+  const bool inflow = (v.flags[idx] & (F_INFLOW | F_SOLID)) == F_INFLOW;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float* m0 = a.mu + (uint32_t)(3 * c + 0) * N;
@@ -203,7 +237,7 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
     const float s = __ldg(m0 + (n.p0 + n.r0 + n.xm)) - __ldg(m0 + (n.p0 + n.r0 + n.xp)) +
                     __ldg(m1 + (n.p0 + n.rm + n.x0)) - __ldg(m1 + (n.p0 + n.rp + n.x0)) +
                     __ldg(m2 + (n.pm + n.r0 + n.x0)) - __ldg(m2 + (n.pp + n.r0 + n.x0));
-    a.ups_out[(uint32_t)c * N + idx] = s;
+    a.ups_out[(uint32_t)c * N + idx] = inflow ? a.ups_out[(uint32_t)c * N + idx] + s : s;
   }
   // scalar adjoint: gather from the neighbours whose departure cell contains this node
   const uint32_t xs[3] = {n.xm, n.x0, n.xp};
@@ -260,6 +294,18 @@ __global__ void k_adj_init(const float* __restrict__ d0, const float* __restrict
     out[idx] = gsum[0];
     out[N + idx] = gsum[1];
     out[2 * N + idx] = gsum[2];
+  }
+}
+
+// The inflow velocity of a node is its stored velocity, carried unchanged from step to step
+// and set with u_0, so the gradient with respect to it is dL/du_0 at inflow nodes.
+__global__ void k_inflow_grad(const float* __restrict__ du0, const uint8_t* __restrict__ flags,
+                              float* __restrict__ out, uint32_t N) {
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+    const bool in = (flags[idx] & (F_INFLOW | F_SOLID)) == F_INFLOW;
+    out[idx] = in ? du0[idx] : 0.0f;
+    out[N + idx] = in ? du0[N + idx] : 0.0f;
+    out[2 * N + idx] = in ? du0[2 * N + idx] : 0.0f;
   }
 }
 
@@ -352,12 +398,6 @@ static lbm_status adjoint_supported(lbm_domain* dom) {
     if (!dom->desc.periodic[a]) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs periodic faces");
   if (B.nx < 3 || B.ny < 3 || B.nz < 3) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs >= 3 nodes per axis");
   if (27ull * B.N >= 0xFFFFFFFFull) return dom->fail(LBM_ERR_UNSUPPORTED, "block too large for the adjoint");
-  std::vector<uint8_t> fl(B.N);
-  cudaError_t e = cudaMemcpyAsync(fl.data(), B.flags, B.N, cudaMemcpyDeviceToHost, dom->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(dom->stream);
-  if (e != cudaSuccess) return dom->cuda_fail(e, "flag read-back");
-  for (uint8_t f : fl)
-    if ((f & F_INFLOW) && !(f & F_SOLID)) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint does not cover inflow nodes");
   return LBM_OK;
 }
 
@@ -381,7 +421,6 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
                                        const float* dL_du, float* dL_du0, float* dL_dinflow) {
   if (!dom) return LBM_ERR_INVALID_ARG;
   cudaSetDevice(dom->desc.device);
-  if (dL_dinflow) return dom->fail(LBM_ERR_UNSUPPORTED, "gradients with respect to inflow are not built");
   TapeState* t = dom->tape;
   if (!t) return dom->fail(LBM_ERR_STATE, "no tape: call lbm_set_tape after lbm_init_macro");
   if (n_steps < 0 || n_steps != dom->steps)
@@ -478,6 +517,7 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
   const int g = (int)std::min<size_t>((N + 255) / 256, 16384);
   k_adj_init<<<g, 256, 0, s>>>(static_cast<const float*>(t->ckpt[0].f), t->ckpt[0].u, B.flags,
                                t->lam[c], t->ups[c], dL_du0, (uint32_t)N);
+  if (dL_dinflow) k_inflow_grad<<<g, 256, 0, s>>>(dL_du0, B.flags, dL_dinflow, (uint32_t)N);
   e = cudaGetLastError();
   if (e != cudaSuccess) return dom->cuda_fail(e, "initial-state adjoint");
   dom->post_error_probe();

@@ -310,11 +310,12 @@ class Domain:
     def set_tape(self, every):
         self.check(self.lib.lbm_set_tape(self.handle, int(every)))
 
-    def adjoint_step(self, n_steps, dL_dc, dL_du0, dL_du=None):
+    def adjoint_step(self, n_steps, dL_dc, dL_du0, dL_du=None, dL_dinflow=None):
         pc, _ = _ptr(dL_dc)
         pu, _ = _ptr(dL_du)
         p0, _ = _ptr(dL_du0)
-        self.check(self.lib.lbm_adjoint_step(self.handle, int(n_steps), pc, pu, p0, None))
+        pi, _ = _ptr(dL_dinflow)
+        self.check(self.lib.lbm_adjoint_step(self.handle, int(n_steps), pc, pu, p0, pi))
 
 
 def step_batch(domains: Sequence[Domain], steps: int):

@@ -82,6 +82,40 @@ def test_adjoint_fixed_rates_matches_fp64_oracle(lib):
     assert e <= 1e-3
 
 
+@pytest.mark.parametrize("scalar_source", [False, True])
+def test_inflow_velocity_gradient_matches_fp64_oracle(lib, scalar_source):
+    """Inflow disk on the x = 0 plane of the periodic box (velocity carried unchanged from
+    step to step): dL/du0 everywhere against the FP64 oracle, dL/d(inflow) equal to dL/du0 at
+    the inflow nodes and 0 elsewhere."""
+    from paper_1807_02284_gb300 import lbm
+    n, steps, every = 12, 10, 4
+    sc, target = synth.adjoint_scene(n=n, seed=11, nu=0.01, amp=0.05)
+    b = sc.blocks[0]
+    rng = np.random.default_rng(3)
+    zi, yi, _ = synth.inflow_disk(b, (6, 6), 3.0, 0.05, rng=rng, noise=0.2, scalar=scalar_source)
+    dom = _domain(sc)
+    dom.init_macro(f32(b.u0), rho=f32(b.rho0), c=f32(b.c0))
+    dom.set_tape(every)
+    dom.step(steps)
+    c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64)
+    dLdc = torch.tensor(c - target.reshape(-1), dtype=torch.float32, device="cuda")
+    g = torch.empty(3 * b.flags.size, dtype=torch.float32, device="cuda")
+    gi = torch.full_like(g, 7.0)
+    dom.adjoint_step(steps, dLdc, g, dL_dinflow=gi)
+    dom.sync()
+    dom.close()
+    gg = g.cpu().numpy().astype(np.float64).reshape(b.u0.shape)
+    gin = gi.cpu().numpy().astype(np.float64).reshape(b.u0.shape)
+    _, go, _ = oracle_grad(sc, target, steps)
+    e = rel(gg, go.numpy())
+    ein = rel(gg[:, zi, yi, 0], go.numpy()[:, zi, yi, 0])
+    print(f"inflow gradient (scalar source {scalar_source}): rel L2 all {e:.2e}, inflow nodes {ein:.2e}")
+    assert e <= 1e-3 and ein <= 1e-3
+    mask = np.zeros(b.flags.shape, bool)
+    mask[zi, yi, 0] = True
+    assert np.array_equal(gin[:, mask], gg[:, mask]) and (gin[:, ~mask] == 0).all()
+
+
 def test_adjoint_config5_copy_32_cubed_200_steps(lib):
     """The smoke-control problem scaled to 32^3 (every length / 4), nu = 1e-3, 200 steps,
     checkpoint every 20: FP32 GPU adjoint against the FP64 oracle gradient."""
