@@ -18,7 +18,12 @@
 // a zero adjoint and the adjoint of U^n collects the equilibrium's Jacobian, the copy and the
 // scalar's departure-point term; dL/du_0 at an inflow node is then the gradient with respect
 // to its (constant) inflow velocity.
-// Scope: one periodic block with >= 3 nodes per axis, FP32 storage.
+// Open faces copy the nearest in-block node, so a slot of a face node can be read by up to 8
+// pulls: those slots are zeroed before pass A and accumulated atomically (every other slot
+// is read once and stored), pass B's lagged-velocity gather uses the clamped differences
+// (a face node's own difference involves itself), and the scalar gather counts a clamped
+// repeat of the node once.
+// Scope: one block with >= 3 nodes per axis, FP32 storage.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -43,8 +48,10 @@ struct AdjArgs {
 
 // Adjoint of the scalar step with respect to the departure velocity: C^{n+1}(x) is the
 // trilinear interpolant of C^n at x - u, so ub -= gam * d(interpolant)/d(fraction) per axis
-// (the fraction grows with the displacement -u; derivative 0 where the displacement is
-// clamped at one node).
+// (the fraction grows with the displacement -u).  The derivative is 0 where the sample does
+// not move with u: a displacement clamped at one node, or a departure point below an open
+// face's first node (the forward pins the sample to that node; at the upper face both
+// corners already coincide).
 __device__ __forceinline__ void scalar_u_vjp(const BlockView& v, int x, int y, int z, float ux,
                                              float uy, float uz, float gam, float (&ub)[3]) {
   if (gam == 0.0f) return;
@@ -56,27 +63,78 @@ __device__ __forceinline__ void scalar_u_vjp(const BlockView& v, int x, int y, i
                     (1 - tx) * tz * (sc.c[6] - sc.c[4]) + tx * tz * (sc.c[7] - sc.c[5]);
   const float dtz = (1 - tx) * (1 - ty) * (sc.c[4] - sc.c[0]) + tx * (1 - ty) * (sc.c[5] - sc.c[1]) +
                     (1 - tx) * ty * (sc.c[6] - sc.c[2]) + tx * ty * (sc.c[7] - sc.c[3]);
-  if (fabsf(ux) < 1.0f) ub[0] -= gam * dtx;
-  if (fabsf(uy) < 1.0f) ub[1] -= gam * dty;
-  if (fabsf(uz) < 1.0f) ub[2] -= gam * dtz;
+  const bool lx = !v.per[0] && x == 0 && ux > 0.0f;
+  const bool ly = !v.per[1] && y == 0 && uy > 0.0f;
+  const bool lz = !v.per[2] && z == 0 && uz > 0.0f;
+  if (fabsf(ux) < 1.0f && !lx) ub[0] -= gam * dtx;
+  if (fabsf(uy) < 1.0f && !ly) ub[1] -= gam * dty;
+  if (fabsf(uz) < 1.0f && !lz) ub[2] -= gam * dtz;
 }
 
-template <int K = 0>
+// Which of the candidate source positions (x-1, x, x+1 per axis, after wrapping or clamping)
+// lie on an open face, as bits 3a + o + 1 (axis a, offset o).  A slot of a node on an open
+// face can be read by more than one pull (the face copies its nearest in-block node), so its
+// adjoint is accumulated there; every other slot is read by exactly one pull and stored.
+using FaceMask = uint32_t;
+
+template <bool OPEN>
+__device__ __forceinline__ FaceMask face_mask(const BlockView& v, int x, int y, int z) {
+  if constexpr (!OPEN) return 0u;
+  FaceMask f = 0u;
+  const int c[3] = {x, y, z}, nn[3] = {v.nx, v.ny, v.nz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int o = -1; o <= 1; ++o) {
+      const int j = nbr(c[a], o, nn[a], v.per[a]);
+      if (!v.per[a] && (j == 0 || j == nn[a] - 1)) f |= 1u << (3 * a + o + 1);
+    }
+  return f;
+}
+
+template <bool OPEN, int K = 0>
 __device__ __forceinline__ void push_all(const float (&A)[27], float* __restrict__ lam,
                                          uint32_t N, const Nbr<uint32_t>& n, uint32_t idx,
-                                         const uint8_t* __restrict__ flags, bool near) {
+                                         const uint8_t* __restrict__ flags, bool near,
+                                         FaceMask fm) {
   if constexpr (K < 27) {
+    constexpr int cx = cxk(K), cy = cyk(K), cz = czk(K);
     const uint32_t src = pull_src<K>(n);
     uint32_t slot = (uint32_t)K * N + src;
-    if (K != 13 && near && (__ldg(flags + src) & F_SOLID)) slot = (uint32_t)(26 - K) * N + idx;
-    lam[slot] = A[K];
-    push_all<K + 1>(A, lam, N, n, idx, flags, near);
+    const bool bb = K != 13 && near && (__ldg(flags + src) & F_SOLID);
+    if (bb) slot = (uint32_t)(26 - K) * N + idx;
+    if constexpr (OPEN) {
+      constexpr FaceMask own = (1u << 1) | (1u << 4) | (1u << 7);
+      constexpr FaceMask src_bits = (1u << (1 - cx)) | (1u << (4 - cy)) | (1u << (7 - cz));
+      const bool face = (fm & (bb ? own : src_bits)) != 0u;
+      if (face) atomicAdd(lam + slot, A[K]);
+      else lam[slot] = A[K];
+    } else {
+      lam[slot] = A[K];
+    }
+    push_all<OPEN, K + 1>(A, lam, N, n, idx, flags, near, fm);
+  }
+}
+
+// Zeroes the adjoint slots of the nodes on open faces before pass A accumulates into them.
+__global__ void k_zero_face_slots(float* __restrict__ lam, int nx, int ny, int nz, int px,
+                                  int py, int pz) {
+  const size_t N = (size_t)nx * ny * nz;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((size_t)nx * ny));
+    const bool face = (!px && (x == 0 || x == nx - 1)) || (!py && (y == 0 || y == ny - 1)) ||
+                      (!pz && (z == 0 || z == nz - 1));
+    if (!face) continue;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) lam[(size_t)k * N + idx] = 0.0f;
   }
 }
 
 // MINB: CTAs per SM the register allocation is bounded for (3: no spills; 4: some spills,
 // more warps in flight); the faster one is chosen at run time.
-template <int MINB>
+// OPEN: some face of the block is open (face slots accumulate; see FaceMask).
+template <int MINB, bool OPEN>
 __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   const BlockView& v = a.fwd;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,7 +171,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
     float Z[27];
 #pragma unroll
     for (int k = 0; k < 27; ++k) Z[k] = 0.0f;
-    push_all(Z, a.lam_out, N, n, idx, v.flags, (fl & F_NEAR_SOLID) != 0);
+    push_all<OPEN>(Z, a.lam_out, N, n, idx, v.flags, (fl & F_NEAR_SOLID) != 0, face_mask<OPEN>(v, x, y, z));
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = 0.0f;
     return;
@@ -200,7 +258,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   raw_axis_vjp<9>(A);
   raw_axis_vjp<3>(A);
   raw_axis_vjp<1>(A);                    // A = adjoint of the pulled populations
-  push_all(A, a.lam_out, N, n, idx, v.flags, near);
+  push_all<OPEN>(A, a.lam_out, N, n, idx, v.flags, near, face_mask<OPEN>(v, x, y, z));
 
   // ---- adjoint of the adaptive factor: K_g = 1 - 1/(phi nu3_g + 1/2)
   float mu_scale = 0.0f;
@@ -218,6 +276,16 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = v.rp.adaptive ? mu_scale * diff[i] : 0.0f;
 }
 
+static void launch_pass_a(const AdjArgs& a, int minb, bool open, dim3 grd, dim3 blk, cudaStream_t s) {
+  if (open) {
+    if (minb == 4) k_adj_a<4, true><<<grd, blk, 0, s>>>(a);
+    else k_adj_a<3, true><<<grd, blk, 0, s>>>(a);
+  } else {
+    if (minb == 4) k_adj_a<4, false><<<grd, blk, 0, s>>>(a);
+    else k_adj_a<3, false><<<grd, blk, 0, s>>>(a);
+  }
+}
+
 __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
   const BlockView& v = a.fwd;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -229,14 +297,28 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
   const uint32_t idx = n.p0 + n.r0 + n.x0;
   // lagged-velocity adjoint (inflow nodes add it to what pass A left there)
   const bool inflow = (v.flags[idx] & (F_INFLOW | F_SOLID)) == F_INFLOW;
+  // node q's difference along axis b is U(q+e_b) - U(q-e_b) with the indices wrapped or
+  // clamped: this node receives +mu_b(q) from q = this - e_b and -mu_b(q) from q = this + e_b
+  // when those nodes exist, and on an open face also its own +mu_b (top: its + neighbour is
+  // itself) or -mu_b (bottom: its - neighbour is itself)
+  const int cc[3] = {x, y, z}, nn[3] = {v.nx, v.ny, v.nz};
+  float wm[3], wp[3], ws[3];            // weights of mu(this - e_b), mu(this + e_b), mu(this)
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const bool per = v.per[b] != 0;
+    wm[b] = (per || cc[b] > 0) ? 1.0f : 0.0f;
+    wp[b] = (per || cc[b] < nn[b] - 1) ? -1.0f : 0.0f;
+    ws[b] = per ? 0.0f : (cc[b] == nn[b] - 1 ? 1.0f : 0.0f) - (cc[b] == 0 ? 1.0f : 0.0f);
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float* m0 = a.mu + (uint32_t)(3 * c + 0) * N;
     const float* m1 = a.mu + (uint32_t)(3 * c + 1) * N;
     const float* m2 = a.mu + (uint32_t)(3 * c + 2) * N;
-    const float s = __ldg(m0 + (n.p0 + n.r0 + n.xm)) - __ldg(m0 + (n.p0 + n.r0 + n.xp)) +
-                    __ldg(m1 + (n.p0 + n.rm + n.x0)) - __ldg(m1 + (n.p0 + n.rp + n.x0)) +
-                    __ldg(m2 + (n.pm + n.r0 + n.x0)) - __ldg(m2 + (n.pp + n.r0 + n.x0));
+    float s = wm[0] * __ldg(m0 + (n.p0 + n.r0 + n.xm)) + wp[0] * __ldg(m0 + (n.p0 + n.r0 + n.xp)) +
+              wm[1] * __ldg(m1 + (n.p0 + n.rm + n.x0)) + wp[1] * __ldg(m1 + (n.p0 + n.rp + n.x0)) +
+              wm[2] * __ldg(m2 + (n.pm + n.r0 + n.x0)) + wp[2] * __ldg(m2 + (n.pp + n.r0 + n.x0));
+    s = fmaf(ws[0], __ldg(m0 + idx), fmaf(ws[1], __ldg(m1 + idx), fmaf(ws[2], __ldg(m2 + idx), s)));
     a.ups_out[(uint32_t)c * N + idx] = inflow ? a.ups_out[(uint32_t)c * N + idx] + s : s;
   }
   // scalar adjoint: gather from the neighbours whose departure cell contains this node
@@ -253,6 +335,11 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
     for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
       for (int dx = 0; dx < 3; ++dx) {
+        // a clamped neighbour index repeats the node itself: count every node once
+        if ((dx == 0 && xs[0] == xs[1]) || (dx == 2 && xs[2] == xs[1]) ||
+            (dy == 0 && rs[0] == rs[1]) || (dy == 2 && rs[2] == rs[1]) ||
+            (dz == 0 && ps[0] == ps[1]) || (dz == 2 && ps[2] == ps[1]))
+          continue;
         const uint32_t j = ps[dz] + rs[dy] + xs[dx];
         if (__ldg(v.flags + j) & (F_SOLID | F_SCALAR_SRC)) continue;
         const float G = __ldg(a.gam_in + j);
@@ -394,8 +481,6 @@ static lbm_status adjoint_supported(lbm_domain* dom) {
   if (dom->desc.grad_mode != LBM_GRAD_LAGGED)
     return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint covers the lagged-gradient relaxation");
   const Block& B = dom->blocks[0];
-  for (int a = 0; a < 3; ++a)
-    if (!dom->desc.periodic[a]) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs periodic faces");
   if (B.nx < 3 || B.ny < 3 || B.nz < 3) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs >= 3 nodes per axis");
   if (27ull * B.N >= 0xFFFFFFFFull) return dom->fail(LBM_ERR_UNSUPPORTED, "block too large for the adjoint");
   return LBM_OK;
@@ -462,6 +547,8 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
   if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint initialisation");
 
   const int n_seg = (n_steps + t->every - 1) / t->every;
+  const bool open_faces = !dom->desc.periodic[0] || !dom->desc.periodic[1] || !dom->desc.periodic[2];
+  const int zgrid = (int)std::min<size_t>((N + 255) / 256, 16384);
   const dim3 blk(128, 1, 1);
   const dim3 grd((B.nx + 127) / 128, B.ny, B.nz);
   for (int sg = n_seg - 1; sg >= 0; --sg) {
@@ -485,16 +572,16 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
       a.gam_out = t->gam[c ^ 1];
       a.mu = t->mu;
       if (t->pass_a_minb == 0) {
-        // time both register bounds on this step's inputs (pass A only writes lam_out and
-        // mu, which the launch below rewrites), keep the faster
+        // time both register bounds on this step's inputs (pass A only writes lam_out, mu and
+        // the inflow nodes' ups_out, which the launches below rewrite), keep the faster
         cudaEvent_t e0, e1, e2;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventCreate(&e2);
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 2; ++r) k_adj_a<3><<<grd, blk, 0, s>>>(a);
+        for (int r = 0; r < 2; ++r) launch_pass_a(a, 3, open_faces, grd, blk, s);
         cudaEventRecord(e1, s);
-        for (int r = 0; r < 2; ++r) k_adj_a<4><<<grd, blk, 0, s>>>(a);
+        for (int r = 0; r < 2; ++r) launch_pass_a(a, 4, open_faces, grd, blk, s);
         cudaEventRecord(e2, s);
         e = cudaEventSynchronize(e2);
         float m3 = 0.f, m4 = 0.f;
@@ -506,8 +593,10 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
         if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint tuning");
         t->pass_a_minb = m4 < m3 ? 4 : 3;
       }
-      if (t->pass_a_minb == 4) k_adj_a<4><<<grd, blk, 0, s>>>(a);
-      else k_adj_a<3><<<grd, blk, 0, s>>>(a);
+      if (open_faces)   // open-face slots accumulate; the tuning launches above also wrote them
+        k_zero_face_slots<<<zgrid, 256, 0, s>>>(a.lam_out, B.nx, B.ny, B.nz, dom->desc.periodic[0],
+                                                dom->desc.periodic[1], dom->desc.periodic[2]);
+      launch_pass_a(a, t->pass_a_minb, open_faces, grd, blk, s);
       k_adj_b<<<grd, blk, 0, s>>>(a);
       e = cudaGetLastError();
       if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint step");

@@ -116,6 +116,43 @@ def test_inflow_velocity_gradient_matches_fp64_oracle(lib, scalar_source):
     assert np.array_equal(gin[:, mask], gg[:, mask]) and (gin[:, ~mask] == 0).all()
 
 
+@pytest.mark.parametrize("plume", [False, True])
+def test_open_faces_adjoint_matches_fp64_oracle(lib, plume):
+    """Open (zero-gradient) faces: a face node's populations are pulled more than once, its
+    velocity enters its own clamped difference, and its scalar sample can clamp.  With
+    plume=True: inflow disk with a scalar source on the x = 0 face and an obstacle, as in the
+    smoke scenes."""
+    from paper_1807_02284_gb300 import lbm
+    n, steps, every = 12, 10, 3
+    sc, target = synth.adjoint_scene(n=n, seed=13, nu=0.01, amp=0.05)
+    sc.periodic = (False, False, False)
+    b = sc.blocks[0]
+    zi = yi = None
+    if plume:
+        rng = np.random.default_rng(4)
+        zi, yi, _ = synth.inflow_disk(b, (6, 6), 3.0, 0.05, rng=rng, noise=0.2, scalar=True)
+        synth.voxelise_spheres(b, [(7.5, 6.0, 6.5, 1.8)])
+    dom = _domain(sc)
+    dom.init_macro(f32(b.u0), rho=f32(b.rho0), c=f32(b.c0))
+    dom.set_tape(every)
+    dom.step(steps)
+    c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64)
+    dLdc = torch.tensor(c - target.reshape(-1), dtype=torch.float32, device="cuda")
+    g = torch.empty(3 * b.flags.size, dtype=torch.float32, device="cuda")
+    dom.adjoint_step(steps, dLdc, g)
+    dom.sync()
+    dom.close()
+    gg = g.cpu().numpy().astype(np.float64).reshape(b.u0.shape)
+    _, go, _ = oracle_grad(sc, target, steps)
+    go = go.numpy()
+    e = rel(gg, go)
+    face = np.zeros(b.flags.shape, bool)
+    face[0], face[-1], face[:, 0], face[:, -1], face[:, :, 0], face[:, :, -1] = (True,) * 6
+    ef = rel(gg[:, face], go[:, face])
+    print(f"open faces (plume {plume}): rel L2 all {e:.2e}, face nodes {ef:.2e}")
+    assert e <= 1e-3 and ef <= 1e-3
+
+
 def test_adjoint_config5_copy_32_cubed_200_steps(lib):
     """The smoke-control problem scaled to 32^3 (every length / 4), nu = 1e-3, 200 steps,
     checkpoint every 20: FP32 GPU adjoint against the FP64 oracle gradient."""
@@ -205,13 +242,18 @@ def test_autograd_function_returns_the_adjoint(lib):
 def test_adjoint_argument_checks(lib):
     from paper_1807_02284_gb300 import lbm
     sc = synth.random_scene(dims=(10, 10, 10), seed=3, periodic=(False, True, True))
-    d = _domain(sc)
     b = sc.blocks[0]
-    d.init_macro(f32(b.u0))
-    with pytest.raises(lbm.LBMError) as ei:
-        d.set_tape(2)
-    assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
-    d.close()
+    for kind in ("fp16", "multiblock", "local"):
+        d = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic,
+                       storage="fp16" if kind == "fp16" else "fp32",
+                       grad_mode="local" if kind == "local" else "lagged")
+        if kind == "multiblock":
+            d.add_scale_block((2.0, 2.0, 2.0), 0.5, (8, 8, 8))
+        d.init_macro(f32(b.u0))
+        with pytest.raises(lbm.LBMError) as ei:
+            d.set_tape(2)
+        assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED, kind
+        d.close()
     sc, target = synth.adjoint_scene(n=8, seed=1)
     d = _domain(sc)
     b = sc.blocks[0]
