@@ -68,6 +68,8 @@ class Blk:
     substeps: int = 1
     integer_ratio: bool = True
     parent: int = -1
+    far: bool = False       # far-field block (h > 1) around `child`
+    child: int = -1
 
     def interior_lo_hi(self):
         lo = self.origin + self.h
@@ -173,6 +175,84 @@ class MultiScale:
             blocks[i].parent = ms._containing_parent(i)
         return ms
 
+    # ------------------------------------------------------------------ far field
+    def outermost(self) -> int:
+        """The block a new far-field block has to surround: the last far block, else s0."""
+        far = [i for i, b in enumerate(self.blocks) if b.far]
+        return far[-1] if far else 0
+
+    @staticmethod
+    def _outer_layer(dims):
+        nx, ny, nz = dims
+        m = torch.zeros((nz, ny, nx), dtype=torch.bool)
+        m[0], m[-1], m[:, 0], m[:, -1], m[:, :, 0], m[:, :, -1] = (True,) * 6
+        return m
+
+    def set_outer_ghost(self, i: int, on: bool):
+        """The outer layer of block i becomes (on) or stops being (off) a scale boundary,
+        except its obstacle and inflow nodes, which keep their own update."""
+        b = self.blocks[i]
+        outer = self._outer_layer(b.dims)
+        fl = b.state.flags
+        keep = (fl & (SOLID | INFLOW)) != 0
+        ghost = outer & ~keep if on else torch.zeros_like(outer)
+        b.state.flags = torch.where(outer, torch.where(ghost, fl | GHOST, fl & ~GHOST), fl)
+
+    def add_far_block(self, origin, h, dims, rho0, u0, c0, flags) -> int:
+        """Far-field block (Sec. 4.2.4, 4.2.5): spacing h > 1, surrounding the outermost
+        block, which from now on takes its outer layer from this block."""
+        if not h > 1.0:
+            raise ValueError("far-field blocks have h > 1")
+        child = self.outermost()
+        c = self.blocks[child]
+        lo_c, hi_c = c.origin, c.origin + (np.array(c.dims) - 1) * c.h
+        lo, hi = np.asarray(origin, float), np.asarray(origin, float) + (np.array(dims) - 1) * h
+        if not (np.all(lo <= lo_c + 1e-9) and np.all(hi_c <= hi + 1e-9)):
+            raise ValueError("a far-field block must contain the outermost block")
+        ref = self.blocks[0].params
+        p = grid.Params(nu=ref.nu / h, periodic=(False, False, False), adaptive=ref.adaptive,
+                        c_src=ref.c_src, grad_mode=ref.grad_mode)
+        conv = lambda a: np.asarray(a, np.float32).astype(np.float64)
+        st = grid.init_state(conv(rho0), conv(u0), conv(c0), flags)
+        self.blocks.append(Blk(origin=np.array(origin, dtype=np.float64), h=float(h),
+                               dims=tuple(dims), state=st, params=p, far=True, child=child))
+        self.set_outer_ghost(child, True)
+        return len(self.blocks) - 1
+
+    def far_step(self, i: int):
+        """One step of far block i (its own dt = h dt_0) from t_n, linearly interpolated back
+        to t_n + dt_0 (Sec. 4.2.4): f = (1 - 1/h) f(t_n) + (1/h) f(t_n + h dt_0); the stored
+        velocity is recomputed from the interpolated populations, the scalar interpolated
+        alike; obstacle and scale-boundary nodes keep their own values."""
+        b = self.blocks[i]
+        old = b.state
+        new = grid.step(old, b.params)
+        th = 1.0 / b.h
+        f = (1.0 - th) * old.f + th * new.f
+        c = (1.0 - th) * old.c + th * new.c
+        _, u = cmr.macros(f.reshape(27, -1).T)
+        u = u.T.reshape(old.u.shape)
+        keep = (old.flags & (GHOST | SOLID | INFLOW)) != 0
+        out = new.clone()
+        out.f = torch.where(keep[None], new.f, f)
+        out.u = torch.where(keep[None], new.u, u)
+        out.c = torch.where(keep, new.c, c)
+        b.state = out
+
+    def far_out_map(self, i: int):
+        """Scale-boundary nodes of far block i's child from block i (Sec. 4.2.5: the larger
+        scale updates the boundary of the smaller one)."""
+        b = self.blocks[i]
+        c = self.blocks[b.child]
+        z, y, x = self._ghost_nodes(c)
+        f, cc, ok = interpolate(b, b.state.f, b.state.c, node_positions(c, z, y, x))
+        z, y, x, f, cc = z[ok], y[ok], x[ok], f[ok], cc[ok]
+        fm = map_populations(f, k_hat(b, c))
+        _, u = cmr.macros(fm)
+        c.state.f[:, z, y, x] = fm.T
+        c.state.u[:, z, y, x] = u.T
+        c.state.c[z, y, x] = cc
+
     def _containing_parent(self, i: int) -> int:
         b = self.blocks[i]
         lo = b.origin
@@ -180,7 +260,7 @@ class MultiScale:
         best = 0
         for j in range(1, len(self.blocks)):
             c = self.blocks[j]
-            if j == i or not c.h > b.h:
+            if j == i or c.far or not c.h > b.h:
                 continue
             clo = c.origin
             chi = c.origin + (np.array(c.dims) - 1) * c.h
@@ -266,8 +346,17 @@ class MultiScale:
         saved = [b.state.clone() for b in self.blocks]
         b0 = self.blocks[0]
         b0.state = grid.step(b0.state, b0.params)
+        far = [i for i, b in enumerate(self.blocks) if b.far]
+        for i in far:                      # far field: one own step, back to t_n + dt_0
+            self.far_step(i)
+        for i in far:                      # overlap of each far block from its child
+            self.post_map(self.blocks[i].child, i)
+        for i in reversed(far):            # scale boundary of each child from its far block
+            self.far_out_map(i)
         for i in range(1, len(self.blocks)):
             b = self.blocks[i]
+            if b.far:
+                continue
             states = [b.state]
             for j in range(1, b.substeps + 1):
                 self.prior_map(i, (j - 1) * b.h, saved)
@@ -284,7 +373,7 @@ class MultiScale:
                 b.state = self.align(b, saved[i], prev, states[-1])
             self.prior_map(i, 1.0, saved)
             for k in range(len(self.blocks)):
-                if self.blocks[k].h > b.h:
+                if self.blocks[k].h > b.h and not self.blocks[k].far:
                     self.post_map(i, k)
         self.step_count += 1
 
