@@ -145,6 +145,10 @@ def _workload(name):
     storage = "fp16" if name.endswith("fp16") else "fp32"
     if name == "multiscale3":
         return synth.multiscale(scale=1.0), "fp32"
+    if name == "farfield256":       # the plume inside a far-field block of spacing 2
+        sc = synth.plume(256)
+        sc.blocks.append(synth.far_block(sc.blocks[0], 2.0, 64.0, seed=9, amp=0.0))
+        return sc, "fp32"
     sc = synth.plume(128 if name.startswith("plume128") else 256)
     return sc, storage
 
@@ -280,6 +284,9 @@ def run_ours(args):
     launches_per_step = 1
     for i in range(1, len(sc.blocks)):
         h = sc.blocks[i].h
+        if h > 1.0:                   # far field: aligned step, overlap and boundary maps
+            launches_per_step += 3
+            continue
         integer = abs(1.0 / h - round(1.0 / h)) < 1e-9 and abs(subs[i] * h - 1.0) < 1e-9
         launches_per_step += 2 * subs[i] + (0 if integer else 1) + 1 + i  # post: i coarser
     K, W = args.steps, args.warmup
@@ -640,6 +647,7 @@ def _variants(args):
                                   ("plume256_local", run_ours, 100, 10),
                                   ("multiscale3", run_ours, 50, 5),
                                   ("dynamic256", run_dynamic, 200, 10),
+                                  ("farfield256", run_ours, 100, 10),
                                   ("batch64", run_batch, 100, 10),
                                   ("adjoint128", run_adjoint, 200, 0)):
         a = copy.copy(args)
@@ -665,7 +673,7 @@ def main():
     ap.add_argument("--workload", default="plume256",
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
                              "multiscale3", "batch64", "adjoint128", "adjoint64",
-                             "plume256_local", "dynamic256"])
+                             "plume256_local", "dynamic256", "farfield256"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -141,22 +141,32 @@ lbm_status lbm_create_domain(const lbm_domain_desc* desc, lbm_domain** out);
 /* Releases every library buffer of the domain.  NULL is accepted. */
 lbm_status lbm_destroy_domain(lbm_domain* dom);
 
-/* Adds a finer scale block (Sec. 4.2: blocks at arbitrary, non-integer spacing ratios
-   overlaid on coarser ones).  origin: position of its node (0,0,0) in reference units;
-   h = dx_s/dx_0 in (0, 1); dims >= 4 per axis.  The whole block must lie inside block 0
-   and inside every block it is nested in; its outermost node layer is the scale boundary
-   (ghost layer) written by prior-mapping.  Blocks must be added coarse to fine (h not
-   increasing).  UNSUPPORTED for h >= 1 (far-field scales) and for FP16 storage; STATE while
-   an adjoint tape is recording; OOM / CUDA when a buffer or table cannot be created, in
-   which case the domain is left exactly as before the call. */
+/* Adds a scale block (Sec. 4.2: blocks at arbitrary, non-integer spacing ratios).
+   origin: position of its node (0,0,0) in reference units; h = dx_s/dx_0 != 1; dims >= 4
+   per axis.
+   h < 1, a finer block: it must lie inside block 0; its outermost node layer is its scale
+   boundary (ghost layer), written by prior-mapping from the finest coarser block that
+   contains it; its interior is post-mapped into every coarser block but the far-field ones.
+   Refined blocks must be added coarse to fine (h not increasing).
+   h > 1, a far-field block (Sec. 4.2.4-4.2.5, the paper's FFD scales): it must contain the
+   outermost block (block 0, or the last far-field block); each reference step it takes one
+   step of its own dt = h dt_0 and is interpolated linearly back to t_n + dt_0, its nodes
+   inside the contained block's interior are mapped from that block, and the contained
+   block's outer layer becomes its scale boundary, mapped from the far-field block (obstacle
+   and inflow nodes keep their own update); the outermost far-field block has open faces.
+   Needs block 0 without periodic faces (UNSUPPORTED otherwise).
+   UNSUPPORTED for FP16 storage; STATE while an adjoint tape is recording; OOM / CUDA when a
+   buffer or table cannot be created, in which case the domain is left exactly as before
+   the call. */
 lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3], double h,
                                const int32_t dims[3], int32_t* block_id);
 
-/* Removes the most recently added refined block (Sec. 5: dynamic scales are discarded and
-   rebuilt; the block's interior has already been post-mapped into every coarser block at
-   the end of each reference step).  Waits for the domain's stream, then releases the
-   block's buffers and tables.  INVALID_ARG unless block_id is the last block and >= 1;
-   STATE while an adjoint tape is recording. */
+/* Removes the most recently added scale block (Sec. 5: dynamic scales are discarded and
+   rebuilt; a refined block's interior has already been post-mapped into every coarser block
+   at the end of each reference step).  Waits for the domain's stream, then releases the
+   block's buffers and tables; removing a far-field block turns the outer layer of the block
+   it contained back into open faces.  INVALID_ARG unless block_id is the last block and
+   >= 1; STATE while an adjoint tape is recording. */
 lbm_status lbm_remove_scale_block(lbm_domain* dom, int32_t block_id);
 
 /* Dynamic scale construction, detection (Sec. 5): among the nodes of a block that are

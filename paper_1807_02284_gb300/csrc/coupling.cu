@@ -196,6 +196,26 @@ cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void k_outer_ghost(uint8_t* flags, int nx, int ny, int nz, int on) {
+  const size_t N = (size_t)nx * ny * nz;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((size_t)nx * ny));
+    const bool edge = x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1;
+    if (!edge) continue;
+    const uint8_t f = flags[idx];
+    const bool ghost = on && !(f & (F_SOLID | F_INFLOW));
+    flags[idx] = ghost ? (uint8_t)(f | F_GHOST) : (uint8_t)(f & ~F_GHOST);
+  }
+}
+
+cudaError_t launch_outer_ghost(uint8_t* flags, int nx, int ny, int nz, int on, cudaStream_t s) {
+  const size_t N = (size_t)nx * ny * nz;
+  const int grid = (int)std::min<size_t>((N + 255) / 256, 65535);
+  k_outer_ghost<<<grid, 256, 0, s>>>(flags, nx, ny, nz, on);
+  return cudaGetLastError();
+}
+
 __global__ void k_set_ghost_layer(uint8_t* flags, int nx, int ny, int nz) {
   const size_t N = (size_t)nx * ny * nz;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
@@ -292,6 +312,125 @@ static void release_block(lbm_domain* dom, Block& B) {
   B.prior.n = 0;
   for (MapTable& t : B.post) dom->dev_free(t.d);
   B.post.clear();
+  dom->dev_free(B.far_in.d);
+  dom->dev_free(B.far_out.d);
+  B.far_in = MapTable();
+  B.far_out = MapTable();
+}
+
+// Table of the nodes of block T that lie in block S's interior span [o + h, o + (n-2) h] on
+// every axis, with their source cells in S (prior-mapping regions of refined blocks' post
+// maps, and of far blocks' overlap).
+static std::vector<MapEntry> interior_table(const Block& S, const Block& T) {
+  std::vector<MapEntry> tab;
+  const int nT[3] = {T.nx, T.ny, T.nz};
+  const int nS[3] = {S.nx, S.ny, S.nz};
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    const double plo = S.origin[a] + S.h, phi = S.origin[a] + (nS[a] - 2) * S.h;
+    lo[a] = std::max(0, (int)std::ceil((plo - 1e-9 - T.origin[a]) / T.h));
+    hi[a] = std::min(nT[a] - 1, (int)std::floor((phi + 1e-9 - T.origin[a]) / T.h));
+    while (lo[a] <= hi[a] && T.origin[a] + lo[a] * T.h < plo - 1e-9) ++lo[a];
+    while (hi[a] >= lo[a] && T.origin[a] + hi[a] * T.h > phi + 1e-9) --hi[a];
+    if (lo[a] > hi[a]) return tab;
+  }
+  tab.reserve((size_t)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1));
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        const double p[3] = {T.origin[0] + x * T.h, T.origin[1] + y * T.h, T.origin[2] + z * T.h};
+        MapEntry m;
+        m.dst = (uint32_t)(((size_t)z * T.ny + y) * T.nx + x);
+        float t[3];
+        cell_of(S, p, &m.src, t);
+        m.tx = t[0]; m.ty = t[1]; m.tz = t[2];
+        tab.push_back(m);
+      }
+  return tab;
+}
+
+// Table of the outer-layer nodes of block T with their source cells in block S.
+static std::vector<MapEntry> outer_table(const Block& S, const Block& T) {
+  std::vector<MapEntry> tab;
+  for (int z = 0; z < T.nz; ++z)
+    for (int y = 0; y < T.ny; ++y)
+      for (int x = 0; x < T.nx; ++x) {
+        const bool edge = x == 0 || y == 0 || z == 0 || x == T.nx - 1 || y == T.ny - 1 ||
+                          z == T.nz - 1;
+        if (!edge) continue;
+        const double p[3] = {T.origin[0] + x * T.h, T.origin[1] + y * T.h, T.origin[2] + z * T.h};
+        MapEntry m;
+        m.dst = (uint32_t)(((size_t)z * T.ny + y) * T.nx + x);
+        float t[3];
+        cell_of(S, p, &m.src, t);
+        m.tx = t[0]; m.ty = t[1]; m.tz = t[2];
+        tab.push_back(m);
+      }
+  return tab;
+}
+
+// Index of the block a new far-field block has to surround: the last far block, else s0.
+static int outermost(const lbm_domain* dom) {
+  int c = 0;
+  for (size_t i = 1; i < dom->blocks.size(); ++i)
+    if (dom->blocks[i].far) c = (int)i;
+  return c;
+}
+
+static lbm_status add_far_block(lbm_domain* dom, const double origin[3], double h,
+                                const int32_t dims[3], int32_t* block_id) {
+  for (int a = 0; a < 3; ++a)
+    if (dom->desc.periodic[a])
+      return dom->fail(LBM_ERR_UNSUPPORTED, "far-field blocks need a reference block without periodic faces");
+  Block F;
+  F.nx = dims[0]; F.ny = dims[1]; F.nz = dims[2];
+  F.N = (size_t)F.nx * F.ny * F.nz;
+  for (int a = 0; a < 3; ++a) F.origin[a] = origin[a];
+  F.h = h;
+  F.nu = dom->desc.nu / h;
+  F.substeps = 1;
+  F.integer_ratio = false;
+  F.rp = dom->relax_params(F.nu);
+  F.far = true;
+  F.child = outermost(dom);
+  const Block& C = dom->blocks[F.child];
+  if (!contains(F, C)) return dom->fail(LBM_ERR_INVALID_ARG, "a far-field block must contain the outermost block");
+  if (std::fabs(1.0 - shear_rate(F.nu)) < 1e-12)
+    return dom->fail(LBM_ERR_INVALID_ARG, "K_hat is undefined for S = 1 (nu = 1/6 on this block)");
+  const int id = (int)dom->blocks.size();
+  lbm_status st = dom->alloc_block_levels(F, 2);
+  if (st != LBM_OK) {
+    release_block(dom, F);
+    return st;
+  }
+  dom->blocks.push_back(F);
+  auto abandon = [dom](lbm_status s) {
+    cudaStreamSynchronize(dom->stream);
+    release_block(dom, dom->blocks.back());
+    dom->blocks.pop_back();
+    return s;
+  };
+  st = dom->clear_block(id);
+  if (st != LBM_OK) return abandon(st);
+  Block& NF = dom->blocks.back();
+  const Block& CC = dom->blocks[NF.child];
+  NF.far_in.src = NF.child;
+  NF.far_in.dst = id;
+  NF.far_in.khat = (float)khat(CC, NF);
+  st = upload_table(dom, interior_table(CC, NF), &NF.far_in);
+  if (st != LBM_OK) return abandon(st);
+  NF.far_out.src = id;
+  NF.far_out.dst = NF.child;
+  NF.far_out.khat = (float)khat(NF, CC);
+  st = upload_table(dom, outer_table(NF, CC), &NF.far_out);
+  if (st != LBM_OK) return abandon(st);
+  Block& CW = dom->blocks[NF.child];
+  const cudaError_t e = launch_outer_ghost(CW.flags, CW.nx, CW.ny, CW.nz, 1, dom->stream);
+  if (e != cudaSuccess) return abandon(dom->cuda_fail(e, "scale-boundary flags"));
+  dom->pick_tiles(id);
+  dom->invalidate_graphs();
+  *block_id = id;
+  return LBM_OK;
 }
 
 extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3], double h,
@@ -300,22 +439,26 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
   cudaSetDevice(dom->desc.device);
   if (!origin || !dims || !block_id) return dom->fail(LBM_ERR_INVALID_ARG, "null argument");
   if (!(h > 0.0) || !std::isfinite(h)) return dom->fail(LBM_ERR_INVALID_ARG, "h must be positive");
-  if (h >= 1.0)
-    return dom->fail(LBM_ERR_UNSUPPORTED, "scales coarser than the reference scale (far field) are not built");
+  if (std::fabs(h - 1.0) < 1e-12) return dom->fail(LBM_ERR_INVALID_ARG, "h = 1 is the reference scale");
   if (dom->desc.storage != LBM_FP32)
-    return dom->fail(LBM_ERR_UNSUPPORTED, "refined blocks need FP32 storage");
+    return dom->fail(LBM_ERR_UNSUPPORTED, "scale blocks need FP32 storage");
   if (dom->tape)
     return dom->fail(LBM_ERR_STATE, "blocks cannot be added while an adjoint tape is recording");
   for (int a = 0; a < 3; ++a)
-    if (dims[a] < 4) return dom->fail(LBM_ERR_INVALID_ARG, "refined blocks need >= 4 nodes per axis");
+    if (dims[a] < 4) return dom->fail(LBM_ERR_INVALID_ARG, "scale blocks need >= 4 nodes per axis");
   if ((double)dims[0] * dims[1] * dims[2] * 27.0 >= 4294967295.0)
-    return dom->fail(LBM_ERR_INVALID_ARG, "refined block too large");
+    return dom->fail(LBM_ERR_INVALID_ARG, "scale block too large");
   if (dims[2] > 65535) return dom->fail(LBM_ERR_INVALID_ARG, "nz must be <= 65535");
-  if (dom->blocks.size() > 1 && h > dom->blocks.back().h + 1e-12)
-    return dom->fail(LBM_ERR_INVALID_ARG, "blocks must be added coarse to fine");
   if ((double)dom->blocks[0].N * 27.0 >= 4294967295.0)
     return dom->fail(LBM_ERR_UNSUPPORTED, "the reference block is too large for coupling tables");
-
+  if (h > 1.0) return add_far_block(dom, origin, h, dims, block_id);
+  {
+    int last = 0;                    // last refined block (far-field blocks do not count)
+    for (size_t i = 1; i < dom->blocks.size(); ++i)
+      if (!dom->blocks[i].far) last = (int)i;
+    if (last > 0 && h > dom->blocks[last].h + 1e-12)
+      return dom->fail(LBM_ERR_INVALID_ARG, "refined blocks must be added coarse to fine");
+  }
   Block B;
   B.nx = dims[0]; B.ny = dims[1]; B.nz = dims[2];
   B.N = (size_t)B.nx * B.ny * B.nz;
@@ -391,41 +534,13 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
   // post tables: nodes of every coarser block inside the new block's interior span
   for (int k = 0; k < id; ++k) {
     const Block& T = dom->blocks[k];
-    if (!(T.h > NB.h)) continue;
-    const int nT[3] = {T.nx, T.ny, T.nz};
-    const int nB[3] = {NB.nx, NB.ny, NB.nz};
-    int lo[3], hi[3];
-    bool empty = false;
-    for (int a = 0; a < 3; ++a) {
-      const double plo = NB.origin[a] + NB.h, phi = NB.origin[a] + (nB[a] - 2) * NB.h;
-      lo[a] = std::max(0, (int)std::ceil((plo - 1e-9 - T.origin[a]) / T.h));
-      hi[a] = std::min(nT[a] - 1, (int)std::floor((phi + 1e-9 - T.origin[a]) / T.h));
-      while (lo[a] <= hi[a] && T.origin[a] + lo[a] * T.h < plo - 1e-9) ++lo[a];
-      while (hi[a] >= lo[a] && T.origin[a] + hi[a] * T.h > phi + 1e-9) --hi[a];
-      if (lo[a] > hi[a]) empty = true;
-    }
+    if (T.far || !(T.h > NB.h)) continue;
     MapTable mt;
     mt.src = id;
     mt.dst = k;
     mt.khat = (float)khat(NB, T);
-    if (!empty) {
-      std::vector<MapEntry> tab;
-      tab.reserve((size_t)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1));
-      for (int z = lo[2]; z <= hi[2]; ++z)
-        for (int y = lo[1]; y <= hi[1]; ++y)
-          for (int x = lo[0]; x <= hi[0]; ++x) {
-            const double p[3] = {T.origin[0] + x * T.h, T.origin[1] + y * T.h,
-                                 T.origin[2] + z * T.h};
-            MapEntry m;
-            m.dst = (uint32_t)(((size_t)z * T.ny + y) * T.nx + x);
-            float t[3];
-            cell_of(NB, p, &m.src, t);
-            m.tx = t[0]; m.ty = t[1]; m.tz = t[2];
-            tab.push_back(m);
-          }
-      st = upload_table(dom, tab, &mt);
-      if (st != LBM_OK) return abandon(st);
-    }
+    st = upload_table(dom, interior_table(NB, T), &mt);
+    if (st != LBM_OK) return abandon(st);
     NB.post.push_back(mt);
   }
   dom->pick_tiles(id);
@@ -445,9 +560,16 @@ extern "C" lbm_status lbm_remove_scale_block(lbm_domain* dom, int32_t block_id) 
   // joined into the domain's stream, so waiting for it makes the buffers free to release
   const cudaError_t e = cudaStreamSynchronize(dom->stream);
   if (e != cudaSuccess) return dom->cuda_fail(e, "cudaStreamSynchronize");
+  const bool far = dom->blocks.back().far;
+  const int child = dom->blocks.back().child;
   release_block(dom, dom->blocks.back());
   dom->blocks.pop_back();
   dom->invalidate_graphs();
+  if (far) {   // the child's outer layer is again an open face
+    Block& C = dom->blocks[child];
+    const cudaError_t e2 = launch_outer_ghost(C.flags, C.nx, C.ny, C.nz, 0, dom->stream);
+    if (e2 != cudaSuccess) return dom->cuda_fail(e2, "scale-boundary flags");
+  }
   return LBM_OK;
 }
 
@@ -497,6 +619,29 @@ static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t, cudaStrea
   return launch_map(a, dom->desc.storage, stream);
 }
 
+// Mapping between the current states of two blocks along a far-field table (the destination
+// nodes carrying any of `skip` are left alone).
+static cudaError_t far_map(lbm_domain* dom, const MapTable& t, uint8_t skip, cudaStream_t stream) {
+  const Block& S = dom->blocks[t.src];
+  Block& T = dom->blocks[t.dst];
+  MapArgs a{};
+  a.table = t.d;
+  a.n = t.n;
+  a.f_lo = a.f_hi = S.lv[S.cur].f;
+  a.c_lo = a.c_hi = S.lv[S.cur].c;
+  a.theta = 0.0f;
+  a.src_flags = S.flags;
+  a.snx = S.nx; a.sny = S.ny; a.snz = S.nz; a.sN = S.N;
+  a.f_dst = T.lv[T.cur].f;
+  a.u_dst = T.lv[T.cur].u;
+  a.c_dst = T.lv[T.cur].c;
+  a.dst_flags = T.flags;
+  a.skip_mask = skip;
+  a.dN = T.N;
+  a.khat = t.khat;
+  return launch_map(a, dom->desc.storage, stream);
+}
+
 // One reference step of Algorithm 1 over all blocks.  Per refined block: the ghost-layer
 // mapping for the next sub-step runs on the auxiliary stream while the current sub-step's
 // collide-stream runs on the main stream (the two write disjoint nodes); the last sub-step
@@ -518,9 +663,40 @@ lbm_status multiscale_step(lbm_domain* dom) {
     if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");
     B0.cur = nxt;
   }
+  // far field (Sec. 4.2.4-4.2.5): every far block takes one step of its own dt = h dt_0 and
+  // is interpolated back to t_n + dt_0 (the fused alignment with weights 0, 1 - 1/h, 1/h);
+  // then, inner to outer, its nodes inside its child's interior come from the child, and,
+  // outer to inner, the child's outer layer comes from it
+  std::vector<int> far;
+  for (size_t bi = 1; bi < dom->blocks.size(); ++bi)
+    if (dom->blocks[bi].far) far.push_back((int)bi);
+  for (int f : far) {
+    Block& F = dom->blocks[f];
+    const int nxt = F.cur ^ 1;
+    BlockView v = dom->view(f, F.cur, nxt);
+    v.f_al0 = F.lv[F.cur].f;
+    v.c_al0 = F.lv[F.cur].c;
+    v.al0 = 0.0f;
+    v.al1 = (float)(1.0 - 1.0 / F.h);
+    v.al2 = (float)(1.0 / F.h);
+    e = launch_step_align(v, F.bx, F.by, s, F.minb);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "far-field step");
+    F.cur = nxt;
+  }
+  for (int f : far) {
+    const Block& F = dom->blocks[f];
+    e = far_map(dom, F.far_in, F_SOLID | F_GHOST, s);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "far-field overlap mapping");
+  }
+  for (size_t k = far.size(); k-- > 0;) {
+    const Block& F = dom->blocks[far[k]];
+    e = far_map(dom, F.far_out, F_SOLID | F_INFLOW, s);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "far-field boundary mapping");
+  }
   for (size_t bi = 1; bi < dom->blocks.size(); ++bi) {
     const int b = (int)bi;
     Block& B = dom->blocks[b];
+    if (B.far) continue;
     const int L = saved[b];
     const int A = (L + 1) % 3, Bv = (L + 2) % 3;
     const bool exact = B.integer_ratio && std::fabs(B.substeps * B.h - 1.0) < 1e-9;

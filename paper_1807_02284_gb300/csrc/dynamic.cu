@@ -162,6 +162,7 @@ extern "C" lbm_status lbm_init_block_from_parent(lbm_domain* dom, int32_t block_
   lbm_status st = dom->check_block(block_id);
   if (st != LBM_OK) return st;
   if (block_id == 0) return dom->fail(LBM_ERR_INVALID_ARG, "the reference block has no parent");
+  if (dom->blocks[block_id].far) return dom->fail(LBM_ERR_INVALID_ARG, "far-field blocks are started with lbm_init_macro");
   Block& B = dom->blocks[block_id];
   const Block& P = dom->blocks[B.prior.src];
   cudaError_t e;
@@ -220,7 +221,7 @@ extern "C" lbm_status lbm_build_dynamic_scale(lbm_domain* dom, int32_t src_block
     if ((double)m / h > 65535.0) return dom->fail(LBM_ERR_INVALID_ARG, "h too small for this reference block");
   }
   const int last = (int)dom->blocks.size() - 1;
-  if (replace_last && (last < 1 || src_block == last))
+  if (replace_last && (last < 1 || src_block == last || dom->blocks[last].far))
     return dom->fail(LBM_ERR_INVALID_ARG, "replace_last needs a refined last block other than the source");
   int64_t count = 0;
   int32_t box[6];

@@ -110,6 +110,9 @@ cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size
 // ---- coupling.cu
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s);
 cudaError_t launch_set_ghost_layer(uint8_t* flags, int nx, int ny, int nz, cudaStream_t s);
+// outer layer of a block surrounded by a far-field block: GHOST on (except obstacle and
+// inflow nodes, which keep their own update) or off
+cudaError_t launch_outer_ghost(uint8_t* flags, int nx, int ny, int nz, int on, cudaStream_t s);
 
 // ---- kernels_batch.cu
 cudaError_t launch_step_batch(const BlockView* views_dev, const WorkItem* items, int n_items,

@@ -307,6 +307,11 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
       if (block_id == 0) for (int a = 0; a < 3; ++a) per[a] = dom->desc.periodic[a];
       e = launch_near_solid(B.flags, B.nx, B.ny, B.nz, per, dom->stream);
     }
+    // a block surrounded by a far-field block keeps its outer layer as scale boundary,
+    // except where the new flags put obstacles or inflow nodes
+    for (size_t i = 1; i < dom->blocks.size() && e == cudaSuccess; ++i)
+      if (dom->blocks[i].far && dom->blocks[i].child == block_id)
+        e = launch_outer_ghost(B.flags, B.nx, B.ny, B.nz, 1, dom->stream);
     if (e != cudaSuccess) return dom->cuda_fail(e, "set flags");
     dom->invalidate_graphs();
     return LBM_OK;

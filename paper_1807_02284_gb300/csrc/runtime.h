@@ -43,6 +43,12 @@ struct Block {
   int bx = 128, by = 2;    // tile of the collide-stream launch
   int minb = 3;            // register bound of the collide-stream launch (CTAs per SM)
   bool tuned = false;      // tile shape chosen by autotune_tiles
+  // far-field block (h > 1, Sec. 4.2.4-4.2.5): it surrounds block `child` (s0 or the previous
+  // far block), takes its nodes inside the child's interior from the child (far_in) and
+  // gives the child its outer layer (far_out)
+  bool far = false;
+  int child = -1;
+  MapTable far_in, far_out;
 };
 
 struct TapeState;          // adjoint tape (adjoint.cu)

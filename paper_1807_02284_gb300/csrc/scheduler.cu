@@ -23,6 +23,10 @@ struct GraphCache {
 static std::vector<int> next_levels(const std::vector<lbm::Block>& blocks, std::vector<int> cur) {
   cur[0] ^= 1;
   for (size_t b = 1; b < blocks.size(); ++b) {
+    if (blocks[b].far) {     // far-field blocks ping-pong like the reference block
+      cur[b] ^= 1;
+      continue;
+    }
     const int L = cur[b], A = (L + 1) % 3, B = (L + 2) % 3;
     int c = L;
     for (int j = 1; j <= blocks[b].substeps; ++j) c = (j == 1) ? A : (c == A ? B : A);

@@ -254,6 +254,20 @@ def smooth_field(block: Block, seed, amp=0.05, wavelength=32.0):
     return u, rho, c
 
 
+def far_block(inner: Block, h: float, pad: float, seed=0, amp=0.02, wavelength=32.0) -> Block:
+    """A far-field block of spacing h (> 1) around ``inner``: it starts ``pad`` reference
+    units below inner's lower corner on every axis and reaches at least ``pad`` beyond its
+    upper corner; seeded smooth velocity, density and scalar fields (the same continuous
+    fields on any block), no obstacles."""
+    lo = np.array(inner.origin, dtype=np.float64) - pad
+    hi = np.array(inner.origin, dtype=np.float64) + (np.array(inner.dims) - 1) * inner.h + pad
+    dims = tuple(int(math.ceil((hi[a] - lo[a]) / h - 1e-9)) + 1 for a in range(3))
+    b = _empty_block(dims, origin=tuple(lo), h=h)
+    u, rho, c = smooth_field(b, seed, amp=amp, wavelength=wavelength)
+    b.u0, b.rho0, b.c0 = u, rho, c
+    return b
+
+
 def multiscale(seed=2, sphere_seed=3, nu=1e-5, u_in=0.08, scale=1.0, flow_amp=0.0) -> Scene:
     """Continuous-scale 3-block domain: s0 128^3 at h=1, s1 96^3 at h=1/1.5 with origin
     (24,32,32), s2 64^3 at h=1/2.25 with origin (36,50,50); 8 seeded spheres (r in [4,12])
