@@ -77,6 +77,17 @@ class Blk:
         return lo, hi
 
 
+def put_nodes(st: grid.State, z, y, x, f_rows, u_rows, c_vals) -> grid.State:
+    """A copy of st with the listed nodes' populations (K, 27), velocities (K, 3) and
+    scalars (K,) replaced (out of place, so reverse-mode differentiation can run through)."""
+    _, Z, Y, X = st.f.shape
+    lin = (z * Y + y) * X + x
+    f = st.f.reshape(27, -1).index_copy(1, lin, f_rows.T.to(st.f.dtype)).reshape(st.f.shape)
+    u = st.u.reshape(3, -1).index_copy(1, lin, u_rows.T.to(st.u.dtype)).reshape(st.u.shape)
+    c = st.c.reshape(-1).index_copy(0, lin, c_vals.to(st.c.dtype)).reshape(st.c.shape)
+    return grid.State(f, u, c, st.flags)
+
+
 def shear_rate(nu: float) -> float:
     return 1.0 / (3.0 * nu + 0.5)
 
@@ -249,9 +260,7 @@ class MultiScale:
         z, y, x, f, cc = z[ok], y[ok], x[ok], f[ok], cc[ok]
         fm = map_populations(f, k_hat(b, c))
         _, u = cmr.macros(fm)
-        c.state.f[:, z, y, x] = fm.T
-        c.state.u[:, z, y, x] = u.T
-        c.state.c[z, y, x] = cc
+        c.state = put_nodes(c.state, z, y, x, fm, u, cc)
 
     def _containing_parent(self, i: int) -> int:
         b = self.blocks[i]
@@ -289,9 +298,7 @@ class MultiScale:
         z, y, x, f, c = z[ok], y[ok], x[ok], f[ok], c[ok]
         fm = map_populations(f, k_hat(p, b))
         _, u = cmr.macros(fm)
-        b.state.f[:, z, y, x] = fm.T
-        b.state.u[:, z, y, x] = u.T
-        b.state.c[z, y, x] = c
+        b.state = put_nodes(b.state, z, y, x, fm, u, c)
 
     def post_map(self, i: int, k: int):
         """Coarser block k's nodes inside block i's interior span from block i."""
@@ -313,9 +320,7 @@ class MultiScale:
         z, y, x, f, c = z[ok], y[ok], x[ok], f[ok], c[ok]
         fm = map_populations(f, k_hat(b, tgt))
         _, u = cmr.macros(fm)
-        tgt.state.f[:, z, y, x] = fm.T
-        tgt.state.u[:, z, y, x] = u.T
-        tgt.state.c[z, y, x] = c
+        tgt.state = put_nodes(tgt.state, z, y, x, fm, u, c)
 
     @staticmethod
     def lagrange3(t0, t1, t2, T):

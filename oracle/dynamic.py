@@ -130,9 +130,7 @@ def add_block_from_parent(ms: coupling.MultiScale, origin, h: float, dims):
     z, y, x, f, c = z[ok], y[ok], x[ok], f[ok], c[ok]
     fm = coupling.map_populations(f, coupling.k_hat(par, b))
     _, u = cmr.macros(fm)
-    st.f[:, z, y, x] = fm.T
-    st.u[:, z, y, x] = u.T
-    st.c[z, y, x] = c
+    b.state = coupling.put_nodes(st, z, y, x, fm, u, c)
     return i
 
 
