@@ -282,10 +282,19 @@ lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every);
    carried unchanged by every step, so dL_du0 at inflow nodes is the gradient with respect to
    that inflow velocity; dL_dinflow (3N floats, device, may be NULL) receives the same values
    at inflow nodes and 0 elsewhere (inflow velocities must not be changed while the tape
-   records).  Single-block domains with FP32 storage, periodic faces and the lagged-gradient
-   (or fixed) relaxation only (UNSUPPORTED otherwise).  Not in the paper. */
+   records).  Continuous-scale domains (refined blocks) are reversed through the whole
+   Algorithm 1 schedule (prior- and post-mapping, sub-steps, temporal alignment); the loss
+   is a function of block 0's final state, dL_du0 is block 0's gradient and
+   lbm_adjoint_block_grad returns the other blocks'.  FP32 storage and the lagged-gradient
+   (or fixed) relaxation only; far-field blocks are not covered (UNSUPPORTED otherwise).
+   Not in the paper. */
 lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dscalar_final,
                             const float* dL_du_final, float* dL_du0, float* dL_dinflow);
+
+/* After lbm_adjoint_step on a domain with refined blocks: copies dL/du_0 of block block_id
+   (3 N_b floats, device) to dL_du0.  STATE if no multi-block reverse sweep has run.  Not in
+   the paper. */
+lbm_status lbm_adjoint_block_grad(lbm_domain* dom, int32_t block_id, float* dL_du0);
 
 /* Largest n_nodes accepted by lbm_reduce_noalloc. */
 #define LBM_REDUCE_NOALLOC_MAX_NODES 67108864

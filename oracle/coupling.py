@@ -20,7 +20,9 @@ With the per-block high-order rates equal on both sides, K_hat_k = 1 for k outsi
 Readings (the paper is silent or ambiguous):
   * Spatial interpolation is trilinear over the 8 nodes of the source cell containing the
     point (Sec. 4.2.2); corners that are obstacle voxels of the source are dropped and the
-    remaining weights renormalised; if all 8 are obstacles the node is left unchanged.
+    remaining weights renormalised; if all 8 are obstacles, a scale-boundary (ghost) node
+    takes the rest state (rho = 1, u = 0, scalar 0: it has no dynamics of its own to keep)
+    and a post-mapped node is left unchanged (it keeps its own update).
   * Prior-mapping source: the nearest coarser block that contains the whole target block
     (Sec. 4.2.5 chooses the nearest coarser scale per node; for nested blocks this is the
     same block).  Post-mapping targets: every coarser block (Sec. 4.2.5), at its nodes that
@@ -86,6 +88,17 @@ def put_nodes(st: grid.State, z, y, x, f_rows, u_rows, c_vals) -> grid.State:
     u = st.u.reshape(3, -1).index_copy(1, lin, u_rows.T.to(st.u.dtype)).reshape(st.u.shape)
     c = st.c.reshape(-1).index_copy(0, lin, c_vals.to(st.c.dtype)).reshape(st.c.shape)
     return grid.State(f, u, c, st.flags)
+
+
+def rest_nodes(st: grid.State, z, y, x) -> grid.State:
+    """Scale-boundary nodes whose source corners are all obstacle voxels: no value can be
+    interpolated, so they take the rest state (rho = 1, u = 0, scalar 0)."""
+    if z.numel() == 0:
+        return st
+    feq = cmr.equilibrium(torch.ones(1, dtype=DT), torch.zeros(1, 3, dtype=DT))
+    k = z.numel()
+    return put_nodes(st, z, y, x, feq.expand(k, 27), torch.zeros(k, 3, dtype=DT),
+                     torch.zeros(k, dtype=DT))
 
 
 def shear_rate(nu: float) -> float:
@@ -257,6 +270,7 @@ class MultiScale:
         c = self.blocks[b.child]
         z, y, x = self._ghost_nodes(c)
         f, cc, ok = interpolate(b, b.state.f, b.state.c, node_positions(c, z, y, x))
+        c.state = rest_nodes(c.state, z[~ok], y[~ok], x[~ok])
         z, y, x, f, cc = z[ok], y[ok], x[ok], f[ok], cc[ok]
         fm = map_populations(f, k_hat(b, c))
         _, u = cmr.macros(fm)
@@ -295,6 +309,7 @@ class MultiScale:
         keep = (b.state.flags[z, y, x] & SOLID) == 0
         z, y, x = z[keep], y[keep], x[keep]
         f, c, ok = interpolate(p, f_src, c_src, node_positions(b, z, y, x))
+        b.state = rest_nodes(b.state, z[~ok], y[~ok], x[~ok])
         z, y, x, f, c = z[ok], y[ok], x[ok], f[ok], c[ok]
         fm = map_populations(f, k_hat(p, b))
         _, u = cmr.macros(fm)

@@ -92,7 +92,9 @@ __device__ __forceinline__ FaceMask face_mask(const BlockView& v, int x, int y, 
   return f;
 }
 
-template <bool OPEN, int K = 0>
+// ACC: add to the adjoint already held by the slot (the reverse of a multi-block schedule,
+// where a level is read by several operations) instead of storing it.
+template <bool OPEN, bool ACC, int K = 0>
 __device__ __forceinline__ void push_all(const float (&A)[27], float* __restrict__ lam,
                                          uint32_t N, const Nbr<uint32_t>& n, uint32_t idx,
                                          const uint8_t* __restrict__ flags, bool near,
@@ -108,12 +110,63 @@ __device__ __forceinline__ void push_all(const float (&A)[27], float* __restrict
       constexpr FaceMask src_bits = (1u << (1 - cx)) | (1u << (4 - cy)) | (1u << (7 - cz));
       const bool face = (fm & (bb ? own : src_bits)) != 0u;
       if (face) atomicAdd(lam + slot, A[K]);
+      else if (ACC) lam[slot] += A[K];
       else lam[slot] = A[K];
     } else {
-      lam[slot] = A[K];
+      if (ACC) lam[slot] += A[K];
+      else lam[slot] = A[K];
     }
-    push_all<OPEN, K + 1>(A, lam, N, n, idx, flags, near, fm);
+    push_all<OPEN, ACC, K + 1>(A, lam, N, n, idx, flags, near, fm);
   }
+}
+
+// Transpose of the collision (and of the scale mapping, which is the same relaxation with
+// other keep factors): K holds the central moments before relaxation at velocity u (it is
+// overwritten), A the adjoint of the post-collision populations on entry and the adjoint of
+// the pre-collision populations on return; the velocity terms are added to ub and the
+// adjoint of the keep factors of the high-order groups to kbar.
+__device__ __forceinline__ void collide_vjp(float (&K)[27], float (&A)[27], float drho, float ux,
+                                            float uy, float uz, float inv, const Keep& kf,
+                                            float (&ub)[3], float (&kbar)[4]) {
+  float T[27];
+  // the inverse sweeps ran z, y, x: undo x first; its input is inv_y(inv_z(relaxed))
+#pragma unroll
+  for (int k = 0; k < 27; ++k) T[k] = K[k];
+  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
+  inv_axis<9>(T, uz);
+  inv_axis<3>(T, uy);
+  inv_axis_vjp<1>(T, A, ux, ub[0]);
+#pragma unroll
+  for (int k = 0; k < 27; ++k) T[k] = K[k];
+  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
+  inv_axis<9>(T, uz);
+  inv_axis_vjp<3>(T, A, uy, ub[1]);
+#pragma unroll
+  for (int k = 0; k < 27; ++k) T[k] = K[k];
+  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
+  inv_axis_vjp<9>(T, A, uz, ub[2]);
+  float bar[4] = {0.f, 0.f, 0.f, 0.f};     // d/d(rho - 1), d/du
+  relax_vjp(K, A, drho, ux, uy, uz, kf, bar, kbar);
+  ub[0] += bar[1];
+  ub[1] += bar[2];
+  ub[2] += bar[3];
+  float drhob = bar[0];
+  // the shifts ran x, y, z: undo z first; its input is unshift_z(K)
+  unshift_axis<9>(K, uz);
+  shift_axis_vjp<9>(K, A, uz, ub[2]);
+  unshift_axis<3>(K, uy);
+  shift_axis_vjp<3>(K, A, uy, ub[1]);
+  unshift_axis<1>(K, ux);
+  shift_axis_vjp<1>(K, A, ux, ub[0]);
+  // u = j / rho with rho = 1 + r_000, j = (r_100, r_010, r_001)
+  drhob -= (ub[0] * ux + ub[1] * uy + ub[2] * uz) * inv;
+  A[kap(0, 0, 0)] += drhob;
+  A[kap(1, 0, 0)] += ub[0] * inv;
+  A[kap(0, 1, 0)] += ub[1] * inv;
+  A[kap(0, 0, 1)] += ub[2] * inv;
+  raw_axis_vjp<9>(A);
+  raw_axis_vjp<3>(A);
+  raw_axis_vjp<1>(A);                    // A = adjoint of the pulled populations
 }
 
 // Zeroes the adjoint slots of the nodes on open faces before pass A accumulates into them.
@@ -133,8 +186,10 @@ __global__ void k_zero_face_slots(float* __restrict__ lam, int nx, int ny, int n
 
 // MINB: CTAs per SM the register allocation is bounded for (3: no spills; 4: some spills,
 // more warps in flight); the faster one is chosen at run time.
-// OPEN: some face of the block is open (face slots accumulate; see FaceMask).
-template <int MINB, bool OPEN>
+// OPEN: some face of the block is open (face slots accumulate; see FaceMask).  ACC: the
+// adjoints of the input level are added to (multi-block reverse), and scale-boundary (ghost)
+// nodes, which the step does not update, are left to the mapping that wrote them.
+template <int MINB, bool OPEN, bool ACC>
 __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   const BlockView& v = a.fwd;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -145,7 +200,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   const Nbr<uint32_t> n = neighbours<uint32_t>(v, x, y, z);
   const uint32_t idx = n.p0 + n.r0 + n.x0;
   const uint8_t fl = v.flags[idx];
-  if (fl & F_SOLID) {
+  if ((fl & F_SOLID) || (ACC && (fl & F_GHOST))) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = 0.0f;
     return;
@@ -165,13 +220,20 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
 #pragma unroll
       for (int a2 = 0; a2 < 3; ++a2) ub[a2] = fmaf(l, 3.0f * c[a2] + 9.0f * cu * c[a2] - 3.0f * u[a2], ub[a2]);
     }
-    a.ups_out[idx] = ub[0];
-    a.ups_out[N + idx] = ub[1];
-    a.ups_out[2 * N + idx] = ub[2];
-    float Z[27];
+    if (ACC) {
+      a.ups_out[idx] += ub[0];
+      a.ups_out[N + idx] += ub[1];
+      a.ups_out[2 * N + idx] += ub[2];
+    } else {
+      a.ups_out[idx] = ub[0];
+      a.ups_out[N + idx] = ub[1];
+      a.ups_out[2 * N + idx] = ub[2];
+      float Z[27];
 #pragma unroll
-    for (int k = 0; k < 27; ++k) Z[k] = 0.0f;
-    push_all<OPEN>(Z, a.lam_out, N, n, idx, v.flags, (fl & F_NEAR_SOLID) != 0, face_mask<OPEN>(v, x, y, z));
+      for (int k = 0; k < 27; ++k) Z[k] = 0.0f;
+      push_all<OPEN, false>(Z, a.lam_out, N, n, idx, v.flags, (fl & F_NEAR_SOLID) != 0,
+                            face_mask<OPEN>(v, x, y, z));
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = 0.0f;
     return;
@@ -218,47 +280,9 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   float A[27];
 #pragma unroll
   for (int k = 0; k < 27; ++k) A[k] = a.lam_in[(uint32_t)k * N + idx];
-  float T[27];
-  // the inverse sweeps ran z, y, x: undo x first; its input is inv_y(inv_z(relaxed))
-#pragma unroll
-  for (int k = 0; k < 27; ++k) T[k] = K[k];
-  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
-  inv_axis<9>(T, uz);
-  inv_axis<3>(T, uy);
-  inv_axis_vjp<1>(T, A, ux, ub[0]);
-#pragma unroll
-  for (int k = 0; k < 27; ++k) T[k] = K[k];
-  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
-  inv_axis<9>(T, uz);
-  inv_axis_vjp<3>(T, A, uy, ub[1]);
-#pragma unroll
-  for (int k = 0; k < 27; ++k) T[k] = K[k];
-  relax_to_equilibrium(T, drho, ux, uy, uz, kf);
-  inv_axis_vjp<9>(T, A, uz, ub[2]);
-  float bar[4] = {0.f, 0.f, 0.f, 0.f};     // d/d(rho - 1), d/du
   float kbar[4] = {0.f, 0.f, 0.f, 0.f};    // d/d(keep factor) of the high-order groups
-  relax_vjp(K, A, drho, ux, uy, uz, kf, bar, kbar);
-  ub[0] += bar[1];
-  ub[1] += bar[2];
-  ub[2] += bar[3];
-  float drhob = bar[0];
-  // the shifts ran x, y, z: undo z first; its input is unshift_z(K)
-  unshift_axis<9>(K, uz);
-  shift_axis_vjp<9>(K, A, uz, ub[2]);
-  unshift_axis<3>(K, uy);
-  shift_axis_vjp<3>(K, A, uy, ub[1]);
-  unshift_axis<1>(K, ux);
-  shift_axis_vjp<1>(K, A, ux, ub[0]);
-  // u = j / rho with rho = 1 + r_000, j = (r_100, r_010, r_001)
-  drhob -= (ub[0] * ux + ub[1] * uy + ub[2] * uz) * inv;
-  A[kap(0, 0, 0)] += drhob;
-  A[kap(1, 0, 0)] += ub[0] * inv;
-  A[kap(0, 1, 0)] += ub[1] * inv;
-  A[kap(0, 0, 1)] += ub[2] * inv;
-  raw_axis_vjp<9>(A);
-  raw_axis_vjp<3>(A);
-  raw_axis_vjp<1>(A);                    // A = adjoint of the pulled populations
-  push_all<OPEN>(A, a.lam_out, N, n, idx, v.flags, near, face_mask<OPEN>(v, x, y, z));
+  collide_vjp(K, A, drho, ux, uy, uz, inv, kf, ub, kbar);
+  push_all<OPEN, ACC>(A, a.lam_out, N, n, idx, v.flags, near, face_mask<OPEN>(v, x, y, z));
 
   // ---- adjoint of the adaptive factor: K_g = 1 - 1/(phi nu3_g + 1/2)
   float mu_scale = 0.0f;
@@ -276,16 +300,21 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = v.rp.adaptive ? mu_scale * diff[i] : 0.0f;
 }
 
-static void launch_pass_a(const AdjArgs& a, int minb, bool open, dim3 grd, dim3 blk, cudaStream_t s) {
-  if (open) {
-    if (minb == 4) k_adj_a<4, true><<<grd, blk, 0, s>>>(a);
-    else k_adj_a<3, true><<<grd, blk, 0, s>>>(a);
+static void launch_pass_a(const AdjArgs& a, int minb, bool open, dim3 grd, dim3 blk, cudaStream_t s,
+                          bool acc = false) {
+  if (acc) {   // multi-block reverse: 3 CTAs/SM, open faces (every refined block has them)
+    if (open) k_adj_a<3, true, true><<<grd, blk, 0, s>>>(a);
+    else k_adj_a<3, false, true><<<grd, blk, 0, s>>>(a);
+  } else if (open) {
+    if (minb == 4) k_adj_a<4, true, false><<<grd, blk, 0, s>>>(a);
+    else k_adj_a<3, true, false><<<grd, blk, 0, s>>>(a);
   } else {
-    if (minb == 4) k_adj_a<4, false><<<grd, blk, 0, s>>>(a);
-    else k_adj_a<3, false><<<grd, blk, 0, s>>>(a);
+    if (minb == 4) k_adj_a<4, false, false><<<grd, blk, 0, s>>>(a);
+    else k_adj_a<3, false, false><<<grd, blk, 0, s>>>(a);
   }
 }
 
+template <bool ACC>
 __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
   const BlockView& v = a.fwd;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -319,7 +348,7 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
               wm[1] * __ldg(m1 + (n.p0 + n.rm + n.x0)) + wp[1] * __ldg(m1 + (n.p0 + n.rp + n.x0)) +
               wm[2] * __ldg(m2 + (n.pm + n.r0 + n.x0)) + wp[2] * __ldg(m2 + (n.pp + n.r0 + n.x0));
     s = fmaf(ws[0], __ldg(m0 + idx), fmaf(ws[1], __ldg(m1 + idx), fmaf(ws[2], __ldg(m2 + idx), s)));
-    a.ups_out[(uint32_t)c * N + idx] = inflow ? a.ups_out[(uint32_t)c * N + idx] + s : s;
+    a.ups_out[(uint32_t)c * N + idx] = (ACC || inflow) ? a.ups_out[(uint32_t)c * N + idx] + s : s;
   }
   // scalar adjoint: gather from the neighbours whose departure cell contains this node
   const uint32_t xs[3] = {n.xm, n.x0, n.xp};
@@ -341,7 +370,7 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
             (dz == 0 && ps[0] == ps[1]) || (dz == 2 && ps[2] == ps[1]))
           continue;
         const uint32_t j = ps[dz] + rs[dy] + xs[dx];
-        if (__ldg(v.flags + j) & (F_SOLID | F_SCALAR_SRC)) continue;
+        if (__ldg(v.flags + j) & (F_SOLID | F_SCALAR_SRC | F_GHOST)) continue;
         const float G = __ldg(a.gam_in + j);
         if (G == 0.0f) continue;
         const Axis1 ax = sl_axis(cx[dx], __ldg(a.u_next + j), v.nx, v.per[0]);
@@ -352,7 +381,7 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
         const float wz = (az.i0 == z ? 1.0f - az.t : 0.0f) + (az.i1 == z ? az.t : 0.0f);
         gam = fmaf(wx * wy * wz, G, gam);
       }
-  a.gam_out[idx] = gam;
+  a.gam_out[idx] = ACC ? a.gam_out[idx] + gam : gam;
 }
 
 // dL/du_0 = Ups^0 + (dD^0/du_0)^T Lam^0 with D^0_k = w_k (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)).
@@ -384,6 +413,152 @@ __global__ void k_adj_init(const float* __restrict__ d0, const float* __restrict
   }
 }
 
+// ---------------------------------------------------------------- multi-block reverse
+
+// Adjoint buffers of one time level of a block (27 planes of populations, 3 of velocity, 1 of
+// scalar).
+struct AdjLevel {
+  float* f = nullptr;
+  float* u = nullptr;
+  float* c = nullptr;
+};
+
+// Transpose of one scale mapping (Sec. 3.2): per table entry the forward interpolation is
+// recomputed, the adjoint of the mapped node (populations, its velocity, its scalar) goes
+// back through the relaxation with keep factor K_hat and then, with the trilinear weights,
+// to the source corners at the two time levels (added atomically: corners are shared).  The
+// mapped node's adjoint is then cleared, since the mapping overwrote its previous value.
+__global__ void __launch_bounds__(128) k_map_vjp(MapArgs a, AdjLevel dst, AdjLevel lo, AdjLevel hi) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n) return;
+  const MapEntry m = a.table[e];
+  if (a.dst_flags[m.dst] & a.skip_mask) return;
+  const uint32_t sN = (uint32_t)a.sN, sy = (uint32_t)a.snx, sz = (uint32_t)a.snx * (uint32_t)a.sny;
+  uint32_t sc[8];
+  float w[8];
+  float wsum = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    sc[c] = m.src + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz;
+    const float wc = ((c & 1) ? m.tx : 1.0f - m.tx) * (((c >> 1) & 1) ? m.ty : 1.0f - m.ty) *
+                     ((c >> 2) ? m.tz : 1.0f - m.tz);
+    w[c] = (__ldg(a.src_flags + sc[c]) & F_SOLID) ? 0.0f : wc;
+    wsum += w[c];
+  }
+  const uint32_t dN = (uint32_t)a.dN, d = m.dst;
+  if (!(wsum > 0.0f)) {
+    if (a.rest_if_empty) {         // the rest state written there depends on nothing
+#pragma unroll
+      for (int k = 0; k < 27; ++k) dst.f[(uint32_t)k * dN + d] = 0.0f;
+      dst.u[d] = dst.u[dN + d] = dst.u[2 * dN + d] = 0.0f;
+      dst.c[d] = 0.0f;
+    }
+    return;
+  }
+  const float inv_w = 1.0f / wsum;
+  const float th = a.theta <= 0.0f ? 0.0f : (a.theta >= 1.0f ? 1.0f : a.theta);
+  const float* flo = static_cast<const float*>(a.f_lo);
+  const float* fhi = static_cast<const float*>(a.f_hi);
+  float K[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    float v = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const uint32_t i = (uint32_t)k * sN + sc[c];
+      const float fl = th < 1.0f ? __ldg(flo + i) : 0.0f;
+      const float fh = th > 0.0f ? __ldg(fhi + i) : 0.0f;
+      v = fmaf(w[c], th > 0.0f ? fmaf(th, fh - fl, fl) : fl, v);
+    }
+    K[k] = v * inv_w;
+  }
+  float A[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    A[k] = dst.f[(uint32_t)k * dN + d];
+    dst.f[(uint32_t)k * dN + d] = 0.0f;
+  }
+  float ub[3] = {dst.u[d], dst.u[dN + d], dst.u[2 * dN + d]};
+  dst.u[d] = dst.u[dN + d] = dst.u[2 * dN + d] = 0.0f;
+  const float cb = dst.c[d];
+  dst.c[d] = 0.0f;
+  raw_moments(K);
+  const float drho = K[kap(0, 0, 0)];
+  const float inv = 1.0f / (1.0f + drho);
+  const float ux = K[kap(1, 0, 0)] * inv, uy = K[kap(0, 1, 0)] * inv, uz = K[kap(0, 0, 1)] * inv;
+  shift_axis<1>(K, ux);
+  shift_axis<3>(K, uy);
+  shift_axis<9>(K, uz);
+  Keep kf;
+  kf.nu = a.khat;
+  kf.g[0] = kf.g[1] = kf.g[2] = kf.g[3] = 1.0f;
+  float kbar[4] = {0.f, 0.f, 0.f, 0.f};
+  collide_vjp(K, A, drho, ux, uy, uz, inv, kf, ub, kbar);   // A = adjoint of the interpolant
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float wc = w[c] * inv_w;
+    if (wc == 0.0f) continue;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+      const uint32_t i = (uint32_t)k * sN + sc[c];
+      if (th < 1.0f) atomicAdd(lo.f + i, (1.0f - th) * wc * A[k]);
+      if (th > 0.0f) atomicAdd(hi.f + i, th * wc * A[k]);
+    }
+    if (th < 1.0f) atomicAdd(lo.c + sc[c], (1.0f - th) * wc * cb);
+    if (th > 0.0f) atomicAdd(hi.c + sc[c], th * wc * cb);
+  }
+}
+
+// Before the transpose of an aligned sub-step (out = al0 f(t_n) + al1 in + al2 step(in), the
+// stored velocity recomputed from out): the velocity adjoint is turned into population
+// adjoints, the al0 and al1 shares go to the t_n level and to the input level node by node,
+// and the al2 share is left in the output level for the step's own transpose (whose stored
+// velocity was not kept).  Obstacle, inflow and ghost nodes are not aligned and are skipped.
+__global__ void k_align_vjp_pre(BlockView v, AdjLevel out, AdjLevel L, AdjLevel in, float al0,
+                                float al1, float al2) {
+  const uint32_t N = (uint32_t)v.N;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+    if (v.flags[idx] & (F_SOLID | F_INFLOW | F_GHOST)) continue;
+    const float* D = static_cast<const float*>(v.d_out);
+    float s = 0.f, j[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+      const float val = D[(uint32_t)k * N + idx];
+      s += val;
+      j[0] += cxk(k) * val;
+      j[1] += cyk(k) * val;
+      j[2] += czk(k) * val;
+    }
+    const float ia = 1.0f / (1.0f + s);
+    const float u[3] = {j[0] * ia, j[1] * ia, j[2] * ia};
+    const float ub[3] = {out.u[idx], out.u[N + idx], out.u[2 * N + idx]};
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+      const float lp = out.f[(uint32_t)k * N + idx] +
+                       ia * (ub[0] * (cxk(k) - u[0]) + ub[1] * (cyk(k) - u[1]) + ub[2] * (czk(k) - u[2]));
+      L.f[(uint32_t)k * N + idx] += al0 * lp;
+      in.f[(uint32_t)k * N + idx] += al1 * lp;
+      out.f[(uint32_t)k * N + idx] = al2 * lp;
+    }
+    out.u[idx] = out.u[N + idx] = out.u[2 * N + idx] = 0.0f;
+    const float cb = out.c[idx];
+    L.c[idx] += al0 * cb;
+    in.c[idx] += al1 * cb;
+    out.c[idx] = al2 * cb;
+  }
+}
+
+// Clears the adjoint of the nodes a collide-stream step wrote (all but the ghost nodes).
+__global__ void k_zero_stepped(AdjLevel out, const uint8_t* __restrict__ flags, uint32_t N) {
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+    if (flags[idx] & F_GHOST) continue;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) out.f[(uint32_t)k * N + idx] = 0.0f;
+    out.u[idx] = out.u[N + idx] = out.u[2 * N + idx] = 0.0f;
+    out.c[idx] = 0.0f;
+  }
+}
+
 // The inflow velocity of a node is its stored velocity, carried unchanged from step to step
 // and set with u_0, so the gradient with respect to it is dL/du_0 at inflow nodes.
 __global__ void k_inflow_grad(const float* __restrict__ du0, const uint8_t* __restrict__ flags,
@@ -405,6 +580,13 @@ struct TapeState {
   float* ups[2] = {nullptr, nullptr};
   float* gam[2] = {nullptr, nullptr};
   float* mu = nullptr;
+  // continuous-scale domains (several blocks)
+  bool multi = false;
+  std::vector<std::vector<Level>> mck;        // [checkpoint][block]: state at the step start
+  std::vector<std::vector<Level>> snap;       // [step of the segment][block]
+  std::vector<std::vector<Level>> scr;        // [block][level]: replay levels (+ a spare)
+  std::vector<std::vector<AdjLevel>> lamb;    // [block][level]: adjoints of the replay levels
+  std::vector<float*> grad;                   // [block]: dL/du_0 of the block
 };
 
 }  // namespace lbm
@@ -429,6 +611,16 @@ void release_tape(lbm_domain* dom) {
     dom->dev_free(t->gam[i]);
   }
   dom->dev_free(t->mu);
+  for (auto& v : t->mck) for (Level& L : v) free_level(dom, L);
+  for (auto& v : t->snap) for (Level& L : v) free_level(dom, L);
+  for (auto& v : t->scr) for (Level& L : v) free_level(dom, L);
+  for (auto& v : t->lamb)
+    for (AdjLevel& A : v) {
+      dom->dev_free(A.f);
+      dom->dev_free(A.u);
+      dom->dev_free(A.c);
+    }
+  for (float* g : t->grad) dom->dev_free(g);
   delete t;
   dom->tape = nullptr;
 }
@@ -451,12 +643,36 @@ static BlockView view_of(lbm_domain* dom, const Level& from, const Level& to) {
   return v;
 }
 
+static cudaError_t copy_level(const Level& D, const Level& S, size_t N, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(D.f, S.f, N * 27 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D.u, S.u, N * 3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D.c, S.c, N * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
 // Records a checkpoint of the current state every `every` steps since the last init.
 lbm_status tape_before_step(lbm_domain* dom) {
   TapeState* t = dom->tape;
   if (!t) return LBM_OK;
   if (dom->steps % t->every != 0) return LBM_OK;
   const size_t i = (size_t)(dom->steps / t->every);
+  if (t->multi) {    // every block's state at the step start
+    while (t->mck.size() <= i) {
+      std::vector<Level> v(dom->blocks.size());
+      for (size_t b = 0; b < v.size(); ++b)
+        if (!alloc_level(dom, dom->blocks[b].N, v[b])) {
+          for (Level& L : v) free_level(dom, L);
+          return dom->fail(LBM_ERR_OOM, "checkpoint allocation failed");
+        }
+      t->mck.push_back(v);
+    }
+    for (size_t b = 0; b < dom->blocks.size(); ++b) {
+      const Block& B = dom->blocks[b];
+      const cudaError_t e = copy_level(t->mck[i][b], B.lv[B.cur], B.N, dom->stream);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "checkpoint copy");
+    }
+    return LBM_OK;
+  }
   Block& B = dom->blocks[0];
   while (t->ckpt.size() <= i) {
     Level L;
@@ -476,7 +692,8 @@ lbm_status tape_before_step(lbm_domain* dom) {
 }
 
 static lbm_status adjoint_supported(lbm_domain* dom) {
-  if (dom->blocks.size() != 1) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint covers single-block domains");
+  for (const Block& B : dom->blocks)
+    if (B.far) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint does not cover far-field blocks");
   if (dom->desc.storage != LBM_FP32) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP32 storage");
   if (dom->desc.grad_mode != LBM_GRAD_LAGGED)
     return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint covers the lagged-gradient relaxation");
@@ -498,8 +715,289 @@ extern "C" lbm_status lbm_set_tape(lbm_domain* dom, int32_t every) {
   if (st != LBM_OK) return st;
   dom->tape = new TapeState();
   dom->tape->every = every;
+  dom->tape->multi = dom->blocks.size() > 1;
   dom->invalidate_graphs();
   return LBM_OK;
+}
+
+// One operation of the Algorithm 1 schedule of a continuous-scale domain, on replay levels
+// numbered from a canonical start (every block's state at t_n in level 0).
+struct MsOp {
+  int kind = 0;                       // 0 collide-stream, 1 aligned collide-stream, 2 mapping
+  int b = 0, in = 0, out = 0, al = 0; // block and levels of a (aligned) collide-stream
+  float al0 = 0.f, al1 = 0.f, al2 = 0.f;
+  const MapTable* t = nullptr;        // mapping: table, source block / levels, destination
+  int src = 0, lo = 0, hi = 0, dst = 0, dlv = 0;
+  float theta = 0.f;
+  uint8_t skip = 0;
+};
+
+// The operations of one reference step in the order multiscale_step issues them (its forked
+// mappings write nodes disjoint from the concurrent collide-stream, so this sequential order
+// computes the same values); `cur` receives every block's level at the end of the step.
+static std::vector<MsOp> ms_ops(const lbm_domain* dom, std::vector<int>& cur) {
+  const int nb = (int)dom->blocks.size();
+  cur.assign(nb, 0);
+  std::vector<int> saved(nb, 0);
+  std::vector<MsOp> ops;
+  MsOp s0;
+  s0.kind = 0; s0.b = 0; s0.in = 0; s0.out = 1;
+  ops.push_back(s0);
+  cur[0] = 1;
+  for (int b = 1; b < nb; ++b) {
+    const Block& B = dom->blocks[b];
+    const int P = B.prior.src, L = 0, A = 1, Bv = 2;
+    const bool exact = B.integer_ratio && std::fabs(B.substeps * B.h - 1.0) < 1e-9;
+    auto prior = [&](float theta, int dlv) {
+      MsOp m;
+      m.kind = 2; m.t = &B.prior; m.src = P; m.lo = saved[P]; m.hi = cur[P]; m.theta = theta;
+      m.dst = b; m.dlv = dlv; m.skip = F_SOLID;
+      return m;
+    };
+    ops.push_back(prior(0.0f, L));
+    int c = L;
+    for (int j = 1; j <= B.substeps; ++j) {
+      const int out = (j == 1) ? A : (c == A ? Bv : A);
+      ops.push_back(prior(j < B.substeps ? (float)(j * B.h) : 1.0f, out));
+      MsOp s;
+      s.b = b; s.in = c; s.out = out;
+      if (j == B.substeps && !exact) {
+        const double t1 = (B.substeps - 1) * B.h, t2 = B.substeps * B.h, T = 1.0;
+        s.kind = 1; s.al = L;
+        s.al0 = (float)((T - t1) * (T - t2) / ((0.0 - t1) * (0.0 - t2)));
+        s.al1 = (float)((T - 0.0) * (T - t2) / ((t1 - 0.0) * (t1 - t2)));
+        s.al2 = (float)((T - 0.0) * (T - t1) / ((t2 - 0.0) * (t2 - t1)));
+      }
+      ops.push_back(s);
+      c = out;
+    }
+    cur[b] = c;
+    for (const MapTable& t : B.post) {
+      MsOp m;
+      m.kind = 2; m.t = &t; m.src = b; m.lo = m.hi = cur[b]; m.theta = 0.0f;
+      m.dst = t.dst; m.dlv = cur[t.dst]; m.skip = F_SOLID | F_GHOST;
+      ops.push_back(m);
+    }
+  }
+  return ops;
+}
+
+static BlockView ms_view(lbm_domain* dom, TapeState* t, int b, int from, int to) {
+  BlockView v = dom->view(b, 0, 0);   // geometry, flags, rates, error word
+  const Level& F = t->scr[b][from];
+  const Level& T = t->scr[b][to];
+  v.d_in = F.f; v.u_in = F.u; v.c_in = F.c;
+  v.d_out = T.f; v.u_out = T.u; v.c_out = T.c;
+  return v;
+}
+
+static MapArgs ms_map_args(lbm_domain* dom, TapeState* t, const MsOp& o) {
+  const Block& S = dom->blocks[o.src];
+  const Block& D = dom->blocks[o.dst];
+  MapArgs a{};
+  a.table = o.t->d;
+  a.n = o.t->n;
+  a.f_lo = t->scr[o.src][o.lo].f;
+  a.f_hi = t->scr[o.src][o.hi].f;
+  a.c_lo = t->scr[o.src][o.lo].c;
+  a.c_hi = t->scr[o.src][o.hi].c;
+  a.theta = o.theta;
+  a.src_flags = S.flags;
+  a.snx = S.nx; a.sny = S.ny; a.snz = S.nz; a.sN = S.N;
+  a.f_dst = t->scr[o.dst][o.dlv].f;
+  a.u_dst = t->scr[o.dst][o.dlv].u;
+  a.c_dst = t->scr[o.dst][o.dlv].c;
+  a.dst_flags = D.flags;
+  a.skip_mask = o.skip;
+  a.dN = D.N;
+  a.khat = o.t->khat;
+  a.rest_if_empty = (o.skip & F_GHOST) ? 0 : 1;   // prior maps write scale boundaries
+  return a;
+}
+
+static cudaError_t ms_forward_op(lbm_domain* dom, TapeState* t, const MsOp& o, cudaStream_t s) {
+  if (o.kind == 2) return launch_map(ms_map_args(dom, t, o), ST_FP32, s);
+  const Block& B = dom->blocks[o.b];
+  BlockView v = ms_view(dom, t, o.b, o.in, o.out);
+  if (o.kind == 1) {
+    v.f_al0 = t->scr[o.b][o.al].f;
+    v.c_al0 = t->scr[o.b][o.al].c;
+    v.al0 = o.al0; v.al1 = o.al1; v.al2 = o.al2;
+    return launch_step_align(v, B.bx, B.by, s, B.minb);
+  }
+  return launch_step(v, ST_FP32, B.bx, B.by, s, B.minb);
+}
+
+// Transpose of one operation, with its forward inputs present in the replay levels.
+static cudaError_t ms_reverse_op(lbm_domain* dom, TapeState* t, const MsOp& o, cudaStream_t s) {
+  if (o.kind == 2) {
+    const MapArgs a = ms_map_args(dom, t, o);
+    if (a.n > 0)
+      k_map_vjp<<<(a.n + 127) / 128, 128, 0, s>>>(a, t->lamb[o.dst][o.dlv], t->lamb[o.src][o.lo],
+                                                    t->lamb[o.src][o.hi]);
+    return cudaGetLastError();
+  }
+  const Block& B = dom->blocks[o.b];
+  const uint32_t N = (uint32_t)B.N;
+  const int g = (int)std::min<size_t>((B.N + 255) / 256, 16384);
+  AdjLevel lin = t->lamb[o.b][o.in], lout = t->lamb[o.b][o.out];
+  const float* u_next = t->scr[o.b][o.out].u;
+  if (o.kind == 1) {
+    // the sub-step's own velocity (the scalar's departure velocity) is not stored by an
+    // aligned step: recompute the plain step into the spare level
+    const int spare = (int)t->scr[o.b].size() - 1;
+    cudaError_t e = launch_step(ms_view(dom, t, o.b, o.in, spare), ST_FP32, B.bx, B.by, s, B.minb);
+    if (e != cudaSuccess) return e;
+    u_next = t->scr[o.b][spare].u;
+    k_align_vjp_pre<<<g, 256, 0, s>>>(ms_view(dom, t, o.b, o.out, o.out), lout,
+                                      t->lamb[o.b][o.al], lin, o.al0, o.al1, o.al2);
+  }
+  AdjArgs a;
+  a.fwd = ms_view(dom, t, o.b, o.in, o.in);
+  a.lam_in = lout.f; a.ups_in = lout.u; a.gam_in = lout.c;
+  a.u_next = u_next;
+  a.lam_out = lin.f; a.ups_out = lin.u; a.gam_out = lin.c;
+  a.mu = t->mu;
+  const bool open = o.b != 0 || !dom->desc.periodic[0] || !dom->desc.periodic[1] || !dom->desc.periodic[2];
+  const dim3 blk(128, 1, 1), grd((B.nx + 127) / 128, B.ny, B.nz);
+  launch_pass_a(a, 3, open, grd, blk, s, true);
+  k_adj_b<true><<<grd, blk, 0, s>>>(a);
+  k_zero_stepped<<<g, 256, 0, s>>>(lout, B.flags, N);
+  return cudaGetLastError();
+}
+
+static bool alloc_adj(lbm_domain* dom, size_t N, AdjLevel& A) {
+  A.f = static_cast<float*>(dom->dev_alloc(N * 27 * sizeof(float)));
+  A.u = static_cast<float*>(dom->dev_alloc(N * 3 * sizeof(float)));
+  A.c = static_cast<float*>(dom->dev_alloc(N * sizeof(float)));
+  return A.f && A.u && A.c;
+}
+
+static cudaError_t zero_adj(const AdjLevel& A, size_t N, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(A.f, 0, N * 27 * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.u, 0, N * 3 * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A.c, 0, N * sizeof(float), s);
+  return e;
+}
+
+// Reverse sweep of a continuous-scale domain: the recorded reference steps are reversed last
+// to first; each segment between checkpoints is replayed once to record every step's start
+// state, and each operation of a step is reversed after a replay of the operations before it
+// from that start state (the level buffers of refined blocks rotate, so an operation's
+// inputs may have been overwritten later in the step).
+static lbm_status adjoint_multiblock(lbm_domain* dom, int n_steps, const float* dL_dc,
+                                     const float* dL_du, float* dL_du0, float* dL_dinflow) {
+  TapeState* t = dom->tape;
+  cudaStream_t s = dom->stream;
+  const int nb = (int)dom->blocks.size();
+  size_t nmax = 0;
+  for (const Block& B : dom->blocks) nmax = std::max(nmax, B.N);
+  // buffers
+  if (t->scr.empty()) {
+    t->scr.resize(nb);
+    t->lamb.resize(nb);
+    t->grad.assign(nb, nullptr);
+    for (int b = 0; b < nb; ++b) {
+      const size_t N = dom->blocks[b].N;
+      const int levels = b == 0 ? 2 : 3;
+      t->scr[b].resize(b == 0 ? 2 : 4);
+      for (Level& L : t->scr[b])
+        if (!alloc_level(dom, N, L)) return dom->fail(LBM_ERR_OOM, "adjoint replay levels");
+      t->lamb[b].resize(levels);
+      for (AdjLevel& A : t->lamb[b])
+        if (!alloc_adj(dom, N, A)) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+      t->grad[b] = static_cast<float*>(dom->dev_alloc(N * 3 * sizeof(float)));
+      if (!t->grad[b]) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+    }
+    t->mu = static_cast<float*>(dom->dev_alloc(nmax * 9 * sizeof(float)));
+    if (!t->mu) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+  }
+  const int seg_len = std::min(t->every, std::max(1, n_steps));
+  while ((int)t->snap.size() < seg_len) {
+    std::vector<Level> v(nb);
+    for (int b = 0; b < nb; ++b)
+      if (!alloc_level(dom, dom->blocks[b].N, v[b])) {
+        for (Level& L : v) free_level(dom, L);
+        return dom->fail(LBM_ERR_OOM, "adjoint step snapshots");
+      }
+    t->snap.push_back(v);
+  }
+  if (t->mck.empty()) {
+    lbm_status st = tape_before_step(dom);
+    if (st != LBM_OK) return st;
+  }
+  std::vector<int> cur_end;
+  const std::vector<MsOp> ops = ms_ops(dom, cur_end);
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < nb && e == cudaSuccess; ++b)
+    for (const AdjLevel& A : t->lamb[b])
+      if (e == cudaSuccess) e = zero_adj(A, dom->blocks[b].N, s);
+  // the loss depends on the reference block's final scalar (and velocity)
+  const size_t N0 = dom->blocks[0].N;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(t->lamb[0][cur_end[0]].c, dL_dc, N0 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && dL_du)
+    e = cudaMemcpyAsync(t->lamb[0][cur_end[0]].u, dL_du, N0 * 3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint initialisation");
+
+  const int n_seg = (n_steps + t->every - 1) / t->every;
+  for (int sg = n_seg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+    const int len = std::min(t->every, n_steps - sg * t->every);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b)
+      e = copy_level(t->scr[b][0], t->mck[sg][b], dom->blocks[b].N, s);
+    for (int i = 0; i < len && e == cudaSuccess; ++i) {
+      for (int b = 0; b < nb && e == cudaSuccess; ++b)
+        e = copy_level(t->snap[i][b], t->scr[b][0], dom->blocks[b].N, s);
+      if (i == len - 1) break;
+      for (const MsOp& o : ops)
+        if (e == cudaSuccess) e = ms_forward_op(dom, t, o, s);
+      for (int b = 0; b < nb; ++b) std::swap(t->scr[b][0], t->scr[b][cur_end[b]]);
+    }
+    for (int i = len - 1; i >= 0 && e == cudaSuccess; --i) {
+      for (int k = (int)ops.size() - 1; k >= 0 && e == cudaSuccess; --k) {
+        for (int b = 0; b < nb && e == cudaSuccess; ++b)
+          e = copy_level(t->scr[b][0], t->snap[i][b], dom->blocks[b].N, s);
+        for (int j = 0; j < k && e == cudaSuccess; ++j) e = ms_forward_op(dom, t, ops[j], s);
+        if (e == cudaSuccess) e = ms_reverse_op(dom, t, ops[k], s);
+      }
+      // the adjoint of this step's start state is in level 0: it is the adjoint of the end
+      // state of the step before, whose replay ends in the levels cur_end
+      if (!(sg == 0 && i == 0))
+        for (int b = 0; b < nb; ++b) std::swap(t->lamb[b][0], t->lamb[b][cur_end[b]]);
+    }
+  }
+  if (e != cudaSuccess) return dom->cuda_fail(e, "multi-block adjoint");
+  for (int b = 0; b < nb; ++b) {
+    const Block& B = dom->blocks[b];
+    const int g = (int)std::min<size_t>((B.N + 255) / 256, 16384);
+    k_adj_init<<<g, 256, 0, s>>>(static_cast<const float*>(t->mck[0][b].f), t->mck[0][b].u, B.flags,
+                                 t->lamb[b][0].f, t->lamb[b][0].u, t->grad[b], (uint32_t)B.N);
+  }
+  e = cudaMemcpyAsync(dL_du0, t->grad[0], N0 * 3 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && dL_dinflow) {
+    const int g = (int)std::min<size_t>((N0 + 255) / 256, 16384);
+    k_inflow_grad<<<g, 256, 0, s>>>(dL_du0, dom->blocks[0].flags, dL_dinflow, (uint32_t)N0);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return dom->cuda_fail(e, "initial-state adjoint");
+  dom->post_error_probe();
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_adjoint_block_grad(lbm_domain* dom, int32_t block_id, float* dL_du0) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  lbm_status st = dom->check_block(block_id);
+  if (st != LBM_OK) return st;
+  if (!dL_du0) return dom->fail(LBM_ERR_INVALID_ARG, "null output");
+  TapeState* t = dom->tape;
+  if (!t || (int)t->grad.size() <= block_id || !t->grad[block_id])
+    return dom->fail(LBM_ERR_STATE, "no multi-block reverse sweep has run");
+  const size_t N = dom->blocks[block_id].N;
+  const cudaError_t e = cudaMemcpyAsync(dL_du0, t->grad[block_id], N * 3 * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "gradient copy");
+  return dom->sync_and_check();
 }
 
 extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dc,
@@ -511,6 +1009,7 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
   if (n_steps < 0 || n_steps != dom->steps)
     return dom->fail(LBM_ERR_INVALID_ARG, "n_steps must equal the steps recorded since lbm_init_macro");
   if (!dL_dc || !dL_du0) return dom->fail(LBM_ERR_INVALID_ARG, "dL_dscalar_final and dL_du0 are required");
+  if (t->multi) return adjoint_multiblock(dom, n_steps, dL_dc, dL_du, dL_du0, dL_dinflow);
   Block& B = dom->blocks[0];
   const size_t N = B.N;
   cudaStream_t s = dom->stream;
@@ -597,7 +1096,7 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
         k_zero_face_slots<<<zgrid, 256, 0, s>>>(a.lam_out, B.nx, B.ny, B.nz, dom->desc.periodic[0],
                                                 dom->desc.periodic[1], dom->desc.periodic[2]);
       launch_pass_a(a, t->pass_a_minb, open_faces, grd, blk, s);
-      k_adj_b<<<grd, blk, 0, s>>>(a);
+      k_adj_b<false><<<grd, blk, 0, s>>>(a);
       e = cudaGetLastError();
       if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint step");
       c ^= 1;

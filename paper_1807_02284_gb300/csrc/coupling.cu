@@ -91,10 +91,12 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
           w[c] = (__ldg(a.src_flags + sc[c]) & F_SOLID) ? 0.0f : wc;  // obstacle corners dropped
           wsum += w[c];
         }
-        if (wsum > 0.0f) inv = 1.0f / wsum;   // every corner an obstacle: node left unchanged
+        if (wsum > 0.0f) inv = 1.0f / wsum;
+        else if (a.rest_if_empty) inv = -1.0f; // every corner an obstacle: rest state
+        // (otherwise the node is left unchanged)
       }
     }
-    if (inv == 0.0f) {
+    if (!(inv > 0.0f)) {
 #pragma unroll
       for (int c = 0; c < 8; ++c) { sc[c] = 0; w[c] = 0.0f; }
     }
@@ -144,11 +146,14 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
     }
     vals[i] = v;
   }
-  const float inv_d = sinv[d];
+  const float inv_d = sinv[d] > 0.0f ? sinv[d] : 0.0f;     // rest state: all zero
 #pragma unroll
   for (int i = 0; i < PAIRS; ++i) sv[d * MAP_LD + (t >> 5) + i * (MAP_THREADS / 32)] = vals[i] * inv_d;
   __syncthreads();
-  if (t < MAP_D && sinv[t] != 0.0f) {
+  if (t < MAP_D && sinv[t] < 0.0f) {   // rest state: shifted populations, u and scalar 0
+    su[0][t] = su[1][t] = su[2][t] = 0.0f;
+  }
+  if (t < MAP_D && sinv[t] > 0.0f) {
     float acc[27];
 #pragma unroll
     for (int k = 0; k < 27; ++k) acc[k] = sv[t * MAP_LD + k];
@@ -578,7 +583,8 @@ static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& sav
                              int dst_level, cudaStream_t stream) {
   Block& B = dom->blocks[b];
   const Block& P = dom->blocks[B.prior.src];
-  MapArgs a;
+  MapArgs a{};
+  a.rest_if_empty = 1;           // scale boundary
   a.table = B.prior.d;
   a.n = B.prior.n;
   a.f_lo = P.lv[saved[B.prior.src]].f;
@@ -601,7 +607,8 @@ static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& sav
 static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t, cudaStream_t stream) {
   const Block& B = dom->blocks[b];
   Block& T = dom->blocks[t.dst];
-  MapArgs a;
+  MapArgs a{};
+  a.rest_if_empty = 0;           // post-mapped nodes keep their own update
   a.table = t.d;
   a.n = t.n;
   a.f_lo = a.f_hi = B.lv[B.cur].f;
@@ -621,10 +628,12 @@ static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t, cudaStrea
 
 // Mapping between the current states of two blocks along a far-field table (the destination
 // nodes carrying any of `skip` are left alone).
-static cudaError_t far_map(lbm_domain* dom, const MapTable& t, uint8_t skip, cudaStream_t stream) {
+static cudaError_t far_map(lbm_domain* dom, const MapTable& t, uint8_t skip, int rest,
+                           cudaStream_t stream) {
   const Block& S = dom->blocks[t.src];
   Block& T = dom->blocks[t.dst];
   MapArgs a{};
+  a.rest_if_empty = rest;
   a.table = t.d;
   a.n = t.n;
   a.f_lo = a.f_hi = S.lv[S.cur].f;
@@ -685,12 +694,12 @@ lbm_status multiscale_step(lbm_domain* dom) {
   }
   for (int f : far) {
     const Block& F = dom->blocks[f];
-    e = far_map(dom, F.far_in, F_SOLID | F_GHOST, s);
+    e = far_map(dom, F.far_in, F_SOLID | F_GHOST, 0, s);
     if (e != cudaSuccess) return dom->cuda_fail(e, "far-field overlap mapping");
   }
   for (size_t k = far.size(); k-- > 0;) {
     const Block& F = dom->blocks[far[k]];
-    e = far_map(dom, F.far_out, F_SOLID | F_INFLOW, s);
+    e = far_map(dom, F.far_out, F_SOLID | F_INFLOW, 1, s);
     if (e != cudaSuccess) return dom->cuda_fail(e, "far-field boundary mapping");
   }
   for (size_t bi = 1; bi < dom->blocks.size(); ++bi) {

@@ -62,6 +62,9 @@ struct MapArgs {
   uint8_t skip_mask;   // destination nodes with any of these flags are left alone
   size_t dN;
   float khat;          // K_hat factor of moments 4..8 (1 for all others)
+  // a destination whose 8 source corners are all obstacle voxels: rest state (scale
+  // boundaries, which have no update of their own) or left unchanged (post-mapped nodes)
+  int rest_if_empty;
   // table == nullptr: entry e is destination node e of a whole block, its source cell
   // computed from the two blocks' geometry (reference units) instead of read from a table
   double o_dst[3], h_dst;

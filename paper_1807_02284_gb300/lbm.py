@@ -85,6 +85,7 @@ _SIGNATURES = {
     "lbm_reduce_batch": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
     "lbm_set_tape": (_I, [_P, _I]),
     "lbm_adjoint_step": (_I, [_P, _I, _P, _P, _P, _P]),
+    "lbm_adjoint_block_grad": (_I, [_P, _I, _P]),
     "lbm_reduce_noalloc": (_I, [_P, _I, _P, C.c_int64, _P, _P]),
     "lbm_barrier_selftest": (_I, [_I, C.c_double, _P]),
     "lbm_last_error": (C.c_char_p, [_P]),
@@ -316,6 +317,10 @@ class Domain:
         p0, _ = _ptr(dL_du0)
         pi, _ = _ptr(dL_dinflow)
         self.check(self.lib.lbm_adjoint_step(self.handle, int(n_steps), pc, pu, p0, pi))
+
+    def adjoint_block_grad(self, block, out):
+        p, _ = _ptr(out)
+        self.check(self.lib.lbm_adjoint_block_grad(self.handle, int(block), p))
 
 
 def step_batch(domains: Sequence[Domain], steps: int):

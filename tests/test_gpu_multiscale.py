@@ -182,9 +182,9 @@ def test_full_size_reference_block_far_field_sampled(lib):
 def test_scale_block_argument_checks(lib):
     from paper_1807_02284_gb300 import lbm
     dom = lbm.Domain((16, 16, 16), 1e-3)
-    with pytest.raises(lbm.LBMError) as ei:
+    with pytest.raises(lbm.LBMError) as ei:               # far field not around s0
         dom.add_scale_block((2, 2, 2), 1.5, (8, 8, 8))
-    assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
+    assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
     with pytest.raises(lbm.LBMError) as ei:
         dom.add_scale_block((10, 10, 10), 0.5, (20, 8, 8))          # sticks out of s0
     assert ei.value.status == lbm.LBM_ERR_INVALID_ARG

@@ -192,3 +192,28 @@ def test_integer_ratio_block_tracks_the_coarse_flow():
     # the trilinear interpolation of the coarse field alone differs by ~2e-3 at 16 nodes
     # per wavelength; two coupled steps must stay within twice that
     assert diff < 0.1 * 0.05
+
+
+def test_scale_boundary_node_inside_a_coarse_obstacle_takes_the_rest_state():
+    """A ghost node whose 8 source corners are all obstacle voxels cannot be interpolated;
+    it holds the rest state (rho = 1, u = 0, scalar 0) after every mapping."""
+    sc = synth.random_scene(dims=(12, 12, 12), seed=5, periodic=(False, False, False), nu=0.01)
+    b0 = sc.blocks[0]
+    b0.flags[:] = 0
+    b0.flags[2:8, 2:8, 2:8] = synth.SOLID            # coarse obstacle cube, nodes 2..7
+    fine = synth._empty_block((10, 10, 10), origin=(3.0, 3.0, 3.0), h=0.5)
+    fine.u0[0] = 0.02
+    fine.c0[:] = 0.7
+    sc.blocks.append(fine)
+    ms = coupling.MultiScale.build(sc)
+    ms.step()
+    b = ms.blocks[1]
+    ghost = (b.state.flags & coupling.GHOST) != 0
+    pos = [3.0 + 0.5 * np.arange(10)] * 3
+    z, y, x = np.meshgrid(*reversed(pos), indexing="ij")
+    inside = (x >= 2) & (x + 1 <= 7) & (y >= 2) & (y + 1 <= 7) & (z >= 2) & (z + 1 <= 7)
+    sel = torch.as_tensor(inside) & ghost
+    assert int(sel.sum()) > 0
+    feq = cmr.equilibrium(torch.ones(1, dtype=torch.float64), torch.zeros(1, 3, dtype=torch.float64))[0]
+    assert torch.allclose(b.state.f[:, sel], feq[:, None].expand(27, int(sel.sum())), atol=1e-15)
+    assert (b.state.u[:, sel] == 0).all() and (b.state.c[sel] == 0).all()
