@@ -54,6 +54,7 @@ class Params:
     body_force: Optional[Sequence[float]] = None
     grad_mode: str = "lagged"    # "lagged" central differences of the stored velocity, or
                                  # "local" strain rate from the node's non-equilibrium moments
+    walls: Sequence[bool] = (False,) * 6   # no-slip wall faces x-, x+, y-, y+, z-, z+
 
 
 @dataclasses.dataclass
@@ -119,6 +120,44 @@ def sample_trilinear(c: torch.Tensor, px, py, pz, periodic) -> torch.Tensor:
     return out
 
 
+def regularized_wall(f_in: torch.Tensor, walls, dims, x, y, z) -> torch.Tensor:
+    """Second-order no-slip wall on flat faces of the block (Sec. 6.1, read as the
+    regularized on-node wall of the cited method), applied to the pulled populations f_in
+    (K, 27) of the listed nodes.  At a node on a wall face, a population whose pull source
+    lies beyond the wall is unknown: it is completed by bounce-back from its opposite (the
+    wall is at rest); where the opposite is unknown too (edges, corners) both take the rest
+    equilibrium w_i rho.  rho is the mass of the completed set (for one wall:
+    sum_{c.n = 0} f + 2 sum_{c.n < 0} f).  All 27 populations are then rebuilt from the
+    equilibrium at (rho, u = 0) and the non-equilibrium stress Pi of the completed set,
+    f_i = w_i rho + w_i / (2 c_s^4) Q_i : Pi with Q_i = c_i c_i - c_s^2 I."""
+    n = dims
+    coord = (x, y, z)
+    unk = torch.zeros(f_in.shape, dtype=torch.bool)
+    for q in range(27):
+        col = torch.zeros(x.shape, dtype=torch.bool)
+        for a in range(3):
+            ca = int(C[q, a])
+            if walls[2 * a] and ca == 1:
+                col |= coord[a] == 0
+            if walls[2 * a + 1] and ca == -1:
+                col |= coord[a] == n[a] - 1
+        unk[:, q] = col
+    node = unk.any(dim=1)
+    if not bool(node.any()):
+        return f_in
+    W = cmr.equilibrium(torch.ones(1, dtype=DT), torch.zeros(1, 3, dtype=DT))[0]   # weights
+    unk_opp = unk[:, OPP]
+    both = unk & unk_opp
+    f_c = torch.where(unk & ~unk_opp, f_in[:, OPP], f_in)
+    rho = torch.where(both, torch.zeros_like(f_c), f_c).sum(1) / (1.0 - (W * both).sum(1))
+    feq = W[None, :] * rho[:, None]
+    f_c = torch.where(both, feq, f_c)
+    pi = torch.einsum("kq,qa,qb->kab", f_c - feq, C, C)
+    Q = C[:, :, None] * C[:, None, :] - torch.eye(3, dtype=DT)[None] / 3.0
+    f_reg = feq + 4.5 * W[None, :] * torch.einsum("qab,kab->kq", Q, pi)
+    return torch.where(node[:, None], f_reg, f_in)
+
+
 def lagged_gradient_norm(u: torch.Tensor, periodic, z, y, x) -> torch.Tensor:
     """|grad u| at the listed nodes: Frobenius norm of the central-difference Jacobian
     d u_a / d x_b ~ (u_a(x + e_b) - u_a(x - e_b)) / 2 of a stored velocity field, with
@@ -180,6 +219,8 @@ def step_cells(st: State, p: Params, z: torch.Tensor, y: torch.Tensor, x: torch.
         from_wall = solid[sz, sy, sx]
         cols.append(torch.where(from_wall, st.f[OPP[q], z, y, x], st.f[q, sz, sy, sx]))
     f_in = torch.stack(cols, dim=-1)
+    if any(p.walls):
+        f_in = regularized_wall(f_in, p.walls, (X, Y, Z), x, y, z)
 
     # 3. adaptive factor from the lagged velocity field
     if p.adaptive and p.grad_mode == "local":

@@ -1,0 +1,81 @@
+"""Pins of the second-order no-slip wall on flat block faces (Sec. 6.1; read as the
+regularized on-node wall of the cited method): second-order convergence of the decay of a
+shear mode between two walls to the Navier-Stokes rate, the exact parabolic curvature of a
+body-forced channel, and the wall-node invariants (mass from the known populations, zero
+momentum, the non-equilibrium stress of the completed set kept)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import cmr, grid
+
+WALLS_Z = (False,) * 4 + (True, True)
+
+
+def _shear_decay_rate_error(H, nu=0.05, U=1e-3):
+    Z = H + 1
+    z = np.arange(Z)
+    u0 = np.zeros((3, Z, 1, 1))
+    u0[0, :, 0, 0] = U * np.sin(math.pi * z / H)      # zero on the wall nodes z = 0, H
+    st = grid.init_state(np.ones((Z, 1, 1)), u0, np.zeros((Z, 1, 1)), np.zeros((Z, 1, 1), np.uint8))
+    p = grid.Params(nu=nu, periodic=(True, True, False), adaptive=False, walls=WALLS_Z)
+    basis = np.sin(math.pi * z / H)
+    t0, t1 = int(0.2 * H * H / nu), int(0.6 * H * H / nu)
+    amps = {}
+    for t in range(1, t1 + 1):
+        st = grid.step(st, p)
+        if t in (t0, t1):
+            amps[t] = float((st.u[0, :, 0, 0].numpy() * basis).sum() / (basis * basis).sum())
+    rate = -math.log(amps[t1] / amps[t0]) / (t1 - t0)
+    return rate / (nu * math.pi ** 2 / H ** 2) - 1.0
+
+
+def test_shear_mode_decay_converges_at_second_order_to_the_navier_stokes_rate():
+    """u_x = U sin(pi z / H) between on-node walls at z = 0 and z = H decays at
+    nu (pi / H)^2; the error of the lattice rate falls 4x per doubling of H."""
+    e8, e16 = _shear_decay_rate_error(8), _shear_decay_rate_error(16)
+    assert abs(e16) < 5e-3
+    assert 3.6 < e8 / e16 < 4.4, (e8, e16)
+
+
+def test_body_forced_channel_profile_has_the_exact_curvature():
+    """Steady body-forced channel between the walls: away from the wall nodes the profile
+    is a parabola of curvature -g / nu exactly (the forcing shifts it by a constant)."""
+    H, nu, g = 8, 0.2, 1e-5
+    Z = H + 1
+    st = grid.init_state(np.ones((Z, 1, 1)), np.zeros((3, Z, 1, 1)), np.zeros((Z, 1, 1)),
+                         np.zeros((Z, 1, 1), np.uint8))
+    p = grid.Params(nu=nu, periodic=(True, True, False), adaptive=False, body_force=(g, 0.0, 0.0),
+                    walls=WALLS_Z)
+    for _ in range(int(8 * H * H / nu)):
+        st = grid.step(st, p)
+    u = st.u[0, :, 0, 0].numpy()
+    d2 = u[3:-1] - 2 * u[2:-2] + u[1:-3]            # z = 2 .. H-2: neighbours are interior nodes
+    assert np.allclose(d2, -g / nu, rtol=1e-6)
+    assert u[0] == 0.0 and u[-1] == 0.0
+
+
+def test_wall_node_invariants():
+    """Random pulled populations on a node of the z- wall: the rebuilt populations carry
+    rho = sum_{c_z = 0} f + 2 sum_{c_z < 0} f, zero momentum and the non-equilibrium
+    stress of the bounce-back-completed set; on an edge (x- and z- walls) the momentum is
+    still zero."""
+    rng = np.random.default_rng(0)
+    W = cmr.equilibrium(torch.ones(1, dtype=torch.float64), torch.zeros(1, 3, dtype=torch.float64))[0]
+    f_in = W[None, :] * (1.0 + 0.1 * torch.as_tensor(rng.standard_normal((1, 27))))
+    x = torch.tensor([3]); y = torch.tensor([2]); z = torch.tensor([0])
+    out = grid.regularized_wall(f_in, WALLS_Z, (8, 8, 8), x, y, z)
+    cz = cmr.C[:, 2]
+    rho = f_in[0, cz == 0].sum() + 2 * f_in[0, cz < 0].sum()
+    assert torch.isclose(out[0].sum(), rho, rtol=1e-14)
+    assert torch.allclose(out[0] @ cmr.C, torch.zeros(3, dtype=torch.float64), atol=1e-15)
+    completed = torch.where(cz > 0, f_in[0, cmr.OPP], f_in[0])
+    neq = completed - W * rho
+    pi_c = torch.einsum("q,qa,qb->ab", neq, cmr.C, cmr.C)
+    pi_o = torch.einsum("q,qa,qb->ab", out[0] - W * rho, cmr.C, cmr.C)
+    assert torch.allclose(pi_o, pi_c, atol=1e-15)
+    edge = grid.regularized_wall(f_in, (True, False, False, False, True, False), (8, 8, 8),
+                                 torch.tensor([0]), y, z)
+    assert torch.allclose(edge[0] @ cmr.C, torch.zeros(3, dtype=torch.float64), atol=1e-15)
