@@ -149,7 +149,7 @@ def _workload(name):
         sc = synth.plume(256)
         sc.blocks.append(synth.far_block(sc.blocks[0], 2.0, 64.0, seed=9, amp=0.0))
         return sc, "fp32"
-    sc = synth.plume(128 if name.startswith("plume128") else 256)
+    sc = synth.plume(128 if name.startswith("plume128") else 256)   # also plume256_walls
     return sc, storage
 
 
@@ -272,6 +272,8 @@ def run_ours(args):
     dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, storage=storage,
                      adaptive=sc.adaptive, c_src=sc.c_src, stream=stream,
                      grad_mode="local" if args.workload.endswith("_local") else "lagged")
+    if args.workload.endswith("_walls"):     # no-slip floor and lid (the second-order wall)
+        dom.set_walls((False, False, False, False, True, True))
     for blk in sc.blocks[1:]:
         dom.add_scale_block(blk.origin, blk.h, blk.dims)
     for i, blk in enumerate(sc.blocks):
@@ -645,6 +647,7 @@ def _variants(args):
     res = {}
     for name, fn, steps, warm in (("plume256_fp16", run_ours, 100, 10),
                                   ("plume256_local", run_ours, 100, 10),
+                                  ("plume256_walls", run_ours, 100, 10),
                                   ("multiscale3", run_ours, 50, 5),
                                   ("dynamic256", run_dynamic, 200, 10),
                                   ("farfield256", run_ours, 100, 10),
@@ -673,7 +676,7 @@ def main():
     ap.add_argument("--workload", default="plume256",
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
                              "multiscale3", "batch64", "adjoint128", "adjoint64",
-                             "plume256_local", "dynamic256", "farfield256"])
+                             "plume256_local", "dynamic256", "farfield256", "plume256_walls"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

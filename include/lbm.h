@@ -59,10 +59,20 @@ enum {
   LBM_BC_FLAGS = 0,  /* uint8 per node (N bytes): bit0 obstacle voxel (halfway bounce-back),
                         bit1 Dirichlet inflow node, bit2 scalar source node.  Replaces the
                         three bits on every node; other bits are library-owned. */
-  LBM_BC_INFLOW = 1  /* array of lbm_inflow_record: marks the nodes as inflow and sets
+  LBM_BC_INFLOW = 1, /* array of lbm_inflow_record: marks the nodes as inflow and sets
                         their inflow velocity (applied to every time level).  Records outside
                         the block or on obstacle voxels / ghost nodes are skipped and
                         reported as LBM_ERR_DIVERGED by the next synchronising call. */
+  LBM_BC_WALLS = 2   /* block 0 only: 6 uint8 (host), non-zero for a no-slip wall on face
+                        x-, x+, y-, y+, z-, z+ (the paper's second-order wall for the ground
+                        and box walls, Sec. 6.1, read as the regularized on-node wall: the
+                        face nodes are wall nodes at rest; populations pulled through the
+                        wall are completed by bounce-back, both of a pair through walls take
+                        the rest equilibrium, and every population is rebuilt from the
+                        equilibrium at (rho, 0) and the non-equilibrium stress of the
+                        completed set before the collision).  Replaces the previous walls.
+                        INVALID_ARG for a wall on a periodic axis; UNSUPPORTED with
+                        far-field blocks. */
 };
 
 typedef struct {
@@ -259,7 +269,7 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
 /* Advances n independent single-block domains by `steps` reference steps with one
    persistent kernel per step over a joint tile work list, captured in one CUDA graph and
    launched on doms[0]'s stream (tile shape chosen by the library's autotuner on first use).
-   Every domain must be single-block, with the same storage and device.  Results are
+   Every domain must be single-block, without wall faces, with the same storage and device.  Results are
    bit-identical to calling lbm_step on each domain. */
 lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t steps);
 

@@ -694,6 +694,7 @@ lbm_status tape_before_step(lbm_domain* dom) {
 static lbm_status adjoint_supported(lbm_domain* dom) {
   for (const Block& B : dom->blocks)
     if (B.far) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint does not cover far-field blocks");
+  if (dom->walls) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint does not cover no-slip walls");
   if (dom->desc.storage != LBM_FP32) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP32 storage");
   if (dom->desc.grad_mode != LBM_GRAD_LAGGED)
     return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint covers the lagged-gradient relaxation");

@@ -264,6 +264,7 @@ extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t
     if (doms[i]->desc.storage != d0->desc.storage) return d0->fail(LBM_ERR_INVALID_ARG, "mixed storage in batch");
     if (doms[i]->desc.device != d0->desc.device) return d0->fail(LBM_ERR_INVALID_ARG, "mixed devices in batch");
     if (doms[i]->tape) return d0->fail(LBM_ERR_UNSUPPORTED, "batched stepping does not record tapes");
+    if (doms[i]->walls) return d0->fail(LBM_ERR_UNSUPPORTED, "batched domains cannot have wall faces");
     if (*doms[i]->h_err & 1) return d0->fail(LBM_ERR_DIVERGED, "a domain of the batch has diverged");
   }
   if (steps == 0) return LBM_OK;

@@ -387,6 +387,7 @@ static lbm_status add_far_block(lbm_domain* dom, const double origin[3], double 
   for (int a = 0; a < 3; ++a)
     if (dom->desc.periodic[a])
       return dom->fail(LBM_ERR_UNSUPPORTED, "far-field blocks need a reference block without periodic faces");
+  if (dom->walls) return dom->fail(LBM_ERR_UNSUPPORTED, "walls and far-field blocks exclude each other");
   Block F;
   F.nx = dims[0]; F.ny = dims[1]; F.nz = dims[2];
   F.N = (size_t)F.nx * F.ny * F.nz;

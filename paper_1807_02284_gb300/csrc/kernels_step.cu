@@ -10,21 +10,26 @@ __constant__ int c_paper_to_cube[27] = {13, 14, 12, 16, 10, 22, 4,  17, 15, 11, 
 
 // MINB: CTAs of 256 threads per SM the registers are bounded for (3: 80 registers, no
 // spills; 4: 64 registers with a small spill, more loads in flight); chosen by autotuning.
-template <typename T, typename IT, bool ALIGN, int MINB>
+template <typename T, typename IT, bool ALIGN, int MINB, bool WALLS>
 __global__ void __launch_bounds__(256, MINB) k_step(BlockView v) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= v.nx || y >= v.ny) return;
-  cell_update<T, IT, ALIGN>(v, x, y, z);
+  cell_update<T, IT, ALIGN, WALLS>(v, x, y, z);
 }
 
 bool fits_32bit_index(size_t N) { return 27ull * (unsigned long long)N < 0xFFFFFFFFull; }
 
 template <typename T, typename IT, bool ALIGN>
 static void launch_step_t(const BlockView& v, dim3 grid, dim3 block, int minb, cudaStream_t s) {
-  if (minb >= 4) k_step<T, IT, ALIGN, 4><<<grid, block, 0, s>>>(v);
-  else k_step<T, IT, ALIGN, 3><<<grid, block, 0, s>>>(v);
+  if (v.walls) {
+    if (minb >= 4) k_step<T, IT, ALIGN, 4, true><<<grid, block, 0, s>>>(v);
+    else k_step<T, IT, ALIGN, 3, true><<<grid, block, 0, s>>>(v);
+  } else {
+    if (minb >= 4) k_step<T, IT, ALIGN, 4, false><<<grid, block, 0, s>>>(v);
+    else k_step<T, IT, ALIGN, 3, false><<<grid, block, 0, s>>>(v);
+  }
 }
 
 cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
@@ -85,9 +90,28 @@ cudaError_t launch_init(const BlockView& v, int storage, const float* rho, const
 __global__ void k_merge_user_flags(uint8_t* flags, const uint8_t* user, size_t N) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
        i += (size_t)gridDim.x * blockDim.x) {
-    const uint8_t keep = flags[i] & (F_GHOST);
+    const uint8_t keep = flags[i] & (F_GHOST | F_WALL);
     flags[i] = keep | (user[i] & (F_SOLID | F_INFLOW | F_SCALAR_SRC));
   }
+}
+
+// F_WALL on the nodes of the wall faces (bits x-, x+, y-, y+, z-, z+), off elsewhere.
+__global__ void k_mark_walls(uint8_t* flags, int nx, int ny, int nz, int walls) {
+  const size_t N = (size_t)nx * ny * nz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((size_t)nx * ny));
+    const bool w = ((walls & 1) && x == 0) || ((walls & 2) && x == nx - 1) ||
+                   ((walls & 4) && y == 0) || ((walls & 8) && y == ny - 1) ||
+                   ((walls & 16) && z == 0) || ((walls & 32) && z == nz - 1);
+    flags[i] = w ? (uint8_t)(flags[i] | F_WALL) : (uint8_t)(flags[i] & ~F_WALL);
+  }
+}
+
+cudaError_t launch_mark_walls(uint8_t* flags, int nx, int ny, int nz, int walls, cudaStream_t s) {
+  const size_t g = ((size_t)nx * ny * nz + 255) / 256;
+  k_mark_walls<<<(int)(g < 8192 ? g : 8192), 256, 0, s>>>(flags, nx, ny, nz, walls);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_merge_user_flags(uint8_t* flags, const uint8_t* user, size_t N,

@@ -119,12 +119,64 @@ __device__ __forceinline__ void flag_error(int* err, bool bad) {
   if (m && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(err, 1);
 }
 
+// No-slip wall node on a flat face of the block (the second-order wall of Sec. 6.1, read as
+// the regularized on-node wall): populations pulled through a wall face are completed by
+// bounce-back from their opposite (wall at rest); where both of a pair come through walls
+// (edges, corners) they take the rest equilibrium; rho is the mass of the completed set and
+// every population is rebuilt as w_i rho + (w_i / (2 c_s^4)) Q_i : Pi from the
+// non-equilibrium stress Pi of the completed set.  On shifted populations d = f - w.
+__device__ __forceinline__ void wall_regularize(float (&d)[27], const BlockView& v, int x, int y,
+                                                int z) {
+  const bool lo[3] = {(v.walls & 1) && x == 0, (v.walls & 4) && y == 0, (v.walls & 16) && z == 0};
+  const bool hi[3] = {(v.walls & 2) && x == v.nx - 1, (v.walls & 8) && y == v.ny - 1,
+                      (v.walls & 32) && z == v.nz - 1};
+  unsigned unk = 0u;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const int c[3] = {cxk(k), cyk(k), czk(k)};
+    bool u = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u |= (lo[a] && c[a] == 1) || (hi[a] && c[a] == -1);
+    if (u) unk |= 1u << k;
+  }
+  float s = 0.0f, wb = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const bool uk = (unk >> k) & 1u, uo = (unk >> (26 - k)) & 1u;
+    if (uk && uo) {
+      wb += wk(k);
+    } else {
+      if (uk) d[k] = d[26 - k];          // the opposite's source is inside: it is known
+      s += d[k];
+    }
+  }
+  const float drho = s / (1.0f - wb);
+  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const bool both = ((unk >> k) & 1u) && ((unk >> (26 - k)) & 1u);
+    const float neq = both ? 0.0f : d[k] - wk(k) * drho;
+    const float cx = (float)cxk(k), cy = (float)cyk(k), cz = (float)czk(k);
+    pxx = fmaf(cx * cx, neq, pxx); pyy = fmaf(cy * cy, neq, pyy); pzz = fmaf(cz * cz, neq, pzz);
+    pxy = fmaf(cx * cy, neq, pxy); pxz = fmaf(cx * cz, neq, pxz); pyz = fmaf(cy * cz, neq, pyz);
+  }
+  const float tr = (pxx + pyy + pzz) * (1.0f / 3.0f);
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const float cx = (float)cxk(k), cy = (float)cyk(k), cz = (float)czk(k);
+    const float qp = cx * cx * pxx + cy * cy * pyy + cz * cz * pzz +
+                     2.0f * (cx * cy * pxy + cx * cz * pxz + cy * cz * pyz) - tr;
+    d[k] = wk(k) * fmaf(4.5f, qp, drho);
+  }
+}
+
 // One node of one block: pull (with bounce-back and face handling), macroscopic moments,
 // adaptive rates from the lagged velocity, CMR collision, store of f~, u and the scalar.
 // Scale-boundary (ghost) nodes of refined blocks are not written: their next values come
 // from the coarse-to-fine mapping, which can therefore run concurrently with this update.
 // ALIGN: last sub-step of a refined block, storing the temporal alignment (see BlockView).
-template <typename T, typename IT, bool ALIGN = false>
+// WALLS: the block has no-slip wall faces (an instance without them carries no wall code).
+template <typename T, typename IT, bool ALIGN = false, bool WALLS = false>
 __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, int z) {
   const IT N = (IT)v.N;
   const T* __restrict__ din = static_cast<const T*>(v.d_in);
@@ -157,6 +209,9 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
   // all independent loads first: the pull and the lagged velocity neighbourhood
   pull_all<T, IT>(d, din, N, n);
   if (fl & F_NEAR_SOLID) bounce_back<T, IT>(d, din, N, v.flags, n, idx);
+  if constexpr (WALLS) {
+    if (fl & F_WALL) wall_regularize(d, v, x, y, z);
+  }
   const float g_lag = (v.rp.adaptive && !v.rp.local) ? grad_norm<IT>(v.u_in, N, n) : 0.0f;
 
   raw_moments(d);

@@ -31,7 +31,7 @@ namespace lbm {
 
 // Cell flags (bits 0..3 are user-visible, bit 4 is derived by the library).
 enum : uint8_t {
-  F_SOLID = 1, F_INFLOW = 2, F_SCALAR_SRC = 4, F_GHOST = 8, F_NEAR_SOLID = 16
+  F_SOLID = 1, F_INFLOW = 2, F_SCALAR_SRC = 4, F_GHOST = 8, F_NEAR_SOLID = 16, F_WALL = 32
 };
 
 __host__ __device__ constexpr int cxk(int k) { return k % 3 - 1; }

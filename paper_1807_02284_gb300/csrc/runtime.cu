@@ -96,6 +96,7 @@ BlockView Domain::view(int b, int from, int to) const {
   v.rp = B.rp;
   v.c_src = (float)desc.c_src;
   v.err = d_err;
+  v.walls = b == 0 ? walls : 0;
   return v;
 }
 
@@ -313,6 +314,26 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
       if (dom->blocks[i].far && dom->blocks[i].child == block_id)
         e = launch_outer_ghost(B.flags, B.nx, B.ny, B.nz, 1, dom->stream);
     if (e != cudaSuccess) return dom->cuda_fail(e, "set flags");
+    dom->invalidate_graphs();
+    return LBM_OK;
+  }
+  if (kind == LBM_BC_WALLS) {
+    if (block_id != 0) return dom->fail(LBM_ERR_INVALID_ARG, "walls are faces of block 0");
+    if (!ptr || nbytes < 6) return dom->fail(LBM_ERR_INVALID_ARG, "walls need 6 bytes");
+    if (on_device) return dom->fail(LBM_ERR_INVALID_ARG, "the wall mask is host memory");
+    const uint8_t* m = static_cast<const uint8_t*>(ptr);
+    int walls = 0;
+    for (int f = 0; f < 6; ++f)
+      if (m[f]) {
+        if (dom->desc.periodic[f / 2]) return dom->fail(LBM_ERR_INVALID_ARG, "a wall on a periodic axis");
+        walls |= 1 << f;
+      }
+    for (size_t i = 1; i < dom->blocks.size(); ++i)
+      if (dom->blocks[i].far && walls)
+        return dom->fail(LBM_ERR_UNSUPPORTED, "walls and far-field blocks exclude each other");
+    const cudaError_t e = launch_mark_walls(B.flags, B.nx, B.ny, B.nz, walls, dom->stream);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "wall flags");
+    dom->walls = walls;
     dom->invalidate_graphs();
     return LBM_OK;
   }

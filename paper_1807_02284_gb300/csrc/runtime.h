@@ -59,6 +59,7 @@ struct GraphCache;         // captured step graphs (scheduler.cu)
 struct lbm_domain {
   lbm_domain_desc desc{};
   unsigned long long serial = 0;        // unique per created domain (keys cached batch plans)
+  int walls = 0;                        // no-slip wall faces of block 0 (LBM_BC_WALLS bits)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t elt = 4;

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "LBM_OK", 1: "LBM_ERR_INVALID_ARG", 2: "LBM_ERR_OOM", 3: "LBM
                 4: "LBM_ERR_DIVERGED", 5: "LBM_ERR_TIMEOUT", 6: "LBM_ERR_UNSUPPORTED",
                 7: "LBM_ERR_STATE"}
 LBM_FP32, LBM_FP16_SHIFTED = 0, 1
-LBM_BC_FLAGS, LBM_BC_INFLOW = 0, 1
+LBM_BC_FLAGS, LBM_BC_INFLOW, LBM_BC_WALLS = 0, 1, 2
 LBM_FIELD_F, LBM_FIELD_U, LBM_FIELD_SCALAR, LBM_FIELD_RHO, LBM_FIELD_FLAGS = 0, 1, 2, 3, 4
 LBM_F32, LBM_F64, LBM_U8 = 0, 1, 2
 LBM_MACRO_RHO, LBM_MACRO_U, LBM_MACRO_SCALAR = 0, 1, 2
@@ -254,6 +254,11 @@ class Domain:
             flags = np.ascontiguousarray(flags, dtype=np.uint8)
         p, dev = _ptr(flags)
         self.check(self.lib.lbm_set_boundary(self.handle, block, LBM_BC_FLAGS, p, _nbytes(flags), dev))
+
+    def set_walls(self, faces):
+        """No-slip wall faces of block 0: six booleans (x-, x+, y-, y+, z-, z+)."""
+        m = np.ascontiguousarray([1 if f else 0 for f in faces], dtype=np.uint8)
+        self.check(self.lib.lbm_set_boundary(self.handle, 0, LBM_BC_WALLS, m.ctypes.data, 6, 0))
 
     def set_inflow(self, records, block=0):
         if isinstance(records, np.ndarray):
