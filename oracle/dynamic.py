@@ -140,3 +140,51 @@ def remove_last_block(ms: coupling.MultiScale):
     if len(ms.blocks) < 2:
         raise ValueError("only refined blocks can be removed")
     ms.blocks.pop()
+
+
+# ------------------------------------------------------------------ static construction
+
+def obstacle_box(flags):
+    """Bounding box (x0, y0, z0, x1, y1, z1) of the obstacle voxels of a block, or None."""
+    zz, yy, xx = np.nonzero((np.asarray(flags) & SOLID) != 0)
+    if zz.size == 0:
+        return None
+    return (int(xx.min()), int(yy.min()), int(zz.min()), int(xx.max()), int(yy.max()), int(zz.max()))
+
+
+def static_scales(flags, n_scales: int, h_min: float, d_max: float, wake: float, flow_axis: int = 0):
+    """Static scale construction (Sec. 5) on the reference block: the distance to the
+    obstacles is quantised into n_scales scales, scale 0 being s0 (h = 1) and scale
+    n_scales - 1 the finest (h = h_min), the spacings linearly interpolated in between.
+    Scale i covers the samples within d_i = d_max (n - 1 - i) / (n - 1) of an obstacle,
+    extended downstream along flow_axis by `wake` (the wake region behind the object).
+
+    Readings: blocks are boxes, and the bounding box of the samples within d of the
+    obstacles is the obstacles' bounding box widened by d; the wake extension is the same
+    for every refined scale; each box is clipped to s0, snapped to the finest whole number of
+    its own spacing inside the clipped span, and kept at >= 4 nodes per axis (growing upward,
+    or shifted down at s0's upper end).  Returns [(origin, h, dims)] for scales 1 .. n-1,
+    coarse to fine (empty without obstacles)."""
+    box = obstacle_box(flags)
+    if box is None or n_scales < 2:
+        return []
+    Z, Y, X = np.asarray(flags).shape
+    ref = (X, Y, Z)
+    out = []
+    for i in range(1, n_scales):
+        h = 1.0 + (h_min - 1.0) * i / (n_scales - 1)
+        d = d_max * (n_scales - 1 - i) / (n_scales - 1)
+        lo = [box[a] - d for a in range(3)]
+        hi = [box[3 + a] + d for a in range(3)]
+        hi[flow_axis] += wake
+        origin, dims = [], []
+        for a in range(3):
+            top = float(ref[a] - 1)
+            l, u = max(lo[a], 0.0), min(hi[a], top)
+            n = max(int(math.floor((u - l) / h + 1e-9)) + 1, 4)
+            if l + (n - 1) * h > top + 1e-9:
+                l = max(0.0, top - (n - 1) * h)
+            origin.append(l)
+            dims.append(n)
+        out.append((tuple(origin), h, tuple(dims)))
+    return out

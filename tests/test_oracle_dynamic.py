@@ -121,3 +121,18 @@ def test_new_block_of_a_uniform_flow_is_its_exact_equilibrium_and_stays_uniform(
         assert torch.allclose(u[2], torch.full_like(u[2], -0.01), atol=1e-13)
     dynamic.remove_last_block(ms)
     assert len(ms.blocks) == 1
+
+
+def test_static_scales_worked_example():
+    """Obstacle voxels spanning x 10..14, y 20..23, z 5..9 in a 64 x 48 x 32 block; 3 scales
+    with h_min = 0.5, d_max = 8, wake 12 along x (worked by hand):
+      scale 1: h = 0.75, d = 4: x [6, 30], y [16, 27], z [1, 13] -> 33, 15, 17 nodes;
+      scale 2: h = 0.5,  d = 0: x [10, 26], y [20, 23], z [5, 9]  -> 33, 7, 9 nodes."""
+    flags = np.zeros((32, 48, 64), np.uint8)
+    flags[5:10, 20:24, 10:15] = grid.SOLID
+    sc = dynamic.static_scales(flags, 3, 0.5, 8.0, 12.0, flow_axis=0)
+    assert len(sc) == 2
+    (o1, h1, d1), (o2, h2, d2) = sc
+    assert h1 == 0.75 and d1 == (33, 15, 17) and np.allclose(o1, (6.0, 16.0, 1.0))
+    assert h2 == 0.5 and d2 == (33, 7, 9) and np.allclose(o2, (10.0, 20.0, 5.0))
+    assert dynamic.static_scales(np.zeros((8, 8, 8), np.uint8), 3, 0.5, 4.0, 0.0) == []
