@@ -211,6 +211,20 @@ lbm_status lbm_build_dynamic_scale(lbm_domain* dom, int32_t src_block, double h,
                                    double g_threshold, double u_threshold, int32_t margin,
                                    int32_t replace_last, int32_t* block_id);
 
+/* Static scale construction (Sec. 5): the distance to the obstacle voxels of block 0 is
+   quantised into n_scales scales, scale 0 being block 0 (h = 1) and scale n_scales - 1 the
+   finest (h = h_min), the spacings linearly interpolated in between; scale i covers the
+   nodes within d_i = d_max (n_scales - 1 - i) / (n_scales - 1) of an obstacle, extended
+   downstream along flow_axis (0, 1, 2 = x, y, z) by `wake` reference units.  Blocks are
+   boxes: scale i is the obstacles' bounding box widened by d_i (plus the wake), clipped to
+   block 0, with floor(extent / h + 1e-9) + 1 nodes per axis, at least 4 (shifted down, not
+   below 0, at block 0's upper end).  The scales are added coarse to fine with
+   lbm_add_scale_block and started with lbm_init_block_from_parent; *n_added receives their
+   number (0 without obstacles).  INVALID_ARG for n_scales < 2, h_min outside (0, 1),
+   negative d_max or wake, a bad axis; the errors of the calls it makes otherwise. */
+lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales, double h_min, double d_max,
+                                   double wake, int32_t flow_axis, int32_t* n_added);
+
 /* Sets boundary data of one block (see LBM_BC_*).  ptr/nbytes describe the caller array;
    it is copied before return (host) or before the next enqueued work (device). */
 lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, const void* ptr,

@@ -93,6 +93,38 @@ __global__ void __launch_bounds__(256) k_detect(BlockView v, float g_thr, float 
   }
 }
 
+// Count and bounding box of the nodes carrying any of `mask` (per-CTA reduction, one atomic
+// per quantity and CTA).
+__global__ void __launch_bounds__(256) k_flag_box(const uint8_t* __restrict__ flags, int nx, int ny,
+                                                  int nz, uint8_t mask, RegionOut* out) {
+  unsigned cnt = 0;
+  int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {-1, -1, -1};
+  for (int r = blockIdx.x; r < ny * nz; r += gridDim.x) {
+    const int y = r % ny, z = r / ny;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      if (!(flags[((size_t)z * ny + y) * nx + x] & mask)) continue;
+      ++cnt;
+      lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
+      lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
+      lo[2] = min(lo[2], z); hi[2] = max(hi[2], z);
+    }
+  }
+  const unsigned full = 0xffffffffu;
+  cnt = __reduce_add_sync(full, cnt);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(full, lo[a]);
+    hi[a] = __reduce_max_sync(full, hi[a]);
+  }
+  if ((threadIdx.x & 31) == 0 && cnt) {
+    atomicAdd(&out->count, (unsigned long long)cnt);
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&out->lo[a], lo[a]);
+      atomicMax(&out->hi[a], hi[a]);
+    }
+  }
+}
+
 // Obstacle and scalar-source bits of a block from the nearest node of another block (index
 // floor(q + 1/2) of the node's position q in the source's node units, clamped); the ghost
 // bit of the destination is kept, every other bit cleared.
@@ -259,3 +291,60 @@ extern "C" lbm_status lbm_build_dynamic_scale(lbm_domain* dom, int32_t src_block
   *block_id = id;
   return LBM_OK;
 }
+
+extern "C" lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales, double h_min,
+                                              double d_max, double wake, int32_t flow_axis,
+                                              int32_t* n_added) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (!n_added) return dom->fail(LBM_ERR_INVALID_ARG, "null n_added");
+  *n_added = 0;
+  if (n_scales < 2 || !(h_min > 0.0 && h_min < 1.0) || !(d_max >= 0.0) || !(wake >= 0.0) ||
+      flow_axis < 0 || flow_axis > 2)
+    return dom->fail(LBM_ERR_INVALID_ARG, "need n_scales >= 2, 0 < h_min < 1, d_max, wake >= 0, axis 0..2");
+  const Block& B0 = dom->blocks[0];
+  RegionOut* d_out = reinterpret_cast<RegionOut*>(dom->d_red);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dom->desc.device);
+  const int grid = std::max(1, std::min(B0.ny * B0.nz, 8 * std::max(sms, 1)));
+  k_detect_init<<<1, 1, 0, dom->stream>>>(d_out);
+  k_flag_box<<<grid, 256, 0, dom->stream>>>(B0.flags, B0.nx, B0.ny, B0.nz, F_SOLID, d_out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dom->h_red, d_out, sizeof(RegionOut), cudaMemcpyDeviceToHost, dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "obstacle box");
+  lbm_status st = dom->sync_and_check();
+  if (st != LBM_OK) return st;
+  RegionOut r;
+  std::memcpy(&r, dom->h_red, sizeof(RegionOut));
+  if (r.count == 0) return LBM_OK;
+  const int ref[3] = {B0.nx, B0.ny, B0.nz};
+  for (int i = 1; i < n_scales; ++i) {
+    const double h = 1.0 + (h_min - 1.0) * i / (n_scales - 1);
+    const double d = d_max * (n_scales - 1 - i) / (n_scales - 1);
+    double origin[3];
+    int32_t dims[3];
+    for (int a = 0; a < 3; ++a) {
+      const double top = (double)(ref[a] - 1);
+      double lo = r.lo[a] - d, hi = r.hi[a] + d;
+      if (a == flow_axis) hi += wake;
+      lo = std::max(lo, 0.0);
+      hi = std::min(hi, top);
+      const int n = std::max((int)std::floor((hi - lo) / h + 1e-9) + 1, 4);
+      if (lo + (n - 1) * h > top + 1e-9) lo = std::max(0.0, top - (n - 1) * h);
+      origin[a] = lo;
+      dims[a] = n;
+    }
+    int32_t id = -1;
+    st = lbm_add_scale_block(dom, origin, h, dims, &id);
+    if (st != LBM_OK) return st;
+    st = lbm_init_block_from_parent(dom, id);
+    if (st != LBM_OK) {
+      lbm_remove_scale_block(dom, id);
+      return st;
+    }
+    ++*n_added;
+  }
+  return LBM_OK;
+}
+

@@ -74,6 +74,8 @@ _SIGNATURES = {
     "lbm_init_block_from_parent": (_I, [_P, _I]),
     "lbm_build_dynamic_scale": (_I, [_P, _I, C.c_double, C.c_double, C.c_double, _I, _I,
                                      C.POINTER(C.c_int32)]),
+    "lbm_build_static_scales": (_I, [_P, _I, C.c_double, C.c_double, C.c_double, _I,
+                                     C.POINTER(C.c_int32)]),
     "lbm_step": (_I, [_P, _I]),
     "lbm_sync": (_I, [_P]),
     "lbm_read_macro": (_I, [_P, _I, _I, _P, C.c_size_t, _I]),
@@ -239,6 +241,14 @@ class Domain:
                                                     int(margin), 1 if replace_last else 0,
                                                     C.byref(bid)))
         return bid.value
+
+    def build_static_scales(self, n_scales: int, h_min: float, d_max: float, wake: float = 0.0,
+                            flow_axis: int = 0) -> int:
+        n = C.c_int32()
+        self.check(self.lib.lbm_build_static_scales(self.handle, int(n_scales), float(h_min),
+                                                    float(d_max), float(wake), int(flow_axis),
+                                                    C.byref(n)))
+        return n.value
 
     def info(self, block=0) -> lbm_block_info:
         i = lbm_block_info()

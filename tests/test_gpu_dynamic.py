@@ -131,3 +131,29 @@ def test_dynamic_scale_argument_checks(lib):
     dom.step(2)
     dom.sync()
     dom.close()
+
+
+def test_static_scales_match_oracle(lib):
+    """Static construction (Sec. 5): 3 scales (h = 1, 0.75, 0.5) around the sphere with a
+    wake along x; the placed blocks equal the oracle's, their started states and the
+    following steps match."""
+    sc = _scene()
+    dom = gpu_multiscale(sc)
+    ms = coupling.MultiScale.build(sc)
+    for _ in range(2):
+        dom.step(1)
+        ms.step()
+    n = dom.build_static_scales(3, 0.5, 4.0, wake=6.0, flow_axis=0)
+    plan = dynamic.static_scales(sc.blocks[0].flags, 3, 0.5, 4.0, 6.0, flow_axis=0)
+    assert n == len(plan) == 2
+    for i, (o, h, d) in enumerate(plan, start=1):
+        info = dom.info(i)
+        assert tuple(info.dims) == d and abs(info.h - h) < 1e-12
+        assert np.allclose(tuple(info.origin), o, atol=1e-12)
+        dynamic.add_block_from_parent(ms, o, h, d)
+    compare(dom, ms, "static scales started")
+    for _ in range(2):
+        dom.step(1)
+        ms.step()
+    compare(dom, ms, "static scales stepped")
+    dom.close()
