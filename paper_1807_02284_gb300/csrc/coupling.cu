@@ -666,6 +666,24 @@ lbm_status multiscale_step(lbm_domain* dom) {
   lbm_status st = dom->aux(&aux);
   if (st != LBM_OK) return st;
   cudaError_t e;
+  const int nb = (int)dom->blocks.size();
+  // early phase, on its own stream, concurrent with s0's step: every refined block's ghost
+  // refresh at t_n and first sub-step need only t_n states (its source's saved level and its
+  // own), so they run while s0 advances (the later sub-steps need s0's new state)
+  cudaStream_t early = dom->post_stream(nb);
+  if (!early) return dom->fail(LBM_ERR_CUDA, "early-phase stream");
+  e = cudaEventRecord(dom->event(4), s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(early, dom->event(4), 0);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "early-phase fork");
+  for (int b = 1; b < nb && e == cudaSuccess; ++b) {
+    Block& B = dom->blocks[b];
+    if (B.far) continue;
+    const int L = saved[b], A = (L + 1) % 3;
+    e = prior_map(dom, b, saved, 0.0f, L, early);
+    if (e == cudaSuccess) e = launch_step(dom->view(b, L, A), dom->desc.storage, B.bx, B.by, early, B.minb);
+    if (e == cudaSuccess) e = cudaEventRecord(dom->event(10 + nb + b), early);
+  }
+  if (e != cudaSuccess) return dom->cuda_fail(e, "early phase");
   {  // reference scale: one step
     Block& B0 = dom->blocks[0];
     const int nxt = B0.cur ^ 1;
@@ -715,8 +733,6 @@ lbm_status multiscale_step(lbm_domain* dom) {
       e = cudaStreamWaitEvent(s, dom->event(10 + B.prior.src), 0);
       if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping join");
     }
-    e = prior_map(dom, b, saved, 0.0f, cur, s);
-    if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
     for (int j = 1; j <= B.substeps; ++j) {
       const int out = (j == 1) ? A : (cur == A ? Bv : A);
       // fork: ghost layer of `out` for the next sub-step (or at t_n + dt_0 after the last)
@@ -727,7 +743,9 @@ lbm_status multiscale_step(lbm_domain* dom) {
       if (e == cudaSuccess) e = cudaEventRecord(dom->event(1), aux);
       if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
       BlockView v = dom->view(b, cur, out);
-      if (j == B.substeps && !exact) {
+      if (j == 1) {                  // ran in the early phase: join it
+        e = cudaStreamWaitEvent(s, dom->event(10 + nb + b), 0);
+      } else if (j == B.substeps && !exact) {
         const double t1 = (B.substeps - 1) * B.h, t2 = B.substeps * B.h, T = 1.0;
         v.f_al0 = B.lv[L].f;
         v.c_al0 = B.lv[L].c;

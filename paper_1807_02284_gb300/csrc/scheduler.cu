@@ -230,8 +230,8 @@ lbm_status lbm_domain::advance(int n) {
     cudaStream_t a = nullptr;
     lbm_status st = aux(&a);
     if (st != LBM_OK) return st;
-    if (!event(10 + (int)blocks.size())) return fail(LBM_ERR_CUDA, "cudaEventCreate");
-    if (!post_stream((int)blocks.size() - 1)) return fail(LBM_ERR_CUDA, "cudaStreamCreate");
+    if (!event(10 + 2 * (int)blocks.size())) return fail(LBM_ERR_CUDA, "cudaEventCreate");
+    if (!post_stream((int)blocks.size())) return fail(LBM_ERR_CUDA, "cudaStreamCreate");
   }
   if (tape != nullptr) return advance_direct(n);
   std::vector<int> start(blocks.size());
