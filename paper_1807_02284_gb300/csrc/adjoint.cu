@@ -314,6 +314,25 @@ static void launch_pass_a(const AdjArgs& a, int minb, bool open, dim3 grd, dim3 
   }
 }
 
+// Weight at this node of the departure sample of the node D steps away along one axis, when
+// neither clamping nor wrap-around can move that sample's cell (the axis is periodic with >= 4
+// nodes, or this node is >= 2 nodes from both ends of an open axis): the sample sits at
+// dsp = clamp(-u, -1, 1) from its node, in the cell [f, f + 1] with f = floor(dsp) and
+// fraction t = dsp - f, so this node is the cell's lower corner when f = -D (weight 1 - t) and
+// its upper corner when f = -D - 1 (weight t).  Same values as sl_axis followed by the corner
+// test of the general gather.
+template <int D>
+__device__ __forceinline__ float sl_weight_interior(float u) {
+  float dsp = -u;
+  if (!(dsp == dsp)) dsp = 0.0f;
+  dsp = fminf(fmaxf(dsp, -1.0f), 1.0f);
+  const float f = floorf(dsp);
+  const float t = dsp - f;
+  float w = f == (float)(-D) ? 1.0f - t : 0.0f;
+  if constexpr (D <= 0) w = f == (float)(-D - 1) ? t : w;
+  return w;
+}
+
 template <bool ACC>
 __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
   const BlockView& v = a.fwd;
@@ -354,6 +373,38 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
   const uint32_t xs[3] = {n.xm, n.x0, n.xp};
   const uint32_t rs[3] = {n.rm, n.r0, n.rp};
   const uint32_t ps[3] = {n.pm, n.p0, n.pp};
+  bool interior = true;
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+    interior = interior && (v.per[b] ? nn[b] >= 4 : (cc[b] >= 2 && cc[b] <= nn[b] - 3));
+  if (interior) {
+    // every neighbour is distinct and its sample's cell neither clamps nor wraps; the sum
+    // runs over the 27 neighbours in the order of the general gather below, a skipped
+    // neighbour adding 0
+    float gam = 0.0f;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const uint32_t j = ps[dz] + rs[dy] + xs[dx];
+          float G = __ldg(a.gam_in + j);
+          if (__ldg(v.flags + j) & (F_SOLID | F_SCALAR_SRC | F_GHOST)) G = 0.0f;
+          const float wx = dx == 0 ? sl_weight_interior<-1>(__ldg(a.u_next + j))
+                         : dx == 1 ? sl_weight_interior<0>(__ldg(a.u_next + j))
+                                   : sl_weight_interior<1>(__ldg(a.u_next + j));
+          const float wy = dy == 0 ? sl_weight_interior<-1>(__ldg(a.u_next + N + j))
+                         : dy == 1 ? sl_weight_interior<0>(__ldg(a.u_next + N + j))
+                                   : sl_weight_interior<1>(__ldg(a.u_next + N + j));
+          const float wz = dz == 0 ? sl_weight_interior<-1>(__ldg(a.u_next + 2 * N + j))
+                         : dz == 1 ? sl_weight_interior<0>(__ldg(a.u_next + 2 * N + j))
+                                   : sl_weight_interior<1>(__ldg(a.u_next + 2 * N + j));
+          gam = fmaf(wx * wy * wz, G, gam);
+        }
+    a.gam_out[idx] = ACC ? a.gam_out[idx] + gam : gam;
+    return;
+  }
   const int cx[3] = {(int)n.xm, x, (int)n.xp};
   const int cy[3] = {(int)(n.rm / (uint32_t)v.nx), y, (int)(n.rp / (uint32_t)v.nx)};
   const int cz[3] = {(int)(n.pm / ((uint32_t)v.nx * v.ny)), z, (int)(n.pp / ((uint32_t)v.nx * v.ny))};
