@@ -215,6 +215,135 @@ def cpu_baseline_measure(budget_s=15.0, storage="fp32"):
                        "bound_u_rel": 1e-5 if storage == "fp32" else None}}
 
 
+def parity_by_variant():
+    """Error against the FP64 oracle of each variant the default line reports, each on a
+    small seeded case of its own kind run through the same kernel instances (a few seconds
+    of oracle time each).  Errors are max-abs velocity errors relative to max|u| (gradient:
+    relative L2 error), with the bound the parity tests hold them to."""
+    import dataclasses
+
+    import torch
+
+    import synth
+    from oracle import adjoint as oadj
+    from oracle import coupling, grid
+    from paper_1807_02284_gb300 import lbm
+    r32 = lambda a: np.asarray(a, dtype=np.float32)
+
+    def single(sc, steps, storage="fp32", grad_mode="lagged", walls=None):
+        b = sc.blocks[0]
+        dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, storage=storage,
+                         adaptive=sc.adaptive, c_src=sc.c_src, grad_mode=grad_mode)
+        if walls:
+            dom.set_walls(walls)
+        dom.set_flags(b.flags)
+        dom.init_macro(r32(b.u0), rho=r32(b.rho0), c=r32(b.c0))
+        dom.step(steps)
+        u = dom.read_field(lbm.LBM_FIELD_U, lbm.LBM_F64).reshape((3,) + b.shape_zyx)
+        dom.close()
+        st = grid.init_state(r32(b.rho0).astype(np.float64), r32(b.u0).astype(np.float64),
+                             r32(b.c0).astype(np.float64), b.flags)
+        p = grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=sc.adaptive, c_src=sc.c_src,
+                        grad_mode=grad_mode)
+        if walls:
+            p = dataclasses.replace(p, walls=tuple(walls))
+        for _ in range(steps):
+            st = grid.step(st, p)
+        uo = st.u.numpy()
+        return float(np.abs(u - uo).max() / np.abs(uo).max())
+
+    def multi(sc, steps, far=()):
+        dom = lbm.Domain(sc.blocks[0].dims, sc.nu, periodic=sc.periodic, adaptive=sc.adaptive,
+                         c_src=sc.c_src)
+        for b in sc.blocks[1:]:
+            dom.add_scale_block(b.origin, b.h, b.dims)
+        for i, b in enumerate(sc.blocks):
+            dom.set_flags(b.flags, block=i)
+            dom.init_macro(r32(b.u0), rho=r32(b.rho0), c=r32(b.c0), block=i)
+        ms = coupling.MultiScale.build(sc)
+        for fb in far:                  # far-field blocks (h > 1) around the scene
+            fid = dom.add_scale_block(fb.origin, fb.h, fb.dims)
+            dom.set_flags(fb.flags, block=fid)
+            dom.init_macro(r32(fb.u0), rho=r32(fb.rho0), c=r32(fb.c0), block=fid)
+            ms.add_far_block(fb.origin, fb.h, fb.dims, fb.rho0, fb.u0, fb.c0, fb.flags)
+        dom.step(steps)
+        for _ in range(steps):
+            ms.step()
+        err, umax = 0.0, 0.0
+        for i, b in enumerate(ms.blocks):
+            u = dom.read_field(lbm.LBM_FIELD_U, lbm.LBM_F64, i).reshape(tuple(b.state.u.shape))
+            uo = b.state.u.numpy()
+            err, umax = max(err, float(np.abs(u - uo).max())), max(umax, float(np.abs(uo).max()))
+        dom.close()
+        return err / umax
+
+    out = {}
+    t0 = time.perf_counter()
+    plume = synth.random_scene(dims=(24, 20, 20), seed=21, periodic=(False, False, False),
+                               spheres=[(10.0, 10.0, 10.0, 3.0)], inflow=(10, 10, 4.0, 0.1),
+                               nu=1e-4)
+    out["plume256_fp16"] = {"u_max_abs_err_rel": single(plume, 6, storage="fp16"),
+                            "bound": 2e-3, "case": "24x20x20 plume-shaped scene, 6 steps"}
+    out["plume256_local"] = {"u_max_abs_err_rel": single(plume, 6, grad_mode="local"),
+                             "bound": 1e-5, "case": "24x20x20 plume-shaped scene, 6 steps"}
+    out["plume256_walls"] = {"u_max_abs_err_rel": single(plume, 6, walls=(False,) * 4 + (True, True)),
+                             "bound": 1e-5,
+                             "case": "24x20x20 plume-shaped scene, floor + lid walls, 6 steps"}
+    ms = synth.multiscale(scale=0.25, nu=2e-3, flow_amp=0.06)
+    out["multiscale3"] = {"u_max_abs_err_rel": multi(ms, 2), "bound": 1e-5,
+                          "case": "the 3-block scene scaled by 1/4 (32^3, 24^3, 16^3), 2 reference steps"}
+    far = synth.random_scene(dims=(20, 18, 16), seed=41, periodic=(False, False, False),
+                             spheres=[(11.0, 9.0, 8.0, 2.5)], inflow=(9, 8, 3.0, 0.08), nu=0.004)
+    fb = synth.far_block(far.blocks[0], 1.5, 6.0, seed=5, amp=0.03)
+    out["farfield256"] = {"u_max_abs_err_rel": multi(far, 3, far=(fb,)), "bound": 1e-5,
+                          "case": "20x18x16 scene inside a far block at h = 1.5, 3 reference steps"}
+    bs = synth.batch(count=2, seed=41, lo=10, hi=16, nu=2e-3)
+    worst = 0.0
+    doms = []
+    for s2 in bs:
+        b = s2.blocks[0]
+        d = lbm.Domain(b.dims, s2.nu, periodic=s2.periodic, adaptive=s2.adaptive, c_src=s2.c_src)
+        d.set_flags(b.flags)
+        d.init_macro(r32(b.u0), rho=r32(b.rho0), c=r32(b.c0))
+        doms.append(d)
+    lbm.step_batch(doms, 3)
+    for d, s2 in zip(doms, bs):
+        b = s2.blocks[0]
+        st = grid.init_state(r32(b.rho0).astype(np.float64), r32(b.u0).astype(np.float64),
+                             r32(b.c0).astype(np.float64), b.flags)
+        p = grid.Params(nu=s2.nu, periodic=s2.periodic, adaptive=s2.adaptive, c_src=s2.c_src)
+        for _ in range(3):
+            st = grid.step(st, p)
+        u = d.read_field(lbm.LBM_FIELD_U, lbm.LBM_F64).reshape((3,) + b.shape_zyx)
+        uo = st.u.numpy()
+        worst = max(worst, float(np.abs(u - uo).max() / np.abs(uo).max()))
+        d.close()
+    out["batch64"] = {"u_max_abs_err_rel": worst, "bound": 1e-5,
+                      "case": "2 simulations (edges 10-16) in one persistent launch, 3 steps"}
+    sc, target = synth.adjoint_scene(n=12, seed=5, nu=0.01, amp=0.05)
+    b = sc.blocks[0]
+    dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, adaptive=sc.adaptive)
+    dom.set_flags(b.flags)
+    dom.init_macro(r32(b.u0), rho=r32(b.rho0), c=r32(b.c0))
+    dom.set_tape(3)
+    dom.step(8)
+    c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64)
+    dldc = torch.tensor(c - target.reshape(-1), dtype=torch.float32, device="cuda")
+    g = torch.empty(3 * b.flags.size, dtype=torch.float32, device="cuda")
+    dom.adjoint_step(8, dldc, g)
+    dom.sync()
+    dom.close()
+    p = grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=sc.adaptive)
+    _, go, _ = oadj.loss_and_grad(r32(b.u0).astype(np.float64), r32(b.rho0).astype(np.float64),
+                                  r32(b.c0).astype(np.float64), b.flags, p, 8, target)
+    go = go.numpy().reshape(-1)
+    gg = g.cpu().numpy().astype(np.float64)
+    out["adjoint128"] = {"grad_rel_l2_err": float(np.linalg.norm(gg - go) / np.linalg.norm(go)),
+                         "bound": 1e-3, "case": "12^3 smoke control, 8 steps, checkpoint every 3"}
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -378,6 +507,11 @@ def run_ours(args):
             line["cpu_baseline"] = cpu_baseline_measure(args.cpu_budget, storage)
         if ws == 1 and args.workload == "plume256" and not args.no_variants:
             line["variants"] = _variants(args)
+            if "cpu_baseline" in line:   # the variants' errors against the FP64 oracle
+                try:
+                    line["cpu_baseline"]["parity_by_variant"] = parity_by_variant()
+                except Exception as ex:  # report, do not hide
+                    line["cpu_baseline"]["parity_by_variant"] = {"error": f"{type(ex).__name__}: {ex}"}
         print(json.dumps(line), flush=True)
     dom.close()
     if ws > 1:
@@ -638,6 +772,112 @@ def run_dynamic(args, emit=True):
     return out
 
 
+def _line_spectra(u, mask_yz, x0, x1):
+    """Mean power spectrum of the velocity fluctuation along x over the lines (y, z) in
+    mask_yz, between x0 and x1 (line mean removed, Hann window, 3 components summed)."""
+    import torch
+    seg = u[:, :, :, x0:x1][:, mask_yz]                      # (3, lines, L)
+    seg = seg - seg.mean(dim=-1, keepdim=True)
+    win = torch.hann_window(x1 - x0, periodic=False, dtype=seg.dtype, device=seg.device)
+    F = torch.fft.rfft(seg * win, dim=-1)
+    return (F.real ** 2 + F.imag ** 2).sum(0).mean(0)        # E(k), k = 0 .. L/2
+
+
+def run_ringing(args, emit=True):
+    """Relaxation comparison on the flow past a sphere at the resolution and viscosity of
+    Fig. 3 (196 x 98 x 98, nu = 1e-4): the same run with fixed high-order relaxation
+    (phi = 1), adaptive relaxation from the lagged velocity gradient, and adaptive relaxation
+    from the node's own strain rate.  Ringing is read from spectra: the power spectrum of the
+    velocity fluctuation along the flow axis on lines outside the jet (distance > 30 from
+    its axis, where the flow is smooth and high wavenumbers are artefacts) and inside it
+    (distance < 12, the turbulence the relaxation should keep), every 250 steps; a run that
+    blows up reports the step by which the library's divergence check caught it.  value =
+    MLUPS of the adaptive (lagged-gradient) run."""
+    import torch
+
+    import synth
+    from paper_1807_02284_gb300 import lbm
+
+    torch.cuda.set_device(0)
+    sc = synth.ringing_channel()
+    b = sc.blocks[0]
+    nx, ny, nz = b.dims
+    N = b.flags.size
+    K = max(args.steps, 1)
+    zz, yy = torch.meshgrid(torch.arange(nz), torch.arange(ny), indexing="ij")
+    r = torch.sqrt((yy - 49.0) ** 2 + (zz - 49.0) ** 2)
+    outer = ((r > 30.0) & (yy >= 4) & (yy < ny - 4) & (zz >= 4) & (zz < nz - 4)).cuda()
+    jet = (r < 12.0).cuda()
+    x0, x1 = 60, nx - 8                                       # downstream of the sphere
+    res, clk = {}, None
+    for mode, adaptive, grad in (("fixed", False, "lagged"), ("adaptive_lagged", True, "lagged"),
+                                 ("adaptive_local", True, "local")):
+        stream = torch.cuda.Stream()
+        dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, adaptive=adaptive,
+                         c_src=sc.c_src, stream=stream, grad_mode=grad)
+        dom.set_flags(b.flags)
+        dom.init_macro(b.u0.astype(np.float32), rho=b.rho0.astype(np.float32),
+                       c=b.c0.astype(np.float32))
+        dom.step(args.warmup)
+        dom.sync()
+        sampler = ClockSampler(0) if mode == "adaptive_lagged" else None
+        if sampler:
+            sampler.start()
+        rec = {"steps": [], "outer_high_k_fraction": [], "jet_fluctuation_energy": [],
+               "jet_high_k_fraction": []}
+        t, done, diverged = 0.0, 0, None
+        u = torch.empty(3 * N, dtype=torch.float32, device="cuda")
+        while done < K:                 # chunks of 250 steps, spectra between the chunks
+            n = min(250, K - done)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dom.step(n)
+            e1.record(stream)
+            e1.synchronize()
+            t += e0.elapsed_time(e1) / 1e3
+            done += n
+            try:
+                dom.read_field(lbm.LBM_FIELD_U, lbm.LBM_F32, out=u)
+                dom.sync()
+            except lbm.LBMError as ex:
+                if ex.status != lbm.LBM_ERR_DIVERGED:
+                    raise
+                diverged = done
+                break
+            uu = u.view(3, nz, ny, nx).double()
+            e_out = _line_spectra(uu, outer, x0, x1)
+            e_jet = _line_spectra(uu, jet, x0, x1)
+            kh = e_out.numel() // 2                           # half the Nyquist wavenumber
+            rec["steps"].append(args.warmup + done)
+            rec["outer_high_k_fraction"].append(float(e_out[kh:].sum() / e_out[1:].sum()))
+            rec["jet_fluctuation_energy"].append(float(e_jet[1:].sum()))
+            rec["jet_high_k_fraction"].append(float(e_jet[kh:].sum() / e_jet[1:].sum()))
+        if sampler:
+            clk = sampler.stop()
+        dom.close()
+        res[mode] = dict(mlups=N * done / t / 1e6,
+                         diverged_by_step=None if diverged is None else args.warmup + diverged,
+                         **rec)
+    peak, peak_src = _peaks()
+    alg, per_fluid = _algorithmic_bytes(b.flags, "fp32")
+    ml = res["adaptive_lagged"]["mlups"]
+    achieved = alg * ml * 1e6 / N / 1e9
+    out = {"metric": "MLUPS", "value": ml, "unit": "MLUPS", "steps": K, "warmup": args.warmup,
+           "higher_is_better": True, "dtype": "f32",
+           "config": {"workload": "ringing196_fp32", "dims": list(b.dims), "nu": sc.nu,
+                      "spectra": "velocity fluctuation along x, x in [60, 188), Hann window; "
+                                 "outer: lines > 30 from the jet axis; jet: lines < 12; "
+                                 "high k: above half the Nyquist wavenumber"},
+           "ringing": res,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                        "kernel": "k_step (adaptive, lagged gradient)"},
+           "clocks": clk}
+    if emit:
+        print(json.dumps(out), flush=True)
+    return out
+
+
 def _variants(args):
     """Measured summaries of the other hot-path variants for the default bench line."""
     import copy
@@ -652,7 +892,8 @@ def _variants(args):
                                   ("dynamic256", run_dynamic, 200, 10),
                                   ("farfield256", run_ours, 100, 10),
                                   ("batch64", run_batch, 100, 10),
-                                  ("adjoint128", run_adjoint, 200, 0)):
+                                  ("adjoint128", run_adjoint, 200, 0),
+                                  ("ringing196", run_ringing, 3000, 10)):
         a = copy.copy(args)
         a.workload, a.steps, a.warmup, a.no_cpu_baseline = name, steps, warm, True
         buf = io.StringIO()
@@ -661,7 +902,8 @@ def _variants(args):
                 fn(a)
             d = json.loads(buf.getvalue().strip().splitlines()[-1])
             res[name] = {k: d[k] for k in ("value", "unit", "ms_per_step", "roofline", "e2e",
-                                           "forward_with_tape_mlups", "config", "detect")
+                                           "forward_with_tape_mlups", "config", "detect",
+                                           "ringing")
                          if k in d}
         except Exception as ex:  # report, do not hide
             res[name] = {"error": f"{type(ex).__name__}: {ex}"}
@@ -676,7 +918,8 @@ def main():
     ap.add_argument("--workload", default="plume256",
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
                              "multiscale3", "batch64", "adjoint128", "adjoint64",
-                             "plume256_local", "dynamic256", "farfield256", "plume256_walls"])
+                             "plume256_local", "dynamic256", "farfield256", "plume256_walls",
+                             "ringing196"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -691,6 +934,8 @@ def main():
         run_batch(args)
     elif args.workload == "dynamic256":
         run_dynamic(args)
+    elif args.workload == "ringing196":
+        run_ringing(args)
     else:
         run_ours(args)
 

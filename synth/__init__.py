@@ -22,6 +22,7 @@ Workloads (shapes follow the paper's smoke and turbulence scenes, Sec. 6):
   ``multiscale``     3-block continuous-scale domain (h = 1, 1/1.5, 1/2.25)
   ``batch``          64 independent plumes with cube edges 24..96
   ``adjoint_scene``  128^3 periodic smoke-control problem (low-mode velocity + blobs)
+  ``ringing_channel`` 196 x 98 x 98 flow past a sphere (relaxation comparison, Fig. 3)
 """
 from __future__ import annotations
 
@@ -231,6 +232,18 @@ def plume(n=256, seed=1, nu=1e-5, u_in=0.1, r_in=16, sphere_r=24) -> Scene:
     voxelise_spheres(b, [(72 * s, n / 2, n / 2, sphere_r * s)])
     return Scene(blocks=[b], periodic=(False, False, False), nu=nu, adaptive=True,
                  name=f"plume_{n}", steps=1000)
+
+
+def ringing_channel(seed=6, nu=1e-4, u_in=0.1, r_in=12, sphere_r=12) -> Scene:
+    """Flow past a sphere in a 196 x 98 x 98 box with nu = 1e-4, the resolution and viscosity
+    of the relaxation comparison of Fig. 3: inflow disk (radius r_in, +/-1% seeded noise) on
+    the x = 0 face, a voxelised sphere at (40, 49, 49), Neumann faces."""
+    rng = np.random.default_rng(seed)
+    b = _empty_block((196, 98, 98))
+    inflow_disk(b, (49.0, 49.0), r_in, u_in, rng=rng, noise=0.01)
+    voxelise_spheres(b, [(40.0, 49.0, 49.0, sphere_r)])
+    return Scene(blocks=[b], periodic=(False, False, False), nu=nu, adaptive=True,
+                 name="ringing_196", steps=2000)
 
 
 def smooth_field(block: Block, seed, amp=0.05, wavelength=32.0):
