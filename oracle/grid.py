@@ -14,6 +14,10 @@ Per step and per node x (LBE of Sec. 1 / Appendix, iterated in pull form):
      Jacobian of the velocity field stored by the previous step (neighbour indices wrap or
      clamp as in 1; obstacle voxels store u = 0).
   4. f~ = f^in - T S (m - m^eq)  (Sec. 3.1, dense solve in ``oracle.cmr``).
+  1b. No-slip walls (Sec. 6.1's second-order wall, read as the regularized on-node wall):
+     on wall faces of the block, and, with ``obstacle_walls``, on the surface voxels of the
+     obstacles (obstacle voxels with a non-obstacle pull source), which then are active wall
+     nodes at rest while only the inner voxels stay inert; see ``regularized_wall``.
   5. Obstacle voxels hold the rest equilibrium and u = 0; inflow nodes hold the
      equilibrium T m^eq(1, u_in) (Dirichlet inflow of Sec. 6.1) with u_in their stored
      velocity; ghost nodes of refined blocks are left untouched (they belong to the
@@ -55,6 +59,7 @@ class Params:
     grad_mode: str = "lagged"    # "lagged" central differences of the stored velocity, or
                                  # "local" strain rate from the node's non-equilibrium moments
     walls: Sequence[bool] = (False,) * 6   # no-slip wall faces x-, x+, y-, y+, z-, z+
+    obstacle_walls: bool = False   # obstacle surfaces as regularized on-node walls
 
 
 @dataclasses.dataclass
@@ -120,19 +125,12 @@ def sample_trilinear(c: torch.Tensor, px, py, pz, periodic) -> torch.Tensor:
     return out
 
 
-def regularized_wall(f_in: torch.Tensor, walls, dims, x, y, z) -> torch.Tensor:
-    """Second-order no-slip wall on flat faces of the block (Sec. 6.1, read as the
-    regularized on-node wall of the cited method), applied to the pulled populations f_in
-    (K, 27) of the listed nodes.  At a node on a wall face, a population whose pull source
-    lies beyond the wall is unknown: it is completed by bounce-back from its opposite (the
-    wall is at rest); where the opposite is unknown too (edges, corners) both take the rest
-    equilibrium w_i rho.  rho is the mass of the completed set (for one wall:
-    sum_{c.n = 0} f + 2 sum_{c.n < 0} f).  All 27 populations are then rebuilt from the
-    equilibrium at (rho, u = 0) and the non-equilibrium stress Pi of the completed set,
-    f_i = w_i rho + w_i / (2 c_s^4) Q_i : Pi with Q_i = c_i c_i - c_s^2 I."""
+def face_unknowns(walls, dims, x, y, z) -> torch.Tensor:
+    """(K, 27) mask of the populations of the listed nodes whose pull source lies beyond a
+    wall face of the block."""
     n = dims
     coord = (x, y, z)
-    unk = torch.zeros(f_in.shape, dtype=torch.bool)
+    unk = torch.zeros((x.shape[0], 27), dtype=torch.bool)
     for q in range(27):
         col = torch.zeros(x.shape, dtype=torch.bool)
         for a in range(3):
@@ -142,6 +140,35 @@ def regularized_wall(f_in: torch.Tensor, walls, dims, x, y, z) -> torch.Tensor:
             if walls[2 * a + 1] and ca == -1:
                 col |= coord[a] == n[a] - 1
         unk[:, q] = col
+    return unk
+
+
+def surface_voxels(flags: torch.Tensor, periodic) -> torch.Tensor:
+    """Obstacle voxels with at least one non-obstacle node among their pull sources (the 26
+    neighbours, wrapped on periodic axes and clamped on open ones)."""
+    Z, Y, X = flags.shape
+    solid = (flags & SOLID) != 0
+    nx = {o: neighbour_index(X, periodic[0], o) for o in (-1, 0, 1)}
+    ny = {o: neighbour_index(Y, periodic[1], o) for o in (-1, 0, 1)}
+    nz = {o: neighbour_index(Z, periodic[2], o) for o in (-1, 0, 1)}
+    open_nb = torch.zeros_like(solid)
+    for q in range(27):
+        cx, cy, cz = (int(v) for v in C[q])
+        open_nb |= ~solid[nz[-cz]][:, ny[-cy]][:, :, nx[-cx]]
+    return solid & open_nb
+
+
+def regularized_wall(f_in: torch.Tensor, unk: torch.Tensor) -> torch.Tensor:
+    """Second-order no-slip wall (Sec. 6.1, read as the regularized on-node wall of the
+    cited method), applied to the pulled populations f_in (K, 27) of the listed nodes; unk
+    (K, 27) marks the populations whose pull source lies beyond the wall (outside a wall face
+    of the block, or inside an obstacle whose surface voxels are the wall nodes).  An unknown
+    population is completed by bounce-back from its opposite (the wall is at rest); where the
+    opposite is unknown too (edges, corners) both take the rest equilibrium w_i rho.  rho is
+    the mass of the completed set (for one wall: sum_{c.n = 0} f + 2 sum_{c.n < 0} f).  All
+    27 populations of a node with an unknown one are then rebuilt from the equilibrium at
+    (rho, u = 0) and the non-equilibrium stress Pi of the completed set,
+    f_i = w_i rho + w_i / (2 c_s^4) Q_i : Pi with Q_i = c_i c_i - c_s^2 I."""
     node = unk.any(dim=1)
     if not bool(node.any()):
         return f_in
@@ -209,18 +236,26 @@ def step_cells(st: State, p: Params, z: torch.Tensor, y: torch.Tensor, x: torch.
     ny = {o: neighbour_index(Y, per[1], o) for o in (-1, 0, 1)}
     nz = {o: neighbour_index(Z, per[2], o) for o in (-1, 0, 1)}
     solid = (st.flags & SOLID) != 0
+    surface = torch.zeros_like(solid)
+    if p.obstacle_walls:          # surface voxels are wall nodes; only the interior is inert
+        surface = surface_voxels(st.flags, per)
+        solid = solid & ~surface
     fl = st.flags[z, y, x]
+    wall_node = surface[z, y, x]
 
-    # 1. pull with halfway bounce-back
-    cols = []
+    # 1. pull with halfway bounce-back (from inert obstacle voxels)
+    cols, from_solid = [], []
     for q in range(27):
         cx, cy, cz = (int(v) for v in C[q])
         sz, sy, sx = nz[-cz][z], ny[-cy][y], nx[-cx][x]
         from_wall = solid[sz, sy, sx]
+        from_solid.append(from_wall)
         cols.append(torch.where(from_wall, st.f[OPP[q], z, y, x], st.f[q, sz, sy, sx]))
     f_in = torch.stack(cols, dim=-1)
-    if any(p.walls):
-        f_in = regularized_wall(f_in, p.walls, (X, Y, Z), x, y, z)
+    if any(p.walls) or p.obstacle_walls:
+        unk = face_unknowns(p.walls, (X, Y, Z), x, y, z)
+        unk |= torch.stack(from_solid, dim=-1) & wall_node[:, None]
+        f_in = regularized_wall(f_in, unk)
 
     # 3. adaptive factor from the lagged velocity field
     if p.adaptive and p.grad_mode == "local":
@@ -237,7 +272,7 @@ def step_cells(st: State, p: Params, z: torch.Tensor, y: torch.Tensor, x: torch.
         f_post = f_post + _forced_shift(rho, u, p.body_force)
 
     # 5. node kinds (selected with where, so the step stays differentiable)
-    is_solid = (fl & SOLID) != 0
+    is_solid = ((fl & SOLID) != 0) & ~wall_node
     is_in = ((fl & INFLOW) != 0) & ~is_solid
     is_ghost = (fl & GHOST) != 0
     u_own = st.u[:, z, y, x].T

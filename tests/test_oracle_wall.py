@@ -2,7 +2,10 @@
 regularized on-node wall of the cited method): second-order convergence of the decay of a
 shear mode between two walls to the Navier-Stokes rate, the exact parabolic curvature of a
 body-forced channel, and the wall-node invariants (mass from the known populations, zero
-momentum, the non-equilibrium stress of the completed set kept)."""
+momentum, the non-equilibrium stress of the completed set kept).  The same wall on the
+surface voxels of obstacles: hand-counted surface voxels, the channel between obstacle
+slabs (the exact curvature, and the same state as the channel between wall faces), and the
+invariants on a voxel with unknown populations from several directions."""
 import math
 
 import numpy as np
@@ -66,7 +69,7 @@ def test_wall_node_invariants():
     W = cmr.equilibrium(torch.ones(1, dtype=torch.float64), torch.zeros(1, 3, dtype=torch.float64))[0]
     f_in = W[None, :] * (1.0 + 0.1 * torch.as_tensor(rng.standard_normal((1, 27))))
     x = torch.tensor([3]); y = torch.tensor([2]); z = torch.tensor([0])
-    out = grid.regularized_wall(f_in, WALLS_Z, (8, 8, 8), x, y, z)
+    out = grid.regularized_wall(f_in, grid.face_unknowns(WALLS_Z, (8, 8, 8), x, y, z))
     cz = cmr.C[:, 2]
     rho = f_in[0, cz == 0].sum() + 2 * f_in[0, cz < 0].sum()
     assert torch.isclose(out[0].sum(), rho, rtol=1e-14)
@@ -76,6 +79,84 @@ def test_wall_node_invariants():
     pi_c = torch.einsum("q,qa,qb->ab", neq, cmr.C, cmr.C)
     pi_o = torch.einsum("q,qa,qb->ab", out[0] - W * rho, cmr.C, cmr.C)
     assert torch.allclose(pi_o, pi_c, atol=1e-15)
-    edge = grid.regularized_wall(f_in, (True, False, False, False, True, False), (8, 8, 8),
-                                 torch.tensor([0]), y, z)
+    edge = grid.regularized_wall(f_in, grid.face_unknowns((True, False, False, False, True, False),
+                                                          (8, 8, 8), torch.tensor([0]), y, z))
     assert torch.allclose(edge[0] @ cmr.C, torch.zeros(3, dtype=torch.float64), atol=1e-15)
+
+
+def test_surface_voxels_of_solid_cubes():
+    """A solid cube of edge e inside a periodic block: its surface voxels are the e^3 - (e-2)^3
+    voxels with a fluid neighbour, the (e-2)^3 others are inert."""
+    for e in (3, 4):
+        fl = np.zeros((10, 10, 10), np.uint8)
+        fl[2:2 + e, 3:3 + e, 4:4 + e] = grid.SOLID
+        surf = grid.surface_voxels(torch.as_tensor(fl), (True, True, True)).numpy()
+        assert surf.sum() == e ** 3 - (e - 2) ** 3
+        assert not surf[3:1 + e, 4:2 + e, 5:3 + e].any()
+        assert not surf[fl == 0].any()
+
+
+def _slab_channel(H, nu, g, steps, obstacles):
+    """Body-forced channel of H + 1 wall-to-wall nodes: between wall faces (z = 0 and z = H),
+    or, on a periodic z axis, between the surfaces (z = 2 and z = H + 2) of an obstacle
+    slab of 6 voxels (z = 0, 1, 2 and H + 2, H + 3, H + 4, joined through the wrap)."""
+    Z = H + 5 if obstacles else H + 1
+    fl = np.zeros((Z, 1, 1), np.uint8)
+    if obstacles:
+        fl[[0, 1, 2, H + 2, H + 3, H + 4]] = grid.SOLID
+    st = grid.init_state(np.ones((Z, 1, 1)), np.zeros((3, Z, 1, 1)), np.zeros((Z, 1, 1)), fl)
+    p = grid.Params(nu=nu, periodic=(True, True, obstacles), adaptive=False,
+                    body_force=(g, 0.0, 0.0), walls=(False,) * 6 if obstacles else WALLS_Z,
+                    obstacle_walls=obstacles)
+    for _ in range(steps):
+        st = grid.step(st, p)
+    return st
+
+
+def test_channel_between_obstacle_slabs_matches_the_wall_face_channel():
+    """With the surface voxels of two obstacle slabs as walls, the nodes from wall to wall
+    carry the state of the channel between two wall faces (the inert voxels behind the
+    surface only feed unknown populations, which the wall replaces), so the profile has the
+    exact curvature -g / nu of the closed form and is zero on the walls."""
+    H, nu, g, steps = 8, 0.2, 1e-5, 200
+    face = _slab_channel(H, nu, g, steps, False)
+    obst = _slab_channel(H, nu, g, steps, True)
+    # obstacle layout: z = 0, 1 inert, z = 2 wall ... z = H + 2 wall, z = H + 3, H + 4 inert
+    sl = slice(2, H + 3)
+    assert torch.allclose(obst.f[:, sl], face.f, atol=1e-15)
+    assert torch.allclose(obst.u[:, sl], face.u, atol=1e-15)
+    inert = [0, 1, H + 3, H + 4]
+    W = cmr.equilibrium(torch.ones(1, dtype=torch.float64), torch.zeros(1, 3, dtype=torch.float64))[0]
+    assert torch.allclose(obst.f[:, inert, 0, 0], W[:, None].expand(27, 4), atol=0)
+    long = _slab_channel(H, nu, g, int(8 * H * H / nu), True)
+    u = long.u[0, sl, 0, 0].numpy()
+    d2 = u[3:-1] - 2 * u[2:-2] + u[1:-3]
+    assert np.allclose(d2, -g / nu, rtol=1e-6)
+    assert abs(u[0]) < 1e-15 and abs(u[-1]) < 1e-15
+
+
+def test_wall_node_with_unknowns_from_several_directions():
+    """The corner voxel of a 2 x 2 x 2 solid block embedded in a larger obstacle: any set of
+    unknown populations gives zero momentum, mass (known + bounce-back completed) /
+    (1 - sum of w over pairs unknown both ways), and the completed set's stress."""
+    rng = np.random.default_rng(3)
+    W = cmr.equilibrium(torch.ones(1, dtype=torch.float64), torch.zeros(1, 3, dtype=torch.float64))[0]
+    f_in = W[None, :] * (1.0 + 0.1 * torch.as_tensor(rng.standard_normal((1, 27))))
+    C = cmr.C
+    # unknown: sources in the octant x - c with c_x >= 0, c_y >= 0, c_z >= 0 (not the rest)
+    unk = ((C[:, 0] >= 0) & (C[:, 1] >= 0) & (C[:, 2] >= 0)).clone()
+    unk[13] = False
+    unk[(C[:, 0] == 1) & (C[:, 1] == -1) & (C[:, 2] == 0)] = True     # and one stray pair
+    unk[(C[:, 0] == -1) & (C[:, 1] == 1) & (C[:, 2] == 0)] = True
+    out = grid.regularized_wall(f_in, unk[None, :])
+    opp = unk[cmr.OPP]
+    both = unk & opp
+    assert both.any() and (unk & ~opp).any()
+    rho = (f_in[0, ~unk].sum() + f_in[0, cmr.OPP][unk & ~opp].sum()) / (1.0 - W[both].sum())
+    assert torch.isclose(out[0].sum(), rho, rtol=1e-14)
+    assert torch.allclose(out[0] @ C, torch.zeros(3, dtype=torch.float64), atol=1e-15)
+    completed = torch.where(unk & ~opp, f_in[0, cmr.OPP], f_in[0])
+    completed = torch.where(both, W * rho, completed)
+    pi_c = torch.einsum("q,qa,qb->ab", completed - W * rho, C, C)
+    pi_o = torch.einsum("q,qa,qb->ab", out[0] - W * rho, C, C)
+    assert torch.allclose(pi_o, pi_c, atol=1e-15)
