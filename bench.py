@@ -230,12 +230,12 @@ def parity_by_variant():
     from paper_1807_02284_gb300 import lbm
     r32 = lambda a: np.asarray(a, dtype=np.float32)
 
-    def single(sc, steps, storage="fp32", grad_mode="lagged", walls=None):
+    def single(sc, steps, storage="fp32", grad_mode="lagged", walls=None, obstacles=False):
         b = sc.blocks[0]
         dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, storage=storage,
                          adaptive=sc.adaptive, c_src=sc.c_src, grad_mode=grad_mode)
-        if walls:
-            dom.set_walls(walls)
+        if walls or obstacles:
+            dom.set_walls(walls or (False,) * 6, obstacles=obstacles)
         dom.set_flags(b.flags)
         dom.init_macro(r32(b.u0), rho=r32(b.rho0), c=r32(b.c0))
         dom.step(steps)
@@ -247,6 +247,7 @@ def parity_by_variant():
                         grad_mode=grad_mode)
         if walls:
             p = dataclasses.replace(p, walls=tuple(walls))
+        p = dataclasses.replace(p, obstacle_walls=obstacles)
         for _ in range(steps):
             st = grid.step(st, p)
         uo = st.u.numpy()
@@ -289,6 +290,9 @@ def parity_by_variant():
     out["plume256_walls"] = {"u_max_abs_err_rel": single(plume, 6, walls=(False,) * 4 + (True, True)),
                              "bound": 1e-5,
                              "case": "24x20x20 plume-shaped scene, floor + lid walls, 6 steps"}
+    out["plume256_regwall"] = {"u_max_abs_err_rel": single(plume, 6, obstacles=True),
+                               "bound": 1e-5,
+                               "case": "24x20x20 plume-shaped scene, sphere surface as walls, 6 steps"}
     ms = synth.multiscale(scale=0.25, nu=2e-3, flow_amp=0.06)
     out["multiscale3"] = {"u_max_abs_err_rel": multi(ms, 2), "bound": 1e-5,
                           "case": "the 3-block scene scaled by 1/4 (32^3, 24^3, 16^3), 2 reference steps"}
@@ -403,6 +407,8 @@ def run_ours(args):
                      grad_mode="local" if args.workload.endswith("_local") else "lagged")
     if args.workload.endswith("_walls"):     # no-slip floor and lid (the second-order wall)
         dom.set_walls((False, False, False, False, True, True))
+    if args.workload.endswith("_regwall"):   # the sphere's surface as the second-order wall
+        dom.set_walls((False,) * 6, obstacles=True)
     for blk in sc.blocks[1:]:
         dom.add_scale_block(blk.origin, blk.h, blk.dims)
     for i, blk in enumerate(sc.blocks):
@@ -785,9 +791,9 @@ def _line_spectra(u, mask_yz, x0, x1):
 
 def run_ringing(args, emit=True):
     """Relaxation comparison on the flow past a sphere at the resolution and viscosity of
-    Fig. 3 (196 x 98 x 98, nu = 1e-4): the same run with fixed high-order relaxation
-    (phi = 1), adaptive relaxation from the lagged velocity gradient, and adaptive relaxation
-    from the node's own strain rate.  Ringing is read from spectra: the power spectrum of the
+    Fig. 3 (196 x 98 x 98, nu = 1e-4, the sphere's surface as regularized walls): the same
+    run with fixed high-order relaxation (phi = 1), adaptive relaxation from the lagged
+    velocity gradient, and adaptive relaxation from the node's own strain rate.  Ringing is read from spectra: the power spectrum of the
     velocity fluctuation along the flow axis on lines outside the jet (distance > 30 from
     its axis, where the flow is smooth and high wavenumbers are artefacts) and inside it
     (distance < 12, the turbulence the relaxation should keep), every 250 steps; a run that
@@ -816,6 +822,7 @@ def run_ringing(args, emit=True):
         dom = lbm.Domain(b.dims, sc.nu, periodic=sc.periodic, adaptive=adaptive,
                          c_src=sc.c_src, stream=stream, grad_mode=grad)
         dom.set_flags(b.flags)
+        dom.set_walls((False,) * 6, obstacles=True)   # the sphere's surface: regularized walls
         dom.init_macro(b.u0.astype(np.float32), rho=b.rho0.astype(np.float32),
                        c=b.c0.astype(np.float32))
         dom.step(args.warmup)
@@ -893,7 +900,8 @@ def _variants(args):
                                   ("farfield256", run_ours, 100, 10),
                                   ("batch64", run_batch, 100, 10),
                                   ("adjoint128", run_adjoint, 200, 0),
-                                  ("ringing196", run_ringing, 3000, 10)):
+                                  ("ringing196", run_ringing, 3000, 10),
+                                  ("plume256_regwall", run_ours, 100, 10)):
         a = copy.copy(args)
         a.workload, a.steps, a.warmup, a.no_cpu_baseline = name, steps, warm, True
         buf = io.StringIO()
@@ -919,7 +927,7 @@ def main():
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
                              "multiscale3", "batch64", "adjoint128", "adjoint64",
                              "plume256_local", "dynamic256", "farfield256", "plume256_walls",
-                             "ringing196"])
+                             "ringing196", "plume256_regwall"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

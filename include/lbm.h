@@ -63,16 +63,22 @@ enum {
                         their inflow velocity (applied to every time level).  Records outside
                         the block or on obstacle voxels / ghost nodes are skipped and
                         reported as LBM_ERR_DIVERGED by the next synchronising call. */
-  LBM_BC_WALLS = 2   /* block 0 only: 6 uint8 (host), non-zero for a no-slip wall on face
-                        x-, x+, y-, y+, z-, z+ (the paper's second-order wall for the ground
-                        and box walls, Sec. 6.1, read as the regularized on-node wall: the
-                        face nodes are wall nodes at rest; populations pulled through the
-                        wall are completed by bounce-back, both of a pair through walls take
-                        the rest equilibrium, and every population is rebuilt from the
-                        equilibrium at (rho, 0) and the non-equilibrium stress of the
-                        completed set before the collision).  Replaces the previous walls.
+  LBM_BC_WALLS = 2   /* block 0 only: 6 or 7 uint8 (host).  Bytes 0..5 non-zero for a no-slip
+                        wall on face x-, x+, y-, y+, z-, z+ (the paper's second-order wall for
+                        the ground and box walls, Sec. 6.1, read as the regularized on-node
+                        wall: the face nodes are wall nodes at rest; populations pulled
+                        through the wall are completed by bounce-back, both of a pair through
+                        walls take the rest equilibrium, and every population is rebuilt from
+                        the equilibrium at (rho, 0) and the non-equilibrium stress of the
+                        completed set before the collision).  Byte 6 (optional) non-zero: the
+                        same wall on the objects, Sec. 6.1 — an obstacle voxel with a
+                        non-obstacle neighbour is a wall node at rest (flag bit 6 instead of
+                        bit 0 in LBM_FIELD_FLAGS), populations pulled from the inner obstacle
+                        voxels are the unknown ones, the inner voxels stay inert; without it
+                        obstacles use halfway bounce-back.  Replaces the previous walls.
                         INVALID_ARG for a wall on a periodic axis; UNSUPPORTED with
-                        far-field blocks. */
+                        far-field blocks, and byte 6 with any refined block (adding a block
+                        to such a domain is UNSUPPORTED too). */
 };
 
 typedef struct {

@@ -446,6 +446,8 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
   if (!origin || !dims || !block_id) return dom->fail(LBM_ERR_INVALID_ARG, "null argument");
   if (!(h > 0.0) || !std::isfinite(h)) return dom->fail(LBM_ERR_INVALID_ARG, "h must be positive");
   if (std::fabs(h - 1.0) < 1e-12) return dom->fail(LBM_ERR_INVALID_ARG, "h = 1 is the reference scale");
+  if (dom->walls & WALLS_OBSTACLES)
+    return dom->fail(LBM_ERR_UNSUPPORTED, "obstacle walls need a single-block domain");
   if (dom->desc.storage != LBM_FP32)
     return dom->fail(LBM_ERR_UNSUPPORTED, "scale blocks need FP32 storage");
   if (dom->tape)

@@ -63,7 +63,7 @@ __global__ void k_init(BlockView v, const float* rho, const float* u, const floa
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
        idx += (size_t)gridDim.x * blockDim.x) {
     T* dout = static_cast<T*>(v.d_out);
-    const bool solid = v.flags[idx] & F_SOLID;
+    const bool solid = v.flags[idx] & (F_SOLID | F_OBST_WALL);   // obstacle voxels start at rest
     const float r = (rho && !solid) ? rho[idx] : 1.0f;
     const float ux = solid ? 0.f : u[idx], uy = solid ? 0.f : u[N + idx],
                 uz = solid ? 0.f : u[2 * N + idx];
@@ -111,6 +111,38 @@ __global__ void k_mark_walls(uint8_t* flags, int nx, int ny, int nz, int walls) 
 cudaError_t launch_mark_walls(uint8_t* flags, int nx, int ny, int nz, int walls, cudaStream_t s) {
   const size_t g = ((size_t)nx * ny * nz + 255) / 256;
   k_mark_walls<<<(int)(g < 8192 ? g : 8192), 256, 0, s>>>(flags, nx, ny, nz, walls);
+  return cudaGetLastError();
+}
+
+// Obstacle surfaces as walls: an obstacle voxel (F_SOLID or F_OBST_WALL) with a non-obstacle
+// pull source is a surface voxel; with `on` it becomes an active wall node (F_OBST_WALL, not
+// F_SOLID), otherwise every obstacle voxel is F_SOLID again.  The obstacle predicate is the
+// same before and after, so the update runs in place.
+__global__ void k_obstacle_walls(uint8_t* flags, int nx, int ny, int nz, int px, int py, int pz,
+                                 int on) {
+  const size_t N = (size_t)nx * ny * nz;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const uint8_t f = flags[idx];
+    if (!(f & (F_SOLID | F_OBST_WALL))) continue;
+    const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((size_t)nx * ny));
+    bool surface = false;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int sx = nbr(x, dx, nx, px), sy = nbr(y, dy, ny, py), sz = nbr(z, dz, nz, pz);
+          surface |= !(flags[((size_t)sz * ny + sy) * nx + sx] & (F_SOLID | F_OBST_WALL));
+        }
+    const uint8_t base = f & (uint8_t)~(F_SOLID | F_OBST_WALL);
+    flags[idx] = (on && surface) ? (uint8_t)(base | F_OBST_WALL) : (uint8_t)(base | F_SOLID);
+  }
+}
+
+cudaError_t launch_obstacle_walls(uint8_t* flags, int nx, int ny, int nz, const int per[3], int on,
+                                  cudaStream_t s) {
+  const size_t N = (size_t)nx * ny * nz;
+  const int grid = (int)((N + 255) / 256 < 65535 ? (N + 255) / 256 : 65535);
+  k_obstacle_walls<<<grid, 256, 0, s>>>(flags, nx, ny, nz, per[0], per[1], per[2], on);
   return cudaGetLastError();
 }
 
@@ -164,7 +196,7 @@ __global__ void k_inflow_records(const InflowRec* rec, int n, uint8_t* flags, fl
     return;
   }
   const size_t idx = ((size_t)r.z * ny + r.y) * nx + r.x;
-  if (flags[idx] & (F_SOLID | F_GHOST)) {
+  if (flags[idx] & (F_SOLID | F_OBST_WALL | F_GHOST)) {
     atomicOr(err, 4);  // obstacle voxels and ghost nodes cannot become inflow nodes
     return;
   }

@@ -119,14 +119,30 @@ __device__ __forceinline__ void flag_error(int* err, bool bad) {
   if (m && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(err, 1);
 }
 
-// No-slip wall node on a flat face of the block (the second-order wall of Sec. 6.1, read as
-// the regularized on-node wall): populations pulled through a wall face are completed by
-// bounce-back from their opposite (wall at rest); where both of a pair come through walls
-// (edges, corners) they take the rest equilibrium; rho is the mass of the completed set and
-// every population is rebuilt as w_i rho + (w_i / (2 c_s^4)) Q_i : Pi from the
-// non-equilibrium stress Pi of the completed set.  On shifted populations d = f - w.
+// Bits k of the populations of a node whose pull source is an inner obstacle voxel.
+template <typename IT, int K = 0>
+__device__ __forceinline__ unsigned solid_sources(const uint8_t* __restrict__ flags,
+                                                  const Nbr<IT>& n) {
+  if constexpr (K < 27) {
+    unsigned b = 0u;
+    if constexpr (K != 13) b = (__ldg(flags + pull_src<K>(n)) & F_SOLID) ? (1u << K) : 0u;
+    return b | solid_sources<IT, K + 1>(flags, n);
+  } else {
+    return 0u;
+  }
+}
+
+// No-slip wall node (the second-order wall of Sec. 6.1, read as the regularized on-node
+// wall) on a flat face of the block or, with obstacle walls, on an obstacle's surface voxel:
+// populations pulled from beyond the wall (through a wall face, or from an inner obstacle
+// voxel) are completed by bounce-back from their opposite (wall at rest); where both of a
+// pair come from beyond the wall (edges, corners) they take the rest equilibrium; rho is the
+// mass of the completed set and every population is rebuilt as
+// w_i rho + (w_i / (2 c_s^4)) Q_i : Pi from the non-equilibrium stress Pi of the completed
+// set.  On shifted populations d = f - w.
+template <typename IT>
 __device__ __forceinline__ void wall_regularize(float (&d)[27], const BlockView& v, int x, int y,
-                                                int z) {
+                                                int z, uint8_t fl, const Nbr<IT>& n) {
   const bool lo[3] = {(v.walls & 1) && x == 0, (v.walls & 4) && y == 0, (v.walls & 16) && z == 0};
   const bool hi[3] = {(v.walls & 2) && x == v.nx - 1, (v.walls & 8) && y == v.ny - 1,
                       (v.walls & 32) && z == v.nz - 1};
@@ -139,6 +155,7 @@ __device__ __forceinline__ void wall_regularize(float (&d)[27], const BlockView&
     for (int a = 0; a < 3; ++a) u |= (lo[a] && c[a] == 1) || (hi[a] && c[a] == -1);
     if (u) unk |= 1u << k;
   }
+  if (fl & F_OBST_WALL) unk |= solid_sources<IT>(v.flags, n);
   float s = 0.0f, wb = 0.0f;
 #pragma unroll
   for (int k = 0; k < 27; ++k) {
@@ -208,9 +225,11 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
 
   // all independent loads first: the pull and the lagged velocity neighbourhood
   pull_all<T, IT>(d, din, N, n);
-  if (fl & F_NEAR_SOLID) bounce_back<T, IT>(d, din, N, v.flags, n, idx);
+  // an obstacle wall node completes what comes from inside the obstacle itself
+  if ((fl & F_NEAR_SOLID) && !(WALLS && (fl & F_OBST_WALL)))
+    bounce_back<T, IT>(d, din, N, v.flags, n, idx);
   if constexpr (WALLS) {
-    if (fl & F_WALL) wall_regularize(d, v, x, y, z);
+    if (fl & (F_WALL | F_OBST_WALL)) wall_regularize<IT>(d, v, x, y, z, fl, n);
   }
   const float g_lag = (v.rp.adaptive && !v.rp.local) ? grad_norm<IT>(v.u_in, N, n) : 0.0f;
 

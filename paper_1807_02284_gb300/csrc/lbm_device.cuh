@@ -29,10 +29,16 @@
 
 namespace lbm {
 
-// Cell flags (bits 0..3 are user-visible, bit 4 is derived by the library).
+// Cell flags (bits 0..3 are user-visible, bits 4..6 are derived by the library).  With
+// obstacle walls on, an obstacle's surface voxels carry F_OBST_WALL instead of F_SOLID (they
+// are active wall nodes at rest) and only its inner voxels keep F_SOLID.
 enum : uint8_t {
-  F_SOLID = 1, F_INFLOW = 2, F_SCALAR_SRC = 4, F_GHOST = 8, F_NEAR_SOLID = 16, F_WALL = 32
+  F_SOLID = 1, F_INFLOW = 2, F_SCALAR_SRC = 4, F_GHOST = 8, F_NEAR_SOLID = 16, F_WALL = 32,
+  F_OBST_WALL = 64
 };
+
+// Bit of BlockView::walls (above the six face bits) for obstacle surfaces as walls.
+constexpr int WALLS_OBSTACLES = 64;
 
 __host__ __device__ constexpr int cxk(int k) { return k % 3 - 1; }
 __host__ __device__ constexpr int cyk(int k) { return (k / 3) % 3 - 1; }

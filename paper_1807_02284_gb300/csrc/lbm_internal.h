@@ -25,7 +25,8 @@ struct BlockView {
   RelaxParams rp;
   float c_src;
   int* err;            // device error word (bit 0: non-finite or non-positive density)
-  int walls = 0;       // no-slip wall faces, bits x-, x+, y-, y+, z-, z+ (nodes flagged F_WALL)
+  int walls = 0;       // no-slip wall faces, bits x-, x+, y-, y+, z-, z+ (nodes flagged F_WALL),
+                       // and WALLS_OBSTACLES: obstacle surfaces are walls (F_OBST_WALL)
   // temporal alignment fused into the last sub-step of a refined block (Sec. 4.2.4): the
   // stored state is L0 f(t_n) + L1 f(t_n+(l-1)h) + L2 f(t_n+lh), with f(t_n+(l-1)h) = d_in
   const void* f_al0 = nullptr;   // populations at t_n
@@ -89,6 +90,8 @@ cudaError_t launch_init(const BlockView& v, int storage, const float* rho, const
 cudaError_t launch_merge_user_flags(uint8_t* flags, const uint8_t* user, size_t N,
                                     cudaStream_t s);
 cudaError_t launch_mark_walls(uint8_t* flags, int nx, int ny, int nz, int walls, cudaStream_t s);
+cudaError_t launch_obstacle_walls(uint8_t* flags, int nx, int ny, int nz, const int per[3], int on,
+                                  cudaStream_t s);
 cudaError_t launch_near_solid(uint8_t* flags, int nx, int ny, int nz, const int per[3],
                               cudaStream_t s);
 cudaError_t launch_inflow_records(const void* rec, int n, uint8_t* flags, float* const* u_levels,

@@ -306,7 +306,9 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
     if (e == cudaSuccess) {
       int per[3] = {0, 0, 0};
       if (block_id == 0) for (int a = 0; a < 3; ++a) per[a] = dom->desc.periodic[a];
-      e = launch_near_solid(B.flags, B.nx, B.ny, B.nz, per, dom->stream);
+      if (block_id == 0 && (dom->walls & WALLS_OBSTACLES))   // the new obstacles' surfaces
+        e = launch_obstacle_walls(B.flags, B.nx, B.ny, B.nz, per, 1, dom->stream);
+      if (e == cudaSuccess) e = launch_near_solid(B.flags, B.nx, B.ny, B.nz, per, dom->stream);
     }
     // a block surrounded by a far-field block keeps its outer layer as scale boundary,
     // except where the new flags put obstacles or inflow nodes
@@ -328,10 +330,22 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
         if (dom->desc.periodic[f / 2]) return dom->fail(LBM_ERR_INVALID_ARG, "a wall on a periodic axis");
         walls |= 1 << f;
       }
+    if (nbytes >= 7 && m[6]) {
+      if (dom->blocks.size() > 1)
+        return dom->fail(LBM_ERR_UNSUPPORTED, "obstacle walls need a single-block domain");
+      walls |= WALLS_OBSTACLES;
+    }
     for (size_t i = 1; i < dom->blocks.size(); ++i)
       if (dom->blocks[i].far && walls)
         return dom->fail(LBM_ERR_UNSUPPORTED, "walls and far-field blocks exclude each other");
-    const cudaError_t e = launch_mark_walls(B.flags, B.nx, B.ny, B.nz, walls, dom->stream);
+    int per[3];
+    for (int a = 0; a < 3; ++a) per[a] = dom->desc.periodic[a];
+    cudaError_t e = launch_mark_walls(B.flags, B.nx, B.ny, B.nz, walls, dom->stream);
+    if (e == cudaSuccess && ((walls | dom->walls) & WALLS_OBSTACLES)) {
+      e = launch_obstacle_walls(B.flags, B.nx, B.ny, B.nz, per, (walls & WALLS_OBSTACLES) ? 1 : 0,
+                                dom->stream);
+      if (e == cudaSuccess) e = launch_near_solid(B.flags, B.nx, B.ny, B.nz, per, dom->stream);
+    }
     if (e != cudaSuccess) return dom->cuda_fail(e, "wall flags");
     dom->walls = walls;
     dom->invalidate_graphs();

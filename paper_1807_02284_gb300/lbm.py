@@ -265,10 +265,13 @@ class Domain:
         p, dev = _ptr(flags)
         self.check(self.lib.lbm_set_boundary(self.handle, block, LBM_BC_FLAGS, p, _nbytes(flags), dev))
 
-    def set_walls(self, faces):
-        """No-slip wall faces of block 0: six booleans (x-, x+, y-, y+, z-, z+)."""
-        m = np.ascontiguousarray([1 if f else 0 for f in faces], dtype=np.uint8)
-        self.check(self.lib.lbm_set_boundary(self.handle, 0, LBM_BC_WALLS, m.ctypes.data, 6, 0))
+    def set_walls(self, faces, obstacles=False):
+        """No-slip wall faces of block 0: six booleans (x-, x+, y-, y+, z-, z+); with
+        ``obstacles`` the surface voxels of the obstacles are walls too (single-block
+        domains)."""
+        m = np.ascontiguousarray([1 if f else 0 for f in faces] + [1 if obstacles else 0],
+                                 dtype=np.uint8)
+        self.check(self.lib.lbm_set_boundary(self.handle, 0, LBM_BC_WALLS, m.ctypes.data, 7, 0))
 
     def set_inflow(self, records, block=0):
         if isinstance(records, np.ndarray):
