@@ -158,7 +158,7 @@ def surface_voxels(flags: torch.Tensor, periodic) -> torch.Tensor:
     return solid & open_nb
 
 
-def regularized_wall(f_in: torch.Tensor, unk: torch.Tensor) -> torch.Tensor:
+def regularized_wall(f_in: torch.Tensor, unk: torch.Tensor, node=None) -> torch.Tensor:
     """Second-order no-slip wall (Sec. 6.1, read as the regularized on-node wall of the
     cited method), applied to the pulled populations f_in (K, 27) of the listed nodes; unk
     (K, 27) marks the populations whose pull source lies beyond the wall (outside a wall face
@@ -166,10 +166,13 @@ def regularized_wall(f_in: torch.Tensor, unk: torch.Tensor) -> torch.Tensor:
     population is completed by bounce-back from its opposite (the wall is at rest); where the
     opposite is unknown too (edges, corners) both take the rest equilibrium w_i rho.  rho is
     the mass of the completed set (for one wall: sum_{c.n = 0} f + 2 sum_{c.n < 0} f).  All
-    27 populations of a node with an unknown one are then rebuilt from the equilibrium at
-    (rho, u = 0) and the non-equilibrium stress Pi of the completed set,
-    f_i = w_i rho + w_i / (2 c_s^4) Q_i : Pi with Q_i = c_i c_i - c_s^2 I."""
-    node = unk.any(dim=1)
+    27 populations of a wall node (``node`` (K,), by default the nodes with an unknown
+    population; a surface voxel is a wall node even when nothing reaches it from inside the
+    obstacle) are then rebuilt from the equilibrium at (rho, u = 0) and the non-equilibrium
+    stress Pi of the completed set, f_i = w_i rho + w_i / (2 c_s^4) Q_i : Pi with
+    Q_i = c_i c_i - c_s^2 I."""
+    if node is None:
+        node = unk.any(dim=1)
     if not bool(node.any()):
         return f_in
     W = cmr.equilibrium(torch.ones(1, dtype=DT), torch.zeros(1, 3, dtype=DT))[0]   # weights
@@ -254,8 +257,9 @@ def step_cells(st: State, p: Params, z: torch.Tensor, y: torch.Tensor, x: torch.
     f_in = torch.stack(cols, dim=-1)
     if any(p.walls) or p.obstacle_walls:
         unk = face_unknowns(p.walls, (X, Y, Z), x, y, z)
+        node = unk.any(dim=1) | wall_node
         unk |= torch.stack(from_solid, dim=-1) & wall_node[:, None]
-        f_in = regularized_wall(f_in, unk)
+        f_in = regularized_wall(f_in, unk, node)
 
     # 3. adaptive factor from the lagged velocity field
     if p.adaptive and p.grad_mode == "local":

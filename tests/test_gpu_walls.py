@@ -62,12 +62,15 @@ def test_wall_argument_checks(lib):
 @pytest.mark.parametrize("faces", [(False,) * 6, (False, False, False, False, True, False)])
 def test_obstacle_surface_walls_match_oracle(lib, faces):
     """Obstacle surfaces as regularized on-node walls (Sec. 6.1 wall on objects): two spheres
-    (one touching the floor when the floor is a wall), an inflow disk, open faces."""
+    (one touching the floor when the floor is a wall; the r = 3 one has surface voxels with
+    no inner neighbour), a plate one voxel thick, an inflow disk, open faces, low viscosity."""
     from paper_1807_02284_gb300 import lbm
     sc = synth.random_scene(dims=(28, 22, 18), seed=53, periodic=(False, False, False),
-                            spheres=[(14.0, 11.0, 9.0, 3.5), (21.0, 7.0, 2.0, 2.5)],
-                            inflow=(11, 9, 3.0, 0.07), nu=0.005)
+                            spheres=[(14.0, 11.0, 9.0, 3.0), (21.0, 7.0, 2.0, 2.5)],
+                            inflow=(11, 9, 3.0, 0.07), nu=1e-4)
     b = sc.blocks[0]
+    b.flags[6:12, 12:18, 23] |= synth.SOLID          # the plate (no inner voxels at all)
+    b.rho0[b.flags & synth.SOLID != 0] = 1.0
     dom = gpu_domain(sc)
     dom.set_walls(faces, obstacles=True)
     dom.init_macro(np.asarray(b.u0, np.float32), rho=np.asarray(b.rho0, np.float32),

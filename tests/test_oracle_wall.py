@@ -160,3 +160,23 @@ def test_wall_node_with_unknowns_from_several_directions():
     pi_c = torch.einsum("q,qa,qb->ab", completed - W * rho, C, C)
     pi_o = torch.einsum("q,qa,qb->ab", out[0] - W * rho, C, C)
     assert torch.allclose(pi_o, pi_c, atol=1e-15)
+
+
+def test_plate_one_voxel_thick_is_a_wall_at_rest():
+    """A plate one voxel thick has no inner voxels, so nothing reaches its voxels from inside
+    the obstacle; they are still wall nodes at rest (zero velocity to rounding, every step)
+    while the flow around the plate moves."""
+    Z, Y, X = 10, 8, 12
+    fl = np.zeros((Z, Y, X), np.uint8)
+    fl[2:8, 2:6, 6] = grid.SOLID                      # a plate normal to x
+    rng = np.random.default_rng(5)
+    u0 = np.zeros((3, Z, Y, X))
+    u0[0] = 0.05 + 0.01 * rng.standard_normal((Z, Y, X))
+    st = grid.init_state(np.ones((Z, Y, X)), u0, np.zeros((Z, Y, X)), fl)
+    assert grid.surface_voxels(st.flags, (True, True, True)).sum() == 24
+    p = grid.Params(nu=0.02, periodic=(True, True, True), obstacle_walls=True)
+    for _ in range(4):
+        st = grid.step(st, p)
+        plate = st.u[:, 2:8, 2:6, 6]
+        assert float(plate.abs().max()) < 1e-15
+    assert float(st.u[0].abs().max()) > 0.01
