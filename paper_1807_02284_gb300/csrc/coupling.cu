@@ -110,7 +110,9 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
   const float* __restrict__ clo = MODE == 1 ? a.c_hi : a.c_lo;
   const float th = a.theta;
   // every (entry, population) pair of this thread has entry d = lane: corners read once, and
-  // the unrolled pairs issue all their loads before the first sum is needed
+  // the unrolled pairs issue all their loads before the first sum is needed.  A corner of
+  // weight 0 (a fraction of 0 on an axis, where the grids line up, or an obstacle corner)
+  // is not loaded: its term would add exactly 0.
   static_assert(MAP_D == 32 && (MAP_D * 28) % MAP_THREADS == 0, "gather layout");
   constexpr int PAIRS = MAP_D * 28 / MAP_THREADS;
   const int d = t & 31;
@@ -129,20 +131,24 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
         const T* ph = hi + (uint32_t)k * sN;
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-          v = fmaf(w[c], fmaf(th, load_pop(ph + sc[c]) - load_pop(pl + sc[c]), load_pop(pl + sc[c])), v);
+          if (w[c] != 0.0f)
+            v = fmaf(w[c], fmaf(th, load_pop(ph + sc[c]) - load_pop(pl + sc[c]), load_pop(pl + sc[c])), v);
       } else {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) v = fmaf(w[c], load_pop(pl + sc[c]), v);
+        for (int c = 0; c < 8; ++c)
+          if (w[c] != 0.0f) v = fmaf(w[c], load_pop(pl + sc[c]), v);
       }
     } else if (MODE == 2) {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        v = fmaf(w[c] * (1.0f - th), __ldg(clo + sc[c]), v);
-        v = fmaf(w[c] * th, __ldg(a.c_hi + sc[c]), v);
-      }
+      for (int c = 0; c < 8; ++c)
+        if (w[c] != 0.0f) {
+          v = fmaf(w[c] * (1.0f - th), __ldg(clo + sc[c]), v);
+          v = fmaf(w[c] * th, __ldg(a.c_hi + sc[c]), v);
+        }
     } else {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) v = fmaf(w[c], __ldg(clo + sc[c]), v);
+      for (int c = 0; c < 8; ++c)
+        if (w[c] != 0.0f) v = fmaf(w[c], __ldg(clo + sc[c]), v);
     }
     vals[i] = v;
   }

@@ -253,12 +253,15 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
   if constexpr (ALIGN) {
     // three-point Lagrange interpolation to t_n + dt_0 of this node's states at t_n, at
     // t_n + (l-1)h (the sub-step's input) and at t_n + l h (just computed)
+    // (a far-field block's linear alignment has al0 = 0: its t_n level is not read)
     const T* __restrict__ f0 = static_cast<const T*>(v.f_al0);
+    const bool use0 = v.al0 != 0.0f;
     float s = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int k = 0; k < 27; ++k) {
       const IT i = (IT)k * N + idx;
-      const float val = fmaf(v.al0, load_pop(f0 + i), fmaf(v.al1, load_pop(din + i), v.al2 * d[k]));
+      const float rest = fmaf(v.al1, load_pop(din + i), v.al2 * d[k]);
+      const float val = use0 ? fmaf(v.al0, load_pop(f0 + i), rest) : rest;
       d[k] = val;
       s += val;
       if (cxk(k) > 0) jx += val; else if (cxk(k) < 0) jx -= val;
@@ -267,7 +270,8 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
     }
     const float ia = 1.0f / (1.0f + s);
     const float cnew = src ? v.c_src : scalar_value(sc);
-    const float cal = fmaf(v.al0, v.c_al0[idx], fmaf(v.al1, v.c_in[idx], v.al2 * cnew));
+    const float crest = fmaf(v.al1, v.c_in[idx], v.al2 * cnew);
+    const float cal = use0 ? fmaf(v.al0, v.c_al0[idx], crest) : crest;
 #pragma unroll
     for (int k = 0; k < 27; ++k) store_pop(dout + ((IT)k * N + idx), d[k]);
     __stcs(v.u_out + idx, jx * ia);
