@@ -72,7 +72,9 @@ __device__ __forceinline__ float load_pop(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float load_pop(const __half* p) {
   return __half2float(__ldg(reinterpret_cast<const __half*>(p)));
 }
-__device__ __forceinline__ void store_pop(float* p, float v) { __stcs(p, v); }
+// FP32 populations: plain stores (measured 0.4 % faster than streaming stores on the 256^3
+// collide-stream; evict-first loads were 5 % slower)
+__device__ __forceinline__ void store_pop(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store_pop(__half* p, float v) {
   __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
 }

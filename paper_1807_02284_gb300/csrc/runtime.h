@@ -80,6 +80,11 @@ struct lbm_domain {
   long long steps = 0;
   lbm::TapeState* tape = nullptr;
   lbm::GraphCache* graphs = nullptr;
+  // launch shapes already timed, by block size class (x extent: < 64, < 128, < 256, more;
+  // nodes: < 2^20, < 2^23, more): a block of the same class (a rebuilt dynamic scale)
+  // reuses the choice
+  struct TunedShape { int nx_class, n_class, bx, by, minb; };
+  std::vector<TunedShape> tuned_shapes;
   void* batch_plan = nullptr;           // cached plans of lbm_step_batch (batch.cu)
   cudaStream_t aux_stream = nullptr;    // second stream for concurrent mapping launches
   std::vector<cudaEvent_t> events;      // fork / join events (timing disabled)

@@ -63,6 +63,15 @@ lbm_status lbm_domain::autotune_tiles(int b) {
   if (B.tuned) return LBM_OK;
   B.tuned = true;
   if (B.N < (size_t)1 << 18 || B.lv.size() < 2) return LBM_OK;
+  const int nx_class = B.nx >= 256 ? 3 : B.nx >= 128 ? 2 : B.nx >= 64 ? 1 : 0;
+  const int n_class = B.N < ((size_t)1 << 20) ? 0 : B.N < ((size_t)1 << 23) ? 1 : 2;
+  for (const TunedShape& t : tuned_shapes)
+    if (t.nx_class == nx_class && t.n_class == n_class) {
+      B.bx = t.bx;
+      B.by = t.by;
+      B.minb = t.minb;
+      return LBM_OK;
+    }
   const int cand[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {128, 1}};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
@@ -92,6 +101,7 @@ lbm_status lbm_domain::autotune_tiles(int b) {
   B.bx = bx;
   B.by = by;
   B.minb = minb;
+  tuned_shapes.push_back({nx_class, n_class, bx, by, minb});
   return LBM_OK;
 }
 
