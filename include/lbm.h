@@ -276,6 +276,18 @@ lbm_status lbm_write_field(lbm_domain* dom, int32_t block_id, int32_t field, int
    word is set. */
 lbm_status lbm_reduce(lbm_domain* dom, int32_t block_id, double out[5]);
 
+/* n >= 1 reference steps (as lbm_step) followed by the lbm_reduce diagnostics of block 0's
+   new state, in one call.  On a single-block domain with 27 N < 2^32 the last step's kernel
+   sums the moments of the state it stores while storing it (collision conserves rho and j,
+   so a fluid node's are those of its pulled populations; per CTA in FP32 within a warp and
+   FP64 across warps, then a fixed-order FP64 sum): no second pass over the populations.
+   The values agree with lbm_reduce of the same state to FP32 rounding of the per-node terms
+   (with FP16-shifted storage they are those of the FP32 state before it is rounded for
+   storage); the stored state is the one lbm_step writes.  Other domains take the steps and
+   then lbm_reduce of block 0.  out is a host array of 5 doubles (the lbm_reduce layout).
+   Synchronises; INVALID_ARG for n < 1 or a null out; DIVERGED as lbm_step / lbm_reduce. */
+lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]);
+
 /* lbm_reduce of block `block_id` of each of n domains (no counterpart in the paper: the
    read-back of a batch), with every reduction queued on its domain's stream before the
    call waits for any.  out is a host array of 5 n doubles, domain i's five values at

@@ -70,6 +70,28 @@ __global__ void __launch_bounds__(192) k_reduce_final(const double* partials, in
   if (lane == 0) out[v] = s;
 }
 
+// Six columns of n partial sums (value-major): one CTA per column, thread t sums entries
+// t, t + 1024, ... in order, then a fixed tree over the threads.
+__global__ void __launch_bounds__(1024) k_reduce_columns(const double* partials, size_t n,
+                                                         double* out) {
+  __shared__ double sh[1024];
+  const double* col = partials + blockIdx.x * n;
+  double s = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += 1024) s += col[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_reduce_columns(const double* partials, size_t n, double* out, cudaStream_t s) {
+  k_reduce_columns<<<6, 1024, 0, s>>>(partials, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
                           double* partials, double* out, cudaStream_t s) {
   const size_t want = (N + REDUCE_THREADS - 1) / REDUCE_THREADS;

@@ -187,14 +187,23 @@ __device__ __forceinline__ void wall_regularize(float (&d)[27], const BlockView&
   }
 }
 
+// Moments of the state a node stores, for the diagnostics fused into the step (the same
+// quantities lbm_reduce sums: the node counts, rho - 1, j).
+struct NodeMoments {
+  float count = 0.f, drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+};
+
 // One node of one block: pull (with bounce-back and face handling), macroscopic moments,
 // adaptive rates from the lagged velocity, CMR collision, store of f~, u and the scalar.
 // Scale-boundary (ghost) nodes of refined blocks are not written: their next values come
 // from the coarse-to-fine mapping, which can therefore run concurrently with this update.
 // ALIGN: last sub-step of a refined block, storing the temporal alignment (see BlockView).
 // WALLS: the block has no-slip wall faces (an instance without them carries no wall code).
-template <typename T, typename IT, bool ALIGN = false, bool WALLS = false>
-__device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, int z) {
+// RED: also return the moments of the stored state in *nm (obstacle voxels and ghost nodes
+// count 0; collision conserves rho and j, so a fluid node's are those of its pulled set).
+template <typename T, typename IT, bool ALIGN = false, bool WALLS = false, bool RED = false>
+__device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, int z,
+                                            NodeMoments* nm = nullptr) {
   const IT N = (IT)v.N;
   const T* __restrict__ din = static_cast<const T*>(v.d_in);
   T* __restrict__ dout = static_cast<T*>(v.d_out);
@@ -213,6 +222,7 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
     } else {  // Dirichlet inflow: equilibrium at rho = 1 and the stored inflow velocity
       ux = v.u_in[idx]; uy = v.u_in[N + idx]; uz = v.u_in[2 * N + idx];
       equilibrium(d, 1.0f, ux, uy, uz);
+      if constexpr (RED) { nm->count = 1.f; nm->jx = ux; nm->jy = uy; nm->jz = uz; }
       cval = (fl & F_SCALAR_SRC) ? v.c_src
                                  : scalar_value(scalar_corners<IT>(v, x, y, z, ux, uy, uz));
     }
@@ -269,6 +279,7 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
       if (czk(k) > 0) jz += val; else if (czk(k) < 0) jz -= val;
     }
     const float ia = 1.0f / (1.0f + s);
+    if constexpr (RED) { nm->count = 1.f; nm->drho = s; nm->jx = jx; nm->jy = jy; nm->jz = jz; }
     const float cnew = src ? v.c_src : scalar_value(sc);
     const float crest = fmaf(v.al1, v.c_in[idx], v.al2 * cnew);
     const float cal = use0 ? fmaf(v.al0, v.c_al0[idx], crest) : crest;
@@ -285,6 +296,10 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
     __stcs(v.u_out + (N + idx), uy);
     __stcs(v.u_out + (2 * N + idx), uz);
     __stcs(v.c_out + idx, src ? v.c_src : scalar_value(sc));
+    if constexpr (RED) {
+      const float rho = 1.0f + drho;
+      nm->count = 1.f; nm->drho = drho; nm->jx = ux * rho; nm->jy = uy * rho; nm->jz = uz * rho;
+    }
   }
 }
 

@@ -114,6 +114,16 @@ constexpr int REDUCE_CTAS = 608;   // 4 CTAs on each of 152 SMs
 constexpr int REDUCE_THREADS = 256;
 cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
                           double* partials, double* out, cudaStream_t s);
+// 27 N < 2^32: every array index of the block fits 32 bits
+bool fits_32bit_index(size_t N);
+// the six column sums of `n` value-major partials (partials[value * n + i])
+cudaError_t launch_reduce_columns(const double* partials, size_t n, double* out, cudaStream_t s);
+// one collide-stream step of a block (32-bit indexing) that also leaves the diagnostics of
+// the stored state in `out` (same six doubles as launch_reduce); `partials` holds
+// 6 * step_reduce_ctas(v, bx, by) doubles
+size_t step_reduce_ctas(const BlockView& v, int bx, int by);
+cudaError_t launch_step_reduce(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
+                               int minb, double* partials, double* out);
 
 // ---- coupling.cu
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s);

@@ -68,6 +68,8 @@ struct lbm_domain {
   int* d_err = nullptr;
   int* h_err = nullptr;                 // pinned
   double* d_partials = nullptr;         // reduction scratch: REDUCE_CTAS * 6 doubles
+  double* d_step_partials = nullptr;    // per-CTA partials of lbm_step_reduce (6 per CTA)
+  size_t step_partials_n = 0;           // CTAs d_step_partials has room for
   double* d_red = nullptr;
   double* h_red = nullptr;              // pinned
   void* staging_buf = nullptr;

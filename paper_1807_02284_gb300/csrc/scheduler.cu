@@ -299,3 +299,51 @@ lbm_status lbm_domain::advance(int n) {
   }
   return advance_direct(n - done);
 }
+
+// lbm_step_reduce: n reference steps whose last one (on a single-block domain with 32-bit
+// indexing) also sums the diagnostics of the state it stores, so that reading mass, momentum
+// and energy back after a step costs no second pass over the populations.  Other domains
+// take the n steps and lbm_reduce of block 0.
+lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (n < 1) return dom->fail(LBM_ERR_INVALID_ARG, "lbm_step_reduce needs at least one step");
+  if (!out) return dom->fail(LBM_ERR_INVALID_ARG, "null output");
+  if (*dom->h_err & 1) return dom->fail(LBM_ERR_DIVERGED, "divergence recorded by an earlier step");
+  Block& B = dom->blocks[0];
+  if (dom->blocks.size() > 1 || !fits_32bit_index(B.N)) {
+    lbm_status st = dom->advance(n);
+    if (st != LBM_OK) return st;
+    return lbm_reduce(dom, 0, out);
+  }
+  lbm_status st = dom->advance(n - 1);
+  if (st == LBM_OK) st = dom->autotune_tiles(0);
+  if (st == LBM_OK) st = tape_before_step(dom);
+  if (st != LBM_OK) return st;
+  const int nxt = B.cur ^ 1;
+  const BlockView v = dom->view(0, B.cur, nxt);
+  const size_t ctas = step_reduce_ctas(v, B.bx, B.by);
+  if (ctas > dom->step_partials_n) {
+    if (dom->d_step_partials) dom->dev_free(dom->d_step_partials);
+    dom->step_partials_n = 0;
+    dom->d_step_partials = static_cast<double*>(dom->dev_alloc(ctas * 6 * sizeof(double)));
+    if (!dom->d_step_partials) return dom->fail(LBM_ERR_OOM, "step-reduce partials");
+    dom->step_partials_n = ctas;
+  }
+  cudaError_t e = launch_step_reduce(v, dom->desc.storage, B.bx, B.by, dom->stream, B.minb,
+                                     dom->d_step_partials, dom->d_red);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");
+  B.cur = nxt;
+  ++dom->steps;
+  e = cudaMemcpyAsync(dom->h_red, dom->d_red, 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                      dom->stream);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "reduce read-back");
+  st = dom->sync_and_check();
+  const double* r = dom->h_red;
+  out[0] = r[0] + r[1];
+  out[1] = r[2];
+  out[2] = r[3];
+  out[3] = r[4];
+  out[4] = r[5];
+  return st;
+}

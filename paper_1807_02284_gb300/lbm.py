@@ -82,6 +82,7 @@ _SIGNATURES = {
     "lbm_read_field": (_I, [_P, _I, _I, _I, _P, C.c_size_t, _I]),
     "lbm_write_field": (_I, [_P, _I, _I, _I, _P, C.c_size_t, _I]),
     "lbm_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
+    "lbm_step_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
     "lbm_get_block_info": (_I, [_P, _I, C.POINTER(lbm_block_info)]),
     "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
     "lbm_reduce_batch": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
@@ -324,6 +325,13 @@ class Domain:
     def reduce(self, block=0) -> np.ndarray:
         out = (C.c_double * 5)()
         self.check(self.lib.lbm_reduce(self.handle, block, out))
+        return np.array(list(out))
+
+    def step_reduce(self, n=1) -> np.ndarray:
+        """``lbm_step_reduce``: n steps, then block 0's diagnostics (mass, momentum x/y/z,
+        kinetic energy), summed by the last step's own kernel where the domain allows."""
+        out = (C.c_double * 5)()
+        self.check(self.lib.lbm_step_reduce(self.handle, int(n), out))
         return np.array(list(out))
 
     def set_tape(self, every):
