@@ -70,25 +70,41 @@ __global__ void __launch_bounds__(192) k_reduce_final(const double* partials, in
   if (lane == 0) out[v] = s;
 }
 
-// Six columns of n partial sums (value-major): one CTA per column, thread t sums entries
-// t, t + 1024, ... in order, then a fixed tree over the threads.
-__global__ void __launch_bounds__(1024) k_reduce_columns(const double* partials, size_t n,
-                                                         double* out) {
-  __shared__ double sh[1024];
-  const double* col = partials + blockIdx.x * n;
-  double s = 0.0;
-  for (size_t i = threadIdx.x; i < n; i += 1024) s += col[i];
-  sh[threadIdx.x] = s;
+// n records of 8 doubles (6 sums + 2 unused), summed in two fixed-order stages so that many
+// SMs share the reads: CTA s of stage 1 sums slice s of the records (thread t: records
+// t, t + 256, ... of the slice, in order, then a fixed tree per value) into
+// stage[s * 6 + value]; stage 2 is k_reduce_final over those partials.
+constexpr int COL_SLICES = 128;
+
+__global__ void __launch_bounds__(256) k_reduce_records(const double* rec, size_t n,
+                                                        double* stage) {
+  __shared__ double sh[6][256];
+  const int sl = blockIdx.x;
+  const size_t per = (n + COL_SLICES - 1) / COL_SLICES;
+  const size_t lo = per * sl, hi = lo + per < n ? lo + per : n;
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (size_t i = lo + threadIdx.x; i < hi; i += 256) {
+#pragma unroll
+    for (int v = 0; v < 6; ++v) s[v] += rec[i * 8 + v];
+  }
+#pragma unroll
+  for (int v = 0; v < 6; ++v) sh[v][threadIdx.x] = s[v];
   __syncthreads();
-  for (int w = 512; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+#pragma unroll
+      for (int v = 0; v < 6; ++v) sh[v][threadIdx.x] += sh[v][threadIdx.x + w];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+  if (threadIdx.x < 6) stage[sl * 6 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-cudaError_t launch_reduce_columns(const double* partials, size_t n, double* out, cudaStream_t s) {
-  k_reduce_columns<<<6, 1024, 0, s>>>(partials, n, out);
+// `partials` holds 8 n + 6 COL_SLICES doubles: the records, then the stage-1 sums.
+cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaStream_t s) {
+  double* stage = partials + 8 * n;
+  k_reduce_records<<<COL_SLICES, 256, 0, s>>>(partials, n, stage);
+  k_reduce_final<<<1, 192, 0, s>>>(stage, COL_SLICES, out);
   return cudaGetLastError();
 }
 

@@ -187,10 +187,20 @@ __device__ __forceinline__ void wall_regularize(float (&d)[27], const BlockView&
   }
 }
 
-// Moments of the state a node stores, for the diagnostics fused into the step (the same
-// quantities lbm_reduce sums: the node counts, rho - 1, j).
-struct NodeMoments {
-  float count = 0.f, drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+// Where a node writes the moments of the state it stores, for the diagnostics fused into
+// the step (the quantities lbm_reduce sums: node count, rho - 1, j, |j|^2 / (2 rho)): six
+// floats at nm[0], nm[stride], ..., nm[5 stride] (shared memory, one column per thread).
+struct NodeMomentsOut {
+  float* nm;
+  int stride;
+  __device__ __forceinline__ void put(float drho, float jx, float jy, float jz, float inv_rho) const {
+    nm[0] = 1.0f;
+    nm[stride] = drho;
+    nm[2 * stride] = jx;
+    nm[3 * stride] = jy;
+    nm[4 * stride] = jz;
+    nm[5 * stride] = 0.5f * (jx * jx + jy * jy + jz * jz) * inv_rho;
+  }
 };
 
 // One node of one block: pull (with bounce-back and face handling), macroscopic moments,
@@ -199,11 +209,13 @@ struct NodeMoments {
 // from the coarse-to-fine mapping, which can therefore run concurrently with this update.
 // ALIGN: last sub-step of a refined block, storing the temporal alignment (see BlockView).
 // WALLS: the block has no-slip wall faces (an instance without them carries no wall code).
-// RED: also return the moments of the stored state in *nm (obstacle voxels and ghost nodes
-// count 0; collision conserves rho and j, so a fluid node's are those of its pulled set).
+// RED: also write the moments of the stored state through *nm (the caller zeroes them first:
+// obstacle voxels and ghost nodes write nothing).  Collision conserves rho and j, so a fluid
+// node's are those of its pulled set, written as soon as they are known, so that nothing
+// is held through the collision.
 template <typename T, typename IT, bool ALIGN = false, bool WALLS = false, bool RED = false>
 __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, int z,
-                                            NodeMoments* nm = nullptr) {
+                                            const NodeMomentsOut* nm = nullptr) {
   const IT N = (IT)v.N;
   const T* __restrict__ din = static_cast<const T*>(v.d_in);
   T* __restrict__ dout = static_cast<T*>(v.d_out);
@@ -222,7 +234,7 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
     } else {  // Dirichlet inflow: equilibrium at rho = 1 and the stored inflow velocity
       ux = v.u_in[idx]; uy = v.u_in[N + idx]; uz = v.u_in[2 * N + idx];
       equilibrium(d, 1.0f, ux, uy, uz);
-      if constexpr (RED) { nm->count = 1.f; nm->jx = ux; nm->jy = uy; nm->jz = uz; }
+      if constexpr (RED) nm->put(0.0f, ux, uy, uz, 1.0f);
       cval = (fl & F_SCALAR_SRC) ? v.c_src
                                  : scalar_value(scalar_corners<IT>(v, x, y, z, ux, uy, uz));
     }
@@ -248,6 +260,10 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
   const float inv = __frcp_rn(1.0f + drho);
   const float ux = d[kap(1, 0, 0)] * inv, uy = d[kap(0, 1, 0)] * inv, uz = d[kap(0, 0, 1)] * inv;
   flag_error(v.err, !(1.0f + drho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 3.0f));
+  if constexpr (RED) {
+    static_assert(!ALIGN, "the fused diagnostics cover plain steps");
+    nm->put(drho, d[kap(1, 0, 0)], d[kap(0, 1, 0)], d[kap(0, 0, 1)], inv);
+  }
 
   // departure-cell scalar loads go out before the collision arithmetic
   ScalarCell sc;
@@ -279,7 +295,6 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
       if (czk(k) > 0) jz += val; else if (czk(k) < 0) jz -= val;
     }
     const float ia = 1.0f / (1.0f + s);
-    if constexpr (RED) { nm->count = 1.f; nm->drho = s; nm->jx = jx; nm->jy = jy; nm->jz = jz; }
     const float cnew = src ? v.c_src : scalar_value(sc);
     const float crest = fmaf(v.al1, v.c_in[idx], v.al2 * cnew);
     const float cal = use0 ? fmaf(v.al0, v.c_al0[idx], crest) : crest;
@@ -296,10 +311,6 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
     __stcs(v.u_out + (N + idx), uy);
     __stcs(v.u_out + (2 * N + idx), uz);
     __stcs(v.c_out + idx, src ? v.c_src : scalar_value(sc));
-    if constexpr (RED) {
-      const float rho = 1.0f + drho;
-      nm->count = 1.f; nm->drho = drho; nm->jx = ux * rho; nm->jy = uy * rho; nm->jz = uz * rho;
-    }
   }
 }
 

@@ -116,11 +116,12 @@ cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size
                           double* partials, double* out, cudaStream_t s);
 // 27 N < 2^32: every array index of the block fits 32 bits
 bool fits_32bit_index(size_t N);
-// the six column sums of `n` value-major partials (partials[value * n + i])
-cudaError_t launch_reduce_columns(const double* partials, size_t n, double* out, cudaStream_t s);
+// the six sums over `n` per-CTA records of 8 doubles (partials[8 i + value]); the buffer
+// holds 8 n + 6 * 128 doubles (the records, then the first stage's sums)
+cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaStream_t s);
 // one collide-stream step of a block (32-bit indexing) that also leaves the diagnostics of
 // the stored state in `out` (same six doubles as launch_reduce); `partials` holds
-// 6 * step_reduce_ctas(v, bx, by) doubles
+// 8 * step_reduce_ctas(v, bx, by) + 6 * 128 doubles
 size_t step_reduce_ctas(const BlockView& v, int bx, int by);
 cudaError_t launch_step_reduce(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
                                int minb, double* partials, double* out);

@@ -326,7 +326,7 @@ lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]) {
   if (ctas > dom->step_partials_n) {
     if (dom->d_step_partials) dom->dev_free(dom->d_step_partials);
     dom->step_partials_n = 0;
-    dom->d_step_partials = static_cast<double*>(dom->dev_alloc(ctas * 6 * sizeof(double)));
+    dom->d_step_partials = static_cast<double*>(dom->dev_alloc((ctas * 8 + 6 * 128) * sizeof(double)));
     if (!dom->d_step_partials) return dom->fail(LBM_ERR_OOM, "step-reduce partials");
     dom->step_partials_n = ctas;
   }
