@@ -96,3 +96,43 @@ def test_fp16_shifted_storage_against_fp32_and_oracle(lib):
     assert abs(r16[0] / r32[0] - 1) < 1e-4
     d32.close()
     d16.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_largest_sizes_take_the_64_bit_index_path_exactly(lib, storage):
+    """A block with 27 N >= 2^32 (here 544^3, 161 M nodes, a 35 GB FP32 state) runs the 64-bit
+    index instance of the collide-stream kernel.  Its result is checked through a property
+    that holds at any size: a periodic 544^3 domain tiled 17 x 17 x 17 from a 32^3 seeded
+    scene (sphere, random velocity, density and scalar) must hold, after 3 steps, exactly the
+    tiled state of the 32^3 domain, which runs the 32-bit instance (same per-node arithmetic,
+    other index arithmetic)."""
+    from paper_1807_02284_gb300 import lbm
+    rep = 17
+    sc = synth.random_scene(dims=(32, 32, 32), seed=61, periodic=(True, True, True),
+                            spheres=[(16.0, 15.0, 17.0, 5.0)], nu=1e-3)
+    b = sc.blocks[0]
+    small = gpu_domain(sc, storage)
+    big_dims = tuple(d * rep for d in b.dims)
+    assert 27 * int(np.prod(big_dims)) >= 2 ** 32
+    big = lbm.Domain(big_dims, sc.nu, periodic=sc.periodic, storage=storage,
+                     adaptive=sc.adaptive, c_src=sc.c_src)
+    big.set_flags(np.tile(b.flags, (rep, rep, rep)))
+    dev = torch.device("cuda")
+    u = torch.tensor(f32(b.u0), device=dev).repeat(1, rep, rep, rep).contiguous()
+    rho = torch.tensor(f32(b.rho0), device=dev).repeat(rep, rep, rep).contiguous()
+    c = torch.tensor(f32(b.c0), device=dev).repeat(rep, rep, rep).contiguous()
+    big.init_macro(u, rho=rho, c=c)
+    del u, rho, c
+    small.step(3)
+    big.step(3)
+    N = int(np.prod(big_dims))
+    for field, comps in ((lbm.LBM_FIELD_U, 3), (lbm.LBM_FIELD_SCALAR, 1), (lbm.LBM_FIELD_RHO, 1)):
+        s = torch.tensor(small.read_field(field, lbm.LBM_F32), device=dev)
+        s = s.reshape((comps,) + b.shape_zyx).repeat(1, rep, rep, rep)
+        g = torch.empty(comps * N, dtype=torch.float32, device=dev)
+        big.read_field(field, lbm.LBM_F32, out=g)
+        big.sync()
+        assert torch.equal(g.reshape(s.shape), s), field
+        del g, s
+    small.close()
+    big.close()
