@@ -77,8 +77,46 @@ class ClockSampler:
         self.dev = device_index
         self.proc = None
         self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+        self.nvml = None
+
+    def _nvml_open(self):
+        """Read-only NVML queries through ctypes (no Python NVML package on every host): the
+        device with the same UUID as the CUDA device.  None when NVML is not available."""
+        import ctypes
+        import threading
+        import torch
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(self.dev).uuid)
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+                return None
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) != 0:   # 1: SM clock
+                return None
+            return {"lib": lib, "h": h, "max": mx.value, "samples": [], "stop": threading.Event()}
+        except Exception:
+            return None
+
+    def _nvml_loop(self):
+        import ctypes
+        n = self.nvml
+        mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while not n["stop"].is_set():
+            if (n["lib"].nvmlDeviceGetClockInfo(n["h"], 1, ctypes.byref(mhz)) == 0 and
+                    n["lib"].nvmlDeviceGetCurrentClocksEventReasons(n["h"], ctypes.byref(rs)) == 0):
+                n["samples"].append((mhz.value, rs.value))
+            n["stop"].wait(0.01)
 
     def start(self):
+        self.nvml = self._nvml_open()
+        if self.nvml is not None:
+            import threading
+            self.thread = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.thread.start()
+            return
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -89,6 +127,20 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        if self.nvml is not None:
+            self.nvml["stop"].set()
+            self.thread.join(timeout=5)
+            smp = self.nvml["samples"]
+            if not smp:
+                return None
+            # clock event reason bits: 0x4 sw power cap, 0x8 hw slowdown, 0x20 sw thermal,
+            # 0x40 hw thermal
+            bits = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+                    0x4: "sw_power_cap"}
+            reasons = sorted({name for _, r in smp for b, name in bits.items() if r & b})
+            return {"sm_mhz": float(np.median([m for m, _ in smp])),
+                    "sm_max_mhz": float(self.nvml["max"]), "reasons": reasons,
+                    "samples": len(smp), "source": "nvml, every 10 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
