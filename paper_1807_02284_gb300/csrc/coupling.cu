@@ -56,11 +56,13 @@ __device__ __forceinline__ MapEntry geometric_entry(const MapArgs& a, uint32_t e
   return m;
 }
 
-constexpr int MAP_D = 32;          // entries per CTA
 constexpr int MAP_THREADS = 128;
 constexpr int MAP_LD = 29;         // shared-memory row stride (odd: no bank conflicts)
 
-template <typename T, int MODE>
+// MAP_D entries per CTA: 32 for small mappings (a ghost layer of a few ten thousand nodes
+// still spreads over every SM), 128 for large ones (one entry per thread: the moment
+// transform of phase 2 runs on every warp instead of one).
+template <typename T, int MODE, int MAP_D>
 __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
   __shared__ float sv[MAP_D * MAP_LD];   // 27 populations + scalar per entry
   __shared__ uint32_t scorner[8][MAP_D];
@@ -113,9 +115,10 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
   // the unrolled pairs issue all their loads before the first sum is needed.  A corner of
   // weight 0 (a fraction of 0 on an axis, where the grids line up, or an obstacle corner)
   // is not loaded: its term would add exactly 0.
-  static_assert(MAP_D == 32 && (MAP_D * 28) % MAP_THREADS == 0, "gather layout");
+  static_assert((MAP_D == 32 || MAP_D == 128) && (MAP_D * 28) % MAP_THREADS == 0, "gather layout");
   constexpr int PAIRS = MAP_D * 28 / MAP_THREADS;
-  const int d = t & 31;
+  constexpr int KSTEP = MAP_THREADS / MAP_D;   // populations apart of one thread's pairs
+  const int d = t % MAP_D;
   uint32_t sc[8];
   float w[8];
 #pragma unroll
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
   float vals[PAIRS];
 #pragma unroll
   for (int i = 0; i < PAIRS; ++i) {
-    const int k = (t >> 5) + i * (MAP_THREADS / 32);
+    const int k = t / MAP_D + i * KSTEP;
     float v = 0.0f;
     if (k < 27) {
       const T* pl = lo + (uint32_t)k * sN;
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
   }
   const float inv_d = sinv[d] > 0.0f ? sinv[d] : 0.0f;     // rest state: all zero
 #pragma unroll
-  for (int i = 0; i < PAIRS; ++i) sv[d * MAP_LD + (t >> 5) + i * (MAP_THREADS / 32)] = vals[i] * inv_d;
+  for (int i = 0; i < PAIRS; ++i) sv[d * MAP_LD + t / MAP_D + i * KSTEP] = vals[i] * inv_d;
   __syncthreads();
   if (t < MAP_D && sinv[t] < 0.0f) {   // rest state: shifted populations, u and scalar 0
     su[0][t] = su[1][t] = su[2][t] = 0.0f;
@@ -184,26 +187,33 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
   if (sinv[d] == 0.0f) return;
   const uint32_t dst = sdst[d];
 #pragma unroll
-  for (int i = 0; i < (31 + MAP_THREADS / 32 - 1) / (MAP_THREADS / 32); ++i) {
-    const int k = (t >> 5) + i * (MAP_THREADS / 32);
+  for (int i = 0; i < (31 + KSTEP - 1) / KSTEP; ++i) {
+    const int k = t / MAP_D + i * KSTEP;
     if (k < 27) store_pop(out + (size_t)k * dN + dst, sv[d * MAP_LD + k]);
     else if (k < 30) a.u_dst[(size_t)(k - 27) * dN + dst] = su[k - 27][d];
     else if (k == 30) a.c_dst[dst] = sv[d * MAP_LD + 27];
   }
 }
 
-template <typename T>
-static void launch_map_t(const MapArgs& a, int grid, cudaStream_t s) {
-  if (a.theta <= 0.0f) k_map<T, 0><<<grid, MAP_THREADS, 0, s>>>(a);
-  else if (a.theta >= 1.0f) k_map<T, 1><<<grid, MAP_THREADS, 0, s>>>(a);
-  else k_map<T, 2><<<grid, MAP_THREADS, 0, s>>>(a);
+template <typename T, int D>
+static void launch_map_t(const MapArgs& a, cudaStream_t s) {
+  const int grid = (a.n + D - 1) / D;
+  if (a.theta <= 0.0f) k_map<T, 0, D><<<grid, MAP_THREADS, 0, s>>>(a);
+  else if (a.theta >= 1.0f) k_map<T, 1, D><<<grid, MAP_THREADS, 0, s>>>(a);
+  else k_map<T, 2, D><<<grid, MAP_THREADS, 0, s>>>(a);
 }
 
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const int grid = (a.n + MAP_D - 1) / MAP_D;
-  if (storage == ST_FP16) launch_map_t<__half>(a, grid, s);
-  else launch_map_t<float>(a, grid, s);
+  // 128 entries per CTA once that still gives every SM about 8 CTAs
+  const bool big = a.n >= 152 * 8 * 128;
+  if (storage == ST_FP16) {
+    if (big) launch_map_t<__half, 128>(a, s);
+    else launch_map_t<__half, 32>(a, s);
+  } else {
+    if (big) launch_map_t<float, 128>(a, s);
+    else launch_map_t<float, 32>(a, s);
+  }
   return cudaGetLastError();
 }
 
