@@ -289,9 +289,12 @@ lbm_status lbm_reduce(lbm_domain* dom, int32_t block_id, double out[5]);
 lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]);
 
 /* lbm_reduce of block `block_id` of each of n domains (no counterpart in the paper: the
-   read-back of a batch), with every reduction queued on its domain's stream before the
-   call waits for any.  out is a host array of 5 n doubles, domain i's five values at
-   out[5 i].  INVALID_ARG for a null list, out or member, n <= 0, or a block id that some
+   read-back of a batch).  Members that share one device, stream and storage are reduced by
+   one launch over chunks of all of them, with one read-back and one wait (the same sums in
+   another order: equal to lbm_reduce's to FP32 rounding of the per-thread partials);
+   otherwise every member's own reduction is queued on its stream before the call waits for
+   any (lbm_reduce's values exactly).  out is a host array of 5 n doubles, domain i's five
+   values at out[5 i].  INVALID_ARG for a null list, out or member, n <= 0, or a block id that some
    member lacks (nothing is launched then); otherwise every member is reduced and the first
    failing member's status is returned (DIVERGED, TIMEOUT, CUDA). */
 lbm_status lbm_reduce_batch(lbm_domain* const* doms, int32_t n, int32_t block_id, double* out);

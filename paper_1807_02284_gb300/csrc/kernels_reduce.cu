@@ -108,6 +108,79 @@ cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaS
   return cudaGetLastError();
 }
 
+// Diagnostics of many domains in one launch (lbm_reduce_batch): a list of chunks, each of
+// one member's nodes; every CTA takes chunks in turn (per-thread compensated FP32 sums, FP64
+// across the CTA, in the order of k_reduce) and writes one record of 8 doubles per chunk.
+template <typename T>
+__global__ void __launch_bounds__(REDUCE_THREADS) k_reduce_items(const RedItem* items, int n_items,
+                                                                 const RedMember* members,
+                                                                 double* records) {
+  __shared__ double sh[REDUCE_THREADS / 32][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const RedItem it = items[w];
+    const RedMember m = members[it.member];
+    const T* d = static_cast<const T*>(m.f);
+    unsigned count = 0;
+    KahanF acc[5];
+    for (size_t idx = it.start + threadIdx.x; idx < it.start + it.len; idx += blockDim.x) {
+      if (m.flags[idx] & (F_SOLID | F_GHOST)) continue;
+      float dd[27];
+#pragma unroll
+      for (int k = 0; k < 27; ++k) dd[k] = load_pop(d + (size_t)k * m.N + idx);
+      float drho, jx, jy, jz;
+      macros(dd, drho, jx, jy, jz);
+      ++count;
+      acc[0].add(drho);
+      acc[1].add(jx);
+      acc[2].add(jy);
+      acc[3].add(jz);
+      acc[4].add(0.5f * (jx * jx + jy * jy + jz * jz) / (1.0f + drho));
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const double v = warp_sum(i == 0 ? (double)count : acc[i - 1].value());
+      if (lane == 0) sh[wid][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      double s = 0;
+      for (int k = 0; k < REDUCE_THREADS / 32; ++k) s += sh[k][threadIdx.x];
+      records[(size_t)w * 8 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per member: its chunks' records (contiguous in the list) in order, then the
+// shuffle tree; the member's device error word rides along in slot 6.
+__global__ void __launch_bounds__(256) k_reduce_items_final(const double* records,
+                                                            const RedMember* members, int n,
+                                                            double* out) {
+  const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (m >= n) return;
+  const RedMember mb = members[m];
+  for (int v = 0; v < 6; ++v) {
+    double s = 0;
+    for (int c = lane; c < mb.n_items; c += 32) s += records[(size_t)(mb.first_item + c) * 8 + v];
+    s = warp_sum(s);
+    if (lane == 0) out[(size_t)m * 8 + v] = s;
+  }
+  if (lane == 0) out[(size_t)m * 8 + 6] = (double)*mb.err;
+}
+
+cudaError_t launch_reduce_items(int storage, const RedItem* items, int n_items,
+                                const RedMember* members, int n_members, double* records,
+                                double* out, cudaStream_t s) {
+  const int ctas = n_items < REDUCE_CTAS ? n_items : REDUCE_CTAS;
+  if (storage == ST_FP16)
+    k_reduce_items<__half><<<ctas, REDUCE_THREADS, 0, s>>>(items, n_items, members, records);
+  else
+    k_reduce_items<float><<<ctas, REDUCE_THREADS, 0, s>>>(items, n_items, members, records);
+  k_reduce_items_final<<<(n_members + 7) / 8, 256, 0, s>>>(records, members, n_members, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
                           double* partials, double* out, cudaStream_t s) {
   const size_t want = (N + REDUCE_THREADS - 1) / REDUCE_THREADS;

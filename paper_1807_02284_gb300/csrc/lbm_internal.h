@@ -116,6 +116,23 @@ cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size
                           double* partials, double* out, cudaStream_t s);
 // 27 N < 2^32: every array index of the block fits 32 bits
 bool fits_32bit_index(size_t N);
+// diagnostics of several domains in one launch: chunks of members' nodes
+struct RedMember {
+  const void* f;          // current populations (27 planes)
+  const uint8_t* flags;
+  const int* err;         // the member's device error word
+  size_t N;
+  int first_item, n_items;
+};
+struct RedItem {
+  int member, pad;
+  size_t start, len;
+};
+// records: 8 doubles per item; out: 8 doubles per member (the six launch_reduce sums, then
+// the member's error word)
+cudaError_t launch_reduce_items(int storage, const RedItem* items, int n_items,
+                                const RedMember* members, int n_members, double* records,
+                                double* out, cudaStream_t s);
 // the six sums over `n` per-CTA records of 8 doubles (partials[8 i + value]); the buffer
 // holds 8 n + 6 * 128 doubles (the records, then the first stage's sums)
 cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaStream_t s);

@@ -538,6 +538,71 @@ lbm_status lbm_reduce(lbm_domain* dom, int32_t block_id, double out[5]) {
   return st;
 }
 
+// lbm_reduce_batch for members that share device, stream and storage: one launch over a
+// list of node chunks of all members, one read-back (sums and error words), one wait.
+static lbm_status reduce_batch_joint(lbm_domain* const* doms, int n, int block_id, double* out) {
+  lbm_domain* d0 = doms[0];
+  constexpr size_t kChunk = 8192;
+  std::vector<RedMember> mem(n);
+  std::vector<RedItem> items;
+  for (int i = 0; i < n; ++i) {
+    Block& B = doms[i]->blocks[block_id];
+    mem[i] = RedMember{B.lv[B.cur].f, B.flags, doms[i]->d_err, B.N, (int)items.size(), 0};
+    for (size_t s = 0; s < B.N; s += kChunk)
+      items.push_back(RedItem{i, 0, s, std::min(kChunk, B.N - s)});
+    mem[i].n_items = (int)items.size() - mem[i].first_item;
+  }
+  const size_t mb = mem.size() * sizeof(RedMember), ib = items.size() * sizeof(RedItem);
+  const size_t rb = items.size() * 8 * sizeof(double), ob = (size_t)n * 8 * sizeof(double);
+  if (d0->rb_host_bytes < mb + ib + ob) {
+    if (d0->rb_host) cudaFreeHost(d0->rb_host);
+    d0->rb_host = nullptr;
+    d0->rb_host_bytes = 0;
+    if (cudaMallocHost(&d0->rb_host, mb + ib + ob) != cudaSuccess) {
+      d0->rb_host = nullptr;
+      return d0->fail(LBM_ERR_OOM, "batch reduction staging");
+    }
+    d0->rb_host_bytes = mb + ib + ob;
+  }
+  if (d0->rb_dev_bytes < mb + ib + rb + ob) {
+    if (d0->rb_dev) d0->dev_free(d0->rb_dev);
+    d0->rb_dev_bytes = 0;
+    d0->rb_dev = d0->dev_alloc(mb + ib + rb + ob);
+    if (!d0->rb_dev) return d0->fail(LBM_ERR_OOM, "batch reduction scratch");
+    d0->rb_dev_bytes = mb + ib + rb + ob;
+  }
+  char* h = static_cast<char*>(d0->rb_host);
+  char* g = static_cast<char*>(d0->rb_dev);
+  std::memcpy(h, mem.data(), mb);
+  std::memcpy(h + mb, items.data(), ib);
+  const RedMember* g_mem = reinterpret_cast<const RedMember*>(g);
+  const RedItem* g_items = reinterpret_cast<const RedItem*>(g + mb);
+  double* g_rec = reinterpret_cast<double*>(g + mb + ib);
+  double* g_out = reinterpret_cast<double*>(g + mb + ib + rb);
+  double* h_out = reinterpret_cast<double*>(h + mb + ib);
+  cudaError_t e = cudaMemcpyAsync(g, h, mb + ib, cudaMemcpyHostToDevice, d0->stream);
+  if (e == cudaSuccess)
+    e = launch_reduce_items(d0->desc.storage, g_items, (int)items.size(), g_mem, n, g_rec, g_out,
+                            d0->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, g_out, ob, cudaMemcpyDeviceToHost, d0->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d0->stream);
+  if (e != cudaSuccess) return d0->cuda_fail(e, "batch reduction");
+  lbm_status first = LBM_OK;
+  for (int i = 0; i < n; ++i) {
+    const double* r = h_out + 8 * (size_t)i;
+    double* o = out + 5 * (size_t)i;
+    o[0] = r[0] + r[1];
+    o[1] = r[2];
+    o[2] = r[3];
+    o[3] = r[4];
+    o[4] = r[5];
+    *doms[i]->h_err = (int)r[6];
+    const lbm_status st = doms[i]->error_status();
+    if (st != LBM_OK && first == LBM_OK) first = st;
+  }
+  return first;
+}
+
 lbm_status lbm_reduce_batch(lbm_domain* const* doms, int32_t n, int32_t block_id, double* out) {
   if (!doms || n <= 0 || !out) return LBM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
@@ -545,6 +610,14 @@ lbm_status lbm_reduce_batch(lbm_domain* const* doms, int32_t n, int32_t block_id
     cudaSetDevice(doms[i]->desc.device);
     const lbm_status st = doms[i]->check_block(block_id);
     if (st != LBM_OK) return st;
+  }
+  bool joint = n >= 2;
+  for (int i = 1; i < n && joint; ++i)
+    joint = doms[i]->desc.device == doms[0]->desc.device && doms[i]->stream == doms[0]->stream &&
+            doms[i]->desc.storage == doms[0]->desc.storage;
+  if (joint) {
+    cudaSetDevice(doms[0]->desc.device);
+    return reduce_batch_joint(doms, n, block_id, out);
   }
   // queue every reduction and its read-back before waiting on any stream
   for (int i = 0; i < n; ++i) {

@@ -88,6 +88,11 @@ struct lbm_domain {
   struct TunedShape { int nx_class, n_class, bx, by, minb; };
   std::vector<TunedShape> tuned_shapes;
   void* batch_plan = nullptr;           // cached plans of lbm_step_batch (batch.cu)
+  // scratch of lbm_reduce_batch when this domain heads the list (device and pinned host)
+  void* rb_dev = nullptr;
+  size_t rb_dev_bytes = 0;
+  void* rb_host = nullptr;
+  size_t rb_host_bytes = 0;
   cudaStream_t aux_stream = nullptr;    // second stream for concurrent mapping launches
   std::vector<cudaEvent_t> events;      // fork / join events (timing disabled)
 

@@ -146,6 +146,12 @@ cudaStream_t lbm_domain::post_stream(int k) {
 void lbm_domain::release_extras() {
   invalidate_graphs();
   release_batch_plan(this);
+  if (rb_dev) dev_free(rb_dev);
+  rb_dev = nullptr;
+  rb_dev_bytes = 0;
+  if (rb_host) cudaFreeHost(rb_host);
+  rb_host = nullptr;
+  rb_host_bytes = 0;
   for (cudaEvent_t ev : events) cudaEventDestroy(ev);
   events.clear();
   for (cudaStream_t st : post_streams) cudaStreamDestroy(st);

@@ -70,8 +70,31 @@ def test_reduce_batch_equals_per_domain_reduce(lib):
     lbm.step_batch(doms, 7)
     r = lbm.reduce_batch(doms)
     assert r.shape == (6, 5)
+    # members on streams of their own: one reduction each, the very values of lbm_reduce
     for i, d in enumerate(doms):
         assert np.array_equal(r[i], d.reduce())
+    # members sharing a stream: one launch over all of them, the same sums in another order
+    # (per-thread compensated FP32 partials over other nodes, FP64 combination)
+    import torch
+    from tests.helpers import f32
+    st = torch.cuda.Stream()
+    shared = []
+    for s in scenes:
+        b = s.blocks[0]
+        d = lbm.Domain(b.dims, s.nu, periodic=s.periodic, adaptive=s.adaptive, c_src=s.c_src,
+                       stream=st)
+        d.set_flags(b.flags)
+        d.init_macro(f32(b.u0), rho=f32(b.rho0), c=f32(b.c0))
+        shared.append(d)
+    lbm.step_batch(shared, 7)
+    r2 = lbm.reduce_batch(shared)
+    for i, d in enumerate(shared):
+        ri = d.reduce()
+        assert abs(r2[i][0] - ri[0]) <= 1e-9 * ri[0]
+        assert np.abs(r2[i][1:] - ri[1:]).max() <= 1e-6 * max(1.0, np.abs(ri[1:]).max())
+        assert np.array_equal(ri, r[i])             # same states as the separate-stream run
+    for d in shared:
+        d.close()
     with pytest.raises(lbm.LBMError) as ei:
         lbm.reduce_batch(doms, block=1)
     assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
