@@ -44,6 +44,8 @@ struct AdjArgs {
   float* ups_out;       // Ups^n
   float* gam_out;       // Gam^n
   float* mu;            // 9 planes: adjoint of the velocity differences of the gradient norm
+  float* sw;            // 9 planes: departure-sample weights of each sender (put_sender)
+  float* sg;            // sender's scalar adjoint, 0 for non-senders
 };
 
 // Adjoint of the scalar step with respect to the departure velocity: C^{n+1}(x) is the
@@ -184,6 +186,43 @@ __global__ void k_zero_face_slots(float* __restrict__ lam, int nx, int ny, int n
   }
 }
 
+// Weight at this node of the departure sample of the node D steps away along one axis, when
+// neither clamping nor wrap-around can move that sample's cell (the axis is periodic with >= 4
+// nodes, or this node is >= 2 nodes from both ends of an open axis): the sample sits at
+// dsp = clamp(-u, -1, 1) from its node, in the cell [f, f + 1] with f = floor(dsp) and
+// fraction t = dsp - f, so this node is the cell's lower corner when f = -D (weight 1 - t) and
+// its upper corner when f = -D - 1 (weight t).  Same values as sl_axis followed by the corner
+// test of the general gather.
+template <int D>
+__device__ __forceinline__ float sl_weight_interior(float u) {
+  float dsp = -u;
+  if (!(dsp == dsp)) dsp = 0.0f;
+  dsp = fminf(fmaxf(dsp, -1.0f), 1.0f);
+  const float f = floorf(dsp);
+  const float t = dsp - f;
+  float w = f == (float)(-D) ? 1.0f - t : 0.0f;
+  if constexpr (D <= 0) w = f == (float)(-D - 1) ? t : w;
+  return w;
+}
+
+// Pass A's part of the scalar gather: this node's departure-sample weights toward the three
+// nodes that can receive from it along each axis (receiver at offset e = -1, 0, +1: plane
+// 3 a + e + 1 of sw) and its scalar adjoint in sg, 0 where the node sends nothing (obstacle,
+// scalar source, scale boundary).  Pass B's interior gather reads these instead of the
+// velocities and flags of its 27 neighbours.  Values for nodes next to an open face are not
+// used (their receivers take the general gather).
+__device__ __forceinline__ void put_sender(const AdjArgs& a, uint32_t N, uint32_t idx, float g,
+                                           float ux, float uy, float uz) {
+  const float u[3] = {ux, uy, uz};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a.sw[(uint32_t)(3 * c + 0) * N + idx] = sl_weight_interior<1>(u[c]);
+    a.sw[(uint32_t)(3 * c + 1) * N + idx] = sl_weight_interior<0>(u[c]);
+    a.sw[(uint32_t)(3 * c + 2) * N + idx] = sl_weight_interior<-1>(u[c]);
+  }
+  a.sg[idx] = g;
+}
+
 // MINB: CTAs per SM the register allocation is bounded for (3: no spills; 4: some spills,
 // more warps in flight); the faster one is chosen at run time.
 // OPEN: some face of the block is open (face slots accumulate; see FaceMask).  ACC: the
@@ -207,6 +246,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   if ((fl & F_SOLID) || (ACC && (fl & F_GHOST))) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = 0.0f;
+    put_sender(a, N, idx, 0.0f, 0.0f, 0.0f, 0.0f);
     return;
   }
   if (fl & F_INFLOW) {
@@ -214,6 +254,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
     // populations are unused (their slots get a zero adjoint) and every adjoint goes to U^n,
     // which pass B completes with the lagged-gradient terms of the neighbours
     const float u[3] = {v.u_in[idx], v.u_in[N + idx], v.u_in[2 * N + idx]};
+    put_sender(a, N, idx, (fl & F_SCALAR_SRC) ? 0.0f : a.gam_in[idx], u[0], u[1], u[2]);
     float ub[3] = {a.ups_in[idx], a.ups_in[N + idx], a.ups_in[2 * N + idx]};
     if (!(fl & F_SCALAR_SRC)) scalar_u_vjp(v, x, y, z, u[0], u[1], u[2], a.gam_in[idx], ub);
 #pragma unroll
@@ -253,6 +294,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   const float drho = K[kap(0, 0, 0)];
   const float inv = __frcp_rn(1.0f + drho);
   const float ux = K[kap(1, 0, 0)] * inv, uy = K[kap(0, 1, 0)] * inv, uz = K[kap(0, 0, 1)] * inv;
+  put_sender(a, N, idx, (fl & F_SCALAR_SRC) ? 0.0f : a.gam_in[idx], ux, uy, uz);
   float diff[9];
   float g = 0.0f;
   if (v.rp.adaptive) {
@@ -318,25 +360,6 @@ static void launch_pass_a(const AdjArgs& a, int minb, bool open, dim3 grd, dim3 
   }
 }
 
-// Weight at this node of the departure sample of the node D steps away along one axis, when
-// neither clamping nor wrap-around can move that sample's cell (the axis is periodic with >= 4
-// nodes, or this node is >= 2 nodes from both ends of an open axis): the sample sits at
-// dsp = clamp(-u, -1, 1) from its node, in the cell [f, f + 1] with f = floor(dsp) and
-// fraction t = dsp - f, so this node is the cell's lower corner when f = -D (weight 1 - t) and
-// its upper corner when f = -D - 1 (weight t).  Same values as sl_axis followed by the corner
-// test of the general gather.
-template <int D>
-__device__ __forceinline__ float sl_weight_interior(float u) {
-  float dsp = -u;
-  if (!(dsp == dsp)) dsp = 0.0f;
-  dsp = fminf(fmaxf(dsp, -1.0f), 1.0f);
-  const float f = floorf(dsp);
-  const float t = dsp - f;
-  float w = f == (float)(-D) ? 1.0f - t : 0.0f;
-  if constexpr (D <= 0) w = f == (float)(-D - 1) ? t : w;
-  return w;
-}
-
 template <bool ACC>
 __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
   const BlockView& v = a.fwd;
@@ -392,18 +415,13 @@ __global__ void __launch_bounds__(128) k_adj_b(AdjArgs a) {
       for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
+          // neighbour j = this + (dx - 1, dy - 1, dz - 1) sends to offset e = 1 - d: its
+          // weights were stored by pass A (put_sender), plane 3 axis + 2 - d
           const uint32_t j = ps[dz] + rs[dy] + xs[dx];
-          float G = __ldg(a.gam_in + j);
-          if (__ldg(v.flags + j) & (F_SOLID | F_SCALAR_SRC | F_GHOST)) G = 0.0f;
-          const float wx = dx == 0 ? sl_weight_interior<-1>(__ldg(a.u_next + j))
-                         : dx == 1 ? sl_weight_interior<0>(__ldg(a.u_next + j))
-                                   : sl_weight_interior<1>(__ldg(a.u_next + j));
-          const float wy = dy == 0 ? sl_weight_interior<-1>(__ldg(a.u_next + N + j))
-                         : dy == 1 ? sl_weight_interior<0>(__ldg(a.u_next + N + j))
-                                   : sl_weight_interior<1>(__ldg(a.u_next + N + j));
-          const float wz = dz == 0 ? sl_weight_interior<-1>(__ldg(a.u_next + 2 * N + j))
-                         : dz == 1 ? sl_weight_interior<0>(__ldg(a.u_next + 2 * N + j))
-                                   : sl_weight_interior<1>(__ldg(a.u_next + 2 * N + j));
+          const float G = __ldg(a.sg + j);
+          const float wx = __ldg(a.sw + (uint32_t)(0 + 2 - dx) * N + j);
+          const float wy = __ldg(a.sw + (uint32_t)(3 + 2 - dy) * N + j);
+          const float wz = __ldg(a.sw + (uint32_t)(6 + 2 - dz) * N + j);
           gam = fmaf(wx * wy * wz, G, gam);
         }
     a.gam_out[idx] = ACC ? a.gam_out[idx] + gam : gam;
@@ -914,6 +932,8 @@ static cudaError_t ms_reverse_op(lbm_domain* dom, TapeState* t, const MsOp& o, c
   a.u_next = u_next;
   a.lam_out = lin.f; a.ups_out = lin.u; a.gam_out = lin.c;
   a.mu = t->mu;
+  a.sw = t->mu + 9 * N;
+  a.sg = t->mu + 18 * N;
   const bool open = o.b != 0 || !dom->desc.periodic[0] || !dom->desc.periodic[1] || !dom->desc.periodic[2];
   const dim3 blk(128, 1, 1), grd((B.nx + 127) / 128, B.ny, B.nz);
   launch_pass_a(a, 3, open, grd, blk, s, true);
@@ -965,7 +985,7 @@ static lbm_status adjoint_multiblock(lbm_domain* dom, int n_steps, const float* 
       t->grad[b] = static_cast<float*>(dom->dev_alloc(N * 3 * sizeof(float)));
       if (!t->grad[b]) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
     }
-    t->mu = static_cast<float*>(dom->dev_alloc(nmax * 9 * sizeof(float)));
+    t->mu = static_cast<float*>(dom->dev_alloc(nmax * 19 * sizeof(float)));   // mu, sw, sg
     if (!t->mu) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
   }
   const int seg_len = std::min(t->every, std::max(1, n_steps));
@@ -1076,7 +1096,7 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
     if (!t->gam[i]) t->gam[i] = static_cast<float*>(dom->dev_alloc(N * sizeof(float)));
     if (!t->lam[i] || !t->ups[i] || !t->gam[i]) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
   }
-  if (!t->mu) t->mu = static_cast<float*>(dom->dev_alloc(N * 9 * sizeof(float)));
+  if (!t->mu) t->mu = static_cast<float*>(dom->dev_alloc(N * 19 * sizeof(float)));   // mu, sw, sg
   if (!t->mu) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
   const int seg_len = std::min(t->every, std::max(1, n_steps));
   while ((int)t->seg.size() < seg_len) {
@@ -1126,6 +1146,8 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
       a.ups_out = t->ups[c ^ 1];
       a.gam_out = t->gam[c ^ 1];
       a.mu = t->mu;
+      a.sw = t->mu + 9 * N;
+      a.sg = t->mu + 18 * N;
       if (t->pass_a_minb == 0) {
         // time both register bounds on this step's inputs (pass A only writes lam_out, mu and
         // the inflow nodes' ups_out, which the launches below rewrite), keep the faster
