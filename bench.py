@@ -654,8 +654,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(E):
-        for d, (t, a) in zip(doms, pins):
-            d.set_inflow(a)
+        lbm.set_inflow_batch(doms, [a for _, a in pins])
         lbm.step_batch(doms, 1)
         lbm.reduce_batch(doms)
     t_e2e = _max_over_ranks(ws, time.perf_counter() - t0)
@@ -674,8 +673,8 @@ def run_batch(args):
                 "e2e": {"value": N * E * ws / t_e2e / 1e6, "unit": "MLUPS",
                         "h2d_bytes_per_step": int(sum(r.nbytes for r in recs)),
                         "d2h_bytes_per_step": 40 * len(mine), "steps": E,
-                        "api": "lbm_set_boundary(INFLOW, pinned host) per member + "
-                               "lbm_step_batch(1) + lbm_reduce_batch(host)"},
+                        "api": "lbm_set_inflow_batch(pinned host) + lbm_step_batch(1) + "
+                               "lbm_reduce_batch(host)"},
                 "gpu_launches": 1, "clocks": clk}
         print(json.dumps(line), flush=True)
     for d in doms:

@@ -299,6 +299,16 @@ lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]);
    failing member's status is returned (DIVERGED, TIMEOUT, CUDA). */
 lbm_status lbm_reduce_batch(lbm_domain* const* doms, int32_t n, int32_t block_id, double* out);
 
+/* LBM_BC_INFLOW records of block 0 of each of n domains (no counterpart in the paper: the
+   input side of a batch step).  recs[i] points to counts[i] host records for domain i (may
+   be null when counts[i] is 0).  Members that share one device and stream get one staged
+   host-to-device copy and one launch (the call returns once the records are staged, before
+   the copy ends); otherwise each member takes lbm_set_boundary(LBM_BC_INFLOW).  Same effect
+   and error reporting as the per-member calls.  INVALID_ARG for a null list, member,
+   recs or counts, or a negative count. */
+lbm_status lbm_set_inflow_batch(lbm_domain* const* doms, int32_t n,
+                                const lbm_inflow_record* const* recs, const int32_t* counts);
+
 lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block_info* info);
 
 /* Advances n independent single-block domains by `steps` reference steps with one

@@ -206,6 +206,36 @@ __global__ void k_inflow_records(const InflowRec* rec, int n, uint8_t* flags, fl
     if (lv[l]) { lv[l][idx] = r.ux; lv[l][N + idx] = r.uy; lv[l][2 * N + idx] = r.uz; }
 }
 
+// Records of several domains in one launch (lbm_set_inflow_batch): record i belongs to
+// member member_of[i]; the same checks and writes as k_inflow_records.
+__global__ void k_inflow_records_multi(const InflowRec* rec, int n, const int* member_of,
+                                       const InflowMember* members) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const InflowMember m = members[member_of[i]];
+  const InflowRec r = rec[i];
+  if (r.x < 0 || r.y < 0 || r.z < 0 || r.x >= m.nx || r.y >= m.ny || r.z >= m.nz) {
+    atomicOr(m.err, 4);
+    return;
+  }
+  const size_t idx = ((size_t)r.z * m.ny + r.y) * m.nx + r.x;
+  if (m.flags[idx] & (F_SOLID | F_OBST_WALL | F_GHOST)) {
+    atomicOr(m.err, 4);
+    return;
+  }
+  m.flags[idx] |= F_INFLOW;
+  for (int l = 0; l < 3; ++l)
+    if (m.u[l]) { m.u[l][idx] = r.ux; m.u[l][m.N + idx] = r.uy; m.u[l][2 * m.N + idx] = r.uz; }
+}
+
+cudaError_t launch_inflow_records_multi(const void* rec, int n, const int* member_of,
+                                        const InflowMember* members, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_inflow_records_multi<<<(n + 255) / 256, 256, 0, s>>>(static_cast<const InflowRec*>(rec), n,
+                                                        member_of, members);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_inflow_records(const void* rec, int n, uint8_t* flags, float* const* u_levels,
                                   int n_levels, int nx, int ny, int nz, size_t N, int* err,
                                   cudaStream_t s) {

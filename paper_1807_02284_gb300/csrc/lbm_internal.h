@@ -94,6 +94,17 @@ cudaError_t launch_obstacle_walls(uint8_t* flags, int nx, int ny, int nz, const 
                                   cudaStream_t s);
 cudaError_t launch_near_solid(uint8_t* flags, int nx, int ny, int nz, const int per[3],
                               cudaStream_t s);
+// one member of lbm_set_inflow_batch: its flags, velocity levels (up to 3, unused null),
+// dims and error word
+struct InflowMember {
+  uint8_t* flags;
+  float* u[3];
+  int nx, ny, nz, pad;
+  size_t N;
+  int* err;
+};
+cudaError_t launch_inflow_records_multi(const void* rec, int n, const int* member_of,
+                                        const InflowMember* members, cudaStream_t s);
 cudaError_t launch_inflow_records(const void* rec, int n, uint8_t* flags, float* const* u_levels,
                                   int n_levels, int nx, int ny, int nz, size_t N, int* err,
                                   cudaStream_t s);

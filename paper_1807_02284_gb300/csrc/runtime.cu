@@ -672,3 +672,83 @@ const char* lbm_last_error(const lbm_domain* dom) {
 }
 
 }  // extern "C"
+
+// LBM_BC_INFLOW records of block 0 of several domains: members sharing device and stream get
+// one staged upload and one launch; otherwise each member takes lbm_set_boundary.
+lbm_status lbm_set_inflow_batch(lbm_domain* const* doms, int32_t n,
+                                const lbm_inflow_record* const* recs, const int32_t* counts) {
+  if (!doms || n <= 0 || !recs || !counts) return LBM_ERR_INVALID_ARG;
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!doms[i] || counts[i] < 0 || (counts[i] > 0 && !recs[i])) return LBM_ERR_INVALID_ARG;
+    total += (size_t)counts[i];
+  }
+  if (total > (size_t)INT32_MAX) return doms[0]->fail(LBM_ERR_INVALID_ARG, "too many records");
+  bool joint = n >= 2;
+  for (int i = 1; i < n && joint; ++i)
+    joint = doms[i]->desc.device == doms[0]->desc.device && doms[i]->stream == doms[0]->stream;
+  if (!joint) {
+    for (int i = 0; i < n; ++i) {
+      const lbm_status st = lbm_set_boundary(doms[i], 0, LBM_BC_INFLOW, recs[i],
+                                             (size_t)counts[i] * sizeof(lbm_inflow_record), 0);
+      if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+  }
+  lbm_domain* d0 = doms[0];
+  cudaSetDevice(d0->desc.device);
+  if (total == 0) return LBM_OK;
+  const size_t rb = total * sizeof(lbm_inflow_record), ob = total * sizeof(int);
+  const size_t mb = (size_t)n * sizeof(InflowMember);
+  const size_t bytes = mb + rb + ob;
+  if (!d0->ib_done && cudaEventCreateWithFlags(&d0->ib_done, cudaEventDisableTiming) != cudaSuccess) {
+    d0->ib_done = nullptr;
+    return d0->fail(LBM_ERR_CUDA, "cudaEventCreate");
+  }
+  // the previous upload from the staging buffer must have left it
+  cudaError_t e = cudaEventSynchronize(d0->ib_done);
+  if (e != cudaSuccess) return d0->cuda_fail(e, "cudaEventSynchronize");
+  if (d0->ib_host_bytes < bytes) {
+    if (d0->ib_host) cudaFreeHost(d0->ib_host);
+    d0->ib_host = nullptr;
+    d0->ib_host_bytes = 0;
+    if (cudaMallocHost(&d0->ib_host, bytes) != cudaSuccess) {
+      d0->ib_host = nullptr;
+      return d0->fail(LBM_ERR_OOM, "inflow batch staging");
+    }
+    d0->ib_host_bytes = bytes;
+  }
+  if (d0->ib_dev_bytes < bytes) {
+    if (d0->ib_dev) d0->dev_free(d0->ib_dev);
+    d0->ib_dev_bytes = 0;
+    d0->ib_dev = d0->dev_alloc(bytes);
+    if (!d0->ib_dev) return d0->fail(LBM_ERR_OOM, "inflow batch buffer");
+    d0->ib_dev_bytes = bytes;
+  }
+  char* h = static_cast<char*>(d0->ib_host);
+  InflowMember* hm = reinterpret_cast<InflowMember*>(h);
+  char* hr = h + mb;
+  int* ho = reinterpret_cast<int*>(h + mb + rb);
+  size_t at = 0;
+  for (int i = 0; i < n; ++i) {
+    Block& B = doms[i]->blocks[0];
+    InflowMember m{};
+    m.flags = B.flags;
+    for (int l = 0; l < 3; ++l) m.u[l] = l < (int)B.lv.size() ? B.lv[l].u : nullptr;
+    m.nx = B.nx; m.ny = B.ny; m.nz = B.nz;
+    m.N = B.N;
+    m.err = doms[i]->d_err;
+    hm[i] = m;
+    std::memcpy(hr + at * sizeof(lbm_inflow_record), recs[i], (size_t)counts[i] * sizeof(lbm_inflow_record));
+    for (int k = 0; k < counts[i]; ++k) ho[at + k] = i;
+    at += (size_t)counts[i];
+  }
+  char* g = static_cast<char*>(d0->ib_dev);
+  e = cudaMemcpyAsync(g, h, bytes, cudaMemcpyHostToDevice, d0->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(d0->ib_done, d0->stream);
+  if (e == cudaSuccess)
+    e = launch_inflow_records_multi(g + mb, (int)total, reinterpret_cast<const int*>(g + mb + rb),
+                                    reinterpret_cast<const InflowMember*>(g), d0->stream);
+  if (e != cudaSuccess) return d0->cuda_fail(e, "inflow batch");
+  return LBM_OK;
+}

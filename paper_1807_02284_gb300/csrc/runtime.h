@@ -93,6 +93,13 @@ struct lbm_domain {
   size_t rb_dev_bytes = 0;
   void* rb_host = nullptr;
   size_t rb_host_bytes = 0;
+  // staging of lbm_set_inflow_batch when this domain heads the list; ib_done marks the end
+  // of the previous upload from ib_host
+  void* ib_dev = nullptr;
+  size_t ib_dev_bytes = 0;
+  void* ib_host = nullptr;
+  size_t ib_host_bytes = 0;
+  cudaEvent_t ib_done = nullptr;
   cudaStream_t aux_stream = nullptr;    // second stream for concurrent mapping launches
   std::vector<cudaEvent_t> events;      // fork / join events (timing disabled)
 

@@ -152,6 +152,15 @@ void lbm_domain::release_extras() {
   if (rb_host) cudaFreeHost(rb_host);
   rb_host = nullptr;
   rb_host_bytes = 0;
+  if (ib_done) cudaEventSynchronize(ib_done);
+  if (ib_dev) dev_free(ib_dev);
+  ib_dev = nullptr;
+  ib_dev_bytes = 0;
+  if (ib_host) cudaFreeHost(ib_host);
+  ib_host = nullptr;
+  ib_host_bytes = 0;
+  if (ib_done) cudaEventDestroy(ib_done);
+  ib_done = nullptr;
   for (cudaEvent_t ev : events) cudaEventDestroy(ev);
   events.clear();
   for (cudaStream_t st : post_streams) cudaStreamDestroy(st);

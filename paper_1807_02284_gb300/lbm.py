@@ -86,6 +86,7 @@ _SIGNATURES = {
     "lbm_get_block_info": (_I, [_P, _I, C.POINTER(lbm_block_info)]),
     "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
     "lbm_reduce_batch": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
+    "lbm_set_inflow_batch": (_I, [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(C.c_int32)]),
     "lbm_set_tape": (_I, [_P, _I]),
     "lbm_adjoint_step": (_I, [_P, _I, _P, _P, _P, _P]),
     "lbm_adjoint_block_grad": (_I, [_P, _I, _P]),
@@ -354,6 +355,20 @@ def step_batch(domains: Sequence[Domain], steps: int):
     lib = load()
     arr = (C.c_void_p * len(domains))(*[d.handle.value for d in domains])
     st = lib.lbm_step_batch(arr, len(domains), int(steps))
+    if st != LBM_OK:
+        domains[0].check(st)
+
+
+def set_inflow_batch(domains: Sequence[Domain], records: Sequence[np.ndarray]):
+    """``lbm_set_inflow_batch``: inflow records (host arrays of INFLOW_RECORD) for block 0
+    of every domain, staged and applied together."""
+    lib = load()
+    n = len(domains)
+    recs = [np.ascontiguousarray(r, dtype=INFLOW_RECORD) for r in records]
+    arr = (C.c_void_p * n)(*[d.handle.value for d in domains])
+    ptrs = (C.c_void_p * n)(*[r.ctypes.data if r.size else None for r in recs])
+    counts = (C.c_int32 * n)(*[int(r.size) for r in recs])
+    st = lib.lbm_set_inflow_batch(arr, n, ptrs, counts)
     if st != LBM_OK:
         domains[0].check(st)
 

@@ -167,3 +167,48 @@ def test_bounded_barrier_reports_timeout_and_context_survives(lib):
     d.step(2)
     d.sync()
     d.close()
+
+
+def test_set_inflow_batch_equals_per_member_calls(lib):
+    """One staged upload and launch for the inflow records of members sharing a stream: the
+    same flags and velocity levels as the per-member lbm_set_boundary calls, and a bad
+    record is reported by its own member only."""
+    import torch
+    from paper_1807_02284_gb300 import lbm
+    from tests.helpers import f32
+    scenes = _scenes(5, seed=44)
+    st = torch.cuda.Stream()
+    joint, single = [], []
+    for s in scenes:
+        b = s.blocks[0]
+        d = lbm.Domain(b.dims, s.nu, periodic=s.periodic, adaptive=s.adaptive, c_src=s.c_src,
+                       stream=st)
+        d.set_flags(b.flags)
+        d.init_macro(f32(b.u0), rho=f32(b.rho0), c=f32(b.c0))
+        joint.append(d)
+        single.append(gpu_domain(s))
+    rng = np.random.default_rng(7)
+    recs = []
+    for s in scenes:
+        r = synth.inflow_records(s.blocks[0])
+        r["ux"] *= (1.0 + 0.05 * rng.random(r.size)).astype(np.float32)
+        recs.append(r)
+    recs[2] = recs[2][:0]                           # a member without records
+    lbm.set_inflow_batch(joint, recs)
+    for d, r in zip(single, recs):
+        d.set_inflow(r)
+    lbm.step_batch(joint, 3)
+    lbm.step_batch(single, 3)
+    for a, b in zip(joint, single):
+        for field, dt in ((lbm.LBM_FIELD_U, lbm.LBM_F32), (lbm.LBM_FIELD_FLAGS, lbm.LBM_U8),
+                          (lbm.LBM_FIELD_F, lbm.LBM_F32)):
+            assert np.array_equal(a.read_field(field, dt), b.read_field(field, dt))
+    bad = synth.inflow_records(scenes[1].blocks[0])[:1].copy()
+    bad["x"] = 10_000                               # outside member 1's block
+    lbm.set_inflow_batch(joint, [recs[0][:0], bad, recs[2], recs[3][:0], recs[4][:0]])
+    with pytest.raises(lbm.LBMError) as ei:
+        joint[1].sync()
+    assert ei.value.status == lbm.LBM_ERR_DIVERGED
+    joint[0].sync()
+    for d in joint + single:
+        d.close()
