@@ -318,6 +318,16 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
    bit-identical to calling lbm_step on each domain. */
 lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t steps);
 
+/* lbm_step_batch with steps >= 1 followed by the lbm_reduce diagnostics of every member's
+   new state, summed by the last step's own kernel (each work item's nodes add their
+   moments as they are stored; the item sums are combined per member in FP64 in a fixed
+   order and copied back by the same captured graph): no second pass over the populations.
+   out is a host array of 5 n doubles (the lbm_reduce_batch layout); the values agree with
+   lbm_reduce's to FP32 rounding of the per-node terms.  Synchronises; INVALID_ARG for
+   steps < 1 or a null out; otherwise the lbm_step_batch errors, and each member's device
+   error word as lbm_reduce_batch reports it. */
+lbm_status lbm_step_batch_reduce(lbm_domain* const* doms, int32_t n, int32_t steps, double* out);
+
 /* Self-test of the bounded device-wide barrier used by lbm_step_batch (no counterpart in the
    paper): launches a small cooperative kernel whose barrier waits for `extra` CTAs that do
    not exist, so every wait expires after about limit_ms (0 < limit_ms <= 5000).  Returns

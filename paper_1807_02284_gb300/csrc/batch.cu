@@ -90,6 +90,89 @@ __global__ void __launch_bounds__(256) k_batch(const BlockView* __restrict__ vie
   }
 }
 
+// k_batch with the diagnostics fused into the last step (lbm_step_batch_reduce): in that
+// step each node adds its moments (from cell_update, into a per-thread shared-memory slot)
+// to its thread's accumulator, and every work item ends with a CTA sum (shuffle tree per
+// warp, warps in order, FP32) stored as one record of 8 doubles, records[item * 8 + value].
+// The populations, velocities and scalars are those of k_batch.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_batch_red(const BlockView* __restrict__ views,
+                                                   const BatchItem* __restrict__ items,
+                                                   int n_items, int chunk, int steps,
+                                                   BarrierState* bs, unsigned int expected_blocks,
+                                                   int* err, long long limit, double* records) {
+  __shared__ float tmp[6][256];
+  __shared__ float acc[6][256];
+  __shared__ float swarp[8][6];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const NodeMomentsOut out{&tmp[0][t], 256};
+  for (int s = 0; s < steps; ++s) {
+    const int p = s & 1;
+    const bool last = s + 1 == steps;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+      const BatchItem it = items[w];
+      const BlockView& v = views[2 * it.dom + p];
+      const uint32_t nx = (uint32_t)v.nx, nxy = (uint32_t)v.nx * (uint32_t)v.ny;
+      const uint32_t end = min((uint32_t)v.N, it.start + (uint32_t)chunk);
+      if (!last) {
+        for (uint32_t idx = it.start + t; idx < end; idx += blockDim.x) {
+          const uint32_t z = idx / nxy;
+          const uint32_t r = idx - z * nxy;
+          const uint32_t y = r / nx;
+          cell_update<T, uint32_t>(v, (int)(r - y * nx), (int)y, (int)z);
+        }
+        continue;
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) acc[i][t] = 0.0f;
+      for (uint32_t idx = it.start + t; idx < end; idx += blockDim.x) {
+        const uint32_t z = idx / nxy;
+        const uint32_t r = idx - z * nxy;
+        const uint32_t y = r / nx;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) tmp[i][t] = 0.0f;
+        cell_update<T, uint32_t, false, false, true>(v, (int)(r - y * nx), (int)y, (int)z, &out);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[i][t] += tmp[i][t];
+      }
+      float val[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) val[i] = acc[i][t];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) val[i] += __shfl_xor_sync(0xffffffffu, val[i], o);
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) swarp[wid][i] = val[i];
+      }
+      __syncthreads();
+      if (t < 8) {
+        float sum = 0.0f;
+        if (t < 6)
+          for (int k = 0; k < (int)(blockDim.x >> 5); ++k) sum += swarp[k][t];
+        records[(size_t)w * 8 + t] = (double)sum;
+      }
+      __syncthreads();
+    }
+    if (s + 1 < steps) {
+      if (!grid_barrier(bs, expected_blocks, err, limit)) return;
+      if (*((volatile int*)err) & 8) return;
+    }
+  }
+}
+
+template <typename T>
+static cudaError_t launch_batch_red_t(const BlockView* views, const BatchItem* items, int n_items,
+                                      int chunk, int steps, BarrierState* bs, int threads,
+                                      int grid, unsigned int expected, int* err, long long limit,
+                                      double* records, cudaStream_t s) {
+  void* args[] = {(void*)&views, (void*)&items, (void*)&n_items, (void*)&chunk, (void*)&steps,
+                  (void*)&bs, (void*)&expected, (void*)&err, (void*)&limit, (void*)&records};
+  return cudaLaunchCooperativeKernel((const void*)k_batch_red<T>, dim3(grid), dim3(threads),
+                                     args, 0, s);
+}
+
 template <typename T, typename IT>
 static cudaError_t launch_batch_t(const BlockView* views, const BatchItem* items, int n_items,
                                   int chunk, int steps, BarrierState* bs, int threads, int grid,
@@ -118,11 +201,12 @@ static cudaError_t launch_batch(int storage, bool i32, const BlockView* views,
   return launch_batch_t<float, uint64_t>(views, items, n_items, chunk, steps, bs, threads, grid, expected, err, limit, cooperative, s);
 }
 
-static int resident_blocks(int storage, bool i32, int threads) {
+static int resident_blocks(int storage, bool i32, int threads, bool red = false) {
   int per_sm = 0, dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const void* fn = storage == ST_FP16
+  const void* fn = red ? (storage == ST_FP16 ? (const void*)k_batch_red<__half> : (const void*)k_batch_red<float>)
+                 : storage == ST_FP16
                        ? (i32 ? (const void*)k_batch<__half, uint32_t> : (const void*)k_batch<__half, uint64_t>)
                        : (i32 ? (const void*)k_batch<float, uint32_t> : (const void*)k_batch<float, uint64_t>);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
@@ -144,6 +228,13 @@ struct BatchPlan {
   int grid = 0;
   cudaGraphExec_t exec = nullptr;
   bool captured = false;
+  // fused diagnostics (lbm_step_batch_reduce): per-item records, per-member sums (sums and
+  // error word, 8 doubles each) copied to pinned host memory by the same graph
+  bool red = false;
+  double* records = nullptr;
+  RedMember* members = nullptr;
+  double* out_dev = nullptr;
+  double* out_host = nullptr;
 };
 
 // Plans cached by the first domain of a batch.  A call with an odd step count flips every
@@ -165,7 +256,64 @@ static void free_plan(lbm_domain* dom, BatchPlan* p) {
   dom->dev_free(p->views);
   dom->dev_free(p->items);
   dom->dev_free(p->bar);
+  if (p->records) dom->dev_free(p->records);
+  if (p->members) dom->dev_free(p->members);
+  if (p->out_dev) dom->dev_free(p->out_dev);
+  if (p->out_host) cudaFreeHost(p->out_host);
   delete p;
+}
+
+// The diagnostics buffers of a plan: one record per work item, the members' item ranges and
+// error words, the per-member sums on the device and in pinned host memory.
+static lbm_status add_red_buffers(lbm_domain* const* doms, int n, BatchPlan* p) {
+  lbm_domain* d0 = doms[0];
+  std::vector<RedMember> hm(n);
+  int at = 0;
+  for (int i = 0; i < n; ++i) {
+    const Block& B = doms[i]->blocks[0];
+    const int cnt = (int)((B.N + (size_t)p->chunk - 1) / (size_t)p->chunk);
+    hm[i] = RedMember{nullptr, nullptr, doms[i]->d_err, B.N, at, cnt};
+    at += cnt;
+  }
+  if (at != p->n_items) return d0->fail(LBM_ERR_STATE, "batch work list and members disagree");
+  p->records = static_cast<double*>(d0->dev_alloc((size_t)p->n_items * 8 * sizeof(double)));
+  p->members = static_cast<RedMember*>(d0->dev_alloc((size_t)n * sizeof(RedMember)));
+  p->out_dev = static_cast<double*>(d0->dev_alloc((size_t)n * 8 * sizeof(double)));
+  if (!p->records || !p->members || !p->out_dev) return d0->fail(LBM_ERR_OOM, "batch diagnostics buffers");
+  if (cudaMallocHost(&p->out_host, (size_t)n * 8 * sizeof(double)) != cudaSuccess) {
+    p->out_host = nullptr;
+    return d0->fail(LBM_ERR_OOM, "batch diagnostics staging");
+  }
+  cudaError_t e = cudaMemcpyAsync(p->members, hm.data(), (size_t)n * sizeof(RedMember),
+                                  cudaMemcpyHostToDevice, d0->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d0->stream);
+  if (e != cudaSuccess) return d0->cuda_fail(e, "batch diagnostics upload");
+  p->red = true;
+  return LBM_OK;
+}
+
+// The work of one batched call on stream s: reset the barrier, the persistent launch, and with
+// fused diagnostics the per-member sums and their copy to pinned host memory.
+static cudaError_t enqueue_batch(lbm_domain* d0, BatchPlan* p, int steps, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(p->bar, 0, sizeof(BarrierState), s);
+  if (e != cudaSuccess) return e;
+  if (!p->red)
+    return launch_batch(d0->desc.storage, p->i32, p->views, p->items, p->n_items, p->chunk, steps,
+                        p->bar, p->threads, p->grid, (unsigned)p->grid, d0->d_err,
+                        kBarrierLimitCycles, true, s);
+  e = d0->desc.storage == ST_FP16
+          ? launch_batch_red_t<__half>(p->views, p->items, p->n_items, p->chunk, steps, p->bar,
+                                       p->threads, p->grid, (unsigned)p->grid, d0->d_err,
+                                       kBarrierLimitCycles, p->records, s)
+          : launch_batch_red_t<float>(p->views, p->items, p->n_items, p->chunk, steps, p->bar,
+                                      p->threads, p->grid, (unsigned)p->grid, d0->d_err,
+                                      kBarrierLimitCycles, p->records, s);
+  const int n = (int)p->serials.size();
+  if (e == cudaSuccess) e = launch_reduce_item_records(p->records, p->members, n, p->out_dev, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->out_host, p->out_dev, (size_t)n * 8 * sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
+  return e;
 }
 
 void release_batch_plan(lbm_domain* dom) {
@@ -251,11 +399,13 @@ static lbm_status tune_chunk(lbm_domain* const* doms, int n, int* chunk_out, int
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t steps) {
+static lbm_status step_batch(lbm_domain* const* doms, int32_t n, int32_t steps, double* out) {
   if (!doms || n <= 0 || !doms[0]) return LBM_ERR_INVALID_ARG;
   lbm_domain* d0 = doms[0];
   cudaSetDevice(d0->desc.device);
+  const bool red = out != nullptr;
   if (steps < 0) return d0->fail(LBM_ERR_INVALID_ARG, "negative step count");
+  if (red && steps < 1) return d0->fail(LBM_ERR_INVALID_ARG, "lbm_step_batch_reduce needs at least one step");
   for (int i = 0; i < n; ++i) {
     if (!doms[i]) return d0->fail(LBM_ERR_INVALID_ARG, "null domain in batch");
     for (int j = 0; j < i; ++j)
@@ -290,7 +440,7 @@ extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t
   BatchPlan* p = nullptr;
   for (size_t k = 0; k < cache->plans.size() && !p; ++k) {
     BatchPlan* q = cache->plans[k];
-    bool same = q->steps == steps && (int)q->serials.size() == n;
+    bool same = q->steps == steps && q->red == red && (int)q->serials.size() == n;
     for (int i = 0; i < n && same; ++i)
       same = q->serials[i] == doms[i]->serial && q->curs[i] == doms[i]->blocks[0].cur;
     if (same) {
@@ -314,20 +464,21 @@ extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t
     p = new (std::nothrow) BatchPlan();
     if (!p) return d0->fail(LBM_ERR_OOM, "out of host memory");
     lbm_status st = build_plan(doms, n, cache->chunk, p);
+    if (st == LBM_OK && red) {
+      p->chunk = cache->chunk;
+      st = add_red_buffers(doms, n, p);
+    }
     if (st != LBM_OK) { free_plan(d0, p); return st; }
     p->threads = cache->threads;
     cache->plans.push_back(p);
     p->steps = steps;
-    p->grid = std::min(resident_blocks(d0->desc.storage, p->i32, p->threads), std::max(1, p->n_items));
-    // capture: reset the barrier, then the cooperative persistent launch
+    p->grid = std::min(resident_blocks(d0->desc.storage, p->i32, p->threads, red), std::max(1, p->n_items));
+    // capture: reset the barrier, then the cooperative persistent launch (and the fused
+    // diagnostics' sums and read-back)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e1 = cudaMemsetAsync(p->bar, 0, sizeof(BarrierState), s);
-      if (e1 == cudaSuccess)
-        e1 = launch_batch(d0->desc.storage, p->i32, p->views, p->items, p->n_items, p->chunk,
-                          steps, p->bar, p->threads, p->grid, (unsigned)p->grid, d0->d_err,
-                          kBarrierLimitCycles, true, s);
+      cudaError_t e1 = enqueue_batch(d0, p, steps, s);
       cudaError_t e2 = cudaStreamEndCapture(s, &g);
       if (e1 == cudaSuccess && e2 == cudaSuccess && g) {
         e = cudaGraphInstantiate(&p->exec, g, 0);
@@ -338,16 +489,7 @@ extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t
     }
     cudaGetLastError();  // a capture the driver refused leaves the direct launch below
   }
-  cudaError_t e;
-  if (p->captured) {
-    e = cudaGraphLaunch(p->exec, s);
-  } else {
-    e = cudaMemsetAsync(p->bar, 0, sizeof(BarrierState), s);
-    if (e == cudaSuccess)
-      e = launch_batch(d0->desc.storage, p->i32, p->views, p->items, p->n_items, p->chunk, steps,
-                       p->bar, p->threads, p->grid, (unsigned)p->grid, d0->d_err,
-                       kBarrierLimitCycles, true, s);
-  }
+  cudaError_t e = p->captured ? cudaGraphLaunch(p->exec, s) : enqueue_batch(d0, p, steps, s);
   if (e != cudaSuccess) return d0->cuda_fail(e, "batched launch");
   for (int i = 0; i < n; ++i) {
     Block& B = doms[i]->blocks[0];
@@ -363,8 +505,36 @@ extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t
       if (doms[i]->stream != s) cudaStreamWaitEvent(doms[i]->stream, done, 0);
     cudaEventDestroy(done);
   }
-  d0->post_error_probe();
-  return LBM_OK;
+  if (!red) {
+    d0->post_error_probe();
+    return LBM_OK;
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return d0->cuda_fail(e, "cudaStreamSynchronize");
+  lbm_status first = LBM_OK;
+  for (int i = 0; i < n; ++i) {
+    const double* r = p->out_host + 8 * (size_t)i;
+    double* o = out + 5 * (size_t)i;
+    o[0] = r[0] + r[1];
+    o[1] = r[2];
+    o[2] = r[3];
+    o[3] = r[4];
+    o[4] = r[5];
+    *doms[i]->h_err = (int)r[6];
+    const lbm_status st = doms[i]->error_status();
+    if (st != LBM_OK && first == LBM_OK) first = st;
+  }
+  return first;
+}
+
+extern "C" lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t steps) {
+  return step_batch(doms, n, steps, nullptr);
+}
+
+extern "C" lbm_status lbm_step_batch_reduce(lbm_domain* const* doms, int32_t n, int32_t steps,
+                                            double* out) {
+  if (!out) return LBM_ERR_INVALID_ARG;
+  return step_batch(doms, n, steps, out);
 }
 
 // Self-test of the bounded device barrier: a cooperative kernel waits for `extra` more CTAs

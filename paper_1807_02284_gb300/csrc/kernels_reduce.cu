@@ -169,6 +169,12 @@ __global__ void __launch_bounds__(256) k_reduce_items_final(const double* record
   if (lane == 0) out[(size_t)m * 8 + 6] = (double)*mb.err;
 }
 
+cudaError_t launch_reduce_item_records(const double* records, const RedMember* members, int n,
+                                      double* out, cudaStream_t s) {
+  k_reduce_items_final<<<(n + 7) / 8, 256, 0, s>>>(records, members, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_items(int storage, const RedItem* items, int n_items,
                                 const RedMember* members, int n_members, double* records,
                                 double* out, cudaStream_t s) {

@@ -144,6 +144,10 @@ struct RedItem {
 cudaError_t launch_reduce_items(int storage, const RedItem* items, int n_items,
                                 const RedMember* members, int n_members, double* records,
                                 double* out, cudaStream_t s);
+// the per-member sums of item records written by another kernel (the batched step's fused
+// diagnostics): member i's items are records first_item .. first_item + n_items - 1
+cudaError_t launch_reduce_item_records(const double* records, const RedMember* members, int n,
+                                      double* out, cudaStream_t s);
 // the six sums over `n` per-CTA records of 8 doubles (partials[8 i + value]); the buffer
 // holds 8 n + 6 * 128 doubles (the records, then the first stage's sums)
 cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaStream_t s);

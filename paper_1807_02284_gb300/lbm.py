@@ -85,6 +85,7 @@ _SIGNATURES = {
     "lbm_step_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
     "lbm_get_block_info": (_I, [_P, _I, C.POINTER(lbm_block_info)]),
     "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
+    "lbm_step_batch_reduce": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
     "lbm_reduce_batch": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
     "lbm_set_inflow_batch": (_I, [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(C.c_int32)]),
     "lbm_set_tape": (_I, [_P, _I]),
@@ -357,6 +358,18 @@ def step_batch(domains: Sequence[Domain], steps: int):
     st = lib.lbm_step_batch(arr, len(domains), int(steps))
     if st != LBM_OK:
         domains[0].check(st)
+
+
+def step_batch_reduce(domains: Sequence[Domain], steps: int) -> np.ndarray:
+    """``lbm_step_batch_reduce``: the batched steps, then every member's five diagnostics
+    (shape (n, 5)) summed by the last step's own kernel."""
+    lib = load()
+    arr = (C.c_void_p * len(domains))(*[d.handle.value for d in domains])
+    out = (C.c_double * (5 * len(domains)))()
+    st = lib.lbm_step_batch_reduce(arr, len(domains), int(steps), out)
+    if st != LBM_OK:
+        domains[0].check(st)
+    return np.array(list(out)).reshape(len(domains), 5)
 
 
 def set_inflow_batch(domains: Sequence[Domain], records: Sequence[np.ndarray]):

@@ -212,3 +212,33 @@ def test_set_inflow_batch_equals_per_member_calls(lib):
     joint[0].sync()
     for d in joint + single:
         d.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_step_batch_reduce_state_and_values(lib, storage):
+    """lbm_step_batch_reduce: the states of lbm_step_batch, and every member's diagnostics
+    within FP32 rounding of lbm_reduce's (FP16: of the FP32 state before its rounding)."""
+    from paper_1807_02284_gb300 import lbm
+    scenes = _scenes(6, seed=45)
+    a = [gpu_domain(s, storage) for s in scenes]
+    b = [gpu_domain(s, storage) for s in scenes]
+    r = lbm.step_batch_reduce(a, 5)
+    lbm.step_batch(b, 5)
+    tol_m, tol_j = (1e-7, 1e-5) if storage == "fp32" else (1e-5, 1e-3)
+    for i, (x, y) in enumerate(zip(a, b)):
+        assert np.array_equal(x.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32),
+                              y.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32))
+        ri = y.reduce()
+        assert abs(r[i][0] - ri[0]) <= tol_m * ri[0]
+        assert np.abs(r[i][1:] - ri[1:]).max() <= tol_j * max(1.0, np.abs(ri[1:]).max())
+    for k in range(3):                                   # single steps, both level parities
+        r = lbm.step_batch_reduce(a, 1)
+        lbm.step_batch(b, 1)
+        for i, y in enumerate(b):
+            ri = y.reduce()
+            assert abs(r[i][0] - ri[0]) <= tol_m * ri[0]
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.step_batch_reduce(a, 0)
+    assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
+    for d in a + b:
+        d.close()
