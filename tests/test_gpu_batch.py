@@ -171,8 +171,9 @@ def test_bounded_barrier_reports_timeout_and_context_survives(lib):
 
 def test_set_inflow_batch_equals_per_member_calls(lib):
     """One staged upload and launch for the inflow records of members sharing a stream: the
-    same flags and velocity levels as the per-member lbm_set_boundary calls, and a bad
-    record is reported by its own member only."""
+    same flags, velocity levels and populations as for members on their own streams (which
+    take the per-member lbm_set_boundary calls), and a bad record is reported by its own
+    member only."""
     import torch
     from paper_1807_02284_gb300 import lbm
     from tests.helpers import f32
@@ -194,9 +195,8 @@ def test_set_inflow_batch_equals_per_member_calls(lib):
         r["ux"] *= (1.0 + 0.05 * rng.random(r.size)).astype(np.float32)
         recs.append(r)
     recs[2] = recs[2][:0]                           # a member without records
-    lbm.set_inflow_batch(joint, recs)
-    for d, r in zip(single, recs):
-        d.set_inflow(r)
+    lbm.set_inflow_batch(joint, recs)                # one staged upload and launch
+    lbm.set_inflow_batch(single, recs)               # own streams: the per-member calls
     lbm.step_batch(joint, 3)
     lbm.step_batch(single, 3)
     for a, b in zip(joint, single):
