@@ -225,10 +225,81 @@ __device__ __forceinline__ void put_sender(const AdjArgs& a, uint32_t N, uint32_
 
 // MINB: CTAs per SM the register allocation is bounded for (3: no spills; 4: some spills,
 // more warps in flight); the faster one is chosen at run time.
+// The populations of a wall node (face wall or obstacle surface) pulled from beyond the wall:
+// the set wall_regularize completes (same tests).
+template <typename IT>
+__device__ __forceinline__ unsigned wall_unknowns(const BlockView& v, int x, int y, int z,
+                                                  uint8_t fl, const Nbr<IT>& n) {
+  const bool lo[3] = {(v.walls & 1) && x == 0, (v.walls & 4) && y == 0, (v.walls & 16) && z == 0};
+  const bool hi[3] = {(v.walls & 2) && x == v.nx - 1, (v.walls & 8) && y == v.ny - 1,
+                      (v.walls & 32) && z == v.nz - 1};
+  unsigned unk = 0u;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const int c[3] = {cxk(k), cyk(k), czk(k)};
+    bool u = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u |= (lo[a] && c[a] == 1) || (hi[a] && c[a] == -1);
+    if (u) unk |= 1u << k;
+  }
+  if (fl & F_OBST_WALL) unk |= solid_sources<IT>(v.flags, n);
+  return unk;
+}
+
+// Transpose of wall_regularize (a linear map of the pulled populations for a fixed unknown
+// set): A holds the adjoint of the rebuilt populations on entry and of the pulled ones on
+// return.  Forward: d'_k = d_k (known), d_opp(k) (unknown, opposite known), excluded (both
+// unknown, weight wb); drho = sum d' / (1 - wb); neq_k = d'_k - w_k drho (0 when both);
+// Pi = sum c c neq; out_k = w_k (drho + 4.5 (c c : Pi - tr(Pi) / 3)).
+template <typename IT>
+__device__ __forceinline__ void wall_regularize_vjp(float (&A)[27], const BlockView& v, int x,
+                                                    int y, int z, uint8_t fl, const Nbr<IT>& n) {
+  const unsigned unk = wall_unknowns<IT>(v, x, y, z, fl, n);
+  float wb = 0.0f, drb = 0.0f;
+  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;   // adjoint of Pi
+  const float third = 1.0f / 3.0f;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    if (((unk >> k) & 1u) && ((unk >> (26 - k)) & 1u)) wb += wk(k);
+    const float cx = (float)cxk(k), cy = (float)cyk(k), cz = (float)czk(k);
+    const float a = A[k];
+    drb = fmaf(wk(k), a, drb);
+    const float q = 4.5f * wk(k) * a;
+    pxx = fmaf(q, cx * cx - third, pxx);
+    pyy = fmaf(q, cy * cy - third, pyy);
+    pzz = fmaf(q, cz * cz - third, pzz);
+    pxy = fmaf(q, 2.0f * cx * cy, pxy);
+    pxz = fmaf(q, 2.0f * cx * cz, pxz);
+    pyz = fmaf(q, 2.0f * cy * cz, pyz);
+  }
+  float db[27];                          // adjoint of the completed set d'
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const bool both = ((unk >> k) & 1u) && ((unk >> (26 - k)) & 1u);
+    const float cx = (float)cxk(k), cy = (float)cyk(k), cz = (float)czk(k);
+    const float nb = cx * cx * pxx + cy * cy * pyy + cz * cz * pzz + cx * cy * pxy +
+                     cx * cz * pxz + cy * cz * pyz;
+    db[k] = both ? 0.0f : nb;
+    if (!both) drb = fmaf(-wk(k), nb, drb);
+  }
+  const float sb = drb / (1.0f - wb);
+#pragma unroll
+  for (int k = 0; k < 27; ++k) A[k] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const bool uk = (unk >> k) & 1u, uo = (unk >> (26 - k)) & 1u;
+    if (uk && uo) continue;
+    const float g = db[k] + sb;
+    if (uk) A[26 - k] += g;              // taken from the opposite population
+    else A[k] += g;
+  }
+}
+
 // OPEN: some face of the block is open (face slots accumulate; see FaceMask).  ACC: the
 // adjoints of the input level are added to (multi-block reverse), and scale-boundary (ghost)
-// nodes, which the step does not update, are left to the mapping that wrote them.
-template <int MINB, bool OPEN, bool ACC>
+// nodes, which the step does not update, are left to the mapping that wrote them.  WALLS:
+// the block has wall faces or obstacle-surface walls (wall_regularize and its transpose).
+template <int MINB, bool OPEN, bool ACC, bool WALLS>
 __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   const BlockView& v = a.fwd;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,8 +359,14 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   // ---- forward recompute up to the central moments
   float K[27];
   pull_all<float, uint32_t>(K, din, N, n);
-  const bool near = (fl & F_NEAR_SOLID) != 0;
+  // as in cell_update: an obstacle wall node completes what comes from inside the obstacle
+  // itself (no bounce-back), every wall node is regularized before the collision
+  const bool near = (fl & F_NEAR_SOLID) != 0 && !(WALLS && (fl & F_OBST_WALL));
   if (near) bounce_back<float, uint32_t>(K, din, N, v.flags, n, idx);
+  const bool wall = WALLS && (fl & (F_WALL | F_OBST_WALL));
+  if constexpr (WALLS) {
+    if (wall) wall_regularize<uint32_t>(K, v, x, y, z, fl, n);
+  }
   raw_moments(K);
   const float drho = K[kap(0, 0, 0)];
   const float inv = __frcp_rn(1.0f + drho);
@@ -328,6 +405,9 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   for (int k = 0; k < 27; ++k) A[k] = a.lam_in[(uint32_t)k * N + idx];
   float kbar[4] = {0.f, 0.f, 0.f, 0.f};    // d/d(keep factor) of the high-order groups
   collide_vjp(K, A, drho, ux, uy, uz, inv, kf, ub, kbar);
+  if constexpr (WALLS) {
+    if (wall) wall_regularize_vjp<uint32_t>(A, v, x, y, z, fl, n);
+  }
   push_all<OPEN, ACC>(A, a.lam_out, N, n, idx, v.flags, near, face_mask<OPEN>(v, x, y, z));
 
   // ---- adjoint of the adaptive factor: K_g = 1 - 1/(phi nu3_g + 1/2)
@@ -346,18 +426,25 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = v.rp.adaptive ? mu_scale * diff[i] : 0.0f;
 }
 
+template <bool WALLS>
+static void launch_pass_a_t(const AdjArgs& a, int minb, bool open, dim3 grd, dim3 blk,
+                            cudaStream_t s, bool acc) {
+  if (acc) {   // multi-block reverse: 3 CTAs/SM, open faces (every refined block has them)
+    if (open) k_adj_a<3, true, true, WALLS><<<grd, blk, 0, s>>>(a);
+    else k_adj_a<3, false, true, WALLS><<<grd, blk, 0, s>>>(a);
+  } else if (open) {
+    if (minb == 4) k_adj_a<4, true, false, WALLS><<<grd, blk, 0, s>>>(a);
+    else k_adj_a<3, true, false, WALLS><<<grd, blk, 0, s>>>(a);
+  } else {
+    if (minb == 4) k_adj_a<4, false, false, WALLS><<<grd, blk, 0, s>>>(a);
+    else k_adj_a<3, false, false, WALLS><<<grd, blk, 0, s>>>(a);
+  }
+}
+
 static void launch_pass_a(const AdjArgs& a, int minb, bool open, dim3 grd, dim3 blk, cudaStream_t s,
                           bool acc = false) {
-  if (acc) {   // multi-block reverse: 3 CTAs/SM, open faces (every refined block has them)
-    if (open) k_adj_a<3, true, true><<<grd, blk, 0, s>>>(a);
-    else k_adj_a<3, false, true><<<grd, blk, 0, s>>>(a);
-  } else if (open) {
-    if (minb == 4) k_adj_a<4, true, false><<<grd, blk, 0, s>>>(a);
-    else k_adj_a<3, true, false><<<grd, blk, 0, s>>>(a);
-  } else {
-    if (minb == 4) k_adj_a<4, false, false><<<grd, blk, 0, s>>>(a);
-    else k_adj_a<3, false, false><<<grd, blk, 0, s>>>(a);
-  }
+  if (a.fwd.walls) launch_pass_a_t<true>(a, minb, open, grd, blk, s, acc);
+  else launch_pass_a_t<false>(a, minb, open, grd, blk, s, acc);
 }
 
 template <bool ACC>
@@ -462,7 +549,7 @@ __global__ void k_adj_init(const float* __restrict__ d0, const float* __restrict
                            const uint8_t* __restrict__ flags, const float* __restrict__ lam,
                            const float* __restrict__ ups, float* __restrict__ out, uint32_t N) {
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
-    if (flags[idx] & F_SOLID) {
+    if (flags[idx] & (F_SOLID | F_OBST_WALL)) {   // obstacle voxels start at rest
       out[idx] = out[N + idx] = out[2 * N + idx] = 0.0f;
       continue;
     }
@@ -767,7 +854,6 @@ lbm_status tape_before_step(lbm_domain* dom) {
 static lbm_status adjoint_supported(lbm_domain* dom) {
   for (const Block& B : dom->blocks)
     if (B.far) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint does not cover far-field blocks");
-  if (dom->walls) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint does not cover no-slip walls");
   if (dom->desc.storage != LBM_FP32) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP32 storage");
   if (dom->desc.grad_mode != LBM_GRAD_LAGGED)
     return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint covers the lagged-gradient relaxation");

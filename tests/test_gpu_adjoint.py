@@ -153,6 +153,45 @@ def test_open_faces_adjoint_matches_fp64_oracle(lib, plume):
     assert e <= 1e-3 and ef <= 1e-3
 
 
+@pytest.mark.parametrize("kind", ["faces", "obstacles", "both"])
+def test_adjoint_with_walls_matches_fp64_oracle(lib, kind):
+    """No-slip walls (the Sec. 6.1 regularized wall): wall faces (floor and lid), obstacle
+    surfaces as walls (a sphere and a plate one voxel thick), or both; the transpose of the
+    wall completion and rebuild against the FP64 oracle's gradient."""
+    import dataclasses
+    from paper_1807_02284_gb300 import lbm
+    n, steps, every = 12, 10, 3
+    sc, target = synth.adjoint_scene(n=n, seed=15, nu=0.01, amp=0.05)
+    sc.periodic = (True, True, False)
+    b = sc.blocks[0]
+    faces = (False,) * 4 + ((True, True) if kind != "obstacles" else (False, False))
+    obst = kind != "faces"
+    if obst:
+        synth.voxelise_spheres(b, [(6.5, 5.5, 6.0, 2.2)])
+        b.flags[3:8, 2:5, 10] |= synth.SOLID
+        b.rho0[(b.flags & synth.SOLID) != 0] = 1.0
+    dom = _domain(sc)
+    dom.set_walls(faces, obstacles=obst)
+    dom.init_macro(f32(b.u0), rho=f32(b.rho0), c=f32(b.c0))
+    dom.set_tape(every)
+    dom.step(steps)
+    c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64)
+    dLdc = torch.tensor(c - target.reshape(-1), dtype=torch.float32, device="cuda")
+    g = torch.empty(3 * b.flags.size, dtype=torch.float32, device="cuda")
+    dom.adjoint_step(steps, dLdc, g)
+    dom.sync()
+    dom.close()
+    gg = g.cpu().numpy().astype(np.float64).reshape(b.u0.shape)
+    p = dataclasses.replace(grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=sc.adaptive),
+                            walls=faces, obstacle_walls=obst)
+    _, go, _ = oadj.loss_and_grad(f32(b.u0).astype(np.float64), f32(b.rho0).astype(np.float64),
+                                  f32(b.c0).astype(np.float64), b.flags, p, steps, target)
+    go = go.numpy()
+    e = rel(gg, go)
+    print(f"walls ({kind}): rel L2 {e:.2e}")
+    assert e <= 1e-3
+
+
 def test_adjoint_config5_copy_32_cubed_200_steps(lib):
     """The smoke-control problem scaled to 32^3 (every length / 4), nu = 1e-3, 200 steps,
     checkpoint every 20: FP32 GPU adjoint against the FP64 oracle gradient."""
