@@ -66,34 +66,39 @@ def loss_only(u0, rho0, c0, flags, p: grid.Params, steps: int, c_target, u_targe
 
 # ---------------------------------------------------------------- continuous-scale domains
 
-def ms_forward(scene, u0s, steps: int, f32_inputs=True):
-    """Runs a continuous-scale domain (oracle.coupling.MultiScale: s0 plus refined blocks)
-    from the equilibria of (rho0_b, u0s[b]) for `steps` reference steps; returns it."""
+def ms_forward(scene, u0s, steps: int, f32_inputs=True, far=()):
+    """Runs a continuous-scale domain (oracle.coupling.MultiScale: s0, refined blocks, and
+    the far-field blocks `far` (synth Blocks, h > 1) added in order after them) from the
+    equilibria of (rho0_b, u0s[b]) for `steps` reference steps; returns it."""
     from . import coupling
     ms = coupling.MultiScale.build(scene, f32_inputs=f32_inputs)
     conv = (lambda a: torch.as_tensor(np.asarray(a, np.float32).astype(np.float64))) \
         if f32_inputs else (lambda a: torch.as_tensor(np.asarray(a, np.float64)))
     for b, sb, u in zip(ms.blocks, scene.blocks, u0s):
         b.state = grid.init_state(conv(sb.rho0), u, conv(sb.c0), b.state.flags)
+    for fb, u in zip(far, u0s[len(scene.blocks):]):
+        i = ms.add_far_block(fb.origin, fb.h, fb.dims, fb.rho0, fb.u0, fb.c0, fb.flags)
+        ms.blocks[i].state = grid.init_state(conv(fb.rho0), u, conv(fb.c0), ms.blocks[i].state.flags)
     for _ in range(steps):
         ms.step()
     return ms
 
 
-def ms_loss_and_grad(scene, steps: int, c_target):
+def ms_loss_and_grad(scene, steps: int, c_target, far=()):
     """L = 1/2 sum over the reference block of (c_T - c_target)^2 and its FP64 gradients
     with respect to every block's initial velocity (reverse-mode through the whole
-    Algorithm 1 schedule: steps, prior- and post-mapping, temporal alignment)."""
+    Algorithm 1 schedule: steps, prior- and post-mapping, temporal alignment, and the
+    far-field blocks' steps and overlap / boundary mappings)."""
     u0s = [torch.as_tensor(np.asarray(b.u0, np.float32).astype(np.float64)).clone().requires_grad_(True)
-           for b in scene.blocks]
-    ms = ms_forward(scene, u0s, steps)
+           for b in list(scene.blocks) + list(far)]
+    ms = ms_forward(scene, u0s, steps, far=far)
     L = 0.5 * ((ms.blocks[0].state.c - torch.as_tensor(np.asarray(c_target), dtype=DT)) ** 2).sum()
     grads = torch.autograd.grad(L, u0s)
     return float(L.detach()), [g.detach() for g in grads], ms
 
 
-def ms_loss_only(scene, u0s, steps: int, c_target):
+def ms_loss_only(scene, u0s, steps: int, c_target, far=()):
     with torch.no_grad():
         ms = ms_forward(scene, [torch.as_tensor(np.asarray(u, np.float64)) for u in u0s], steps,
-                        f32_inputs=False)
+                        f32_inputs=False, far=far)
         return float(0.5 * ((ms.blocks[0].state.c - torch.as_tensor(np.asarray(c_target), dtype=DT)) ** 2).sum())

@@ -852,8 +852,6 @@ lbm_status tape_before_step(lbm_domain* dom) {
 }
 
 static lbm_status adjoint_supported(lbm_domain* dom) {
-  for (const Block& B : dom->blocks)
-    if (B.far) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint does not cover far-field blocks");
   if (dom->desc.storage != LBM_FP32) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP32 storage");
   if (dom->desc.grad_mode != LBM_GRAD_LAGGED)
     return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint covers the lagged-gradient relaxation");
@@ -904,8 +902,40 @@ static std::vector<MsOp> ms_ops(const lbm_domain* dom, std::vector<int>& cur) {
   s0.kind = 0; s0.b = 0; s0.in = 0; s0.out = 1;
   ops.push_back(s0);
   cur[0] = 1;
+  // far-field blocks (Sec. 4.2.4-4.2.5): their aligned steps, then inner to outer the nodes
+  // inside each child's interior from the child, then outer to inner each child's outer
+  // layer from its far block (the refined blocks' operations below read only levels these
+  // leave alone, so the sequential order computes the forward's values)
+  std::vector<int> far;
+  for (int b = 1; b < nb; ++b)
+    if (dom->blocks[b].far) far.push_back(b);
+  for (int f : far) {
+    const Block& F = dom->blocks[f];
+    MsOp s;
+    s.kind = 1; s.b = f; s.in = 0; s.out = 1; s.al = 0;
+    s.al0 = 0.0f;
+    s.al1 = (float)(1.0 - 1.0 / F.h);
+    s.al2 = (float)(1.0 / F.h);
+    ops.push_back(s);
+    cur[f] = 1;
+  }
+  for (int f : far) {
+    const MapTable& t = dom->blocks[f].far_in;
+    MsOp m;
+    m.kind = 2; m.t = &t; m.src = t.src; m.lo = m.hi = cur[t.src]; m.theta = 0.0f;
+    m.dst = f; m.dlv = cur[f]; m.skip = F_SOLID | F_GHOST;
+    ops.push_back(m);
+  }
+  for (size_t k = far.size(); k-- > 0;) {
+    const MapTable& t = dom->blocks[far[k]].far_out;
+    MsOp m;
+    m.kind = 2; m.t = &t; m.src = far[k]; m.lo = m.hi = cur[far[k]]; m.theta = 0.0f;
+    m.dst = t.dst; m.dlv = cur[t.dst]; m.skip = F_SOLID | F_INFLOW;
+    ops.push_back(m);
+  }
   for (int b = 1; b < nb; ++b) {
     const Block& B = dom->blocks[b];
+    if (B.far) continue;
     const int P = B.prior.src, L = 0, A = 1, Bv = 2;
     const bool exact = B.integer_ratio && std::fabs(B.substeps * B.h - 1.0) < 1e-9;
     auto prior = [&](float theta, int dlv) {

@@ -106,3 +106,29 @@ def test_oracle_multiscale_gradient_matches_central_differences():
     ad1 = float((grads[1].numpy() * vs[1]).sum())
     assert abs(ad1) > 1e-6 * abs(ad)              # the refined block's start matters
     assert abs(fd - ad) <= 2e-6 * abs(fd), (fd, ad)
+
+
+def test_oracle_farfield_gradient_matches_central_differences():
+    """The reference block inside a far-field block (h = 1.5: the far block's aligned step,
+    the overlap mapping into it and the boundary mapping out of it): the gradient of the
+    reference block's final scalar loss with respect to both blocks' initial velocities
+    agrees with central differences along a direction, and the far block's start matters."""
+    sc = synth.random_scene(dims=(12, 10, 10), seed=47, periodic=(False, False, False),
+                            spheres=[(6.0, 5.0, 5.0, 1.6)], nu=0.01)
+    fb = synth.far_block(sc.blocks[0], 1.5, 4.0, seed=6, amp=0.03)
+    target = np.zeros(sc.blocks[0].shape_zyx)
+    steps = 3
+    L, grads, _ = adjoint.ms_loss_and_grad(sc, steps, target, far=(fb,))
+    assert len(grads) == 2
+    rng = np.random.default_rng(5)
+    blocks = list(sc.blocks) + [fb]
+    vs = [rng.standard_normal(b.u0.shape) for b in blocks]
+    u0 = [np.asarray(b.u0, np.float32).astype(np.float64) for b in blocks]
+    eps = 1e-7
+    lp = adjoint.ms_loss_only(sc, [u + eps * v for u, v in zip(u0, vs)], steps, target, far=(fb,))
+    lm = adjoint.ms_loss_only(sc, [u - eps * v for u, v in zip(u0, vs)], steps, target, far=(fb,))
+    fd = (lp - lm) / (2 * eps)
+    ad = sum(float((g.numpy() * v).sum()) for g, v in zip(grads, vs))
+    ad1 = float((grads[1].numpy() * vs[1]).sum())
+    assert abs(ad1) > 1e-6 * abs(ad)              # the far block's start matters
+    assert abs(fd - ad) <= 2e-6 * abs(fd), (fd, ad)
