@@ -352,8 +352,9 @@ lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every);
    is a function of block 0's final state, dL_du0 is block 0's gradient and
    lbm_adjoint_block_grad returns the other blocks'.  No-slip walls (wall faces and
    obstacle-surface walls, LBM_BC_WALLS) are reversed through the exact transpose of their
-   completion and rebuild.  FP32 storage and the lagged-gradient (or fixed) relaxation only;
-   far-field blocks are not covered (UNSUPPORTED otherwise).  Not in the paper. */
+   completion and rebuild, far-field blocks through their aligned steps and overlap and
+   boundary mappings.  FP32 storage and the lagged-gradient (or fixed) relaxation only
+   (UNSUPPORTED otherwise).  Not in the paper. */
 lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dscalar_final,
                             const float* dL_du_final, float* dL_du0, float* dL_dinflow);
 
