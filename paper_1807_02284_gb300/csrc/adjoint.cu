@@ -127,9 +127,13 @@ __device__ __forceinline__ void push_all(const float (&A)[27], float* __restrict
 // overwritten), A the adjoint of the post-collision populations on entry and the adjoint of
 // the pre-collision populations on return; the velocity terms are added to ub and the
 // adjoint of the keep factors of the high-order groups to kbar.
+// With `local` set (the strain-rate mode of the adaptive factor), the factor's input g is
+// local_strain of the central moments K, so the keep factors' adjoint flows back into K, rho
+// and u here (between the relaxation's transpose and the shifts').
 __device__ __forceinline__ void collide_vjp(float (&K)[27], float (&A)[27], float drho, float ux,
                                             float uy, float uz, float inv, const Keep& kf,
-                                            float (&ub)[3], float (&kbar)[4]) {
+                                            float (&ub)[3], float (&kbar)[4],
+                                            const RelaxParams* local = nullptr, float g = 0.0f) {
   float T[27];
   // the inverse sweeps ran z, y, x: undo x first; its input is inv_y(inv_z(relaxed))
 #pragma unroll
@@ -153,6 +157,41 @@ __device__ __forceinline__ void collide_vjp(float (&K)[27], float (&A)[27], floa
   ub[1] += bar[2];
   ub[2] += bar[3];
   float drhob = bar[0];
+  if (local && g > 0.0f && g * local->inv_gmax < 1.0f) {
+    // g = (3 S_nu / (2 rho)) sqrt(2 ss), ss = |P|^2 of the non-equilibrium second central
+    // moments P_ab = K_ab - K^eq_ab (see local_strain): dg/dP_aa = g P_aa / ss,
+    // dg/dP_ab = 2 g P_ab / ss (a != b), dg/d(rho - 1) = -g / rho - sum_a dg/dP_aa / 3,
+    // dg/du_a = sum_b dg/dP_ab dP_ab/du_a
+    float phib = 0.0f;
+#pragma unroll
+    for (int gi = 0; gi < 4; ++gi) {
+      const float S = 1.0f - kf.g[gi];
+      phib = fmaf(kbar[gi], local->nuh3[gi] * S * S, phib);
+    }
+    const float gb = phib * local->a * local->inv_gmax;   // phi = a g / g_max + b below the clamp
+    const float dr3 = drho * (1.0f / 3.0f);
+    const float pxx = K[kap(2, 0, 0)] - (dr3 - ux * ux);
+    const float pyy = K[kap(0, 2, 0)] - (dr3 - uy * uy);
+    const float pzz = K[kap(0, 0, 2)] - (dr3 - uz * uz);
+    const float pxy = K[kap(1, 1, 0)] + ux * uy;
+    const float pxz = K[kap(1, 0, 1)] + ux * uz;
+    const float pyz = K[kap(0, 1, 1)] + uy * uz;
+    const float ss = fmaf(pxx, pxx, fmaf(pyy, pyy, pzz * pzz)) +
+                     2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz));
+    if (ss > 0.0f) {
+      const float c = gb * g / ss;
+      A[kap(2, 0, 0)] = fmaf(c, pxx, A[kap(2, 0, 0)]);
+      A[kap(0, 2, 0)] = fmaf(c, pyy, A[kap(0, 2, 0)]);
+      A[kap(0, 0, 2)] = fmaf(c, pzz, A[kap(0, 0, 2)]);
+      A[kap(1, 1, 0)] = fmaf(2.0f * c, pxy, A[kap(1, 1, 0)]);
+      A[kap(1, 0, 1)] = fmaf(2.0f * c, pxz, A[kap(1, 0, 1)]);
+      A[kap(0, 1, 1)] = fmaf(2.0f * c, pyz, A[kap(0, 1, 1)]);
+      drhob -= c * (pxx + pyy + pzz) * (1.0f / 3.0f) + gb * g * inv;
+      ub[0] += 2.0f * c * (ux * pxx + uy * pxy + uz * pxz);
+      ub[1] += 2.0f * c * (uy * pyy + ux * pxy + uz * pyz);
+      ub[2] += 2.0f * c * (uz * pzz + ux * pxz + uy * pyz);
+    }
+  }
   // the shifts ran x, y, z: undo z first; its input is unshift_z(K)
   unshift_axis<9>(K, uz);
   shift_axis_vjp<9>(K, A, uz, ub[2]);
@@ -374,7 +413,8 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   put_sender(a, N, idx, (fl & F_SCALAR_SRC) ? 0.0f : a.gam_in[idx], ux, uy, uz);
   float diff[9];
   float g = 0.0f;
-  if (v.rp.adaptive) {
+  const bool local = v.rp.adaptive && v.rp.local;
+  if (v.rp.adaptive && !local) {
     float s = 0.0f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -387,10 +427,11 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
     }
     g = 0.5f * sqrtf(s);
   }
-  const Keep kf = keep_factors(v.rp, g);
   shift_axis<1>(K, ux);
   shift_axis<3>(K, uy);
   shift_axis<9>(K, uz);                  // K = central moments before relaxation
+  if (local) g = local_strain(K, drho, ux, uy, uz, v.rp.s_nu);
+  const Keep kf = keep_factors(v.rp, g);
 
   // ---- adjoint of the stored velocity and of the scalar step
   float ub[3];
@@ -404,15 +445,15 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
 #pragma unroll
   for (int k = 0; k < 27; ++k) A[k] = a.lam_in[(uint32_t)k * N + idx];
   float kbar[4] = {0.f, 0.f, 0.f, 0.f};    // d/d(keep factor) of the high-order groups
-  collide_vjp(K, A, drho, ux, uy, uz, inv, kf, ub, kbar);
+  collide_vjp(K, A, drho, ux, uy, uz, inv, kf, ub, kbar, local ? &v.rp : nullptr, g);
   if constexpr (WALLS) {
     if (wall) wall_regularize_vjp<uint32_t>(A, v, x, y, z, fl, n);
   }
   push_all<OPEN, ACC>(A, a.lam_out, N, n, idx, v.flags, near, face_mask<OPEN>(v, x, y, z));
 
   // ---- adjoint of the adaptive factor: K_g = 1 - 1/(phi nu3_g + 1/2)
-  float mu_scale = 0.0f;
-  if (v.rp.adaptive && g > 0.0f && g * v.rp.inv_gmax < 1.0f) {
+  float mu_scale = 0.0f;          // (the local-strain mode has no lagged-velocity dependence)
+  if (v.rp.adaptive && !local && g > 0.0f && g * v.rp.inv_gmax < 1.0f) {
     float phib = 0.0f;
 #pragma unroll
     for (int gi = 0; gi < 4; ++gi) {
@@ -423,7 +464,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
     mu_scale = gb * 0.25f / g;                        // dg/d(diff) = diff / (4 g)
   }
 #pragma unroll
-  for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = v.rp.adaptive ? mu_scale * diff[i] : 0.0f;
+  for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = (v.rp.adaptive && !local) ? mu_scale * diff[i] : 0.0f;
 }
 
 template <bool WALLS>
@@ -853,8 +894,6 @@ lbm_status tape_before_step(lbm_domain* dom) {
 
 static lbm_status adjoint_supported(lbm_domain* dom) {
   if (dom->desc.storage != LBM_FP32) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP32 storage");
-  if (dom->desc.grad_mode != LBM_GRAD_LAGGED)
-    return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint covers the lagged-gradient relaxation");
   const Block& B = dom->blocks[0];
   if (B.nx < 3 || B.ny < 3 || B.nz < 3) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs >= 3 nodes per axis");
   if (27ull * B.N >= 0xFFFFFFFFull) return dom->fail(LBM_ERR_UNSUPPORTED, "block too large for the adjoint");

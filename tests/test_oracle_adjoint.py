@@ -1,6 +1,7 @@
 """Pin of the FP64 adjoint oracle: reverse-mode gradients of the smoke-control loss agree
 with central finite differences of the same FP64 forward model."""
 import numpy as np
+import pytest
 import torch
 
 import synth
@@ -131,4 +132,31 @@ def test_oracle_farfield_gradient_matches_central_differences():
     ad = sum(float((g.numpy() * v).sum()) for g, v in zip(grads, vs))
     ad1 = float((grads[1].numpy() * vs[1]).sum())
     assert abs(ad1) > 1e-6 * abs(ad)              # the far block's start matters
+    assert abs(fd - ad) <= 2e-6 * abs(fd), (fd, ad)
+
+
+@pytest.mark.parametrize("mode", ["local", "walls"])
+def test_oracle_gradient_local_strain_and_walls_match_central_differences(mode):
+    """The adaptive factor from the node's own strain rate, or no-slip walls (a floor and an
+    obstacle with its surface as walls): the forward model the oracle differentiates agrees
+    with central differences along a direction."""
+    import dataclasses
+    sc, target = synth.adjoint_scene(n=8, seed=11, nu=0.02, amp=0.06)
+    b = sc.blocks[0]
+    if mode == "local":
+        p = grid.Params(nu=sc.nu, periodic=(True, True, True), adaptive=True, grad_mode="local")
+    else:
+        synth.voxelise_spheres(b, [(4.5, 3.5, 4.0, 1.5)])
+        b.rho0[(b.flags & synth.SOLID) != 0] = 1.0
+        p = dataclasses.replace(grid.Params(nu=sc.nu, periodic=(True, True, False), adaptive=True),
+                                walls=(False,) * 4 + (True, False), obstacle_walls=True)
+    steps = 5
+    L, g, _ = adjoint.loss_and_grad(b.u0, b.rho0, b.c0, b.flags, p, steps, target)
+    v = np.random.default_rng(6).standard_normal(b.u0.shape)
+    eps = 1e-7
+    lp = adjoint.loss_only(b.u0 + eps * v, b.rho0, b.c0, b.flags, p, steps, target)
+    lm = adjoint.loss_only(b.u0 - eps * v, b.rho0, b.c0, b.flags, p, steps, target)
+    fd = (lp - lm) / (2 * eps)
+    ad = float((g.numpy() * v).sum())
+    assert abs(ad) > 1e-9
     assert abs(fd - ad) <= 2e-6 * abs(fd), (fd, ad)
