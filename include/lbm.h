@@ -353,8 +353,8 @@ lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every);
    lbm_adjoint_block_grad returns the other blocks'.  No-slip walls (wall faces and
    obstacle-surface walls, LBM_BC_WALLS) are reversed through the exact transpose of their
    completion and rebuild, far-field blocks through their aligned steps and overlap and
-   boundary mappings.  FP32 storage and the lagged-gradient (or fixed) relaxation only
-   (UNSUPPORTED otherwise).  Not in the paper. */
+   boundary mappings.  Every relaxation mode (lagged gradient, local strain rate, fixed
+   rates); FP32 storage only (UNSUPPORTED otherwise).  Not in the paper. */
 lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dscalar_final,
                             const float* dL_du_final, float* dL_du0, float* dL_dinflow);
 
