@@ -30,7 +30,7 @@ def _declared():
     return names
 
 
-def test_header_declares_the_survey_entry_points():
+def test_header_declares_the_hot_path_entry_points():
     names = _declared()
     for n in ("lbm_create_domain", "lbm_destroy_domain", "lbm_add_scale_block",
               "lbm_set_boundary", "lbm_init_macro", "lbm_step", "lbm_read_macro",
