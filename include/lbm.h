@@ -311,6 +311,26 @@ lbm_status lbm_set_inflow_batch(lbm_domain* const* doms, int32_t n,
 
 lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block_info* info);
 
+/* Halo planes of a domain split into slabs along z (no counterpart in the paper: several
+   devices or processes each advance one slab with one halo plane on each side, and the
+   edge planes are exchanged before every step; the pull of Sec. 1 reads a halo plane only
+   through the 9 populations whose c_z points into the slab).  A packed plane of block 0's
+   current state holds population rows as stored (storage element size) padded to a
+   multiple of 16 bytes — dir +1: the 9 slots with c_z = +1 (cube order 18..26), the ones a
+   slab above pulls; dir -1: the 9 with c_z = -1 (0..8); dir 0: all 27 — then the 3 velocity
+   rows and the scalar row (FP32), then the node flags (one byte each, derived bits
+   included), nx * ny entries per row.  lbm_plane_bytes gives its size (0 for a null domain
+   or another dir).  lbm_pack_plane copies plane z into dev_buf, lbm_unpack_plane copies
+   dev_buf into plane z (the population slots of another dir are left as they are); both
+   are queued on the domain's stream (dev_buf is device memory of at least lbm_plane_bytes
+   bytes, 16-byte aligned, owned by the caller; its size cannot be checked here).
+   INVALID_ARG for a null or unaligned buffer, dir outside {-1, 0, +1} or z outside
+   [0, nz); UNSUPPORTED for a domain with refined or far-field blocks; STATE while a tape
+   records. */
+size_t lbm_plane_bytes(const lbm_domain* dom, int32_t dir);
+lbm_status lbm_pack_plane(lbm_domain* dom, int32_t z, int32_t dir, void* dev_buf);
+lbm_status lbm_unpack_plane(lbm_domain* dom, int32_t z, int32_t dir, const void* dev_buf);
+
 /* Advances n independent single-block domains by `steps` reference steps with one
    persistent kernel per step over a joint tile work list, captured in one CUDA graph and
    launched on doms[0]'s stream (tile shape chosen by the library's autotuner on first use).

@@ -86,6 +86,9 @@ _SIGNATURES = {
     "lbm_get_block_info": (_I, [_P, _I, C.POINTER(lbm_block_info)]),
     "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
     "lbm_step_batch_reduce": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
+    "lbm_plane_bytes": (C.c_size_t, [_P, _I]),
+    "lbm_pack_plane": (_I, [_P, _I, _I, _P]),
+    "lbm_unpack_plane": (_I, [_P, _I, _I, _P]),
     "lbm_reduce_batch": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
     "lbm_set_inflow_batch": (_I, [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(C.c_int32)]),
     "lbm_set_tape": (_I, [_P, _I]),
@@ -328,6 +331,29 @@ class Domain:
         out = (C.c_double * 5)()
         self.check(self.lib.lbm_reduce(self.handle, block, out))
         return np.array(list(out))
+
+    def plane_bytes(self, direction=0) -> int:
+        """Bytes of a packed z-plane: direction +1 / -1 carry the 9 populations with c_z = +1 / -1,
+        direction 0 all 27 (plus velocity, scalar and flags)."""
+        return int(self.lib.lbm_plane_bytes(self.handle, int(direction)))
+
+    def _plane_buffer(self, buf, direction):
+        p, dev = _ptr(buf)
+        if not dev:
+            raise ValueError("plane buffers are device memory")
+        if _nbytes(buf) < self.plane_bytes(direction) or (p or 0) % 16:
+            raise ValueError("a plane buffer holds plane_bytes(direction) bytes, 16-byte aligned")
+        return p
+
+    def pack_plane(self, z, buf, direction=0):
+        """Copies z-plane `z` of the current state into the device tensor `buf`."""
+        self.check(self.lib.lbm_pack_plane(self.handle, int(z), int(direction),
+                                           self._plane_buffer(buf, direction)))
+
+    def unpack_plane(self, z, buf, direction=0):
+        """Copies the device tensor `buf` into z-plane `z` of the current state."""
+        self.check(self.lib.lbm_unpack_plane(self.handle, int(z), int(direction),
+                                             self._plane_buffer(buf, direction)))
 
     def step_reduce(self, n=1) -> np.ndarray:
         """``lbm_step_reduce``: n steps, then block 0's diagnostics (mass, momentum x/y/z,

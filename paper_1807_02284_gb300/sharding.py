@@ -1,14 +1,25 @@
-"""Placement of independent simulations on ranks (one process per GPU).
+"""Work placement across ranks (one process per GPU).
 
-Batched simulations share nothing, so a multi-GPU run needs no collective on the data path:
-each rank advances its own subset.  Subsets are chosen by greedy largest-first bin packing
-on the lattice-node count, which keeps the slowest rank (the one that sets the wall time)
-close to the mean.  Timing and throughput are combined with one max / sum reduction.
+Independent simulations: batched simulations share nothing, so a multi-GPU run needs no
+collective on the data path: each rank advances its own subset.  Subsets are chosen by
+greedy largest-first bin packing on the lattice-node count, which keeps the slowest rank (the
+one that sets the wall time) close to the mean.  Timing and throughput are combined with one
+max / sum reduction.
+
+One large domain (no counterpart in the paper, which runs one GPU): the domain is cut into
+slabs of whole z-planes, one per rank.  Each slab is a domain of its own with one halo plane
+on every side that borders another slab; before every step the edge planes of the current
+state are exchanged point to point — the 9 populations (as stored) that cross the cut into
+the receiving slab, velocity, scalar and node flags — so that every owned node sees the same
+pull sources, lagged velocities and scalar samples as in the undivided domain.  One halo
+plane is enough: the step reads only the 26 nearest neighbours and the scalar's departure
+point moves at most one node per step.
 """
 from __future__ import annotations
 
 import heapq
-from typing import List, Sequence
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
 
 
 def shard_by_cells(sizes: Sequence[int], world: int) -> List[List[int]]:
@@ -43,3 +54,252 @@ def reduce_timing(seconds: float, work: float, group=None):
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     dist.all_reduce(w, op=dist.ReduceOp.SUM, group=group)
     return float(t.item()), float(w.item())
+
+
+# ----------------------------------------------------------------------- slabs along z
+
+DOWN, UP = 0, 1     # message tags: a slab's first owned plane goes down, its last goes up
+# Population direction carried by each message: a plane sent down fills the upper halo of
+# the slab below, whose top nodes pull from it the populations with c_z = -1; a plane sent
+# up carries those with c_z = +1.
+DIRECTION = {DOWN: -1, UP: +1}
+
+
+def slab_ranges(nz: int, world: int) -> List[Tuple[int, int]]:
+    """Owned planes [z0, z1) per rank: nz split as evenly as possible, lower ranks first."""
+    if world < 1 or nz < world:
+        raise ValueError("need 1 <= world <= nz")
+    base, extra = divmod(nz, world)
+    out, z = [], 0
+    for r in range(world):
+        n = base + (1 if r < extra else 0)
+        out.append((z, z + n))
+        z += n
+    return out
+
+
+@dataclass(frozen=True)
+class SlabPlan:
+    """One rank's slab: owned planes [z0, z1) of nz, halo planes below (lo) and above (hi),
+    the neighbouring ranks and the local domain's z periodicity."""
+    rank: int
+    world: int
+    nz: int
+    z0: int
+    z1: int
+    lo: int
+    hi: int
+    lower: Optional[int]
+    upper: Optional[int]
+    local_periodic_z: bool
+
+    @property
+    def local_nz(self) -> int:
+        return self.z1 - self.z0 + self.lo + self.hi
+
+    @property
+    def owned(self) -> slice:
+        """Local z indices of the owned planes."""
+        return slice(self.lo, self.lo + self.z1 - self.z0)
+
+    def global_planes(self) -> List[int]:
+        """Global z index of every local plane (halo planes included)."""
+        return [(self.z0 - self.lo + i) % self.nz for i in range(self.local_nz)]
+
+    def transfers(self):
+        """The halo exchange of one step, in issue order: (kind, local z, peer rank, tag).
+        Sends come first, then receives; between one pair of ranks the messages of each
+        direction are matched in this order, which also holds for two ranks that are each
+        other's lower and upper neighbour."""
+        out = []
+        if self.lower is not None:
+            out.append(("send", self.lo, self.lower, DOWN))
+        if self.upper is not None:
+            out.append(("send", self.lo + self.z1 - self.z0 - 1, self.upper, UP))
+        if self.upper is not None:
+            out.append(("recv", self.local_nz - 1, self.upper, DOWN))
+        if self.lower is not None:
+            out.append(("recv", 0, self.lower, UP))
+        return out
+
+
+def slab_plan(nz: int, world: int, rank: int, periodic_z: bool) -> SlabPlan:
+    """The slab of `rank`: with a periodic z axis every slab has both halos (a single slab
+    keeps its own periodic wrap and has none); otherwise the global end faces stay the end
+    faces of the first and last slab, without a halo there."""
+    z0, z1 = slab_ranges(nz, world)[rank]
+    if world == 1:
+        return SlabPlan(rank, 1, nz, z0, z1, 0, 0, None, None, bool(periodic_z))
+    lower = (rank - 1) % world if (periodic_z or rank > 0) else None
+    upper = (rank + 1) % world if (periodic_z or rank < world - 1) else None
+    return SlabPlan(rank, world, nz, z0, z1, int(lower is not None), int(upper is not None),
+                    lower, upper, False)
+
+
+class SlabDomain:
+    """One rank's slab of a domain of `dims` (nx, ny, nz) cut along z.
+
+    Global inputs (flags, walls, inflow records, initial fields) are given for the whole
+    domain and sliced here; ``read_owned`` returns this slab's owned planes.  ``step`` runs
+    the halo exchange through ``torch.distributed`` before every step; ``step_local``
+    advances several slabs held by one process.  ``make_domain(dims, periodic)`` builds the
+    slab's domain (default: an ``lbm.Domain`` with the remaining keyword arguments)."""
+
+    def __init__(self, dims, nu, rank=0, world=1, periodic=(False, False, False),
+                 make_domain=None, **domain_kw):
+        import torch
+        nx, ny, nz = (int(v) for v in dims)
+        self.dims = (nx, ny, nz)
+        self.periodic = tuple(bool(p) for p in periodic)
+        self.plan = slab_plan(nz, world, rank, self.periodic[2])
+        local_periodic = (self.periodic[0], self.periodic[1], self.plan.local_periodic_z)
+        if make_domain is None:
+            from . import lbm
+
+            def make_domain(d, p):
+                return lbm.Domain(d, nu, periodic=p, **domain_kw)
+        self.dom = make_domain((nx, ny, self.plan.local_nz), local_periodic)
+        dev = getattr(self.dom, "plane_device", "cuda")
+        self.bufs = {(k, tag): torch.empty(self.dom.plane_bytes(DIRECTION[tag]),
+                                           dtype=torch.uint8, device=dev)
+                     for (k, _, _, tag) in self.plan.transfers()}
+
+    # ------------------------------------------------------------------ global inputs
+    def local(self, a):
+        """Local planes (halos included) of a global array shaped (..., nz, ny, nx)."""
+        import numpy as np
+        return np.ascontiguousarray(np.take(np.asarray(a), self.plan.global_planes(), axis=-3))
+
+    def owned(self, a):
+        """Owned planes of a local array shaped (..., local_nz, ny, nx)."""
+        return a[..., self.plan.owned, :, :]
+
+    def set_flags(self, flags):
+        self.dom.set_flags(self.local(flags))
+
+    def set_walls(self, faces, obstacles=False):
+        """Wall faces (x-, x+, y-, y+, z-, z+) of the whole domain: a z face belongs to the
+        slab that holds that end of the (non-periodic) z axis."""
+        faces = [bool(f) for f in faces]
+        if (faces[4] or faces[5]) and self.periodic[2]:
+            raise ValueError("z wall faces need a non-periodic z axis")
+        faces[4] = faces[4] and self.plan.lo == 0 and self.plan.z0 == 0
+        faces[5] = faces[5] and self.plan.hi == 0 and self.plan.z1 == self.plan.nz
+        self.dom.set_walls(faces, obstacles=obstacles)
+
+    def set_inflow(self, records):
+        """Inflow records in global coordinates; those on a local plane are kept, moved to
+        local z (a record on a halo plane also arrives with the owner's flags)."""
+        import numpy as np
+        from . import lbm
+        rec = np.asarray(records, dtype=lbm.INFLOW_RECORD)
+        planes = np.asarray(self.plan.global_planes())
+        keep = []
+        for i, g in enumerate(planes):
+            r = rec[rec["z"] == g].copy()
+            r["z"] = i
+            keep.append(r)
+        out = np.concatenate(keep) if keep else rec[:0]
+        if len(out):
+            self.dom.set_inflow(out)
+
+    def init_macro(self, u, rho=None, c=None):
+        import numpy as np
+        loc = [None if a is None else self.local(np.asarray(a, dtype=np.float32))
+               for a in (u, rho, c)]
+        self.dom.init_macro(loc[0], rho=loc[1], c=loc[2])
+
+    def read_owned(self, field, dtype=None):
+        """A field of this slab's owned planes, shaped (comp, planes, ny, nx) or
+        (planes, ny, nx) for one-component fields."""
+        from . import lbm
+        dt = lbm.LBM_F64 if dtype is None else dtype
+        a = self.dom.read_field(field, dt)
+        nx, ny, _ = self.dims
+        comp = a.size // (nx * ny * self.plan.local_nz)
+        a = a.reshape((comp, self.plan.local_nz, ny, nx))
+        a = self.owned(a)
+        return a[0] if comp == 1 else a
+
+    # ------------------------------------------------------------------ halo exchange
+    def _pack(self):
+        for kind, z, _, tag in self.plan.transfers():
+            if kind == "send":
+                self.dom.pack_plane(z, self.bufs[(kind, tag)], DIRECTION[tag])
+
+    def _unpack(self, source=None):
+        for kind, z, peer, tag in self.plan.transfers():
+            if kind == "recv":
+                buf = self.bufs[(kind, tag)] if source is None else source(peer, tag)
+                self.dom.unpack_plane(z, buf, DIRECTION[tag])
+
+    def exchange(self, group=None):
+        """Halo exchange of the current state with the neighbouring ranks (any backend;
+        device buffers are staged through host memory for backends other than NCCL)."""
+        tr = self.plan.transfers()
+        if not tr:
+            return
+        import torch
+        import torch.distributed as dist
+        self._pack()
+        self.dom.sync()
+        nccl = dist.get_backend(group) == "nccl"
+        staged = {}
+        ops = []
+        for kind, _, peer, tag in tr:
+            t = self.bufs[(kind, tag)]
+            if t.is_cuda and not nccl:
+                t = staged.setdefault((kind, tag), t.cpu())
+            g_peer = peer if group is None else dist.get_global_rank(group, peer)
+            fn = dist.isend if kind == "send" else dist.irecv
+            ops.append(dist.P2POp(fn, t, g_peer, group, tag))
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+        for (kind, tag), t in staged.items():
+            if kind == "recv":
+                self.bufs[(kind, tag)].copy_(t)
+        if any(t.is_cuda for t in self.bufs.values()):
+            torch.cuda.synchronize()
+        self._unpack()
+
+    def step(self, n=1, group=None):
+        """n steps of the whole domain, this rank's slab: exchange, then step."""
+        for _ in range(int(n)):
+            self.exchange(group)
+            self.dom.step(1)
+
+    def sync(self):
+        self.dom.sync()
+
+    def close(self):
+        self.dom.close()
+
+
+def step_local(slabs: Sequence[SlabDomain], n: int = 1):
+    """n steps of a domain whose slabs (rank = list index) are all held by this process:
+    every slab packs its edge planes, every neighbour unpacks them from the sender's buffer,
+    then every slab steps.  Slabs on one stream are ordered by it (nothing waits on the
+    host); otherwise each phase waits for the previous one on every slab's stream."""
+    by_rank = {s.plan.rank: s for s in slabs}
+    if sorted(by_rank) != list(range(len(slabs))):
+        raise ValueError("slabs must be ranks 0 .. n-1 of one cut")
+    s0 = getattr(slabs[0].dom, "torch_stream", None)
+    shared = s0 is not None and all(getattr(s.dom, "torch_stream", None) == s0 for s in slabs)
+
+    def sender(peer, tag):
+        return by_rank[peer].bufs[("send", tag)]
+
+    def wait_all():
+        if not shared:
+            for s in slabs:
+                s.sync()
+    for _ in range(int(n)):
+        for s in slabs:
+            s._pack()
+        wait_all()
+        for s in slabs:
+            s._unpack(sender)
+        wait_all()
+        for s in slabs:
+            s.dom.step(1)
+        wait_all()

@@ -63,3 +63,179 @@ def test_two_rank_gloo_sharding_and_timing():
         assert w_tot == float(sum(sizes))         # all simulations counted once
         flat = sorted(i for s in got for i in s)
         assert flat == list(range(64))
+
+
+# ------------------------------------------------------------------ slabs of one domain
+
+class _StencilDomain:
+    """Host stand-in for a slab's domain with the library's data dependence, in integers so
+    that an exchange mistake (a wrong plane, peer, slot or direction) changes owned values
+    exactly: slot s of `a` moves along z by c_z = s - 1 and is pulled from x - c_z with the
+    library's neighbour rule (periodic axes wrap, open axes clamp) and from all 9 x/y
+    neighbours; `g` (like the lagged velocity) enters through central differences along z.
+    A plane of direction +1 / -1 carries slot 2 / 0 and g, direction 0 all slots.  Plane
+    buffers live on the host."""
+    plane_device = "cpu"
+    P = 1_000_003
+
+    def __init__(self, dims, periodic):
+        self.nx, self.ny, self.nz = dims
+        self.periodic = periodic
+        self.a = np.zeros((3, self.nz, self.ny, self.nx), np.int64)
+        self.g = np.zeros((self.nz, self.ny, self.nx), np.int64)
+
+    @staticmethod
+    def slots(direction):
+        return {1: [2], -1: [0], 0: [0, 1, 2]}[direction]
+
+    def plane_bytes(self, direction=0):
+        return (len(self.slots(direction)) + 1) * self.nx * self.ny * 8
+
+    def pack_plane(self, z, buf, direction=0):
+        rows = [self.a[s, z] for s in self.slots(direction)] + [self.g[z]]
+        buf.numpy()[:] = np.stack(rows).reshape(-1).view(np.uint8)
+
+    def unpack_plane(self, z, buf, direction=0):
+        rows = buf.numpy().view(np.int64).reshape(-1, self.ny, self.nx)
+        for r, s in enumerate(self.slots(direction)):
+            self.a[s, z] = rows[r]
+        self.g[z] = rows[-1]
+
+    def sync(self):
+        pass
+
+    def _nbr(self, ax, o):
+        m = (self.nz, self.ny, self.nx)[ax]
+        j = np.arange(m) + o
+        return j % m if self.periodic[2 - ax] else np.clip(j, 0, m - 1)
+
+    def step(self, n=1):
+        for _ in range(n):
+            pulled = np.zeros_like(self.a)
+            for s in range(3):
+                zs = self._nbr(0, -(s - 1))
+                for k, (dy, dx) in enumerate(np.ndindex(3, 3)):
+                    ys, xs = self._nbr(1, dy - 1), self._nbr(2, dx - 1)
+                    pulled[s] += (k + 1 + 3 * s) * self.a[s][np.ix_(zs, ys, xs)]
+            dg = self.g[self._nbr(0, 1)] - self.g[self._nbr(0, -1)]
+            mix = np.array([[2, 1, 0], [1, 3, 1], [0, 1, 5]])
+            self.a = (np.einsum("st,tzyx->szyx", mix, pulled) + dg) % self.P
+            self.g = (pulled.sum(0) + 7 * self.g) % self.P
+
+
+def _stencil_init(shape_zyx, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.integers(0, 1000, size=(3,) + shape_zyx).astype(np.int64),
+            rng.integers(0, 1000, size=shape_zyx).astype(np.int64))
+
+
+def _stencil_reference(a, g, periodic, steps):
+    d = _StencilDomain(g.shape[::-1], periodic)
+    d.a, d.g = a.copy(), g.copy()
+    d.step(steps)
+    return d.a, d.g
+
+
+def _stencil_slabs(a, g, periodic, world, ranks):
+    out = []
+    for r in ranks:
+        s = sharding.SlabDomain(g.shape[::-1], 0.0, rank=r, world=world, periodic=periodic,
+                                make_domain=_StencilDomain)
+        s.dom.a, s.dom.g = s.local(a), s.local(g)
+        out.append(s)
+    return out
+
+
+def _owned_stencil(slabs):
+    return (np.concatenate([s.owned(s.dom.a) for s in slabs], axis=1),
+            np.concatenate([s.owned(s.dom.g) for s in slabs], axis=0))
+
+
+def test_slab_plan_covers_every_plane_once_with_the_right_halos():
+    for nz in (5, 7, 16):
+        for world in (1, 2, 3, 5):
+            for per in (False, True):
+                plans = [sharding.slab_plan(nz, world, r, per) for r in range(world)]
+                owned = [g for p in plans for g in p.global_planes()[p.owned]]
+                assert owned == list(range(nz))
+                for p in plans:
+                    g = p.global_planes()
+                    if p.lo:
+                        assert g[0] == (p.z0 - 1) % nz
+                    if p.hi:
+                        assert g[-1] == p.z1 % nz
+                    assert (p.lo == 0) == (world == 1 or (not per and p.rank == 0))
+                    assert (p.hi == 0) == (world == 1 or (not per and p.rank == world - 1))
+                    assert p.local_periodic_z == (per and world == 1)
+                # every send is one receive of the peer, of the same global plane
+                for p in plans:
+                    for kind, z, peer, tag in p.transfers():
+                        if kind != "send":
+                            continue
+                        q = plans[peer]
+                        rz = [zz for k2, zz, pr, t2 in q.transfers()
+                              if k2 == "recv" and pr == p.rank and t2 == tag]
+                        assert len(rz) == 1
+                        assert q.global_planes()[rz[0]] == p.global_planes()[z]
+    with pytest.raises(ValueError):
+        sharding.slab_ranges(3, 4)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3])
+@pytest.mark.parametrize("periodic", [(True, False, True), (False, True, False)])
+def test_local_slabs_reproduce_the_undivided_stencil(world, periodic):
+    a, g = _stencil_init((9, 5, 6), 7)
+    want = _stencil_reference(a, g, periodic, 4)
+    slabs = _stencil_slabs(a, g, periodic, world, range(world))
+    sharding.step_local(slabs, 4)
+    got = _owned_stencil(slabs)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    if world > 1:
+        # without the exchange, or with the two directions swapped, the owned planes next
+        # to a cut go wrong
+        slabs = _stencil_slabs(a, g, periodic, world, range(world))
+        for s in slabs:
+            s.dom.step(4)
+        assert not np.array_equal(_owned_stencil(slabs)[0], want[0])
+        swapped = {sharding.DOWN: +1, sharding.UP: -1}
+        old = dict(sharding.DIRECTION)
+        try:
+            sharding.DIRECTION.update(swapped)
+            slabs = _stencil_slabs(a, g, periodic, world, range(world))
+            sharding.step_local(slabs, 4)
+        finally:
+            sharding.DIRECTION.update(old)
+        assert not np.array_equal(_owned_stencil(slabs)[0], want[0])
+
+
+def _slab_worker(rank, world, port, periodic, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    a, g = _stencil_init((8, 4, 5), 11)
+    (s,) = _stencil_slabs(a, g, periodic, world, [rank])
+    s.step(3)
+    q.put((rank, s.owned(s.dom.a), s.owned(s.dom.g)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("periodic", [(False, False, True), (True, True, False)])
+def test_two_rank_gloo_slab_exchange_reproduces_the_undivided_stencil(periodic):
+    """Two ranks that are each other's lower and upper neighbour (periodic z) and a plain
+    cut (open z): the exchange goes through torch.distributed point-to-point messages."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_worker, args=(r, 2, port, periodic, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in procs), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    a, g = _stencil_init((8, 4, 5), 11)
+    want = _stencil_reference(a, g, periodic, 3)
+    assert np.array_equal(np.concatenate([r[1] for r in res], axis=1), want[0])
+    assert np.array_equal(np.concatenate([r[2] for r in res], axis=0), want[1])
