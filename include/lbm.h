@@ -374,7 +374,10 @@ lbm_status lbm_set_tape(lbm_domain* dom, int32_t checkpoint_every);
    obstacle-surface walls, LBM_BC_WALLS) are reversed through the exact transpose of their
    completion and rebuild, far-field blocks through their aligned steps and overlap and
    boundary mappings.  Every relaxation mode (lagged gradient, local strain rate, fixed
-   rates); FP32 storage only (UNSUPPORTED otherwise).  Not in the paper. */
+   rates).  With FP16-shifted storage the checkpoints hold the stored deviations widened
+   exactly to FP32 and each segment is replayed and reversed in FP32: the gradient is that
+   of the FP32 step taken from the stored states, the storage rounding being passed
+   through unchanged.  Not in the paper. */
 lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const float* dL_dscalar_final,
                             const float* dL_du_final, float* dL_du0, float* dL_dinflow);
 

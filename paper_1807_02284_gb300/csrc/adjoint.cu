@@ -851,6 +851,14 @@ static cudaError_t copy_level(const Level& D, const Level& S, size_t N, cudaStre
   return e;
 }
 
+// FP16-shifted storage keeps the deviations d = f - w in half precision; a checkpoint holds
+// them widened (exactly) to FP32, and the segment replays and transposes run on FP32 levels.
+__global__ void k_widen(const __half* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = __half2float(in[i]);
+}
+
 // Records a checkpoint of the current state every `every` steps since the last init.
 lbm_status tape_before_step(lbm_domain* dom) {
   TapeState* t = dom->tape;
@@ -885,7 +893,16 @@ lbm_status tape_before_step(lbm_domain* dom) {
   }
   const Level& S = B.lv[B.cur];
   Level& D = t->ckpt[i];
-  cudaError_t e = cudaMemcpyAsync(D.f, S.f, B.N * 27 * sizeof(float), cudaMemcpyDeviceToDevice, dom->stream);
+  cudaError_t e;
+  if (dom->desc.storage == LBM_FP16_SHIFTED) {
+    const size_t n = B.N * 27;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)152 * 16);
+    k_widen<<<grid, 256, 0, dom->stream>>>(static_cast<const __half*>(S.f),
+                                           static_cast<float*>(D.f), n);
+    e = cudaGetLastError();
+  } else {
+    e = cudaMemcpyAsync(D.f, S.f, B.N * 27 * sizeof(float), cudaMemcpyDeviceToDevice, dom->stream);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(D.u, S.u, B.N * 3 * sizeof(float), cudaMemcpyDeviceToDevice, dom->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(D.c, S.c, B.N * sizeof(float), cudaMemcpyDeviceToDevice, dom->stream);
   if (e != cudaSuccess) return dom->cuda_fail(e, "checkpoint copy");
@@ -893,7 +910,6 @@ lbm_status tape_before_step(lbm_domain* dom) {
 }
 
 static lbm_status adjoint_supported(lbm_domain* dom) {
-  if (dom->desc.storage != LBM_FP32) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs FP32 storage");
   const Block& B = dom->blocks[0];
   if (B.nx < 3 || B.ny < 3 || B.nz < 3) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs >= 3 nodes per axis");
   if (27ull * B.N >= 0xFFFFFFFFull) return dom->fail(LBM_ERR_UNSUPPORTED, "block too large for the adjoint");
