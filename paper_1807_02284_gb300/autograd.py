@@ -1,10 +1,12 @@
 """torch.autograd wrapper of the hand-written adjoint (lbm_set_tape / lbm_adjoint_step).
 
-``SmokeRollout.apply(u0, dom, steps, every, rho0, c0)`` initialises ``dom`` (a single-block
-periodic FP32 ``lbm.Domain``) at the equilibrium of (rho0, u0, c0), advances it ``steps``
-steps with a checkpoint every ``every`` steps, and returns the final scalar field (float32,
-one value per node, index (z*ny + y)*nx + x).  Its backward runs the library's reverse sweep
-and returns dL/du0 with the layout of u0 (3 planes).  Only argument marshalling happens here.
+``SmokeRollout.apply(u0, dom, steps, every, rho0, c0)`` initialises block 0 of ``dom`` (an
+``lbm.Domain`` in any configuration the adjoint covers: periodic or open faces, walls,
+obstacles, inflow nodes, FP32 or FP16-shifted storage) at the equilibrium of (rho0, u0, c0),
+advances it ``steps`` steps with a checkpoint every ``every`` steps, and returns block 0's
+final scalar field (float32, one value per node, index (z*ny + y)*nx + x).  Its backward
+runs the library's reverse sweep and returns dL/du0 with the layout of u0 (3 planes).  Only
+argument marshalling happens here.
 """
 from __future__ import annotations
 
