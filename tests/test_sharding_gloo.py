@@ -221,14 +221,17 @@ def _slab_worker(rank, world, port, periodic, q):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("periodic", [(False, False, True), (True, True, False)])
-def test_two_rank_gloo_slab_exchange_reproduces_the_undivided_stencil(periodic):
-    """Two ranks that are each other's lower and upper neighbour (periodic z) and a plain
-    cut (open z): the exchange goes through torch.distributed point-to-point messages."""
+@pytest.mark.parametrize("world,periodic", [(2, (False, False, True)), (2, (True, True, False)),
+                                            (3, (False, True, True))])
+def test_gloo_slab_exchange_reproduces_the_undivided_stencil(world, periodic):
+    """Two ranks that are each other's lower and upper neighbour (periodic z), a plain cut
+    (open z) and a ring of three: the exchange goes through torch.distributed
+    point-to-point messages."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_slab_worker, args=(r, 2, port, periodic, q)) for r in range(2)]
+    procs = [ctx.Process(target=_slab_worker, args=(r, world, port, periodic, q))
+             for r in range(world)]
     for p in procs:
         p.start()
     res = sorted((q.get(timeout=120) for _ in procs), key=lambda r: r[0])
@@ -239,3 +242,64 @@ def test_two_rank_gloo_slab_exchange_reproduces_the_undivided_stencil(periodic):
     want = _stencil_reference(a, g, periodic, 3)
     assert np.array_equal(np.concatenate([r[1] for r in res], axis=1), want[0])
     assert np.array_equal(np.concatenate([r[2] for r in res], axis=0), want[1])
+
+
+class _RecordingDomain:
+    """Records what a slab hands to its domain (flags, walls, inflow records, fields)."""
+    plane_device = "cpu"
+
+    def __init__(self, dims, periodic):
+        self.dims, self.periodic, self.calls = dims, periodic, {}
+
+    def plane_bytes(self, direction=0):
+        return 16
+
+    def set_flags(self, flags):
+        self.calls["flags"] = flags
+
+    def set_walls(self, faces, obstacles=False):
+        self.calls["walls"] = (list(faces), obstacles)
+
+    def set_inflow(self, records):
+        self.calls["inflow"] = records
+
+    def init_macro(self, u, rho=None, c=None):
+        self.calls["init"] = (u, rho, c)
+
+
+def test_slab_inputs_are_sliced_from_the_global_domain():
+    from paper_1807_02284_gb300 import lbm
+    nx, ny, nz = 4, 3, 10
+    flags = np.arange(nz * ny * nx, dtype=np.int64).reshape(nz, ny, nx) % 251
+    u = np.random.default_rng(2).random((3, nz, ny, nx))
+    rec = np.zeros(4, dtype=lbm.INFLOW_RECORD)
+    rec["z"] = [0, 3, 4, 9]
+    rec["x"] = [1, 2, 3, 0]
+    for per in (False, True):
+        slabs = [sharding.SlabDomain((nx, ny, nz), 0.0, rank=r, world=3,
+                                     periodic=(False, False, per), make_domain=_RecordingDomain)
+                 for r in range(3)]
+        for s in slabs:
+            s.set_flags(flags.astype(np.uint8))
+            s.set_walls((True, False, False, True, not per, not per), obstacles=True)
+            s.set_inflow(rec)
+            s.init_macro(u, c=u[0])
+            g = s.plan.global_planes()
+            d = s.dom
+            assert d.dims == (nx, ny, len(g)) and d.periodic == (False, False, False)
+            assert np.array_equal(d.calls["flags"], flags[g].astype(np.uint8))
+            assert np.array_equal(d.calls["init"][0], u[:, g].astype(np.float32))
+            assert d.calls["init"][1] is None
+            assert np.array_equal(d.calls["init"][2], u[0][g].astype(np.float32))
+            faces, obst = d.calls["walls"]
+            assert faces[:4] == [True, False, False, True] and obst
+            # a z wall face only where the slab holds that end of the open axis
+            assert faces[4] == (not per and s.plan.rank == 0)
+            assert faces[5] == (not per and s.plan.rank == 2)
+            r = d.calls["inflow"]
+            want = sorted((int(x), g.index(int(z))) for x, z in zip(rec["x"], rec["z"])
+                          if int(z) in g)
+            assert sorted(zip(r["x"].tolist(), r["z"].tolist())) == want
+    with pytest.raises(ValueError):
+        sharding.SlabDomain((nx, ny, nz), 0.0, rank=0, world=2, periodic=(False, False, True),
+                            make_domain=_RecordingDomain).set_walls((False,) * 4 + (True, False))
