@@ -39,7 +39,6 @@ import numpy as np
 import torch
 
 from . import cmr, coupling, grid
-from .cmr import DT
 
 SOLID, INFLOW, SCALAR_SRC, GHOST = grid.SOLID, grid.INFLOW, grid.SCALAR_SRC, grid.GHOST
 

@@ -6,7 +6,6 @@ import pytest
 
 import synth
 from oracle import coupling, dynamic
-from tests.helpers import f32
 from tests.test_gpu_multiscale import compare, gpu_multiscale
 
 pytestmark = pytest.mark.gpu

@@ -9,7 +9,6 @@ import math
 
 import numpy as np
 import pytest
-import torch
 
 import synth
 from oracle import grid

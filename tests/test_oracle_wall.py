@@ -9,7 +9,6 @@ invariants on a voxel with unknown populations from several directions."""
 import math
 
 import numpy as np
-import pytest
 import torch
 
 from oracle import cmr, grid
