@@ -1,0 +1,46 @@
+"""Host logic of bench.py on CPU: the algorithmic byte count the roofline divides by, and
+the JSON line of the reference arm (the FP64 oracle timed on the host cores)."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_algorithmic_bytes_count_each_node_kind():
+    flags = np.zeros((2, 3, 4), np.uint8)          # 24 nodes
+    flags[0, 0, :2] = 1                              # 2 obstacle voxels
+    flags[1, 2, 1:4] = 2                             # 3 inflow nodes
+    flags[1, 0, 0] = 3                               # obstacle and inflow: counted as obstacle
+    fluid, solid, inflow = 24 - 3 - 3, 3, 3
+    total, per_fluid = bench._algorithmic_bytes(flags, "fp32")
+    assert per_fluid == 27 * 4 * 2 + 12 * 2 + 4 * 2 + 1 == 249
+    assert total == fluid * 249 + solid * (27 * 4 + 12 + 4 + 1) + inflow * (27 * 4 + 24 + 8 + 1)
+    total16, per16 = bench._algorithmic_bytes(flags, "fp16")
+    assert per16 == 141
+    assert total16 == fluid * 141 + solid * (27 * 2 + 17) + inflow * (27 * 2 + 33)
+    assert bench._algorithmic_bytes(flags, "fp32", local=True)[1] == 237
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "dtype", "data", "config"):
+        assert k in line, k
+    assert line["metric"] == "MLUPS" and line["unit"] == "MLUPS" and line["value"] > 0
+    assert line["steps"] == 1 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
