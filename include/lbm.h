@@ -315,11 +315,12 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
    devices or processes each advance one slab with one halo plane on each side, and the
    edge planes are exchanged before every step; the pull of Sec. 1 reads a halo plane only
    through the 9 populations whose c_z points into the slab).  A packed plane of block 0's
-   current state holds population rows as stored (storage element size) padded to a
-   multiple of 16 bytes — dir +1: the 9 slots with c_z = +1 (cube order 18..26), the ones a
-   slab above pulls; dir -1: the 9 with c_z = -1 (0..8); dir 0: all 27 — then the 3 velocity
-   rows and the scalar row (FP32), then the node flags (one byte each, derived bits
-   included), nx * ny entries per row.  lbm_plane_bytes gives its size (0 for a null domain
+   current state holds population rows as stored (storage element size, shifted, in the
+   library's internal slot order) padded to a multiple of 16 bytes — dir +1: the 9
+   populations with c_z = +1, the ones a slab above pulls; dir -1: the 9 with c_z = -1;
+   dir 0: all 27 — then the 3 velocity rows and the scalar row (FP32), then the node flags
+   (one byte each, derived bits included), nx * ny entries per row.  The buffer is meant for
+   lbm_unpack_plane of a domain with the same nx, ny and storage, not for reading.  lbm_plane_bytes gives its size (0 for a null domain
    or another dir).  lbm_pack_plane copies plane z into dev_buf, lbm_unpack_plane copies
    dev_buf into plane z (the population slots of another dir are left as they are); both
    are queued on the domain's stream (dev_buf is device memory of at least lbm_plane_bytes
