@@ -320,10 +320,11 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
    populations with c_z = +1, the ones a slab above pulls; dir -1: the 9 with c_z = -1;
    dir 0: all 27 — then the 3 velocity rows and the scalar row (FP32), then the node flags
    (one byte each, derived bits included), nx * ny entries per row.  The buffer is meant for
-   lbm_unpack_plane of a domain with the same nx, ny and storage, not for reading.  lbm_plane_bytes gives its size (0 for a null domain
-   or another dir).  lbm_pack_plane copies plane z into dev_buf, lbm_unpack_plane copies
-   dev_buf into plane z (the population slots of another dir are left as they are); both
-   are queued on the domain's stream (dev_buf is device memory of at least lbm_plane_bytes
+   lbm_unpack_plane of a domain with the same nx, ny and storage, not for reading.
+   lbm_plane_bytes gives its size (0 for a null domain or another dir).  lbm_pack_plane
+   copies plane z into dev_buf, lbm_unpack_plane copies dev_buf into plane z (the
+   population slots of another dir are left as they are); both are queued on the domain's
+   stream (dev_buf is device memory of at least lbm_plane_bytes
    bytes, 16-byte aligned, owned by the caller; its size cannot be checked here).
    INVALID_ARG for a null or unaligned buffer, dir outside {-1, 0, +1} or z outside
    [0, nz); UNSUPPORTED for a domain with refined or far-field blocks; STATE while a tape
