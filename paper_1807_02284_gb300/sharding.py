@@ -221,6 +221,24 @@ class SlabDomain:
         a = self.owned(a)
         return a[0] if comp == 1 else a
 
+    def gather_owned(self, field, dtype=None, dst=0, group=None):
+        """A field of the whole domain, assembled on rank `dst` from every rank's owned
+        planes (read back to the host, sent with ``gather_object``); other ranks get None.
+        Without a process group the slab's own planes are returned."""
+        import numpy as np
+        import torch.distributed as dist
+        a = self.read_owned(field, dtype)
+        if not (dist.is_available() and dist.is_initialized()):
+            return a
+        me = dist.get_rank(group)
+        parts = [None] * dist.get_world_size(group) if me == dst else None
+        g_dst = dst if group is None else dist.get_global_rank(group, dst)
+        dist.gather_object((self.plan.z0, a), parts, dst=g_dst, group=group)
+        if me != dst:
+            return None
+        parts.sort(key=lambda p: p[0])
+        return np.concatenate([p[1] for p in parts], axis=-3)
+
     # ------------------------------------------------------------------ halo exchange
     def _pack(self):
         for kind, z, _, tag in self.plan.transfers():

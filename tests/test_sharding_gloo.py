@@ -104,6 +104,9 @@ class _StencilDomain:
     def sync(self):
         pass
 
+    def read_field(self, field, dtype=None):
+        return self.a.reshape(-1).copy()
+
     def _nbr(self, ax, o):
         m = (self.nz, self.ny, self.nx)[ax]
         j = np.arange(m) + o
@@ -216,7 +219,8 @@ def _slab_worker(rank, world, port, periodic, q):
     a, g = _stencil_init((8, 4, 5), 11)
     (s,) = _stencil_slabs(a, g, periodic, world, [rank])
     s.step(3)
-    q.put((rank, s.owned(s.dom.a), s.owned(s.dom.g)))
+    whole = s.gather_owned(0, dst=world - 1)           # field argument unused by the stand-in
+    q.put((rank, s.owned(s.dom.a), s.owned(s.dom.g), whole))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -242,6 +246,8 @@ def test_gloo_slab_exchange_reproduces_the_undivided_stencil(world, periodic):
     want = _stencil_reference(a, g, periodic, 3)
     assert np.array_equal(np.concatenate([r[1] for r in res], axis=1), want[0])
     assert np.array_equal(np.concatenate([r[2] for r in res], axis=0), want[1])
+    assert all(r[3] is None for r in res[:-1])         # assembled on the last rank only
+    assert np.array_equal(res[-1][3], want[0])
 
 
 class _RecordingDomain:
