@@ -44,3 +44,15 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == "plume32_oracle"
+    assert line["config"]["nodes"] == 32 ** 3
+
+
+def test_repeat_record_reports_the_median_call():
+    times = [0.30, 0.10, 0.20, 0.50]          # seconds per K-step call
+    rec = bench.repeat_record(times, 10, 1000)
+    assert rec["count"] == 4 and rec["steps_per_call"] == 10
+    assert rec["ms_per_step_median"] == np.median(times) / 10 * 1e3
+    assert rec["ms_per_step_best"] == 0.10 / 10 * 1e3 and rec["ms_per_step_worst"] == 50.0
+    assert rec["value_best"] == 1000 * 10 / 0.10 / 1e6
+    assert abs(rec["device_seconds"] - 1.1) < 1e-12

@@ -199,3 +199,143 @@ def test_scale_block_argument_checks(lib):
         d16.add_scale_block((2, 2, 2), 0.5, (8, 8, 8))
     assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
     d16.close()
+
+
+@pytest.mark.parametrize("kind", ["nested", "far"])
+def test_schedule_exact_on_affine_scalar_transport(lib, kind):
+    """The exact Algorithm 1 case of the oracle pin (uniform flow, scalar affine in space,
+    blocks at h = 1/1.5 and 1/2.25, or a refined block inside s0 inside a far block at h = 2):
+    every checked node of every block holds c0 + G . (x - U n) after each reference step, to
+    float32 rounding, and agrees with the oracle."""
+    from paper_1807_02284_gb300 import lbm
+    from tests import test_oracle_schedule as ts
+    if kind == "nested":
+        sc, far = ts.nested_scene(), None
+    else:
+        sc, far = ts.far_scene()
+    dom = gpu_multiscale(sc)
+    blocks = list(sc.blocks)
+    if far is not None:
+        fid = dom.add_scale_block(far.origin, far.h, far.dims)
+        dom.set_flags(far.flags, block=fid)
+        dom.init_macro(f32(far.u0), rho=f32(far.rho0), c=f32(far.c0), block=fid)
+        blocks.append(far)
+    ms = ts.build(kind)
+    for n in range(1, 4):
+        dom.step(1)
+        ms.step()
+        for i, (b, m) in enumerate(zip(blocks, ts.checked_masks(ms, n))):
+            c = dom.read_field(lbm.LBM_FIELD_SCALAR, lbm.LBM_F64, i).reshape(b.shape_zyx)
+            want = ts.exact_scalar(b.origin, b.h, b.dims, n)
+            e_exact = float(np.abs(c - want)[m].max())
+            e_oracle = max_err(c, ms.blocks[i].state.c.numpy())
+            print(f"{kind} step {n} block {i}: |c - exact| = {e_exact:.2e}, "
+                  f"|c - oracle| = {e_oracle:.2e}")
+            assert e_exact < 3e-6 and e_oracle < 3e-6, (n, i)
+    dom.close()
+
+
+def _oracle_blocks_from_gpu(dom, sc):
+    """Oracle blocks holding the GPU's current float32 states (widened exactly) and flags."""
+    from paper_1807_02284_gb300 import lbm
+    out = []
+    for i, b in enumerate(sc.blocks):
+        f, u, c = read_block(dom, i, b.shape_zyx)
+        fl = dom.read_field(lbm.LBM_FIELD_FLAGS, lbm.LBM_U8, i).reshape(b.shape_zyx) & 0x0F
+        st = grid.State(torch.from_numpy(f), torch.from_numpy(u), torch.from_numpy(c),
+                        torch.from_numpy(fl.astype(np.uint8)))
+        out.append(coupling.Blk(origin=np.array(b.origin, dtype=np.float64), h=float(b.h),
+                                dims=tuple(b.dims), state=st,
+                                params=grid.Params(nu=sc.nu / b.h, periodic=(False,) * 3)))
+    return out
+
+
+def _check_mapped(label, src, dst, z, y, x, rng, n=3000, f_tol=4e-7, c_tol=2e-6):
+    """dst's stored values at sampled nodes (z, y, x) against the oracle's trilinear
+    interpolation of src's state at their positions followed by the K_hat mapping
+    (Sec. 3.2, Sec. 4.2.2); nodes whose corners are all obstacles hold the rest state."""
+    from oracle import cmr
+    assert z.numel() > 0, label
+    pick = torch.from_numpy(rng.choice(z.numel(), size=min(n, z.numel()), replace=False))
+    z, y, x = z[pick], y[pick], x[pick]
+    f, c, ok = coupling.interpolate(src, src.state.f, src.state.c,
+                                    coupling.node_positions(dst, z, y, x))
+    fm = coupling.map_populations(f[ok], coupling.k_hat(src, dst))
+    _, um = cmr.macros(fm)
+    got_f = dst.state.f[:, z, y, x].T
+    got_u = dst.state.u[:, z, y, x].T
+    got_c = dst.state.c[z, y, x]
+    ef = float((got_f[ok] - fm).abs().max())
+    eu = float((got_u[ok] - um).abs().max())
+    ec = float((got_c[ok] - c[ok]).abs().max())
+    umax = float(um.abs().max())
+    print(f"{label}: {int(pick.numel())} nodes ({int((~ok).sum())} at rest) |df|={ef:.2e} "
+          f"|du|={eu:.2e} (max|u| {umax:.3f}) |dc|={ec:.2e}")
+    assert ef <= f_tol and eu <= U_REL * max(umax, 1e-3) and ec <= c_tol, label
+    if bool((~ok).any()):
+        rest = cmr.equilibrium(torch.ones(1, dtype=torch.float64),
+                               torch.zeros(1, 3, dtype=torch.float64))[0]
+        assert float((got_f[~ok] - rest).abs().max()) <= f_tol, label
+
+
+def _span_nodes(tgt, src):
+    """Nodes of tgt inside src's interior span (Sec. 4.2.5 post-mapping targets) that are
+    neither ghost nor obstacle nodes of tgt."""
+    lo, hi = src.interior_lo_hi()
+    zz, yy, xx = torch.meshgrid(*(torch.arange(n) for n in reversed(tgt.dims)), indexing="ij")
+    zz, yy, xx = zz.reshape(-1), yy.reshape(-1), xx.reshape(-1)
+    pos = coupling.node_positions(tgt, zz, yy, xx)
+    inside = torch.ones(pos.shape[0], dtype=torch.bool)
+    for a in range(3):
+        inside &= (pos[:, a] >= lo[a] - 1e-9) & (pos[:, a] <= hi[a] + 1e-9)
+    inside &= (tgt.state.flags[zz, yy, xx] & (coupling.GHOST | coupling.SOLID)) == 0
+    sel = torch.nonzero(inside).flatten()
+    return zz[sel], yy[sel], xx[sel]
+
+
+def _drop_touching(src, dst, nodes, finer):
+    """Leave out dst nodes whose trilinear source cell in src has a corner of non-zero weight
+    among src's nodes inside the finer block's interior span: those corners are post-mapped
+    from the finer block after dst's mapping was taken within the step."""
+    z, y, x = nodes
+    lo, hi = finer.interior_lo_hi()
+    a_lo = np.ceil((lo - src.origin) / src.h - 1e-9)
+    a_hi = np.floor((hi - src.origin) / src.h + 1e-9)
+    q = (coupling.node_positions(dst, z, y, x) - torch.as_tensor(src.origin)) / src.h
+    touch = torch.ones(z.shape, dtype=torch.bool)
+    for a in range(3):
+        i0 = torch.floor(q[:, a] + 1e-9).long()
+        i1 = torch.where(q[:, a] - i0.to(q.dtype) > 1e-9, i0 + 1, i0)   # weight-0 corner ignored
+        touch &= (i1 >= int(a_lo[a])) & (i0 <= int(a_hi[a]))
+    keep = ~touch
+    return z[keep], y[keep], x[keep]
+
+
+def test_full_size_mappings_sampled(lib):
+    """Full-size 3-block scene with a seeded non-uniform flow and the 8 obstacles, after two
+    reference steps: sampled nodes of every mapping of Algorithm 1 against the oracle's
+    interpolation and K_hat mapping of the GPU's own source state -- the ghost layers of s1
+    (from s0) and s2 (from s1), and the post-mapped nodes of s0 from s1 (about 240k entries:
+    the large-mapping kernel variant), of s0 from s2 and of s1 from s2.  Within one step s1
+    is post-mapped into s0 before s2 is post-mapped into s1, so s0 targets whose s1 cell
+    touches s1's nodes inside s2's span are left out of the s1 -> s0 check."""
+    sc = synth.multiscale(scale=1.0, flow_amp=0.06)
+    dom = gpu_multiscale(sc)
+    dom.step(2)
+    dom.sync()
+    s0, s1, s2 = _oracle_blocks_from_gpu(dom, sc)
+    rng = np.random.default_rng(12)
+    for label, src, dst in (("s1 ghost layer from s0", s0, s1), ("s2 ghost layer from s1", s1, s2)):
+        g = ((dst.state.flags & coupling.GHOST) != 0) & ((dst.state.flags & coupling.SOLID) == 0)
+        nodes = torch.nonzero(g, as_tuple=True)
+        if src is s1:
+            nodes = _drop_touching(s1, s2, nodes, s2)
+        _check_mapped(label, src, dst, *nodes, rng)
+    nodes = _span_nodes(s0, s1)
+    assert nodes[0].numel() >= 155_000                    # the large-mapping variant
+    _check_mapped("s0 post-mapped from s1", s1, s0, *_drop_touching(s1, s0, nodes, s2), rng)
+    z, y, x = _span_nodes(s0, s2)
+    _check_mapped("s0 post-mapped from s2", s2, s0, z, y, x, rng)
+    z, y, x = _span_nodes(s1, s2)
+    _check_mapped("s1 post-mapped from s2", s2, s1, z, y, x, rng)
+    dom.close()
