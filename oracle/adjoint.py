@@ -16,7 +16,7 @@ import numpy as np
 import torch
 from torch.utils.checkpoint import checkpoint
 
-from . import grid
+from . import cmr, grid
 from .cmr import DT
 
 
@@ -26,19 +26,56 @@ def _step_tensors(f, u, c, flags, p):
 
 
 def forward(u0: torch.Tensor, rho0, c0, flags, p: grid.Params, steps: int,
-            use_checkpoint: bool = True):
-    """Runs `steps` steps from the equilibrium of (rho0, u0); returns the final State."""
+            use_checkpoint: bool = True, restart=None):
+    """Runs `steps` steps from the equilibrium of (rho0, u0); returns the final State.
+
+    ``restart`` (optional) maps step numbers n to states (f, u, c): at the start of step n
+    the running state takes those values while its derivative passes through unchanged
+    (straight-through), which is how a reverse sweep that replays each segment from a stored
+    checkpoint sees a forward whose stored states were rounded (FP16-shifted storage)."""
     flags_t = torch.as_tensor(np.asarray(flags).astype(np.uint8)) \
         if not isinstance(flags, torch.Tensor) else flags
     st = grid.init_state(torch.as_tensor(np.asarray(rho0), dtype=DT), u0,
                          torch.as_tensor(np.asarray(c0), dtype=DT), flags_t)
     f, u, c = st.f, st.u, st.c
-    for _ in range(steps):
+    for n in range(steps):
+        if restart is not None and n in restart:
+            rf, ru, rc = restart[n]
+            f = f + (rf - f).detach()
+            u = u + (ru - u).detach()
+            c = c + (rc - c).detach()
         if use_checkpoint and torch.is_grad_enabled():
             f, u, c = checkpoint(_step_tensors, f, u, c, flags_t, p, use_reentrant=False)
         else:
             f, u, c = _step_tensors(f, u, c, flags_t, p)
     return grid.State(f, u, c, flags_t)
+
+
+def round_shifted_to_half(f: torch.Tensor) -> torch.Tensor:
+    """FP16-shifted storage of populations (27, ...): the deviation d = f - w from the lattice
+    weights rounded to binary16 (round to nearest even), then widened back."""
+    w = cmr.equilibrium(torch.ones(1, dtype=DT), torch.zeros(1, 3, dtype=DT))[0]
+    w = w.reshape((27,) + (1,) * (f.dim() - 1))
+    return (f - w).to(torch.float16).to(DT) + w
+
+
+def fp16_storage_checkpoints(u0, rho0, c0, flags, p: grid.Params, steps: int, every: int):
+    """States of the FP16-shifted-storage forward (the deviations rounded to binary16 after
+    the initialisation and after every step; velocity and scalar kept in full precision) at
+    every multiple of `every` below `steps`: the checkpoints a reverse sweep replays from."""
+    with torch.no_grad():
+        flags_t = torch.as_tensor(np.asarray(flags).astype(np.uint8))
+        st = grid.init_state(torch.as_tensor(np.asarray(rho0), dtype=DT),
+                             torch.as_tensor(np.asarray(u0), dtype=DT),
+                             torch.as_tensor(np.asarray(c0), dtype=DT), flags_t)
+        st.f = round_shifted_to_half(st.f)
+        out = {}
+        for n in range(steps):
+            if n % every == 0:
+                out[n] = (st.f.clone(), st.u.clone(), st.c.clone())
+            st = grid.step(st, p)
+            st.f = round_shifted_to_half(st.f)
+        return out
 
 
 def loss_fn(st: grid.State, c_target, u_target=None):
@@ -48,10 +85,11 @@ def loss_fn(st: grid.State, c_target, u_target=None):
     return L
 
 
-def loss_and_grad(u0, rho0, c0, flags, p: grid.Params, steps: int, c_target, u_target=None):
-    """(L, dL/du0, c_T) in float64."""
+def loss_and_grad(u0, rho0, c0, flags, p: grid.Params, steps: int, c_target, u_target=None,
+                  restart=None):
+    """(L, dL/du0, c_T) in float64 (``restart``: see ``forward``)."""
     u = torch.as_tensor(np.asarray(u0), dtype=DT).clone().requires_grad_(True)
-    st = forward(u, rho0, c0, flags, p, steps)
+    st = forward(u, rho0, c0, flags, p, steps, restart=restart)
     L = loss_fn(st, c_target, u_target)
     (g,) = torch.autograd.grad(L, u)
     return float(L.detach()), g.detach(), st.c.detach()

@@ -160,3 +160,57 @@ def test_oracle_gradient_local_strain_and_walls_match_central_differences(mode):
     ad = float((g.numpy() * v).sum())
     assert abs(ad) > 1e-9
     assert abs(fd - ad) <= 2e-6 * abs(fd), (fd, ad)
+
+
+def test_binary16_rounding_of_the_shifted_populations():
+    """FP16-shifted storage keeps d = f - w in IEEE binary16 (round to nearest, ties to even):
+    representable deviations are kept exactly, ties go to the even significand, normal
+    values move by at most half an ulp (2^-11 relative), values below the smallest normal
+    (2^-14) by at most half the subnormal spacing (2^-25)."""
+    from oracle import cmr
+    w = cmr.equilibrium(torch.ones(1, dtype=torch.float64), torch.zeros(1, 3, dtype=torch.float64))[0]
+    d = torch.tensor([0.0, 2.0 ** -10, -3 * 2.0 ** -12, 1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11,
+                      2.0 ** -20, 3 * 2.0 ** -26], dtype=torch.float64)
+    want = torch.tensor([0.0, 2.0 ** -10, -3 * 2.0 ** -12, 1.0, 1 + 2.0 ** -9, 2.0 ** -20,
+                         2.0 ** -24], dtype=torch.float64)
+    f = w[:, None] + d[None, :]
+    got = adjoint.round_shifted_to_half(f) - w[:, None]
+    # (adding and removing w costs at most an ulp of the sum in float64)
+    assert torch.allclose(got, want[None, :].expand(27, -1), rtol=0, atol=2.3e-16)
+    g = torch.Generator().manual_seed(3)
+    dr = (torch.rand(27, 4096, generator=g, dtype=torch.float64) - 0.5) * 2.0 ** \
+        torch.randint(-30, 0, (27, 4096), generator=g).to(torch.float64)
+    dr = (w[:, None] + dr) - w[:, None]           # the deviations the populations carry
+    err = (adjoint.round_shifted_to_half(w[:, None] + dr) - w[:, None] - dr).abs()
+    bound = torch.where(dr.abs() >= 2.0 ** -14, dr.abs() * 2.0 ** -11,
+                        torch.full_like(dr, 2.0 ** -25))
+    assert bool((err <= bound * (1 + 1e-12) + 1e-16).all())
+
+
+def test_restart_passes_the_derivative_through():
+    """Restarting the forward from states equal to its own keeps loss and gradient exactly;
+    restarting from the FP16-storage checkpoints moves the trajectory by the storage
+    rounding only (the deviations are small: a few 1e-4 of the populations)."""
+    sc, target = synth.adjoint_scene(n=8, seed=7, nu=0.02, amp=0.05)
+    b = sc.blocks[0]
+    p = grid.Params(nu=sc.nu, periodic=sc.periodic, adaptive=True)
+    steps, every = 6, 2
+    L, g, _ = adjoint.loss_and_grad(b.u0, b.rho0, b.c0, b.flags, p, steps, target)
+    own = {}
+    with torch.no_grad():
+        st = grid.init_state(b.rho0, b.u0, b.c0, b.flags)
+        for n in range(steps):
+            if n % every == 0:
+                own[n] = (st.f.clone(), st.u.clone(), st.c.clone())
+            st = grid.step(st, p)
+    L1, g1, _ = adjoint.loss_and_grad(b.u0, b.rho0, b.c0, b.flags, p, steps, target, restart=own)
+    assert L1 == L and torch.equal(g1, g)
+    ck = adjoint.fp16_storage_checkpoints(b.u0, b.rho0, b.c0, b.flags, p, steps, every)
+    assert sorted(ck) == [0, 2, 4]
+    for n, (f, u, c) in ck.items():
+        fo, uo, co = own[n]
+        assert float((f - fo).abs().max()) < 1e-4
+        assert float((u - uo).abs().max()) < 1e-4 * 0.05 * 10
+    L2, g2, _ = adjoint.loss_and_grad(b.u0, b.rho0, b.c0, b.flags, p, steps, target, restart=ck)
+    assert abs(L2 - L) < 1e-3 * abs(L)
+    assert float(torch.linalg.norm(g2 - g) / torch.linalg.norm(g)) < 1e-3
