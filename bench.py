@@ -192,17 +192,24 @@ def _max_over_ranks(ws, val):
     return float(t.item())
 
 
-def timed_repeats(ws, dev, stream, run_k, min_total_s=1.0, min_repeats=3, max_repeats=400):
-    """Times back-to-back calls of ``run_k`` (one call = the K timed steps), each bracketed by
-    a barrier and a device synchronize on both sides and timed with CUDA events on the
+def timed_repeats(ws, dev, stream, run_k, reset=None, min_total_s=1.0, min_repeats=3,
+                  max_repeats=400):
+    """Times repeated calls of ``run_k`` (one call = the K timed steps), each bracketed by a
+    barrier and a device synchronize on both sides and timed with CUDA events on the
     library's stream, until at least ``min_total_s`` of device time and ``min_repeats`` calls
-    have been taken.  Clocks are sampled across all of them.  Returns the per-call device
-    times (max over ranks) and the clock record."""
+    have been taken.  ``reset`` (untimed, before every call after the first) puts the
+    workload back to its state before the first call, so every call steps the same flow
+    (the scenes are only stable for their configured number of steps).  Clocks are sampled
+    across all calls.  Returns the per-call device times (max over ranks) and the clock
+    record."""
     import torch
     clocks = ClockSampler(dev)
     times, total = [], 0.0
     clocks.start()
     while len(times) < max_repeats and (len(times) < min_repeats or total < min_total_s):
+        if times and reset is not None:
+            reset()
+            torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         _barrier(ws)
@@ -537,8 +544,12 @@ def run_ours(args):
         dom.add_scale_block(blk.origin, blk.h, blk.dims)
     for i, blk in enumerate(sc.blocks):
         dom.set_flags(blk.flags, block=i)
-        dom.init_macro(blk.u0.astype(np.float32), rho=blk.rho0.astype(np.float32),
-                       c=blk.c0.astype(np.float32), block=i)
+
+    def init_state():
+        for i, blk in enumerate(sc.blocks):
+            dom.init_macro(blk.u0.astype(np.float32), rho=blk.rho0.astype(np.float32),
+                           c=blk.c0.astype(np.float32), block=i)
+    init_state()
     # lattice updates and launches per reference step (refined blocks sub-cycle)
     subs = [dom.info(i).substeps for i in range(len(sc.blocks))]
     N = sum(s * blk.flags.size for s, blk in zip(subs, sc.blocks))
@@ -562,7 +573,11 @@ def run_ours(args):
     # call is repeated until at least a second of device time; value is the median call
     dom.step(W)
     dom.sync()
-    times, clk = timed_repeats(ws, dev, stream, lambda: dom.step(K))
+
+    def reset():
+        init_state()
+        dom.step(W)
+    times, clk = timed_repeats(ws, dev, stream, lambda: dom.step(K), reset)
     dom.sync()
     t_max = float(np.median(times))
     t_dev = t_max
@@ -681,7 +696,13 @@ def run_batch(args):
     lbm.step_batch(doms, K)          # builds and captures the K-step plan outside the timing
     for d in doms:
         d.sync()
-    times, clk = timed_repeats(ws, dev, stream, lambda: lbm.step_batch(doms, K))
+    def reset():
+        for sc, d in zip(mine, doms):
+            b = sc.blocks[0]
+            d.init_macro(b.u0.astype(np.float32), rho=b.rho0.astype(np.float32),
+                         c=b.c0.astype(np.float32))
+        lbm.step_batch(doms, W)
+    times, clk = timed_repeats(ws, dev, stream, lambda: lbm.step_batch(doms, K), reset)
     for d in doms:
         d.sync()
     t_max = float(np.median(times))

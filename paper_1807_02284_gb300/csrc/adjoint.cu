@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   }
   raw_moments(K);
   const float drho = K[kap(0, 0, 0)];
-  const float inv = __frcp_rn(1.0f + drho);
+  const float inv = fast_rcp(1.0f + drho);
   const float ux = K[kap(1, 0, 0)] * inv, uy = K[kap(0, 1, 0)] * inv, uz = K[kap(0, 0, 1)] * inv;
   put_sender(a, N, idx, (fl & F_SCALAR_SRC) ? 0.0f : a.gam_in[idx], ux, uy, uz);
   float diff[9];

@@ -31,6 +31,45 @@ __device__ __forceinline__ Nbr<IT> neighbours(const BlockView& v, int x, int y, 
   return n;
 }
 
+// A node whose y and z neighbours need no wrap or clamp (1 <= y <= ny - 2, 1 <= z <= nz - 2):
+// its rows and planes are plain offsets, the same for a whole warp of an x-row, so every
+// pull source is a warp-uniform offset plus the lane's x source.  The x neighbours keep the
+// face rules (wrap or clamp).  Same indices, loads and values as the general path.
+__device__ __forceinline__ bool inner_yz(const BlockView& v, int y, int z) {
+  return (unsigned)(y - 1) < (unsigned)(v.ny - 2) && (unsigned)(z - 1) < (unsigned)(v.nz - 2);
+}
+
+template <typename IT>
+__device__ __forceinline__ Nbr<IT> neighbours_inner(const BlockView& v, int x, int y, int z) {
+  Nbr<IT> n;
+  const IT nx = (IT)v.nx, nxy = (IT)v.nx * (IT)v.ny;
+  n.xm = (IT)nbr(x, -1, v.nx, v.per[0]);
+  n.x0 = (IT)x;
+  n.xp = (IT)nbr(x, 1, v.nx, v.per[0]);
+  n.r0 = nx * (IT)y;
+  n.rm = n.r0 - nx;
+  n.rp = n.r0 + nx;
+  n.p0 = nxy * (IT)z;
+  n.pm = n.p0 - nxy;
+  n.pp = n.p0 + nxy;
+  return n;
+}
+
+// Pull of an inner_yz node: plane K at rows y - c_y, z - c_z is the offset
+// K N - c_z nx ny - c_y nx from the lane's row (uniform over the warp); am, a0, ap are the
+// lane's row index plus its x source for c_x = +1, 0, -1.
+template <typename T, typename IT, int K = 0>
+__device__ __forceinline__ void pull_inner(float (&d)[27], const T* __restrict__ din, IT N,
+                                           IT nx, IT nxy, IT am, IT a0, IT ap) {
+  if constexpr (K < 27) {
+    constexpr int cx = cxk(K), cy = cyk(K), cz = czk(K);
+    const IT off = (IT)K * N - (IT)cz * nxy - (IT)cy * nx;
+    const IT a = cx > 0 ? am : cx < 0 ? ap : a0;
+    d[K] = load_pop(din + (off + a));
+    pull_inner<T, IT, K + 1>(d, din, N, nx, nxy, am, a0, ap);
+  }
+}
+
 // Source node of the pull for velocity slot k: x - c_k.
 template <int K, typename IT>
 __device__ __forceinline__ IT pull_src(const Nbr<IT>& n) {
@@ -63,6 +102,22 @@ __device__ __forceinline__ void bounce_back(float (&d)[27], const T* __restrict_
     }
     bounce_back<T, IT, K + 1>(d, din, N, flags, n, idx);
   }
+}
+
+// grad_norm of an inner_yz node (same loads and arithmetic order as grad_norm).
+template <typename IT>
+__device__ __forceinline__ float grad_norm_inner(const float* __restrict__ U, IT N, IT nx, IT nxy,
+                                                 IT idx, IT im, IT ip) {
+  float s = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float* Ua = U + (IT)a * N;
+    const float dx = __ldg(Ua + ip) - __ldg(Ua + im);
+    const float dy = __ldg(Ua + (idx + nx)) - __ldg(Ua + (idx - nx));
+    const float dz = __ldg(Ua + (idx + nxy)) - __ldg(Ua + (idx - nxy));
+    s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, s)));
+  }
+  return 0.5f * sqrtf(s);
 }
 
 template <typename IT>
@@ -219,7 +274,8 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
   const IT N = (IT)v.N;
   const T* __restrict__ din = static_cast<const T*>(v.d_in);
   T* __restrict__ dout = static_cast<T*>(v.d_out);
-  const Nbr<IT> n = neighbours<IT>(v, x, y, z);
+  const bool inner = inner_yz(v, y, z);
+  const Nbr<IT> n = inner ? neighbours_inner<IT>(v, x, y, z) : neighbours<IT>(v, x, y, z);
   const IT idx = n.p0 + n.r0 + n.x0;
   const uint8_t fl = __ldg(v.flags + idx);
   float d[27];
@@ -246,18 +302,24 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
   }
 
   // all independent loads first: the pull and the lagged velocity neighbourhood
-  pull_all<T, IT>(d, din, N, n);
+  const IT nxI = (IT)v.nx, nxyI = (IT)v.nx * (IT)v.ny;
+  const IT row = n.p0 + n.r0;
+  if (inner) pull_inner<T, IT>(d, din, N, nxI, nxyI, row + n.xm, idx, row + n.xp);
+  else pull_all<T, IT>(d, din, N, n);
   // an obstacle wall node completes what comes from inside the obstacle itself
   if ((fl & F_NEAR_SOLID) && !(WALLS && (fl & F_OBST_WALL)))
     bounce_back<T, IT>(d, din, N, v.flags, n, idx);
   if constexpr (WALLS) {
     if (fl & (F_WALL | F_OBST_WALL)) wall_regularize<IT>(d, v, x, y, z, fl, n);
   }
-  const float g_lag = (v.rp.adaptive && !v.rp.local) ? grad_norm<IT>(v.u_in, N, n) : 0.0f;
+  float g_lag = 0.0f;
+  if (v.rp.adaptive && !v.rp.local)
+    g_lag = inner ? grad_norm_inner<IT>(v.u_in, N, nxI, nxyI, idx, row + n.xm, row + n.xp)
+                  : grad_norm<IT>(v.u_in, N, n);
 
   raw_moments(d);
   const float drho = d[kap(0, 0, 0)];
-  const float inv = __frcp_rn(1.0f + drho);
+  const float inv = fast_rcp(1.0f + drho);
   const float ux = d[kap(1, 0, 0)] * inv, uy = d[kap(0, 1, 0)] * inv, uz = d[kap(0, 0, 1)] * inv;
   flag_error(v.err, !(1.0f + drho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 3.0f));
   if constexpr (RED) {

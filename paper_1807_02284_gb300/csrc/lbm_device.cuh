@@ -100,6 +100,14 @@ struct RelaxParams {
   int local;         // 1: |grad u| from the node's non-equilibrium moments, 0: lagged field
 };
 
+// Hardware reciprocal (PTX rcp.approx.ftz.f32, at most 1 ulp from the exact value): the
+// arguments here are densities and relaxation denominators near 1, far from denormals.
+__device__ __forceinline__ float fast_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Sec. 4.1: S_i = 1/(3 phi nu'_i + 1/2) for i >= 9 with phi = a min(|grad u|/g_max, 1) + b.
 __device__ __forceinline__ Keep keep_factors(const RelaxParams& rp, float grad_norm) {
   Keep kf;
@@ -107,7 +115,7 @@ __device__ __forceinline__ Keep keep_factors(const RelaxParams& rp, float grad_n
   float phi = 1.0f;
   if (rp.adaptive) phi = rp.a * fminf(grad_norm * rp.inv_gmax, 1.0f) + rp.b;
 #pragma unroll
-  for (int g = 0; g < 4; ++g) kf.g[g] = 1.0f - __frcp_rn(fmaf(phi, rp.nuh3[g], 0.5f));
+  for (int g = 0; g < 4; ++g) kf.g[g] = 1.0f - fast_rcp(fmaf(phi, rp.nuh3[g], 0.5f));
   return kf;
 }
 
@@ -158,7 +166,9 @@ __device__ __forceinline__ void shift_axis(float (&v)[27], float u) {
     v[b + 2 * STRIDE] = fmaf(-u, r1 + k1, r2);
   }
 }
-// Central moments about u (orders 0,1,2) back to the three populations of the line.
+// Central moments about u (orders 0,1,2) back to the three populations of the line: raw
+// moments r1 = u k0 + k1, r2 = u (k1 + r1) + k2, then f(-1) = (r2 - r1)/2, f(0) = k0 - r2,
+// f(+1) = (r2 + r1)/2 (seven operations per line).
 template <int STRIDE>
 __device__ __forceinline__ void inv_axis(float (&v)[27], float u) {
 #pragma unroll
@@ -167,9 +177,10 @@ __device__ __forceinline__ void inv_axis(float (&v)[27], float u) {
     const float k0 = v[b], k1 = v[b + STRIDE], k2 = v[b + 2 * STRIDE];
     const float r1 = fmaf(u, k0, k1);
     const float r2 = fmaf(u, k1 + r1, k2);
-    v[b] = 0.5f * (r2 - r1);
+    const float h1 = 0.5f * r1;
+    v[b] = fmaf(0.5f, r2, -h1);
     v[b + STRIDE] = k0 - r2;
-    v[b + 2 * STRIDE] = 0.5f * (r2 + r1);
+    v[b + 2 * STRIDE] = fmaf(0.5f, r2, h1);
   }
 }
 
