@@ -23,7 +23,10 @@
 // is read once and stored), pass B's lagged-velocity gather uses the clamped differences
 // (a face node's own difference involves itself), and the scalar gather counts a clamped
 // repeat of the node once.
-// Scope: one block with >= 3 nodes per axis, FP32 storage.
+// Scope: blocks with >= 3 nodes per axis, FP32 or FP16-shifted storage (the checkpoints of
+// an FP16 run hold its deviations widened to FP32; replays and transposes run in FP32), and
+// continuous-scale domains of refined and far-field blocks (the reversed Algorithm 1
+// schedule further below).
 #include <cuda_runtime.h>
 
 #include <vector>
