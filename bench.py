@@ -294,6 +294,88 @@ def _host_cores():
         return os.cpu_count() or 1
 
 
+def _outer_layer(dims):
+    nx, ny, nz = dims
+    m = np.zeros((nz, ny, nx), bool)
+    m[0], m[-1], m[:, 0], m[:, -1], m[:, :, 0], m[:, :, -1] = (True,) * 6
+    return m
+
+
+def _positions(blk, mask):
+    z, y, x = np.nonzero(mask)
+    o = np.asarray(blk.origin, float)
+    return np.stack([o[0] + blk.h * x, o[1] + blk.h * y, o[2] + blk.h * z], 1)
+
+
+def _source_nodes(src, pos):
+    """Distinct nodes of block ``src`` that the trilinear interpolation at reference-unit
+    points ``pos`` reads with a non-zero weight (obstacle corners dropped), as in the
+    mapping kernel."""
+    dims = np.asarray(src.dims)
+    q = (pos - np.asarray(src.origin, float)) / src.h
+    i0 = np.clip(np.floor(q + 1e-9).astype(np.int64), 0, np.maximum(dims - 2, 0))
+    t = q - i0
+    solid = (src.flags & 1) != 0
+    keys = []
+    for c in range(8):
+        off = np.array([c & 1, (c >> 1) & 1, c >> 2])
+        w = np.prod(np.where(off[None, :] == 1, t, 1.0 - t), axis=1)
+        idx = np.minimum(i0 + off[None, :], dims[None, :] - 1)
+        lin = (idx[:, 2] * dims[1] + idx[:, 1]) * dims[0] + idx[:, 0]
+        keep = (w > 1e-12) & ~solid.reshape(-1)[lin]
+        keys.append(lin[keep])
+    return int(np.unique(np.concatenate(keys)).size)
+
+
+def _coupling_bytes(sc, subs):
+    """Algorithmic bytes per reference step of the continuous-scale coupling (Sec. 3.2,
+    4.2.4, 4.2.5) beyond the collide-stream updates: each mapping writes 27 populations,
+    the velocity and the scalar of each destination node (124 B) and reads 27 populations,
+    the scalar and the flag byte of every distinct source node it interpolates from (113 B
+    per source time level); the fused temporal alignment also reads each updated node's
+    populations and scalar at t_n (112 B).  A refined block with l sub-steps takes l + 1
+    ghost-layer mappings per step (the refresh at t_n, one before each later sub-step, the
+    one at t_n + dt_0), reading 2 l source levels in total; post-mapping reads one level."""
+    blocks = sc.blocks
+    out = {"ghost": 0, "post": 0, "align": 0}
+    W, R = 124, 113
+    for i, b in enumerate(blocks[1:], start=1):
+        if b.h >= 1.0:
+            continue
+        lo = np.asarray(b.origin, float)
+        hi = lo + (np.asarray(b.dims) - 1) * b.h
+        par = 0
+        for j, c in enumerate(blocks[1:], start=1):      # nearest coarser block around b
+            clo = np.asarray(c.origin, float)
+            chi = clo + (np.asarray(c.dims) - 1) * c.h
+            if j != i and c.h > b.h and np.all(clo <= lo + 1e-9) and np.all(hi <= chi + 1e-9) \
+                    and c.h < blocks[par].h:
+                par = j
+        ghost = _outer_layer(b.dims) & ((b.flags & 1) == 0)
+        l = subs[i]
+        src = _source_nodes(blocks[par], _positions(b, ghost))
+        out["ghost"] += (l + 1) * int(ghost.sum()) * W + 2 * l * src * R
+        if abs(1.0 / b.h - round(1.0 / b.h)) > 1e-9:
+            upd = (~_outer_layer(b.dims)) & ((b.flags & 1) == 0)
+            out["align"] += int(upd.sum()) * 112
+        ilo, ihi = lo + b.h, hi - b.h
+        interior = np.zeros(b.shape_zyx, bool)
+        interior[1:-1, 1:-1, 1:-1] = True
+        for k, t in enumerate(blocks):
+            if not t.h > b.h:
+                continue
+            tpos = _positions(t, np.ones(t.shape_zyx, bool))
+            inside = np.all((tpos >= ilo - 1e-9) & (tpos <= ihi + 1e-9), axis=1)
+            tmask = inside.reshape(t.shape_zyx) & ((t.flags & 1) == 0)
+            if k > 0:
+                tmask &= ~_outer_layer(t.dims)
+            n_t = int(tmask.sum())
+            if n_t:
+                out["post"] += n_t * W + _source_nodes(b, _positions(t, tmask)) * R
+    out["total"] = out["ghost"] + out["post"] + out["align"]
+    return out
+
+
 def cpu_baseline_measure(budget_s=24.0, storage="fp32"):
     """The FP64 oracle as it stands, on a bounded sample of the plume workload: the same
     scene geometry scaled to a 32^3 box (inflow disk, sphere, open faces), timed with one
@@ -585,16 +667,31 @@ def run_ours(args):
     reps = repeat_record(times, K, N * ws)
 
     alg_bytes, per_fluid = 0, 0
-    for s, blk in zip(subs, sc.blocks):
-        ab, per_fluid = _algorithmic_bytes(blk.flags, storage,
-                                           local=args.workload.endswith("_local"))
+    refined = [blk.h < 1.0 for blk in sc.blocks]
+    for i, (s, blk) in enumerate(zip(subs, sc.blocks)):
+        fl = blk.flags
+        if refined[i]:           # scale-boundary nodes are written by mapping, not updated
+            fl = fl[~_outer_layer(blk.dims)]
+        ab, per_fluid = _algorithmic_bytes(fl, storage, local=args.workload.endswith("_local"))
         alg_bytes += s * ab
+    step_bytes = alg_bytes
+    coupling = _coupling_bytes(sc, subs) if any(refined) else None
+    if coupling is not None:
+        alg_bytes += coupling["total"]
     peak, peak_src = _peaks()
     achieved = alg_bytes / (t_dev / K) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": _profiled_traffic(args.workload),
                 "peak_source": peak_src, "kernel": "k_step (fused pull/collide/scalar)",
                 "bytes_per_fluid_node": per_fluid}
+    if coupling is not None:
+        roofline["kernel"] = ("whole Algorithm 1 step: k_step sub-steps (fused alignment) and "
+                              "k_map prior- / post-mappings")
+        roofline["bytes_per_reference_step"] = {"collide_stream": int(step_bytes),
+                                                "alignment": coupling["align"],
+                                                "ghost_mappings": coupling["ghost"],
+                                                "post_mappings": coupling["post"]}
+        roofline["frac_collide_stream_bytes_only"] = step_bytes / (t_dev / K) / 1e9 / peak
     i0 = dom.info(0)
     roofline["launch"] = {"tile": [int(i0.tile[0]), int(i0.tile[1])],
                           "ctas_per_sm": int(i0.ctas_per_sm)}

@@ -56,3 +56,23 @@ def test_repeat_record_reports_the_median_call():
     assert rec["ms_per_step_best"] == 0.10 / 10 * 1e3 and rec["ms_per_step_worst"] == 50.0
     assert rec["value_best"] == 1000 * 10 / 0.10 / 1e6
     assert abs(rec["device_seconds"] - 1.1) < 1e-12
+
+
+def test_coupling_bytes_of_a_worked_two_block_case():
+    """s0 8^3 with a block at h = 1/2, origin (2, 2, 2), 7^3 nodes (reference span [2, 5]):
+    every scale-boundary position has a coordinate on the cube's surface, so its corners of
+    non-zero weight are the 4^3 - 2^3 = 56 surface nodes of s0 in [2, 5]^3; post-mapping
+    targets the 8 s0 nodes with coordinates 3, 4, which sit exactly on fine nodes (one corner
+    each).  Two sub-steps land on t_n + dt_0: no alignment."""
+    import synth
+    s0 = synth._empty_block((8, 8, 8))
+    s1 = synth._empty_block((7, 7, 7), origin=(2.0, 2.0, 2.0), h=0.5)
+    sc = synth.Scene(blocks=[s0, s1], periodic=(False,) * 3, nu=0.01)
+    got = bench._coupling_bytes(sc, [1, 2])
+    ghost_nodes = 7 ** 3 - 5 ** 3
+    assert got["ghost"] == 3 * ghost_nodes * 124 + 4 * 56 * 113
+    assert got["post"] == 8 * 124 + 8 * 113
+    assert got["align"] == 0
+    s1b = synth._empty_block((7, 7, 7), origin=(2.0, 2.0, 2.0), h=1 / 1.5)
+    sc2 = synth.Scene(blocks=[synth._empty_block((8, 8, 8)), s1b], periodic=(False,) * 3, nu=0.01)
+    assert bench._coupling_bytes(sc2, [1, 2])["align"] == 5 ** 3 * 112
