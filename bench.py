@@ -246,7 +246,8 @@ def _workload(name):
         sc = synth.plume(256)
         sc.blocks.append(synth.far_block(sc.blocks[0], 2.0, 64.0, seed=9, amp=0.0))
         return sc, "fp32"
-    sc = synth.plume(128 if name.startswith("plume128") else 256)   # also plume256_walls
+    m = re.match(r"plume(\d+)", name)       # plume256, plume128_fp16, plume256_walls, ...
+    sc = synth.plume(int(m.group(1)) if m else 256)
     return sc, storage
 
 
@@ -1226,6 +1227,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--workload", default="plume256",
                     choices=["plume256", "plume256_fp16", "plume128", "plume128_fp16",
+                             "plume192", "plume192_fp16",
                              "multiscale3", "batch64", "adjoint128", "adjoint64",
                              "plume256_local", "dynamic256", "farfield256", "plume256_walls",
                              "ringing196", "plume256_regwall", "plume256_slab2"])

@@ -407,7 +407,9 @@ lbm_status lbm_adjoint_block_grad(lbm_domain* dom, int32_t block_id, float* dL_d
      cuda_stream  stream the work is enqueued on (NULL = legacy default stream); the call
              does not synchronise.
    The first call on a device (with that device current) looks up the array's device
-   address; make that first call before any stream capture.  All calls share the one array,
+   address and keeps it for the life of the process; make that first call before any
+   stream capture, and do not call this entry point again after a context reset
+   (cudaDeviceReset) of that device, which invalidates the address.  All calls share the one array,
    so calls whose work overlaps on the GPU (different streams, or different host threads on
    one device) race with each other; serialise them.  Errors are reported through
    lbm_last_error(NULL). */

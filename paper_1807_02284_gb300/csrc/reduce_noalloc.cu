@@ -11,6 +11,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
+#include "reduce_util.cuh"
 
 namespace lbm {
 
@@ -25,44 +26,42 @@ static_assert(NOALLOC_MAX_CTAS * NOALLOC_NODES_PER_CTA == LBM_REDUCE_NOALLOC_MAX
 // CTAs it launches before reading them, so nothing has to start at zero.
 static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_CTAS * 6];
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // f: 27 planes of unshifted populations in the paper's order; one CTA per chunk of nodes.
+// Per node the deviations f - w from the lattice weights are summed in FP32 (small numbers:
+// no cancellation against the weights), per thread with compensated FP32 sums, and combined
+// across threads in FP64 in a fixed order.
 template <typename I>
 __global__ void __launch_bounds__(NOALLOC_THREADS)
 k_reduce_noalloc(const I* __restrict__ f, const uint8_t* __restrict__ flags, size_t N,
                  double* __restrict__ partials) {
   const size_t lo = (size_t)blockIdx.x * NOALLOC_NODES_PER_CTA;
   const size_t hi = lo + NOALLOC_NODES_PER_CTA < N ? lo + NOALLOC_NODES_PER_CTA : N;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  unsigned count = 0;
+  KahanF acc[5];
   for (size_t idx = lo + threadIdx.x; idx < hi; idx += NOALLOC_THREADS) {
     if (flags && (flags[idx] & (F_SOLID | F_GHOST))) continue;
-    double drho = 0, jx = 0, jy = 0, jz = 0;
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int q = 0; q < 27; ++q) {
       const int k = paper_to_cube(q);
-      const double v = (double)f[(size_t)q * N + idx];
-      drho += v - wkd(k);
-      jx += cxk(k) * v;
-      jy += cyk(k) * v;
-      jz += czk(k) * v;
+      const float d = (float)(f[(size_t)q * N + idx] - (I)wkd(k));
+      drho += d;
+      if (cxk(k) > 0) jx += d; else if (cxk(k) < 0) jx -= d;
+      if (cyk(k) > 0) jy += d; else if (cyk(k) < 0) jy -= d;
+      if (czk(k) > 0) jz += d; else if (czk(k) < 0) jz -= d;
     }
-    acc[0] += 1.0;
-    acc[1] += drho;
-    acc[2] += jx;
-    acc[3] += jy;
-    acc[4] += jz;
-    acc[5] += 0.5 * (jx * jx + jy * jy + jz * jz) / (1.0 + drho);
+    ++count;
+    acc[0].add(drho);
+    acc[1].add(jx);
+    acc[2].add(jy);
+    acc[3].add(jz);
+    acc[4].add(0.5f * (jx * jx + jy * jy + jz * jz) / (1.0f + drho));
   }
   __shared__ double sh[NOALLOC_THREADS / 32][6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    const double w = warp_sum_d(acc[i]);
+    const double w = warp_sum(i == 0 ? (double)count : acc[i - 1].value());
     if (lane == 0) sh[wid][i] = w;
   }
   __syncthreads();
@@ -73,14 +72,16 @@ k_reduce_noalloc(const I* __restrict__ f, const uint8_t* __restrict__ flags, siz
   }
 }
 
-__global__ void k_reduce_noalloc_final(const double* __restrict__ partials, int n_ctas,
-                                       double* __restrict__ out) {
+// One warp per value: lane l sums partials l, l + 32, ... in order, a fixed shuffle tree
+// combines the lanes; mass = node count + sum of (rho - 1).
+__global__ void __launch_bounds__(192) k_reduce_noalloc_final(const double* __restrict__ partials,
+                                                              int n_ctas, double* __restrict__ out) {
   __shared__ double tot[6];
-  if (threadIdx.x < 6) {
-    double s = 0;
-    for (int b = 0; b < n_ctas; ++b) s += partials[b * 6 + threadIdx.x];
-    tot[threadIdx.x] = s;
-  }
+  const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double s = 0;
+  for (int b = lane; b < n_ctas; b += 32) s += partials[b * 6 + v];
+  s = warp_sum(s);
+  if (lane == 0) tot[v] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     out[0] = tot[0] + tot[1];
@@ -93,6 +94,8 @@ __global__ void k_reduce_noalloc_final(const double* __restrict__ partials, int 
 
 // Device address of the scratch array, looked up once per device with that device current.
 // In host code the array's name is only a host-side stand-in, so kernels get this address.
+// The cached address belongs to the device's primary context: a context reset
+// (cudaDeviceReset) invalidates it, and the entry point must not be called afterwards.
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
@@ -147,7 +150,7 @@ extern "C" lbm_status lbm_reduce_noalloc(const void* f, int32_t dtype, const uin
   else
     k_reduce_noalloc<float><<<n_ctas, NOALLOC_THREADS, 0, s>>>(static_cast<const float*>(f),
                                                                flags, N, scratch);
-  k_reduce_noalloc_final<<<1, 32, 0, s>>>(scratch, n_ctas, out);
+  k_reduce_noalloc_final<<<1, 192, 0, s>>>(scratch, n_ctas, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     lbm_set_global_error(cudaGetErrorString(e));

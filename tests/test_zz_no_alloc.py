@@ -64,3 +64,41 @@ def test_noalloc_reduce_rejects_sizes_beyond_its_scratch(lib):
                                 C.c_void_p(dummy.data_ptr()), None)
     assert st == lbm.LBM_ERR_INVALID_ARG
     assert b"n_nodes" in lib.lbm_last_error(None)
+
+
+def _reference(f, flags, N):
+    """Mass, momentum and kinetic energy of non-obstacle, non-ghost nodes, in FP64 from the
+    definitions (rho = sum f, j = sum c f over the paper's velocity list)."""
+    from oracle import cmr
+    f = f.view(27, N).double()
+    keep = (flags & 9) == 0
+    rho = f.sum(0)
+    j = cmr.C.to(f.device).T @ f
+    return np.array([float(rho[keep].sum()), *(float(j[a][keep].sum()) for a in range(3)),
+                     float((0.5 * (j * j).sum(0) / rho)[keep].sum())])
+
+
+def test_noalloc_reduce_many_partials_between_small_calls(lib):
+    """A 128^3 field (128 per-CTA partials) between two small calls (3 partials): no call
+    depends on what an earlier call of another size left in the shared scratch."""
+    from oracle import cmr
+    from paper_1807_02284_gb300 import lbm
+    stream = torch.cuda.current_stream()
+    w = cmr.equilibrium(torch.ones(1, dtype=torch.float64),
+                        torch.zeros(1, 3, dtype=torch.float64))[0].cuda()
+    out = torch.empty(5, dtype=torch.float64, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(7)
+    for n in (40 * 36 * 30, 128 ** 3, 40 * 36 * 30):
+        f = (w[:, None] * (1.0 + 0.02 * (2 * torch.rand(27, n, generator=g, device="cuda",
+                                                       dtype=torch.float64) - 1))).contiguous()
+        flags = (torch.rand(n, generator=g, device="cuda") < 0.05).to(torch.uint8)
+        flags[::97] |= 8
+        ref = _reference(f, flags, n)
+        for dt, arr in ((lbm.LBM_F64, f), (lbm.LBM_F32, f.float())):
+            out.fill_(float("nan"))
+            st = lib.lbm_reduce_noalloc(C.c_void_p(arr.data_ptr()), dt,
+                                        C.c_void_p(flags.data_ptr()), n,
+                                        C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
+            assert st == lbm.LBM_OK
+            torch.cuda.synchronize()
+            _check(out.cpu().numpy(), ref)
