@@ -139,6 +139,8 @@ typedef struct {
   int32_t tile[2];   /* x, y extent of the collide-stream thread tile (chosen by autotuning) */
   int32_t ctas_per_sm; /* CTAs per SM the collide-stream kernel's registers are bounded for
                           (3 or 4, chosen by autotuning together with the tile) */
+  int32_t parent;      /* a refined block's prior-mapping source (the finest coarser block
+                          containing it); -1 for the reference block and far-field blocks */
 } lbm_block_info;
 
 /* Version of this header's ABI. */
@@ -332,6 +334,67 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
 size_t lbm_plane_bytes(const lbm_domain* dom, int32_t dir);
 lbm_status lbm_pack_plane(lbm_domain* dom, int32_t z, int32_t dir, void* dev_buf);
 lbm_status lbm_unpack_plane(lbm_domain* dom, int32_t z, int32_t dir, const void* dev_buf);
+
+/* One reference step of Algorithm 1 (Sec. 4.2.4-4.2.5) as a sequence of phases, so that the
+   blocks of one continuous-scale domain can be placed on several devices or processes (no
+   counterpart in the paper, which runs one GPU).  Every participant holds the whole domain
+   (same blocks, flags and initial state) and issues the same phases in the same order:
+     LBM_PHASE_BEGIN                       records every block's level at t_n;
+     LBM_PHASE_REFERENCE                   the reference block's step (block ignored);
+     then for every refined block b = 1, 2, ... in order:
+       LBM_PHASE_BLOCK, b                  b's sub-cycle: scale boundary at t_n from its
+                                           prior-mapping source (lerped between that block's
+                                           levels at t_n and now), l sub-steps, the last with
+                                           the temporal alignment, scale boundary at
+                                           t_n + dt_0;
+       LBM_PHASE_POST, b                   post-mapping of b's interior into every coarser
+                                           block;
+     LBM_PHASE_END                         closes the step (one step is counted).
+   compute != 0 launches the phase's work on the domain's stream; compute == 0 only advances
+   the block's time levels the way the work would, so the level indices stay the same on
+   every participant.  A block's owner computes its phases; before LBM_PHASE_BLOCK of b the
+   owner of b's prior-mapping source sends it the boxes of
+   lbm_mapping_boxes(LBM_BOX_PRIOR_SOURCE) at LBM_LEVEL_START and LBM_LEVEL_CURRENT, and
+   after LBM_PHASE_POST of b the owner of b sends the LBM_BOX_POST_TARGET box of every
+   coarser block it post-mapped into to that block's owner.  With every phase computed the result is bit for
+   bit that of lbm_step(dom, 1).  STATE for a phase out of this order or while an adjoint
+   tape records; UNSUPPORTED for domains with far-field blocks; INVALID_ARG for an unknown
+   phase or a block that is not refined. */
+enum {
+  LBM_PHASE_BEGIN = 0, LBM_PHASE_REFERENCE = 1, LBM_PHASE_BLOCK = 2, LBM_PHASE_POST = 3,
+  LBM_PHASE_END = 4
+};
+lbm_status lbm_step_phase(lbm_domain* dom, int32_t phase, int32_t block, int32_t compute);
+
+/* Node boxes (inclusive index ranges lo[0..2] .. hi[0..2] in x, y, z) of one block that the
+   mappings of refined block `block` exchange with block `other`:
+     LBM_BOX_PRIOR_SOURCE  other = block's prior-mapping source: six boxes, one per face of
+                           block (every corner of the trilinear cell of a scale-boundary node
+                           lies in the box of its face);
+     LBM_BOX_POST_TARGET   other = a coarser block: one box holding every node of `other`
+                           that block's post-mapping writes (none if it writes none).
+   boxes receives 6 int32 per box (lo then hi), room for 6 boxes; *n_boxes their number.
+   INVALID_ARG for null pointers, a block that is not refined or a wrong `other`. */
+enum { LBM_BOX_PRIOR_SOURCE = 0, LBM_BOX_POST_TARGET = 1 };
+lbm_status lbm_mapping_boxes(const lbm_domain* dom, int32_t block, int32_t kind, int32_t other,
+                             int32_t* boxes, int32_t* n_boxes);
+
+/* A node box of a block's state as a device buffer: 27 population planes as stored (shifted,
+   library slot order), 3 velocity planes and the scalar plane, FP32, one value per box node
+   in x-fastest order (lbm_box_bytes gives the size: 124 bytes per node; 0 for an invalid
+   box).  level: LBM_LEVEL_CURRENT, or LBM_LEVEL_START (the level at LBM_PHASE_BEGIN, inside
+   a phased step).  lbm_unpack_box leaves the nodes whose flags carry any bit of skip_flags
+   (LBM_FIELD_FLAGS bits) unchanged.  Queued on the domain's stream; dev_buf is caller-owned
+   device memory, 16-byte aligned, of lbm_box_bytes bytes.  INVALID_ARG for a box outside
+   the block, a null or unaligned buffer or another level; UNSUPPORTED without FP32 storage;
+   STATE for LBM_LEVEL_START outside a phased step. */
+enum { LBM_LEVEL_CURRENT = 0, LBM_LEVEL_START = 1 };
+size_t lbm_box_bytes(const lbm_domain* dom, int32_t block, const int32_t lo[3],
+                     const int32_t hi[3]);
+lbm_status lbm_pack_box(lbm_domain* dom, int32_t block, int32_t level, const int32_t lo[3],
+                        const int32_t hi[3], void* dev_buf);
+lbm_status lbm_unpack_box(lbm_domain* dom, int32_t block, int32_t level, const int32_t lo[3],
+                          const int32_t hi[3], const void* dev_buf, int32_t skip_flags);
 
 /* Advances n independent single-block domains by `steps` reference steps with one
    persistent kernel per step over a joint tile work list, captured in one CUDA graph and

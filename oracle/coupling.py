@@ -362,8 +362,14 @@ class MultiScale:
         return out
 
     # --------------------------------------------------------------------- Algorithm 1
-    def step(self):
-        saved = [b.state.clone() for b in self.blocks]
+    # One reference step, split into the phases a placement of blocks on several ranks
+    # exchanges data between (begin, reference, per refined block its sub-cycle and its
+    # post-mapping, end); step() runs them in order.
+    def begin(self):
+        self.saved = [b.state.clone() for b in self.blocks]
+
+    def step_reference(self):
+        """s0's step, then the far-field blocks' steps and their two mappings."""
         b0 = self.blocks[0]
         b0.state = grid.step(b0.state, b0.params)
         far = [i for i, b in enumerate(self.blocks) if b.far]
@@ -373,29 +379,47 @@ class MultiScale:
             self.post_map(self.blocks[i].child, i)
         for i in reversed(far):            # scale boundary of each child from its far block
             self.far_out_map(i)
-        for i in range(1, len(self.blocks)):
-            b = self.blocks[i]
-            if b.far:
-                continue
-            states = [b.state]
-            for j in range(1, b.substeps + 1):
-                self.prior_map(i, (j - 1) * b.h, saved)
-                if j == 1:
-                    # the block's t_n state, with its ghost layer refreshed from the source
-                    # at t_n, is what finer blocks interpolate from
-                    saved[i] = b.state.clone()
-                b.state = grid.step(b.state, b.params)
-                states.append(b.state)
-            if b.integer_ratio and abs(b.substeps * b.h - 1.0) < 1e-9:
-                b.state = b.state.clone()
-            else:
-                prev = states[-2] if len(states) >= 2 else states[0]
-                b.state = self.align(b, saved[i], prev, states[-1])
-            self.prior_map(i, 1.0, saved)
-            for k in range(len(self.blocks)):
-                if self.blocks[k].h > b.h and not self.blocks[k].far:
-                    self.post_map(i, k)
+
+    def step_block(self, i):
+        """Refined block i's sub-cycle: sub-steps with their scale boundaries, temporal
+        alignment, and the scale boundary at t_n + dt_0."""
+        b = self.blocks[i]
+        saved = self.saved
+        states = [b.state]
+        for j in range(1, b.substeps + 1):
+            self.prior_map(i, (j - 1) * b.h, saved)
+            if j == 1:
+                # the block's t_n state, with its ghost layer refreshed from the source
+                # at t_n, is what finer blocks interpolate from
+                saved[i] = b.state.clone()
+            b.state = grid.step(b.state, b.params)
+            states.append(b.state)
+        if b.integer_ratio and abs(b.substeps * b.h - 1.0) < 1e-9:
+            b.state = b.state.clone()
+        else:
+            prev = states[-2] if len(states) >= 2 else states[0]
+            b.state = self.align(b, saved[i], prev, states[-1])
+        self.prior_map(i, 1.0, saved)
+
+    def post_block(self, i):
+        """Post-mapping of refined block i into every coarser block."""
+        b = self.blocks[i]
+        for k in range(len(self.blocks)):
+            if self.blocks[k].h > b.h and not self.blocks[k].far:
+                self.post_map(i, k)
+
+    def end(self):
         self.step_count += 1
+
+    def step(self):
+        self.begin()
+        self.step_reference()
+        for i in range(1, len(self.blocks)):
+            if self.blocks[i].far:
+                continue
+            self.step_block(i)
+            self.post_block(i)
+        self.end()
 
     def run(self, n):
         for _ in range(n):

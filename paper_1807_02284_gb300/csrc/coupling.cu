@@ -342,19 +342,26 @@ static void release_block(lbm_domain* dom, Block& B) {
 // Table of the nodes of block T that lie in block S's interior span [o + h, o + (n-2) h] on
 // every axis, with their source cells in S (prior-mapping regions of refined blocks' post
 // maps, and of far blocks' overlap).
-static std::vector<MapEntry> interior_table(const Block& S, const Block& T) {
-  std::vector<MapEntry> tab;
+// Index box of the nodes of block T inside block S's interior span [o + h, o + (n-2) h] on
+// every axis; false if it is empty.
+static bool interior_box(const Block& S, const Block& T, int lo[3], int hi[3]) {
   const int nT[3] = {T.nx, T.ny, T.nz};
   const int nS[3] = {S.nx, S.ny, S.nz};
-  int lo[3], hi[3];
   for (int a = 0; a < 3; ++a) {
     const double plo = S.origin[a] + S.h, phi = S.origin[a] + (nS[a] - 2) * S.h;
     lo[a] = std::max(0, (int)std::ceil((plo - 1e-9 - T.origin[a]) / T.h));
     hi[a] = std::min(nT[a] - 1, (int)std::floor((phi + 1e-9 - T.origin[a]) / T.h));
     while (lo[a] <= hi[a] && T.origin[a] + lo[a] * T.h < plo - 1e-9) ++lo[a];
     while (hi[a] >= lo[a] && T.origin[a] + hi[a] * T.h > phi + 1e-9) --hi[a];
-    if (lo[a] > hi[a]) return tab;
+    if (lo[a] > hi[a]) return false;
   }
+  return true;
+}
+
+static std::vector<MapEntry> interior_table(const Block& S, const Block& T) {
+  std::vector<MapEntry> tab;
+  int lo[3], hi[3];
+  if (!interior_box(S, T, lo, hi)) return tab;
   tab.reserve((size_t)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1));
   for (int z = lo[2]; z <= hi[2]; ++z)
     for (int y = lo[1]; y <= hi[1]; ++y)
@@ -800,4 +807,282 @@ lbm_status multiscale_step(lbm_domain* dom) {
       if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping join");
     }
   return LBM_OK;
+}
+
+// ------------------------------------------------------------------ phase-by-phase stepping
+//
+// One reference step of Algorithm 1 as a sequence of calls, so that the blocks of one
+// continuous-scale domain can be advanced by different processes (each holds the whole
+// domain, computes the blocks it owns and receives, between phases, the node boxes of other
+// blocks that its mappings read or that other ranks' mappings wrote).  Every rank issues the
+// same phases; a phase that a rank does not compute only advances the block's time levels
+// exactly as computing it would, so level indices agree on all ranks.  The kernels, their
+// inputs and their order are those of multiscale_step (launched one after another on the
+// domain's stream), so the results are bit-identical to lbm_step.
+
+namespace lbm {
+
+// Packs (dir 0) or unpacks (dir 1) the box lo..hi of one level of a block: 27 population
+// planes as stored (FP32), then 3 velocity planes and the scalar plane, nb values each.
+// Unpacking leaves nodes whose flags carry any bit of `skip` unchanged.
+__global__ void k_box(float* f, float* u, float* c, const uint8_t* flags, int nx, int ny,
+                      size_t N, int3 lo, int3 dim, size_t nb, float* buf, int dir, int skip) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nb;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int x = lo.x + (int)(i % dim.x);
+    const int y = lo.y + (int)((i / dim.x) % dim.y);
+    const int z = lo.z + (int)(i / ((size_t)dim.x * dim.y));
+    const size_t idx = ((size_t)z * ny + y) * nx + x;
+    if (dir == 0) {
+#pragma unroll
+      for (int k = 0; k < 27; ++k) buf[(size_t)k * nb + i] = f[(size_t)k * N + idx];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) buf[(size_t)(27 + a) * nb + i] = u[(size_t)a * N + idx];
+      buf[(size_t)30 * nb + i] = c[idx];
+    } else {
+      if (flags[idx] & skip) continue;
+#pragma unroll
+      for (int k = 0; k < 27; ++k) f[(size_t)k * N + idx] = buf[(size_t)k * nb + i];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) u[(size_t)a * N + idx] = buf[(size_t)(27 + a) * nb + i];
+      c[idx] = buf[(size_t)30 * nb + i];
+    }
+  }
+}
+
+}  // namespace lbm
+
+namespace {
+
+// Level a refined block ends a reference step in, starting from level L (the rotation of
+// multiscale_step: the first sub-step writes L + 1, then the other two levels alternate).
+int final_level(const Block& B, int L) {
+  const int A = (L + 1) % 3, Bv = (L + 2) % 3;
+  int c = L;
+  for (int j = 1; j <= B.substeps; ++j) c = (j == 1) ? A : (c == A ? Bv : A);
+  return c;
+}
+
+// The whole sub-cycle of refined block b in one stream: ghost layer at t_n, then per
+// sub-step the collide-stream (the last one with the temporal alignment unless the ratio
+// is an integer) followed by the ghost layer of its output level.
+cudaError_t block_subcycle(lbm_domain* dom, int b, cudaStream_t s) {
+  Block& B = dom->blocks[b];
+  const std::vector<int>& saved = dom->phase_saved;
+  const int L = saved[b];
+  const int A = (L + 1) % 3, Bv = (L + 2) % 3;
+  const bool exact = B.integer_ratio && std::fabs(B.substeps * B.h - 1.0) < 1e-9;
+  cudaError_t e = prior_map(dom, b, saved, 0.0f, L, s);
+  int cur = L;
+  for (int j = 1; j <= B.substeps && e == cudaSuccess; ++j) {
+    const int out = (j == 1) ? A : (cur == A ? Bv : A);
+    BlockView v = dom->view(b, cur, out);
+    if (j == B.substeps && !exact) {
+      const double t1 = (B.substeps - 1) * B.h, t2 = B.substeps * B.h, T = 1.0;
+      v.f_al0 = B.lv[L].f;
+      v.c_al0 = B.lv[L].c;
+      v.al0 = (float)((T - t1) * (T - t2) / ((0.0 - t1) * (0.0 - t2)));
+      v.al1 = (float)((T - 0.0) * (T - t2) / ((t1 - 0.0) * (t1 - t2)));
+      v.al2 = (float)((T - 0.0) * (T - t1) / ((t2 - 0.0) * (t2 - t1)));
+      e = launch_step_align(v, B.bx, B.by, s, B.minb);
+    } else {
+      e = launch_step(v, dom->desc.storage, B.bx, B.by, s, B.minb);
+    }
+    const float theta = j < B.substeps ? (float)(j * B.h) : 1.0f;
+    if (e == cudaSuccess) e = prior_map(dom, b, saved, theta, out, s);
+    cur = out;
+  }
+  B.cur = cur;
+  return e;
+}
+
+// Ghost-layer source box of refined block b in its parent P, face f (axis f / 2, low or high
+// side f % 2): the parent nodes that are corners of the trilinear cells of that face's nodes.
+void prior_face_box(const Block& P, const Block& B, int f, int lo[3], int hi[3]) {
+  const int nB[3] = {B.nx, B.ny, B.nz}, nP[3] = {P.nx, P.ny, P.nz};
+  for (int a = 0; a < 3; ++a) {
+    double p0 = B.origin[a], p1 = B.origin[a] + (nB[a] - 1) * B.h;
+    if (a == f / 2) p0 = p1 = (f % 2) ? p1 : p0;
+    int i0 = (int)std::floor((p0 - P.origin[a]) / P.h);
+    int i1 = (int)std::floor((p1 - P.origin[a]) / P.h);
+    i0 = std::max(0, std::min(i0, std::max(nP[a] - 2, 0)));
+    i1 = std::max(0, std::min(i1, std::max(nP[a] - 2, 0)));
+    lo[a] = i0;
+    hi[a] = std::min(i1 + 1, nP[a] - 1);
+  }
+}
+
+bool valid_box(const Block& B, const int32_t lo[3], const int32_t hi[3]) {
+  const int n[3] = {B.nx, B.ny, B.nz};
+  for (int a = 0; a < 3; ++a)
+    if (lo[a] < 0 || hi[a] >= n[a] || lo[a] > hi[a]) return false;
+  return true;
+}
+
+size_t box_nodes(const int32_t lo[3], const int32_t hi[3]) {
+  return (size_t)(hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_step_phase(lbm_domain* dom, int32_t phase, int32_t block,
+                                     int32_t compute) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  const int nb = (int)dom->blocks.size();
+  cudaStream_t s = dom->stream;
+  cudaError_t e = cudaSuccess;
+  switch (phase) {
+    case LBM_PHASE_BEGIN: {
+      if (dom->phase_open) return dom->fail(LBM_ERR_STATE, "a phased step is already open");
+      if (dom->tape) return dom->fail(LBM_ERR_STATE, "phased steps do not record an adjoint tape");
+      for (int b = 1; b < nb; ++b)
+        if (dom->blocks[b].far)
+          return dom->fail(LBM_ERR_UNSUPPORTED, "phased steps cover refined blocks, not far-field blocks");
+      for (int b = 0; b < nb; ++b) {
+        lbm_status st = dom->autotune_tiles(b);
+        if (st != LBM_OK) return st;
+      }
+      dom->phase_saved.assign(nb, 0);
+      for (int b = 0; b < nb; ++b) dom->phase_saved[b] = dom->blocks[b].cur;
+      dom->phase_done.assign(nb, 0);
+      dom->phase_ref_done = false;
+      dom->phase_open = true;
+      return LBM_OK;
+    }
+    case LBM_PHASE_REFERENCE: {
+      if (!dom->phase_open || dom->phase_ref_done)
+        return dom->fail(LBM_ERR_STATE, "the reference phase follows LBM_PHASE_BEGIN, once");
+      Block& B0 = dom->blocks[0];
+      const int nxt = B0.cur ^ 1;
+      if (compute) e = launch_step(dom->view(0, B0.cur, nxt), dom->desc.storage, B0.bx, B0.by, s, B0.minb);
+      if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");
+      B0.cur = nxt;
+      dom->phase_ref_done = true;
+      return LBM_OK;
+    }
+    case LBM_PHASE_BLOCK:
+    case LBM_PHASE_POST: {
+      if (!dom->phase_open || !dom->phase_ref_done)
+        return dom->fail(LBM_ERR_STATE, "block phases follow the reference phase");
+      if (block < 1 || block >= nb) return dom->fail(LBM_ERR_INVALID_ARG, "block must be a refined block");
+      if (phase == LBM_PHASE_BLOCK) {
+        for (int b = 1; b < block; ++b)
+          if (dom->phase_done[b] != 2)
+            return dom->fail(LBM_ERR_STATE, "blocks are advanced in order, each after the previous one's post-mapping");
+        if (dom->phase_done[block] != 0) return dom->fail(LBM_ERR_STATE, "block already advanced");
+        Block& B = dom->blocks[block];
+        if (compute) {
+          e = block_subcycle(dom, block, s);
+          if (e != cudaSuccess) return dom->cuda_fail(e, "refined-block sub-cycle");
+        } else {
+          B.cur = final_level(B, dom->phase_saved[block]);
+        }
+        dom->phase_done[block] = 1;
+      } else {
+        if (dom->phase_done[block] != 1) return dom->fail(LBM_ERR_STATE, "post-mapping follows the block's sub-cycle");
+        if (compute) {
+          const Block& B = dom->blocks[block];
+          for (size_t t = 0; t < B.post.size() && e == cudaSuccess; ++t) e = post_map(dom, block, B.post[t], s);
+          if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping");
+        }
+        dom->phase_done[block] = 2;
+      }
+      return LBM_OK;
+    }
+    case LBM_PHASE_END: {
+      if (!dom->phase_open || !dom->phase_ref_done)
+        return dom->fail(LBM_ERR_STATE, "no phased step to end");
+      for (int b = 1; b < nb; ++b)
+        if (dom->phase_done[b] != 2) return dom->fail(LBM_ERR_STATE, "every block's phases come before the end");
+      dom->phase_open = false;
+      ++dom->steps;
+      return LBM_OK;
+    }
+    default:
+      return dom->fail(LBM_ERR_INVALID_ARG, "unknown phase");
+  }
+}
+
+extern "C" lbm_status lbm_mapping_boxes(const lbm_domain* dom_c, int32_t block, int32_t kind,
+                                        int32_t other, int32_t* boxes, int32_t* n_boxes) {
+  lbm_domain* dom = const_cast<lbm_domain*>(dom_c);
+  if (!dom || !boxes || !n_boxes) return LBM_ERR_INVALID_ARG;
+  const int nb = (int)dom->blocks.size();
+  if (block < 1 || block >= nb || dom->blocks[block].far)
+    return dom->fail(LBM_ERR_INVALID_ARG, "block must be a refined block");
+  const Block& B = dom->blocks[block];
+  *n_boxes = 0;
+  if (kind == LBM_BOX_PRIOR_SOURCE) {
+    if (other != B.prior.src) return dom->fail(LBM_ERR_INVALID_ARG, "other must be the block's prior-mapping source");
+    const Block& P = dom->blocks[other];
+    for (int f = 0; f < 6; ++f) {
+      int lo[3], hi[3];
+      prior_face_box(P, B, f, lo, hi);
+      for (int a = 0; a < 3; ++a) { boxes[6 * f + a] = lo[a]; boxes[6 * f + 3 + a] = hi[a]; }
+    }
+    *n_boxes = 6;
+    return LBM_OK;
+  }
+  if (kind == LBM_BOX_POST_TARGET) {
+    if (other < 0 || other >= nb) return dom->fail(LBM_ERR_INVALID_ARG, "other must be a block");
+    bool has = false;
+    for (const MapTable& t : B.post) has |= t.dst == other && t.n > 0;
+    if (!has) return LBM_OK;         // no post-mapping into `other`
+    int lo[3], hi[3];
+    if (!interior_box(B, dom->blocks[other], lo, hi)) return LBM_OK;
+    for (int a = 0; a < 3; ++a) { boxes[a] = lo[a]; boxes[3 + a] = hi[a]; }
+    *n_boxes = 1;
+    return LBM_OK;
+  }
+  return dom->fail(LBM_ERR_INVALID_ARG, "unknown box kind");
+}
+
+extern "C" size_t lbm_box_bytes(const lbm_domain* dom, int32_t block, const int32_t lo[3],
+                                const int32_t hi[3]) {
+  if (!dom || !lo || !hi || block < 0 || block >= (int32_t)dom->blocks.size()) return 0;
+  if (!valid_box(dom->blocks[block], lo, hi)) return 0;
+  return box_nodes(lo, hi) * 31 * sizeof(float);
+}
+
+static lbm_status box_transfer(lbm_domain* dom, int32_t block, int32_t level, const int32_t lo[3],
+                               const int32_t hi[3], void* buf, int dir, int32_t skip) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (!lo || !hi || !buf) return dom->fail(LBM_ERR_INVALID_ARG, "null box or buffer");
+  if (reinterpret_cast<uintptr_t>(buf) % 16 != 0) return dom->fail(LBM_ERR_INVALID_ARG, "buffer must be 16-byte aligned");
+  if (block < 0 || block >= (int32_t)dom->blocks.size()) return dom->fail(LBM_ERR_INVALID_ARG, "no such block");
+  if (dom->desc.storage != LBM_FP32) return dom->fail(LBM_ERR_UNSUPPORTED, "node boxes need FP32 storage");
+  Block& B = dom->blocks[block];
+  if (!valid_box(B, lo, hi)) return dom->fail(LBM_ERR_INVALID_ARG, "box outside the block");
+  int lv = B.cur;
+  if (level == LBM_LEVEL_START) {
+    if (!dom->phase_open) return dom->fail(LBM_ERR_STATE, "the start level exists inside a phased step");
+    lv = dom->phase_saved[block];
+  } else if (level != LBM_LEVEL_CURRENT) {
+    return dom->fail(LBM_ERR_INVALID_ARG, "level must be LBM_LEVEL_START or LBM_LEVEL_CURRENT");
+  }
+  const size_t nb = box_nodes(lo, hi);
+  const int3 l3 = make_int3(lo[0], lo[1], lo[2]);
+  const int3 d3 = make_int3(hi[0] - lo[0] + 1, hi[1] - lo[1] + 1, hi[2] - lo[2] + 1);
+  const size_t g = (nb + 255) / 256;
+  const int grid = (int)(g < 4096 ? g : 4096);
+  Level& L = B.lv[lv];
+  k_box<<<grid, 256, 0, dom->stream>>>(static_cast<float*>(L.f), L.u, L.c, B.flags, B.nx, B.ny,
+                                       B.N, l3, d3, nb, static_cast<float*>(buf), dir, skip);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return dom->cuda_fail(e, "node box copy");
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_pack_box(lbm_domain* dom, int32_t block, int32_t level,
+                                   const int32_t lo[3], const int32_t hi[3], void* dev_buf) {
+  return box_transfer(dom, block, level, lo, hi, dev_buf, 0, 0);
+}
+
+extern "C" lbm_status lbm_unpack_box(lbm_domain* dom, int32_t block, int32_t level,
+                                     const int32_t lo[3], const int32_t hi[3],
+                                     const void* dev_buf, int32_t skip_flags) {
+  return box_transfer(dom, block, level, lo, hi, const_cast<void*>(dev_buf), 1,
+                      skip_flags & 0xFF);
 }

@@ -190,7 +190,7 @@ const void* Domain::device_source(const void* src, size_t bytes, int on_device,
 
 extern "C" {
 
-int32_t lbm_abi_version(void) { return 3; }
+int32_t lbm_abi_version(void) { return 4; }
 
 lbm_status lbm_default_desc(lbm_domain_desc* d) {
   if (!d) return LBM_ERR_INVALID_ARG;
@@ -663,6 +663,7 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
   info->tile[0] = B.bx;
   info->tile[1] = B.by;
   info->ctas_per_sm = B.minb;
+  info->parent = (block_id == 0 || B.far) ? -1 : B.parent;
   return LBM_OK;
 }
 

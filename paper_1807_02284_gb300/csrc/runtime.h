@@ -105,6 +105,13 @@ struct lbm_domain {
 
   std::vector<cudaStream_t> post_streams;  // one per post-mapping target block
 
+  // a reference step run phase by phase (lbm_step_phase): each block's level at the step
+  // start, and per block 0 (nothing yet), 1 (sub-cycle done), 2 (post-mapping done)
+  bool phase_open = false;
+  bool phase_ref_done = false;
+  std::vector<int> phase_saved;
+  std::vector<char> phase_done;
+
   lbm_status aux(cudaStream_t* out);    // the auxiliary stream, created on first use
   cudaEvent_t event(int i);             // fork / join event i, created on first use
   cudaStream_t post_stream(int k);      // stream of post-mappings into block k

@@ -51,7 +51,7 @@ LBM_GRAD_LAGGED, LBM_GRAD_LOCAL = 0, 1
 class lbm_block_info(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("origin", C.c_double * 3), ("h", C.c_double),
                 ("nu", C.c_double), ("substeps", C.c_int32), ("steps", C.c_int64),
-                ("tile", C.c_int32 * 2), ("ctas_per_sm", C.c_int32)]
+                ("tile", C.c_int32 * 2), ("ctas_per_sm", C.c_int32), ("parent", C.c_int32)]
 
 
 INFLOW_RECORD = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"),
@@ -89,6 +89,11 @@ _SIGNATURES = {
     "lbm_plane_bytes": (C.c_size_t, [_P, _I]),
     "lbm_pack_plane": (_I, [_P, _I, _I, _P]),
     "lbm_unpack_plane": (_I, [_P, _I, _I, _P]),
+    "lbm_step_phase": (_I, [_P, _I, _I, _I]),
+    "lbm_mapping_boxes": (_I, [_P, _I, _I, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_box_bytes": (C.c_size_t, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "lbm_pack_box": (_I, [_P, _I, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _P]),
+    "lbm_unpack_box": (_I, [_P, _I, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32), _P, _I]),
     "lbm_reduce_batch": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
     "lbm_set_inflow_batch": (_I, [C.POINTER(_P), _I, C.POINTER(_P), C.POINTER(C.c_int32)]),
     "lbm_set_tape": (_I, [_P, _I]),
@@ -99,6 +104,9 @@ _SIGNATURES = {
     "lbm_last_error": (C.c_char_p, [_P]),
 }
 LBM_REDUCE_NOALLOC_MAX_NODES = 67108864
+LBM_PHASE_BEGIN, LBM_PHASE_REFERENCE, LBM_PHASE_BLOCK, LBM_PHASE_POST, LBM_PHASE_END = 0, 1, 2, 3, 4
+LBM_BOX_PRIOR_SOURCE, LBM_BOX_POST_TARGET = 0, 1
+LBM_LEVEL_CURRENT, LBM_LEVEL_START = 0, 1
 
 _lib = None
 
@@ -261,6 +269,13 @@ class Domain:
         self.check(self.lib.lbm_get_block_info(self.handle, block, C.byref(i)))
         return i
 
+    def n_blocks(self) -> int:
+        """Number of blocks of the domain (the reference block, refined and far-field ones)."""
+        i, n = lbm_block_info(), 0
+        while self.lib.lbm_get_block_info(self.handle, n, C.byref(i)) == LBM_OK:
+            n += 1
+        return n
+
     def n_nodes(self, block=0) -> int:
         i = self.info(block)
         return int(i.dims[0]) * int(i.dims[1]) * int(i.dims[2])
@@ -354,6 +369,49 @@ class Domain:
         """Copies the device tensor `buf` into z-plane `z` of the current state."""
         self.check(self.lib.lbm_unpack_plane(self.handle, int(z), int(direction),
                                              self._plane_buffer(buf, direction)))
+
+    def step_phase(self, phase, block=0, compute=True):
+        """One phase of a reference step (LBM_PHASE_*), computed or only advancing levels."""
+        self.check(self.lib.lbm_step_phase(self.handle, int(phase), int(block), int(bool(compute))))
+
+    def mapping_boxes(self, block, kind, other):
+        """Node boxes [(lo, hi), ...] of block `other` exchanged by refined block `block`'s
+        mappings (LBM_BOX_PRIOR_SOURCE: its source, six faces; LBM_BOX_POST_TARGET: what its
+        post-mapping writes into `other`)."""
+        buf = (C.c_int32 * 36)()
+        n = C.c_int32(0)
+        self.check(self.lib.lbm_mapping_boxes(self.handle, int(block), int(kind), int(other),
+                                              buf, C.byref(n)))
+        return [(tuple(buf[6 * i:6 * i + 3]), tuple(buf[6 * i + 3:6 * i + 6]))
+                for i in range(n.value)]
+
+    @staticmethod
+    def _box(lo, hi):
+        return (C.c_int32 * 3)(*[int(v) for v in lo]), (C.c_int32 * 3)(*[int(v) for v in hi])
+
+    def box_bytes(self, block, lo, hi) -> int:
+        l, h = self._box(lo, hi)
+        return int(self.lib.lbm_box_bytes(self.handle, int(block), l, h))
+
+    def _box_buffer(self, buf, block, lo, hi):
+        p, dev = _ptr(buf)
+        if not dev:
+            raise ValueError("box buffers are device memory")
+        if _nbytes(buf) < self.box_bytes(block, lo, hi) or (p or 0) % 16:
+            raise ValueError("a box buffer holds box_bytes() bytes, 16-byte aligned")
+        return p
+
+    def pack_box(self, block, level, lo, hi, buf):
+        """Copies a node box of block `block` (level LBM_LEVEL_*) into the device tensor buf."""
+        l, h = self._box(lo, hi)
+        self.check(self.lib.lbm_pack_box(self.handle, int(block), int(level), l, h,
+                                         self._box_buffer(buf, block, lo, hi)))
+
+    def unpack_box(self, block, level, lo, hi, buf, skip_flags=0):
+        """Copies the device tensor buf into a node box, leaving nodes with skip_flags bits."""
+        l, h = self._box(lo, hi)
+        self.check(self.lib.lbm_unpack_box(self.handle, int(block), int(level), l, h,
+                                           self._box_buffer(buf, block, lo, hi), int(skip_flags)))
 
     def step_reduce(self, n=1) -> np.ndarray:
         """``lbm_step_reduce``: n steps, then block 0's diagnostics (mass, momentum x/y/z,

@@ -321,3 +321,203 @@ def step_local(slabs: Sequence[SlabDomain], n: int = 1):
         for s in slabs:
             s.dom.step(1)
         wait_all()
+
+
+# ------------------------------------------------ blocks of one continuous-scale domain
+
+# One reference step of Algorithm 1 reads, for every refined block, its prior-mapping source
+# around the block's scale boundary at t_n and at t_n + dt_0, and writes its post-mapping
+# into every coarser block.  With the blocks of one domain placed on several ranks, every
+# rank holds the whole domain and steps it phase by phase (lbm_step_phase), computing the
+# phases of the blocks it owns; the node boxes those mappings touch move between phases:
+#   ("prior", b) before block b's sub-cycle: the source block's boxes at t_n (LEVEL_START,
+#                with the source's own scale boundary at t_n refreshed by its sub-cycle) and
+#                at t_n + dt_0 (LEVEL_CURRENT, after every earlier block's post-mapping into
+#                it), to b's owner;
+#   ("post", b)  after block b's post-mapping, computed by b's owner into its copy of every
+#                coarser block: the written box to that block's owner (obstacle and
+#                scale-boundary nodes of the box are left alone there: no mapping writes
+#                them).
+SOLID_BIT, GHOST_BIT = 1, 8
+
+
+@dataclass(frozen=True)
+class BoxMove:
+    """One node box moved between ranks at one stage of a reference step."""
+    stage: tuple
+    block: int
+    level: int
+    lo: tuple
+    hi: tuple
+    src: int
+    dst: int
+    skip: int
+
+
+def place_blocks(updates: Sequence[int], world: int) -> List[int]:
+    """Owner rank of every block: largest-first packing of the lattice updates per reference
+    step (nodes x sub-steps), as for independent simulations."""
+    owner = [0] * len(updates)
+    for r, idx in enumerate(shard_by_cells(updates, world)):
+        for i in idx:
+            owner[i] = r
+    return owner
+
+
+def block_moves(parents: Sequence[int], owner: Sequence[int], boxes) -> List[BoxMove]:
+    """The box moves of one reference step, in stage order.  parents[b] is block b's
+    prior-mapping source (-1: not a refined block); boxes(b, kind, other) lists the (lo, hi)
+    boxes of lbm_mapping_boxes."""
+    from . import lbm
+    refined = [b for b in range(len(parents)) if parents[b] >= 0]
+    moves: List[BoxMove] = []
+    for b in refined:
+        p = parents[b]
+        if owner[p] != owner[b]:
+            for level in (lbm.LBM_LEVEL_START, lbm.LBM_LEVEL_CURRENT):
+                for lo, hi in boxes(b, lbm.LBM_BOX_PRIOR_SOURCE, p):
+                    moves.append(BoxMove(("prior", b), p, level, tuple(lo), tuple(hi),
+                                         owner[p], owner[b], 0))
+        for k in range(len(parents)):
+            if k == b or owner[k] == owner[b]:
+                continue
+            for lo, hi in boxes(b, lbm.LBM_BOX_POST_TARGET, k):
+                moves.append(BoxMove(("post", b), k, lbm.LBM_LEVEL_CURRENT, tuple(lo), tuple(hi),
+                                     owner[b], owner[k], SOLID_BIT | GHOST_BIT))
+    return moves
+
+
+class PlacedDomain:
+    """One rank's view of a continuous-scale domain whose blocks are placed on ranks.
+
+    ``dom`` holds the whole domain (every block built, flagged and initialised the same way
+    on every rank); ``owner[b]`` is the rank that computes block b.  ``step`` advances one
+    reference step through ``torch.distributed`` point-to-point messages (any backend;
+    device buffers are staged through host memory for backends other than NCCL);
+    ``step_local`` advances the ranks held by one process."""
+
+    def __init__(self, dom, owner: Sequence[int], rank: int):
+        import torch
+        from . import lbm
+        self.dom = dom
+        self.rank = int(rank)
+        nb = dom.n_blocks()
+        self.owner = [int(o) for o in owner]
+        if len(self.owner) != nb:
+            raise ValueError("one owner per block")
+        self.parents = [dom.info(b).parent for b in range(nb)]
+        self.refined = [b for b in range(nb) if self.parents[b] >= 0]
+        self.moves = block_moves(self.parents, self.owner,
+                                 lambda b, kind, other: dom.mapping_boxes(b, kind, other))
+        dev = getattr(dom, "box_device", "cuda")
+        self.bufs = {}
+        for i, m in enumerate(self.moves):
+            if self.rank in (m.src, m.dst):
+                nbytes = dom.box_bytes(m.block, m.lo, m.hi)
+                self.bufs[i] = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.lbm = lbm
+
+    def stage_moves(self, stage):
+        return [(i, m) for i, m in enumerate(self.moves) if m.stage == stage]
+
+    def pack(self, stage):
+        for i, m in self.stage_moves(stage):
+            if m.src == self.rank:
+                self.dom.pack_box(m.block, m.level, m.lo, m.hi, self.bufs[i])
+
+    def unpack(self, stage, source=None):
+        for i, m in self.stage_moves(stage):
+            if m.dst == self.rank:
+                buf = self.bufs[i] if source is None else source(i, m)
+                self.dom.unpack_box(m.block, m.level, m.lo, m.hi, buf, m.skip)
+
+    def exchange(self, stage, group=None):
+        """The moves of one stage through torch.distributed (tag = move index)."""
+        mine = [(i, m) for i, m in self.stage_moves(stage) if self.rank in (m.src, m.dst)]
+        if not mine:
+            return
+        import torch
+        import torch.distributed as dist
+        self.pack(stage)
+        self.dom.sync()
+        nccl = dist.get_backend(group) == "nccl"
+        staged, ops = {}, []
+        for i, m in mine:
+            t = self.bufs[i]
+            if t.is_cuda and not nccl:
+                t = staged.setdefault(i, t.cpu())
+            peer = m.dst if m.src == self.rank else m.src
+            g_peer = peer if group is None else dist.get_global_rank(group, peer)
+            fn = dist.isend if m.src == self.rank else dist.irecv
+            ops.append(dist.P2POp(fn, t, g_peer, group, i))
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+        for i, t in staged.items():
+            if self.moves[i].dst == self.rank:
+                self.bufs[i].copy_(t)
+        if any(t.is_cuda for t in self.bufs.values()):
+            torch.cuda.synchronize()
+        self.unpack(stage)
+
+    def schedule(self):
+        """One reference step as a list of ("phase", phase, block) and ("stage", stage)
+        items, in order."""
+        lbm = self.lbm
+        items = [("phase", lbm.LBM_PHASE_BEGIN, 0), ("phase", lbm.LBM_PHASE_REFERENCE, 0)]
+        for b in self.refined:
+            items += [("stage", ("prior", b)), ("phase", lbm.LBM_PHASE_BLOCK, b),
+                      ("phase", lbm.LBM_PHASE_POST, b), ("stage", ("post", b))]
+        items.append(("phase", lbm.LBM_PHASE_END, 0))
+        return items
+
+    def run_phase(self, phase, block):
+        """One phase, computed if this rank owns the block it advances."""
+        lbm = self.lbm
+        compute = phase in (lbm.LBM_PHASE_REFERENCE, lbm.LBM_PHASE_BLOCK, lbm.LBM_PHASE_POST) \
+            and self.owner[block] == self.rank
+        self.dom.step_phase(phase, block, compute)
+
+    def step(self, n=1, group=None):
+        """n reference steps, exchanging through torch.distributed."""
+        for _ in range(int(n)):
+            for item in self.schedule():
+                if item[0] == "phase":
+                    self.run_phase(item[1], item[2])
+                else:
+                    self.exchange(item[1], group)
+
+    def sync(self):
+        self.dom.sync()
+
+
+def step_placed_local(ranks: Sequence[PlacedDomain], n: int = 1):
+    """n reference steps of a domain whose ranks (list index = rank) are all held by this
+    process, in lockstep: every rank runs each phase, and at every stage each sender packs
+    its boxes and each receiver unpacks them from the sender's buffer.  With every rank's
+    domain on one stream nothing waits on the host; otherwise each stage waits for every
+    rank's stream."""
+    if [r.rank for r in ranks] != list(range(len(ranks))):
+        raise ValueError("ranks must be 0 .. n-1 of one placement")
+    s0 = getattr(ranks[0].dom, "torch_stream", None)
+    shared = s0 is not None and all(getattr(r.dom, "torch_stream", None) == s0 for r in ranks)
+
+    def wait_all():
+        if not shared:
+            for r in ranks:
+                r.dom.sync()
+
+    def source(i, m):
+        return ranks[m.src].bufs[i]
+
+    for _ in range(int(n)):
+        for item in ranks[0].schedule():
+            if item[0] == "phase":
+                for r in ranks:
+                    r.run_phase(item[1], item[2])
+            else:
+                wait_all()
+                for r in ranks:
+                    r.pack(item[1])
+                wait_all()
+                for r in ranks:
+                    r.unpack(item[1], source)

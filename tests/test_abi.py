@@ -49,7 +49,7 @@ def test_library_exports_every_declared_symbol(built):
 def test_library_loads_and_validates_on_host(built):
     from paper_1807_02284_gb300 import lbm
     lib = lbm.load()
-    assert lib.lbm_abi_version() == 3
+    assert lib.lbm_abi_version() == 4
     d = lbm.lbm_domain_desc()
     assert lib.lbm_default_desc(C.byref(d)) == lbm.LBM_OK
     assert (d.a, d.b, d.g_max) == (-4.0, 5.0, 0.1)
@@ -79,6 +79,11 @@ def test_library_loads_and_validates_on_host(built):
     assert lib.lbm_plane_bytes(None, 0) == 0
     for fn in (lib.lbm_pack_plane, lib.lbm_unpack_plane):
         assert fn(None, 0, 0, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_step_phase(None, 0, 0, 1) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_mapping_boxes(None, 1, 0, 0, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_box_bytes(None, 0, None, None) == 0
+    assert lib.lbm_pack_box(None, 0, 0, None, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_unpack_box(None, 0, 0, None, None, None, 0) == lbm.LBM_ERR_INVALID_ARG
 
 
 def test_struct_layouts_match_header():
