@@ -240,7 +240,7 @@ def repeat_record(times, K, units_per_step):
 def _workload(name):
     import synth
     storage = "fp16" if name.endswith("fp16") else "fp32"
-    if name == "multiscale3":
+    if name.startswith("multiscale3"):     # also multiscale3_regwall
         return synth.multiscale(scale=1.0), "fp32"
     if name == "farfield256":       # the plume inside a far-field block of spacing 2
         sc = synth.plume(256)
@@ -465,15 +465,17 @@ def parity_by_variant():
         uo = st.u.numpy()
         return float(np.abs(u - uo).max() / np.abs(uo).max())
 
-    def multi(sc, steps, far=()):
+    def multi(sc, steps, far=(), obstacle_walls=False):
         dom = lbm.Domain(sc.blocks[0].dims, sc.nu, periodic=sc.periodic, adaptive=sc.adaptive,
                          c_src=sc.c_src)
+        if obstacle_walls:
+            dom.set_walls((False,) * 6, obstacles=True)
         for b in sc.blocks[1:]:
             dom.add_scale_block(b.origin, b.h, b.dims)
         for i, b in enumerate(sc.blocks):
             dom.set_flags(b.flags, block=i)
             dom.init_macro(r32(b.u0), rho=r32(b.rho0), c=r32(b.c0), block=i)
-        ms = coupling.MultiScale.build(sc)
+        ms = coupling.MultiScale.build(sc, obstacle_walls=obstacle_walls)
         for fb in far:                  # far-field blocks (h > 1) around the scene
             fid = dom.add_scale_block(fb.origin, fb.h, fb.dims)
             dom.set_flags(fb.flags, block=fid)
@@ -508,6 +510,9 @@ def parity_by_variant():
     ms = synth.multiscale(scale=0.25, nu=2e-3, flow_amp=0.06)
     out["multiscale3"] = {"u_max_abs_err_rel": multi(ms, 2), "bound": 1e-5,
                           "case": "the 3-block scene scaled by 1/4 (32^3, 24^3, 16^3), 2 reference steps"}
+    out["multiscale3_regwall"] = {"u_max_abs_err_rel": multi(ms, 2, obstacle_walls=True),
+                                  "bound": 1e-5,
+                                  "case": "the same scene, sphere surfaces as walls in every block"}
     far = synth.random_scene(dims=(20, 18, 16), seed=41, periodic=(False, False, False),
                              spheres=[(11.0, 9.0, 8.0, 2.5)], inflow=(9, 8, 3.0, 0.08), nu=0.004)
     fb = synth.far_block(far.blocks[0], 1.5, 6.0, seed=5, amp=0.03)
@@ -1197,6 +1202,7 @@ def _variants(args):
                                   ("plume256_local", run_ours, 100, 10),
                                   ("plume256_walls", run_ours, 100, 10),
                                   ("multiscale3", run_ours, 48, 48),
+                                  ("multiscale3_regwall", run_ours, 48, 48),
                                   ("dynamic256", run_dynamic, 200, 10),
                                   ("farfield256", run_ours, 96, 96),
                                   ("batch64", run_batch, 100, 10),
@@ -1230,7 +1236,8 @@ def main():
                              "plume192", "plume192_fp16",
                              "multiscale3", "batch64", "adjoint128", "adjoint64",
                              "plume256_local", "dynamic256", "farfield256", "plume256_walls",
-                             "ringing196", "plume256_regwall", "plume256_slab2"])
+                             "ringing196", "plume256_regwall", "plume256_slab2",
+                             "multiscale3_regwall"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP16 / multi-scale / batch / adjoint summaries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -75,10 +75,15 @@ enum {
                         non-obstacle neighbour is a wall node at rest (flag bit 6 instead of
                         bit 0 in LBM_FIELD_FLAGS), populations pulled from the inner obstacle
                         voxels are the unknown ones, the inner voxels stay inert; without it
-                        obstacles use halfway bounce-back.  Replaces the previous walls.
+                        obstacles use halfway bounce-back.  Byte 6 applies to every refined
+                        block too (their faces are scale boundaries, never walls); the
+                        continuous-scale mappings treat every obstacle voxel, surface or
+                        inner, as an obstacle (a dropped interpolation corner, a destination
+                        left alone).  Replaces the previous walls.
                         INVALID_ARG for a wall on a periodic axis; UNSUPPORTED with
-                        far-field blocks, and byte 6 with any refined block (adding a block
-                        to such a domain is UNSUPPORTED too). */
+                        far-field blocks.  With byte 6 set, blocks started from their parent
+                        (lbm_init_block_from_parent, dynamic and static scale construction)
+                        and the adjoint of a domain with refined blocks are UNSUPPORTED. */
 };
 
 typedef struct {

@@ -41,7 +41,9 @@ Readings (the paper is silent or ambiguous):
     Lagrange interpolant through its states at t_n, t_n + (l-1) h and t_n + l h; the
     stored velocity is recomputed from the interpolated populations and the scalar is
     interpolated alike; the ghost layer is the mapping of the source at t_n + dt_0.  The
-    block's clock is then aligned with s0.
+    block's clock is then aligned with s0.  Every node the sub-steps update is aligned,
+    the obstacles' surface voxels too when they are walls (they are updated wall nodes);
+    inert obstacle voxels and ghost nodes keep their last state.
   * Ghost and post-mapped nodes carry the velocity of their mapped populations (the
     mapping keeps rho and u) and the trilinearly interpolated scalar.
 """
@@ -169,9 +171,12 @@ class MultiScale:
         self.step_count = 0
 
     @staticmethod
-    def build(scene, f32_inputs=True) -> "MultiScale":
+    def build(scene, f32_inputs=True, obstacle_walls=False) -> "MultiScale":
         """Blocks of a ``synth.Scene``: block 0 is s0; refined blocks get ghost flags,
-        nu_b = nu_0 / h_b, substep counts and their prior-mapping parent."""
+        nu_b = nu_0 / h_b, substep counts and their prior-mapping parent.  With
+        ``obstacle_walls`` every block takes its obstacles' surface voxels as the
+        second-order wall (``grid.Params.obstacle_walls``); the mappings keep treating every
+        obstacle voxel as an obstacle (dropped corner, destination left alone)."""
         blocks = []
         for i, sb in enumerate(scene.blocks):
             conv = (lambda a: np.asarray(a, np.float32).astype(np.float64)) if f32_inputs \
@@ -188,7 +193,8 @@ class MultiScale:
             h = float(sb.h)
             nu_b = scene.nu / h
             per = tuple(scene.periodic) if i == 0 else (False, False, False)
-            p = grid.Params(nu=nu_b, periodic=per, adaptive=scene.adaptive, c_src=scene.c_src)
+            p = grid.Params(nu=nu_b, periodic=per, adaptive=scene.adaptive, c_src=scene.c_src,
+                            obstacle_walls=obstacle_walls)
             ratio = 1.0 / h
             l = max(1, math.ceil(ratio - 1e-9))
             blocks.append(Blk(origin=np.array(sb.origin, dtype=np.float64), h=h,
@@ -354,6 +360,8 @@ class MultiScale:
         u = torch.einsum("qzyx,qa->azyx", f, cmr.C) / rho
         ghost = (b.state.flags & GHOST) != 0
         solid = (b.state.flags & SOLID) != 0
+        if b.params.obstacle_walls:     # surface voxels are updated wall nodes: aligned too
+            solid = solid & ~grid.surface_voxels(b.state.flags, b.params.periodic)
         keep = ghost | solid
         out = s_last.clone()
         out.f = torch.where(keep[None], s_last.f, f)

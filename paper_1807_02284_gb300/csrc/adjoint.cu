@@ -916,6 +916,8 @@ static lbm_status adjoint_supported(lbm_domain* dom) {
   const Block& B = dom->blocks[0];
   if (B.nx < 3 || B.ny < 3 || B.nz < 3) return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint needs >= 3 nodes per axis");
   if (27ull * B.N >= 0xFFFFFFFFull) return dom->fail(LBM_ERR_UNSUPPORTED, "block too large for the adjoint");
+  if (dom->blocks.size() > 1 && (dom->walls & WALLS_OBSTACLES))
+    return dom->fail(LBM_ERR_UNSUPPORTED, "the adjoint of obstacle-surface walls covers single-block domains");
   return LBM_OK;
 }
 

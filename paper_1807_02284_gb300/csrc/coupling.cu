@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
           sc[c] = m.src + (c & 1) + ((c >> 1) & 1) * sy + (c >> 2) * sz;
           const float wc = ((c & 1) ? m.tx : 1.0f - m.tx) * (((c >> 1) & 1) ? m.ty : 1.0f - m.ty) *
                            ((c >> 2) ? m.tz : 1.0f - m.tz);
-          w[c] = (__ldg(a.src_flags + sc[c]) & F_SOLID) ? 0.0f : wc;  // obstacle corners dropped
+          // obstacle corners are dropped (inner voxels, and surface voxels taken as walls)
+          w[c] = (__ldg(a.src_flags + sc[c]) & (F_SOLID | F_OBST_WALL)) ? 0.0f : wc;
           wsum += w[c];
         }
         if (wsum > 0.0f) inv = 1.0f / wsum;
@@ -469,8 +470,6 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
   if (!origin || !dims || !block_id) return dom->fail(LBM_ERR_INVALID_ARG, "null argument");
   if (!(h > 0.0) || !std::isfinite(h)) return dom->fail(LBM_ERR_INVALID_ARG, "h must be positive");
   if (std::fabs(h - 1.0) < 1e-12) return dom->fail(LBM_ERR_INVALID_ARG, "h = 1 is the reference scale");
-  if (dom->walls & WALLS_OBSTACLES)
-    return dom->fail(LBM_ERR_UNSUPPORTED, "obstacle walls need a single-block domain");
   if (dom->desc.storage != LBM_FP32)
     return dom->fail(LBM_ERR_UNSUPPORTED, "scale blocks need FP32 storage");
   if (dom->tape)
@@ -624,7 +623,7 @@ static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& sav
   a.u_dst = B.lv[dst_level].u;
   a.c_dst = B.lv[dst_level].c;
   a.dst_flags = B.flags;
-  a.skip_mask = F_SOLID;
+  a.skip_mask = F_SOLID | F_OBST_WALL;   // obstacle voxels keep their own state
   a.dN = B.N;
   a.khat = B.prior.khat;
   return launch_map(a, dom->desc.storage, stream);
@@ -646,7 +645,7 @@ static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t, cudaStrea
   a.u_dst = T.lv[T.cur].u;
   a.c_dst = T.lv[T.cur].c;
   a.dst_flags = T.flags;
-  a.skip_mask = F_SOLID | F_GHOST;
+  a.skip_mask = F_SOLID | F_OBST_WALL | F_GHOST;
   a.dN = T.N;
   a.khat = t.khat;
   return launch_map(a, dom->desc.storage, stream);

@@ -195,6 +195,8 @@ extern "C" lbm_status lbm_init_block_from_parent(lbm_domain* dom, int32_t block_
   if (st != LBM_OK) return st;
   if (block_id == 0) return dom->fail(LBM_ERR_INVALID_ARG, "the reference block has no parent");
   if (dom->blocks[block_id].far) return dom->fail(LBM_ERR_INVALID_ARG, "far-field blocks are started with lbm_init_macro");
+  if (dom->walls & WALLS_OBSTACLES)
+    return dom->fail(LBM_ERR_UNSUPPORTED, "blocks started from their parent do not take obstacle-surface walls");
   Block& B = dom->blocks[block_id];
   const Block& P = dom->blocks[B.prior.src];
   cudaError_t e;
@@ -242,6 +244,8 @@ extern "C" lbm_status lbm_build_dynamic_scale(lbm_domain* dom, int32_t src_block
   if (!dom) return LBM_ERR_INVALID_ARG;
   cudaSetDevice(dom->desc.device);
   if (!block_id) return dom->fail(LBM_ERR_INVALID_ARG, "null block_id");
+  if (dom->walls & WALLS_OBSTACLES)
+    return dom->fail(LBM_ERR_UNSUPPORTED, "dynamic scales do not take obstacle-surface walls");
   *block_id = -1;
   lbm_status st = dom->check_block(src_block);
   if (st != LBM_OK) return st;
@@ -299,6 +303,8 @@ extern "C" lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales,
   cudaSetDevice(dom->desc.device);
   if (!n_added) return dom->fail(LBM_ERR_INVALID_ARG, "null n_added");
   *n_added = 0;
+  if (dom->walls & WALLS_OBSTACLES)
+    return dom->fail(LBM_ERR_UNSUPPORTED, "static scales do not take obstacle-surface walls");
   if (n_scales < 2 || !(h_min > 0.0 && h_min < 1.0) || !(d_max >= 0.0) || !(wake >= 0.0) ||
       flow_axis < 0 || flow_axis > 2)
     return dom->fail(LBM_ERR_INVALID_ARG, "need n_scales >= 2, 0 < h_min < 1, d_max, wake >= 0, axis 0..2");

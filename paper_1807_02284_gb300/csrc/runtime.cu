@@ -96,7 +96,9 @@ BlockView Domain::view(int b, int from, int to) const {
   v.rp = B.rp;
   v.c_src = (float)desc.c_src;
   v.err = d_err;
-  v.walls = b == 0 ? walls : 0;
+  // wall faces are faces of the reference block; obstacle surfaces are walls in every block
+  // that is not a far-field block
+  v.walls = b == 0 ? walls : (B.far ? 0 : (walls & WALLS_OBSTACLES));
   return v;
 }
 
@@ -306,7 +308,7 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
     if (e == cudaSuccess) {
       int per[3] = {0, 0, 0};
       if (block_id == 0) for (int a = 0; a < 3; ++a) per[a] = dom->desc.periodic[a];
-      if (block_id == 0 && (dom->walls & WALLS_OBSTACLES))   // the new obstacles' surfaces
+      if ((dom->walls & WALLS_OBSTACLES) && !B.far)   // the new obstacles' surfaces
         e = launch_obstacle_walls(B.flags, B.nx, B.ny, B.nz, per, 1, dom->stream);
       if (e == cudaSuccess) e = launch_near_solid(B.flags, B.nx, B.ny, B.nz, per, dom->stream);
     }
@@ -330,11 +332,7 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
         if (dom->desc.periodic[f / 2]) return dom->fail(LBM_ERR_INVALID_ARG, "a wall on a periodic axis");
         walls |= 1 << f;
       }
-    if (nbytes >= 7 && m[6]) {
-      if (dom->blocks.size() > 1)
-        return dom->fail(LBM_ERR_UNSUPPORTED, "obstacle walls need a single-block domain");
-      walls |= WALLS_OBSTACLES;
-    }
+    if (nbytes >= 7 && m[6]) walls |= WALLS_OBSTACLES;
     for (size_t i = 1; i < dom->blocks.size(); ++i)
       if (dom->blocks[i].far && walls)
         return dom->fail(LBM_ERR_UNSUPPORTED, "walls and far-field blocks exclude each other");
@@ -345,6 +343,15 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
       e = launch_obstacle_walls(B.flags, B.nx, B.ny, B.nz, per, (walls & WALLS_OBSTACLES) ? 1 : 0,
                                 dom->stream);
       if (e == cudaSuccess) e = launch_near_solid(B.flags, B.nx, B.ny, B.nz, per, dom->stream);
+    }
+    // obstacle surfaces of the refined blocks (their faces are scale boundaries, not walls)
+    const int zero[3] = {0, 0, 0};
+    for (size_t i = 1; i < dom->blocks.size() && e == cudaSuccess; ++i) {
+      Block& R = dom->blocks[i];
+      if (!((walls | dom->walls) & WALLS_OBSTACLES)) break;
+      e = launch_obstacle_walls(R.flags, R.nx, R.ny, R.nz, zero, (walls & WALLS_OBSTACLES) ? 1 : 0,
+                                dom->stream);
+      if (e == cudaSuccess) e = launch_near_solid(R.flags, R.nx, R.ny, R.nz, zero, dom->stream);
     }
     if (e != cudaSuccess) return dom->cuda_fail(e, "wall flags");
     dom->walls = walls;

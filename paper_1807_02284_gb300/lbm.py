@@ -288,8 +288,7 @@ class Domain:
 
     def set_walls(self, faces, obstacles=False):
         """No-slip wall faces of block 0: six booleans (x-, x+, y-, y+, z-, z+); with
-        ``obstacles`` the surface voxels of the obstacles are walls too (single-block
-        domains)."""
+        ``obstacles`` the surface voxels of the obstacles are walls too, in every block."""
         m = np.ascontiguousarray([1 if f else 0 for f in faces] + [1 if obstacles else 0],
                                  dtype=np.uint8)
         self.check(self.lib.lbm_set_boundary(self.handle, 0, LBM_BC_WALLS, m.ctypes.data, 7, 0))

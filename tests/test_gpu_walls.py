@@ -116,16 +116,17 @@ def test_obstacle_wall_argument_checks(lib):
     from paper_1807_02284_gb300 import lbm
     dom = lbm.Domain((16, 16, 16), 0.01, periodic=(False, False, False))
     dom.set_walls((False,) * 6, obstacles=True)
-    with pytest.raises(lbm.LBMError) as ei:
-        dom.add_scale_block((4.0, 4.0, 4.0), 0.5, (8, 8, 8))
-    assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
     dom.set_tape(2)                                  # the adjoint covers obstacle walls
     dom.set_tape(0)
-    dom.set_walls((False,) * 6)
-    dom.add_scale_block((4.0, 4.0, 4.0), 0.5, (8, 8, 8))
-    with pytest.raises(lbm.LBMError) as ei:
-        dom.set_walls((False,) * 6, obstacles=True)
+    dom.add_scale_block((4.0, 4.0, 4.0), 0.5, (8, 8, 8))   # refined blocks take them too
+    with pytest.raises(lbm.LBMError) as ei:          # but not their adjoint
+        dom.set_tape(2)
     assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
+    with pytest.raises(lbm.LBMError) as ei:          # nor blocks started from their parent
+        dom.init_block_from_parent(1)
+    assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
+    dom.set_walls((False,) * 6)
+    dom.set_walls((False,) * 6, obstacles=True)
     dom.step(2)
     dom.sync()
     dom.close()
