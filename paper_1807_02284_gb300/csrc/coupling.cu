@@ -164,23 +164,48 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
     su[0][t] = su[1][t] = su[2][t] = 0.0f;
   }
   if (t < MAP_D && sinv[t] > 0.0f) {
+    // K_hat differs from 1 only on moments 4..8 (the shear and deviatoric second moments),
+    // so the mapping adds to the interpolated populations the inverse transform of
+    // (K_hat - 1) times their non-equilibrium deviatoric second central moments: the same
+    // linear map as relaxing every central moment with keep factor K_hat on moments 4..8
+    // and 1 elsewhere, without transforming the 21 moments it leaves unchanged.
     float acc[27];
 #pragma unroll
     for (int k = 0; k < 27; ++k) acc[k] = sv[t * MAP_LD + k];
     raw_moments(acc);
     const float drho = acc[kap(0, 0, 0)];
     const float inv = 1.0f / (1.0f + drho);
-    const float ux = acc[kap(1, 0, 0)] * inv, uy = acc[kap(0, 1, 0)] * inv,
-                uz = acc[kap(0, 0, 1)] * inv;
-    Keep kf;
-    kf.nu = a.khat;
-    kf.g[0] = kf.g[1] = kf.g[2] = kf.g[3] = 1.0f;
-    collide_from_raw(acc, drho, ux, uy, uz, kf);
+    const float X = acc[kap(1, 0, 0)] * inv, Y = acc[kap(0, 1, 0)] * inv,
+                Z = acc[kap(0, 0, 1)] * inv;
+    // second central moments of the shifted populations about u, from the raw ones
+    const float R0 = drho, Rx = acc[kap(1, 0, 0)], Ry = acc[kap(0, 1, 0)], Rz = acc[kap(0, 0, 1)];
+    const float kxx = acc[kap(2, 0, 0)] + X * fmaf(X, R0, -2.0f * Rx);
+    const float kyy = acc[kap(0, 2, 0)] + Y * fmaf(Y, R0, -2.0f * Ry);
+    const float kzz = acc[kap(0, 0, 2)] + Z * fmaf(Z, R0, -2.0f * Rz);
+    const float kxy = acc[kap(1, 1, 0)] - X * Ry - Y * Rx + X * Y * R0;
+    const float kxz = acc[kap(1, 0, 1)] - X * Rz - Z * Rx + X * Z * R0;
+    const float kyz = acc[kap(0, 1, 1)] - Y * Rz - Z * Ry + Y * Z * R0;
+    // non-equilibrium parts (equilibrium offsets as in relax_to_equilibrium) scaled by K - 1
+    const float km1 = a.khat - 1.0f;
+    const float dr3 = drho * (1.0f / 3.0f);
+    const float A = kxx - (dr3 - X * X), B = kyy - (dr3 - Y * Y), Cc = kzz - (dr3 - Z * Z);
+    float dk[27];
 #pragma unroll
-    for (int k = 0; k < 27; ++k) sv[t * MAP_LD + k] = acc[k];
-    su[0][t] = ux;
-    su[1][t] = uy;
-    su[2][t] = uz;
+    for (int k = 0; k < 27; ++k) dk[k] = 0.0f;
+    dk[kap(1, 1, 0)] = km1 * (kxy + X * Y);
+    dk[kap(1, 0, 1)] = km1 * (kxz + X * Z);
+    dk[kap(0, 1, 1)] = km1 * (kyz + Y * Z);
+    dk[kap(2, 0, 0)] = km1 * (1.0f / 3.0f) * (2.0f * A - B - Cc);
+    dk[kap(0, 2, 0)] = km1 * (1.0f / 3.0f) * (2.0f * B - A - Cc);
+    dk[kap(0, 0, 2)] = km1 * (1.0f / 3.0f) * (2.0f * Cc - A - B);
+    inv_axis<9>(dk, Z);
+    inv_axis<3>(dk, Y);
+    inv_axis<1>(dk, X);
+#pragma unroll
+    for (int k = 0; k < 27; ++k) sv[t * MAP_LD + k] += dk[k];
+    su[0][t] = X;
+    su[1][t] = Y;
+    su[2][t] = Z;
   }
   __syncthreads();
   T* out = static_cast<T*>(a.f_dst);
