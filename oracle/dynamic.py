@@ -187,3 +187,98 @@ def static_scales(flags, n_scales: int, h_min: float, d_max: float, wake: float,
             dims.append(n)
         out.append((tuple(origin), h, tuple(dims)))
     return out
+
+
+# ------------------------------------------------------------- soft-shadow wake (Sec. 5)
+
+def light_samples(flags, flow_axis: int, n_light: int):
+    """Points of the inlet taken as the area light source: the inflow nodes (in index order,
+    every ceil(count / n_light)-th one), or, without inflow nodes, the nodes of the upstream
+    face (index 0 along flow_axis) the same way.  Returns an (M, 3) int array of (x, y, z)."""
+    f = np.asarray(flags)
+    z, y, x = np.nonzero((f & INFLOW) != 0)
+    if z.size == 0:
+        Z, Y, X = f.shape
+        face = np.zeros_like(f, dtype=bool)
+        sl = [slice(None)] * 3
+        sl[2 - flow_axis] = 0
+        face[tuple(sl)] = True
+        z, y, x = np.nonzero(face)
+    stride = -(-z.size // n_light)
+    return np.stack([x, y, z], 1)[::stride]
+
+
+def visibility(flags, nodes, lights):
+    """Number of light samples each node (K, 3 ints x, y, z) sees: the straight segment from
+    the node to the sample crosses no obstacle voxel.  The segment is walked in 2 m steps, m
+    the largest coordinate difference; step k sits at p + d k / (2 m) and is checked at its
+    nearest voxel, floor(q + 1/2), all in integer arithmetic (the two end points are not
+    checked)."""
+    f = np.asarray(flags)
+    solid = (f & SOLID) != 0
+    nodes = np.asarray(nodes, np.int64)
+    count = np.zeros(len(nodes), np.int64)
+    for L in np.asarray(lights, np.int64):
+        d = L[None, :] - nodes
+        m = np.abs(d).max(1)
+        n = 2 * m
+        blocked = np.zeros(len(nodes), bool)
+        for k in range(1, int(n.max(initial=0))):
+            act = np.nonzero(k < n)[0]
+            if act.size == 0:
+                break
+            na = n[act][:, None]
+            v = (2 * (nodes[act] * na + d[act] * k) + na) // (2 * na)
+            blocked[act] |= solid[v[:, 2], v[:, 1], v[:, 0]]
+        count += ~blocked
+    return count
+
+
+def shadow_scales(flags, n_scales: int, h_min: float, d_max: float, wake: float,
+                  flow_axis: int = 0, n_light: int = 16):
+    """Static scale construction with the wake shaped like a soft shadow (Sec. 5): the inlet
+    is an area light source (light_samples); a node downstream of the obstacles (from the
+    obstacles' upstream end to `wake` past their downstream end along flow_axis, obstacle
+    voxels excluded) that sees c of the M samples belongs to the wake of scale i (i = 1 .. n-1,
+    coarse to fine) when c (n - 1) <= (n - 1 - i) M: the finest scale takes the umbra (c = 0),
+    coarser ones more and more of the penumbra.  Scale i covers the obstacles' box widened by
+    d_i (as in static_scales) together with the bounding box of its wake nodes, clipped and
+    snapped like static_scales.  Returns [(origin, h, dims)] for scales 1 .. n-1."""
+    box = obstacle_box(flags)
+    if box is None or n_scales < 2:
+        return []
+    f = np.asarray(flags)
+    Z, Y, X = f.shape
+    ref = (X, Y, Z)
+    lights = light_samples(f, flow_axis, n_light)
+    M = len(lights)
+    lo_a = int(box[flow_axis])
+    hi_a = int(min(math.floor(box[3 + flow_axis] + wake), ref[flow_axis] - 1))
+    zz, yy, xx = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    coord = (xx, yy, zz)
+    cand = (coord[flow_axis] >= lo_a) & (coord[flow_axis] <= hi_a) & ((f & SOLID) == 0)
+    zi, yi, xi = np.nonzero(cand)
+    nodes = np.stack([xi, yi, zi], 1)
+    c = visibility(f, nodes, lights)
+    out = []
+    for i in range(1, n_scales):
+        h = 1.0 + (h_min - 1.0) * i / (n_scales - 1)
+        d = d_max * (n_scales - 1 - i) / (n_scales - 1)
+        lo = [box[a] - d for a in range(3)]
+        hi = [box[3 + a] + d for a in range(3)]
+        sel = c * (n_scales - 1) <= (n_scales - 1 - i) * M
+        if sel.any():
+            for a in range(3):
+                lo[a] = min(lo[a], float(nodes[sel, a].min()))
+                hi[a] = max(hi[a], float(nodes[sel, a].max()))
+        origin, dims = [], []
+        for a in range(3):
+            top = float(ref[a] - 1)
+            l, u = max(lo[a], 0.0), min(hi[a], top)
+            n = max(int(math.floor((u - l) / h + 1e-9)) + 1, 4)
+            if l + (n - 1) * h > top + 1e-9:
+                l = max(0.0, top - (n - 1) * h)
+            origin.append(l)
+            dims.append(n)
+        out.append((tuple(origin), h, tuple(dims)))
+    return out

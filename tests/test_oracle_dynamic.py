@@ -136,3 +136,65 @@ def test_static_scales_worked_example():
     assert h1 == 0.75 and d1 == (33, 15, 17) and np.allclose(o1, (6.0, 16.0, 1.0))
     assert h2 == 0.5 and d2 == (33, 7, 9) and np.allclose(o2, (10.0, 20.0, 5.0))
     assert dynamic.static_scales(np.zeros((8, 8, 8), np.uint8), 3, 0.5, 4.0, 0.0) == []
+
+
+def test_visibility_of_a_cube_from_a_point_light():
+    """One light point at (0, 24, 24) and an obstacle cube of voxels 20..27 on every axis
+    (faces at 19.5 and 27.5): the segment from a node at x, off the light's axis by dy, dz,
+    is off the axis by (dy, dz) x' / x where it crosses the plane x'.  It runs inside the
+    cube's cross-section [-4.5, 3.5]^2 for all x' in [19.5, 27.5] when
+    max(|dy|, |dz|) 27.5 / x < 3.5 (dark), and outside it for all x' when
+    max(|dy|, |dz|) 19.5 / x > 4.5 (lit); one voxel of margin on each side for the voxel
+    rounding.  Nodes upstream of the cube are all lit."""
+    flags = np.zeros((48, 48, 64), np.uint8)
+    flags[20:28, 20:28, 20:28] = grid.SOLID
+    light = np.array([[0, 24, 24]])
+    rng = np.random.default_rng(3)
+    pts = np.stack([rng.integers(30, 64, 2000), rng.integers(0, 48, 2000),
+                    rng.integers(0, 48, 2000)], 1)
+    c = dynamic.visibility(flags, pts, light)
+    x = pts[:, 0].astype(float)
+    r = np.maximum(np.abs(pts[:, 1] - 24.0), np.abs(pts[:, 2] - 24.0))
+    dark = r * 27.5 / x < 2.5
+    lit = r * 19.5 / x > 5.5
+    assert dark.sum() > 20 and lit.sum() > 20
+    assert (c[dark] == 0).all() and (c[lit] == 1).all()
+    up = np.stack([rng.integers(1, 19, 50), rng.integers(0, 48, 50), rng.integers(0, 48, 50)], 1)
+    assert (dynamic.visibility(flags, up, light) == 1).all()
+
+
+def test_light_samples_follow_the_inlet():
+    flags = np.zeros((10, 12, 16), np.uint8)
+    assert len(dynamic.light_samples(flags, 0, 16)) == 15       # 120 face nodes, every 8th
+    flags[3:6, 4:8, 0] = grid.INFLOW
+    ls = dynamic.light_samples(flags, 0, 4)
+    assert len(ls) == 4 and (ls[:, 0] == 0).all()               # 12 inflow nodes, every 3rd
+    assert set(map(tuple, ls[:, 1:])) <= {(y, z) for z in range(3, 6) for y in range(4, 8)}
+
+
+def test_shadow_scales_worked_example():
+    """Two light points, one each side of an obstacle plate: behind the plate the nodes that
+    see neither light (c = 0) form the umbra of the finest scale, those that see one of the
+    two the penumbra the coarser scale adds; with 3 scales (thresholds c <= 1 and c = 0)
+    scale 2's wake box is the umbra's box and scale 1's the union with the penumbra's, and
+    both include the obstacle box widened by d."""
+    flags = np.zeros((9, 40, 48), np.uint8)
+    flags[:, 16:24, 12:14] = grid.SOLID                        # plate x 12..13, y 16..23
+    flags[4, 10, 0] = flags[4, 29, 0] = grid.INFLOW            # lights at y = 10 and y = 29
+    lights = dynamic.light_samples(flags, 0, 16)
+    assert len(lights) == 2
+    sc = dynamic.shadow_scales(flags, 3, 0.5, 0.0, 20.0, flow_axis=0)
+    zz, yy, xx = np.meshgrid(np.arange(9), np.arange(40), np.arange(48), indexing="ij")
+    cand = (xx >= 12) & (xx <= 33) & ((flags & grid.SOLID) == 0)
+    nodes = np.stack([xx[cand], yy[cand], zz[cand]], 1)
+    c = dynamic.visibility(flags, nodes, lights)
+    umbra, pen = nodes[c == 0], nodes[c <= 1]
+    assert len(umbra) > 0 and len(pen) > len(umbra)
+    (o1, h1, d1), (o2, h2, d2) = sc
+    for (o, h, d), sel in (((o1, h1, d1), pen), ((o2, h2, d2), umbra)):
+        for a in range(3):
+            lo = min(float(sel[:, a].min()), [12, 16, 0][a])
+            assert o[a] == max(lo, 0.0)
+            hi = max(float(sel[:, a].max()), [13, 23, 8][a])
+            top = [47, 39, 8][a]
+            assert d[a] == max(int(math.floor((min(hi, top) - o[a]) / h + 1e-9)) + 1, 4)
