@@ -234,9 +234,29 @@ lbm_status lbm_build_dynamic_scale(lbm_domain* dom, int32_t src_block, double h,
    below 0, at block 0's upper end).  The scales are added coarse to fine with
    lbm_add_scale_block and started with lbm_init_block_from_parent; *n_added receives their
    number (0 without obstacles).  INVALID_ARG for n_scales < 2, h_min outside (0, 1),
-   negative d_max or wake, a bad axis; the errors of the calls it makes otherwise. */
+   negative d_max or wake, a bad axis; UNSUPPORTED when the domain has obstacle-surface walls
+   (LBM_BC_WALLS byte 6); the errors of the calls it makes otherwise. */
 lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales, double h_min, double d_max,
                                    double wake, int32_t flow_axis, int32_t* n_added);
+
+/* Static scale construction with the wake shaped as a soft shadow (Sec. 5: the inlet seen as
+   an area light source, the darker shadow behind the obstacles taking the finer scales).
+   The light is sampled at M <= n_light points: the inflow nodes of block 0 in index order
+   (x fastest), every ceil(count / n_light)-th one, or, with no inflow node, the nodes of
+   block 0's upstream face (index 0 along flow_axis) the same way.  Every node of block 0
+   that is not an obstacle voxel and lies along flow_axis between the obstacles' upstream end
+   and min(floor(downstream end + wake), last node) counts the samples it sees: the segment
+   to a sample is walked in 2 m steps (m its largest coordinate difference), step k checked
+   at the nearest node of p + d k / (2 m) computed in integers as
+   (2 (p 2m + d k) + 2m) div (4m), end points excluded, and the sample is hidden when one of
+   them is an obstacle voxel.  A node that sees c samples belongs to the wake of scale i
+   (1 .. n_scales - 1) when c (n_scales - 1) <= (n_scales - 1 - i) M.  Scale i's box is the
+   union of the obstacles' box widened by d_i (as above, without the straight wake) and the
+   bounding box of its wake nodes, clipped, sized and started as above.  INVALID_ARG as
+   above and for n_light < 1 or n_scales > 8; UNSUPPORTED with obstacle-surface walls. */
+lbm_status lbm_build_static_scales_shadow(lbm_domain* dom, int32_t n_scales, double h_min,
+                                          double d_max, double wake, int32_t flow_axis,
+                                          int32_t n_light, int32_t* n_added);
 
 /* Sets boundary data of one block (see LBM_BC_*).  ptr/nbytes describe the caller array;
    it is copied before return (host) or before the next enqueued work (device). */

@@ -148,6 +148,85 @@ __global__ void k_nearest_flags(uint8_t* dflags, int dnx, int dny, int dnz, doub
   }
 }
 
+// Soft-shadow wake of the static scale construction (Sec. 5): every non-obstacle node of the
+// slab a0 <= coordinate <= a1 along `axis` counts the light samples (lights: M points, 3
+// ints each) whose segment to it crosses no obstacle voxel.  The segment is walked in 2 m
+// steps (m its largest coordinate difference), step k checked at the nearest voxel of
+// p + d k / (2 m) in integer arithmetic (end points not checked).  A node that sees c samples
+// belongs to the wake of refined scale s = 1 .. nsc - 1 when c (nsc - 1) <= (nsc - 1 - s) M;
+// out[s - 1] receives the count and bounding box of those nodes (per-thread, then per-warp
+// reductions, then one atomic per warp and value: the result does not depend on order).
+constexpr int SHADOW_MAX_SCALES = 8;
+
+__global__ void __launch_bounds__(256) k_shadow(const uint8_t* __restrict__ flags, int nx, int ny,
+                                                int nz, int axis, int a0, int a1,
+                                                const int* __restrict__ lights, int M, int nsc,
+                                                RegionOut* out) {
+  int ext[3] = {nx, ny, nz}, org[3] = {0, 0, 0};
+  ext[axis] = a1 - a0 + 1;
+  org[axis] = a0;
+  const long long total = (long long)ext[0] * ext[1] * ext[2];
+  unsigned cnt[SHADOW_MAX_SCALES - 1];
+  int lo[SHADOW_MAX_SCALES - 1][3], hi[SHADOW_MAX_SCALES - 1][3];
+#pragma unroll
+  for (int s = 0; s < SHADOW_MAX_SCALES - 1; ++s) {
+    cnt[s] = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { lo[s][a] = INT_MAX; hi[s][a] = -1; }
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p[3] = {org[0] + (int)(i % ext[0]), org[1] + (int)((i / ext[0]) % ext[1]),
+                      org[2] + (int)(i / ((long long)ext[0] * ext[1]))};
+    if (flags[((size_t)p[2] * ny + p[1]) * nx + p[0]] & F_SOLID) continue;
+    int c = 0;
+    for (int j = 0; j < M; ++j) {
+      const long long d[3] = {(long long)lights[3 * j] - p[0], (long long)lights[3 * j + 1] - p[1],
+                              (long long)lights[3 * j + 2] - p[2]};
+      long long m = d[0] < 0 ? -d[0] : d[0];
+      for (int a = 1; a < 3; ++a) m = max(m, d[a] < 0 ? -d[a] : d[a]);
+      const long long n = 2 * m;
+      bool blocked = false;
+      for (long long k = 1; k < n && !blocked; ++k) {
+        long long v[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] = (2 * (p[a] * n + d[a] * k) + n) / (2 * n);
+        blocked = (flags[((size_t)v[2] * ny + v[1]) * nx + v[0]] & F_SOLID) != 0;
+      }
+      c += blocked ? 0 : 1;
+    }
+#pragma unroll
+    for (int s = 1; s < SHADOW_MAX_SCALES; ++s) {
+      if (s < nsc && (long long)c * (nsc - 1) <= (long long)(nsc - 1 - s) * M) {
+        ++cnt[s - 1];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          lo[s - 1][a] = min(lo[s - 1][a], p[a]);
+          hi[s - 1][a] = max(hi[s - 1][a], p[a]);
+        }
+      }
+    }
+  }
+  const unsigned full = 0xffffffffu;
+#pragma unroll
+  for (int s = 0; s < SHADOW_MAX_SCALES - 1; ++s) {
+    const unsigned cs = __reduce_add_sync(full, cnt[s]);
+    int l[3], h[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      l[a] = __reduce_min_sync(full, lo[s][a]);
+      h[a] = __reduce_max_sync(full, hi[s][a]);
+    }
+    if ((threadIdx.x & 31) == 0 && cs && s + 1 < nsc) {
+      atomicAdd(&out[s].count, (unsigned long long)cs);
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&out[s].lo[a], l[a]);
+        atomicMax(&out[s].hi[a], h[a]);
+      }
+    }
+  }
+}
+
 }  // namespace lbm
 
 using namespace lbm;
@@ -296,9 +375,11 @@ extern "C" lbm_status lbm_build_dynamic_scale(lbm_domain* dom, int32_t src_block
   return LBM_OK;
 }
 
-extern "C" lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales, double h_min,
-                                              double d_max, double wake, int32_t flow_axis,
-                                              int32_t* n_added) {
+// Static scale construction (Sec. 5); n_light > 0 shapes each scale's wake as a soft shadow
+// (k_shadow), n_light == 0 extends every box straight downstream by `wake`.
+static lbm_status static_scales(lbm_domain* dom, int32_t n_scales, double h_min, double d_max,
+                                double wake, int32_t flow_axis, int32_t n_light,
+                                int32_t* n_added) {
   if (!dom) return LBM_ERR_INVALID_ARG;
   cudaSetDevice(dom->desc.device);
   if (!n_added) return dom->fail(LBM_ERR_INVALID_ARG, "null n_added");
@@ -308,6 +389,8 @@ extern "C" lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales,
   if (n_scales < 2 || !(h_min > 0.0 && h_min < 1.0) || !(d_max >= 0.0) || !(wake >= 0.0) ||
       flow_axis < 0 || flow_axis > 2)
     return dom->fail(LBM_ERR_INVALID_ARG, "need n_scales >= 2, 0 < h_min < 1, d_max, wake >= 0, axis 0..2");
+  if (n_light < 0 || (n_light > 0 && n_scales > SHADOW_MAX_SCALES))
+    return dom->fail(LBM_ERR_INVALID_ARG, "a shadow-shaped wake needs n_light >= 1 and n_scales <= 8");
   const Block& B0 = dom->blocks[0];
   RegionOut* d_out = reinterpret_cast<RegionOut*>(dom->d_red);
   int sms = 0;
@@ -325,6 +408,57 @@ extern "C" lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales,
   std::memcpy(&r, dom->h_red, sizeof(RegionOut));
   if (r.count == 0) return LBM_OK;
   const int ref[3] = {B0.nx, B0.ny, B0.nz};
+  // the wake of every refined scale: a straight extension, or the soft shadow's boxes
+  std::vector<RegionOut> shadow;
+  if (n_light > 0) {
+    // light samples: the inflow nodes (every ceil(count / n_light)-th in index order), or the
+    // nodes of the upstream face without inflow nodes
+    std::vector<uint8_t> fl(B0.N);
+    e = cudaMemcpyAsync(fl.data(), B0.flags, B0.N, cudaMemcpyDeviceToHost, dom->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(dom->stream);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "flags read-back");
+    std::vector<int> pts;
+    for (int pass = 0; pass < 2 && pts.empty(); ++pass)
+      for (size_t i = 0; i < B0.N; ++i) {
+        const int x = (int)(i % B0.nx), y = (int)((i / B0.nx) % B0.ny), z = (int)(i / ((size_t)B0.nx * B0.ny));
+        const int c[3] = {x, y, z};
+        if (pass == 0 ? (fl[i] & F_INFLOW) != 0 : c[flow_axis] == 0) {
+          pts.push_back(x); pts.push_back(y); pts.push_back(z);
+        }
+      }
+    const size_t count = pts.size() / 3, stride = (count + n_light - 1) / n_light;
+    std::vector<int> lights;
+    for (size_t j = 0; j < count; j += stride)
+      for (int a = 0; a < 3; ++a) lights.push_back(pts[3 * j + a]);
+    const int M = (int)(lights.size() / 3);
+    const int a0 = r.lo[flow_axis];
+    const int a1 = std::min((int)std::floor(r.hi[flow_axis] + wake), ref[flow_axis] - 1);
+    int* d_lights = static_cast<int*>(dom->dev_alloc(lights.size() * sizeof(int)));
+    RegionOut* d_sh = static_cast<RegionOut*>(dom->dev_alloc((SHADOW_MAX_SCALES - 1) * sizeof(RegionOut)));
+    if (!d_lights || !d_sh) {
+      dom->dev_free(d_lights);
+      dom->dev_free(d_sh);
+      return dom->fail(LBM_ERR_OOM, "shadow buffers");
+    }
+    shadow.resize(SHADOW_MAX_SCALES - 1);
+    e = cudaMemcpyAsync(d_lights, lights.data(), lights.size() * sizeof(int), cudaMemcpyHostToDevice, dom->stream);
+    for (int s = 0; s < SHADOW_MAX_SCALES - 1 && e == cudaSuccess; ++s) {
+      k_detect_init<<<1, 1, 0, dom->stream>>>(d_sh + s);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_shadow<<<std::max(sms, 1) * 8, 256, 0, dom->stream>>>(B0.flags, B0.nx, B0.ny, B0.nz, flow_axis, a0, a1,
+                                                          d_lights, M, n_scales, d_sh);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(shadow.data(), d_sh, (SHADOW_MAX_SCALES - 1) * sizeof(RegionOut),
+                          cudaMemcpyDeviceToHost, dom->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(dom->stream);
+    dom->dev_free(d_lights);
+    dom->dev_free(d_sh);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "shadow");
+  }
   for (int i = 1; i < n_scales; ++i) {
     const double h = 1.0 + (h_min - 1.0) * i / (n_scales - 1);
     const double d = d_max * (n_scales - 1 - i) / (n_scales - 1);
@@ -333,7 +467,14 @@ extern "C" lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales,
     for (int a = 0; a < 3; ++a) {
       const double top = (double)(ref[a] - 1);
       double lo = r.lo[a] - d, hi = r.hi[a] + d;
-      if (a == flow_axis) hi += wake;
+      if (n_light > 0) {
+        if (shadow[i - 1].count) {
+          lo = std::min(lo, (double)shadow[i - 1].lo[a]);
+          hi = std::max(hi, (double)shadow[i - 1].hi[a]);
+        }
+      } else if (a == flow_axis) {
+        hi += wake;
+      }
       lo = std::max(lo, 0.0);
       hi = std::min(hi, top);
       const int n = std::max((int)std::floor((hi - lo) / h + 1e-9) + 1, 4);
@@ -352,5 +493,19 @@ extern "C" lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales,
     ++*n_added;
   }
   return LBM_OK;
+}
+
+extern "C" lbm_status lbm_build_static_scales(lbm_domain* dom, int32_t n_scales, double h_min,
+                                              double d_max, double wake, int32_t flow_axis,
+                                              int32_t* n_added) {
+  return static_scales(dom, n_scales, h_min, d_max, wake, flow_axis, 0, n_added);
+}
+
+extern "C" lbm_status lbm_build_static_scales_shadow(lbm_domain* dom, int32_t n_scales,
+                                                     double h_min, double d_max, double wake,
+                                                     int32_t flow_axis, int32_t n_light,
+                                                     int32_t* n_added) {
+  if (dom && n_light < 1) return dom->fail(LBM_ERR_INVALID_ARG, "n_light must be >= 1");
+  return static_scales(dom, n_scales, h_min, d_max, wake, flow_axis, n_light, n_added);
 }
 

@@ -76,6 +76,8 @@ _SIGNATURES = {
                                      C.POINTER(C.c_int32)]),
     "lbm_build_static_scales": (_I, [_P, _I, C.c_double, C.c_double, C.c_double, _I,
                                      C.POINTER(C.c_int32)]),
+    "lbm_build_static_scales_shadow": (_I, [_P, _I, C.c_double, C.c_double, C.c_double, _I, _I,
+                                            C.POINTER(C.c_int32)]),
     "lbm_step": (_I, [_P, _I]),
     "lbm_sync": (_I, [_P]),
     "lbm_read_macro": (_I, [_P, _I, _I, _P, C.c_size_t, _I]),
@@ -262,6 +264,15 @@ class Domain:
         self.check(self.lib.lbm_build_static_scales(self.handle, int(n_scales), float(h_min),
                                                     float(d_max), float(wake), int(flow_axis),
                                                     C.byref(n)))
+        return n.value
+
+    def build_static_scales_shadow(self, n_scales: int, h_min: float, d_max: float,
+                                   wake: float, flow_axis: int = 0, n_light: int = 16) -> int:
+        """Static scales whose wakes follow the soft shadow of the obstacles lit by the inlet."""
+        n = C.c_int32()
+        self.check(self.lib.lbm_build_static_scales_shadow(self.handle, int(n_scales), float(h_min),
+                                                           float(d_max), float(wake), int(flow_axis),
+                                                           int(n_light), C.byref(n)))
         return n.value
 
     def info(self, block=0) -> lbm_block_info:

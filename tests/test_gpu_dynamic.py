@@ -156,3 +156,58 @@ def test_static_scales_match_oracle(lib):
         ms.step()
     compare(dom, ms, "static scales stepped")
     dom.close()
+
+
+def test_shadow_scales_match_oracle(lib):
+    """Static construction with the soft-shadow wake (Sec. 5): the inflow disk lights the
+    sphere, 4 scales (h = 1, 5/6, 2/3, 1/2); the blocks placed from the GPU's integer
+    visibility counts equal the oracle's (which differ from the straight wake's here), their
+    started states and the following steps match."""
+    sc = _scene()
+    dom = gpu_multiscale(sc)
+    ms = coupling.MultiScale.build(sc)
+    for _ in range(2):
+        dom.step(1)
+        ms.step()
+    n = dom.build_static_scales_shadow(4, 0.5, 2.0, wake=6.0, flow_axis=0, n_light=16)
+    plan = dynamic.shadow_scales(sc.blocks[0].flags, 4, 0.5, 2.0, 6.0, flow_axis=0, n_light=16)
+    assert plan != dynamic.static_scales(sc.blocks[0].flags, 4, 0.5, 2.0, 6.0, flow_axis=0)
+    assert n == len(plan) == 3
+    for i, (o, h, d) in enumerate(plan, start=1):
+        info = dom.info(i)
+        assert tuple(info.dims) == d and abs(info.h - h) < 1e-12
+        assert np.allclose(tuple(info.origin), o, atol=1e-12)
+        dynamic.add_block_from_parent(ms, o, h, d)
+    compare(dom, ms, "shadow scales started")
+    for _ in range(2):
+        dom.step(1)
+        ms.step()
+    compare(dom, ms, "shadow scales stepped")
+    dom.close()
+
+
+def test_shadow_scales_point_light_cone(lib):
+    """A cube lit by one inflow node on the upstream face: with 2 scales and d = 0 the refined
+    block is the bounding box of the cube and its shadow cone (the nodes that see c = 0 of
+    M = 1 samples), as the oracle counts it; without obstacles nothing is added."""
+    from paper_1807_02284_gb300 import lbm
+    dims = (40, 24, 24)
+    shape = dims[::-1]
+    flags = np.zeros(shape, np.uint8)
+    flags[9:15, 9:15, 10:16] = 1                     # cube x 10..15, y 9..14, z 9..14
+    flags[12, 12, 0] = 2                             # one inflow node
+    plan = dynamic.shadow_scales(flags, 2, 0.5, 0.0, 20.0, flow_axis=0, n_light=4)
+    assert len(plan) == 1
+    (o, h, d), = plan
+    assert d[0] > (15 - 10) / h + 1                 # the cone reaches past the cube
+    for fl, n_want in ((flags, 1), (flags & 2, 0)):
+        dom = lbm.Domain(dims, 0.01)
+        dom.set_flags(fl)
+        dom.init_macro(np.zeros(shape + (3,), np.float32), rho=np.ones(shape, np.float32),
+                       c=np.zeros(shape, np.float32))
+        assert dom.build_static_scales_shadow(2, 0.5, 0.0, 20.0, 0, 4) == n_want
+        if n_want:
+            info = dom.info(1)
+            assert tuple(info.dims) == d and abs(info.h - h) < 1e-12
+            assert np.allclose(tuple(info.origin), o, atol=1e-12)
+        dom.close()
