@@ -19,10 +19,12 @@
 // scalar's departure-point term; dL/du_0 at an inflow node is then the gradient with respect
 // to its (constant) inflow velocity.
 // Open faces copy the nearest in-block node, so a slot of a face node can be read by up to 8
-// pulls: those slots are zeroed before pass A and accumulated atomically (every other slot
-// is read once and stored), pass B's lagged-velocity gather uses the clamped differences
-// (a face node's own difference involves itself), and the scalar gather counts a clamped
-// repeat of the node once.
+// pulls: the one pull that reads it without clamping (or the node's own bounce-back) stores
+// into the slot, every clamped pull stores its adjoint in a side buffer indexed by the reading
+// node and direction, and k_face_gather then adds those to the slots in a fixed order (no
+// atomics: the gradients are bit-reproducible).  Pass B's lagged-velocity gather uses the
+// clamped differences (a face node's own difference involves itself), and the scalar gather
+// counts a clamped repeat of the node once.
 // Scope: blocks with >= 3 nodes per axis, FP32 or FP16-shifted storage (the checkpoints of
 // an FP16 run hold its deviations widened to FP32; replays and transposes run in FP32), and
 // continuous-scale domains of refined and far-field blocks (the reversed Algorithm 1
@@ -49,6 +51,7 @@ struct AdjArgs {
   float* mu;            // 9 planes: adjoint of the velocity differences of the gradient norm
   float* sw;            // 9 planes: departure-sample weights of each sender (put_sender)
   float* sg;            // sender's scalar adjoint, 0 for non-senders
+  float* side;          // open faces: adjoints of the clamped pulls (FaceSide layout)
 };
 
 // Adjoint of the scalar step with respect to the departure velocity: C^{n+1}(x) is the
@@ -76,52 +79,84 @@ __device__ __forceinline__ void scalar_u_vjp(const BlockView& v, int x, int y, i
   if (fabsf(uz) < 1.0f && !lz) ub[2] -= gam * dtz;
 }
 
-// Which of the candidate source positions (x-1, x, x+1 per axis, after wrapping or clamping)
-// lie on an open face, as bits 3a + o + 1 (axis a, offset o).  A slot of a node on an open
-// face can be read by more than one pull (the face copies its nearest in-block node), so its
-// adjoint is accumulated there; every other slot is read by exactly one pull and stored.
-using FaceMask = uint32_t;
+// Open faces.  A pull whose source x - e_K lies outside the block along a non-periodic axis
+// reads the nearest in-block node instead (the clamped copy), so a face node's slot can be
+// read by several pulls.  Bits 2a / 2a + 1 of a node's clamp mask say that the node lies on
+// the open lower / upper face of axis a; the pull of direction K is clamped on axis a when
+// e_K,a = +1 and bit 2a is set, or e_K,a = -1 and bit 2a + 1 is set.
+using ClampMask = uint32_t;
 
 template <bool OPEN>
-__device__ __forceinline__ FaceMask face_mask(const BlockView& v, int x, int y, int z) {
+__device__ __forceinline__ ClampMask clamp_mask(const BlockView& v, int x, int y, int z) {
   if constexpr (!OPEN) return 0u;
-  FaceMask f = 0u;
   const int c[3] = {x, y, z}, nn[3] = {v.nx, v.ny, v.nz};
+  ClampMask m = 0u;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int o = -1; o <= 1; ++o) {
-      const int j = nbr(c[a], o, nn[a], v.per[a]);
-      if (!v.per[a] && (j == 0 || j == nn[a] - 1)) f |= 1u << (3 * a + o + 1);
-    }
-  return f;
+  for (int a = 0; a < 3; ++a) {
+    if (v.per[a]) continue;
+    if (c[a] == 0) m |= 1u << (2 * a);
+    if (c[a] == nn[a] - 1) m |= 2u << (2 * a);
+  }
+  return m;
+}
+
+// Side buffer of the clamped pulls: one entry per (reading node, direction), filed under the
+// lowest axis a0 on which the pull is clamped.  That node lies on face (a0, lower / upper),
+// and the direction has e_K,a0 = +1 / -1, so 9 directions remain, numbered by the other two
+// components (b < c): j = 3 (e_b + 1) + (e_c + 1).  Face (a0, side) holds 9 planes of its
+// area n_b n_c, the position x_b + n_b x_c; faces follow in the order x-, x+, y-, y+, z-, z+.
+// 9 * 2 * (ny nz + nx nz + nx ny) floats per block.
+__host__ __device__ __forceinline__ size_t face_side_floats(int nx, int ny, int nz) {
+  return (size_t)18 * ((size_t)ny * nz + (size_t)nx * nz + (size_t)nx * ny);
+}
+
+__device__ __forceinline__ uint32_t face_side_index(int nx, int ny, int nz, int a0, int hi,
+                                                    const int (&p)[3], const int (&e)[3]) {
+  const uint32_t A0 = (uint32_t)ny * nz, A1 = (uint32_t)nx * nz, A2 = (uint32_t)nx * ny;
+  const uint32_t area = a0 == 0 ? A0 : (a0 == 1 ? A1 : A2);
+  const uint32_t off = 9u * (a0 == 0 ? 0u : (a0 == 1 ? 2u * A0 : 2u * (A0 + A1))) + 9u * hi * area;
+  const int b = a0 == 0 ? 1 : 0, c = a0 == 2 ? 1 : 2;
+  const int nb = b == 0 ? nx : ny;
+  const uint32_t pos = (uint32_t)p[b] + (uint32_t)nb * (uint32_t)p[c];
+  const uint32_t j = (uint32_t)(3 * (e[b] + 1) + (e[c] + 1));
+  return off + j * area + pos;
 }
 
 // ACC: add to the adjoint already held by the slot (the reverse of a multi-block schedule,
-// where a level is read by several operations) instead of storing it.
+// where a level is read by several operations) instead of storing it.  Every slot has at most
+// one unclamped reader or bounce-back writer, so the plain store / add never collides; a
+// clamped pull goes to the side buffer (its own entry) and k_face_gather adds it later.
 template <bool OPEN, bool ACC, int K = 0>
 __device__ __forceinline__ void push_all(const float (&A)[27], float* __restrict__ lam,
                                          uint32_t N, const Nbr<uint32_t>& n, uint32_t idx,
                                          const uint8_t* __restrict__ flags, bool near,
-                                         FaceMask fm) {
+                                         ClampMask cm, const BlockView& v, int x, int y, int z,
+                                         float* __restrict__ side) {
   if constexpr (K < 27) {
     constexpr int cx = cxk(K), cy = cyk(K), cz = czk(K);
     const uint32_t src = pull_src<K>(n);
     uint32_t slot = (uint32_t)K * N + src;
     const bool bb = K != 13 && near && (__ldg(flags + src) & F_SOLID);
     if (bb) slot = (uint32_t)(26 - K) * N + idx;
+    bool stored = false;
     if constexpr (OPEN) {
-      constexpr FaceMask own = (1u << 1) | (1u << 4) | (1u << 7);
-      constexpr FaceMask src_bits = (1u << (1 - cx)) | (1u << (4 - cy)) | (1u << (7 - cz));
-      const bool face = (fm & (bb ? own : src_bits)) != 0u;
-      if (face) atomicAdd(lam + slot, A[K]);
-      else if (ACC) lam[slot] += A[K];
-      else lam[slot] = A[K];
-    } else {
+      constexpr ClampMask kb = (cx == 1 ? 1u : cx == -1 ? 2u : 0u) |
+                               (cy == 1 ? 4u : cy == -1 ? 8u : 0u) |
+                               (cz == 1 ? 16u : cz == -1 ? 32u : 0u);
+      const ClampMask hit = cm & kb;
+      if (hit != 0u && !bb) {
+        const int a0 = (hit & 3u) ? 0 : ((hit & 12u) ? 1 : 2);
+        const int hi = (hit >> (2 * a0)) & 2u ? 1 : 0;
+        const int p[3] = {x, y, z}, e[3] = {cx, cy, cz};
+        side[face_side_index(v.nx, v.ny, v.nz, a0, hi, p, e)] = A[K];
+        stored = true;
+      }
+    }
+    if (!stored) {
       if (ACC) lam[slot] += A[K];
       else lam[slot] = A[K];
     }
-    push_all<OPEN, ACC, K + 1>(A, lam, N, n, idx, flags, near, fm);
+    push_all<OPEN, ACC, K + 1>(A, lam, N, n, idx, flags, near, cm, v, x, y, z, side);
   }
 }
 
@@ -213,18 +248,97 @@ __device__ __forceinline__ void collide_vjp(float (&K)[27], float (&A)[27], floa
   raw_axis_vjp<1>(A);                    // A = adjoint of the pulled populations
 }
 
-// Zeroes the adjoint slots of the nodes on open faces before pass A accumulates into them.
+// The nodes of a block's open faces, each once: thread t walks the open faces in the order
+// x-, x+, y-, y+, z-, z+ and skips a node that an earlier open face already holds.
+__device__ __forceinline__ bool open_face_node(size_t t, int nx, int ny, int nz, const int (&per)[3],
+                                               int (&p)[3]) {
+  const int nn[3] = {nx, ny, nz};
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const int a = f >> 1;
+    if (per[a]) continue;
+    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+    const size_t area = (size_t)nn[b] * nn[c];
+    if (t >= area) {
+      t -= area;
+      continue;
+    }
+    p[a] = (f & 1) ? nn[a] - 1 : 0;
+    p[b] = (int)(t % nn[b]);
+    p[c] = (int)(t / nn[b]);
+    for (int a2 = 0; a2 < a; ++a2)
+      if (!per[a2] && (p[a2] == 0 || p[a2] == nn[a2] - 1)) return false;
+    return true;
+  }
+  return false;
+}
+
+__host__ __device__ __forceinline__ size_t open_face_threads(int nx, int ny, int nz, const int (&per)[3]) {
+  return (per[0] ? 0 : 2 * (size_t)ny * nz) + (per[1] ? 0 : 2 * (size_t)nx * nz) +
+         (per[2] ? 0 : 2 * (size_t)nx * ny);
+}
+
+// Zeroes the adjoint slots of the nodes on open faces before pass A: a face slot that no pull
+// reads unclamped only receives the clamped pulls' sum, which k_face_gather adds.
 __global__ void k_zero_face_slots(float* __restrict__ lam, int nx, int ny, int nz, int px,
                                   int py, int pz) {
   const size_t N = (size_t)nx * ny * nz;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((size_t)nx * ny));
-    const bool face = (!px && (x == 0 || x == nx - 1)) || (!py && (y == 0 || y == ny - 1)) ||
-                      (!pz && (z == 0 || z == nz - 1));
-    if (!face) continue;
+  const int per[3] = {px, py, pz};
+  const size_t T = open_face_threads(nx, ny, nz, per);
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < T;
+       t += (size_t)gridDim.x * blockDim.x) {
+    int p[3];
+    if (!open_face_node(t, nx, ny, nz, per, p)) continue;
+    const size_t idx = ((size_t)p[2] * ny + p[1]) * nx + p[0];
 #pragma unroll
     for (int k = 0; k < 27; ++k) lam[(size_t)k * N + idx] = 0.0f;
+  }
+}
+
+// After pass A: every open-face slot (k, s) adds the adjoints of the clamped pulls that read
+// it, in a fixed order, and clears their side entries (each is read by exactly this slot, so
+// the buffer is all zeros again for the next launch).  The readers x of (k, s) have, per axis
+// a, either x_a = s_a + e_k,a (unclamped) or x_a = s_a where s_a is the face that the pull
+// leaves (e_k,a = +1 at s_a = 0, -1 at s_a = n_a - 1); the combinations with at least one
+// clamped axis are taken in the order of their axis bits.
+__global__ void k_face_gather(float* __restrict__ lam, float* __restrict__ side, int nx, int ny,
+                              int nz, int px, int py, int pz) {
+  const size_t N = (size_t)nx * ny * nz;
+  const int per[3] = {px, py, pz}, nn[3] = {nx, ny, nz};
+  const size_t T = open_face_threads(nx, ny, nz, per);
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < T;
+       t += (size_t)gridDim.x * blockDim.x) {
+    int s[3];
+    if (!open_face_node(t, nx, ny, nz, per, s)) continue;
+    const size_t idx = ((size_t)s[2] * ny + s[1]) * nx + s[0];
+    for (int k = 0; k < 27; ++k) {
+      const int e[3] = {k % 3 - 1, (k / 3) % 3 - 1, k / 9 - 1};
+      float sum = 0.0f;
+      bool any = false;
+      for (int combo = 1; combo < 8; ++combo) {
+        int xr[3];
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (combo & (1 << a)) {   // clamped on axis a
+            ok = ok && !per[a] && ((e[a] == 1 && s[a] == 0) || (e[a] == -1 && s[a] == nn[a] - 1));
+            xr[a] = s[a];
+          } else {
+            int q = s[a] + e[a];
+            if (per[a]) q = q < 0 ? q + nn[a] : (q >= nn[a] ? q - nn[a] : q);
+            ok = ok && q >= 0 && q < nn[a];
+            xr[a] = q;
+          }
+        }
+        if (!ok) continue;
+        const int a0 = (combo & 1) ? 0 : ((combo & 2) ? 1 : 2);
+        const uint32_t si = face_side_index(nx, ny, nz, a0, e[a0] == -1 ? 1 : 0, xr, e);
+        sum += side[si];
+        side[si] = 0.0f;
+        any = true;
+      }
+      if (any) lam[(size_t)k * N + idx] += sum;
+    }
   }
 }
 
@@ -337,7 +451,7 @@ __device__ __forceinline__ void wall_regularize_vjp(float (&A)[27], const BlockV
   }
 }
 
-// OPEN: some face of the block is open (face slots accumulate; see FaceMask).  ACC: the
+// OPEN: some face of the block is open (clamped pulls go to the side buffer).  ACC: the
 // adjoints of the input level are added to (multi-block reverse), and scale-boundary (ghost)
 // nodes, which the step does not update, are left to the mapping that wrote them.  WALLS:
 // the block has wall faces or obstacle-surface walls (wall_regularize and its transpose).
@@ -390,7 +504,7 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
 #pragma unroll
       for (int k = 0; k < 27; ++k) Z[k] = 0.0f;
       push_all<OPEN, false>(Z, a.lam_out, N, n, idx, v.flags, (fl & F_NEAR_SOLID) != 0,
-                            face_mask<OPEN>(v, x, y, z));
+                            clamp_mask<OPEN>(v, x, y, z), v, x, y, z, a.side);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) a.mu[(uint32_t)i * N + idx] = 0.0f;
@@ -452,7 +566,8 @@ __global__ void __launch_bounds__(128, MINB) k_adj_a(AdjArgs a) {
   if constexpr (WALLS) {
     if (wall) wall_regularize_vjp<uint32_t>(A, v, x, y, z, fl, n);
   }
-  push_all<OPEN, ACC>(A, a.lam_out, N, n, idx, v.flags, near, face_mask<OPEN>(v, x, y, z));
+  push_all<OPEN, ACC>(A, a.lam_out, N, n, idx, v.flags, near, clamp_mask<OPEN>(v, x, y, z), v, x,
+                      y, z, a.side);
 
   // ---- adjoint of the adaptive factor: K_g = 1 - 1/(phi nu3_g + 1/2)
   float mu_scale = 0.0f;          // (the local-strain mode has no lagged-velocity dependence)
@@ -784,6 +899,7 @@ struct TapeState {
   float* ups[2] = {nullptr, nullptr};
   float* gam[2] = {nullptr, nullptr};
   float* mu = nullptr;
+  float* side = nullptr;      // clamped pulls of open faces (all zeros between launches)
   // continuous-scale domains (several blocks)
   bool multi = false;
   std::vector<std::vector<Level>> mck;        // [checkpoint][block]: state at the step start
@@ -815,6 +931,7 @@ void release_tape(lbm_domain* dom) {
     dom->dev_free(t->gam[i]);
   }
   dom->dev_free(t->mu);
+  dom->dev_free(t->side);
   for (auto& v : t->mck) for (Level& L : v) free_level(dom, L);
   for (auto& v : t->snap) for (Level& L : v) free_level(dom, L);
   for (auto& v : t->scr) for (Level& L : v) free_level(dom, L);
@@ -1110,9 +1227,16 @@ static cudaError_t ms_reverse_op(lbm_domain* dom, TapeState* t, const MsOp& o, c
   a.mu = t->mu;
   a.sw = t->mu + 9 * N;
   a.sg = t->mu + 18 * N;
+  a.side = t->side;
   const bool open = o.b != 0 || !dom->desc.periodic[0] || !dom->desc.periodic[1] || !dom->desc.periodic[2];
   const dim3 blk(128, 1, 1), grd((B.nx + 127) / 128, B.ny, B.nz);
   launch_pass_a(a, 3, open, grd, blk, s, true);
+  if (open) {
+    const int px = a.fwd.per[0], py = a.fwd.per[1], pz = a.fwd.per[2];
+    const int per3[3] = {px, py, pz};
+    const int fg = (int)std::max<size_t>(1, std::min<size_t>((open_face_threads(B.nx, B.ny, B.nz, per3) + 255) / 256, 4096));
+    k_face_gather<<<fg, 256, 0, s>>>(lin.f, t->side, B.nx, B.ny, B.nz, px, py, pz);
+  }
   k_adj_b<true><<<grd, blk, 0, s>>>(a);
   k_zero_stepped<<<g, 256, 0, s>>>(lout, B.flags, N);
   return cudaGetLastError();
@@ -1162,7 +1286,12 @@ static lbm_status adjoint_multiblock(lbm_domain* dom, int n_steps, const float* 
       if (!t->grad[b]) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
     }
     t->mu = static_cast<float*>(dom->dev_alloc(nmax * 19 * sizeof(float)));   // mu, sw, sg
-    if (!t->mu) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+    size_t side = 0;
+    for (const Block& B : dom->blocks) side = std::max(side, face_side_floats(B.nx, B.ny, B.nz));
+    t->side = static_cast<float*>(dom->dev_alloc(side * sizeof(float)));
+    if (!t->mu || !t->side) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+    cudaError_t e = cudaMemsetAsync(t->side, 0, side * sizeof(float), s);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint buffers");
   }
   const int seg_len = std::min(t->every, std::max(1, n_steps));
   while ((int)t->snap.size() < seg_len) {
@@ -1274,6 +1403,13 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
   }
   if (!t->mu) t->mu = static_cast<float*>(dom->dev_alloc(N * 19 * sizeof(float)));   // mu, sw, sg
   if (!t->mu) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+  if (!t->side) {
+    const size_t side = face_side_floats(B.nx, B.ny, B.nz);
+    t->side = static_cast<float*>(dom->dev_alloc(side * sizeof(float)));
+    if (!t->side) return dom->fail(LBM_ERR_OOM, "adjoint buffers");
+    cudaError_t e = cudaMemsetAsync(t->side, 0, side * sizeof(float), s);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint buffers");
+  }
   const int seg_len = std::min(t->every, std::max(1, n_steps));
   while ((int)t->seg.size() < seg_len) {
     Level L;
@@ -1299,7 +1435,8 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
 
   const int n_seg = (n_steps + t->every - 1) / t->every;
   const bool open_faces = !dom->desc.periodic[0] || !dom->desc.periodic[1] || !dom->desc.periodic[2];
-  const int zgrid = (int)std::min<size_t>((N + 255) / 256, 16384);
+  const int per3[3] = {dom->desc.periodic[0], dom->desc.periodic[1], dom->desc.periodic[2]};
+  const int zgrid = (int)std::max<size_t>(1, std::min<size_t>((open_face_threads(B.nx, B.ny, B.nz, per3) + 255) / 256, 4096));
   const dim3 blk(128, 1, 1);
   const dim3 grd((B.nx + 127) / 128, B.ny, B.nz);
   for (int sg = n_seg - 1; sg >= 0; --sg) {
@@ -1324,6 +1461,7 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
       a.mu = t->mu;
       a.sw = t->mu + 9 * N;
       a.sg = t->mu + 18 * N;
+      a.side = t->side;
       if (t->pass_a_minb == 0) {
         // time both register bounds on this step's inputs (pass A only writes lam_out, mu and
         // the inflow nodes' ups_out, which the launches below rewrite), keep the faster
@@ -1346,10 +1484,14 @@ extern "C" lbm_status lbm_adjoint_step(lbm_domain* dom, int32_t n_steps, const f
         if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint tuning");
         t->pass_a_minb = m4 < m3 ? 4 : 3;
       }
-      if (open_faces)   // open-face slots accumulate; the tuning launches above also wrote them
+      // (the tuning launches store the same values pass A stores below, side entries included)
+      if (open_faces)
         k_zero_face_slots<<<zgrid, 256, 0, s>>>(a.lam_out, B.nx, B.ny, B.nz, dom->desc.periodic[0],
                                                 dom->desc.periodic[1], dom->desc.periodic[2]);
       launch_pass_a(a, t->pass_a_minb, open_faces, grd, blk, s);
+      if (open_faces)
+        k_face_gather<<<zgrid, 256, 0, s>>>(a.lam_out, t->side, B.nx, B.ny, B.nz, dom->desc.periodic[0],
+                                            dom->desc.periodic[1], dom->desc.periodic[2]);
       k_adj_b<false><<<grd, blk, 0, s>>>(a);
       e = cudaGetLastError();
       if (e != cudaSuccess) return dom->cuda_fail(e, "adjoint step");
