@@ -647,8 +647,9 @@ def run_ours(args):
         if h > 1.0:                   # far field: aligned step, overlap and boundary maps
             launches_per_step += 3
             continue
-        integer = abs(1.0 / h - round(1.0 / h)) < 1e-9 and abs(subs[i] * h - 1.0) < 1e-9
-        launches_per_step += 2 * subs[i] + (0 if integer else 1) + 1 + i  # post: i coarser
+        # ghost layer at t_n, the first sub-step, the gather-and-blend ghost layer after it,
+        # then a ghost layer and a sub-step per later sub-step; post-maps into i coarser blocks
+        launches_per_step += 2 * subs[i] + 1 + i
     K, W = args.steps, args.warmup
     if len(sc.blocks) > 1:
         # multi-block steps replay CUDA graphs captured per level-rotation state: time a

@@ -29,7 +29,11 @@ namespace lbm {
 //      16, when mixing two time levels) gathered loads of one population, into shared memory;
 //   2. one thread per entry: moments, K_hat rescale, back to populations (Sec. 3.2);
 //   3. one thread per (entry, population) pair: the stores.
-// MODE 0: source level lo only; 1: level hi only; 2: (1 - theta) lo + theta hi.
+// MODE 0: source level lo only; 1: level hi only; 2: (1 - theta) lo + theta hi.  Ghost layers
+// of refined blocks also keep the normalised trilinear interpolant of the gathered level in
+// a.ghost_store (GHOST_PLANES planes of a.n floats, see k_ghost_finish): MODE 5 maps level lo
+// (the ghost layer at t_n), MODE 4 maps level hi blended with the stored interpolant of the
+// earlier level, a.ghost_blend, at weight theta (the ghost layer after the first sub-step).
 // Entry of destination node e of a whole block: the source cell containing the node's
 // position and the fractions inside it, in the same double-precision steps as the host
 // tables (cell_of), so both give identical entries.
@@ -54,6 +58,48 @@ __device__ __forceinline__ MapEntry geometric_entry(const MapArgs& a, uint32_t e
   m.src = (uint32_t)(((size_t)i0[2] * a.sny + i0[1]) * a.snx + i0[0]);
   m.tx = t[0]; m.ty = t[1]; m.tz = t[2];
   return m;
+}
+
+// K_hat rescale of interpolated shifted populations (Sec. 3.2): K_hat differs from 1 only on
+// moments 4..8 (the shear and deviatoric second moments), so the mapping adds to the
+// populations the inverse transform of (K_hat - 1) times their non-equilibrium deviatoric
+// second central moments: the same linear map as relaxing every central moment with keep
+// factor K_hat on moments 4..8 and 1 elsewhere, without transforming the 21 moments it leaves
+// unchanged.  acc holds the populations on entry (it is overwritten), dk receives the
+// correction to add to them and u the velocity of the interpolated populations.
+__device__ __forceinline__ void khat_delta(float (&acc)[27], float khat, float (&dk)[27],
+                                           float (&u)[3]) {
+  raw_moments(acc);
+  const float drho = acc[kap(0, 0, 0)];
+  const float inv = 1.0f / (1.0f + drho);
+  const float X = acc[kap(1, 0, 0)] * inv, Y = acc[kap(0, 1, 0)] * inv,
+              Z = acc[kap(0, 0, 1)] * inv;
+  // second central moments of the shifted populations about u, from the raw ones
+  const float R0 = drho, Rx = acc[kap(1, 0, 0)], Ry = acc[kap(0, 1, 0)], Rz = acc[kap(0, 0, 1)];
+  const float kxx = acc[kap(2, 0, 0)] + X * fmaf(X, R0, -2.0f * Rx);
+  const float kyy = acc[kap(0, 2, 0)] + Y * fmaf(Y, R0, -2.0f * Ry);
+  const float kzz = acc[kap(0, 0, 2)] + Z * fmaf(Z, R0, -2.0f * Rz);
+  const float kxy = acc[kap(1, 1, 0)] - X * Ry - Y * Rx + X * Y * R0;
+  const float kxz = acc[kap(1, 0, 1)] - X * Rz - Z * Rx + X * Z * R0;
+  const float kyz = acc[kap(0, 1, 1)] - Y * Rz - Z * Ry + Y * Z * R0;
+  // non-equilibrium parts (equilibrium offsets as in relax_to_equilibrium) scaled by K - 1
+  const float km1 = khat - 1.0f;
+  const float dr3 = drho * (1.0f / 3.0f);
+  const float A = kxx - (dr3 - X * X), B = kyy - (dr3 - Y * Y), Cc = kzz - (dr3 - Z * Z);
+#pragma unroll
+  for (int k = 0; k < 27; ++k) dk[k] = 0.0f;
+  dk[kap(1, 1, 0)] = km1 * (kxy + X * Y);
+  dk[kap(1, 0, 1)] = km1 * (kxz + X * Z);
+  dk[kap(0, 1, 1)] = km1 * (kyz + Y * Z);
+  dk[kap(2, 0, 0)] = km1 * (1.0f / 3.0f) * (2.0f * A - B - Cc);
+  dk[kap(0, 2, 0)] = km1 * (1.0f / 3.0f) * (2.0f * B - A - Cc);
+  dk[kap(0, 0, 2)] = km1 * (1.0f / 3.0f) * (2.0f * Cc - A - B);
+  inv_axis<9>(dk, Z);
+  inv_axis<3>(dk, Y);
+  inv_axis<1>(dk, X);
+  u[0] = X;
+  u[1] = Y;
+  u[2] = Z;
 }
 
 constexpr int MAP_THREADS = 128;
@@ -108,9 +154,9 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
     sinv[t] = inv;
   }
   __syncthreads();
-  const T* __restrict__ lo = static_cast<const T*>(MODE == 1 ? a.f_hi : a.f_lo);
+  const T* __restrict__ lo = static_cast<const T*>(MODE == 1 || MODE == 4 ? a.f_hi : a.f_lo);
   const T* __restrict__ hi = static_cast<const T*>(a.f_hi);
-  const float* __restrict__ clo = MODE == 1 ? a.c_hi : a.c_lo;
+  const float* __restrict__ clo = MODE == 1 || MODE == 4 ? a.c_hi : a.c_lo;
   const float th = a.theta;
   // every (entry, population) pair of this thread has entry d = lane: corners read once, and
   // the unrolled pairs issue all their loads before the first sum is needed.  A corner of
@@ -157,68 +203,127 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapArgs a) {
     vals[i] = v;
   }
   const float inv_d = sinv[d] > 0.0f ? sinv[d] : 0.0f;     // rest state: all zero
+  if constexpr (MODE >= 4) {
+    float* S = a.ghost_store;
+    const size_t n = (size_t)a.n;
+    if (d < nloc) {
 #pragma unroll
-  for (int i = 0; i < PAIRS; ++i) sv[d * MAP_LD + t / MAP_D + i * KSTEP] = vals[i] * inv_d;
-  __syncthreads();
-  if (t < MAP_D && sinv[t] < 0.0f) {   // rest state: shifted populations, u and scalar 0
-    su[0][t] = su[1][t] = su[2][t] = 0.0f;
+      for (int i = 0; i < PAIRS; ++i) {
+        const int k = t / MAP_D + i * KSTEP;
+        if (k < 28) S[(size_t)k * n + e0 + d] = vals[i] * inv_d;
+      }
+    }
+    if (t < nloc) S[(size_t)28 * n + e0 + t] = sinv[t] > 0.0f ? 1.0f : (sinv[t] < 0.0f ? -1.0f : 0.0f);
   }
-  if (t < MAP_D && sinv[t] > 0.0f) {
-    // K_hat differs from 1 only on moments 4..8 (the shear and deviatoric second moments),
-    // so the mapping adds to the interpolated populations the inverse transform of
-    // (K_hat - 1) times their non-equilibrium deviatoric second central moments: the same
-    // linear map as relaxing every central moment with keep factor K_hat on moments 4..8
-    // and 1 elsewhere, without transforming the 21 moments it leaves unchanged.
+  {
+#pragma unroll
+    for (int i = 0; i < PAIRS; ++i) {
+      float v = vals[i] * inv_d;
+      if constexpr (MODE == 4) {   // (1 - theta) earlier interpolant + theta this one
+        const int k = t / MAP_D + i * KSTEP;
+        if (k < 28 && d < nloc) {
+          const float vlo = a.ghost_blend[(size_t)k * a.n + e0 + d];
+          v = fmaf(th, v - vlo, vlo);
+        }
+      }
+      sv[d * MAP_LD + t / MAP_D + i * KSTEP] = v;
+    }
+    __syncthreads();
+    if (t < MAP_D && sinv[t] < 0.0f) {   // rest state: shifted populations, u and scalar 0
+      su[0][t] = su[1][t] = su[2][t] = 0.0f;
+    }
+    if (t < MAP_D && sinv[t] > 0.0f) {
+      float acc[27], dk[27], u[3];
+#pragma unroll
+      for (int k = 0; k < 27; ++k) acc[k] = sv[t * MAP_LD + k];
+      khat_delta(acc, a.khat, dk, u);
+#pragma unroll
+      for (int k = 0; k < 27; ++k) sv[t * MAP_LD + k] += dk[k];
+      su[0][t] = u[0];
+      su[1][t] = u[1];
+      su[2][t] = u[2];
+    }
+    __syncthreads();
+    T* out = static_cast<T*>(a.f_dst);
+    const size_t dN = a.dN;
+    if (sinv[d] == 0.0f) return;
+    const uint32_t dst = sdst[d];
+#pragma unroll
+    for (int i = 0; i < (31 + KSTEP - 1) / KSTEP; ++i) {
+      const int k = t / MAP_D + i * KSTEP;
+      if (k < 27) store_pop(out + (size_t)k * dN + dst, sv[d * MAP_LD + k]);
+      else if (k < 30) a.u_dst[(size_t)(k - 27) * dN + dst] = su[k - 27][d];
+      else if (k == 30) a.c_dst[dst] = sv[d * MAP_LD + 27];
+    }
+  }
+}
+
+// A refined block's ghost layer at t_n + theta dt_0 from the trilinear interpolants of its
+// source at t_n (slo) and at t_n + dt_0 (shi), kept by k_map<MODE 5 / 4> once per source
+// level and reference step: MODE 0 takes slo, 1 shi, 2 (1 - theta) slo + theta shi (the trilinear
+// map is linear, so this equals interpolating the time-blended source), then the K_hat rescale
+// (Sec. 3.2).  Buffer layout: planes 0..26 the shifted populations, 27 the scalar, 28 the
+// entry's status (1 mapped, -1 every corner an obstacle: rest state, 0 destination left
+// alone), each plane a.n floats in table order.  One thread per entry.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_ghost_finish(const MapEntry* __restrict__ table, int n,
+                                                      const float* __restrict__ slo,
+                                                      const float* __restrict__ shi, float theta,
+                                                      float khat, float* __restrict__ f_dst,
+                                                      float* __restrict__ u_dst,
+                                                      float* __restrict__ c_dst, size_t dN) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const size_t nn = (size_t)n;
+  const float* __restrict__ s0 = MODE == 1 ? shi : slo;
+  const float status = s0[28 * nn + e];
+  if (status == 0.0f) return;
+  const uint32_t dst = table[e].dst;
+  // the blended interpolant of plane k (read again for the stores: L1 / L2 hits)
+  auto value = [&](int k) {
+    const float lo = s0[(size_t)k * nn + e];
+    return MODE == 2 ? fmaf(theta, shi[(size_t)k * nn + e] - lo, lo) : lo;
+  };
+  float dk[27], u[3] = {0.0f, 0.0f, 0.0f}, c = 0.0f;
+  if (status > 0.0f) {
     float acc[27];
 #pragma unroll
-    for (int k = 0; k < 27; ++k) acc[k] = sv[t * MAP_LD + k];
-    raw_moments(acc);
-    const float drho = acc[kap(0, 0, 0)];
-    const float inv = 1.0f / (1.0f + drho);
-    const float X = acc[kap(1, 0, 0)] * inv, Y = acc[kap(0, 1, 0)] * inv,
-                Z = acc[kap(0, 0, 1)] * inv;
-    // second central moments of the shifted populations about u, from the raw ones
-    const float R0 = drho, Rx = acc[kap(1, 0, 0)], Ry = acc[kap(0, 1, 0)], Rz = acc[kap(0, 0, 1)];
-    const float kxx = acc[kap(2, 0, 0)] + X * fmaf(X, R0, -2.0f * Rx);
-    const float kyy = acc[kap(0, 2, 0)] + Y * fmaf(Y, R0, -2.0f * Ry);
-    const float kzz = acc[kap(0, 0, 2)] + Z * fmaf(Z, R0, -2.0f * Rz);
-    const float kxy = acc[kap(1, 1, 0)] - X * Ry - Y * Rx + X * Y * R0;
-    const float kxz = acc[kap(1, 0, 1)] - X * Rz - Z * Rx + X * Z * R0;
-    const float kyz = acc[kap(0, 1, 1)] - Y * Rz - Z * Ry + Y * Z * R0;
-    // non-equilibrium parts (equilibrium offsets as in relax_to_equilibrium) scaled by K - 1
-    const float km1 = a.khat - 1.0f;
-    const float dr3 = drho * (1.0f / 3.0f);
-    const float A = kxx - (dr3 - X * X), B = kyy - (dr3 - Y * Y), Cc = kzz - (dr3 - Z * Z);
-    float dk[27];
-#pragma unroll
-    for (int k = 0; k < 27; ++k) dk[k] = 0.0f;
-    dk[kap(1, 1, 0)] = km1 * (kxy + X * Y);
-    dk[kap(1, 0, 1)] = km1 * (kxz + X * Z);
-    dk[kap(0, 1, 1)] = km1 * (kyz + Y * Z);
-    dk[kap(2, 0, 0)] = km1 * (1.0f / 3.0f) * (2.0f * A - B - Cc);
-    dk[kap(0, 2, 0)] = km1 * (1.0f / 3.0f) * (2.0f * B - A - Cc);
-    dk[kap(0, 0, 2)] = km1 * (1.0f / 3.0f) * (2.0f * Cc - A - B);
-    inv_axis<9>(dk, Z);
-    inv_axis<3>(dk, Y);
-    inv_axis<1>(dk, X);
-#pragma unroll
-    for (int k = 0; k < 27; ++k) sv[t * MAP_LD + k] += dk[k];
-    su[0][t] = X;
-    su[1][t] = Y;
-    su[2][t] = Z;
+    for (int k = 0; k < 27; ++k) acc[k] = value(k);
+    c = value(27);
+    khat_delta(acc, khat, dk, u);
   }
-  __syncthreads();
-  T* out = static_cast<T*>(a.f_dst);
-  const size_t dN = a.dN;
-  if (sinv[d] == 0.0f) return;
-  const uint32_t dst = sdst[d];
 #pragma unroll
-  for (int i = 0; i < (31 + KSTEP - 1) / KSTEP; ++i) {
-    const int k = t / MAP_D + i * KSTEP;
-    if (k < 27) store_pop(out + (size_t)k * dN + dst, sv[d * MAP_LD + k]);
-    else if (k < 30) a.u_dst[(size_t)(k - 27) * dN + dst] = su[k - 27][d];
-    else if (k == 30) a.c_dst[dst] = sv[d * MAP_LD + 27];
+  for (int k = 0; k < 27; ++k) f_dst[(size_t)k * dN + dst] = status > 0.0f ? value(k) + dk[k] : 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u_dst[(size_t)a * dN + dst] = u[a];
+  c_dst[dst] = c;
+}
+
+cudaError_t launch_ghost_map(const MapArgs& a, bool first, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const bool big = a.n >= 152 * 8 * 128;
+  if (first) {
+    if (big) k_map<float, 5, 128><<<(a.n + 127) / 128, MAP_THREADS, 0, s>>>(a);
+    else k_map<float, 5, 32><<<(a.n + 31) / 32, MAP_THREADS, 0, s>>>(a);
+  } else {
+    if (big) k_map<float, 4, 128><<<(a.n + 127) / 128, MAP_THREADS, 0, s>>>(a);
+    else k_map<float, 4, 32><<<(a.n + 31) / 32, MAP_THREADS, 0, s>>>(a);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ghost_finish(const MapEntry* table, int n, const float* slo, const float* shi,
+                                float theta, float khat, float* f_dst, float* u_dst,
+                                float* c_dst, size_t dN, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (n + 127) / 128;
+  if (theta <= 0.0f)
+    k_ghost_finish<0><<<grid, 128, 0, s>>>(table, n, slo, shi, theta, khat, f_dst, u_dst, c_dst, dN);
+  else if (theta >= 1.0f)
+    k_ghost_finish<1><<<grid, 128, 0, s>>>(table, n, slo, shi, theta, khat, f_dst, u_dst, c_dst, dN);
+  else
+    k_ghost_finish<2><<<grid, 128, 0, s>>>(table, n, slo, shi, theta, khat, f_dst, u_dst, c_dst, dN);
+  return cudaGetLastError();
 }
 
 template <typename T, int D>
@@ -357,6 +462,10 @@ static void release_block(lbm_domain* dom, Block& B) {
   dom->dev_free(B.prior.d);
   B.prior.d = nullptr;
   B.prior.n = 0;
+  for (float*& g : B.gs) {
+    dom->dev_free(g);
+    g = nullptr;
+  }
   for (MapTable& t : B.post) dom->dev_free(t.d);
   B.post.clear();
   dom->dev_free(B.far_in.d);
@@ -585,6 +694,10 @@ extern "C" lbm_status lbm_add_scale_block(lbm_domain* dom, const double origin[3
     NB.prior.khat = (float)khat(P, NB);
     st = upload_table(dom, tab, &NB.prior);
     if (st != LBM_OK) return abandon(st);
+    for (float*& g : NB.gs) {
+      g = static_cast<float*>(dom->dev_alloc((size_t)GHOST_PLANES * tab.size() * sizeof(float)));
+      if (!g) return abandon(dom->fail(LBM_ERR_OOM, "ghost-layer interpolant buffers"));
+    }
   }
   // post tables: nodes of every coarser block inside the new block's interior span
   for (int k = 0; k < id; ++k) {
@@ -628,8 +741,16 @@ extern "C" lbm_status lbm_remove_scale_block(lbm_domain* dom, int32_t block_id) 
   return LBM_OK;
 }
 
-// Prior-mapping of block b's ghost layer at time t_n + theta dt_0 into level `dst_level`.
-static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& saved, float theta,
+// Prior-mapping of block b's ghost layer (Sec. 3.2, Algorithm 1).  The ghost layer at
+// t_n + theta dt_0 is the K_hat-rescaled trilinear interpolant of the parent blended linearly
+// in time between its levels at t_n and t_n + dt_0; the trilinear part is linear, so it is
+// gathered once per parent level and reference step, and kept in the block's interpolant
+// buffers (0 = t_n, 1 = t_n + dt_0).  ghost_map gathers a level and writes a ghost layer in
+// the same launch: first = true the parent's level `src_level` at t_n (ghost layer at
+// theta = 0 into `dst_level`), first = false its level at t_n + dt_0, blended with buffer 0
+// at `theta` (the ghost layer after the first sub-step).  Every later ghost layer of the step
+// only blends the two buffers and rescales (ghost_finish).
+static cudaError_t ghost_map(lbm_domain* dom, int b, bool first, int src_level, float theta,
                              int dst_level, cudaStream_t stream) {
   Block& B = dom->blocks[b];
   const Block& P = dom->blocks[B.prior.src];
@@ -637,11 +758,9 @@ static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& sav
   a.rest_if_empty = 1;           // scale boundary
   a.table = B.prior.d;
   a.n = B.prior.n;
-  a.f_lo = P.lv[saved[B.prior.src]].f;
-  a.c_lo = P.lv[saved[B.prior.src]].c;
-  a.f_hi = P.lv[P.cur].f;
-  a.c_hi = P.lv[P.cur].c;
-  a.theta = theta;
+  a.f_lo = a.f_hi = P.lv[src_level].f;
+  a.c_lo = a.c_hi = P.lv[src_level].c;
+  a.theta = first ? 0.0f : theta;
   a.src_flags = P.flags;
   a.snx = P.nx; a.sny = P.ny; a.sN = P.N;
   a.f_dst = B.lv[dst_level].f;
@@ -651,7 +770,17 @@ static cudaError_t prior_map(lbm_domain* dom, int b, const std::vector<int>& sav
   a.skip_mask = F_SOLID | F_OBST_WALL;   // obstacle voxels keep their own state
   a.dN = B.N;
   a.khat = B.prior.khat;
-  return launch_map(a, dom->desc.storage, stream);
+  a.ghost_store = B.gs[first ? 0 : 1];
+  a.ghost_blend = B.gs[0];
+  return launch_ghost_map(a, first, stream);
+}
+
+static cudaError_t ghost_finish(lbm_domain* dom, int b, float theta, int dst_level,
+                                cudaStream_t stream) {
+  Block& B = dom->blocks[b];
+  const Level& D = B.lv[dst_level];
+  return launch_ghost_finish(B.prior.d, B.prior.n, B.gs[0], B.gs[1], theta, B.prior.khat,
+                             static_cast<float*>(D.f), D.u, D.c, B.N, stream);
 }
 
 static cudaError_t post_map(lbm_domain* dom, int b, const MapTable& t, cudaStream_t stream) {
@@ -728,7 +857,8 @@ lbm_status multiscale_step(lbm_domain* dom) {
     Block& B = dom->blocks[b];
     if (B.far) continue;
     const int L = saved[b], A = (L + 1) % 3;
-    e = prior_map(dom, b, saved, 0.0f, L, early);
+    e = ghost_map(dom, b, true, saved[B.prior.src], 0.0f, L, early);
+    if (e == cudaSuccess) e = cudaEventRecord(dom->event(10 + 2 * nb + b), early);
     if (e == cudaSuccess) e = launch_step(dom->view(b, L, A), dom->desc.storage, B.bx, B.by, early, B.minb);
     if (e == cudaSuccess) e = cudaEventRecord(dom->event(10 + nb + b), early);
   }
@@ -782,19 +912,31 @@ lbm_status multiscale_step(lbm_domain* dom) {
       e = cudaStreamWaitEvent(s, dom->event(10 + B.prior.src), 0);
       if (e != cudaSuccess) return dom->cuda_fail(e, "post-mapping join");
     }
+    // the early phase's interpolant at t_n is needed from the first ghost layer on, its first
+    // sub-step only by the second one
+    e = cudaStreamWaitEvent(s, dom->event(10 + 2 * nb + b), 0);
+    if (e != cudaSuccess) return dom->cuda_fail(e, "early-phase join");
     for (int j = 1; j <= B.substeps; ++j) {
       const int out = (j == 1) ? A : (cur == A ? Bv : A);
-      // fork: ghost layer of `out` for the next sub-step (or at t_n + dt_0 after the last)
+      // ghost layer of `out` for the next sub-step (or at t_n + dt_0 after the last): forked,
+      // concurrent with this sub-step's collide-stream (disjoint nodes), except after the
+      // first sub-step, which ran in the early phase: there the source's new level is
+      // gathered (once for every later ghost layer of the step) and blended
       const float theta = j < B.substeps ? (float)(j * B.h) : 1.0f;
+      if (j == 1) {
+        e = ghost_map(dom, b, false, dom->blocks[B.prior.src].cur, theta, out, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, dom->event(10 + nb + b), 0);
+        if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
+        cur = out;
+        continue;
+      }
       e = cudaEventRecord(dom->event(0), s);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, dom->event(0), 0);
-      if (e == cudaSuccess) e = prior_map(dom, b, saved, theta, out, aux);
+      if (e == cudaSuccess) e = ghost_finish(dom, b, theta, out, aux);
       if (e == cudaSuccess) e = cudaEventRecord(dom->event(1), aux);
       if (e != cudaSuccess) return dom->cuda_fail(e, "prior-mapping");
       BlockView v = dom->view(b, cur, out);
-      if (j == 1) {                  // ran in the early phase: join it
-        e = cudaStreamWaitEvent(s, dom->event(10 + nb + b), 0);
-      } else if (j == B.substeps && !exact) {
+      if (j == B.substeps && !exact) {
         const double t1 = (B.substeps - 1) * B.h, t2 = B.substeps * B.h, T = 1.0;
         v.f_al0 = B.lv[L].f;
         v.c_al0 = B.lv[L].c;
@@ -896,7 +1038,7 @@ cudaError_t block_subcycle(lbm_domain* dom, int b, cudaStream_t s) {
   const int L = saved[b];
   const int A = (L + 1) % 3, Bv = (L + 2) % 3;
   const bool exact = B.integer_ratio && std::fabs(B.substeps * B.h - 1.0) < 1e-9;
-  cudaError_t e = prior_map(dom, b, saved, 0.0f, L, s);
+  cudaError_t e = ghost_map(dom, b, true, saved[B.prior.src], 0.0f, L, s);
   int cur = L;
   for (int j = 1; j <= B.substeps && e == cudaSuccess; ++j) {
     const int out = (j == 1) ? A : (cur == A ? Bv : A);
@@ -913,7 +1055,9 @@ cudaError_t block_subcycle(lbm_domain* dom, int b, cudaStream_t s) {
       e = launch_step(v, dom->desc.storage, B.bx, B.by, s, B.minb);
     }
     const float theta = j < B.substeps ? (float)(j * B.h) : 1.0f;
-    if (e == cudaSuccess) e = prior_map(dom, b, saved, theta, out, s);
+    if (e == cudaSuccess)
+      e = j == 1 ? ghost_map(dom, b, false, dom->blocks[B.prior.src].cur, theta, out, s)
+                 : ghost_finish(dom, b, theta, out, s);
     cur = out;
   }
   B.cur = cur;

@@ -73,6 +73,11 @@ struct MapArgs {
   double o_src[3], h_src;
   int dnx, dny;
   int snz;
+  // ghost layers of refined blocks (k_map modes 4 and 5): the trilinear interpolant of the
+  // gathered source level is also stored here (GHOST_PLANES planes of n floats), and mode 4
+  // blends it in time with the interpolant `ghost_blend` of the source's earlier level
+  float* ghost_store;
+  const float* ghost_blend;
 };
 
 // One tile of the batched work list: a BX x BY patch of one z-plane of one simulation.
@@ -160,6 +165,14 @@ cudaError_t launch_step_reduce(const BlockView& v, int storage, int bx, int by, 
 
 // ---- coupling.cu
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s);
+// ghost layer of a refined block that also keeps the source's trilinear interpolant
+// (a.ghost_store): first = true maps level a.f_lo at t_n; first = false maps level a.f_hi
+// blended at a.theta with the interpolant a.ghost_blend of the earlier level (FP32)
+cudaError_t launch_ghost_map(const MapArgs& a, bool first, cudaStream_t s);
+// ghost layer at t_n + theta dt_0 from the two interpolant buffers, K_hat rescaled
+cudaError_t launch_ghost_finish(const MapEntry* table, int n, const float* slo, const float* shi,
+                                float theta, float khat, float* f_dst, float* u_dst,
+                                float* c_dst, size_t dN, cudaStream_t s);
 cudaError_t launch_set_ghost_layer(uint8_t* flags, int nx, int ny, int nz, cudaStream_t s);
 // outer layer of a block surrounded by a far-field block: GHOST on (except obstacle and
 // inflow nodes, which keep their own update) or off

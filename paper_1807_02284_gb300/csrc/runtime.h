@@ -24,8 +24,14 @@ struct MapTable {
   float khat = 1.0f;       // K_hat factor of moments 4..8 for src -> dst
 };
 
+// Planes of a ghost-layer interpolant buffer: 27 shifted populations, the scalar, the status.
+constexpr int GHOST_PLANES = 29;
+
 struct Block {
   MapTable prior;                 // ghost layer <- parent (refined blocks)
+  // trilinear interpolants of the ghost layer from the parent at t_n (0) and t_n + dt_0 (1),
+  // GHOST_PLANES x prior.n floats each (refined blocks)
+  float* gs[2] = {nullptr, nullptr};
   std::vector<MapTable> post;     // every coarser block <- this block's interior
   int nx = 0, ny = 0, nz = 0;
   size_t N = 0;

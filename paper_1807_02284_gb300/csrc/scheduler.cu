@@ -255,7 +255,7 @@ lbm_status lbm_domain::advance(int n) {
     cudaStream_t a = nullptr;
     lbm_status st = aux(&a);
     if (st != LBM_OK) return st;
-    if (!event(10 + 2 * (int)blocks.size())) return fail(LBM_ERR_CUDA, "cudaEventCreate");
+    if (!event(10 + 3 * (int)blocks.size())) return fail(LBM_ERR_CUDA, "cudaEventCreate");
     if (!post_stream((int)blocks.size())) return fail(LBM_ERR_CUDA, "cudaStreamCreate");
   }
   if (tape != nullptr) return advance_direct(n);
