@@ -80,8 +80,10 @@ enum {
                         continuous-scale mappings treat every obstacle voxel, surface or
                         inner, as an obstacle (a dropped interpolation corner, a destination
                         left alone).  Replaces the previous walls.
-                        INVALID_ARG for a wall on a periodic axis; UNSUPPORTED with
-                        far-field blocks.  With byte 6 set, blocks started from their parent
+                        INVALID_ARG for a wall on a periodic axis; UNSUPPORTED for wall
+                        faces (bytes 0-5) with far-field blocks; byte 6 alone combines with
+                        them (far-field blocks keep halfway bounce-back on their own obstacle
+                        voxels).  With byte 6 set, blocks started from their parent
                         (lbm_init_block_from_parent, dynamic and static scale construction)
                         and the adjoint of a domain with refined blocks are UNSUPPORTED. */
 };
@@ -177,7 +179,8 @@ lbm_status lbm_destroy_domain(lbm_domain* dom);
    inside the contained block's interior are mapped from that block, and the contained
    block's outer layer becomes its scale boundary, mapped from the far-field block (obstacle
    and inflow nodes keep their own update); the outermost far-field block has open faces.
-   Needs block 0 without periodic faces (UNSUPPORTED otherwise).
+   Needs block 0 without periodic faces and without wall faces (UNSUPPORTED otherwise);
+   obstacle-surface walls (LBM_BC_WALLS byte 6) are allowed.
    UNSUPPORTED for FP16 storage; STATE while an adjoint tape is recording; OOM / CUDA when a
    buffer or table cannot be created, in which case the domain is left exactly as before
    the call. */

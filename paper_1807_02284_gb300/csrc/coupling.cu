@@ -356,7 +356,7 @@ __global__ void k_outer_ghost(uint8_t* flags, int nx, int ny, int nz, int on) {
     const bool edge = x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1;
     if (!edge) continue;
     const uint8_t f = flags[idx];
-    const bool ghost = on && !(f & (F_SOLID | F_INFLOW));
+    const bool ghost = on && !(f & (F_SOLID | F_OBST_WALL | F_INFLOW));
     flags[idx] = ghost ? (uint8_t)(f | F_GHOST) : (uint8_t)(f & ~F_GHOST);
   }
 }
@@ -545,7 +545,8 @@ static lbm_status add_far_block(lbm_domain* dom, const double origin[3], double 
   for (int a = 0; a < 3; ++a)
     if (dom->desc.periodic[a])
       return dom->fail(LBM_ERR_UNSUPPORTED, "far-field blocks need a reference block without periodic faces");
-  if (dom->walls) return dom->fail(LBM_ERR_UNSUPPORTED, "walls and far-field blocks exclude each other");
+  if (dom->walls & ~WALLS_OBSTACLES)
+    return dom->fail(LBM_ERR_UNSUPPORTED, "wall faces and far-field blocks exclude each other");
   Block F;
   F.nx = dims[0]; F.ny = dims[1]; F.nz = dims[2];
   F.N = (size_t)F.nx * F.ny * F.nz;
@@ -897,7 +898,7 @@ lbm_status multiscale_step(lbm_domain* dom) {
   }
   for (size_t k = far.size(); k-- > 0;) {
     const Block& F = dom->blocks[far[k]];
-    e = far_map(dom, F.far_out, F_SOLID | F_INFLOW, 1, s);
+    e = far_map(dom, F.far_out, F_SOLID | F_OBST_WALL | F_INFLOW, 1, s);
     if (e != cudaSuccess) return dom->cuda_fail(e, "far-field boundary mapping");
   }
   for (size_t bi = 1; bi < dom->blocks.size(); ++bi) {

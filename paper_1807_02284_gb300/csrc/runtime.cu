@@ -334,8 +334,8 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
       }
     if (nbytes >= 7 && m[6]) walls |= WALLS_OBSTACLES;
     for (size_t i = 1; i < dom->blocks.size(); ++i)
-      if (dom->blocks[i].far && walls)
-        return dom->fail(LBM_ERR_UNSUPPORTED, "walls and far-field blocks exclude each other");
+      if (dom->blocks[i].far && (walls & ~WALLS_OBSTACLES))
+        return dom->fail(LBM_ERR_UNSUPPORTED, "wall faces and far-field blocks exclude each other");
     int per[3];
     for (int a = 0; a < 3; ++a) per[a] = dom->desc.periodic[a];
     cudaError_t e = launch_mark_walls(B.flags, B.nx, B.ny, B.nz, walls, dom->stream);
@@ -349,6 +349,7 @@ lbm_status lbm_set_boundary(lbm_domain* dom, int32_t block_id, int32_t kind, con
     for (size_t i = 1; i < dom->blocks.size() && e == cudaSuccess; ++i) {
       Block& R = dom->blocks[i];
       if (!((walls | dom->walls) & WALLS_OBSTACLES)) break;
+      if (R.far) continue;             // far-field blocks keep halfway bounce-back
       e = launch_obstacle_walls(R.flags, R.nx, R.ny, R.nz, zero, (walls & WALLS_OBSTACLES) ? 1 : 0,
                                 dom->stream);
       if (e == cudaSuccess) e = launch_near_solid(R.flags, R.nx, R.ny, R.nz, zero, dom->stream);

@@ -104,3 +104,42 @@ def test_far_block_argument_checks(lib):
         per.add_scale_block((-4.0, -4.0, -4.0), 2.0, (11, 11, 11))
     assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
     per.close()
+
+
+@pytest.mark.parametrize("walls_first", [True, False])
+def test_far_block_with_obstacle_walls(lib, walls_first):
+    """The open-boundary setting of Sec. 4.2.4 / 6.1 with the second-order wall on the
+    obstacle's surface: a far block around s0 whose sphere is a regularized wall (the far
+    block keeps halfway bounce-back for its own obstacle voxels, which s0 overwrites); parity
+    with the oracle for both orders of setting the walls and adding the far block.  Wall
+    faces and far-field blocks still exclude each other."""
+    from paper_1807_02284_gb300 import lbm
+    from oracle import grid
+    sc = _scene()
+    dom = gpu_multiscale(sc)
+    b0 = sc.blocks[0]
+
+    def walls():
+        dom.set_walls((False,) * 6, obstacles=True)
+        dom.init_macro(f32(b0.u0), rho=f32(b0.rho0), c=f32(b0.c0), block=0)
+    ms = coupling.MultiScale.build(sc, obstacle_walls=True)
+    if walls_first:
+        walls()
+        fid, fb = _add_far(dom, ms, b0, 1.5, 6.0, seed=5)
+    else:
+        fid, fb = _add_far(dom, ms, b0, 1.5, 6.0, seed=5)
+        walls()
+    s = grid.surface_voxels(ms.blocks[0].state.flags, ms.blocks[0].params.periodic)
+    fl = dom.read_field(lbm.LBM_FIELD_FLAGS, lbm.LBM_U8, 0).reshape(b0.shape_zyx)
+    assert s.sum() > 0 and np.array_equal((fl & 64) != 0, s.numpy())
+    ffl = dom.read_field(lbm.LBM_FIELD_FLAGS, lbm.LBM_U8, fid).reshape(fb.shape_zyx)
+    assert not (ffl & 64).any()                      # the far block has no wall nodes
+    assert np.array_equal(fl & 8, ms.blocks[0].state.flags.numpy() & 8)
+    for _ in range(4):
+        dom.step(1)
+        ms.step()
+    compare(dom, ms, f"far field + obstacle walls (walls first {walls_first})")
+    with pytest.raises(lbm.LBMError) as ei:
+        dom.set_walls((False, False, False, False, True, False), obstacles=True)
+    assert ei.value.status == lbm.LBM_ERR_UNSUPPORTED
+    dom.close()
