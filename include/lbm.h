@@ -318,6 +318,24 @@ lbm_status lbm_reduce(lbm_domain* dom, int32_t block_id, double out[5]);
    Synchronises; INVALID_ARG for n < 1 or a null out; DIVERGED as lbm_step / lbm_reduce. */
 lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]);
 
+/* lbm_step_reduce without the wait (not in the paper: it lets a caller queue the next step,
+   and that step's inflow upload, before it reads this step's diagnostics, so that the GPU
+   never idles on the host).  Enqueues the same n steps and diagnostics on the domain's
+   stream, followed by a copy of the 5 values (lbm_reduce layout, combined on the device)
+   into out, and returns; *ticket receives this call's number (1, 2, ... per domain).  out
+   is host memory that must stay valid, and unread, until lbm_wait_results(ticket) (or
+   lbm_sync) returns; pinned memory keeps the copy asynchronous, pageable memory makes this
+   call wait for it.  Later calls do not reuse out.  INVALID_ARG for n < 1 or a null out or
+   ticket; DIVERGED when an earlier step recorded divergence; errors of enqueueing as
+   lbm_step. */
+lbm_status lbm_step_reduce_async(lbm_domain* dom, int32_t n, double out[5], int64_t* ticket);
+
+/* Waits until the lbm_step_reduce_async call that returned `ticket`, and every earlier one,
+   has written its out array.  Returns DIVERGED (or TIMEOUT) when the device error word
+   copied with those results says so, as lbm_sync does; INVALID_ARG for a ticket this domain
+   has not issued. */
+lbm_status lbm_wait_results(lbm_domain* dom, int64_t ticket);
+
 /* lbm_reduce of block `block_id` of each of n domains (no counterpart in the paper: the
    read-back of a batch).  Members that share one device, stream and storage are reduced by
    one launch over chunks of all of them, with one read-back and one wait (the same sums in

@@ -41,13 +41,19 @@ __global__ void __launch_bounds__(REDUCE_THREADS, 4) k_reduce(const T* d, const 
 }
 
 // One warp per value: lane l sums partials l, l + 32, ... in order, then a fixed shuffle
-// tree combines the lanes, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(192) k_reduce_final(const double* partials, int n, double* out) {
+// tree combines the lanes, so the result does not depend on scheduling.  out5 (optional)
+// also receives the five diagnostics in the lbm_reduce layout (mass = out[0] + out[1]).
+__global__ void __launch_bounds__(192) k_reduce_final(const double* partials, int n, double* out,
+                                                      double* out5) {
   const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double s = 0;
   for (int b = lane; b < n; b += 32) s += partials[b * 6 + v];
   s = warp_sum(s);
   if (lane == 0) out[v] = s;
+  if (out5 != nullptr) {
+    __syncthreads();
+    if (threadIdx.x < 5) out5[threadIdx.x] = threadIdx.x == 0 ? out[0] + out[1] : out[threadIdx.x + 1];
+  }
 }
 
 // n records of 8 doubles (6 sums + 2 unused), summed in two fixed-order stages so that many
@@ -81,10 +87,11 @@ __global__ void __launch_bounds__(256) k_reduce_records(const double* rec, size_
 }
 
 // `partials` holds 8 n + 6 COL_SLICES doubles: the records, then the stage-1 sums.
-cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaStream_t s) {
+cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaStream_t s,
+                                  double* out5) {
   double* stage = partials + 8 * n;
   k_reduce_records<<<COL_SLICES, 256, 0, s>>>(partials, n, stage);
-  k_reduce_final<<<1, 192, 0, s>>>(stage, COL_SLICES, out);
+  k_reduce_final<<<1, 192, 0, s>>>(stage, COL_SLICES, out, out5);
   return cudaGetLastError();
 }
 
@@ -168,14 +175,14 @@ cudaError_t launch_reduce_items(int storage, const RedItem* items, int n_items,
 }
 
 cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
-                          double* partials, double* out, cudaStream_t s) {
+                          double* partials, double* out, cudaStream_t s, double* out5) {
   const size_t want = (N + REDUCE_THREADS - 1) / REDUCE_THREADS;
   const int ctas = (int)(want < (size_t)REDUCE_CTAS ? (want > 0 ? want : 1) : REDUCE_CTAS);
   if (storage == ST_FP16)
     k_reduce<__half><<<ctas, REDUCE_THREADS, 0, s>>>((const __half*)d, flags, N, partials);
   else
     k_reduce<float><<<ctas, REDUCE_THREADS, 0, s>>>((const float*)d, flags, N, partials);
-  k_reduce_final<<<1, 192, 0, s>>>(partials, ctas, out);
+  k_reduce_final<<<1, 192, 0, s>>>(partials, ctas, out, out5);
   return cudaGetLastError();
 }
 

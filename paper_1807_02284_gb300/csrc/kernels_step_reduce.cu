@@ -55,25 +55,30 @@ size_t step_reduce_ctas(const BlockView& v, int bx, int by) {
   return (size_t)((v.nx + bx - 1) / bx) * ((v.ny + by - 1) / by) * v.nz;
 }
 
-// The register bound of 3 CTAs per SM: at 4 the extra live values of the diagnostics spill.
+// The register bound the step's autotuner chose for the block (the diagnostics add no live
+// values through the collision: both bounds compile without spills).
 template <typename T>
-static void launch_step_reduce_t(const BlockView& v, dim3 grid, dim3 block, double* partials,
-                                 cudaStream_t s) {
-  if (v.walls) k_step_reduce<T, 3, true><<<grid, block, 0, s>>>(v, partials);
-  else k_step_reduce<T, 3, false><<<grid, block, 0, s>>>(v, partials);
+static void launch_step_reduce_t(const BlockView& v, dim3 grid, dim3 block, int minb,
+                                 double* partials, cudaStream_t s) {
+  if (minb >= 4) {
+    if (v.walls) k_step_reduce<T, 4, true><<<grid, block, 0, s>>>(v, partials);
+    else k_step_reduce<T, 4, false><<<grid, block, 0, s>>>(v, partials);
+  } else {
+    if (v.walls) k_step_reduce<T, 3, true><<<grid, block, 0, s>>>(v, partials);
+    else k_step_reduce<T, 3, false><<<grid, block, 0, s>>>(v, partials);
+  }
 }
 
 // 32-bit indexing only (27 N < 2^32): the caller checks fits_32bit_index.
 cudaError_t launch_step_reduce(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
-                               int minb, double* partials, double* out) {
+                               int minb, double* partials, double* out, double* out5) {
   dim3 block(bx, by, 1);
   dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, v.nz);
-  (void)minb;
-  if (storage == ST_FP16) launch_step_reduce_t<__half>(v, grid, block, partials, s);
-  else launch_step_reduce_t<float>(v, grid, block, partials, s);
+  if (storage == ST_FP16) launch_step_reduce_t<__half>(v, grid, block, minb, partials, s);
+  else launch_step_reduce_t<float>(v, grid, block, minb, partials, s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_reduce_columns(partials, step_reduce_ctas(v, bx, by), out, s);
+  return launch_reduce_columns(partials, step_reduce_ctas(v, bx, by), out, s, out5);
 }
 
 }  // namespace lbm

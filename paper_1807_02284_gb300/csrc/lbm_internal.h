@@ -128,8 +128,9 @@ cudaError_t launch_convert(const void* in, int in_f64, void* out, int out_f64, s
 // final six doubles {count, sum drho, sum jx, sum jy, sum jz, sum |j|^2/(2 rho)} into `out`.
 constexpr int REDUCE_CTAS = 608;   // 4 CTAs on each of 152 SMs
 constexpr int REDUCE_THREADS = 256;
+// out: the 6 sums; out5 (optional, device): the 5 diagnostics in the lbm_reduce layout
 cudaError_t launch_reduce(const void* d, int storage, const uint8_t* flags, size_t N,
-                          double* partials, double* out, cudaStream_t s);
+                          double* partials, double* out, cudaStream_t s, double* out5 = nullptr);
 // 27 N < 2^32: every array index of the block fits 32 bits
 bool fits_32bit_index(size_t N);
 // diagnostics of several domains in one launch: chunks of members' nodes
@@ -155,13 +156,14 @@ cudaError_t launch_reduce_item_records(const double* records, const RedMember* m
                                       double* out, cudaStream_t s);
 // the six sums over `n` per-CTA records of 8 doubles (partials[8 i + value]); the buffer
 // holds 8 n + 6 * 128 doubles (the records, then the first stage's sums)
-cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaStream_t s);
+cudaError_t launch_reduce_columns(double* partials, size_t n, double* out, cudaStream_t s,
+                                  double* out5 = nullptr);
 // one collide-stream step of a block (32-bit indexing) that also leaves the diagnostics of
 // the stored state in `out` (same six doubles as launch_reduce); `partials` holds
 // 8 * step_reduce_ctas(v, bx, by) + 6 * 128 doubles
 size_t step_reduce_ctas(const BlockView& v, int bx, int by);
 cudaError_t launch_step_reduce(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
-                               int minb, double* partials, double* out);
+                               int minb, double* partials, double* out, double* out5 = nullptr);
 
 // ---- coupling.cu
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s);

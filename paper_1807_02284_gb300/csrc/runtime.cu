@@ -256,7 +256,9 @@ lbm_status lbm_create_domain(const lbm_domain_desc* desc, lbm_domain** out) {
   *dom->h_err = 0;
   dom->d_err = static_cast<int*>(dom->dev_alloc(64));
   dom->d_partials = static_cast<double*>(dom->dev_alloc(REDUCE_CTAS * 6 * sizeof(double)));
-  dom->d_red = static_cast<double*>(dom->dev_alloc(8 * sizeof(double)));
+  // 8 doubles: reduction sums and other small results; 8 more: the combined diagnostics of
+  // lbm_step_reduce_async
+  dom->d_red = static_cast<double*>(dom->dev_alloc(16 * sizeof(double)));
   if (!dom->d_err || !dom->d_partials || !dom->d_red) {
     g_create_error = "allocation failed"; lbm_destroy_domain(dom); return LBM_ERR_OOM;
   }

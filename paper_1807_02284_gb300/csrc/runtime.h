@@ -84,6 +84,11 @@ struct lbm_domain {
   void* small_dev = nullptr;
   size_t small_bytes = 0;
   cudaEvent_t small_done = nullptr;
+  // lbm_step_reduce_async: one event per ticket slot (ticket t uses slot (t - 1) % 16; a
+  // later ticket's event in the same slot completes after it, so waiting on it is safe)
+  static constexpr int kResultSlots = 16;
+  cudaEvent_t result_ev[kResultSlots] = {};
+  long long results_issued = 0;
   std::string last_error;
   long long steps = 0;
   lbm::TapeState* tape = nullptr;

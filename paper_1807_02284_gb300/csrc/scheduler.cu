@@ -172,6 +172,10 @@ void lbm_domain::release_extras() {
   small_host = nullptr;
   if (small_done) cudaEventDestroy(small_done);
   small_done = nullptr;
+  for (cudaEvent_t& ev : result_ev) {
+    if (ev) cudaEventDestroy(ev);
+    ev = nullptr;
+  }
 }
 
 // Small host arrays (inflow records) go through a pinned bounce buffer so the copy is
@@ -319,17 +323,17 @@ lbm_status lbm_domain::advance(int n) {
 // indexing) also sums the diagnostics of the state it stores, so that reading mass, momentum
 // and energy back after a step costs no second pass over the populations.  Other domains
 // take the n steps and lbm_reduce of block 0.
-lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]) {
-  if (!dom) return LBM_ERR_INVALID_ARG;
-  cudaSetDevice(dom->desc.device);
-  if (n < 1) return dom->fail(LBM_ERR_INVALID_ARG, "lbm_step_reduce needs at least one step");
-  if (!out) return dom->fail(LBM_ERR_INVALID_ARG, "null output");
-  if (*dom->h_err & 1) return dom->fail(LBM_ERR_DIVERGED, "divergence recorded by an earlier step");
+// Enqueues n steps and the diagnostics of block 0's new state: the 6 sums into dom->d_red
+// and, when out5 (device) is given, the 5 combined values.  On a single-block domain with
+// 27 N < 2^32 the last step's own kernel sums them; otherwise a separate reduction follows.
+static lbm_status enqueue_step_reduce(lbm_domain* dom, int32_t n, double* out5) {
   Block& B = dom->blocks[0];
   if (dom->blocks.size() > 1 || !fits_32bit_index(B.N)) {
     lbm_status st = dom->advance(n);
     if (st != LBM_OK) return st;
-    return lbm_reduce(dom, 0, out);
+    const cudaError_t e = launch_reduce(B.lv[B.cur].f, dom->desc.storage, B.flags, B.N,
+                                        dom->d_partials, dom->d_red, dom->stream, out5);
+    return e == cudaSuccess ? LBM_OK : dom->cuda_fail(e, "reduce");
   }
   lbm_status st = dom->advance(n - 1);
   if (st == LBM_OK) st = dom->autotune_tiles(0);
@@ -345,13 +349,24 @@ lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]) {
     if (!dom->d_step_partials) return dom->fail(LBM_ERR_OOM, "step-reduce partials");
     dom->step_partials_n = ctas;
   }
-  cudaError_t e = launch_step_reduce(v, dom->desc.storage, B.bx, B.by, dom->stream, B.minb,
-                                     dom->d_step_partials, dom->d_red);
+  const cudaError_t e = launch_step_reduce(v, dom->desc.storage, B.bx, B.by, dom->stream, B.minb,
+                                           dom->d_step_partials, dom->d_red, out5);
   if (e != cudaSuccess) return dom->cuda_fail(e, "collide-stream launch");
   B.cur = nxt;
   ++dom->steps;
-  e = cudaMemcpyAsync(dom->h_red, dom->d_red, 6 * sizeof(double), cudaMemcpyDeviceToHost,
-                      dom->stream);
+  return LBM_OK;
+}
+
+lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (n < 1) return dom->fail(LBM_ERR_INVALID_ARG, "lbm_step_reduce needs at least one step");
+  if (!out) return dom->fail(LBM_ERR_INVALID_ARG, "null output");
+  if (*dom->h_err & 1) return dom->fail(LBM_ERR_DIVERGED, "divergence recorded by an earlier step");
+  lbm_status st = enqueue_step_reduce(dom, n, nullptr);
+  if (st != LBM_OK) return st;
+  const cudaError_t e = cudaMemcpyAsync(dom->h_red, dom->d_red, 6 * sizeof(double),
+                                        cudaMemcpyDeviceToHost, dom->stream);
   if (e != cudaSuccess) return dom->cuda_fail(e, "reduce read-back");
   st = dom->sync_and_check();
   const double* r = dom->h_red;
@@ -361,4 +376,41 @@ lbm_status lbm_step_reduce(lbm_domain* dom, int32_t n, double out[5]) {
   out[3] = r[4];
   out[4] = r[5];
   return st;
+}
+
+lbm_status lbm_step_reduce_async(lbm_domain* dom, int32_t n, double out[5], int64_t* ticket) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (n < 1) return dom->fail(LBM_ERR_INVALID_ARG, "lbm_step_reduce_async needs at least one step");
+  if (!out || !ticket) return dom->fail(LBM_ERR_INVALID_ARG, "null output or ticket");
+  if (*dom->h_err & 1) return dom->fail(LBM_ERR_DIVERGED, "divergence recorded by an earlier step");
+  const int slot = (int)(dom->results_issued % lbm_domain::kResultSlots);
+  if (!dom->result_ev[slot] &&
+      cudaEventCreateWithFlags(&dom->result_ev[slot], cudaEventDisableTiming) != cudaSuccess) {
+    dom->result_ev[slot] = nullptr;
+    return dom->fail(LBM_ERR_CUDA, "cudaEventCreate");
+  }
+  double* d_out5 = dom->d_red + 8;
+  lbm_status st = enqueue_step_reduce(dom, n, d_out5);
+  if (st != LBM_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(out, d_out5, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  dom->stream);
+  if (e == cudaSuccess) {
+    dom->post_error_probe();
+    e = cudaEventRecord(dom->result_ev[slot], dom->stream);
+  }
+  if (e != cudaSuccess) return dom->cuda_fail(e, "reduce read-back");
+  *ticket = ++dom->results_issued;
+  return LBM_OK;
+}
+
+lbm_status lbm_wait_results(lbm_domain* dom, int64_t ticket) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (ticket < 1 || ticket > dom->results_issued)
+    return dom->fail(LBM_ERR_INVALID_ARG, "not a ticket of lbm_step_reduce_async on this domain");
+  const int slot = (int)((ticket - 1) % lbm_domain::kResultSlots);
+  const cudaError_t e = cudaEventSynchronize(dom->result_ev[slot]);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "cudaEventSynchronize");
+  return dom->error_status();
 }

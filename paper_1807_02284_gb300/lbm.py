@@ -85,6 +85,8 @@ _SIGNATURES = {
     "lbm_write_field": (_I, [_P, _I, _I, _I, _P, C.c_size_t, _I]),
     "lbm_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
     "lbm_step_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
+    "lbm_step_reduce_async": (_I, [_P, _I, _P, C.POINTER(C.c_int64)]),
+    "lbm_wait_results": (_I, [_P, C.c_int64]),
     "lbm_get_block_info": (_I, [_P, _I, C.POINTER(lbm_block_info)]),
     "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
     "lbm_step_batch_reduce": (_I, [C.POINTER(_P), _I, _I, C.POINTER(C.c_double)]),
@@ -429,6 +431,20 @@ class Domain:
         out = (C.c_double * 5)()
         self.check(self.lib.lbm_step_reduce(self.handle, int(n), out))
         return np.array(list(out))
+
+    def step_reduce_async(self, n, out) -> int:
+        """``lbm_step_reduce_async``: enqueues n steps and block 0's diagnostics, to be copied
+        into ``out`` (5 float64 values in host memory, pinned for an asynchronous copy: a
+        numpy array or a CPU torch tensor); returns the ticket for ``wait_results``."""
+        ptr, dev = _ptr(out)
+        if dev or _nbytes(out) < 5 * 8 or str(out.dtype) not in ("float64", "torch.float64"):
+            raise ValueError("out must be 5 float64 values in host memory")
+        t = C.c_int64()
+        self.check(self.lib.lbm_step_reduce_async(self.handle, int(n), C.c_void_p(ptr), C.byref(t)))
+        return t.value
+
+    def wait_results(self, ticket: int):
+        self.check(self.lib.lbm_wait_results(self.handle, int(ticket)))
 
     def set_tape(self, every):
         self.check(self.lib.lbm_set_tape(self.handle, int(every)))

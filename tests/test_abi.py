@@ -71,6 +71,8 @@ def test_library_loads_and_validates_on_host(built):
     assert lib.lbm_sync(None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_destroy_domain(None) == lbm.LBM_OK
     assert lib.lbm_step_reduce(None, 1, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_step_reduce_async(None, 1, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_wait_results(None, 1) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_set_tape(None, 1) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_adjoint_step(None, 1, None, None, None, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_reduce_batch(None, 0, 0, None) == lbm.LBM_ERR_INVALID_ARG

@@ -91,3 +91,48 @@ def test_step_reduce_argument_checks(lib):
     assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
     dom.step_reduce(1)
     dom.close()
+
+
+@pytest.mark.parametrize("multiblock", [False, True])
+def test_step_reduce_async_equals_step_reduce(lib, multiblock):
+    """lbm_step_reduce_async, pipelined the way a streaming caller uses it (inflow upload
+    and the next step queued before the previous diagnostics are read, pinned outputs),
+    gives bit for bit the values and the state of the same sequence of lbm_step_reduce
+    calls; the multi-block fallback (steps, then the separate reduction) likewise."""
+    import torch
+    from paper_1807_02284_gb300 import lbm
+    if multiblock:
+        from tests.test_gpu_multiscale import gpu_multiscale
+        sc = synth.multiscale(scale=0.25, nu=2e-3, flow_amp=0.06)
+        d1, d2 = gpu_multiscale(sc), gpu_multiscale(sc)
+    else:
+        sc = _scene(periodic=(False, False, False))
+        d1, d2 = gpu_domain(sc), gpu_domain(sc)
+    recs = synth.inflow_records(sc.blocks[0])
+    ref, got, tickets = [], [], []
+    out = torch.zeros((6, 5), dtype=torch.float64, pin_memory=True)
+    for i in range(6):
+        r = recs.copy()
+        r["ux"] *= np.float32(1.0 + 0.01 * i)
+        d1.set_inflow(r)
+        ref.append(d1.step_reduce(1 + i % 2))
+        d2.set_inflow(r)
+        tickets.append(d2.step_reduce_async(1 + i % 2, out[i]))
+        if i > 0:
+            d2.wait_results(tickets[i - 1])
+            got.append(out[i - 1].numpy().copy())
+    d2.wait_results(tickets[-1])
+    got.append(out[5].numpy().copy())
+    assert tickets == list(range(1, 7))
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b), (a, b)
+    assert np.array_equal(d1.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32),
+                          d2.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32))
+    with pytest.raises(lbm.LBMError) as ei:          # a ticket this domain has not issued
+        d2.wait_results(7)
+    assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
+    with pytest.raises(lbm.LBMError) as ei:
+        d2.step_reduce_async(0, out[0])
+    assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
+    d1.close()
+    d2.close()
