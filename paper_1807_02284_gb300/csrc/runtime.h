@@ -150,6 +150,7 @@ struct lbm_domain {
   void on_state_reset(int b);
   lbm_status advance(int n);            // Algorithm 1, n reference steps
   lbm_status advance_direct(int n);     // same, launched without graph capture
+  lbm_status advance_single(int m);     // m steps from one-step graphs (several blocks)
 };
 
 using Domain = lbm_domain;

@@ -15,7 +15,8 @@ namespace lbm {
 // block).  Each graph advances `chunk` reference steps, a multiple of the period after which
 // the level assignment repeats, so it ends in the assignment it started from.
 struct GraphCache {
-  std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> exec;
+  std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> exec;     // chunk-step graphs
+  std::vector<std::pair<std::vector<int>, cudaGraphExec_t>> single;   // one-step graphs
   int chunk = 0;
 };
 
@@ -108,6 +109,8 @@ lbm_status lbm_domain::autotune_tiles(int b) {
 void lbm_domain::invalidate_graphs() {
   if (!graphs) return;
   for (auto& kv : graphs->exec)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : graphs->single)
     if (kv.second) cudaGraphExecDestroy(kv.second);
   delete graphs;
   graphs = nullptr;
@@ -246,6 +249,43 @@ lbm_status lbm_domain::advance_direct(int n) {
 
 // Without a tape, steps are replayed from captured graphs of `chunk` reference steps (a
 // multiple of the level-rotation period, at least 16 steps); the remainder launches directly.
+// m reference steps of a continuous-scale domain from one-step graphs captured per level
+// assignment (the schedule of one step is 16 launches with forks and joins on several
+// streams; replaying it as one graph leaves the GPU no gaps between them).  Single-block
+// domains launch their one kernel directly.
+lbm_status lbm_domain::advance_single(int m) {
+  if (blocks.size() == 1 || !graphs) return advance_direct(m);
+  for (int i = 0; i < m; ++i) {
+    std::vector<int> key(blocks.size());
+    for (size_t b = 0; b < blocks.size(); ++b) key[b] = blocks[b].cur;
+    cudaGraphExec_t exec = nullptr;
+    for (auto& kv : graphs->single)
+      if (kv.first == key) exec = kv.second;
+    if (!exec) {
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+      const lbm_status st = multiscale_step(this);
+      cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+      for (size_t b = 0; b < blocks.size(); ++b) blocks[b].cur = key[b];
+      if (st != LBM_OK || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return st != LBM_OK ? st : cuda_fail(e2, "step graph capture");
+      }
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      graphs->single.push_back({key, exec});
+    }
+    const cudaError_t e = cudaGraphLaunch(exec, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    const std::vector<int> s = next_levels(blocks, key);
+    for (size_t b = 0; b < blocks.size(); ++b) blocks[b].cur = s[b];
+    ++steps;
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_domain::advance(int n) {
   if (n > 0) {
     for (size_t b = 0; b < blocks.size(); ++b) {
@@ -274,7 +314,7 @@ lbm_status lbm_domain::advance(int n) {
     graphs->chunk = period * ((16 + period - 1) / period);
   }
   const int chunk = graphs->chunk;
-  if (n < 2 * chunk) return advance_direct(n);
+  if (n < 2 * chunk) return advance_single(n);
   int done = 0;
   while (n - done >= chunk) {
     std::vector<int> key(blocks.size());
@@ -316,7 +356,7 @@ lbm_status lbm_domain::advance(int n) {
     steps += chunk;
     done += chunk;
   }
-  return advance_direct(n - done);
+  return advance_single(n - done);
 }
 
 // lbm_step_reduce: n reference steps whose last one (on a single-block domain with 32-bit
