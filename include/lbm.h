@@ -459,6 +459,17 @@ lbm_status lbm_step_batch(lbm_domain* const* doms, int32_t n, int32_t steps);
    error word as lbm_reduce_batch reports it. */
 lbm_status lbm_step_batch_reduce(lbm_domain* const* doms, int32_t n, int32_t steps, double* out);
 
+/* lbm_step_batch_reduce without the wait (not in the paper; the batched counterpart of
+   lbm_step_reduce_async): the same steps and diagnostics are enqueued, the 5 n values are
+   combined on the device and copied into out behind them, and the call returns.  *ticket
+   receives a ticket of doms[0] (the sequence lbm_step_reduce_async uses): lbm_wait_results
+   (doms[0], ticket) waits for out, and reports DIVERGED when any member's error word was set
+   by then (every member's error bits are folded into doms[0]'s).  out (pinned host memory
+   for an asynchronous copy) must stay valid and unread until then.  INVALID_ARG for a null
+   out or ticket; otherwise as lbm_step_batch_reduce. */
+lbm_status lbm_step_batch_reduce_async(lbm_domain* const* doms, int32_t n, int32_t steps,
+                                       double* out, int64_t* ticket);
+
 /* Self-test of the bounded device-wide barrier used by lbm_step_batch (no counterpart in the
    paper): launches a small cooperative kernel whose barrier waits for `extra` CTAs that do
    not exist, so every wait expires after about limit_ms (0 < limit_ms <= 5000).  Returns

@@ -235,6 +235,7 @@ struct BatchPlan {
   RedMember* members = nullptr;
   double* out_dev = nullptr;
   double* out_host = nullptr;
+  double* out5_dev = nullptr;   // lbm_step_batch_reduce_async: 5 values per member
 };
 
 // Plans cached by the first domain of a batch.  A call with an odd step count flips every
@@ -259,6 +260,7 @@ static void free_plan(lbm_domain* dom, BatchPlan* p) {
   if (p->records) dom->dev_free(p->records);
   if (p->members) dom->dev_free(p->members);
   if (p->out_dev) dom->dev_free(p->out_dev);
+  if (p->out5_dev) dom->dev_free(p->out5_dev);
   if (p->out_host) cudaFreeHost(p->out_host);
   delete p;
 }
@@ -279,7 +281,9 @@ static lbm_status add_red_buffers(lbm_domain* const* doms, int n, BatchPlan* p) 
   p->records = static_cast<double*>(d0->dev_alloc((size_t)p->n_items * 8 * sizeof(double)));
   p->members = static_cast<RedMember*>(d0->dev_alloc((size_t)n * sizeof(RedMember)));
   p->out_dev = static_cast<double*>(d0->dev_alloc((size_t)n * 8 * sizeof(double)));
-  if (!p->records || !p->members || !p->out_dev) return d0->fail(LBM_ERR_OOM, "batch diagnostics buffers");
+  p->out5_dev = static_cast<double*>(d0->dev_alloc((size_t)n * 5 * sizeof(double)));
+  if (!p->records || !p->members || !p->out_dev || !p->out5_dev)
+    return d0->fail(LBM_ERR_OOM, "batch diagnostics buffers");
   if (cudaMallocHost(&p->out_host, (size_t)n * 8 * sizeof(double)) != cudaSuccess) {
     p->out_host = nullptr;
     return d0->fail(LBM_ERR_OOM, "batch diagnostics staging");
@@ -399,7 +403,26 @@ static lbm_status tune_chunk(lbm_domain* const* doms, int n, int* chunk_out, int
   return LBM_OK;
 }
 
-static lbm_status step_batch(lbm_domain* const* doms, int32_t n, int32_t steps, double* out) {
+// Per-member sums (8 doubles: 6 sums, the member's error word, unused) to the 5 diagnostics of
+// the lbm_reduce layout, and every member's error bits into the first domain's error word.
+__global__ void k_batch_combine(const double* __restrict__ sums, int n, double* __restrict__ out5,
+                                int* err0) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  const double* r = sums + 8 * (size_t)m;
+  double* o = out5 + 5 * (size_t)m;
+  o[0] = r[0] + r[1];
+  o[1] = r[2];
+  o[2] = r[3];
+  o[3] = r[4];
+  o[4] = r[5];
+  const int e = (int)r[6];
+  if (e) atomicOr(err0, e);
+}
+
+// ticket != nullptr: lbm_step_batch_reduce_async (the values go to out on the stream).
+static lbm_status step_batch(lbm_domain* const* doms, int32_t n, int32_t steps, double* out,
+                             int64_t* ticket = nullptr) {
   if (!doms || n <= 0 || !doms[0]) return LBM_ERR_INVALID_ARG;
   lbm_domain* d0 = doms[0];
   cudaSetDevice(d0->desc.device);
@@ -509,6 +532,25 @@ static lbm_status step_batch(lbm_domain* const* doms, int32_t n, int32_t steps, 
     d0->post_error_probe();
     return LBM_OK;
   }
+  if (ticket) {
+    const int slot = (int)(d0->results_issued % lbm_domain::kResultSlots);
+    if (!d0->result_ev[slot] &&
+        cudaEventCreateWithFlags(&d0->result_ev[slot], cudaEventDisableTiming) != cudaSuccess) {
+      d0->result_ev[slot] = nullptr;
+      return d0->fail(LBM_ERR_CUDA, "cudaEventCreate");
+    }
+    k_batch_combine<<<(n + 63) / 64, 64, 0, s>>>(p->out_dev, n, p->out5_dev, d0->d_err);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, p->out5_dev, (size_t)n * 5 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) {
+      d0->post_error_probe();
+      e = cudaEventRecord(d0->result_ev[slot], s);
+    }
+    if (e != cudaSuccess) return d0->cuda_fail(e, "batch diagnostics read-back");
+    *ticket = ++d0->results_issued;
+    return LBM_OK;
+  }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return d0->cuda_fail(e, "cudaStreamSynchronize");
   lbm_status first = LBM_OK;
@@ -535,6 +577,12 @@ extern "C" lbm_status lbm_step_batch_reduce(lbm_domain* const* doms, int32_t n, 
                                             double* out) {
   if (!out) return LBM_ERR_INVALID_ARG;
   return step_batch(doms, n, steps, out);
+}
+
+extern "C" lbm_status lbm_step_batch_reduce_async(lbm_domain* const* doms, int32_t n,
+                                                  int32_t steps, double* out, int64_t* ticket) {
+  if (!out || !ticket) return LBM_ERR_INVALID_ARG;
+  return step_batch(doms, n, steps, out, ticket);
 }
 
 // Self-test of the bounded device barrier: a cooperative kernel waits for `extra` more CTAs

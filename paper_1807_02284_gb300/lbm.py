@@ -86,6 +86,7 @@ _SIGNATURES = {
     "lbm_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
     "lbm_step_reduce": (_I, [_P, _I, C.POINTER(C.c_double)]),
     "lbm_step_reduce_async": (_I, [_P, _I, _P, C.POINTER(C.c_int64)]),
+    "lbm_step_batch_reduce_async": (_I, [C.POINTER(_P), _I, _I, _P, C.POINTER(C.c_int64)]),
     "lbm_wait_results": (_I, [_P, C.c_int64]),
     "lbm_get_block_info": (_I, [_P, _I, C.POINTER(lbm_block_info)]),
     "lbm_step_batch": (_I, [C.POINTER(_P), _I, _I]),
@@ -480,6 +481,22 @@ def step_batch_reduce(domains: Sequence[Domain], steps: int) -> np.ndarray:
     if st != LBM_OK:
         domains[0].check(st)
     return np.array(list(out)).reshape(len(domains), 5)
+
+
+def step_batch_reduce_async(domains: Sequence[Domain], steps: int, out) -> int:
+    """``lbm_step_batch_reduce_async``: the batched steps and every member's diagnostics,
+    copied into ``out`` (5 n float64 values in host memory, pinned for an asynchronous copy);
+    returns the ticket to pass to ``domains[0].wait_results``."""
+    lib = load()
+    ptr, dev = _ptr(out)
+    if dev or _nbytes(out) < 5 * 8 * len(domains) or str(out.dtype) not in ("float64", "torch.float64"):
+        raise ValueError("out must be 5 n float64 values in host memory")
+    arr = (C.c_void_p * len(domains))(*[d.handle.value for d in domains])
+    t = C.c_int64()
+    st = lib.lbm_step_batch_reduce_async(arr, len(domains), int(steps), C.c_void_p(ptr), C.byref(t))
+    if st != LBM_OK:
+        domains[0].check(st)
+    return t.value
 
 
 def set_inflow_batch(domains: Sequence[Domain], records: Sequence[np.ndarray]):

@@ -242,3 +242,35 @@ def test_step_batch_reduce_state_and_values(lib, storage):
     assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
     for d in a + b:
         d.close()
+
+
+def test_step_batch_reduce_async_equals_sync(lib):
+    """lbm_step_batch_reduce_async pipelined (the next batched step queued before the previous
+    diagnostics are waited for) gives bit for bit the values and states of the same sequence
+    of lbm_step_batch_reduce calls; its tickets come from the first domain's sequence."""
+    import torch
+    from paper_1807_02284_gb300 import lbm
+    scenes = _scenes(6, seed=47)
+    a = [gpu_domain(s) for s in scenes]
+    b = [gpu_domain(s) for s in scenes]
+    out = torch.zeros((5, len(b), 5), dtype=torch.float64, pin_memory=True)
+    ref, got, tickets = [], [], []
+    for k in range(5):
+        ref.append(lbm.step_batch_reduce(a, 1 + k % 2))
+        tickets.append(lbm.step_batch_reduce_async(b, 1 + k % 2, out[k]))
+        if k:
+            b[0].wait_results(tickets[k - 1])
+            got.append(out[k - 1].numpy().copy())
+    b[0].wait_results(tickets[-1])
+    got.append(out[4].numpy().copy())
+    assert tickets == list(range(1, 6))
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32),
+                              y.read_field(lbm.LBM_FIELD_F, lbm.LBM_F32))
+    with pytest.raises(lbm.LBMError) as ei:
+        lbm.step_batch_reduce_async(b, 0, out[0])
+    assert ei.value.status == lbm.LBM_ERR_INVALID_ARG
+    for d in a + b:
+        d.close()
