@@ -4,67 +4,99 @@
 // reverse needs are reconstructed from the central moments with the exact inverse sweeps
 // (unshift_axis, inv_axis), so a node's reverse keeps three 27-arrays live instead of seven.
 // The equilibrium offsets Delta(rho - 1, u) of the relaxation are differentiated with a small
-// forward-mode dual number (value plus four partials).
+// forward-mode dual number (value plus the partials with respect to rho - 1 and u that are not
+// zero by construction).
 #pragma once
 #include "lbm_device.cuh"
 
 namespace lbm {
 
-// Value and partials with respect to (rho - 1, u_x, u_y, u_z).
-struct D4 {
-  float v, d0, d1, d2, d3;
+// Value and the partials with respect to (rho - 1, u_x, u_y, u_z) whose bits are set in M
+// (bit 0: rho - 1, bits 1-3: u_x, u_y, u_z).  Partials that are zero by construction are
+// neither stored nor computed: IEEE arithmetic does not let the compiler drop 0 * x, so a
+// dense dual number would multiply every zero partial out.
+template <unsigned M>
+struct Dual {
+  float v;
+  float d[4];
 };
-__device__ __forceinline__ D4 d4c(float c) { return D4{c, 0.f, 0.f, 0.f, 0.f}; }
-__device__ __forceinline__ D4 operator+(D4 a, D4 b) { return D4{a.v + b.v, a.d0 + b.d0, a.d1 + b.d1, a.d2 + b.d2, a.d3 + b.d3}; }
-__device__ __forceinline__ D4 operator-(D4 a, D4 b) { return D4{a.v - b.v, a.d0 - b.d0, a.d1 - b.d1, a.d2 - b.d2, a.d3 - b.d3}; }
-__device__ __forceinline__ D4 operator-(D4 a) { return D4{-a.v, -a.d0, -a.d1, -a.d2, -a.d3}; }
-__device__ __forceinline__ D4 operator*(D4 a, D4 b) {
-  return D4{a.v * b.v, a.d0 * b.v + a.v * b.d0, a.d1 * b.v + a.v * b.d1, a.d2 * b.v + a.v * b.d2,
-            a.d3 * b.v + a.v * b.d3};
-}
-__device__ __forceinline__ D4 operator*(D4 a, float s) { return D4{a.v * s, a.d0 * s, a.d1 * s, a.d2 * s, a.d3 * s}; }
-__device__ __forceinline__ D4 operator+(D4 a, float s) { return D4{a.v + s, a.d0, a.d1, a.d2, a.d3}; }
-__device__ __forceinline__ D4 operator-(float s, D4 a) { return D4{s - a.v, -a.d0, -a.d1, -a.d2, -a.d3}; }
+template <unsigned M>
+__device__ __forceinline__ constexpr bool dual_has(int i) { return ((M >> i) & 1u) != 0u; }
 
-// Delta_abc = kappa^eq_abc - kappa_abc(w) of the relaxed moments (the diagonal second-order
-// slots hold rho/3 - 1/3 - u_a^2); the same algebra as relax_to_equilibrium.
-__device__ __forceinline__ void delta_moments(D4 drho, D4 X, D4 Y, D4 Z, D4 (&D)[27]) {
-  const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
-  const D4 X2 = X * X, Y2 = Y * Y, Z2 = Z * Z;
-  D[kap(1, 1, 0)] = -(X * Y);
-  D[kap(1, 0, 1)] = -(X * Z);
-  D[kap(0, 1, 1)] = -(Y * Z);
-  const D4 dr3 = drho * third;
-  D[kap(2, 0, 0)] = dr3 - X2;
-  D[kap(0, 2, 0)] = dr3 - Y2;
-  D[kap(0, 0, 2)] = dr3 - Z2;
-  D[kap(1, 2, 0)] = X * (third - drho * Y2);
-  D[kap(1, 0, 2)] = X * (third - drho * Z2);
-  D[kap(2, 1, 0)] = Y * (third - drho * X2);
-  D[kap(0, 1, 2)] = Y * (third - drho * Z2);
-  D[kap(2, 0, 1)] = Z * (third - drho * X2);
-  D[kap(0, 2, 1)] = Z * (third - drho * Y2);
-  D[kap(1, 1, 1)] = -(drho * X * Y * Z);
-  const D4 r3m1 = drho * 3.0f + 2.0f;
-  const D4 dr9 = drho * ninth;
-  D[kap(2, 2, 0)] = r3m1 * X2 * Y2 + dr9 - (X2 + Y2) * third;
-  D[kap(2, 0, 2)] = r3m1 * X2 * Z2 + dr9 - (X2 + Z2) * third;
-  D[kap(0, 2, 2)] = r3m1 * Y2 * Z2 + dr9 - (Y2 + Z2) * third;
-  D[kap(2, 1, 1)] = Y * Z * (r3m1 * X2 - d4c(third));
-  D[kap(1, 2, 1)] = X * Z * (r3m1 * Y2 - d4c(third));
-  D[kap(1, 1, 2)] = X * Y * (r3m1 * Z2 - d4c(third));
-  const D4 o6 = drho * (-6.0f) + (-5.0f);
-  D[kap(1, 2, 2)] = X * (o6 * Y2 * Z2 + (ninth - dr3 * (Y2 + Z2)));
-  D[kap(2, 1, 2)] = Y * (o6 * X2 * Z2 + (ninth - dr3 * (X2 + Z2)));
-  D[kap(2, 2, 1)] = Z * (o6 * X2 * Y2 + (ninth - dr3 * (X2 + Y2)));
-  const D4 rho = drho + 1.0f;
-  const D4 p2 = X2 * Y2 + X2 * Z2 + Y2 * Z2;
-  D[kap(2, 2, 2)] = (rho * 10.0f + (-1.0f)) * X2 * Y2 * Z2 + (rho + (-third)) * p2 +
-                    drho * (1.0f / 27.0f) - (X2 + Y2 + Z2) * ninth;
-  D[kap(0, 0, 0)] = d4c(0.f);
-  D[kap(1, 0, 0)] = d4c(0.f);
-  D[kap(0, 1, 0)] = d4c(0.f);
-  D[kap(0, 0, 1)] = d4c(0.f);
+template <unsigned A, unsigned B>
+__device__ __forceinline__ Dual<A | B> operator+(const Dual<A>& a, const Dual<B>& b) {
+  Dual<A | B> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    r.d[i] = dual_has<A>(i) && dual_has<B>(i) ? a.d[i] + b.d[i]
+             : dual_has<A>(i)                 ? a.d[i]
+             : dual_has<B>(i)                 ? b.d[i]
+                                              : 0.0f;
+  return r;
+}
+template <unsigned A, unsigned B>
+__device__ __forceinline__ Dual<A | B> operator-(const Dual<A>& a, const Dual<B>& b) {
+  Dual<A | B> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    r.d[i] = dual_has<A>(i) && dual_has<B>(i) ? a.d[i] - b.d[i]
+             : dual_has<A>(i)                 ? a.d[i]
+             : dual_has<B>(i)                 ? -b.d[i]
+                                              : 0.0f;
+  return r;
+}
+template <unsigned A, unsigned B>
+__device__ __forceinline__ Dual<A | B> operator*(const Dual<A>& a, const Dual<B>& b) {
+  Dual<A | B> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    r.d[i] = dual_has<A>(i) && dual_has<B>(i) ? a.d[i] * b.v + a.v * b.d[i]
+             : dual_has<A>(i)                 ? a.d[i] * b.v
+             : dual_has<B>(i)                 ? a.v * b.d[i]
+                                              : 0.0f;
+  return r;
+}
+template <unsigned A>
+__device__ __forceinline__ Dual<A> operator-(const Dual<A>& a) {
+  Dual<A> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.d[i] = dual_has<A>(i) ? -a.d[i] : 0.0f;
+  return r;
+}
+template <unsigned A>
+__device__ __forceinline__ Dual<A> operator*(const Dual<A>& a, float s) {
+  Dual<A> r;
+  r.v = a.v * s;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.d[i] = dual_has<A>(i) ? a.d[i] * s : 0.0f;
+  return r;
+}
+template <unsigned A>
+__device__ __forceinline__ Dual<A> operator+(const Dual<A>& a, float s) {
+  Dual<A> r = a;
+  r.v = a.v + s;
+  return r;
+}
+template <unsigned A>
+__device__ __forceinline__ Dual<A> operator-(float s, const Dual<A>& a) {
+  Dual<A> r;
+  r.v = s - a.v;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.d[i] = dual_has<A>(i) ? -a.d[i] : 0.0f;
+  return r;
+}
+__device__ __forceinline__ Dual<0u> dual_const(float c) { return Dual<0u>{c, {0.f, 0.f, 0.f, 0.f}}; }
+
+// bar[i] += db * d(dl)/d(variable i) for the partials dl carries
+template <unsigned M>
+__device__ __forceinline__ void dual_grad(float db, const Dual<M>& dl, float (&bar)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (dual_has<M>(i)) bar[i] = fmaf(db, dl.d[i], bar[i]);
 }
 
 // Central moments about u back to raw moments (inverse of shift_axis).
@@ -151,28 +183,28 @@ __device__ __forceinline__ void relax_vjp(const float (&v)[27], float (&A)[27], 
   // Each moment's Delta (with its four partials) is formed and consumed at once, so only a
   // few dual numbers are live at any time.
   const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
-  const D4 dr{drho, 1.f, 0.f, 0.f, 0.f}, x{X, 0.f, 1.f, 0.f, 0.f}, y{Y, 0.f, 0.f, 1.f, 0.f},
-           z{Z, 0.f, 0.f, 0.f, 1.f};
-  auto grad = [&](float db, const D4& dl) {
-    bar[0] = fmaf(db, dl.d0, bar[0]);
-    bar[1] = fmaf(db, dl.d1, bar[1]);
-    bar[2] = fmaf(db, dl.d2, bar[2]);
-    bar[3] = fmaf(db, dl.d3, bar[3]);
-  };
+  const Dual<1u> dr{drho, {1.f, 0.f, 0.f, 0.f}};
+  const Dual<2u> x{X, {0.f, 1.f, 0.f, 0.f}};
+  const Dual<4u> y{Y, {0.f, 0.f, 1.f, 0.f}};
+  const Dual<8u> z{Z, {0.f, 0.f, 0.f, 1.f}};
   // out_i = Delta_i + K (v_i - Delta_i): dv_i = K o, dDelta_i = (1 - K) o, dK = o (v_i - Delta_i)
-  auto one = [&](int i, const D4& dl, float K, int grp) {
+  auto one = [&](int i, const auto& dl, float K, int grp) {
     const float o = A[i];
     A[i] = K * o;
     if (grp >= 0) kbar[grp] = fmaf(o, v[i] - dl.v, kbar[grp]);
-    grad((1.0f - K) * o, dl);
+    dual_grad((1.0f - K) * o, dl, bar);
   };
   one(kap(1, 1, 0), -(x * y), kf.nu, -1);
   one(kap(1, 0, 1), -(x * z), kf.nu, -1);
   one(kap(0, 1, 1), -(y * z), kf.nu, -1);
-  const D4 x2 = x * x, y2 = y * y, z2 = z * z;
+  const auto x2 = x * x;
+  const auto y2 = y * y;
+  const auto z2 = z * z;
   {  // second-order diagonal: deviators at the shear rate, trace at group 9..16
-    const D4 dr3 = dr * third;
-    const D4 ex = dr3 - x2, ey = dr3 - y2, ez = dr3 - z2;
+    const auto dr3 = dr * third;
+    const auto ex = dr3 - x2;
+    const auto ey = dr3 - y2;
+    const auto ez = dr3 - z2;
     const float Aa = v[kap(2, 0, 0)] - ex.v, Bb = v[kap(0, 2, 0)] - ey.v, Cc = v[kap(0, 0, 2)] - ez.v;
     const float o2 = A[kap(2, 0, 0)], o3 = A[kap(0, 2, 0)], o4 = A[kap(0, 0, 2)];
     const float trb = (o2 + o3 + o4) * third;
@@ -185,9 +217,9 @@ __device__ __forceinline__ void relax_vjp(const float (&v)[27], float (&A)[27], 
     A[kap(2, 0, 0)] = Ab;
     A[kap(0, 2, 0)] = Bb_;
     A[kap(0, 0, 2)] = Cb;
-    grad(o2 - Ab, ex);
-    grad(o3 - Bb_, ey);
-    grad(o4 - Cb, ez);
+    dual_grad(o2 - Ab, ex, bar);
+    dual_grad(o3 - Bb_, ey, bar);
+    dual_grad(o4 - Cb, ez, bar);
   }
   one(kap(1, 2, 0), x * (third - dr * y2), kf.g[0], 0);
   one(kap(1, 0, 2), x * (third - dr * z2), kf.g[0], 0);
@@ -197,26 +229,26 @@ __device__ __forceinline__ void relax_vjp(const float (&v)[27], float (&A)[27], 
   one(kap(0, 2, 1), z * (third - dr * y2), kf.g[0], 0);
   one(kap(1, 1, 1), -(dr * x * y * z), kf.g[0], 0);
   {
-    const D4 r3m1 = dr * 3.0f + 2.0f;   // 3 rho - 1
-    const D4 dr9 = dr * ninth;
+    const auto r3m1 = dr * 3.0f + 2.0f;   // 3 rho - 1
+    const auto dr9 = dr * ninth;
     one(kap(2, 2, 0), r3m1 * x2 * y2 + dr9 - (x2 + y2) * third, kf.g[1], 1);
     one(kap(2, 0, 2), r3m1 * x2 * z2 + dr9 - (x2 + z2) * third, kf.g[1], 1);
     one(kap(0, 2, 2), r3m1 * y2 * z2 + dr9 - (y2 + z2) * third, kf.g[1], 1);
-    one(kap(2, 1, 1), y * z * (r3m1 * x2 - d4c(third)), kf.g[1], 1);
-    one(kap(1, 2, 1), x * z * (r3m1 * y2 - d4c(third)), kf.g[1], 1);
-    one(kap(1, 1, 2), x * y * (r3m1 * z2 - d4c(third)), kf.g[1], 1);
+    one(kap(2, 1, 1), y * z * (r3m1 * x2 - dual_const(third)), kf.g[1], 1);
+    one(kap(1, 2, 1), x * z * (r3m1 * y2 - dual_const(third)), kf.g[1], 1);
+    one(kap(1, 1, 2), x * y * (r3m1 * z2 - dual_const(third)), kf.g[1], 1);
   }
   {
-    const D4 o6 = dr * (-6.0f) + (-5.0f);   // 1 - 6 rho
-    const D4 dr3 = dr * third;
+    const auto o6 = dr * (-6.0f) + (-5.0f);   // 1 - 6 rho
+    const auto dr3 = dr * third;
     one(kap(1, 2, 2), x * (o6 * y2 * z2 + (ninth - dr3 * (y2 + z2))), kf.g[2], 2);
     one(kap(2, 1, 2), y * (o6 * x2 * z2 + (ninth - dr3 * (x2 + z2))), kf.g[2], 2);
     one(kap(2, 2, 1), z * (o6 * x2 * y2 + (ninth - dr3 * (x2 + y2))), kf.g[2], 2);
   }
   {
-    const D4 rho = dr + 1.0f;
-    const D4 p2 = x2 * y2 + x2 * z2 + y2 * z2;
-    const D4 d222 = (rho * 10.0f + (-1.0f)) * x2 * y2 * z2 + (rho + (-third)) * p2 +
+    const auto rho = dr + 1.0f;
+    const auto p2 = x2 * y2 + x2 * z2 + y2 * z2;
+    const auto d222 = (rho * 10.0f + (-1.0f)) * x2 * y2 * z2 + (rho + (-third)) * p2 +
                     dr * (1.0f / 27.0f) - (x2 + y2 + z2) * ninth;
     one(kap(2, 2, 2), d222, kf.g[3], 3);
   }
