@@ -381,6 +381,23 @@ size_t lbm_plane_bytes(const lbm_domain* dom, int32_t dir);
 lbm_status lbm_pack_plane(lbm_domain* dom, int32_t z, int32_t dir, void* dev_buf);
 lbm_status lbm_unpack_plane(lbm_domain* dom, int32_t z, int32_t dir, const void* dev_buf);
 
+/* One step of a slab of a domain cut along z with its halo exchange overlapped (no
+   counterpart in the paper).  lo / hi (0 or 1) say whether plane 0 / plane nz - 1 is a halo
+   plane (a neighbouring slab's plane) rather than an end face of the whole domain.  The
+   owned planes next to the halos, 1 (lo) and nz - 2 (hi), are stepped first; once written
+   they are packed into send_lo (lbm_pack_plane layout, dir -1) and send_hi (dir +1) on
+   pack_stream (a cudaStream_t, or NULL for an internal stream), while the other owned planes
+   are stepped on the domain's stream; then the domain's level advances as after lbm_step.
+   Halo planes are not stepped: before the next step the caller puts the neighbours' planes
+   into them with lbm_unpack_plane (z = 0 with dir +1, z = nz - 1 with dir -1), after waiting
+   for their transport.  Owned nodes end exactly as with lbm_step.  send buffers: device
+   memory of lbm_plane_bytes bytes, 16-byte aligned, owned by the caller, not to be read
+   before pack_stream reaches the packing.  INVALID_ARG for a null or unaligned send buffer
+   that is needed or fewer than two owned planes; UNSUPPORTED with refined or far-field
+   blocks; STATE while a tape records; DIVERGED as lbm_step. */
+lbm_status lbm_step_slab(lbm_domain* dom, int32_t lo, int32_t hi, void* send_lo, void* send_hi,
+                         void* pack_stream);
+
 /* One reference step of Algorithm 1 (Sec. 4.2.4-4.2.5) as a sequence of phases, so that the
    blocks of one continuous-scale domain can be placed on several devices or processes (no
    counterpart in the paper, which runs one GPU).  Every participant holds the whole domain

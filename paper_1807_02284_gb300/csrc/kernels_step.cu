@@ -14,7 +14,7 @@ template <typename T, typename IT, bool ALIGN, int MINB, bool WALLS>
 __global__ void __launch_bounds__(256, MINB) k_step(BlockView v) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = blockIdx.z + v.z_first;
   if (x >= v.nx || y >= v.ny) return;
   cell_update<T, IT, ALIGN, WALLS>(v, x, y, z);
 }
@@ -43,6 +43,25 @@ cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStr
   } else {
     if (i32) launch_step_t<float, uint32_t, false>(v, grid, block, minb, s);
     else launch_step_t<float, uint64_t, false>(v, grid, block, minb, s);
+  }
+  return cudaGetLastError();
+}
+
+// The step of planes [z0, z0 + count) only (a slab's send planes before its other planes).
+cudaError_t launch_step_planes(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
+                               int minb, int z0, int count) {
+  if (count <= 0) return cudaSuccess;
+  BlockView w = v;
+  w.z_first = z0;
+  dim3 block(bx, by, 1);
+  dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, count);
+  const bool i32 = fits_32bit_index(v.N);
+  if (storage == ST_FP16) {
+    if (i32) launch_step_t<__half, uint32_t, false>(w, grid, block, minb, s);
+    else launch_step_t<__half, uint64_t, false>(w, grid, block, minb, s);
+  } else {
+    if (i32) launch_step_t<float, uint32_t, false>(w, grid, block, minb, s);
+    else launch_step_t<float, uint64_t, false>(w, grid, block, minb, s);
   }
   return cudaGetLastError();
 }

@@ -32,6 +32,7 @@ struct BlockView {
   const void* f_al0 = nullptr;   // populations at t_n
   const float* c_al0 = nullptr;  // scalar at t_n
   float al0 = 0.f, al1 = 0.f, al2 = 0.f;
+  int z_first = 0;     // plane of the launch's first z index (a launch over some planes only)
 };
 
 // One node mapped between scales: destination node index, index of the source cell's
@@ -167,6 +168,8 @@ cudaError_t launch_step_reduce(const BlockView& v, int storage, int bx, int by, 
 
 // ---- coupling.cu
 cudaError_t launch_map(const MapArgs& a, int storage, cudaStream_t s);
+cudaError_t launch_step_planes(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
+                               int minb, int z0, int count);
 // ghost layer of a refined block that also keeps the source's trilinear interpolant
 // (a.ghost_store): first = true maps level a.f_lo at t_n; first = false maps level a.f_hi
 // blended at a.theta with the interpolant a.ghost_blend of the earlier level (FP32)

@@ -51,22 +51,22 @@ __global__ void k_plane(T* f, float* u, float* c, uint8_t* flags, size_t N, size
   }
 }
 
+// Plane z of level `level` of block 0 to (PACK) or from the buffer, on stream s.
 template <bool PACK>
-static cudaError_t launch_plane(lbm_domain* dom, int z, int dir, void* buf) {
+static cudaError_t launch_plane(lbm_domain* dom, int level, int z, int dir, void* buf,
+                                cudaStream_t s) {
   Block& B = dom->blocks[0];
   const size_t P = (size_t)B.nx * B.ny, base = (size_t)z * P;
   const int grid = (int)std::min<size_t>((P + 255) / 256, 4096);
-  Level& L = B.lv[B.cur];
+  Level& L = B.lv[level];
   unsigned char* b = static_cast<unsigned char*>(buf);
   const int k0 = plane_first(dir), nk = plane_rows(dir);
   if (dom->desc.storage == LBM_FP16_SHIFTED)
-    k_plane<__half, PACK><<<grid, 256, 0, dom->stream>>>(static_cast<__half*>(L.f), L.u, L.c,
-                                                         B.flags, B.N, base, P, k0, nk,
-                                                         pop_rows_bytes(P, 2, dir), b);
+    k_plane<__half, PACK><<<grid, 256, 0, s>>>(static_cast<__half*>(L.f), L.u, L.c, B.flags, B.N,
+                                               base, P, k0, nk, pop_rows_bytes(P, 2, dir), b);
   else
-    k_plane<float, PACK><<<grid, 256, 0, dom->stream>>>(static_cast<float*>(L.f), L.u, L.c,
-                                                        B.flags, B.N, base, P, k0, nk,
-                                                        pop_rows_bytes(P, 4, dir), b);
+    k_plane<float, PACK><<<grid, 256, 0, s>>>(static_cast<float*>(L.f), L.u, L.c, B.flags, B.N,
+                                              base, P, k0, nk, pop_rows_bytes(P, 4, dir), b);
   return cudaGetLastError();
 }
 
@@ -97,7 +97,7 @@ static lbm_status plane_args(lbm_domain* dom, int32_t z, int32_t dir, const void
 extern "C" lbm_status lbm_pack_plane(lbm_domain* dom, int32_t z, int32_t dir, void* dev_buf) {
   lbm_status st = plane_args(dom, z, dir, dev_buf);
   if (st != LBM_OK) return st;
-  const cudaError_t e = launch_plane<true>(dom, z, dir, dev_buf);
+  const cudaError_t e = launch_plane<true>(dom, dom->blocks[0].cur, z, dir, dev_buf, dom->stream);
   return e == cudaSuccess ? LBM_OK : dom->cuda_fail(e, "pack plane");
 }
 
@@ -105,6 +105,53 @@ extern "C" lbm_status lbm_unpack_plane(lbm_domain* dom, int32_t z, int32_t dir,
                                        const void* dev_buf) {
   lbm_status st = plane_args(dom, z, dir, dev_buf);
   if (st != LBM_OK) return st;
-  const cudaError_t e = launch_plane<false>(dom, z, dir, const_cast<void*>(dev_buf));
+  const cudaError_t e = launch_plane<false>(dom, dom->blocks[0].cur, z, dir,
+                                            const_cast<void*>(dev_buf), dom->stream);
   return e == cudaSuccess ? LBM_OK : dom->cuda_fail(e, "unpack plane");
+}
+
+// One step of a slab whose halo exchange overlaps its work: the owned planes next to the
+// halos (the planes the neighbours need next) are stepped first, packed on pack_stream as soon
+// as they are written, while the remaining owned planes are stepped on the domain's stream;
+// halo planes are not stepped (the next unpack overwrites what the pull reads of them).
+extern "C" lbm_status lbm_step_slab(lbm_domain* dom, int32_t lo, int32_t hi, void* send_lo,
+                                    void* send_hi, void* pack_stream) {
+  if (!dom) return LBM_ERR_INVALID_ARG;
+  cudaSetDevice(dom->desc.device);
+  if (dom->blocks.size() != 1) return dom->fail(LBM_ERR_UNSUPPORTED, "slab steps need a single-block domain");
+  if (dom->tape) return dom->fail(LBM_ERR_STATE, "slab steps do not record an adjoint tape");
+  Block& B = dom->blocks[0];
+  const int zlo = lo ? 1 : 0, zhi = hi ? B.nz - 2 : B.nz - 1;   // first and last owned plane
+  if (zhi - zlo < 1) return dom->fail(LBM_ERR_INVALID_ARG, "a slab step needs at least two owned planes");
+  auto bad = [](const void* b) { return !b || reinterpret_cast<uintptr_t>(b) % 16 != 0; };
+  if ((lo && bad(send_lo)) || (hi && bad(send_hi)))
+    return dom->fail(LBM_ERR_INVALID_ARG, "send buffer null or not 16-byte aligned");
+  if (*dom->h_err & 1) return dom->fail(LBM_ERR_DIVERGED, "divergence recorded by an earlier step");
+  lbm_status st = dom->autotune_tiles(0);
+  if (st != LBM_OK) return st;
+  cudaStream_t ps = static_cast<cudaStream_t>(pack_stream);
+  if (!ps) {
+    st = dom->aux(&ps);
+    if (st != LBM_OK) return st;
+  }
+  cudaEvent_t ev = dom->event(7);
+  if (!ev) return dom->fail(LBM_ERR_CUDA, "cudaEventCreate");
+  const int nxt = B.cur ^ 1;
+  const BlockView v = dom->view(0, B.cur, nxt);
+  const int storage = dom->desc.storage;
+  cudaError_t e = cudaSuccess;
+  if (lo) e = launch_step_planes(v, storage, B.bx, B.by, dom->stream, B.minb, zlo, 1);
+  if (hi && e == cudaSuccess) e = launch_step_planes(v, storage, B.bx, B.by, dom->stream, B.minb, zhi, 1);
+  if ((lo || hi) && e == cudaSuccess) {
+    e = cudaEventRecord(ev, dom->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ps, ev, 0);
+    if (lo && e == cudaSuccess) e = launch_plane<true>(dom, nxt, zlo, -1, send_lo, ps);
+    if (hi && e == cudaSuccess) e = launch_plane<true>(dom, nxt, zhi, +1, send_hi, ps);
+  }
+  const int i0 = zlo + (lo ? 1 : 0), i1 = zhi - (hi ? 1 : 0);
+  if (e == cudaSuccess) e = launch_step_planes(v, storage, B.bx, B.by, dom->stream, B.minb, i0, i1 - i0 + 1);
+  if (e != cudaSuccess) return dom->cuda_fail(e, "slab step");
+  B.cur = nxt;
+  ++dom->steps;
+  return LBM_OK;
 }

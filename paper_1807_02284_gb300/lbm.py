@@ -94,6 +94,7 @@ _SIGNATURES = {
     "lbm_plane_bytes": (C.c_size_t, [_P, _I]),
     "lbm_pack_plane": (_I, [_P, _I, _I, _P]),
     "lbm_unpack_plane": (_I, [_P, _I, _I, _P]),
+    "lbm_step_slab": (_I, [_P, _I, _I, _P, _P, _P]),
     "lbm_step_phase": (_I, [_P, _I, _I, _I]),
     "lbm_mapping_boxes": (_I, [_P, _I, _I, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "lbm_box_bytes": (C.c_size_t, [_P, _I, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -187,6 +188,11 @@ class Domain:
         if stream is None:
             import torch
             stream = torch.cuda.current_stream(device)
+            if stream.cuda_stream == 0:
+                # the default stream has no handle to pass (NULL would make the library create
+                # a private stream torch does not know): give the domain a stream of its own
+                # that torch_stream names, so that waits on torch_stream order its work
+                stream = torch.cuda.Stream(device=device)
         self.torch_stream = stream
         d.cuda_stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
         if torch_allocator:
@@ -382,6 +388,16 @@ class Domain:
         """Copies the device tensor `buf` into z-plane `z` of the current state."""
         self.check(self.lib.lbm_unpack_plane(self.handle, int(z), int(direction),
                                              self._plane_buffer(buf, direction)))
+
+    def step_slab(self, lo, hi, send_lo=None, send_hi=None, pack_stream=None):
+        """``lbm_step_slab``: one step of a slab, its send planes stepped first and packed on
+        ``pack_stream`` (a torch stream, or None for an internal one) while the other owned
+        planes step; halo planes are left to the next unpack."""
+        plo = self._plane_buffer(send_lo, -1) if lo else None
+        phi = self._plane_buffer(send_hi, +1) if hi else None
+        ps = None if pack_stream is None else C.c_void_p(
+            pack_stream.cuda_stream if hasattr(pack_stream, "cuda_stream") else pack_stream)
+        self.check(self.lib.lbm_step_slab(self.handle, 1 if lo else 0, 1 if hi else 0, plo, phi, ps))
 
     def step_phase(self, phase, block=0, compute=True):
         """One phase of a reference step (LBM_PHASE_*), computed or only advancing levels."""

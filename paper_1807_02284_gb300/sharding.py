@@ -163,6 +163,10 @@ class SlabDomain:
         self.bufs = {(k, tag): torch.empty(self.dom.plane_bytes(DIRECTION[tag]),
                                            dtype=torch.uint8, device=dev)
                      for (k, _, _, tag) in self.plan.transfers()}
+        # the halos hold the neighbours' current edge planes (an exchange or a pipelined step
+        # since the state last changed from outside)
+        self._halos_current = False
+        self._pack_stream = None
 
     # ------------------------------------------------------------------ global inputs
     def local(self, a):
@@ -176,6 +180,7 @@ class SlabDomain:
 
     def set_flags(self, flags):
         self.dom.set_flags(self.local(flags))
+        self._halos_current = False
 
     def set_walls(self, faces, obstacles=False):
         """Wall faces (x-, x+, y-, y+, z-, z+) of the whole domain: a z face belongs to the
@@ -186,6 +191,7 @@ class SlabDomain:
         faces[4] = faces[4] and self.plan.lo == 0 and self.plan.z0 == 0
         faces[5] = faces[5] and self.plan.hi == 0 and self.plan.z1 == self.plan.nz
         self.dom.set_walls(faces, obstacles=obstacles)
+        self._halos_current = False
 
     def set_inflow(self, records):
         """Inflow records in global coordinates; those on a local plane are kept, moved to
@@ -202,12 +208,14 @@ class SlabDomain:
         out = np.concatenate(keep) if keep else rec[:0]
         if len(out):
             self.dom.set_inflow(out)
+        self._halos_current = False
 
     def init_macro(self, u, rho=None, c=None):
         import numpy as np
         loc = [None if a is None else self.local(np.asarray(a, dtype=np.float32))
                for a in (u, rho, c)]
         self.dom.init_macro(loc[0], rho=loc[1], c=loc[2])
+        self._halos_current = False
 
     def read_owned(self, field, dtype=None):
         """A field of this slab's owned planes, shaped (comp, planes, ny, nx) or
@@ -257,11 +265,34 @@ class SlabDomain:
         tr = self.plan.transfers()
         if not tr:
             return
-        import torch
-        import torch.distributed as dist
         self._pack()
         self.dom.sync()
+        self._transport(group)
+        self._unpack()
+        self._halos_current = True
+
+    def _transport(self, group=None, stream=None):
+        """Sends the packed edge planes and receives the neighbours' into the recv buffers.
+        With NCCL and a `stream` (the stream the planes were packed on) nothing waits on the
+        host: the messages follow the packing, and the domain's stream waits for them."""
+        import torch
+        import torch.distributed as dist
+        tr = self.plan.transfers()
         nccl = dist.get_backend(group) == "nccl"
+        if stream is not None and nccl:
+            ops = []
+            for kind, _, peer, tag in tr:
+                g_peer = peer if group is None else dist.get_global_rank(group, peer)
+                fn = dist.isend if kind == "send" else dist.irecv
+                ops.append(dist.P2POp(fn, self.bufs[(kind, tag)], g_peer, group, tag))
+            with torch.cuda.stream(stream):
+                reqs = dist.batch_isend_irecv(ops)
+            with torch.cuda.stream(self.dom.torch_stream):
+                for req in reqs:
+                    req.wait()
+            return
+        if stream is not None:
+            stream.synchronize()
         staged = {}
         ops = []
         for kind, _, peer, tag in tr:
@@ -278,13 +309,39 @@ class SlabDomain:
                 self.bufs[(kind, tag)].copy_(t)
         if any(t.is_cuda for t in self.bufs.values()):
             torch.cuda.synchronize()
-        self._unpack()
+
+    def _step_sends(self, stream=None):
+        """One step of this slab whose new edge planes are packed into the send buffers on
+        `stream` while its other planes step (the domain's lbm_step_slab)."""
+        lo, hi = self.plan.lower is not None, self.plan.upper is not None
+        self.dom.step_slab(lo, hi, self.bufs.get(("send", DOWN)), self.bufs.get(("send", UP)),
+                           stream)
 
     def step(self, n=1, group=None):
-        """n steps of the whole domain, this rank's slab: exchange, then step."""
-        for _ in range(int(n)):
+        """n steps of the whole domain, this rank's slab.  With a domain that has
+        ``step_slab``: an exchange of the current edge planes if the halos are not current,
+        then per step the send planes first, their transport while the other planes step,
+        and the unpack into the halos before the next step.  Otherwise: exchange, then step."""
+        if not self.plan.transfers():
+            self.dom.step(int(n))
+            return
+        if not hasattr(self.dom, "step_slab"):
+            for _ in range(int(n)):
+                self.exchange(group)
+                self.dom.step(1)
+            self._halos_current = False
+            return
+        import torch
+        if not self._halos_current:
             self.exchange(group)
-            self.dom.step(1)
+        on_gpu = any(t.is_cuda for t in self.bufs.values())
+        if on_gpu and self._pack_stream is None:
+            self._pack_stream = torch.cuda.Stream(device=next(iter(self.bufs.values())).device)
+        for _ in range(int(n)):
+            self._step_sends(self._pack_stream)
+            self._transport(group, self._pack_stream if on_gpu else None)
+            self._unpack()
+        self._halos_current = True
 
     def sync(self):
         self.dom.sync()
@@ -294,10 +351,14 @@ class SlabDomain:
 
 
 def step_local(slabs: Sequence[SlabDomain], n: int = 1):
-    """n steps of a domain whose slabs (rank = list index) are all held by this process:
-    every slab packs its edge planes, every neighbour unpacks them from the sender's buffer,
-    then every slab steps.  Slabs on one stream are ordered by it (nothing waits on the
-    host); otherwise each phase waits for the previous one on every slab's stream."""
+    """n steps of a domain whose slabs (rank = list index) are all held by this process.
+    With domains that have ``step_slab``: the current edge planes are exchanged once if the
+    halos are not current, then per step every slab steps its send planes first and packs
+    them on one shared stream while its other planes step, and every neighbour unpacks them
+    from the sender's buffer once that stream has packed them.  Otherwise every slab packs
+    its edge planes, every neighbour unpacks them, then every slab steps.  Slabs on one
+    stream are ordered by it (nothing waits on the host); otherwise each phase waits for the
+    previous one on every slab's stream."""
     by_rank = {s.plan.rank: s for s in slabs}
     if sorted(by_rank) != list(range(len(slabs))):
         raise ValueError("slabs must be ranks 0 .. n-1 of one cut")
@@ -311,16 +372,46 @@ def step_local(slabs: Sequence[SlabDomain], n: int = 1):
         if not shared:
             for s in slabs:
                 s.sync()
-    for _ in range(int(n)):
+
+    def exchange_all():
         for s in slabs:
             s._pack()
         wait_all()
         for s in slabs:
             s._unpack(sender)
         wait_all()
+    if len(slabs) > 1 and all(hasattr(s.dom, "step_slab") for s in slabs):
+        import torch
+        if not all(s._halos_current for s in slabs):
+            exchange_all()
+        on_gpu = any(t.is_cuda for s in slabs for t in s.bufs.values())
+        pack = None
+        if on_gpu:
+            if slabs[0]._pack_stream is None:
+                slabs[0]._pack_stream = torch.cuda.Stream(
+                    device=next(iter(slabs[0].bufs.values())).device)
+            pack = slabs[0]._pack_stream
+        for _ in range(int(n)):
+            for s in slabs:
+                s._step_sends(pack)
+            if on_gpu:
+                done = pack.record_event()
+                for s in slabs:
+                    s.dom.torch_stream.wait_event(done)
+            wait_all()
+            for s in slabs:
+                s._unpack(sender)
+            wait_all()
+        for s in slabs:
+            s._halos_current = True
+        return
+    for _ in range(int(n)):
+        exchange_all()
         for s in slabs:
             s.dom.step(1)
         wait_all()
+    for s in slabs:
+        s._halos_current = False
 
 
 # ------------------------------------------------ blocks of one continuous-scale domain

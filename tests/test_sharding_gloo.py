@@ -104,6 +104,20 @@ class _StencilDomain:
     def sync(self):
         pass
 
+    def step_slab(self, lo, hi, send_lo=None, send_hi=None, pack_stream=None):
+        """The library's slab step: a step, then the new first / last owned planes packed
+        (direction -1 / +1); the halo planes are left as stale as the library leaves them."""
+        keep_a, keep_g = self.a.copy(), self.g.copy()
+        self.step(1)
+        for z, on in ((0, lo), (self.nz - 1, hi)):
+            if on:
+                self.a[:, z] = keep_a[:, z] - 1          # stale, and visibly so
+                self.g[z] = keep_g[z] - 1
+        if lo:
+            self.pack_plane(1, send_lo, -1)
+        if hi:
+            self.pack_plane(self.nz - 2, send_hi, +1)
+
     def read_field(self, field, dtype=None):
         return self.a.reshape(-1).copy()
 
@@ -139,11 +153,18 @@ def _stencil_reference(a, g, periodic, steps):
     return d.a, d.g
 
 
-def _stencil_slabs(a, g, periodic, world, ranks):
+class _PlainStencilDomain(_StencilDomain):
+    """The stand-in without a slab step: exchange, then a plain step of every plane."""
+    @property
+    def step_slab(self):
+        raise AttributeError("step_slab")
+
+
+def _stencil_slabs(a, g, periodic, world, ranks, plain=False):
     out = []
     for r in ranks:
         s = sharding.SlabDomain(g.shape[::-1], 0.0, rank=r, world=world, periodic=periodic,
-                                make_domain=_StencilDomain)
+                                make_domain=_PlainStencilDomain if plain else _StencilDomain)
         s.dom.a, s.dom.g = s.local(a), s.local(g)
         out.append(s)
     return out
@@ -184,13 +205,18 @@ def test_slab_plan_covers_every_plane_once_with_the_right_halos():
         sharding.slab_ranges(3, 4)
 
 
+@pytest.mark.parametrize("plain", [False, True])
 @pytest.mark.parametrize("world", [1, 2, 3])
 @pytest.mark.parametrize("periodic", [(True, False, True), (False, True, False)])
-def test_local_slabs_reproduce_the_undivided_stencil(world, periodic):
+def test_local_slabs_reproduce_the_undivided_stencil(world, periodic, plain):
+    """Slabs of one process: the pipelined slab step (send planes first, halo planes left
+    stale until the unpack) and, with plain=True, exchange-then-step; stepped in two calls
+    (the pipelined path keeps its halos current between them)."""
     a, g = _stencil_init((9, 5, 6), 7)
     want = _stencil_reference(a, g, periodic, 4)
-    slabs = _stencil_slabs(a, g, periodic, world, range(world))
-    sharding.step_local(slabs, 4)
+    slabs = _stencil_slabs(a, g, periodic, world, range(world), plain)
+    sharding.step_local(slabs, 3)
+    sharding.step_local(slabs, 1)
     got = _owned_stencil(slabs)
     assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
     if world > 1:
