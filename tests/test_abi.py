@@ -80,6 +80,7 @@ def test_library_loads_and_validates_on_host(built):
     assert lib.lbm_step_batch_reduce(None, 1, 1, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_step_batch_reduce_async(None, 1, 1, None, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_plane_bytes(None, 0) == 0
+    assert lib.lbm_step_slab(None, 1, 1, None, None, None) == lbm.LBM_ERR_INVALID_ARG
     for fn in (lib.lbm_pack_plane, lib.lbm_unpack_plane):
         assert fn(None, 0, 0, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_step_phase(None, 0, 0, 1) == lbm.LBM_ERR_INVALID_ARG

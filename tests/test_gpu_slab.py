@@ -214,3 +214,28 @@ def test_two_process_slabs_through_torch_distributed(lib):
         assert p.exitcode == 0
     want = _undivided(_scene((False, True, True)), 6, None, False)
     _assert_same([r[1] for r in res], want)
+
+
+def test_step_slab_argument_checks(lib):
+    """lbm_step_slab refuses a missing or unaligned send buffer for a halo side, a slab with
+    fewer than two owned planes, and domains with refined blocks."""
+    import torch
+    from paper_1807_02284_gb300 import lbm
+    dom = lbm.Domain((8, 6, 6), 0.01, periodic=(True, True, False))
+    nb = dom.plane_bytes(-1)
+    buf = torch.zeros(nb + 16, dtype=torch.uint8, device="cuda")
+    st = dom.lib.lbm_step_slab(dom.handle, 1, 0, None, None, None)
+    assert st == lbm.LBM_ERR_INVALID_ARG
+    st = dom.lib.lbm_step_slab(dom.handle, 1, 0, buf.data_ptr() + 8, None, None)
+    assert st == lbm.LBM_ERR_INVALID_ARG                     # not 16-byte aligned
+    dom.close()
+    thin = lbm.Domain((8, 6, 3), 0.01, periodic=(True, True, False))
+    b2 = torch.zeros(thin.plane_bytes(1), dtype=torch.uint8, device="cuda")
+    st = thin.lib.lbm_step_slab(thin.handle, 1, 1, b2.data_ptr(), b2.data_ptr(), None)
+    assert st == lbm.LBM_ERR_INVALID_ARG                     # one owned plane
+    thin.close()
+    multi = lbm.Domain((16, 16, 16), 0.01)
+    multi.add_scale_block((4.0, 4.0, 4.0), 0.5, (8, 8, 8))
+    st = multi.lib.lbm_step_slab(multi.handle, 0, 0, None, None, None)
+    assert st == lbm.LBM_ERR_UNSUPPORTED
+    multi.close()
