@@ -701,7 +701,8 @@ def run_ours(args):
         roofline["frac_collide_stream_bytes_only"] = step_bytes / (t_dev / K) / 1e9 / peak
     i0 = dom.info(0)
     roofline["launch"] = {"tile": [int(i0.tile[0]), int(i0.tile[1])],
-                          "ctas_per_sm": int(i0.ctas_per_sm)}
+                          "ctas_per_sm": int(i0.ctas_per_sm),
+                          "nodes_per_thread": int(i0.nodes_per_thread)}
 
     # ---- end to end through the public API with host buffers
     E = max(3, min(K, 50))

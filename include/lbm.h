@@ -143,11 +143,16 @@ typedef struct {
   double nu;         /* viscosity in this block's lattice units (nu_0 / h, Sec. 3.2 Eq. 4) */
   int32_t substeps;  /* sub-steps per reference step (1 for s0) */
   int64_t steps;     /* reference steps taken by the domain */
-  int32_t tile[2];   /* x, y extent of the collide-stream thread tile (chosen by autotuning) */
+  int32_t tile[2];   /* x, y extent in nodes of one CTA of the collide-stream kernel (chosen
+                        by autotuning) */
   int32_t ctas_per_sm; /* CTAs per SM the collide-stream kernel's registers are bounded for
-                          (3 or 4, chosen by autotuning together with the tile) */
+                          (chosen by autotuning together with the tile) */
   int32_t parent;      /* a refined block's prior-mapping source (the finest coarser block
                           containing it); -1 for the reference block and far-field blocks */
+  int32_t nodes_per_thread; /* 1: one node per thread (tile[0] x tile[1] threads per CTA,
+                               3 or 4 CTAs per SM); 2: two neighbouring x-nodes per thread
+                               with paired FP32 arithmetic (half the threads, 4 or 5 CTAs
+                               per SM; blocks with an even x-extent) */
 } lbm_block_info;
 
 /* Version of this header's ABI. */

@@ -19,10 +19,61 @@ __global__ void __launch_bounds__(256, MINB) k_step(BlockView v) {
   cell_update<T, IT, ALIGN, WALLS>(v, x, y, z);
 }
 
+// Two nodes (x, x + 1) per thread, x = 2 (thread's column): MINB CTAs of at most 128 threads
+// per SM (128 registers per thread at 4, no spills; 96 at 5, a small spill).
+template <typename T, typename IT, int MINB, bool WALLS>
+__global__ void __launch_bounds__(128, MINB) k_step2(BlockView v) {
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z + v.z_first;
+  if (x >= v.nx || y >= v.ny) return;
+  cell_update_pair<T, IT, WALLS>(v, x, y, z);
+}
+
 bool fits_32bit_index(size_t N) { return 27ull * (unsigned long long)N < 0xFFFFFFFFull; }
+
+template <typename T, typename IT, int MINB>
+static void launch_step2_b(const BlockView& v, dim3 grid, dim3 block, cudaStream_t s) {
+  if (v.walls) k_step2<T, IT, MINB, true><<<grid, block, 0, s>>>(v);
+  else k_step2<T, IT, MINB, false><<<grid, block, 0, s>>>(v);
+}
+
+template <typename T, typename IT>
+static void launch_step2_t(const BlockView& v, dim3 grid, dim3 block, int b, cudaStream_t s) {
+  if (b >= 5) launch_step2_b<T, IT, 5>(v, grid, block, s);
+  else launch_step2_b<T, IT, 4>(v, grid, block, s);
+}
+
+static bool aligned_to(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// The two-node kernel reads and writes aligned pairs of every array: it needs an even nx
+// (then every row, plane and level starts on an even node) and pair-aligned base pointers.
+static bool pair_ok(const BlockView& v, int storage, int bx, int by) {
+  const size_t pe = storage == ST_FP16 ? 4 : 8;
+  return (v.nx % 2) == 0 && bx % 2 == 0 && (bx / 2) * by <= 128 && aligned_to(v.d_in, pe) &&
+         aligned_to(v.d_out, pe) && aligned_to(v.u_in, 8) && aligned_to(v.u_out, 8) &&
+         aligned_to(v.c_in, 8) && aligned_to(v.c_out, 8) && aligned_to(v.flags, 2);
+}
+
+// grid.z = planes; the tile bx x by of nodes becomes bx / 2 x by threads.
+static void launch_step2(const BlockView& v, int storage, int bx, int by, int b, unsigned planes,
+                         cudaStream_t s) {
+  const int tx = bx / 2;
+  dim3 block(tx, by, 1);
+  dim3 grid((v.nx / 2 + tx - 1) / tx, (v.ny + by - 1) / by, planes);
+  const bool i32 = fits_32bit_index(v.N);
+  if (storage == ST_FP16) {
+    if (i32) launch_step2_t<__half, uint32_t>(v, grid, block, b, s);
+    else launch_step2_t<__half, uint64_t>(v, grid, block, b, s);
+  } else {
+    if (i32) launch_step2_t<float, uint32_t>(v, grid, block, b, s);
+    else launch_step2_t<float, uint64_t>(v, grid, block, b, s);
+  }
+}
 
 template <typename T, typename IT, bool ALIGN>
 static void launch_step_t(const BlockView& v, dim3 grid, dim3 block, int minb, cudaStream_t s) {
+  minb = step_scalar_bound(minb);
   if (v.walls) {
     if (minb >= 4) k_step<T, IT, ALIGN, 4, true><<<grid, block, 0, s>>>(v);
     else k_step<T, IT, ALIGN, 3, true><<<grid, block, 0, s>>>(v);
@@ -34,6 +85,10 @@ static void launch_step_t(const BlockView& v, dim3 grid, dim3 block, int minb, c
 
 cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
                         int minb) {
+  if (step_is_pair(minb) && pair_ok(v, storage, bx, by)) {
+    launch_step2(v, storage, bx, by, minb - STEP_PAIR, (unsigned)v.nz, s);
+    return cudaGetLastError();
+  }
   dim3 block(bx, by, 1);
   dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, v.nz);
   const bool i32 = fits_32bit_index(v.N);
@@ -53,6 +108,10 @@ cudaError_t launch_step_planes(const BlockView& v, int storage, int bx, int by, 
   if (count <= 0) return cudaSuccess;
   BlockView w = v;
   w.z_first = z0;
+  if (step_is_pair(minb) && pair_ok(w, storage, bx, by)) {
+    launch_step2(w, storage, bx, by, minb - STEP_PAIR, (unsigned)count, s);
+    return cudaGetLastError();
+  }
   dim3 block(bx, by, 1);
   dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, count);
   const bool i32 = fits_32bit_index(v.N);

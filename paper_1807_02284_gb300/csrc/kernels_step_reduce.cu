@@ -60,7 +60,7 @@ size_t step_reduce_ctas(const BlockView& v, int bx, int by) {
 template <typename T>
 static void launch_step_reduce_t(const BlockView& v, dim3 grid, dim3 block, int minb,
                                  double* partials, cudaStream_t s) {
-  if (minb >= 4) {
+  if (step_scalar_bound(minb) >= 4) {
     if (v.walls) k_step_reduce<T, 4, true><<<grid, block, 0, s>>>(v, partials);
     else k_step_reduce<T, 4, false><<<grid, block, 0, s>>>(v, partials);
   } else {

@@ -169,6 +169,11 @@ __device__ __forceinline__ float scalar_value(const ScalarCell& s) {
   return fmaf(s.tz, b1 - b0, b0);
 }
 
+// Non-positive or non-finite density, or a velocity far outside the lattice's range.
+__device__ __forceinline__ bool unphysical(float drho, float ux, float uy, float uz) {
+  return !(1.0f + drho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 3.0f);
+}
+
 __device__ __forceinline__ void flag_error(int* err, bool bad) {
   const unsigned m = __ballot_sync(__activemask(), bad);
   if (m && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(err, 1);
@@ -319,9 +324,10 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
 
   raw_moments(d);
   const float drho = d[kap(0, 0, 0)];
-  const float inv = fast_rcp(1.0f + drho);
-  const float ux = d[kap(1, 0, 0)] * inv, uy = d[kap(0, 1, 0)] * inv, uz = d[kap(0, 0, 1)] * inv;
-  flag_error(v.err, !(1.0f + drho > 0.0f) || !(fabsf(ux) + fabsf(uy) + fabsf(uz) < 3.0f));
+  const float inv = fast_rcp(__fadd_rn(1.0f, drho));
+  const float ux = __fmul_rn(d[kap(1, 0, 0)], inv), uy = __fmul_rn(d[kap(0, 1, 0)], inv),
+              uz = __fmul_rn(d[kap(0, 0, 1)], inv);
+  flag_error(v.err, unphysical(drho, ux, uy, uz));
   if constexpr (RED) {
     static_assert(!ALIGN, "the fused diagnostics cover plain steps");
     nm->put(drho, d[kap(1, 0, 0)], d[kap(0, 1, 0)], d[kap(0, 0, 1)], inv);
@@ -374,6 +380,106 @@ __device__ __forceinline__ void cell_update(const BlockView& v, int x, int y, in
     __stcs(v.u_out + (2 * N + idx), uz);
     __stcs(v.c_out + idx, src ? v.c_src : scalar_value(sc));
   }
+}
+
+
+// ---- two nodes per thread (k_step2): nodes x and x + 1 of one row, x even, nx even, so that
+// their stored values are aligned pairs.  The pair path covers inner_yz fluid nodes without
+// bounce-back, walls or inflow (almost all nodes of a block); any other pair takes
+// cell_update node by node.  Every value equals cell_update's for the same node: the loads,
+// the lane arithmetic (float2 forms of the same rounded operations) and the stores are the
+// per-node ones, only issued two at a time.
+
+// Pull of the pair: c_x = 0 planes are one aligned pair load; c_x = +1 reads (x - 1, x),
+// c_x = -1 reads (x + 1, x + 2), as two single loads (am0: node x's source x - 1, ap1: node
+// x + 1's source x + 2, both with the face rules; a0: the pair's own index).
+template <typename T, typename IT, int K = 0>
+__device__ __forceinline__ void pull_pair(float2 (&d)[27], const T* __restrict__ din, IT N, IT nx,
+                                          IT nxy, IT am0, IT a0, IT ap1) {
+  if constexpr (K < 27) {
+    constexpr int cx = cxk(K), cy = cyk(K), cz = czk(K);
+    const IT off = (IT)K * N - (IT)cz * nxy - (IT)cy * nx;
+    if constexpr (cx == 0) {
+      d[K] = load_pop2(din + (off + a0));
+    } else if constexpr (cx > 0) {
+      d[K] = make_float2(load_pop(din + (off + am0)), load_pop(din + (off + a0)));
+    } else {
+      d[K] = make_float2(load_pop(din + (off + a0 + 1)), load_pop(din + (off + ap1)));
+    }
+    pull_pair<T, IT, K + 1>(d, din, N, nx, nxy, am0, a0, ap1);
+  }
+}
+
+// grad_norm_inner of both nodes (the y and z differences as aligned pair loads).
+template <typename IT>
+__device__ __forceinline__ float2 grad_norm_pair(const float* __restrict__ U, IT N, IT nx, IT nxy,
+                                                 IT a0, IT am0, IT ap1) {
+  float2 s = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float* Ua = U + (IT)a * N;
+    const float2 c = __ldg(reinterpret_cast<const float2*>(Ua + a0));
+    const float2 dx = vsub(make_float2(c.y, __ldg(Ua + ap1)), make_float2(__ldg(Ua + am0), c.x));
+    const float2 dy = vsub(__ldg(reinterpret_cast<const float2*>(Ua + (a0 + nx))),
+                           __ldg(reinterpret_cast<const float2*>(Ua + (a0 - nx))));
+    const float2 dz = vsub(__ldg(reinterpret_cast<const float2*>(Ua + (a0 + nxy))),
+                           __ldg(reinterpret_cast<const float2*>(Ua + (a0 - nxy))));
+    s = vfma(dx, dx, vfma(dy, dy, vfma(dz, dz, s)));
+  }
+  return make_float2(0.5f * sqrtf(s.x), 0.5f * sqrtf(s.y));
+}
+
+template <typename T, typename IT, bool WALLS>
+__device__ __forceinline__ void cell_update_pair(const BlockView& v, int x, int y, int z) {
+  const IT N = (IT)v.N;
+  const IT nxI = (IT)v.nx, nxyI = (IT)v.nx * (IT)v.ny;
+  const IT row = nxyI * (IT)z + nxI * (IT)y;
+  const IT a0 = row + (IT)x;
+  const unsigned fl2 = __ldg(reinterpret_cast<const unsigned short*>(v.flags + a0));
+  const uint8_t fl0 = (uint8_t)(fl2 & 0xffu), fl1 = (uint8_t)(fl2 >> 8);
+  constexpr uint8_t kNodeWise = F_SOLID | F_INFLOW | F_GHOST | F_NEAR_SOLID | F_WALL | F_OBST_WALL;
+  if (!inner_yz(v, y, z) || ((fl0 | fl1) & kNodeWise)) {
+    cell_update<T, IT, false, WALLS>(v, x, y, z);
+    cell_update<T, IT, false, WALLS>(v, x + 1, y, z);
+    return;
+  }
+  const T* __restrict__ din = static_cast<const T*>(v.d_in);
+  T* __restrict__ dout = static_cast<T*>(v.d_out);
+  const IT am0 = row + (IT)nbr(x, -1, v.nx, v.per[0]);
+  const IT ap1 = row + (IT)nbr(x + 1, 1, v.nx, v.per[0]);
+  float2 d[27];
+  pull_pair<T, IT>(d, din, N, nxI, nxyI, am0, a0, ap1);
+  float2 g_lag = make_float2(0.0f, 0.0f);
+  if (v.rp.adaptive && !v.rp.local) g_lag = grad_norm_pair<IT>(v.u_in, N, nxI, nxyI, a0, am0, ap1);
+
+  raw_moments(d);
+  const float2 drho = d[kap(0, 0, 0)];
+  const float2 inv = make_float2(fast_rcp(__fadd_rn(1.0f, drho.x)), fast_rcp(__fadd_rn(1.0f, drho.y)));
+  const float2 ux = vmul(d[kap(1, 0, 0)], inv), uy = vmul(d[kap(0, 1, 0)], inv),
+               uz = vmul(d[kap(0, 0, 1)], inv);
+  flag_error(v.err, unphysical(drho.x, ux.x, uy.x, uz.x) || unphysical(drho.y, ux.y, uy.y, uz.y));
+
+  const bool src0 = (fl0 & F_SCALAR_SRC) != 0, src1 = (fl1 & F_SCALAR_SRC) != 0;
+  ScalarCell sc0, sc1;
+  if (!src0) sc0 = scalar_corners<IT>(v, x, y, z, ux.x, uy.x, uz.x);
+  if (!src1) sc1 = scalar_corners<IT>(v, x + 1, y, z, ux.y, uy.y, uz.y);
+
+  central_from_raw(d, ux, uy, uz);
+  float2 g = g_lag;
+  if (v.rp.adaptive && v.rp.local) {
+    const float2 ss = local_strain_sq(d, drho, ux, uy, uz);
+    g = make_float2(strain_from_sq(ss.x, drho.x, v.rp.s_nu), strain_from_sq(ss.y, drho.y, v.rp.s_nu));
+  }
+  const KeepT<float2> kf = pair_keep(keep_factors(v.rp, g.x), keep_factors(v.rp, g.y));
+  collide_from_central(d, drho, ux, uy, uz, kf);
+
+#pragma unroll
+  for (int k = 0; k < 27; ++k) store_pop2(dout + ((IT)k * N + a0), d[k]);
+  __stcs(reinterpret_cast<float2*>(v.u_out + a0), ux);
+  __stcs(reinterpret_cast<float2*>(v.u_out + (N + a0)), uy);
+  __stcs(reinterpret_cast<float2*>(v.u_out + (2 * N + a0)), uz);
+  __stcs(reinterpret_cast<float2*>(v.c_out + a0),
+         make_float2(src0 ? v.c_src : scalar_value(sc0), src1 ? v.c_src : scalar_value(sc1)));
 }
 
 }  // namespace lbm

@@ -84,12 +84,60 @@ __device__ __forceinline__ void store_pop(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store_pop(__half* p, float v) {
   __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
 }
+// Two consecutive populations of one plane (p aligned to two elements).
+__device__ __forceinline__ float2 load_pop2(const float* p) {
+  float2 v;
+  asm volatile("ld.global.nc.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 load_pop2(const __half* p) {
+  return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+}
+__device__ __forceinline__ void store_pop2(float* p, float2 v) {
+  *reinterpret_cast<float2*>(p) = v;
+}
+__device__ __forceinline__ void store_pop2(__half* p, float2 v) {
+  const __half2 h = __floats2half2_rn(v.x, v.y);
+  __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&h));
+}
+
+// Lane arithmetic of the collision.  V is float (one node per thread) or float2 (two
+// nodes of a row per thread, the sm_100 paired FP32 instructions); every operation is an
+// explicitly rounded intrinsic (no contraction left to the compiler) and the float2 forms
+// are the float forms per component, so both widths give bit-identical nodes.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as a + (-1) b: the product is exact, so the one rounding is that of the difference
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vneg(float2 a) { return __fmul2_rn(a, make_float2(-1.0f, -1.0f)); }
+template <typename V> __device__ __forceinline__ V vsplat(float c);
+template <> __device__ __forceinline__ float vsplat<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 vsplat<float2>(float c) { return make_float2(c, c); }
 
 // Relaxation "keep" factors 1 - S for the moment groups of the Appendix.
-struct Keep {
-  float nu;      // moments 4..8 (shear / deviatoric stress), S = 1/(3 nu + 1/2)
-  float g[4];    // high-order groups 9..16, 17..22, 23..25, 26
+template <typename V>
+struct KeepT {
+  V nu;      // moments 4..8 (shear / deviatoric stress), S = 1/(3 nu + 1/2)
+  V g[4];    // high-order groups 9..16, 17..22, 23..25, 26
 };
+using Keep = KeepT<float>;
+
+// The keep factors of two nodes as one pair.
+__device__ __forceinline__ KeepT<float2> pair_keep(const Keep& a, const Keep& b) {
+  KeepT<float2> k;
+  k.nu = make_float2(a.nu, b.nu);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) k.g[g] = make_float2(a.g[g], b.g[g]);
+  return k;
+}
 
 struct RelaxParams {
   float s_nu;        // S for moments 4..8
@@ -111,11 +159,11 @@ __device__ __forceinline__ float fast_rcp(float x) {
 // Sec. 4.1: S_i = 1/(3 phi nu'_i + 1/2) for i >= 9 with phi = a min(|grad u|/g_max, 1) + b.
 __device__ __forceinline__ Keep keep_factors(const RelaxParams& rp, float grad_norm) {
   Keep kf;
-  kf.nu = 1.0f - rp.s_nu;
+  kf.nu = __fsub_rn(1.0f, rp.s_nu);
   float phi = 1.0f;
-  if (rp.adaptive) phi = rp.a * fminf(grad_norm * rp.inv_gmax, 1.0f) + rp.b;
+  if (rp.adaptive) phi = __fmaf_rn(rp.a, fminf(__fmul_rn(grad_norm, rp.inv_gmax), 1.0f), rp.b);
 #pragma unroll
-  for (int g = 0; g < 4; ++g) kf.g[g] = 1.0f - fast_rcp(fmaf(phi, rp.nuh3[g], 0.5f));
+  for (int g = 0; g < 4; ++g) kf.g[g] = __fsub_rn(1.0f, fast_rcp(__fmaf_rn(phi, rp.nuh3[g], 0.5f)));
   return kf;
 }
 
@@ -142,134 +190,147 @@ __host__ __device__ constexpr int line_base(int l) {
   return (STRIDE == 1) ? 3 * l : (STRIDE == 3) ? (l % 3) + 9 * (l / 3) : l;
 }
 
-// Raw 3-point moments of one line (slots = velocity -1, 0, +1) -> orders 0, 1, 2.
-template <int STRIDE>
-__device__ __forceinline__ void raw_axis(float (&v)[27]) {
+// Raw 3-point moments of one line (slots = velocity -1, 0, +1) -> orders 0, 1, 2:
+// (a + c) + m, c - a, a + c (three operations per line).
+template <int STRIDE, typename V>
+__device__ __forceinline__ void raw_axis(V (&v)[27]) {
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     const int b = line_base<STRIDE>(l);
-    const float a = v[b], m = v[b + STRIDE], c = v[b + 2 * STRIDE];
-    v[b] = a + m + c;
-    v[b + STRIDE] = c - a;
-    v[b + 2 * STRIDE] = c + a;
+    const V a = v[b], m = v[b + STRIDE], c = v[b + 2 * STRIDE];
+    const V ac = vadd(a, c);
+    v[b] = vadd(ac, m);
+    v[b + STRIDE] = vsub(c, a);
+    v[b + 2 * STRIDE] = ac;
   }
 }
 // Binomial shift of raw moments (orders 0,1,2) to central moments about u.
-template <int STRIDE>
-__device__ __forceinline__ void shift_axis(float (&v)[27], float u) {
+template <int STRIDE, typename V>
+__device__ __forceinline__ void shift_axis(V (&v)[27], V u) {
+  const V nu = vneg(u);
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     const int b = line_base<STRIDE>(l);
-    const float r0 = v[b], r1 = v[b + STRIDE], r2 = v[b + 2 * STRIDE];
-    const float k1 = fmaf(-u, r0, r1);
+    const V r0 = v[b], r1 = v[b + STRIDE], r2 = v[b + 2 * STRIDE];
+    const V k1 = vfma(nu, r0, r1);
     v[b + STRIDE] = k1;
-    v[b + 2 * STRIDE] = fmaf(-u, r1 + k1, r2);
+    v[b + 2 * STRIDE] = vfma(nu, vadd(r1, k1), r2);
   }
 }
 // Central moments about u (orders 0,1,2) back to the three populations of the line: raw
-// moments r1 = u k0 + k1, r2 = u (k1 + r1) + k2, then f(-1) = (r2 - r1)/2, f(0) = k0 - r2,
-// f(+1) = (r2 + r1)/2 (seven operations per line).
-template <int STRIDE>
-__device__ __forceinline__ void inv_axis(float (&v)[27], float u) {
+// moments r1 = u k0 + k1, r2 = u (k1 + r1) + k2, then f(-1) = r2/2 - r1/2, f(0) = k0 - r2,
+// f(+1) = r2/2 + r1/2 (seven operations per line; the halvings are exact).
+template <int STRIDE, typename V>
+__device__ __forceinline__ void inv_axis(V (&v)[27], V u) {
+  const V half = vsplat<V>(0.5f), mhalf = vsplat<V>(-0.5f);
 #pragma unroll
   for (int l = 0; l < 9; ++l) {
     const int b = line_base<STRIDE>(l);
-    const float k0 = v[b], k1 = v[b + STRIDE], k2 = v[b + 2 * STRIDE];
-    const float r1 = fmaf(u, k0, k1);
-    const float r2 = fmaf(u, k1 + r1, k2);
-    const float h1 = 0.5f * r1;
-    v[b] = fmaf(0.5f, r2, -h1);
-    v[b + STRIDE] = k0 - r2;
-    v[b + 2 * STRIDE] = fmaf(0.5f, r2, h1);
+    const V k0 = v[b], k1 = v[b + STRIDE], k2 = v[b + 2 * STRIDE];
+    const V r1 = vfma(u, k0, k1);
+    const V r2 = vfma(u, vadd(k1, r1), k2);
+    const V h2 = vmul(half, r2);
+    v[b] = vfma(mhalf, r1, h2);
+    v[b + STRIDE] = vsub(k0, r2);
+    v[b + 2 * STRIDE] = vfma(half, r1, h2);
   }
 }
 
 // kappa index of orders (a, b, c)
 __host__ __device__ constexpr int kap(int a, int b, int c) { return a + 3 * b + 9 * c; }
 
+// Relaxation of one central moment towards its offset dl with keep factor k.
+template <typename V>
+__device__ __forceinline__ void relax1(V& m, V dl, V k) { m = vfma(k, vsub(m, dl), dl); }
+
 // Relaxation of the central moments of d towards Delta (see header), in place.
 // v holds central moments of the shifted populations about u; keep factors kf; K = 1 - S.
-__device__ __forceinline__ void relax_to_equilibrium(float (&v)[27], float drho, float X,
-                                                     float Y, float Z, const Keep& kf) {
-  const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
-  const float X2 = X * X, Y2 = Y * Y, Z2 = Z * Z;
-#define LBM_RELAX(IDX, DELTA, K)              \
-  {                                           \
-    const float dl = (DELTA);                 \
-    v[IDX] = fmaf((K), v[IDX] - dl, dl);      \
-  }
+template <typename V>
+__device__ __forceinline__ void relax_to_equilibrium(V (&v)[27], V drho, V X, V Y, V Z,
+                                                     const KeepT<V>& kf) {
+  const V third = vsplat<V>(1.0f / 3.0f), ninth = vsplat<V>(1.0f / 9.0f);
+  const V mthird = vsplat<V>(-1.0f / 3.0f);
+  const V X2 = vmul(X, X), Y2 = vmul(Y, Y), Z2 = vmul(Z, Z);
+  const V nX = vneg(X), nY = vneg(Y), ndrho = vneg(drho);
   // second order, off-diagonal (m_4, m_5, m_6): kappa^eq = 0, kappa(w) = u_a u_b
-  LBM_RELAX(kap(1, 1, 0), -X * Y, kf.nu)
-  LBM_RELAX(kap(1, 0, 1), -X * Z, kf.nu)
-  LBM_RELAX(kap(0, 1, 1), -Y * Z, kf.nu)
+  relax1(v[kap(1, 1, 0)], vmul(nX, Y), kf.nu);
+  relax1(v[kap(1, 0, 1)], vmul(nX, Z), kf.nu);
+  relax1(v[kap(0, 1, 1)], vmul(nY, Z), kf.nu);
   // second order, diagonal: kappa^eq = rho/3, kappa(w) = 1/3 + u_a^2
+  const V dr3 = vmul(drho, third);
   {
-    const float dr3 = drho * third;
-    const float ex = dr3 - X2, ey = dr3 - Y2, ez = dr3 - Z2;
-    const float A = v[kap(2, 0, 0)] - ex, B = v[kap(0, 2, 0)] - ey, Cc = v[kap(0, 0, 2)] - ez;
-    const float d1 = kf.nu * (A - B);
-    const float d2 = kf.nu * (A - Cc);
-    const float tr = kf.g[0] * (A + B + Cc);
-    v[kap(2, 0, 0)] = ex + third * (tr + d1 + d2);
-    v[kap(0, 2, 0)] = ey + third * (tr - 2.0f * d1 + d2);
-    v[kap(0, 0, 2)] = ez + third * (tr + d1 - 2.0f * d2);
+    const V ex = vsub(dr3, X2), ey = vsub(dr3, Y2), ez = vsub(dr3, Z2);
+    const V A = vsub(v[kap(2, 0, 0)], ex), B = vsub(v[kap(0, 2, 0)], ey);
+    const V Cc = vsub(v[kap(0, 0, 2)], ez);
+    const V d1 = vmul(kf.nu, vsub(A, B));
+    const V d2 = vmul(kf.nu, vsub(A, Cc));
+    const V tr = vmul(kf.g[0], vadd(vadd(A, B), Cc));
+    const V m2 = vsplat<V>(-2.0f);
+    v[kap(2, 0, 0)] = vfma(third, vadd(vadd(tr, d1), d2), ex);
+    v[kap(0, 2, 0)] = vfma(third, vadd(vfma(m2, d1, tr), d2), ey);
+    v[kap(0, 0, 2)] = vfma(third, vfma(m2, d2, vadd(tr, d1)), ez);
   }
   // third order (m_10 .. m_16)
-  LBM_RELAX(kap(1, 2, 0), X * fmaf(-drho, Y2, third), kf.g[0])
-  LBM_RELAX(kap(1, 0, 2), X * fmaf(-drho, Z2, third), kf.g[0])
-  LBM_RELAX(kap(2, 1, 0), Y * fmaf(-drho, X2, third), kf.g[0])
-  LBM_RELAX(kap(0, 1, 2), Y * fmaf(-drho, Z2, third), kf.g[0])
-  LBM_RELAX(kap(2, 0, 1), Z * fmaf(-drho, X2, third), kf.g[0])
-  LBM_RELAX(kap(0, 2, 1), Z * fmaf(-drho, Y2, third), kf.g[0])
-  LBM_RELAX(kap(1, 1, 1), -drho * X * Y * Z, kf.g[0])
+  relax1(v[kap(1, 2, 0)], vmul(X, vfma(ndrho, Y2, third)), kf.g[0]);
+  relax1(v[kap(1, 0, 2)], vmul(X, vfma(ndrho, Z2, third)), kf.g[0]);
+  relax1(v[kap(2, 1, 0)], vmul(Y, vfma(ndrho, X2, third)), kf.g[0]);
+  relax1(v[kap(0, 1, 2)], vmul(Y, vfma(ndrho, Z2, third)), kf.g[0]);
+  relax1(v[kap(2, 0, 1)], vmul(Z, vfma(ndrho, X2, third)), kf.g[0]);
+  relax1(v[kap(0, 2, 1)], vmul(Z, vfma(ndrho, Y2, third)), kf.g[0]);
+  relax1(v[kap(1, 1, 1)], vmul(vmul(vmul(ndrho, X), Y), Z), kf.g[0]);
+  const V X2Y2 = vmul(X2, Y2), X2Z2 = vmul(X2, Z2), Y2Z2 = vmul(Y2, Z2);
   // fourth order (m_17 .. m_22)
   {
-    const float r3m1 = fmaf(3.0f, drho, 2.0f);  // 3 rho - 1
-    const float dr9 = drho * ninth;
-    LBM_RELAX(kap(2, 2, 0), fmaf(r3m1, X2 * Y2, dr9 - (X2 + Y2) * third), kf.g[1])
-    LBM_RELAX(kap(2, 0, 2), fmaf(r3m1, X2 * Z2, dr9 - (X2 + Z2) * third), kf.g[1])
-    LBM_RELAX(kap(0, 2, 2), fmaf(r3m1, Y2 * Z2, dr9 - (Y2 + Z2) * third), kf.g[1])
-    LBM_RELAX(kap(2, 1, 1), Y * Z * fmaf(r3m1, X2, -third), kf.g[1])
-    LBM_RELAX(kap(1, 2, 1), X * Z * fmaf(r3m1, Y2, -third), kf.g[1])
-    LBM_RELAX(kap(1, 1, 2), X * Y * fmaf(r3m1, Z2, -third), kf.g[1])
+    const V r3m1 = vfma(vsplat<V>(3.0f), drho, vsplat<V>(2.0f));  // 3 rho - 1
+    const V dr9 = vmul(drho, ninth);
+    relax1(v[kap(2, 2, 0)], vfma(r3m1, X2Y2, vfma(vadd(X2, Y2), mthird, dr9)), kf.g[1]);
+    relax1(v[kap(2, 0, 2)], vfma(r3m1, X2Z2, vfma(vadd(X2, Z2), mthird, dr9)), kf.g[1]);
+    relax1(v[kap(0, 2, 2)], vfma(r3m1, Y2Z2, vfma(vadd(Y2, Z2), mthird, dr9)), kf.g[1]);
+    relax1(v[kap(2, 1, 1)], vmul(vmul(Y, Z), vfma(r3m1, X2, mthird)), kf.g[1]);
+    relax1(v[kap(1, 2, 1)], vmul(vmul(X, Z), vfma(r3m1, Y2, mthird)), kf.g[1]);
+    relax1(v[kap(1, 1, 2)], vmul(vmul(X, Y), vfma(r3m1, Z2, mthird)), kf.g[1]);
   }
   // fifth order (m_23 .. m_25)
   {
-    const float o6 = fmaf(-6.0f, drho, -5.0f);  // 1 - 6 rho
-    const float dr3 = drho * third;
-    LBM_RELAX(kap(1, 2, 2), X * fmaf(o6, Y2 * Z2, fmaf(-dr3, Y2 + Z2, ninth)), kf.g[2])
-    LBM_RELAX(kap(2, 1, 2), Y * fmaf(o6, X2 * Z2, fmaf(-dr3, X2 + Z2, ninth)), kf.g[2])
-    LBM_RELAX(kap(2, 2, 1), Z * fmaf(o6, X2 * Y2, fmaf(-dr3, X2 + Y2, ninth)), kf.g[2])
+    const V o6 = vfma(vsplat<V>(-6.0f), drho, vsplat<V>(-5.0f));  // 1 - 6 rho
+    const V ndr3 = vneg(dr3);
+    relax1(v[kap(1, 2, 2)], vmul(X, vfma(o6, Y2Z2, vfma(ndr3, vadd(Y2, Z2), ninth))), kf.g[2]);
+    relax1(v[kap(2, 1, 2)], vmul(Y, vfma(o6, X2Z2, vfma(ndr3, vadd(X2, Z2), ninth))), kf.g[2]);
+    relax1(v[kap(2, 2, 1)], vmul(Z, vfma(o6, X2Y2, vfma(ndr3, vadd(X2, Y2), ninth))), kf.g[2]);
   }
   // sixth order (m_26)
   {
-    const float rho = 1.0f + drho;
-    const float p2 = X2 * Y2 + X2 * Z2 + Y2 * Z2;
-    const float d222 = fmaf(fmaf(10.0f, rho, -1.0f), X2 * Y2 * Z2,
-                            fmaf(rho - third, p2, fmaf(drho, 1.0f / 27.0f, -(X2 + Y2 + Z2) * ninth)));
-    LBM_RELAX(kap(2, 2, 2), d222, kf.g[3])
+    const V rho = vadd(vsplat<V>(1.0f), drho);
+    const V p2 = vadd(vadd(X2Y2, X2Z2), Y2Z2);
+    const V s2 = vadd(vadd(X2, Y2), Z2);
+    const V lo = vfma(drho, vsplat<V>(1.0f / 27.0f), vmul(s2, vsplat<V>(-1.0f / 9.0f)));
+    const V d222 = vfma(vfma(vsplat<V>(10.0f), rho, vsplat<V>(-1.0f)), vmul(X2Y2, Z2),
+                        vfma(vsub(rho, third), p2, lo));
+    relax1(v[kap(2, 2, 2)], d222, kf.g[3]);
   }
-#undef LBM_RELAX
   // orders 0 and 1 (S_0..3 = 0) are left as they are
 }
 
 // Raw moment sweeps: afterwards v[kap(0,0,0)] = rho - 1 and v[kap(1,0,0)] = j_x etc.
-__device__ __forceinline__ void raw_moments(float (&v)[27]) {
+template <typename V>
+__device__ __forceinline__ void raw_moments(V (&v)[27]) {
   raw_axis<1>(v);
   raw_axis<3>(v);
   raw_axis<9>(v);
 }
 
 // Raw moments -> central moments about u (in place).
-__device__ __forceinline__ void central_from_raw(float (&v)[27], float ux, float uy, float uz) {
+template <typename V>
+__device__ __forceinline__ void central_from_raw(V (&v)[27], V ux, V uy, V uz) {
   shift_axis<1>(v, ux);
   shift_axis<3>(v, uy);
   shift_axis<9>(v, uz);
 }
 
 // Relaxation of central moments and the inverse sweeps back to populations (in place).
-__device__ __forceinline__ void collide_from_central(float (&v)[27], float drho, float ux,
-                                                     float uy, float uz, const Keep& kf) {
+template <typename V>
+__device__ __forceinline__ void collide_from_central(V (&v)[27], V drho, V ux, V uy, V uz,
+                                                     const KeepT<V>& kf) {
   relax_to_equilibrium(v, drho, ux, uy, uz, kf);
   inv_axis<9>(v, uz);
   inv_axis<3>(v, uy);
@@ -278,8 +339,9 @@ __device__ __forceinline__ void collide_from_central(float (&v)[27], float drho,
 
 // Collision of shifted populations given their raw moments (from raw_moments) and u:
 // raw -> central, relax towards equilibrium, back to populations (in place).
-__device__ __forceinline__ void collide_from_raw(float (&v)[27], float drho, float ux, float uy,
-                                                 float uz, const Keep& kf) {
+template <typename V>
+__device__ __forceinline__ void collide_from_raw(V (&v)[27], V drho, V ux, V uy, V uz,
+                                                 const KeepT<V>& kf) {
   central_from_raw(v, ux, uy, uz);
   collide_from_central(v, drho, ux, uy, uz, kf);
 }
@@ -287,19 +349,26 @@ __device__ __forceinline__ void collide_from_raw(float (&v)[27], float drho, flo
 // |grad u| from a node's central moments (of the shifted populations, before relaxation):
 // the non-equilibrium second moments Pi = kappa - Delta give the strain rate through
 // Pi^(1) = -2 c_s^2 rho S_hat / S (Sec. 4.2.1, c_s^2 = 1/3); returns sqrt(2 S_hat : S_hat).
+template <typename V>
+__device__ __forceinline__ V local_strain_sq(const V (&v)[27], V drho, V X, V Y, V Z) {
+  const V dr3 = vmul(drho, vsplat<V>(1.0f / 3.0f));
+  const V pxx = vsub(v[kap(2, 0, 0)], vsub(dr3, vmul(X, X)));
+  const V pyy = vsub(v[kap(0, 2, 0)], vsub(dr3, vmul(Y, Y)));
+  const V pzz = vsub(v[kap(0, 0, 2)], vsub(dr3, vmul(Z, Z)));
+  const V pxy = vfma(X, Y, v[kap(1, 1, 0)]);
+  const V pxz = vfma(X, Z, v[kap(1, 0, 1)]);
+  const V pyz = vfma(Y, Z, v[kap(0, 1, 1)]);
+  const V dg = vfma(pxx, pxx, vfma(pyy, pyy, vmul(pzz, pzz)));
+  const V od = vfma(pxy, pxy, vfma(pxz, pxz, vmul(pyz, pyz)));
+  return vfma(vsplat<V>(2.0f), od, dg);
+}
+__device__ __forceinline__ float strain_from_sq(float ss, float drho, float s_nu) {
+  const float scale = __fdiv_rn(__fmul_rn(1.5f, s_nu), __fadd_rn(1.0f, drho));
+  return __fmul_rn(scale, sqrtf(__fmul_rn(2.0f, ss)));
+}
 __device__ __forceinline__ float local_strain(const float (&v)[27], float drho, float X, float Y,
                                               float Z, float s_nu) {
-  const float dr3 = drho * (1.0f / 3.0f);
-  const float pxx = v[kap(2, 0, 0)] - (dr3 - X * X);
-  const float pyy = v[kap(0, 2, 0)] - (dr3 - Y * Y);
-  const float pzz = v[kap(0, 0, 2)] - (dr3 - Z * Z);
-  const float pxy = v[kap(1, 1, 0)] + X * Y;
-  const float pxz = v[kap(1, 0, 1)] + X * Z;
-  const float pyz = v[kap(0, 1, 1)] + Y * Z;
-  const float ss = fmaf(pxx, pxx, fmaf(pyy, pyy, pzz * pzz)) +
-                   2.0f * fmaf(pxy, pxy, fmaf(pxz, pxz, pyz * pyz));
-  const float scale = 1.5f * s_nu / (1.0f + drho);
-  return scale * sqrtf(2.0f * ss);
+  return strain_from_sq(local_strain_sq(v, drho, X, Y, Z), drho, s_nu);
 }
 
 // Equilibrium (shifted) for given rho, u.

@@ -88,6 +88,14 @@ struct WorkItem {
 };
 
 // ---- kernels_step.cu
+// Register-bound code of the collide-stream launch (chosen by autotuning with the tile
+// bx x by of nodes): 3 or 4 = CTAs of bx by one-node threads per SM; STEP_PAIR + b = the
+// two-node kernel k_step2 (bx / 2 x by threads per CTA, b CTAs per SM), which needs an even
+// nx and falls back to the one-node kernel (bound 4) otherwise.  Kernels without a two-node
+// form (fused diagnostics, fused alignment) take step_scalar_bound of the code.
+constexpr int STEP_PAIR = 16;
+inline bool step_is_pair(int minb) { return minb >= STEP_PAIR; }
+inline int step_scalar_bound(int minb) { return minb >= STEP_PAIR ? 4 : minb; }
 cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
                         int minb = 3);
 cudaError_t launch_step_align(const BlockView& v, int bx, int by, cudaStream_t s, int minb = 3);

@@ -672,8 +672,10 @@ lbm_status lbm_get_block_info(const lbm_domain* dom, int32_t block_id, lbm_block
   info->steps = dom->steps;
   info->tile[0] = B.bx;
   info->tile[1] = B.by;
-  info->ctas_per_sm = B.minb;
+  const bool pair = step_is_pair(B.minb) && B.nx % 2 == 0;
+  info->ctas_per_sm = pair ? B.minb - STEP_PAIR : step_scalar_bound(B.minb);
   info->parent = (block_id == 0 || B.far) ? -1 : B.parent;
+  info->nodes_per_thread = pair ? 2 : 1;
   return LBM_OK;
 }
 

@@ -51,7 +51,8 @@ LBM_GRAD_LAGGED, LBM_GRAD_LOCAL = 0, 1
 class lbm_block_info(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("origin", C.c_double * 3), ("h", C.c_double),
                 ("nu", C.c_double), ("substeps", C.c_int32), ("steps", C.c_int64),
-                ("tile", C.c_int32 * 2), ("ctas_per_sm", C.c_int32), ("parent", C.c_int32)]
+                ("tile", C.c_int32 * 2), ("ctas_per_sm", C.c_int32), ("parent", C.c_int32),
+                ("nodes_per_thread", C.c_int32)]
 
 
 INFLOW_RECORD = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"),
