@@ -151,7 +151,7 @@ typedef struct {
                           containing it); -1 for the reference block and far-field blocks */
   int32_t nodes_per_thread; /* 1: one node per thread (tile[0] x tile[1] threads per CTA,
                                3 or 4 CTAs per SM); 2: two neighbouring x-nodes per thread
-                               with paired FP32 arithmetic (half the threads, 4 or 5 CTAs
+                               with paired FP32 arithmetic (half the threads, 4 to 6 CTAs
                                per SM; blocks with an even x-extent) */
 } lbm_block_info;
 

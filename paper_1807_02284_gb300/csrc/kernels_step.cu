@@ -20,14 +20,20 @@ __global__ void __launch_bounds__(256, MINB) k_step(BlockView v) {
 }
 
 // Two nodes (x, x + 1) per thread, x = 2 (thread's column): MINB CTAs of at most 128 threads
-// per SM (128 registers per thread at 4, no spills; 96 at 5, a small spill).
+// per SM (128 registers per thread at 4; 96 at 5 and 80 at 6, with small spills).
 template <typename T, typename IT, int MINB, bool WALLS>
 __global__ void __launch_bounds__(128, MINB) k_step2(BlockView v) {
   const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z + v.z_first;
   if (x >= v.nx || y >= v.ny) return;
-  cell_update_pair<T, IT, WALLS>(v, x, y, z);
+  if constexpr (pair_corners_async<T>()) {
+    __shared__ float corners[16][128];     // each thread's scalar corners, column t
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    cell_update_pair<T, IT, WALLS>(v, x, y, z, &corners[0][t], 128);
+  } else {
+    cell_update_pair<T, IT, WALLS>(v, x, y, z, nullptr, 0);
+  }
 }
 
 bool fits_32bit_index(size_t N) { return 27ull * (unsigned long long)N < 0xFFFFFFFFull; }
@@ -40,7 +46,8 @@ static void launch_step2_b(const BlockView& v, dim3 grid, dim3 block, cudaStream
 
 template <typename T, typename IT>
 static void launch_step2_t(const BlockView& v, dim3 grid, dim3 block, int b, cudaStream_t s) {
-  if (b >= 5) launch_step2_b<T, IT, 5>(v, grid, block, s);
+  if (b >= 6) launch_step2_b<T, IT, 6>(v, grid, block, s);
+  else if (b == 5) launch_step2_b<T, IT, 5>(v, grid, block, s);
   else launch_step2_b<T, IT, 4>(v, grid, block, s);
 }
 

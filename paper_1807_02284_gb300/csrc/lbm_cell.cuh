@@ -429,8 +429,56 @@ __device__ __forceinline__ float2 grad_norm_pair(const float* __restrict__ U, IT
   return make_float2(0.5f * sqrtf(s.x), 0.5f * sqrtf(s.y));
 }
 
+// The departure cell's eight scalar corners of one node, copied asynchronously (cp.async,
+// 4 bytes each, through L1) into this thread's shared-memory slots slot[i * stride]: the
+// values are in flight through the collision without holding registers.
+template <typename IT>
+__device__ __forceinline__ void scalar_corners_async(const BlockView& v, int x, int y, int z,
+                                                     float ux, float uy, float uz, float* slot,
+                                                     int stride) {
+  const Axis1 ax = sl_axis(x, ux, v.nx, v.per[0]);
+  const Axis1 ay = sl_axis(y, uy, v.ny, v.per[1]);
+  const Axis1 az = sl_axis(z, uz, v.nz, v.per[2]);
+  const IT nx = (IT)v.nx, nxy = (IT)v.nx * (IT)v.ny;
+  const IT z0 = nxy * (IT)az.i0, z1 = nxy * (IT)az.i1, y0 = nx * (IT)ay.i0, y1 = nx * (IT)ay.i1;
+  const IT x0 = (IT)ax.i0, x1 = (IT)ax.i1;
+  const IT src[8] = {z0 + y0 + x0, z0 + y0 + x1, z0 + y1 + x0, z0 + y1 + x1,
+                     z1 + y0 + x0, z1 + y0 + x1, z1 + y1 + x0, z1 + y1 + x1};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(slot + i * stride);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(v.c_in + src[i])
+                 : "memory");
+  }
+}
+
+// scalar_value of the corners copied by scalar_corners_async (after cp.async.wait_group);
+// the weights are recomputed from the same velocity.
+__device__ __forceinline__ float scalar_value_slots(const BlockView& v, int x, int y, int z,
+                                                    float ux, float uy, float uz,
+                                                    const float* slot, int stride) {
+  ScalarCell s;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s.c[i] = slot[i * stride];
+  s.tx = sl_axis(x, ux, v.nx, v.per[0]).t;
+  s.ty = sl_axis(y, uy, v.ny, v.per[1]).t;
+  s.tz = sl_axis(z, uz, v.nz, v.per[2]).t;
+  return scalar_value(s);
+}
+
+// FP16 storage takes the scalar corners through shared memory: its pair kernel is bound by
+// the registers that hold loads in flight (occupancy), and without the corners' 22 live
+// registers it runs at 5 CTAs per SM without spills (256^3 plume: 26.7 -> 27.4 GLUPS).  The
+// FP32 pair kernel is bound by DRAM bandwidth and runs faster with the corners in registers
+// (24.9 against 23.8 GLUPS).
+template <typename T>
+constexpr bool pair_corners_async() { return sizeof(T) == 2; }
+
+// slot: this thread's 16 shared-memory floats (slot[i * stride], i < 16) for the corners
+// when pair_corners_async<T>(), unused otherwise.
 template <typename T, typename IT, bool WALLS>
-__device__ __forceinline__ void cell_update_pair(const BlockView& v, int x, int y, int z) {
+__device__ __forceinline__ void cell_update_pair(const BlockView& v, int x, int y, int z,
+                                                 float* slot, int stride) {
   const IT N = (IT)v.N;
   const IT nxI = (IT)v.nx, nxyI = (IT)v.nx * (IT)v.ny;
   const IT row = nxyI * (IT)z + nxI * (IT)y;
@@ -460,9 +508,16 @@ __device__ __forceinline__ void cell_update_pair(const BlockView& v, int x, int 
   flag_error(v.err, unphysical(drho.x, ux.x, uy.x, uz.x) || unphysical(drho.y, ux.y, uy.y, uz.y));
 
   const bool src0 = (fl0 & F_SCALAR_SRC) != 0, src1 = (fl1 & F_SCALAR_SRC) != 0;
+  constexpr bool kAsync = pair_corners_async<T>();
   ScalarCell sc0, sc1;
-  if (!src0) sc0 = scalar_corners<IT>(v, x, y, z, ux.x, uy.x, uz.x);
-  if (!src1) sc1 = scalar_corners<IT>(v, x + 1, y, z, ux.y, uy.y, uz.y);
+  if constexpr (kAsync) {
+    if (!src0) scalar_corners_async<IT>(v, x, y, z, ux.x, uy.x, uz.x, slot, stride);
+    if (!src1) scalar_corners_async<IT>(v, x + 1, y, z, ux.y, uy.y, uz.y, slot + 8 * stride, stride);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  } else {
+    if (!src0) sc0 = scalar_corners<IT>(v, x, y, z, ux.x, uy.x, uz.x);
+    if (!src1) sc1 = scalar_corners<IT>(v, x + 1, y, z, ux.y, uy.y, uz.y);
+  }
 
   central_from_raw(d, ux, uy, uz);
   float2 g = g_lag;
@@ -478,8 +533,16 @@ __device__ __forceinline__ void cell_update_pair(const BlockView& v, int x, int 
   __stcs(reinterpret_cast<float2*>(v.u_out + a0), ux);
   __stcs(reinterpret_cast<float2*>(v.u_out + (N + a0)), uy);
   __stcs(reinterpret_cast<float2*>(v.u_out + (2 * N + a0)), uz);
-  __stcs(reinterpret_cast<float2*>(v.c_out + a0),
-         make_float2(src0 ? v.c_src : scalar_value(sc0), src1 ? v.c_src : scalar_value(sc1)));
+  float c0 = v.c_src, c1 = v.c_src;
+  if constexpr (kAsync) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!src0) c0 = scalar_value_slots(v, x, y, z, ux.x, uy.x, uz.x, slot, stride);
+    if (!src1) c1 = scalar_value_slots(v, x + 1, y, z, ux.y, uy.y, uz.y, slot + 8 * stride, stride);
+  } else {
+    if (!src0) c0 = scalar_value(sc0);
+    if (!src1) c1 = scalar_value(sc1);
+  }
+  __stcs(reinterpret_cast<float2*>(v.c_out + a0), make_float2(c0, c1));
 }
 
 }  // namespace lbm

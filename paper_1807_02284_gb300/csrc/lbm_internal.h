@@ -90,9 +90,9 @@ struct WorkItem {
 // ---- kernels_step.cu
 // Register-bound code of the collide-stream launch (chosen by autotuning with the tile
 // bx x by of nodes): 3 or 4 = CTAs of bx by one-node threads per SM; STEP_PAIR + b = the
-// two-node kernel k_step2 (bx / 2 x by threads per CTA, b CTAs per SM), which needs an even
-// nx and falls back to the one-node kernel (bound 4) otherwise.  Kernels without a two-node
-// form (fused diagnostics, fused alignment) take step_scalar_bound of the code.
+// two-node kernel k_step2 (bx / 2 x by threads per CTA, b = 4, 5 or 6 CTAs per SM), which
+// needs an even nx and falls back to the one-node kernel (bound 4) otherwise.  Kernels
+// without a two-node form (fused diagnostics, fused alignment) take step_scalar_bound.
 constexpr int STEP_PAIR = 16;
 inline bool step_is_pair(int minb) { return minb >= STEP_PAIR; }
 inline int step_scalar_bound(int minb) { return minb >= STEP_PAIR ? 4 : minb; }

@@ -47,7 +47,7 @@ void lbm_domain::pick_tiles(int b) {
   if (const char* env = std::getenv("LBM_TILE")) {  // "bx,by[,minb]" forces a launch shape
     int bx = 0, by = 0, mb = 3;
     const int n = std::sscanf(env, "%d,%d,%d", &bx, &by, &mb);
-    const bool mb_ok = mb == 3 || mb == 4 || mb == STEP_PAIR + 4 || mb == STEP_PAIR + 5;
+    const bool mb_ok = mb == 3 || mb == 4 || (mb >= STEP_PAIR + 4 && mb <= STEP_PAIR + 6);
     if (n >= 2 && bx > 0 && by > 0 && bx * by <= 256 && bx % 32 == 0 && mb_ok) {
       B.bx = bx;
       B.by = by;
@@ -76,8 +76,8 @@ lbm_status lbm_domain::autotune_tiles(int b) {
     }
   const int cand[][2] = {{32, 8}, {64, 4}, {128, 2}, {256, 1}, {32, 4}, {64, 2}, {128, 1}};
   // bound codes: one-node kernel at 3 or 4 CTAs of the tile per SM, then (even nx) the
-  // two-node kernel at 4 or 5 CTAs of half the threads, on tiles of at least 64 x-nodes
-  const int bounds[] = {3, 4, STEP_PAIR + 4, STEP_PAIR + 5};
+  // two-node kernel at 4, 5 or 6 CTAs of half the threads, on tiles of at least 64 x-nodes
+  const int bounds[] = {3, 4, STEP_PAIR + 4, STEP_PAIR + 5, STEP_PAIR + 6};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "event");
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(cudaGetLastError(), "event"); }

@@ -2,8 +2,8 @@
 FP32 arithmetic) against the one-node kernel and the FP64 oracle, through the C-ABI.
 
 The launch shape is forced with LBM_TILE ("bx,by,code": code 3 or 4 = one-node kernel,
-20 or 21 = two-node kernel with 4 or 5 CTAs per SM), read when a block is created.  Every
-launch shape computes the same values, so the two kernels must agree bit for bit on
+20, 21 or 22 = two-node kernel with 4, 5 or 6 CTAs per SM), read when a block is created.
+Every launch shape computes the same values, so the two kernels must agree bit for bit on
 populations, velocity and scalar, for every kind of node the pair path hands back to the
 one-node update (obstacle voxels and their neighbours, inflow, faces, walls, scalar
 sources) and for both storage types and gradient modes."""
@@ -16,7 +16,7 @@ from tests.helpers import gpu_domain, gpu_state, max_err, oracle_params, oracle_
 
 pytestmark = pytest.mark.gpu
 
-ONE_NODE, PAIR4, PAIR5 = "64,4,3", "64,4,20", "128,2,21"
+ONE_NODE, PAIR4, PAIR5, PAIR6 = "64,4,3", "64,4,20", "128,2,21", "256,1,22"
 
 SCENES = {
     "open_sphere_inflow": dict(dims=(46, 33, 21), seed=2, periodic=(False, False, False),
@@ -67,7 +67,7 @@ def test_pair_kernel_is_bit_identical(lib, monkeypatch, name, storage):
     sc = _with_scalar_sources(synth.random_scene(**SCENES[name]), 7)
     ref = _run(monkeypatch, ONE_NODE, sc, 6, storage)
     assert ref[0].nodes_per_thread == 1 and ref[0].ctas_per_sm == 3
-    for tile, bound in ((PAIR4, 4), (PAIR5, 5)):
+    for tile, bound in ((PAIR4, 4), (PAIR5, 5), (PAIR6, 6)):
         got = _run(monkeypatch, tile, sc, 6, storage)
         assert got[0].nodes_per_thread == 2 and got[0].ctas_per_sm == bound
         _assert_identical(ref, got, f"{name} {storage} {tile}")
