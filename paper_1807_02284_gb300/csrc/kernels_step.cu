@@ -55,7 +55,7 @@ static bool aligned_to(const void* p, size_t a) { return ((uintptr_t)p % a) == 0
 
 // The two-node kernel reads and writes aligned pairs of every array: it needs an even nx
 // (then every row, plane and level starts on an even node) and pair-aligned base pointers.
-static bool pair_ok(const BlockView& v, int storage, int bx, int by) {
+bool step_pair_ok(const BlockView& v, int storage, int bx, int by) {
   const size_t pe = storage == ST_FP16 ? 4 : 8;
   return (v.nx % 2) == 0 && bx % 2 == 0 && (bx / 2) * by <= 128 && aligned_to(v.d_in, pe) &&
          aligned_to(v.d_out, pe) && aligned_to(v.u_in, 8) && aligned_to(v.u_out, 8) &&
@@ -92,7 +92,7 @@ static void launch_step_t(const BlockView& v, dim3 grid, dim3 block, int minb, c
 
 cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
                         int minb) {
-  if (step_is_pair(minb) && pair_ok(v, storage, bx, by)) {
+  if (step_is_pair(minb) && step_pair_ok(v, storage, bx, by)) {
     launch_step2(v, storage, bx, by, minb - STEP_PAIR, (unsigned)v.nz, s);
     return cudaGetLastError();
   }
@@ -115,7 +115,7 @@ cudaError_t launch_step_planes(const BlockView& v, int storage, int bx, int by, 
   if (count <= 0) return cudaSuccess;
   BlockView w = v;
   w.z_first = z0;
-  if (step_is_pair(minb) && pair_ok(w, storage, bx, by)) {
+  if (step_is_pair(minb) && step_pair_ok(w, storage, bx, by)) {
     launch_step2(w, storage, bx, by, minb - STEP_PAIR, (unsigned)count, s);
     return cudaGetLastError();
   }

@@ -259,7 +259,8 @@ struct NodeMomentsOut {
     nm[2 * stride] = jx;
     nm[3 * stride] = jy;
     nm[4 * stride] = jz;
-    nm[5 * stride] = 0.5f * (jx * jx + jy * jy + jz * jz) * inv_rho;
+    const float jj = __fmaf_rn(jz, jz, __fmaf_rn(jy, jy, __fmul_rn(jx, jx)));
+    nm[5 * stride] = __fmul_rn(__fmul_rn(0.5f, jj), inv_rho);   // explicit: one value per node
   }
 };
 
@@ -475,10 +476,13 @@ template <typename T>
 constexpr bool pair_corners_async() { return sizeof(T) == 2; }
 
 // slot: this thread's 16 shared-memory floats (slot[i * stride], i < 16) for the corners
-// when pair_corners_async<T>(), unused otherwise.
-template <typename T, typename IT, bool WALLS>
+// when pair_corners_async<T>(), unused otherwise.  RED: the two nodes' moments go through
+// nm0 and nm1 as cell_update's RED form writes them.
+template <typename T, typename IT, bool WALLS, bool RED = false>
 __device__ __forceinline__ void cell_update_pair(const BlockView& v, int x, int y, int z,
-                                                 float* slot, int stride) {
+                                                 float* slot, int stride,
+                                                 const NodeMomentsOut* nm0 = nullptr,
+                                                 const NodeMomentsOut* nm1 = nullptr) {
   const IT N = (IT)v.N;
   const IT nxI = (IT)v.nx, nxyI = (IT)v.nx * (IT)v.ny;
   const IT row = nxyI * (IT)z + nxI * (IT)y;
@@ -487,8 +491,8 @@ __device__ __forceinline__ void cell_update_pair(const BlockView& v, int x, int 
   const uint8_t fl0 = (uint8_t)(fl2 & 0xffu), fl1 = (uint8_t)(fl2 >> 8);
   constexpr uint8_t kNodeWise = F_SOLID | F_INFLOW | F_GHOST | F_NEAR_SOLID | F_WALL | F_OBST_WALL;
   if (!inner_yz(v, y, z) || ((fl0 | fl1) & kNodeWise)) {
-    cell_update<T, IT, false, WALLS>(v, x, y, z);
-    cell_update<T, IT, false, WALLS>(v, x + 1, y, z);
+    cell_update<T, IT, false, WALLS, RED>(v, x, y, z, nm0);
+    cell_update<T, IT, false, WALLS, RED>(v, x + 1, y, z, nm1);
     return;
   }
   const T* __restrict__ din = static_cast<const T*>(v.d_in);
@@ -506,6 +510,11 @@ __device__ __forceinline__ void cell_update_pair(const BlockView& v, int x, int 
   const float2 ux = vmul(d[kap(1, 0, 0)], inv), uy = vmul(d[kap(0, 1, 0)], inv),
                uz = vmul(d[kap(0, 0, 1)], inv);
   flag_error(v.err, unphysical(drho.x, ux.x, uy.x, uz.x) || unphysical(drho.y, ux.y, uy.y, uz.y));
+  if constexpr (RED) {
+    const float2 jx = d[kap(1, 0, 0)], jy = d[kap(0, 1, 0)], jz = d[kap(0, 0, 1)];
+    nm0->put(drho.x, jx.x, jy.x, jz.x, inv.x);
+    nm1->put(drho.y, jx.y, jy.y, jz.y, inv.y);
+  }
 
   const bool src0 = (fl0 & F_SCALAR_SRC) != 0, src1 = (fl1 & F_SCALAR_SRC) != 0;
   constexpr bool kAsync = pair_corners_async<T>();

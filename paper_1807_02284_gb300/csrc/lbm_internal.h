@@ -96,6 +96,9 @@ struct WorkItem {
 constexpr int STEP_PAIR = 16;
 inline bool step_is_pair(int minb) { return minb >= STEP_PAIR; }
 inline int step_scalar_bound(int minb) { return minb >= STEP_PAIR ? 4 : minb; }
+// Whether the two-node kernels can run this view with the node tile bx x by (even nx,
+// pair-aligned arrays, at most 128 threads).
+bool step_pair_ok(const BlockView& v, int storage, int bx, int by);
 cudaError_t launch_step(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
                         int minb = 3);
 cudaError_t launch_step_align(const BlockView& v, int bx, int by, cudaStream_t s, int minb = 3);

@@ -118,3 +118,31 @@ def test_pair_kernel_matches_oracle(lib, monkeypatch):
     eu, ef, ec = max_err(u, st.u.numpy()), max_err(f, st.f.numpy()), max_err(c, st.c.numpy())
     print(f"pair kernel: |du|={eu:.2e} (max|u| {umax:.3f}) |df|={ef:.2e} |dc|={ec:.2e}")
     assert eu <= 1e-5 * umax and ef <= 2e-7 and ec <= 1e-6
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("walls", [False, True])
+def test_pair_step_reduce_is_bit_identical(lib, monkeypatch, storage, walls):
+    """lbm_step_reduce with the two-node fused-diagnostics kernel: on the same node tile it
+    writes the same CTA records as the one-node kernel, so the five values and the stored
+    state agree bit for bit (the records, and so the last bits of the values, follow the
+    tile; the state does not)."""
+    from paper_1807_02284_gb300 import lbm
+    sc = _with_scalar_sources(synth.random_scene(**SCENES["open_sphere_inflow"]), 5)
+
+    def run(tile):
+        monkeypatch.setenv("LBM_TILE", tile)
+        dom = gpu_domain(sc, storage=storage)
+        if walls:
+            dom.set_walls((False, False, True, True, True, True), obstacles=True)
+        vals = [dom.step_reduce(2), dom.step_reduce(1)]
+        f, u, c = gpu_state(dom, sc.blocks[0].shape_zyx, dtype=lbm.LBM_F32)
+        dom.close()
+        return vals, (f, u, c)
+
+    for one, pair in ((ONE_NODE, PAIR4), ("128,2,4", PAIR5)):
+        ref, got = run(one), run(pair)
+        for a, b in zip(ref[0], got[0]):
+            assert np.array_equal(a, b), f"{pair}: {a} vs {b}"
+        for name, x, y in zip("fuc", ref[1], got[1]):
+            assert np.array_equal(x, y), f"{pair}: {name} differs"
