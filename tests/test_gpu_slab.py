@@ -239,3 +239,21 @@ def test_step_slab_argument_checks(lib):
     st = multi.lib.lbm_step_slab(multi.handle, 0, 0, None, None, None)
     assert st == lbm.LBM_ERR_UNSUPPORTED
     multi.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_slabs_on_the_two_node_kernel_reproduce_the_one_node_domain(lib, monkeypatch, storage):
+    """The slab steps (send planes first, then the rest, as plane ranges) on the two-node
+    kernel against the undivided domain on the one-node kernel, bit for bit."""
+    from paper_1807_02284_gb300 import sharding
+    sc = _scene((False, True, True))
+    monkeypatch.setenv("LBM_TILE", "64,4,3")
+    want = _undivided(sc, 7, None, False, storage=storage)
+    monkeypatch.setenv("LBM_TILE", "64,4,20")
+    slabs = [_slab(sc, r, 2, None, False, storage=storage) for r in range(2)]
+    assert slabs[0].dom.info(0).nodes_per_thread == 2
+    sharding.step_local(slabs, 7)
+    parts = [_owned(s) for s in slabs]
+    for s in slabs:
+        s.close()
+    _assert_same(parts, want)
