@@ -4,12 +4,35 @@
 
 namespace lbm {
 
+// End of a fused-diagnostics CTA: each warp has written the sums of its gpw 32-node groups to
+// swarp (lane 0); the last warp to get here (shared-memory counter `done`, zeroed before
+// any warp counts) adds the nwarps * gpw group sums in order and stores the CTA's record of
+// 8 doubles (6 sums, 2 zeros).  No warp waits for the others' updates.
+__device__ __forceinline__ void finish_cta_record(float (*swarp)[6], unsigned& done, int lane,
+                                                  int nwarps, int gpw, double* partials) {
+  unsigned last = 0u;
+  if (lane == 0) {
+    __threadfence_block();
+    last = atomicAdd(&done, 1u) == (unsigned)(nwarps - 1);
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last && lane < 8) {
+    __threadfence_block();
+    const volatile float* sv = &swarp[0][0];
+    float s = 0.0f;
+    if (lane < 6)
+      for (int k = 0; k < nwarps * gpw; ++k) s += sv[k * 6 + lane];
+    const size_t cta = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    partials[cta * 8 + lane] = (double)s;
+  }
+}
+
 // A step that also sums the diagnostics of the state it stores (lbm_step_reduce): every node
 // writes its moments into its warp's shared-memory columns as soon as they are known, so
 // nothing is held through the collision; after the update each warp reads its nodes' six
 // values back and sums them with a shuffle tree (six independent chains, a short tail at
-// the end of every warp's life), and once every warp is done warp 0 adds the warps' sums in
-// order and stores one record of 8 doubles (6 sums, 2 unused: two whole 32-byte sectors) at
+// the end of every warp's life), and the last warp to finish adds the warps' sums in order
+// and stores one record of 8 doubles (6 sums, 2 unused: two whole 32-byte sectors) at
 // partials[cta * 8 + value].  All of it in FP32 (FP64's issue rate on this part
 // is a small fraction of FP32's); the records are summed in FP64 afterwards, in a fixed
 // order.  Same populations, velocity and scalar as k_step.
@@ -17,6 +40,7 @@ template <typename T, int MINB, bool WALLS>
 __global__ void __launch_bounds__(256, MINB) k_step_reduce(BlockView v, double* partials) {
   __shared__ float snm[8][6][32];
   __shared__ float swarp[8][6];
+  __shared__ unsigned done;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -25,6 +49,8 @@ __global__ void __launch_bounds__(256, MINB) k_step_reduce(BlockView v, double* 
   float(*col)[32] = snm[w];
 #pragma unroll
   for (int i = 0; i < 6; ++i) col[i][lane] = 0.0f;
+  if (t == 0) done = 0u;
+  __syncthreads();                          // the counter is set before any warp counts
   const NodeMomentsOut out{&col[0][lane], 32};
   if (x < v.nx && y < v.ny) cell_update<T, uint32_t, false, WALLS, true>(v, x, y, z, &out);
   __syncwarp();
@@ -39,37 +65,34 @@ __global__ void __launch_bounds__(256, MINB) k_step_reduce(BlockView v, double* 
 #pragma unroll
     for (int i = 0; i < 6; ++i) swarp[w][i] = val[i];
   }
-  __syncthreads();
-  if (t < 8) {
-    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-    float s = 0.0f;
-    if (t < 6)
-      for (int k = 0; k < nw; ++k) s += swarp[k][t];
-    const size_t cta = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-    partials[cta * 8 + t] = (double)s;
-  }
+  finish_cta_record(swarp, done, lane, (blockDim.x * blockDim.y + 31) >> 5, 1, partials);
 }
 
 // k_step_reduce with two nodes per thread (k_step2's update): the CTA covers the same bx x by
-// nodes as k_step_reduce's, every node's moments go to the shared-memory column of the
-// one-node thread that would own it (t = row * bx + x offset), and each warp sums two of
-// the eight 32-column groups with the same shuffle tree, so the CTA records (and the
-// diagnostics) are bit-identical to k_step_reduce's.
+// nodes as k_step_reduce's and every node's moments go to the shared-memory column of the
+// one-node thread that would own it (t = row * bx + x offset = 2 * thread + 0 or 1), so warp
+// w holds exactly the 32-node groups 2w and 2w + 1 and sums them with the same shuffle
+// tree after a warp barrier only; the last warp to finish (a shared-memory counter) adds
+// the eight group sums in order.  The CTA records, and the diagnostics, are bit-identical
+// to k_step_reduce's on the same node tile, and no warp waits for the others' collision.
 template <typename T, int MINB, bool WALLS>
 __global__ void __launch_bounds__(128, MINB) k_step2_reduce(BlockView v, double* partials) {
   __shared__ float snm[8][6][32];
   __shared__ float swarp[8][6];
+  __shared__ unsigned done;
   const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   const int t = threadIdx.y * blockDim.x + threadIdx.x;
-  const int bx = 2 * blockDim.x;
-  const int t0 = threadIdx.y * bx + 2 * threadIdx.x, t1 = t0 + 1;
+  const int lane = t & 31, w = t >> 5;
+  const int t0 = 2 * t, t1 = t0 + 1;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     snm[t0 >> 5][i][t0 & 31] = 0.0f;
     snm[t1 >> 5][i][t1 & 31] = 0.0f;
   }
+  if (t == 0) done = 0u;
+  __syncthreads();                          // the counter is set before any warp counts
   const NodeMomentsOut out0{&snm[t0 >> 5][0][t0 & 31], 32};
   const NodeMomentsOut out1{&snm[t1 >> 5][0][t1 & 31], 32};
   if (x < v.nx && y < v.ny) {
@@ -80,10 +103,10 @@ __global__ void __launch_bounds__(128, MINB) k_step2_reduce(BlockView v, double*
       cell_update_pair<T, uint32_t, WALLS, true>(v, x, y, z, nullptr, 0, &out0, &out1);
     }
   }
-  __syncthreads();
-  const int lane = t & 31, w = t >> 5;
-  const int nv = (bx * blockDim.y + 31) >> 5;     // 32-node groups of the tile
-  for (int g = w; g < nv; g += (blockDim.x * blockDim.y + 31) >> 5) {
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int g = 2 * w + h;
     float val[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) val[i] = snm[g][i][lane];
@@ -96,14 +119,7 @@ __global__ void __launch_bounds__(128, MINB) k_step2_reduce(BlockView v, double*
       for (int i = 0; i < 6; ++i) swarp[g][i] = val[i];
     }
   }
-  __syncthreads();
-  if (t < 8) {
-    float s = 0.0f;
-    if (t < 6)
-      for (int k = 0; k < nv; ++k) s += swarp[k][t];
-    const size_t cta = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-    partials[cta * 8 + t] = (double)s;
-  }
+  finish_cta_record(swarp, done, lane, (blockDim.x * blockDim.y + 31) >> 5, 2, partials);
 }
 
 // records written by one k_step_reduce launch (one per CTA)
