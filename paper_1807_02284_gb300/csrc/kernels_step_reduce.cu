@@ -157,10 +157,12 @@ static void launch_step2_reduce_t(const BlockView& v, dim3 grid, dim3 block, int
 }
 
 // 32-bit indexing only (27 N < 2^32): the caller checks fits_32bit_index.  A two-node bound
-// code runs k_step2_reduce (same CTA grid and records) where the block allows pairs.
+// code runs k_step2_reduce (same CTA grid and records) where the block allows pairs and the
+// CTA is whole warps (its warp w owns the 32-node groups 2w and 2w + 1).
 cudaError_t launch_step_reduce(const BlockView& v, int storage, int bx, int by, cudaStream_t s,
                                int minb, double* partials, double* out, double* out5) {
-  if (step_is_pair(minb) && step_pair_ok(v, storage, bx, by) && bx * by <= 256) {
+  if (step_is_pair(minb) && step_pair_ok(v, storage, bx, by) && bx * by <= 256 &&
+      ((bx / 2) * by) % 32 == 0) {
     dim3 block(bx / 2, by, 1);
     dim3 grid((v.nx + bx - 1) / bx, (v.ny + by - 1) / by, v.nz);
     if (storage == ST_FP16) launch_step2_reduce_t<__half>(v, grid, block, minb - STEP_PAIR, partials, s);
