@@ -155,7 +155,8 @@ typedef struct {
                                per SM; blocks with an even x-extent) */
 } lbm_block_info;
 
-/* Version of this header's ABI. */
+/* Version of this header's ABI (5: lbm_block_info ends with nodes_per_thread; a caller built
+   against version 4 passes a smaller struct and must not call lbm_get_block_info). */
 int32_t lbm_abi_version(void);
 
 /* Fills *desc with the paper's defaults (a=-4, b=5, g_max=0.1, nu' table, adaptive on,

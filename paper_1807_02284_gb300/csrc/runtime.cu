@@ -192,7 +192,7 @@ const void* Domain::device_source(const void* src, size_t bytes, int on_device,
 
 extern "C" {
 
-int32_t lbm_abi_version(void) { return 4; }
+int32_t lbm_abi_version(void) { return 5; }
 
 lbm_status lbm_default_desc(lbm_domain_desc* d) {
   if (!d) return LBM_ERR_INVALID_ARG;

@@ -116,10 +116,12 @@ LBM_BOX_PRIOR_SOURCE, LBM_BOX_POST_TARGET = 0, 1
 LBM_LEVEL_CURRENT, LBM_LEVEL_START = 0, 1
 
 _lib = None
+ABI_VERSION = 5      # lbm_abi_version() of the include/lbm.h these structs mirror
 
 
 def load(path: str = LIB_PATH):
-    """Loads the built CUDA library (raises if it has not been built)."""
+    """Loads the built CUDA library (raises if it has not been built, or was built from
+    another version of the ABI than the structs declared here)."""
     global _lib
     if _lib is not None:
         return _lib
@@ -131,6 +133,9 @@ def load(path: str = LIB_PATH):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    if lib.lbm_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"{path} has ABI version {lib.lbm_abi_version()}, the binding "
+                           f"expects {ABI_VERSION}: rebuild the library")
     _lib = lib
     return lib
 

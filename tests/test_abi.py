@@ -49,7 +49,7 @@ def test_library_exports_every_declared_symbol(built):
 def test_library_loads_and_validates_on_host(built):
     from paper_1807_02284_gb300 import lbm
     lib = lbm.load()
-    assert lib.lbm_abi_version() == 4
+    assert lib.lbm_abi_version() == 5
     d = lbm.lbm_domain_desc()
     assert lib.lbm_default_desc(C.byref(d)) == lbm.LBM_OK
     assert (d.a, d.b, d.g_max) == (-4.0, 5.0, 0.1)
